@@ -1,0 +1,848 @@
+// Oracle: plain, slow FP64 CPU implementation of the AMR ideal-MHD advance of
+// every patch on every refinement level with extended ghost zones.
+//
+// TEST INFRASTRUCTURE ONLY. Only tests/, the smoke check and the CPU-baseline
+// leg of the benchmark may build, load or call this code; the product path
+// (the CUDA library and its binding) never does, and shares no code with it.
+//
+// What it computes, and where that comes from:
+//  * Patches, levels, ratio R = 2, nesting of every level above 0 inside the
+//    next coarser one (Sec. 2).
+//  * Levels advance in the recursive order 0,1,2,2,1,2,2 with the operations
+//    (P)rolongate, (A)dvance, (S)ynchronize = reflux, (R)estrict (Sec. 4).
+//  * Extended ghost zones decouple the levels (Abstract, Sec. 1): the ghost
+//    shell of width 4 = R x reach 2 of a level above 0 is prolonged once per
+//    parent step from the parent's state at the start of that step; sub-step 1
+//    updates the interior plus 2 ghost layers, sub-step 2 the interior.
+//    Same-level ghosts are refreshed before every sub-step (reading R7).
+//  * The per-cell numerics (not in the paper) follow readings R1-R5 in
+//    mhd_core.hpp; prolongation, reflux, restriction and CFL follow R6-R9.
+//
+// Representation: unlike the patch-based product path, each level is one
+// array over the whole periodic domain at that level's resolution. The
+// level's region is the union of its patch interiors; a cell's ghost value in
+// any patch is either another patch's interior value or a prolonged value, both
+// of which are the single global value here, so the union of all patches'
+// ghosted boxes behaves exactly like the band of width 4 around the region.
+// This keeps the oracle free of any patch bookkeeping.
+//
+// Only periodic boundaries are implemented.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "mhd_core.hpp"
+
+namespace oracle {
+
+static const int G = 4;  // ghost width
+
+struct Patch { int level, lo[3], hi[3]; };
+
+struct Level {
+  int N[3] = {1, 1, 1};  // cells per dimension
+  double dx[3] = {1, 1, 1}, idx[3] = {1, 1, 1};
+  size_t ncell = 0;
+  std::vector<double> u[NFIELD];      // cell fields and face fields, index (k*Ny + j)*Nx + i
+  std::vector<double> start[NFIELD];  // state at the start of the latest sub-step
+  std::vector<int8_t> dist;           // Chebyshev distance to the region, -1 if > 4
+  std::vector<int8_t> cov;            // cell covered by the next finer level
+  // work arrays
+  std::vector<double> W[NFIELD], Wh[NFIELD], S[3][NFIELD], ref[3], F[3][NFIELD], E[3];
+  std::vector<int8_t> tmask;          // target distance map used by one advance
+  // registers of this level's C/F boundary with its parent (indexed on the parent level)
+  std::vector<double> rflux[3][NFIELD];    // per parent face: fine time-integrated flux (S1 + S2)
+  std::vector<double> rcoarse[3][NFIELD];  // per parent face: coarse time-integrated flux C
+  std::vector<double> remf[3], remfc[3];   // the same for the EMF of parent edges
+  std::vector<int8_t> cf_face[3], cf_edge[3];
+};
+
+struct Sim {
+  int dim = 2;
+  int base[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  double gamma = 5.0 / 3.0, cfl = 0.4;
+  double eps = 1e-12;
+  int nlev = 1;
+  std::vector<Patch> patches;
+  std::vector<Level> lev;
+  long long cell_updates = 0;
+  int flags = 0;  // test-only switches: bit 0 skips the cell reflux (a planted
+                  // mistake); bit 1 replaces minmod by the unlimited centred slope
+};
+
+// ---------------------------------------------------------------- indexing
+static inline int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+static inline size_t at(const Level& L, int i, int j, int k) {
+  return ((size_t)wrapi(k, L.N[2]) * L.N[1] + wrapi(j, L.N[1])) * L.N[0] + wrapi(i, L.N[0]);
+}
+static inline size_t atd(const Level& L, int i, int j, int k, int d, int s) {
+  int o[3] = {i, j, k};
+  o[d] += s;
+  return at(L, o[0], o[1], o[2]);
+}
+template <class F> static void for_cells(const Level& L, F f) {
+  for (int k = 0; k < L.N[2]; ++k)
+    for (int j = 0; j < L.N[1]; ++j)
+      for (int i = 0; i < L.N[0]; ++i) f(i, j, k);
+}
+
+// Cell-field list: in 3D rho, m, E; in 2D also Bz, which is cell-centred and
+// advanced by its fluxes there.
+static int cell_fields(const Sim& S, int* f) {
+  int n = 0;
+  f[n++] = RHO; f[n++] = MX; f[n++] = MY; f[n++] = MZ; f[n++] = EN;
+  if (S.dim == 2) f[n++] = BZ;
+  return n;
+}
+static inline bool is_face_field(const Sim& S, int f) { return f == BX || f == BY || (f == BZ && S.dim == 3); }
+
+// Chebyshev dilation of a distance map (0 = seed) up to 4, with periodic wrap.
+static void dilate(const Sim& S, const Level& L, std::vector<int8_t>& d) {
+  const int kz = S.dim == 3 ? 1 : 0;
+  for (int r = 1; r <= G; ++r) {
+    std::vector<int8_t> nd = d;
+    for_cells(L, [&](int i, int j, int k) {
+      size_t q = at(L, i, j, k);
+      if (d[q] >= 0) return;
+      for (int c = -kz; c <= kz; ++c)
+        for (int b = -1; b <= 1; ++b)
+          for (int a = -1; a <= 1; ++a)
+            if (d[at(L, i + a, j + b, k + c)] == r - 1) { nd[q] = (int8_t)r; return; }
+    });
+    d.swap(nd);
+  }
+}
+
+// ---------------------------------------------------------------- setup
+static int validate_and_build(Sim& S) {
+  // Sec. 2: levels l>0 nested in level l-1 with ratio 2; patches aligned to
+  // parent cells; no same-level overlap; level 0 tiles the domain.
+  S.lev.assign(S.nlev, Level());
+  for (int l = 0; l < S.nlev; ++l) {
+    Level& L = S.lev[l];
+    for (int d = 0; d < 3; ++d) {
+      L.N[d] = d < S.dim ? (S.base[d] << l) : 1;
+      L.dx[d] = d < S.dim ? (S.hi[d] - S.lo[d]) / L.N[d] : 1.0;
+      L.idx[d] = 1.0 / L.dx[d];
+    }
+    L.ncell = (size_t)L.N[0] * L.N[1] * L.N[2];
+    for (int f = 0; f < NFIELD; ++f) { L.u[f].assign(L.ncell, 0.0); L.start[f].assign(L.ncell, 0.0); }
+    L.dist.assign(L.ncell, -1);
+    L.cov.assign(L.ncell, 0);
+  }
+  for (const Patch& p : S.patches) {
+    if (p.level < 0 || p.level >= S.nlev) return -1;
+    Level& L = S.lev[p.level];
+    for (int d = 0; d < 3; ++d) {
+      int lo = p.lo[d], hi = p.hi[d];
+      if (d >= S.dim) { if (lo != 0 || hi != 1) return -1; continue; }
+      if (lo < 0 || hi > L.N[d] || hi <= lo) return -1;
+      if (p.level > 0 && ((lo & 1) || (hi & 1))) return -1;
+    }
+    for (int k = p.lo[2]; k < p.hi[2]; ++k)
+      for (int j = p.lo[1]; j < p.hi[1]; ++j)
+        for (int i = p.lo[0]; i < p.hi[0]; ++i) {
+          size_t q = at(L, i, j, k);
+          if (L.dist[q] == 0) return -3;  // same-level overlap
+          L.dist[q] = 0;
+        }
+  }
+  for (size_t q = 0; q < S.lev[0].ncell; ++q)
+    if (S.lev[0].dist[q] != 0) return -1;  // level 0 must tile the domain
+  for (int l = 1; l < S.nlev; ++l) {
+    Level& F = S.lev[l];
+    Level& C = S.lev[l - 1];
+    // covered coarse cells and proper nesting (R11): every coarse cell within
+    // Chebyshev distance 3 of a covered cell lies in the coarse region.
+    for_cells(F, [&](int i, int j, int k) {
+      if (F.dist[at(F, i, j, k)] == 0) C.cov[at(C, i >> 1, j >> 1, k >> 1)] = 1;
+    });
+    bool ok = true;
+    const int kz = S.dim == 3 ? 3 : 0;
+    for_cells(C, [&](int i, int j, int k) {
+      if (!C.cov[at(C, i, j, k)]) return;
+      for (int c = -kz; c <= kz; ++c)
+        for (int b = -3; b <= 3; ++b)
+          for (int a = -3; a <= 3; ++a)
+            if (C.dist[at(C, i + a, j + b, k + c)] != 0) ok = false;
+    });
+    if (!ok) return -2;
+  }
+  for (int l = 0; l < S.nlev; ++l) dilate(S, S.lev[l], S.lev[l].dist);
+  // C/F faces and edges of level l (>0) on its parent level.
+  for (int l = 1; l < S.nlev; ++l) {
+    Level& F = S.lev[l];
+    Level& C = S.lev[l - 1];
+    for (int d = 0; d < 3; ++d) {
+      F.cf_face[d].assign(C.ncell, 0);
+      F.cf_edge[d].assign(C.ncell, 0);
+      for (int f = 0; f < NFIELD; ++f) { F.rflux[d][f].assign(C.ncell, 0.0); F.rcoarse[d][f].assign(C.ncell, 0.0); }
+      F.remf[d].assign(C.ncell, 0.0);
+      F.remfc[d].assign(C.ncell, 0.0);
+    }
+    for_cells(C, [&](int i, int j, int k) {
+      size_t q = at(C, i, j, k);
+      for (int d = 0; d < S.dim; ++d)
+        if (C.cov[atd(C, i, j, k, d, -1)] != C.cov[q]) F.cf_face[d][q] = 1;
+      // edges along c with the (a,b) plane: 4 surrounding cells
+      for (int c = 0; c < 3; ++c) {
+        if (S.dim == 2 && c != 2) continue;
+        int a = (c + 1) % 3, b = (c + 2) % 3;
+        int o[3] = {i, j, k};
+        int n = 0;
+        for (int sb = -1; sb <= 0; ++sb)
+          for (int sa = -1; sa <= 0; ++sa) {
+            int p[3] = {o[0], o[1], o[2]};
+            p[a] += sa; p[b] += sb;
+            n += C.cov[at(C, p[0], p[1], p[2])];
+          }
+        if (n >= 1 && n <= 3) F.cf_edge[c][q] = 1;
+      }
+    });
+  }
+  return 0;
+}
+
+static void alloc_work(const Sim& S, Level& L) {
+  if (L.W[0].size() == L.ncell) return;
+  for (int f = 0; f < NFIELD; ++f) {
+    L.W[f].assign(L.ncell, 0.0); L.Wh[f].assign(L.ncell, 0.0);
+    for (int d = 0; d < 3; ++d) { L.S[d][f].assign(L.ncell, 0.0); L.F[d][f].assign(L.ncell, 0.0); }
+  }
+  for (int d = 0; d < 3; ++d) { L.ref[d].assign(L.ncell, 0.0); L.E[d].assign(L.ncell, 0.0); }
+  (void)S;
+}
+
+// ---------------------------------------------------------------- advance
+static inline void cell_bc(const Sim& S, const Level& L, int i, int j, int k, double* bc) {
+  size_t q = at(L, i, j, k);
+  bc[0] = 0.5 * (L.u[BX][q] + L.u[BX][atd(L, i, j, k, 0, 1)]);
+  bc[1] = 0.5 * (L.u[BY][q] + L.u[BY][atd(L, i, j, k, 1, 1)]);
+  bc[2] = S.dim == 3 ? 0.5 * (L.u[BZ][q] + L.u[BZ][atd(L, i, j, k, 2, 1)]) : L.u[BZ][q];
+}
+
+static void prim_at(const Sim& S, const Level& L, int i, int j, int k, double* w) {
+  size_t q = at(L, i, j, k);
+  double u[5] = {L.u[RHO][q], L.u[MX][q], L.u[MY][q], L.u[MZ][q], L.u[EN][q]};
+  double bc[3];
+  cell_bc(S, L, i, j, k, bc);
+  cons_to_prim(u, bc, S.gamma - 1.0, w);
+}
+
+// One level update with time step dt of the target cell set T = {dist_t <= 0}
+// where dist_t is L.tmask (Chebyshev distance to the target, -1 beyond 4):
+// W on T+2, predictor on T+1, fluxes between T+1 cells, EMFs at edges whose 4
+// cells are in T+1, then cells of T and faces touching T are updated.
+static void advance_masked(Sim& S, Level& L, double dt) {
+  alloc_work(S, L);
+  const int dim = S.dim;
+  const std::vector<int8_t>& tm = L.tmask;
+  auto in = [&](size_t q, int r) { return tm[q] >= 0 && tm[q] <= r; };
+  const double gamma = S.gamma;
+  // primitives
+  for_cells(L, [&](int i, int j, int k) {
+    size_t q = at(L, i, j, k);
+    if (!in(q, 2)) return;
+    double w[8];
+    prim_at(S, L, i, j, k, w);
+    for (int f = 0; f < 8; ++f) L.W[f][q] = w[f];
+  });
+  // slopes and half-step predictor (R1, R2)
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = 0.5 * dt * L.idx[d];
+  for_cells(L, [&](int i, int j, int k) {
+    size_t q = at(L, i, j, k);
+    if (!in(q, 1)) return;
+    double w[8], s[3][8];
+    for (int f = 0; f < 8; ++f) w[f] = L.W[f][q];
+    for (int d = 0; d < dim; ++d) {
+      size_t qm = atd(L, i, j, k, d, -1), qp = atd(L, i, j, k, d, 1);
+      for (int f = 0; f < 8; ++f) {
+        if (f == BX + d) s[d][f] = L.u[BX + d][qp] - L.u[BX + d][q];
+        else if (S.flags & 2) s[d][f] = 0.5 * ((w[f] - L.W[f][qm]) + (L.W[f][qp] - w[f]));
+        else s[d][f] = minmod(w[f] - L.W[f][qm], L.W[f][qp] - w[f]);
+        L.S[d][f][q] = s[d][f];
+      }
+    }
+    double ir = 1.0 / w[0];
+    double wh[8];
+    for (int f = 0; f < 8; ++f) wh[f] = w[f];
+    for (int d = 0; d < dim; ++d) {
+      double dw[8];
+      prim_rhs(w, s[d], d, gamma, ir, dw);
+      for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h[d] * dw[f];
+    }
+    for (int f = 0; f < 8; ++f) L.Wh[f][q] = wh[f];
+    // cell-centre reference EMF -(v x B) at the half step (R5)
+    L.ref[0][q] = wh[3] * wh[6] - wh[2] * wh[7];
+    L.ref[1][q] = wh[1] * wh[7] - wh[3] * wh[5];
+    L.ref[2][q] = wh[2] * wh[5] - wh[1] * wh[6];
+  });
+  // HLLD fluxes at d-faces (R3, R4); face stored at the cell on its high side
+  for (int d = 0; d < dim; ++d) {
+    const int t = (d + 1) % 3, u = (d + 2) % 3;
+    for_cells(L, [&](int i, int j, int k) {
+      size_t qr = at(L, i, j, k), ql = atd(L, i, j, k, d, -1);
+      if (!in(qr, 1) || !in(ql, 1)) return;
+      double wl[8], wr[8];
+      for (int f = 0; f < 8; ++f) {
+        wl[f] = L.Wh[f][ql] + 0.5 * L.S[d][f][ql];
+        wr[f] = L.Wh[f][qr] - 0.5 * L.S[d][f][qr];
+      }
+      double bn = 0.5 * (wl[5 + d] + wr[5 + d]);
+      double rl[7] = {wl[0], wl[1 + d], wl[1 + t], wl[1 + u], wl[4], wl[5 + t], wl[5 + u]};
+      double rr[7] = {wr[0], wr[1 + d], wr[1 + t], wr[1 + u], wr[4], wr[5 + t], wr[5 + u]};
+      double fr[7];
+      hlld(rl, rr, bn, gamma, S.eps, fr);
+      L.F[d][RHO][qr] = fr[0];
+      L.F[d][MX + d][qr] = fr[1];
+      L.F[d][MX + t][qr] = fr[2];
+      L.F[d][MX + u][qr] = fr[3];
+      L.F[d][EN][qr] = fr[4];
+      L.F[d][BX + t][qr] = fr[5];
+      L.F[d][BX + u][qr] = fr[6];
+      L.F[d][BX + d][qr] = 0.0;
+    });
+  }
+  // edge EMFs (R5): E_c at the edge (a-1/2, b-1/2), stored at cell (a, b)
+  for (int c = 0; c < 3; ++c) {
+    if (dim == 2 && c != 2) continue;
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    for_cells(L, [&](int i, int j, int k) {
+      size_t q11 = at(L, i, j, k);
+      size_t q01 = atd(L, i, j, k, a, -1);
+      size_t q10 = atd(L, i, j, k, b, -1);
+      int o[3] = {i, j, k};
+      o[a] -= 1; o[b] -= 1;
+      size_t q00 = at(L, o[0], o[1], o[2]);
+      if (!in(q11, 1) || !in(q01, 1) || !in(q10, 1) || !in(q00, 1)) return;
+      // E_c on an a-face is -F_a[B_b]; on a b-face it is +F_b[B_a].
+      double ea_hi = -L.F[a][BX + b][q11], ea_lo = -L.F[a][BX + b][q10];
+      double eb_hi = L.F[b][BX + a][q11], eb_lo = L.F[b][BX + a][q01];
+      L.E[c][q11] = gs_edge_emf(ea_lo, ea_hi, eb_lo, eb_hi, L.ref[c][q00], L.ref[c][q10],
+                                L.ref[c][q01], L.ref[c][q11], L.F[a][RHO][q10], L.F[a][RHO][q11],
+                                L.F[b][RHO][q01], L.F[b][RHO][q11]);
+    });
+  }
+  // updates: new values into Wh storage reused as the output buffer
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  double dtd[3];
+  for (int d = 0; d < 3; ++d) dtd[d] = dt * L.idx[d];
+  std::vector<double> nu[NFIELD];
+  for (int f = 0; f < NFIELD; ++f) nu[f] = L.u[f];
+  for_cells(L, [&](int i, int j, int k) {
+    size_t q = at(L, i, j, k);
+    // cell update
+    if (in(q, 0)) {
+      if (L.dist[q] == 0) S.cell_updates++;
+      for (int n = 0; n < ncf; ++n) {
+        int f = cf[n];
+        double v = L.u[f][q];
+        for (int d = 0; d < dim; ++d) v = v - dtd[d] * (L.F[d][f][atd(L, i, j, k, d, 1)] - L.F[d][f][q]);
+        nu[f][q] = v;
+      }
+    }
+    // face updates: d-face stored at q (between q-e_d and q)
+    for (int d = 0; d < dim; ++d) {
+      size_t qm = atd(L, i, j, k, d, -1);
+      if (!in(q, 0) && !in(qm, 0)) continue;
+      double v = L.u[BX + d][q];
+      if (dim == 2) {
+        if (d == 0) v = v - dtd[1] * (L.E[2][atd(L, i, j, k, 1, 1)] - L.E[2][q]);
+        else        v = v + dtd[0] * (L.E[2][atd(L, i, j, k, 0, 1)] - L.E[2][q]);
+      } else {
+        if (d == 0) {
+          v = v - dtd[1] * (L.E[2][atd(L, i, j, k, 1, 1)] - L.E[2][q]);
+          v = v + dtd[2] * (L.E[1][atd(L, i, j, k, 2, 1)] - L.E[1][q]);
+        } else if (d == 1) {
+          v = v - dtd[2] * (L.E[0][atd(L, i, j, k, 2, 1)] - L.E[0][q]);
+          v = v + dtd[0] * (L.E[2][atd(L, i, j, k, 0, 1)] - L.E[2][q]);
+        } else {
+          v = v - dtd[0] * (L.E[1][atd(L, i, j, k, 0, 1)] - L.E[1][q]);
+          v = v + dtd[1] * (L.E[0][atd(L, i, j, k, 1, 1)] - L.E[0][q]);
+        }
+      }
+      nu[BX + d][q] = v;
+    }
+  });
+  for (int f = 0; f < NFIELD; ++f) L.u[f].swap(nu[f]);
+}
+
+// ---------------------------------------------------------------- prolongation (R8)
+// Conserved cell fields: minmod-limited linear, children average to the parent.
+// Face B: fine faces on coarse faces = coarse face + minmod transverse slopes;
+// fine faces inside a coarse cell from the divergence-free quadratic
+// reconstruction (Balsara 2001): mean of the two bracketing fine faces plus
+// (dx_n/8) sum over the transverse t of (d/dn-slope of B_t on the high t-face
+// - the same on the low t-face) / dx_t.
+static double prolong_cell(const Sim& S, const Level& C, int f, int ci, int cj, int ck, int oa, int ob, int oc) {
+  const std::vector<double>& u = C.start[f];
+  size_t q = at(C, ci, cj, ck);
+  double v = u[q];
+  const int off[3] = {oa, ob, oc};
+  double r = u[q];
+  for (int d = 0; d < S.dim; ++d) {
+    double sl = minmod(u[q] - u[atd(C, ci, cj, ck, d, -1)], u[atd(C, ci, cj, ck, d, 1)] - u[q]);
+    r = r + sl * (off[d] ? 0.25 : -0.25);
+  }
+  (void)v;
+  return r;
+}
+
+// Fine value of B_n on the coarse n-face stored at coarse cell (ci,cj,ck),
+// at the fine sub-face with transverse offsets given by fine parities.
+static double prolong_coincident(const Sim& S, const Level& C, int n, int ci, int cj, int ck, const int* par) {
+  const std::vector<double>& b = C.start[BX + n];
+  size_t q = at(C, ci, cj, ck);
+  double v = b[q];
+  for (int d = 0; d < S.dim; ++d) {
+    if (d == n) continue;
+    double sl = minmod(b[q] - b[atd(C, ci, cj, ck, d, -1)], b[atd(C, ci, cj, ck, d, 1)] - b[q]);
+    v = v + sl * (par[d] ? 0.25 : -0.25);
+  }
+  return v;
+}
+
+// Transverse slope along direction d of B_t on the coarse t-face stored at (ci,cj,ck).
+static double face_slope(const Level& C, int t, int d, int ci, int cj, int ck) {
+  const std::vector<double>& b = C.start[BX + t];
+  size_t q = at(C, ci, cj, ck);
+  return minmod(b[q] - b[atd(C, ci, cj, ck, d, -1)], b[atd(C, ci, cj, ck, d, 1)] - b[q]);
+}
+
+// Fine n-face at fine index (fi,fj,fk) (position fi-1/2 etc. along n).
+static double prolong_face(const Sim& S, const Level& C, const Level& F, int n, int fi, int fj, int fk) {
+  int fidx[3] = {fi, fj, fk};
+  int cidx[3], par[3];
+  for (int d = 0; d < 3; ++d) {
+    if (d < S.dim) { cidx[d] = fidx[d] >> 1; par[d] = fidx[d] & 1; }
+    else { cidx[d] = 0; par[d] = 0; }
+  }
+  if (!par[n]) return prolong_coincident(S, C, n, cidx[0], cidx[1], cidx[2], par);
+  // interior face of coarse cell cidx: bracketing coincident fine faces
+  int hi[3] = {cidx[0], cidx[1], cidx[2]};
+  hi[n] += 1;
+  double lo_v = prolong_coincident(S, C, n, cidx[0], cidx[1], cidx[2], par);
+  double hi_v = prolong_coincident(S, C, n, hi[0], hi[1], hi[2], par);
+  double corr = 0.0;
+  for (int t = 0; t < S.dim; ++t) {
+    if (t == n) continue;
+    int th[3] = {cidx[0], cidx[1], cidx[2]};
+    th[t] += 1;
+    double s_hi = face_slope(C, t, n, th[0], th[1], th[2]);
+    double s_lo = face_slope(C, t, n, cidx[0], cidx[1], cidx[2]);
+    corr = corr + (C.dx[n] / C.dx[t]) * (s_hi - s_lo);
+  }
+  (void)F;
+  return 0.5 * (lo_v + hi_v) + 0.125 * corr;
+}
+
+// P: fill the band (1 <= dist <= 4) of level l from level l-1's start state.
+static void prolong_band(Sim& S, int l) {
+  Level& F = S.lev[l];
+  const Level& C = S.lev[l - 1];
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  for_cells(F, [&](int i, int j, int k) {
+    size_t q = at(F, i, j, k);
+    int8_t dd = F.dist[q];
+    if (dd >= 1) {
+      for (int n = 0; n < ncf; ++n)
+        F.u[cf[n]][q] = prolong_cell(S, C, cf[n], i >> 1, j >> 1, S.dim == 3 ? k >> 1 : 0, i & 1, j & 1, S.dim == 3 ? (k & 1) : 0);
+    }
+    // d-face between q-e_d and q: band face if not owned (no adjacent region
+    // cell) and adjacent to a band cell
+    for (int d = 0; d < S.dim; ++d) {
+      size_t qm = atd(F, i, j, k, d, -1);
+      int8_t dm = F.dist[qm];
+      if (dd == 0 || dm == 0) continue;
+      if (dd < 0 && dm < 0) continue;
+      F.u[BX + d][q] = prolong_face(S, C, F, d, i, j, k);
+    }
+  });
+}
+
+// ---------------------------------------------------------------- registers, reflux, restriction (R9)
+static void record_coarse_registers(Sim& S, int l, double dt) {
+  Level& C = S.lev[l];
+  Level& F = S.lev[l + 1];
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  for (int d = 0; d < S.dim; ++d)
+    for (size_t q = 0; q < C.ncell; ++q) {
+      if (!F.cf_face[d][q]) continue;
+      for (int n = 0; n < ncf; ++n) { F.rflux[d][cf[n]][q] = 0.0; F.rcoarse[d][cf[n]][q] = dt * C.F[d][cf[n]][q]; }
+    }
+  for (int c = 0; c < 3; ++c) {
+    if (S.dim == 2 && c != 2) continue;
+    for (size_t q = 0; q < C.ncell; ++q)
+      if (F.cf_edge[c][q]) { F.remf[c][q] = 0.0; F.remfc[c][q] = dt * C.E[c][q]; }
+  }
+}
+
+// Pairwise sum of 2, 4 or 8 values in the given order: ((v0+v1)+(v2+v3))+...
+// (R9: exact for equal values, so uniform states stay bitwise uniform).
+static double tree_sum(const double* v, int n) {
+  if (n == 1) return v[0];
+  if (n == 2) return v[0] + v[1];
+  if (n == 4) return (v[0] + v[1]) + (v[2] + v[3]);
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+}
+
+// Fine side of the registers after one fine sub-step of dt: per C/F coarse
+// face R += (dt 2^-(dim-1)) * tree_sum(fine sub-face fluxes in z,y,x order);
+// per C/F coarse edge R += (dt 2^-(dim-2)) * tree_sum(fine sub-edges along it).
+static void add_fine_registers(Sim& S, int l, double dt) {
+  Level& F = S.lev[l];
+  Level& C = S.lev[l - 1];
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  const double af = dt * (S.dim == 3 ? 0.25 : 0.5);
+  const double ae = dt * (S.dim == 3 ? 0.5 : 1.0);
+  for_cells(C, [&](int i, int j, int k) {
+    size_t q = at(C, i, j, k);
+    for (int d = 0; d < S.dim; ++d) {
+      if (!F.cf_face[d][q]) continue;
+      size_t qf[4];
+      int m = 0;
+      for (int c2 = 0; c2 < 2; ++c2)
+        for (int c1 = 0; c1 < 2; ++c1)
+          for (int c0 = 0; c0 < 2; ++c0) {
+            int o[3] = {c0, c1, c2};
+            if (o[d] != 0) continue;
+            if (S.dim == 2 && c2 != 0) continue;
+            qf[m++] = at(F, 2 * i + o[0], 2 * j + o[1], S.dim == 3 ? 2 * k + o[2] : 0);
+          }
+      for (int n = 0; n < ncf; ++n) {
+        double v[4];
+        for (int s = 0; s < m; ++s) v[s] = F.F[d][cf[n]][qf[s]];
+        F.rflux[d][cf[n]][q] += af * tree_sum(v, m);
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      if (S.dim == 2 && c != 2) continue;
+      if (!F.cf_edge[c][q]) continue;
+      int nsub = S.dim == 3 ? 2 : 1;
+      double v[2];
+      for (int sidx = 0; sidx < nsub; ++sidx) {
+        int o[3] = {2 * i, 2 * j, S.dim == 3 ? 2 * k : 0};
+        o[c] += sidx;
+        v[sidx] = F.E[c][at(F, o[0], o[1], o[2])];
+      }
+      F.remf[c][q] += ae * tree_sum(v, nsub);
+    }
+  });
+}
+
+static void restrict_cell(const Sim& S, Level& C, const Level& F, int i, int j, int k, double wc) {
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  const int kz = S.dim == 3 ? 2 : 1;
+  size_t q = at(C, i, j, k);
+  for (int n = 0; n < ncf; ++n) {
+    double v[8];
+    int m = 0;
+    for (int c = 0; c < kz; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) v[m++] = F.u[cf[n]][at(F, 2 * i + a, 2 * j + b, S.dim == 3 ? 2 * k + c : 0)];
+    C.u[cf[n]][q] = tree_sum(v, m) * wc;
+  }
+}
+
+static void restrict_face(const Sim& S, Level& C, const Level& F, int d, int i, int j, int k, double wf) {
+  const int kz = S.dim == 3 ? 2 : 1;
+  double v[4];
+  int m = 0;
+  for (int c = 0; c < kz; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        int o[3] = {a, b, c};
+        if (o[d] != 0) continue;
+        v[m++] = F.u[BX + d][at(F, 2 * i + o[0], 2 * j + o[1], S.dim == 3 ? 2 * k + o[2] : 0)];
+      }
+  C.u[BX + d][at(C, i, j, k)] = tree_sum(v, m) * wf;
+}
+
+static void reflux_and_restrict(Sim& S, int l) {
+  // level l is the fine level; corrections go to level l-1
+  Level& F = S.lev[l];
+  Level& C = S.lev[l - 1];
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  // S: cell reflux on uncovered coarse cells, faces in order x-,x+,y-,y+,z-,z+
+  for_cells(C, [&](int i, int j, int k) {
+    size_t q = at(C, i, j, k);
+    if (C.cov[q] || (S.flags & 1)) return;
+    for (int d = 0; d < S.dim; ++d) {
+      size_t qlo = q, qhi = atd(C, i, j, k, d, 1);
+      if (F.cf_face[d][qlo])
+        for (int n = 0; n < ncf; ++n)
+          C.u[cf[n]][q] = C.u[cf[n]][q] + (F.rflux[d][cf[n]][qlo] - F.rcoarse[d][cf[n]][qlo]) * C.idx[d];
+      if (F.cf_face[d][qhi])
+        for (int n = 0; n < ncf; ++n)
+          C.u[cf[n]][q] = C.u[cf[n]][q] - (F.rflux[d][cf[n]][qhi] - F.rcoarse[d][cf[n]][qhi]) * C.idx[d];
+    }
+  });
+  // EMF correction on uncovered coarse faces adjacent to C/F edges
+  for_cells(C, [&](int i, int j, int k) {
+    size_t q = at(C, i, j, k);
+    for (int d = 0; d < S.dim; ++d) {
+      size_t qm = atd(C, i, j, k, d, -1);
+      if (C.cov[q] || C.cov[qm]) continue;
+      double v = C.u[BX + d][q];
+      auto add = [&](int c, size_t qe, double coef) {
+        if (F.cf_edge[c][qe]) v = v + coef * (F.remf[c][qe] - F.remfc[c][qe]);
+      };
+      if (S.dim == 2) {
+        if (d == 0) { add(2, q, C.idx[1]); add(2, atd(C, i, j, k, 1, 1), -C.idx[1]); }
+        else        { add(2, q, -C.idx[0]); add(2, atd(C, i, j, k, 0, 1), C.idx[0]); }
+      } else if (d == 0) {
+        add(2, q, C.idx[1]); add(2, atd(C, i, j, k, 1, 1), -C.idx[1]);
+        add(1, q, -C.idx[2]); add(1, atd(C, i, j, k, 2, 1), C.idx[2]);
+      } else if (d == 1) {
+        add(0, q, C.idx[2]); add(0, atd(C, i, j, k, 2, 1), -C.idx[2]);
+        add(2, q, -C.idx[0]); add(2, atd(C, i, j, k, 0, 1), C.idx[0]);
+      } else {
+        add(1, q, C.idx[0]); add(1, atd(C, i, j, k, 0, 1), -C.idx[0]);
+        add(0, q, -C.idx[1]); add(0, atd(C, i, j, k, 1, 1), C.idx[1]);
+      }
+      C.u[BX + d][q] = v;
+    }
+  });
+  // R: restriction of covered cells and of faces in the closure of the fine
+  // region: pairwise sums in z,y,x child order times 2^-dim (2^-(dim-1)).
+  const double wc = S.dim == 3 ? 0.125 : 0.25;
+  const double wf = S.dim == 3 ? 0.25 : 0.5;
+  for_cells(C, [&](int i, int j, int k) {
+    size_t q = at(C, i, j, k);
+    if (C.cov[q]) restrict_cell(S, C, F, i, j, k, wc);
+    for (int d = 0; d < S.dim; ++d) {
+      size_t qm = atd(C, i, j, k, d, -1);
+      if (!C.cov[q] && !C.cov[qm]) continue;
+      restrict_face(S, C, F, d, i, j, k, wf);
+    }
+  });
+}
+
+// ---------------------------------------------------------------- CFL (R6)
+static double level_rate(const Sim& S, const Level& L) {
+  double m = 0.0;
+  for_cells(L, [&](int i, int j, int k) {
+    size_t q = at(L, i, j, k);
+    if (L.dist[q] != 0) return;
+    double w[8];
+    prim_at(S, L, i, j, k, w);
+    if (!(w[0] > 0.0) || !(w[4] > 0.0)) { m = NAN; return; }
+    double r = 0.0;
+    for (int d = 0; d < S.dim; ++d) {
+      int t = (d + 1) % 3, u = (d + 2) % 3;
+      double cf = fast_speed(w[0], w[4], w[5 + d], w[5 + t], w[5 + u], S.gamma);
+      r = r + (fabs(w[1 + d]) + cf) * L.idx[d];
+    }
+    if (std::isnan(m)) return;
+    if (std::isnan(r)) m = NAN;
+    else if (r > m) m = r;
+  });
+  return m;
+}
+
+static double cfl_dt(const Sim& S) {
+  double mmax = 0.0;
+  double scale = 1.0;
+  for (int l = 0; l < S.nlev; ++l) {
+    double m = level_rate(S, S.lev[l]) * scale;
+    if (std::isnan(m)) return NAN;
+    if (m > mmax) mmax = m;
+    scale *= 0.5;
+  }
+  return S.cfl / mmax;
+}
+
+// ---------------------------------------------------------------- recursion (Sec. 4)
+static void level_substep(Sim& S, int l, int s, double dt) {
+  Level& L = S.lev[l];
+  const int w = (l == 0) ? 0 : (s == 1 ? 2 : 0);
+  if (l > 0 && s == 1) prolong_band(S, l);  // P
+  for (int f = 0; f < NFIELD; ++f) L.start[f] = L.u[f];
+  L.tmask.assign(L.ncell, -1);
+  for (size_t q = 0; q < L.ncell; ++q)
+    if (L.dist[q] >= 0 && L.dist[q] <= w) L.tmask[q] = 0;
+  dilate(S, L, L.tmask);
+  advance_masked(S, L, dt);  // A
+  if (l > 0) add_fine_registers(S, l, dt);
+  if (l + 1 < S.nlev) {
+    record_coarse_registers(S, l, dt);
+    level_substep(S, l + 1, 1, dt * 0.5);
+    level_substep(S, l + 1, 2, dt * 0.5);
+    reflux_and_restrict(S, l + 1);  // S and R
+  }
+}
+
+}  // namespace oracle
+
+// ================================================================ C API
+using namespace oracle;
+
+extern "C" {
+
+void* oc_new(int dim, const int* base, const double* lo, const double* hi, int nlev, double gamma, double cfl) {
+  Sim* s = new Sim();
+  s->dim = dim;
+  for (int d = 0; d < 3; ++d) {
+    s->base[d] = d < dim ? base[d] : 1;
+    s->lo[d] = lo[d];
+    s->hi[d] = hi[d];
+  }
+  s->nlev = nlev;
+  s->gamma = gamma;
+  s->cfl = cfl;
+  return s;
+}
+
+void oc_free(void* h) { delete (Sim*)h; }
+
+// patches: n x 7 int32 (level, lo0, lo1, lo2, hi0, hi1, hi2). 0 ok, -1 invalid,
+// -2 nesting violated, -3 same-level overlap.
+int oc_set_patches(void* h, const int* p, int n) {
+  Sim* s = (Sim*)h;
+  s->patches.clear();
+  for (int i = 0; i < n; ++i) {
+    Patch q;
+    q.level = p[7 * i];
+    for (int d = 0; d < 3; ++d) { q.lo[d] = p[7 * i + 1 + d]; q.hi[d] = p[7 * i + 4 + d]; }
+    s->patches.push_back(q);
+  }
+  return validate_and_build(*s);
+}
+
+// Whole-level arrays, x fastest. Cell fields: (Nz, Ny, Nx). Face field along
+// d: one extra entry along d (entry N_d repeats entry 0 on output, ignored on input).
+static void field_shape(const Sim& s, int level, int field, int* n) {
+  const Level& L = s.lev[level];
+  for (int d = 0; d < 3; ++d) n[d] = L.N[d];
+  if (is_face_field(s, field)) n[field - BX] += 1;
+}
+
+long long oc_field_size(void* h, int level, int field) {
+  Sim* s = (Sim*)h;
+  int n[3];
+  field_shape(*s, level, field, n);
+  return (long long)n[0] * n[1] * n[2];
+}
+
+int oc_set_field(void* h, int level, int field, const double* a) {
+  Sim* s = (Sim*)h;
+  Level& L = s->lev[level];
+  int n[3];
+  field_shape(*s, level, field, n);
+  for (int k = 0; k < L.N[2]; ++k)
+    for (int j = 0; j < L.N[1]; ++j)
+      for (int i = 0; i < L.N[0]; ++i) L.u[field][at(L, i, j, k)] = a[((size_t)k * n[1] + j) * n[0] + i];
+  return 0;
+}
+
+int oc_get_field(void* h, int level, int field, double* a) {
+  Sim* s = (Sim*)h;
+  Level& L = s->lev[level];
+  int n[3];
+  field_shape(*s, level, field, n);
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) a[((size_t)k * n[1] + j) * n[0] + i] = L.u[field][at(L, i, j, k)];
+  return 0;
+}
+
+double oc_cfl_dt(void* h) { return cfl_dt(*(Sim*)h); }
+
+// One coarse step (all levels, recursive order). dt0 <= 0: use the CFL dt.
+double oc_step(void* h, double dt0) {
+  Sim* s = (Sim*)h;
+  if (!(dt0 > 0)) dt0 = cfl_dt(*s);
+  level_substep(*s, 0, 1, dt0);
+  return dt0;
+}
+
+long long oc_cell_updates(void* h) { return ((Sim*)h)->cell_updates; }
+
+// Test-only planted mistakes (controls showing that a pin can fail).
+void oc_set_flags(void* h, int flags) { ((Sim*)h)->flags = flags; }
+
+// Region (dist == 0) and covered masks of a level, as int8 over (Nz, Ny, Nx).
+int oc_get_masks(void* h, int level, signed char* dist, signed char* cov) {
+  Sim* s = (Sim*)h;
+  Level& L = s->lev[level];
+  for (size_t q = 0; q < L.ncell; ++q) { dist[q] = L.dist[q]; cov[q] = L.cov[q]; }
+  return 0;
+}
+
+// One single-level step of dt updating only the listed target cells (and
+// their faces): targets are (i,j,k) triples on level 0 of a one-level sim.
+// Used to check sampled outputs of large runs one by one.
+int oc_step_targets(void* h, double dt, const int* ijk, int n) {
+  Sim* s = (Sim*)h;
+  Level& L = s->lev[0];
+  L.tmask.assign(L.ncell, -1);
+  for (int m = 0; m < n; ++m) L.tmask[at(L, ijk[3 * m], ijk[3 * m + 1], ijk[3 * m + 2])] = 0;
+  dilate(*s, L, L.tmask);
+  advance_masked(*s, L, dt);
+  return 0;
+}
+
+// Stand-alone kernels for pins.
+void oc_hlld(const double* ql, const double* qr, double bn, double gamma, double eps, double* f) {
+  hlld(ql, qr, bn, gamma, eps, f);
+}
+void oc_flux(const double* q, double bn, double gamma, double* f) {
+  double u[7];
+  mhd_flux(q, bn, 1.0 / (gamma - 1.0), f, u);
+}
+double oc_minmod(double a, double b) { return minmod(a, b); }
+double oc_fast_speed(double rho, double p, double bn, double bt, double bu, double gamma) {
+  return fast_speed(rho, p, bn, bt, bu, gamma);
+}
+double oc_gs_edge(const double* a) {
+  return gs_edge_emf(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11]);
+}
+
+// Prolongation of one coarse cell's children from a (2*1+1)^dim coarse block
+// given as whole-level arrays of a one-level sim: writes the 2^dim children
+// cell values of every cell field and all fine faces of the coarse cell into
+// a fine scratch sim built by the caller (same domain, base doubled).
+int oc_prolong_all(void* hc, void* hf) {
+  Sim* c = (Sim*)hc;
+  Sim* f = (Sim*)hf;
+  Level& C = c->lev[0];
+  Level& F = f->lev[0];
+  for (int fl = 0; fl < NFIELD; ++fl) C.start[fl] = C.u[fl];
+  int cf[6];
+  const int ncf = cell_fields(*c, cf);
+  for_cells(F, [&](int i, int j, int k) {
+    size_t q = at(F, i, j, k);
+    for (int n = 0; n < ncf; ++n)
+      F.u[cf[n]][q] = prolong_cell(*c, C, cf[n], i >> 1, j >> 1, c->dim == 3 ? k >> 1 : 0, i & 1, j & 1, c->dim == 3 ? (k & 1) : 0);
+    for (int d = 0; d < c->dim; ++d) F.u[BX + d][q] = prolong_face(*c, C, F, d, i, j, k);
+  });
+  return 0;
+}
+
+// Restriction of a fine one-level sim onto a coarse one-level sim (all cells
+// covered): the R operation alone.
+int oc_restrict_all(void* hc, void* hf) {
+  Sim* c = (Sim*)hc;
+  Sim* f = (Sim*)hf;
+  Level& C = c->lev[0];
+  Level& F = f->lev[0];
+  const double wc = c->dim == 3 ? 0.125 : 0.25;
+  const double wf = c->dim == 3 ? 0.25 : 0.5;
+  for_cells(C, [&](int i, int j, int k) {
+    restrict_cell(*c, C, F, i, j, k, wc);
+    for (int d = 0; d < c->dim; ++d) restrict_face(*c, C, F, d, i, j, k, wf);
+  });
+  return 0;
+}
+
+}  // extern "C"

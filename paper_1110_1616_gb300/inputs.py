@@ -1,0 +1,310 @@
+"""Seeded synthetic inputs: patch hierarchies and initial states.
+
+This module holds the workloads only (patch layouts, initial conditions, random
+draws); it contains none of the advance's arithmetic. Both the CUDA path and the
+CPU oracle take their inputs from here, so each sees identical arrays.
+
+State format: ``{level: [rho, mx, my, mz, E, bx, by, bz]}``; each entry is a
+whole-level numpy float64 array over the periodic domain at that level's
+resolution, x fastest: cell fields have shape (Nz, Ny, Nx); the face field
+along d has one extra entry along d (entry N_d repeats entry 0). In 2D, Nz = 1
+and bz is a cell field.
+
+Patches are ``(level, lo, hi)`` with half-open level-l cell index boxes
+(2D: lo[2] = 0, hi[2] = 1). Patch ids are list positions.
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+GAMMA = 5.0 / 3.0
+
+
+@dataclass
+class Problem:
+    name: str
+    dim: int
+    base: tuple
+    patches: list
+    nlev: int
+    state: dict
+    gamma: float = GAMMA
+    cfl: float = 0.4
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    meta: dict = field(default_factory=dict)
+
+    def level_n(self, level):
+        return tuple(self.base[d] << level if d < self.dim else 1 for d in range(3))
+
+    def cells_per_coarse_step(self):
+        """Work per coarse step: sum over levels of cells x 2^level."""
+        tot = 0
+        for (l, lo, hi) in self.patches:
+            n = 1
+            for d in range(self.dim):
+                n *= hi[d] - lo[d]
+            tot += n << l
+        return tot
+
+
+# ----------------------------------------------------------------- layouts
+def tile(level, lo, hi, psize, dim):
+    """Tiles the box [lo, hi) of level `level` with patches of edge psize
+    (z, y, x order of creation)."""
+    out = []
+    rng = [range(lo[d], hi[d], psize) if d < dim else range(0, 1) for d in range(3)]
+    for k in rng[2]:
+        for j in rng[1]:
+            for i in rng[0]:
+                plo = (i, j, k if dim == 3 else 0)
+                phi = (min(i + psize, hi[0]), min(j + psize, hi[1]), min(k + psize, hi[2]) if dim == 3 else 1)
+                out.append((level, plo, phi))
+    return out
+
+
+def _cell_centres(n, lo, hi, dim):
+    xs = [lo[d] + (np.arange(n[d]) + 0.5) * (hi[d] - lo[d]) / n[d] for d in range(3)]
+    z, y, x = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return x, y, z
+
+
+def _faces_from_cells_periodic(a, axis):
+    """Face array along `axis` (one extra entry repeating entry 0)."""
+    first = np.take(a, [0], axis=axis)
+    return np.concatenate([a, first], axis=axis)
+
+
+def _energy(rho, vx, vy, vz, p, bcx, bcy, bcz, gamma):
+    return p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bcx * bcx + bcy * bcy + bcz * bcz)
+
+
+def _cell_b_from_faces(bx, by, bz, dim):
+    bcx = 0.5 * (bx[:, :, :-1] + bx[:, :, 1:])
+    bcy = 0.5 * (by[:, :-1, :] + by[:, 1:, :])
+    bcz = 0.5 * (bz[:-1, :, :] + bz[1:, :, :]) if dim == 3 else bz
+    return bcx, bcy, bcz
+
+
+def _b_from_az_2d(az_corner, n, dx, dy):
+    """Face B from a corner vector potential A_z of shape (Ny+1, Nx+1)."""
+    bx = (az_corner[1:, :] - az_corner[:-1, :]) / dy  # (Ny, Nx+1)
+    by = -(az_corner[:, 1:] - az_corner[:, :-1]) / dx  # (Ny+1, Nx)
+    return bx[None], by[None]
+
+
+def _state_2d(n, rho, vx, vy, vz, p, bx, by, bz, gamma):
+    bcx, bcy, bcz = _cell_b_from_faces(bx, by, bz, 2)
+    e = _energy(rho, vx, vy, vz, p, bcx, bcy, bcz, gamma)
+    return [rho, rho * vx, rho * vy, rho * vz, e, bx, by, bz]
+
+
+# ----------------------------------------------------------------- problems
+def orszag_tang(n_base=64, psize=16, refine=True, noise=1e-3, seed=1, gamma=GAMMA):
+    """2D Orszag-Tang vortex on periodic [0,1]^2 with seeded density noise
+    rho (1 + noise U(-1,1)); one static refined level over the central half of
+    the base grid (in base cells [n/4, 3n/4)), ratio 2."""
+    rng = np.random.default_rng(seed)
+    patches = tile(0, (0, 0, 0), (n_base, n_base, 1), psize, 2)
+    nlev = 1
+    if refine:
+        a, b = n_base // 2, 3 * n_base // 2  # level-1 indices of the central half
+        patches += tile(1, (a, a, 0), (b, b, 1), psize, 2)
+        nlev = 2
+    b0 = 1.0 / math.sqrt(4.0 * math.pi)
+    state = {}
+    for l in range(nlev):
+        n = (n_base << l, n_base << l, 1)
+        dx = 1.0 / n[0]
+        x, y, _ = _cell_centres(n, (0, 0, 0), (1, 1, 1), 2)
+        rho = np.full(x.shape, 25.0 / (36.0 * math.pi))
+        if noise:
+            rho = rho * (1.0 + noise * rng.uniform(-1.0, 1.0, size=x.shape))
+        p = np.full(x.shape, 5.0 / (12.0 * math.pi))
+        vx = -np.sin(2 * math.pi * y)
+        vy = np.sin(2 * math.pi * x)
+        vz = np.zeros_like(x)
+        xc = np.arange(n[0] + 1) * dx
+        yc = np.arange(n[1] + 1) * dx
+        Y, X = np.meshgrid(yc, xc, indexing="ij")
+        az = b0 * (np.cos(4 * math.pi * X) / (4 * math.pi) + np.cos(2 * math.pi * Y) / (2 * math.pi))
+        bx, by = _b_from_az_2d(az, n, dx, dx)
+        bz = np.zeros_like(x)
+        state[l] = _state_2d(n, rho, vx, vy, vz, p, bx, by, bz, gamma)
+    return Problem("orszag_tang_2d", 2, (n_base, n_base, 1), patches, nlev, state, gamma=gamma,
+                   meta={"seed": seed, "noise": noise})
+
+
+def alfven_2d(n=32, psize=16, amp=1e-6, t=0.0, gamma=GAMMA):
+    """Circularly polarised linear Alfven wave on periodic [0,1]^2 travelling
+    along k = 2 pi (1,1) with B0 = (1,1)/sqrt(2), rho = 1, p = 1/gamma; the
+    in-plane perturbation comes from a vector potential so face B is
+    divergence-free. The exact solution at time t is the initial state with
+    the phase shifted by omega t, omega = |k| v_A, v_A = 1 (period 1/sqrt 2)."""
+    patches = tile(0, (0, 0, 0), (n, n, 1), psize, 2)
+    state = {0: alfven_2d_state(n, amp, t, gamma)}
+    return Problem("alfven_2d", 2, (n, n, 1), patches, 1, state, gamma=gamma, meta={"amp": amp})
+
+
+def alfven_2d_state(n, amp, t=0.0, gamma=GAMMA):
+    k = 2 * math.pi
+    omega = 2 * math.pi * math.sqrt(2.0)
+    b0 = 1.0 / math.sqrt(2.0)
+    dx = 1.0 / n
+    x, y, _ = _cell_centres((n, n, 1), (0, 0, 0), (1, 1, 1), 2)
+    ph = k * (x + y) - omega * t
+    rho = np.ones_like(x)
+    p = np.full_like(x, 1.0 / gamma)
+    s2 = 1.0 / math.sqrt(2.0)
+    vx = amp * np.cos(ph) * s2
+    vy = -amp * np.cos(ph) * s2
+    vz = -amp * np.sin(ph)
+    bz = amp * np.sin(ph)
+    xc = np.arange(n + 1) * dx
+    Y, X = np.meshgrid(xc, xc, indexing="ij")
+    phc = k * (X + Y) - omega * t
+    az = -amp * np.sin(phc) / (2 * math.pi * math.sqrt(2.0))
+    bx, by = _b_from_az_2d(az, (n, n, 1), dx, dx)
+    bx = bx + b0
+    by = by + b0
+    return _state_2d((n, n, 1), rho, vx, vy, vz, p, bx, by, bz, gamma)
+
+
+def blast_3d(n=128, psize=16, gamma=GAMMA):
+    """3D blast wave on periodic [0,1]^3: rho = 1, p = 0.1, p = 10 for cell
+    centres with r^2 < 0.01 around (1/2,1/2,1/2), v = 0, uniform
+    B = (1,1,1)/sqrt(3)."""
+    patches = tile(0, (0, 0, 0), (n, n, n), psize, 3)
+    nn = (n, n, n)
+    x, y, z = _cell_centres(nn, (0, 0, 0), (1, 1, 1), 3)
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2
+    rho = np.ones_like(x)
+    p = np.where(r2 < 0.01, 10.0, 0.1)
+    b = 1.0 / math.sqrt(3.0)
+    bx = np.full((n, n, n + 1), b)
+    by = np.full((n, n + 1, n), b)
+    bz = np.full((n + 1, n, n), b)
+    zero = np.zeros_like(x)
+    e = _energy(rho, zero, zero, zero, p, b, b, b, gamma)
+    state = {0: [rho, zero.copy(), zero.copy(), zero.copy(), e, bx, by, bz]}
+    return Problem("blast_3d", 3, nn, patches, 1, state, gamma=gamma)
+
+
+def uniform_state(dim, base, patches, nlev, seed=0, gamma=GAMMA):
+    """A random constant state on every level."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 2.0)
+    v = rng.uniform(-1, 1, size=3)
+    p = rng.uniform(0.2, 2.0)
+    b = rng.uniform(-1, 1, size=3)
+    if dim == 2:
+        pass
+    state = {}
+    for l in range(nlev):
+        n = tuple(base[d] << l if d < dim else 1 for d in range(3))
+        shp = (n[2], n[1], n[0])
+        one = np.ones(shp)
+        e = _energy(rho, v[0], v[1], v[2], p, b[0], b[1], b[2], gamma)
+        bx = np.full((n[2], n[1], n[0] + 1), b[0])
+        by = np.full((n[2], n[1] + 1, n[0]), b[1])
+        bz = np.full((n[2] + 1, n[1], n[0]), b[2]) if dim == 3 else one * b[2]
+        state[l] = [one * rho, one * rho * v[0], one * rho * v[1], one * rho * v[2], one * e, bx, by, bz]
+    return state
+
+
+def random_smooth_2d(n, nlev, seed=0, amp=0.05, gamma=GAMMA):
+    """A smooth random 2D state (few Fourier modes) on every level of a
+    hierarchy with base n x n; face B from a vector potential."""
+    rng = np.random.default_rng(seed)
+    modes = [(rng.integers(1, 3), rng.integers(1, 3), rng.uniform(0, 2 * math.pi)) for _ in range(3)]
+    coef = rng.normal(size=(7, 3)) * amp
+    state = {}
+    for l in range(nlev):
+        nn = (n << l, n << l, 1)
+        dx = 1.0 / nn[0]
+        x, y, _ = _cell_centres(nn, (0, 0, 0), (1, 1, 1), 2)
+
+        def f(c, X, Y):
+            s = 0.0
+            for m, (kx, ky, ph) in enumerate(modes):
+                s = s + coef[c, m] * np.sin(2 * math.pi * (kx * X + ky * Y) + ph)
+            return s
+
+        rho = 1.0 + f(0, x, y)
+        vx = 0.3 + f(1, x, y)
+        vy = -0.2 + f(2, x, y)
+        vz = f(3, x, y)
+        p = 1.0 + f(4, x, y)
+        bz = 0.3 + f(5, x, y)
+        xc = np.arange(nn[0] + 1) * dx
+        Y, X = np.meshgrid(xc, xc, indexing="ij")
+        az = f(6, X, Y) / (2 * math.pi) + 0.6 * Y - 0.4 * X
+        bx, by = _b_from_az_2d(az, nn, dx, dx)
+        state[l] = _state_2d(nn, rho, vx, vy, vz, p, bx, by, bz, gamma)
+    return state
+
+
+def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
+    """A random properly nested periodic hierarchy: level 0 tiled by patches
+    of random widths; finer levels a few random boxes aligned to parent cells,
+    each at least 3 parent cells inside a parent-level patch (so the nesting
+    rule holds), possibly touching each other and the periodic seam."""
+    rng = np.random.default_rng(seed)
+    # level 0: random cuts per dimension
+    cuts = []
+    for d in range(3):
+        if d >= dim:
+            cuts.append([0, 1])
+            continue
+        c = [0]
+        while c[-1] < base:
+            w = int(rng.choice([8, 12, 16]))
+            c.append(min(base, c[-1] + w))
+        if c[-1] - c[-2] < 4:
+            c.pop(-2)
+        cuts.append(c)
+    patches = []
+    for k in range(len(cuts[2]) - 1):
+        for j in range(len(cuts[1]) - 1):
+            for i in range(len(cuts[0]) - 1):
+                patches.append((0, (cuts[0][i], cuts[1][j], cuts[2][k]), (cuts[0][i + 1], cuts[1][j + 1], cuts[2][k + 1])))
+    for l in range(1, nlev):
+        parents = [p for p in patches if p[0] == l - 1]
+        n_l = base << l
+        made = []
+        tries = 0
+        while len(made) < 3 and tries < max_tries:
+            tries += 1
+            par = parents[rng.integers(len(parents))]
+            lo, hi = [], []
+            ok = True
+            for d in range(3):
+                if d >= dim:
+                    lo.append(0)
+                    hi.append(1)
+                    continue
+                plo, phi = par[1][d] + 3, par[2][d] - 3  # parent cells
+                if l - 1 == 0:  # level 0 covers the whole domain
+                    plo, phi = 0, base
+                if phi - plo < 2:
+                    ok = False
+                    break
+                a = int(rng.integers(plo, phi - 1))
+                b = int(rng.integers(a + 1, min(phi, a + 6) + 1))
+                lo.append(2 * a)
+                hi.append(2 * b)
+            if not ok:
+                continue
+            cand = (l, tuple(lo), tuple(hi))
+            # reject overlaps with already-made boxes on this level
+            clash = False
+            for m in made:
+                if all(not (cand[2][d] <= m[1][d] or cand[1][d] >= m[2][d]) for d in range(dim)):
+                    clash = True
+            if clash:
+                continue
+            made.append(cand)
+            _ = n_l
+        patches += made
+    return patches
