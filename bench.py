@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the batched AMR ideal-MHD advance on GB300.
+
+Workload: 3D periodic blast wave, 128^3 cells split into 512 patches of 16^3
+(rho = 1, p = 0.1, p = 10 inside r < 0.1, uniform B = (1,1,1)/sqrt 3). A step
+is one coarse step of the whole hot path: CFL reduction, ghost fill, the level
+advance (MUSCL-Hancock + minmod, HLLD, constrained transport) of every patch,
+replayed as one CUDA graph. The headline runs the mixed-precision path (FP32
+stencil, FP64 primitive recovery, registers, dt). Also reported: the FP64 path,
+the FP64 one-patch-per-launch baseline, the level advance alone against the
+HBM roofline, an end-to-end run through the C ABI with host buffers, and the
+CPU oracle.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s on 1 GB300 (FP32 vs FP64) and achieved HBM GB/s vs peak"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=128)
+    p.add_argument("--psize", type=int, default=16)
+    p.add_argument("--skip-extras", action="store_true", help="headline only (no FP64/baseline/e2e/oracle legs)")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.t0 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_ctx(pb, precision, strict=False, baseline=False, graph=True):
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    stream = torch.cuda.Stream()
+    ctx = A.context_for(pb, precision=precision, strict_fp64=strict, stream=stream.cuda_stream)
+    if baseline:
+        ctx.set_option(A.OPT_ADVANCE, 1)
+    if not graph:
+        ctx.set_option(A.OPT_GRAPH, 0)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    ctx.load_state(pb.state)
+    torch.cuda.synchronize()
+    return ctx, stream
+
+
+def timed_steps(ctx, stream, k):
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    l0 = ctx.query(A.Q_KERNEL_LAUNCHES)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(k, want_dt=False)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), ctx.query(A.Q_KERNEL_LAUNCHES) - l0
+
+
+def advance_alone(ctx, stream, reps):
+    """CUDA-event time of the level advance alone (fill outside the timed
+    brackets), averaged over reps calls on the launching stream."""
+    import torch
+    dt = ctx.cfl_dt()
+    tot = 0.0
+    for _ in range(reps):
+        ctx.fill_ghosts(0, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.advance_level(0, dt, 1)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps
+
+
+def e2e_run(pb, precision, k):
+    """Through the C ABI with host buffers: every step uploads the state from
+    pinned host memory, advances one coarse step and reads the state back."""
+    import numpy as np
+    import torch
+    ctx, stream = make_ctx(pb, precision)
+    host_in = []
+    for f in range(8):
+        a = torch.from_numpy(ctx.pack(pb.state, f)).pin_memory()
+        host_in.append(a)
+    host_out = [torch.empty_like(a).pin_memory() for a in host_in]
+    from paper_1110_1616_gb300 import amrmhd as A
+    lib = A.lib()
+    import ctypes as C
+
+    def one():
+        for f in range(8):
+            ctx._check(lib.amrmhd_set_state_packed(ctx.h, f, C.c_void_p(host_in[f].data_ptr()), 0), "set")
+        ctx.step(1, want_dt=False)
+        for f in range(8):
+            ctx._check(lib.amrmhd_get_state_packed(ctx.h, f, C.c_void_p(host_out[f].data_ptr()), 0), "get")
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        one()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    nbytes = sum(a.numel() * 8 for a in host_in)
+    cells = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
+    del ctx
+    torch.cuda.empty_cache()
+    _ = np
+    return cells * k / t, nbytes
+
+
+def cpu_oracle_rate(pb, steps=1):
+    from oracle import OracleSim
+    s = OracleSim(pb.dim, pb.base, pb.patches, pb.nlev, gamma=pb.gamma, cfl=pb.cfl)
+    s.set_state(pb.state)
+    c0 = s.cell_updates()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+    t = time.perf_counter() - t0
+    return (s.cell_updates() - c0) / t, t
+
+
+def run_reference(args, world, rank):
+    """The oracle, as it stands, on the host cores: each step is one coarse step
+    of a bounded sample of the workload (the same blast physics and 16^3 patches
+    at 64^3 = 1/8 of the cells)."""
+    if rank != 0:
+        return
+    from paper_1110_1616_gb300 import inputs
+    from oracle import OracleSim
+    n = max(args.n // 2, 32)
+    pb = inputs.blast_3d(n, args.psize)
+    s = OracleSim(pb.dim, pb.base, pb.patches, pb.nlev, gamma=pb.gamma, cfl=pb.cfl)
+    s.set_state(pb.state)
+    for _ in range(args.warmup):
+        s.step()
+    c0 = s.cell_updates()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    t = time.perf_counter() - t0
+    v = (s.cell_updates() - c0) / t
+    sample = "blast %d^3 in %d^3 patches (1/%d of the %d^3 workload), %d coarse steps" % (
+        n, args.psize, (args.n // n) ** 3, args.n, args.steps)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "blast3d_%d_p%d" % (args.n, args.psize), "global_batch": 1,
+                       "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args) if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import build as B
+    from paper_1110_1616_gb300 import inputs
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    pb = inputs.blast_3d(args.n, args.psize)
+    cells_step = pb.cells_per_coarse_step()
+    pk = peaks()
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+
+    clocks = Clocks(local)
+    clocks.start()
+    ctx, stream = make_ctx(pb, A.MIXED)
+    ctx.step(args.warmup, want_dt=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms, launches = timed_steps(ctx, stream, args.steps)
+    clk = clocks.stop()
+    ms_max = allmax(world, ms)
+    value = cells_step * args.steps * world / (ms_max / 1e3)
+
+    # level advance alone, against the HBM roofline (algorithmic bytes: the 8
+    # stored fields read and written once per cell update, 16 x 4 B in FP32)
+    t_adv = advance_alone(ctx, stream, 20)
+    alg_bytes = 16 * 4 * cells_step
+    achieved = alg_bytes / (t_adv / 1e3) / 1e9
+    arena_gb = ctx.query(A.Q_ARENA_BYTES) / 1e9
+    del ctx
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if not args.skip_extras:
+        ctx64, s64 = make_ctx(pb, A.FP64)
+        ctx64.step(2, want_dt=False)
+        k64 = max(5, args.steps // 5)
+        ms64, _ = timed_steps(ctx64, s64, k64)
+        extras["fp64"] = {"value": cells_step * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
+                          "steps": k64}
+        del ctx64
+        torch.cuda.empty_cache()
+        ctxb, sb = make_ctx(pb, A.FP64, baseline=True, graph=False)
+        ctxb.step(1, want_dt=False)
+        kb = max(3, args.steps // 20)
+        msb, _ = timed_steps(ctxb, sb, kb)
+        vb = cells_step * kb / (msb / 1e3)
+        extras["baseline_fp64_one_patch_per_launch"] = {"value": vb, "unit": UNIT, "ms_per_step": msb / kb,
+                                                        "steps": kb}
+        extras["speedup_vs_fp64_one_patch_per_launch"] = value / world / vb
+        del ctxb
+        torch.cuda.empty_cache()
+    e2e = None
+    if not args.skip_extras:
+        ke = max(3, args.steps // 10)
+        ve, nbytes = e2e_run(pb, A.MIXED, ke)
+        e2e = {"value": ve * world, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    cpu = None
+    if rank == 0 and not args.skip_extras:
+        rate, t = cpu_oracle_rate(pb, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "1 coarse step of the same %d^3 blast, single-threaded FP64 (%.1f s)" % (args.n, t)}
+    barrier(world)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "blast3d_%d_p%d" % (args.n, args.psize), "global_batch": world,
+                   "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "precision": "mixed",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (arena %.2f GB: ping-pong state and stage scratch)" % arena_gb},
+        "roofline": {"bound": "hbm", "kernel": "advance_level (staged: prim, predict, 3 flux, 3 emf, update)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
+                     "traffic": None, "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_adv},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

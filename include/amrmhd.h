@@ -1,0 +1,209 @@
+/*
+ * amrmhd: GB300 (sm_103a) patch-based AMR ideal-MHD level advance.
+ *
+ * C ABI of libamrmhd.so. Plain pointers and sizes only. Every call returns an
+ * amrmhd_status; after an error, amrmhd_last_error() describes it. All device
+ * work is ordered on the stream given to amrmhd_create. A context is not
+ * thread-safe.
+ *
+ * The objects follow the paper's statement of patch-based AMR (Carroll-Nellenback
+ * et al., "Efficient Parallelization for AMR MHD Multiphysics Calculations",
+ * Sec. 2): a patch (grid) is a regular cell array on one level l; cells of level l
+ * are R = 2 times finer than level l-1; every patch above level 0 is nested in the
+ * coarser level. Ghost zones decouple the hyperbolic advance of each patch
+ * (Abstract, Sec. 1); the levels advance in the recursive order 0,1,2,2,1,2,2 with
+ * prolongation, advance, synchronization (reflux) and restriction (Sec. 4).
+ *
+ * Memory ownership: the caller allocates the arena (one device allocation of the
+ * size amrmhd_set_hierarchy reports, e.g. a torch tensor) and owns it; the
+ * library owns its integer maps, small device scalars and CUDA graphs.
+ *
+ * State layout inside the arena (for reference; use get/set_state to move data):
+ * two state buffers (ping-pong), each holding, for every patch in (level, id)
+ * order, 8 field arrays rho, mx, my, mz, E, Bx, By, Bz. A patch with interior
+ * n_x x n_y x n_z stores each field over its ghosted box of extent
+ * (n_x+9) x (n_y+9) x (n_z+9) (2D: z extent 1), x fastest, index
+ * (i+4) + (n_x+9)*((j+4) + (n_y+9)*(k+4)) for patch-local cell (i,j,k),
+ * i in [-4, n_x+4); face field B_d at that index is the face at the low side of
+ * cell (i,j,k) along d. In 2D, Bz is cell-centred. Element type: double
+ * (AMRMHD_FP64) or float (AMRMHD_MIXED).
+ */
+#ifndef AMRMHD_H
+#define AMRMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amrmhd_ctx amrmhd_ctx; /* opaque, library-owned */
+
+typedef enum {
+  AMRMHD_OK = 0,
+  AMRMHD_EINVAL = -1,    /* bad argument or malformed patch list */
+  AMRMHD_ENEST = -2,     /* proper nesting violated (Sec. 2 nesting, 3-cell margin) */
+  AMRMHD_EOVERLAP = -3,  /* two patches of one level overlap */
+  AMRMHD_ENOMEM = -4,    /* arena too small or a library allocation failed */
+  AMRMHD_ECUDA = -5,     /* a CUDA runtime call failed */
+  AMRMHD_ENONPHYS = -6,  /* non-finite or non-positive density/pressure found by the CFL reduction */
+  AMRMHD_ETIMEOUT = -7,  /* a bounded device wait gave up */
+  AMRMHD_ESTATE = -8     /* call out of order (no hierarchy, no arena, wrong step sequence) */
+} amrmhd_status;
+
+enum { AMRMHD_FP64 = 0, AMRMHD_MIXED = 1 };
+enum { AMRMHD_BC_PERIODIC = 0 };
+
+typedef struct {
+  int32_t dim;         /* 2 or 3 */
+  int32_t base[3];     /* level-0 cells per dimension (base[2] = 1 in 2D) */
+  double lo[3], hi[3]; /* physical domain */
+  int32_t nghost;      /* must be 4 (= R x stencil reach 2) */
+  int32_t ratio;       /* must be 2 */
+  int32_t max_level;   /* highest level index allowed (levels 0..max_level) */
+  int32_t precision;   /* AMRMHD_FP64: all FP64; AMRMHD_MIXED: FP32 stencil, FP64
+                          primitive recovery, registers, dt and CFL */
+  int32_t bc[3][2];    /* AMRMHD_BC_PERIODIC on every side (only periodic is built) */
+  double gamma;        /* ratio of specific heats */
+  double cfl;          /* Courant number of the sum-form rate (e.g. 0.4) */
+  int32_t strict_fp64; /* 1: FP64 kernels compiled without FMA contraction (bitwise
+                          reproducible parity build); 0: contraction allowed */
+} amrmhd_config;
+
+/* A patch: level and half-open box [lo, hi) in level-l cell indices, inside
+ * [0, base*2^l). Above level 0, lo and hi must be even (aligned to parent
+ * cells). Patch ids are positions in the array given to set_hierarchy. */
+typedef struct {
+  int32_t level;
+  int32_t lo[3];
+  int32_t hi[3];
+} amrmhd_patch;
+
+/* Creates a context. cfg is copied. cuda_stream: the cudaStream_t all work of
+ * the context is ordered on; NULL makes the library create its own
+ * non-blocking stream at bind_arena (the legacy default stream cannot be
+ * captured into a CUDA graph). No device call is made until bind_arena. */
+amrmhd_status amrmhd_create(const amrmhd_config* cfg, void* cuda_stream, amrmhd_ctx** out);
+
+/* Destroys a context and frees library-owned memory (not the arena). */
+amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx);
+
+/* Installs a hierarchy (patches copied). Validates: boxes inside the level
+ * domain and aligned, level 0 tiles the domain, no same-level overlap
+ * (AMRMHD_EOVERLAP), every level-l cell's parent cell has all cells within 3
+ * parent cells in the parent region (AMRMHD_ENEST). Builds the neighbour lists
+ * by inheritance from the parents' neighbours (Sec. 3.1) and all ghost,
+ * prolongation, register and restriction maps. *arena_bytes receives the arena
+ * size the caller must allocate and bind. Host-only: needs no GPU. */
+amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches, int32_t n,
+                                   size_t* arena_bytes);
+
+/* Binds caller-owned device memory of at least arena_bytes bytes (256-byte
+ * aligned) and uploads the maps. Must follow set_hierarchy. */
+amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Copies one field of one patch in or out of the current state buffer.
+ * Values are double. Layout: the patch's interior, x fastest: cell fields
+ * n_z x n_y x n_x; the face field along d has n_d + 1 entries along d (both
+ * boundary faces). src/dst is device memory if *_on_device is 1, else host
+ * memory. set_state synchronises nothing; get_state to host synchronises the
+ * context stream. */
+amrmhd_status amrmhd_set_state(amrmhd_ctx* ctx, int32_t patch, int32_t field, const void* src,
+                               int32_t src_on_device);
+amrmhd_status amrmhd_get_state(amrmhd_ctx* ctx, int32_t patch, int32_t field, void* dst,
+                               int32_t dst_on_device);
+
+/* Packed form of the same: all patches in id order, each in the layout above,
+ * concatenated; field f of every patch. amrmhd_packed_size gives the element
+ * count of one packed field. */
+amrmhd_status amrmhd_packed_size(amrmhd_ctx* ctx, int32_t field, int64_t* count);
+amrmhd_status amrmhd_set_state_packed(amrmhd_ctx* ctx, int32_t field, const double* src, int32_t src_on_device);
+amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* dst, int32_t dst_on_device);
+
+/* Exports integer map `which` (AMRMHD_MAP_*) as rows of int32; *width receives
+ * the row width, *len the total int count; up to cap ints are written to dst
+ * (host memory; dst may be NULL to query the size). Host-only. Row formats:
+ *  NEIGHBORS      (p, q, sx, sy, sz): same-level q, periodic shift s, whose
+ *                 shifted interior meets p's ghosted box; sorted.
+ *  GHOST_CELLS    (p, Ldst, kind, src, Lsrc) for every ghost cell of p in z,y,x
+ *                 order; kind 0 = same-level copy, 1 = prolongation from the parent
+ *                 cell Lsrc of coarse patch src.
+ *  GHOST_FACES    (p, d, Ldst, kind, src, Lsrc), faces not owned by p; the
+ *                 same-level source is the owner with the smallest (id, index).
+ *  CF_FACES       (l, qc, d, Lface, side, pf, Lfine): coarse faces between a
+ *                 covered and an uncovered level-(l-1) cell; qc owns the uncovered
+ *                 cell; side = +1 if the face is that cell's low face; pf holds the
+ *                 fine sub-faces, Lfine is the first (z,y,x order).
+ *  CF_EDGES       (l, qc, c, Ledge, pf, Lfine): c-edges with 1..3 covered cells
+ *                 around; owners with the smallest (id, index).
+ *  EMF_FACES      (l, qc, d, Lface, e0, e1, e2, e3): every owner copy of a coarse
+ *                 face with both cells uncovered touching a C/F edge; e* are
+ *                 CF_EDGES row numbers or -1 (slots: t2-edges at the face and
+ *                 one up along t1, t1-edges at the face and one up along t2,
+ *                 t1 = (d+1)%3, t2 = (d+2)%3).
+ *  RESTRICT_CELLS (l, qc, Lcell, pf, Lchild0).
+ *  RESTRICT_FACES (l, qc, d, Lface, pf, Lfine0) for every owner copy.
+ *  REFLUX_CELLS   (l, qc, Lcell, f0..f5): CF_FACES row numbers of the cell's
+ *                 x-, x+, y-, y+, z-, z+ faces or -1.
+ * Local indices L are into the patch's ghosted box of extent n+9 per dimension. */
+enum {
+  AMRMHD_MAP_NEIGHBORS = 0, AMRMHD_MAP_GHOST_CELLS = 1, AMRMHD_MAP_GHOST_FACES = 2,
+  AMRMHD_MAP_CF_FACES = 3, AMRMHD_MAP_CF_EDGES = 4, AMRMHD_MAP_EMF_FACES = 5,
+  AMRMHD_MAP_RESTRICT_CELLS = 6, AMRMHD_MAP_RESTRICT_FACES = 7, AMRMHD_MAP_REFLUX_CELLS = 8
+};
+amrmhd_status amrmhd_export_map(amrmhd_ctx* ctx, int32_t which, int32_t* dst, int64_t cap, int64_t* len,
+                                int32_t* width);
+
+/* Ghost fill of every patch of `level` (same-level copies incl. periodic
+ * images; with substep 1 on a level above 0 also prolongation of the other
+ * ghosts from the parent level's state at the start of its current sub-step).
+ * Substep 2 refreshes only same-level ghosts (prolonged ghosts keep the values
+ * evolved by substep 1: extended ghost zones, Abstract and Sec. 1). */
+amrmhd_status amrmhd_fill_ghosts(amrmhd_ctx* ctx, int32_t level, int32_t substep);
+
+/* Advances every patch of `level` by dt (MUSCL-Hancock + minmod, HLLD, CT).
+ * Level 0 updates the interior; above level 0, substep 1 updates the interior
+ * plus 2 ghost layers and substep 2 the interior. Records the coarse-side
+ * registers of the next finer level's C/F boundary and the fine-side registers
+ * of this level's boundary for this substep. Must follow fill_ghosts(level). */
+amrmhd_status amrmhd_advance_level(amrmhd_ctx* ctx, int32_t level, double dt, int32_t substep);
+
+/* Synchronization and restriction of fine_level into fine_level-1 (Sec. 4's S
+ * and R): reflux of the C/F flux and EMF registers into uncovered coarse cells
+ * and faces, then averaging of the covered coarse cells and of the coarse
+ * faces in the closure of the fine region. Must follow both substeps of
+ * fine_level after advance_level(fine_level-1). */
+amrmhd_status amrmhd_reflux_restrict(amrmhd_ctx* ctx, int32_t fine_level);
+
+/* dt0 = cfl / max_l (2^-l max over level-l cells of sum_d (|v_d| + c_f,d)/dx_d),
+ * computed on the device in FP64; synchronises the stream.
+ * AMRMHD_ENONPHYS if a density or pressure is not finite and positive. */
+amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0);
+
+/* n_coarse full coarse steps (CFL dt each, then the whole recursion), run as a
+ * captured CUDA graph. dt_used (host, may be NULL) receives the n_coarse dt0
+ * values. Synchronises the stream at the end and reports device errors. */
+amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used);
+
+/* Integer queries: AMRMHD_Q_* */
+enum {
+  AMRMHD_Q_NPATCH = 0, AMRMHD_Q_NLEVEL = 1, AMRMHD_Q_CELLS = 2, AMRMHD_Q_CELL_UPDATES_PER_STEP = 3,
+  AMRMHD_Q_ARENA_BYTES = 4, AMRMHD_Q_KERNEL_LAUNCHES = 5
+};
+amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
+
+/* Options (set before set_hierarchy): AMRMHD_OPT_* */
+enum {
+  AMRMHD_OPT_ADVANCE = 0,  /* 0: staged kernels batched over a level (default); 1: the
+                              same kernels launched one patch at a time (baseline) */
+  AMRMHD_OPT_GRAPH = 1     /* 1 (default): amrmhd_step replays a CUDA graph; 0: plain launches */
+};
+amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
+
+const char* amrmhd_last_error(const amrmhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMRMHD_H */

@@ -13,6 +13,12 @@
 //  * A d-face at position g (g_d = face index, the face at g_d - 1/2) is owned
 //    by p when g_d is in [lo_d, hi_d] and the other coordinates in [lo, hi).
 //  * Periodic images: shifts s in {-1,0,1}^dim times the level size.
+//  * Neighbours: same-level q whose shifted interior meets p's ghosted box
+//    widened by one cell, [lo-5, hi+5), so that every owner of one of p's ghost
+//    faces is a neighbour.
+//  * Face-copy lists (EMF_FACES, RESTRICT_FACES) hold every stored copy of a
+//    face: each owner patch and, for a patch spanning the periodic domain, each
+//    of its two representatives of the seam face.
 //  * Kinds: 0 same-level copy, 1 prolongation from the parent level.
 #include <algorithm>
 #include <cstdint>
@@ -90,19 +96,18 @@ static int find_face(const H& h, int l, const int* g, int d, int* L) {
   return best;
 }
 
-// All owners of a d-face (each patch at most once, smallest local index).
+// Every stored copy of a d-face: (patch, local index) over all owners and
+// all periodic images (a patch spanning the domain stores the seam face twice).
 static void face_owners(const H& h, int l, const int* g, int d, std::vector<std::pair<int, int>>& out) {
   out.clear();
   for (int q = 0; q < (int)h.p.size(); ++q) {
     if (h.p[q].level != l) continue;
-    int bl = -1;
     for (auto& s : shifts(h.dim)) {
       int gg[3] = {g[0] - s[0] * h.N(l, 0), g[1] - s[1] * h.N(l, 1), h.dim == 3 ? g[2] - s[2] * h.N(l, 2) : 0};
       if (!face_owned(h.p[q], gg, d, h.dim)) continue;
-      int li = h.loc(q, gg);
-      if (bl < 0 || li < bl) bl = li;
+      std::pair<int, int> e = {q, h.loc(q, gg)};
+      if (std::find(out.begin(), out.end(), e) == out.end()) out.push_back(e);
     }
-    if (bl >= 0) out.push_back({q, bl});
   }
 }
 
@@ -180,7 +185,7 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
           bool hit = true;
           for (int d = 0; d < dim; ++d) {
             int lo = h.p[b].lo[d] + s[d] * h.N(h.p[a].level, d), hi = h.p[b].hi[d] + s[d] * h.N(h.p[a].level, d);
-            if (hi <= h.p[a].lo[d] - 4 || lo >= h.p[a].hi[d] + 4) hit = false;
+            if (hi <= h.p[a].lo[d] - 5 || lo >= h.p[a].hi[d] + 5) hit = false;
           }
           if (hit) emit({a, b, s[0], s[1], s[2]});
         }

@@ -1,0 +1,273 @@
+"""Thin ctypes binding of libamrmhd.so (include/amrmhd.h): argument
+marshalling only. Every step of the advance runs in the library's CUDA kernels;
+PyTorch supplies the device arena and the stream. If the library is missing,
+loading fails loudly: there is no fallback implementation."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libamrmhd.so")
+HEADER = os.path.join(HERE, "..", "include", "amrmhd.h")
+
+OK, EINVAL, ENEST, EOVERLAP, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+FP64, MIXED = 0, 1
+MAPS = {
+    "neighbors": 0, "ghost_cells": 1, "ghost_faces": 2, "cf_faces": 3, "cf_edges": 4,
+    "emf_faces": 5, "restrict_cells": 6, "restrict_faces": 7, "reflux_cells": 8,
+}
+Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
+OPT_ADVANCE, OPT_GRAPH = 0, 1
+
+
+class AmrmhdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("amrmhd status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("base", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("nghost", C.c_int32), ("ratio", C.c_int32), ("max_level", C.c_int32), ("precision", C.c_int32),
+        ("bc", (C.c_int32 * 2) * 3), ("gamma", C.c_double), ("cfl", C.c_double), ("strict_fp64", C.c_int32),
+    ]
+
+
+class Patch(C.Structure):
+    _fields_ = [("level", C.c_int32), ("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libamrmhd.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libamrmhd.so not built: run `python -m paper_1110_1616_gb300.build` "
+                              "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "amrmhd_create": [C.POINTER(Config), vp, C.POINTER(vp)],
+            "amrmhd_destroy": [vp],
+            "amrmhd_set_hierarchy": [vp, C.POINTER(Patch), i32, C.POINTER(C.c_size_t)],
+            "amrmhd_bind_arena": [vp, vp, C.c_size_t],
+            "amrmhd_set_state": [vp, i32, i32, vp, i32],
+            "amrmhd_get_state": [vp, i32, i32, vp, i32],
+            "amrmhd_packed_size": [vp, i32, C.POINTER(i64)],
+            "amrmhd_set_state_packed": [vp, i32, vp, i32],
+            "amrmhd_get_state_packed": [vp, i32, vp, i32],
+            "amrmhd_export_map": [vp, i32, vp, i64, C.POINTER(i64), C.POINTER(i32)],
+            "amrmhd_fill_ghosts": [vp, i32, i32],
+            "amrmhd_advance_level": [vp, i32, dbl, i32],
+            "amrmhd_reflux_restrict": [vp, i32],
+            "amrmhd_cfl_dt": [vp, C.POINTER(dbl)],
+            "amrmhd_step": [vp, i32, vp],
+            "amrmhd_query": [vp, i32, C.POINTER(i64)],
+            "amrmhd_set_option": [vp, i32, i64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.amrmhd_last_error.argtypes = [vp]
+        L.amrmhd_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the entry points declared in include/amrmhd.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:amrmhd_status|const char\*)\s+(amrmhd_\w+)\s*\(", txt, re.M)))
+
+
+def make_config(dim, base, precision=FP64, max_level=10, gamma=5.0 / 3.0, cfl=0.4, lo=(0, 0, 0), hi=(1, 1, 1),
+                strict_fp64=True):
+    c = Config()
+    c.dim = dim
+    b = tuple(base) + (1,) * (3 - len(base))
+    for d in range(3):
+        c.base[d] = b[d] if d < dim else 1
+        c.lo[d] = lo[d]
+        c.hi[d] = hi[d]
+        c.bc[d][0] = c.bc[d][1] = 0
+    c.nghost, c.ratio, c.max_level, c.precision = 4, 2, max_level, precision
+    c.gamma, c.cfl, c.strict_fp64 = gamma, cfl, 1 if strict_fp64 else 0
+    return c
+
+
+class Context:
+    """One amrmhd context. `stream` is an integer cudaStream_t (0/None: the
+    library makes its own)."""
+
+    def __init__(self, cfg, stream=None):
+        self.cfg = cfg
+        self.h = C.c_void_p()
+        self._check(lib().amrmhd_create(C.byref(cfg), C.c_void_p(stream or 0), C.byref(self.h)), "create")
+        self.arena = None
+        self.patches = []
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib().amrmhd_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = lib().amrmhd_last_error(self.h).decode() if getattr(self, "h", None) and self.h.value else what
+            raise AmrmhdError(st, "%s: %s" % (what, msg))
+
+    # ------------------------------------------------------------ hierarchy and memory
+    def set_hierarchy(self, patches):
+        arr = (Patch * len(patches))()
+        for i, (l, lo, hi) in enumerate(patches):
+            arr[i].level = l
+            for d in range(3):
+                arr[i].lo[d] = lo[d]
+                arr[i].hi[d] = hi[d]
+        nb = C.c_size_t(0)
+        st = lib().amrmhd_set_hierarchy(self.h, arr, len(patches), C.byref(nb))
+        if st != OK:
+            raise AmrmhdError(st, lib().amrmhd_last_error(self.h).decode())
+        self.patches = list(patches)
+        return nb.value
+
+    def bind_arena(self, tensor_or_ptr, nbytes=None):
+        if hasattr(tensor_or_ptr, "data_ptr"):
+            self.arena = tensor_or_ptr
+            ptr, nbytes = tensor_or_ptr.data_ptr(), tensor_or_ptr.numel() * tensor_or_ptr.element_size()
+        else:
+            ptr = tensor_or_ptr
+        self._check(lib().amrmhd_bind_arena(self.h, C.c_void_p(ptr), nbytes), "bind_arena")
+
+    def alloc_arena(self, device="cuda"):
+        import torch
+        nbytes = self.query(Q_ARENA_BYTES)
+        t = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-t.data_ptr()) % 256
+        self.bind_arena(t.data_ptr() + off, nbytes)
+        self.arena = t
+        return t
+
+    # ------------------------------------------------------------ state I/O
+    def packed_size(self, field):
+        n = C.c_int64(0)
+        self._check(lib().amrmhd_packed_size(self.h, field, C.byref(n)), "packed_size")
+        return n.value
+
+    def set_field_packed(self, field, arr):
+        if hasattr(arr, "data_ptr"):
+            self._check(lib().amrmhd_set_state_packed(self.h, field, C.c_void_p(arr.data_ptr()), 1), "set_state_packed")
+        else:
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            self._check(lib().amrmhd_set_state_packed(self.h, field, a.ctypes.data_as(C.c_void_p), 0), "set_state_packed")
+
+    def get_field_packed(self, field, out=None):
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(lib().amrmhd_get_state_packed(self.h, field, C.c_void_p(out.data_ptr()), 1), "get_state_packed")
+            return out
+        a = np.empty(self.packed_size(field), dtype=np.float64)
+        self._check(lib().amrmhd_get_state_packed(self.h, field, a.ctypes.data_as(C.c_void_p), 0), "get_state_packed")
+        return a
+
+    def get_field(self, patch, field):
+        l, lo, hi = self.patches[patch]
+        shp = self.field_shape(patch, field)
+        a = np.empty(shp, dtype=np.float64)
+        self._check(lib().amrmhd_get_state(self.h, patch, field, a.ctypes.data_as(C.c_void_p), 0), "get_state")
+        return a
+
+    def set_field(self, patch, field, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.field_shape(patch, field))
+        self._check(lib().amrmhd_set_state(self.h, patch, field, a.ctypes.data_as(C.c_void_p), 0), "set_state")
+
+    def field_shape(self, patch, field):
+        l, lo, hi = self.patches[patch]
+        dim = self.cfg.dim
+        n = [hi[d] - lo[d] if d < dim else 1 for d in range(3)]
+        if field >= 5 and not (dim == 2 and field == 7):
+            n[field - 5] += 1
+        return (n[2], n[1], n[0])
+
+    # packing of whole-level arrays (inputs format) into the library's packed layout
+    def pack(self, state, field):
+        parts = []
+        for (l, lo, hi) in self.patches:
+            a = state[l][field]
+            shp_extra = [0, 0, 0]
+            if field >= 5 and not (self.cfg.dim == 2 and field == 7):
+                shp_extra[field - 5] = 1
+            sl = tuple(slice(lo[d], hi[d] + shp_extra[d]) for d in (2, 1, 0))
+            parts.append(a[sl].ravel())
+        return np.concatenate(parts)
+
+    def unpack(self, packed, field):
+        out = []
+        o = 0
+        for p in range(len(self.patches)):
+            shp = self.field_shape(p, field)
+            n = int(np.prod(shp))
+            out.append(packed[o:o + n].reshape(shp))
+            o += n
+        return out
+
+    def load_state(self, state):
+        for f in range(8):
+            self.set_field_packed(f, self.pack(state, f))
+
+    def read_state(self):
+        """Per-patch arrays: out[field][patch]."""
+        return [self.unpack(self.get_field_packed(f), f) for f in range(8)]
+
+    # ------------------------------------------------------------ operations
+    def fill_ghosts(self, level, substep=1):
+        self._check(lib().amrmhd_fill_ghosts(self.h, level, substep), "fill_ghosts")
+
+    def advance_level(self, level, dt, substep=1):
+        self._check(lib().amrmhd_advance_level(self.h, level, float(dt), substep), "advance_level")
+
+    def reflux_restrict(self, fine_level):
+        self._check(lib().amrmhd_reflux_restrict(self.h, fine_level), "reflux_restrict")
+
+    def cfl_dt(self):
+        v = C.c_double(0)
+        self._check(lib().amrmhd_cfl_dt(self.h, C.byref(v)), "cfl_dt")
+        return v.value
+
+    def step(self, n=1, want_dt=True):
+        buf = np.zeros(max(n, 1), dtype=np.float64) if want_dt else None
+        self._check(lib().amrmhd_step(self.h, n, buf.ctypes.data_as(C.c_void_p) if want_dt else None), "step")
+        return buf
+
+    def query(self, what):
+        v = C.c_int64(0)
+        self._check(lib().amrmhd_query(self.h, what, C.byref(v)), "query")
+        return v.value
+
+    def set_option(self, opt, value):
+        self._check(lib().amrmhd_set_option(self.h, opt, value), "set_option")
+
+    def export_map(self, which):
+        if isinstance(which, str):
+            which = MAPS[which]
+        n, w = C.c_int64(0), C.c_int32(0)
+        self._check(lib().amrmhd_export_map(self.h, which, None, 0, C.byref(n), C.byref(w)), "export_map")
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        self._check(lib().amrmhd_export_map(self.h, which, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n),
+                                            C.byref(w)), "export_map")
+        return out[: n.value].reshape(-1, w.value)
+
+
+def context_for(problem, precision=FP64, strict_fp64=True, stream=None):
+    """Context + hierarchy for an inputs.Problem (no device memory yet)."""
+    cfg = make_config(problem.dim, problem.base, precision=precision, gamma=problem.gamma, cfl=problem.cfl,
+                      lo=problem.lo, hi=problem.hi, strict_fp64=strict_fp64)
+    ctx = Context(cfg, stream)
+    ctx.set_hierarchy(problem.patches)
+    return ctx

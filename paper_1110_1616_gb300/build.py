@@ -1,0 +1,64 @@
+"""Builds libamrmhd.so in-tree for sm_103a (nvcc for the CUDA units, g++ for
+the host hierarchy builder, compiled in parallel)."""
+import concurrent.futures as cf
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT, "libamrmhd.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "nvcc")
+UNITS = [
+    ("api.cu", []),
+    ("kernels_fast.cu", []),
+    ("kernels_strict.cu", ["--fmad=false"]),
+]
+HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "mhd_device.cuh"]
+
+
+def _sources():
+    s = [os.path.join(CSRC, u) for u, _ in UNITS] + [os.path.join(CSRC, "hierarchy.cpp")]
+    s += [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "amrmhd.h")]
+    return s
+
+
+def up_to_date():
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(s) <= t for s in _sources())
+
+
+def build(force=False, verbose=False):
+    if not force and up_to_date():
+        return LIB
+    os.makedirs(OUT, exist_ok=True)
+    jobs = []
+    for unit, extra in UNITS:
+        obj = os.path.join(OUT, unit.replace(".cu", ".o"))
+        cmd = [NVCC, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *extra, "-c",
+               os.path.join(CSRC, unit), "-o", obj]
+        jobs.append((cmd, obj))
+    hobj = os.path.join(OUT, "hierarchy.o")
+    jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-c", os.path.join(CSRC, "hierarchy.cpp"), "-o", hobj], hobj))
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        futs = [ex.submit(subprocess.run, cmd, capture_output=True, text=True) for cmd, _ in jobs]
+        for (cmd, _), f in zip(jobs, futs):
+            r = f.result()
+            if r.returncode != 0:
+                raise RuntimeError("build failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
+            if verbose:
+                print(r.stdout + r.stderr)
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stderr))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

@@ -1,0 +1,763 @@
+// C-ABI of libamrmhd.so (declared in include/amrmhd.h): context, hierarchy,
+// arena binding, state I/O, the level operations (fill, advance, reflux and
+// restriction, CFL) and the CUDA-graph coarse step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/amrmhd.h"
+#include "hierarchy.hpp"
+#include "kernels.hpp"
+
+using amrk::DPatch;
+using amrk::LevelArgs;
+using amrk::RowArgs;
+
+namespace {
+
+struct DevList {  // a device int list with its row count
+  int* p = nullptr;
+  int64_t n = 0;
+};
+
+struct LevelDev {
+  int* ids = nullptr;  // patch ids of the level (device)
+  int npatch = 0;
+  int maxn[3] = {1, 1, 1};
+  DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
+  DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
+  int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
+};
+
+}  // namespace
+
+struct amrmhd_ctx {
+  amrmhd_config cfg;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
+  std::string err;
+  amrmhd::Hierarchy H;
+  bool have_h = false, bound = false;
+  int variant = amrk::V_FP64;
+  const amrk::Ops* ops = nullptr;
+  int64_t opt_advance = 0, opt_graph = 1;
+  // arena layout (bytes)
+  std::vector<long long> off, fs, soff;
+  long long state_elems = 0, scr_elems = 0;
+  size_t o_state[2] = {0, 0}, o_scr = 0, o_creg = 0, o_freg = 0, o_ecreg = 0, o_efreg = 0, o_stage = 0;
+  size_t arena_bytes = 0;
+  char* arena = nullptr;
+  int64_t ncf = 0, nce = 0, stage_elems = 0;
+  // packed I/O offsets: kind 0 cells, 1..3 faces along x,y,z
+  std::vector<long long> poff[4];
+  long long ptotal[4] = {0, 0, 0, 0};
+  // library-owned device memory
+  std::vector<void*> dev_allocs;
+  DPatch* dP = nullptr;
+  int* d_iota = nullptr;
+  long long* d_poff[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d_scal = nullptr;              // [0] CFL dt0, [1 + l] dt given to advance_level(l)
+  unsigned long long* d_slots = nullptr;  // per-level CFL maxima + step counter
+  unsigned int* d_err = nullptr;
+  double* d_hist = nullptr;
+  int64_t hist_cap = 0;
+  std::vector<LevelDev> lev;
+  std::vector<int> cur, start;
+  int maxn_all[3] = {1, 1, 1};
+  // graphs, one per parity of level 0's buffer
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<int> g_cur_after[2], g_start_after[2];
+  int g_launches[2] = {0, 0};
+  long long launches = 0;
+};
+
+namespace {
+
+amrmhd_status fail(amrmhd_ctx* c, amrmhd_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// dt history capacity of one amrmhd_step chunk (the graphs bake this buffer in)
+constexpr int64_t kHistCap = 4096;
+
+void free_device(amrmhd_ctx* ctx) {
+  for (int i = 0; i < 2; ++i)
+    if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
+  for (void* p : ctx->dev_allocs) cudaFree(p);
+  ctx->dev_allocs.clear();
+  ctx->lev.clear();
+  ctx->bound = false;
+}
+
+template <class T> T* dbuf(amrmhd_ctx* ctx, size_t count, cudaError_t* e) {
+  void* p = nullptr;
+  *e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  if (*e == cudaSuccess) ctx->dev_allocs.push_back(p);
+  return (T*)p;
+}
+
+void* state_buf(amrmhd_ctx* ctx, int b) { return ctx->arena + ctx->o_state[b]; }
+
+LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int w) {
+  LevelArgs a;
+  const LevelDev& L = ctx->lev[l];
+  a.P = ctx->dP;
+  a.ids = L.ids;
+  a.npatch = L.npatch;
+  for (int d = 0; d < 3; ++d) a.maxn[d] = L.maxn[d];
+  a.cur = state_buf(ctx, ctx->cur[l]);
+  a.nxt = state_buf(ctx, ctx->cur[l] ^ 1);
+  a.scr = ctx->arena + ctx->o_scr;
+  a.dtp = dtp;
+  a.dtscale = dtscale;
+  for (int d = 0; d < 3; ++d) {
+    int N = d < ctx->cfg.dim ? (ctx->cfg.base[d] << l) : 1;
+    double dx = d < ctx->cfg.dim ? (ctx->cfg.hi[d] - ctx->cfg.lo[d]) / N : 1.0;
+    a.idx[d] = 1.0 / dx;
+  }
+  a.gamma = ctx->cfg.gamma;
+  a.w = w;
+  return a;
+}
+
+RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level) {
+  RowArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = ctx->dP;
+  a.rows = L.p;
+  a.nrows = L.n;
+  a.scr = ctx->arena + ctx->o_scr;
+  a.creg = (double*)(ctx->arena + ctx->o_creg);
+  a.freg = (double*)(ctx->arena + ctx->o_freg);
+  a.ecreg = (double*)(ctx->arena + ctx->o_ecreg);
+  a.efreg = (double*)(ctx->arena + ctx->o_efreg);
+  double dx[3];
+  for (int d = 0; d < 3; ++d) {
+    int N = d < ctx->cfg.dim ? (ctx->cfg.base[d] << coarse_level) : 1;
+    dx[d] = d < ctx->cfg.dim ? (ctx->cfg.hi[d] - ctx->cfg.lo[d]) / N : 1.0;
+    a.idx[d] = 1.0 / dx[d];
+  }
+  for (int n = 0; n < 3; ++n)
+    for (int t = 0; t < 3; ++t) a.ratio[n][t] = dx[n] / dx[t];
+  a.substep = 1;
+  return a;
+}
+
+// Register rows of level l (as fine level) start at global rows cf_face0 /
+// cf_edge0: the register arrays are indexed by the global row number, so the
+// per-level argument pointers are offset to the level's first row.
+void offset_regs(amrmhd_ctx* ctx, RowArgs& a, int l) {
+  a.creg += ctx->lev[l].cf_face0 * 6;
+  a.freg += ctx->lev[l].cf_face0 * 12;
+  a.ecreg += ctx->lev[l].cf_edge0;
+  a.efreg += ctx->lev[l].cf_edge0 * 2;
+}
+
+// ----- the level operations, shared by the direct calls and graph capture
+void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
+  ctx->start[l] = ctx->cur[l];
+  const LevelDev& L = ctx->lev[l];
+  RowArgs a = row_args(ctx, L.same_cells, l);
+  a.fbuf = state_buf(ctx, ctx->cur[l]);
+  ctx->ops->fill_same_cells(a, ctx->stream, nl);
+  a.rows = L.same_faces.p;
+  a.nrows = L.same_faces.n;
+  ctx->ops->fill_same_faces(a, ctx->stream, nl);
+  if (s == 1 && l > 0) {
+    RowArgs b = row_args(ctx, L.prol_cells, l - 1);
+    b.fbuf = state_buf(ctx, ctx->cur[l]);
+    b.cbuf = state_buf(ctx, ctx->start[l - 1]);
+    ctx->ops->prolong_cells(b, ctx->stream, nl);
+    b.rows = L.prol_faces.p;
+    b.nrows = L.prol_faces.n;
+    ctx->ops->prolong_faces(b, ctx->stream, nl);
+  }
+}
+
+void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, int* nl) {
+  const int w = (l == 0) ? 0 : (s == 1 ? 2 : 0);
+  LevelArgs a = level_args(ctx, l, dtp, dtscale, w);
+  if (ctx->opt_advance == 1) {
+    // one launch sequence per patch (baseline)
+    const LevelDev& L = ctx->lev[l];
+    for (int i = 0; i < L.npatch; ++i) {
+      LevelArgs b = a;
+      b.ids = L.ids + i;
+      b.npatch = 1;
+      ctx->ops->advance(b, ctx->stream, nl);
+    }
+  } else {
+    ctx->ops->advance(a, ctx->stream, nl);
+  }
+  const int nlev = ctx->H.nlev;
+  if (l + 1 < nlev) {
+    const LevelDev& F = ctx->lev[l + 1];
+    RowArgs f = row_args(ctx, F.cf_faces, l);
+    offset_regs(ctx, f, l + 1);
+    f.dtp = dtp;
+    f.dtscale = dtscale;
+    RowArgs e = f;
+    e.rows = F.cf_edges.p;
+    e.nrows = F.cf_edges.n;
+    ctx->ops->reg_coarse(f, e, ctx->stream, nl);
+  }
+  if (l > 0) {
+    const LevelDev& F = ctx->lev[l];
+    RowArgs f = row_args(ctx, F.cf_faces, l - 1);
+    offset_regs(ctx, f, l);
+    f.dtp = dtp;
+    f.dtscale = dtscale;
+    f.substep = s;
+    RowArgs e = f;
+    e.rows = F.cf_edges.p;
+    e.nrows = F.cf_edges.n;
+    ctx->ops->reg_fine(f, e, ctx->stream, nl);
+  }
+  ctx->cur[l] ^= 1;
+}
+
+void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl) {
+  const LevelDev& F = ctx->lev[l];
+  RowArgs a = row_args(ctx, F.reflux_cells, l - 1);
+  a.cbuf = state_buf(ctx, ctx->cur[l - 1]);
+  a.fbuf = state_buf(ctx, ctx->cur[l]);
+  // reflux rows hold global C/F face row numbers: registers are not offset here
+  ctx->ops->reflux_cells(a, ctx->stream, nl);
+  a.rows = F.emf_faces.p;
+  a.nrows = F.emf_faces.n;
+  ctx->ops->reflux_faces(a, ctx->stream, nl);
+  a.rows = F.restrict_cells.p;
+  a.nrows = F.restrict_cells.n;
+  ctx->ops->restrict_cells(a, ctx->stream, nl);
+  a.rows = F.restrict_faces.p;
+  a.nrows = F.restrict_faces.n;
+  ctx->ops->restrict_faces(a, ctx->stream, nl);
+}
+
+void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
+  const int nlev = ctx->H.nlev;
+  amrk::launch_zero_u64(ctx->d_slots, nlev, ctx->stream);
+  for (int l = 0; l < nlev; ++l) {
+    amrk::CflArgs a;
+    a.P = ctx->dP;
+    a.ids = ctx->lev[l].ids;
+    a.npatch = ctx->lev[l].npatch;
+    for (int d = 0; d < 3; ++d) a.maxn[d] = ctx->lev[l].maxn[d];
+    a.cur = state_buf(ctx, ctx->cur[l]);
+    for (int d = 0; d < 3; ++d) {
+      int N = d < ctx->cfg.dim ? (ctx->cfg.base[d] << l) : 1;
+      a.idx[d] = 1.0 / (d < ctx->cfg.dim ? (ctx->cfg.hi[d] - ctx->cfg.lo[d]) / N : 1.0);
+    }
+    a.gamma = ctx->cfg.gamma;
+    a.slot = ctx->d_slots + l;
+    a.err = ctx->d_err;
+    ctx->ops->cfl(a, ctx->stream, nl);
+  }
+  amrk::launch_cfl_finalize(ctx->d_slots, nlev, ctx->cfg.cfl, ctx->d_scal, hist, ctx->d_err, ctx->stream);
+  if (nl) *nl += 2;
+}
+
+// the recursive order 0,1,2,2,1,2,2 of Sec. 4 with P, A, S, R
+void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl) {
+  op_fill(ctx, l, s, nl);
+  op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, nl);
+  if (l + 1 < ctx->H.nlev) {
+    op_level_step(ctx, l + 1, 1, nl);
+    op_level_step(ctx, l + 1, 2, nl);
+    op_reflux_restrict(ctx, l + 1, nl);
+  }
+}
+
+void op_coarse_step(amrmhd_ctx* ctx, int* nl) {
+  op_cfl(ctx, ctx->d_hist, nl);
+  op_level_step(ctx, 0, 1, nl);
+}
+
+amrmhd_status check_bound(amrmhd_ctx* ctx) {
+  if (!ctx) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  if (!ctx->bound) return fail(ctx, AMRMHD_ESTATE, "no arena bound");
+  return AMRMHD_OK;
+}
+
+const std::vector<int32_t>* map_vec(amrmhd_ctx* ctx, int which, int* width) {
+  const amrmhd::Hierarchy& H = ctx->H;
+  switch (which) {
+    case AMRMHD_MAP_GHOST_CELLS: *width = 5; return &H.ghost_cells;
+    case AMRMHD_MAP_GHOST_FACES: *width = 6; return &H.ghost_faces;
+    case AMRMHD_MAP_CF_FACES: *width = 7; return &H.cf_faces;
+    case AMRMHD_MAP_CF_EDGES: *width = 6; return &H.cf_edges;
+    case AMRMHD_MAP_EMF_FACES: *width = 8; return &H.emf_faces;
+    case AMRMHD_MAP_RESTRICT_CELLS: *width = 5; return &H.restrict_cells;
+    case AMRMHD_MAP_RESTRICT_FACES: *width = 6; return &H.restrict_faces;
+    case AMRMHD_MAP_REFLUX_CELLS: *width = 9; return &H.reflux_cells;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+amrmhd_status amrmhd_create(const amrmhd_config* cfg, void* cuda_stream, amrmhd_ctx** out) {
+  if (!cfg || !out) return AMRMHD_EINVAL;
+  *out = nullptr;
+  if (cfg->dim != 2 && cfg->dim != 3) return AMRMHD_EINVAL;
+  if (cfg->nghost != 4 || cfg->ratio != 2) return AMRMHD_EINVAL;
+  if (cfg->precision != AMRMHD_FP64 && cfg->precision != AMRMHD_MIXED) return AMRMHD_EINVAL;
+  if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0) || cfg->max_level < 0 || cfg->max_level > 20) return AMRMHD_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (d < cfg->dim && (cfg->base[d] < 8 || !(cfg->hi[d] > cfg->lo[d]))) return AMRMHD_EINVAL;
+    if (d >= cfg->dim && cfg->base[d] != 1) return AMRMHD_EINVAL;
+    for (int s = 0; s < 2; ++s)
+      if (d < cfg->dim && cfg->bc[d][s] != AMRMHD_BC_PERIODIC) return AMRMHD_EINVAL;
+  }
+  amrmhd_ctx* ctx = new amrmhd_ctx();
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cfg->precision == AMRMHD_MIXED) ctx->variant = amrk::V_MIXED;
+  else ctx->variant = cfg->strict_fp64 ? amrk::V_FP64_STRICT : amrk::V_FP64;
+  ctx->ops = ctx->variant == amrk::V_FP64_STRICT ? amrk::ops_strict(cfg->dim) : amrk::ops_fast(ctx->variant, cfg->dim);
+  *out = ctx;
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx) {
+  if (!ctx) return AMRMHD_EINVAL;
+  free_device(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return AMRMHD_EINVAL;
+  if (option == AMRMHD_OPT_ADVANCE && (value == 0 || value == 1)) ctx->opt_advance = value;
+  else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
+  else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
+  for (int i = 0; i < 2; ++i)
+    if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches, int32_t n, size_t* arena_bytes) {
+  if (!ctx || !patches || n <= 0) return fail(ctx, AMRMHD_EINVAL, "bad arguments");
+  free_device(ctx);
+  ctx->have_h = false;
+  amrmhd::Hierarchy& H = ctx->H;
+  H.dim = ctx->cfg.dim;
+  for (int d = 0; d < 3; ++d) H.base[d] = ctx->cfg.base[d];
+  H.max_level = ctx->cfg.max_level;
+  std::vector<int32_t> rows(7 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    rows[7 * i] = patches[i].level;
+    for (int d = 0; d < 3; ++d) { rows[7 * i + 1 + d] = patches[i].lo[d]; rows[7 * i + 4 + d] = patches[i].hi[d]; }
+  }
+  int st = H.build(rows.data(), n);
+  if (st != AMRMHD_OK) return fail(ctx, (amrmhd_status)st, H.err);
+  // arena layout: patches in (level, id) order
+  const int np = (int)H.p.size();
+  const size_t elem = ctx->ops->elem;
+  ctx->off.assign(np, 0);
+  ctx->fs.assign(np, 0);
+  ctx->soff.assign(np, 0);
+  long long acc = 0, sacc = 0;
+  for (int l = 0; l < H.nlev; ++l)
+    for (int q : H.level_patches[l]) {
+      const long long e = (long long)H.p[q].ext[0] * H.p[q].ext[1] * H.p[q].ext[2];
+      const long long f = (e + 63) / 64 * 64;
+      ctx->fs[q] = f;
+      ctx->off[q] = acc;
+      acc += 8 * f;
+      ctx->soff[q] = sacc;
+      sacc += amrk::SC_N * f;
+    }
+  ctx->state_elems = acc;
+  ctx->scr_elems = sacc;
+  ctx->ncf = (int64_t)H.cf_faces.size() / 7;
+  ctx->nce = (int64_t)H.cf_edges.size() / 6;
+  for (int k = 0; k < 4; ++k) {
+    ctx->poff[k].assign(np, 0);
+    long long t = 0;
+    for (int q = 0; q < np; ++q) {
+      ctx->poff[k][q] = t;
+      long long c = 1;
+      for (int d = 0; d < H.dim; ++d) c *= H.p[q].n[d] + (k == d + 1 ? 1 : 0);
+      if (k == 3 && H.dim == 2) c = 0;
+      t += c;
+    }
+    ctx->ptotal[k] = t;
+  }
+  ctx->stage_elems = std::max(std::max(ctx->ptotal[0], ctx->ptotal[1]), std::max(ctx->ptotal[2], ctx->ptotal[3]));
+  size_t o = 0;
+  ctx->o_state[0] = o; o = align256(o + (size_t)acc * elem);
+  ctx->o_state[1] = o; o = align256(o + (size_t)acc * elem);
+  ctx->o_scr = o; o = align256(o + (size_t)sacc * elem);
+  ctx->o_creg = o; o = align256(o + (size_t)ctx->ncf * 6 * sizeof(double));
+  ctx->o_freg = o; o = align256(o + (size_t)ctx->ncf * 12 * sizeof(double));
+  ctx->o_ecreg = o; o = align256(o + (size_t)ctx->nce * sizeof(double));
+  ctx->o_efreg = o; o = align256(o + (size_t)ctx->nce * 2 * sizeof(double));
+  ctx->o_stage = o; o = align256(o + (size_t)ctx->stage_elems * sizeof(double));
+  ctx->arena_bytes = o;
+  ctx->have_h = true;
+  if (arena_bytes) *arena_bytes = o;
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "bind_arena before set_hierarchy");
+  if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(ctx, AMRMHD_EINVAL, "arena must be a 256-byte aligned device pointer");
+  if (bytes < ctx->arena_bytes) return fail(ctx, AMRMHD_ENOMEM, "arena smaller than required");
+  free_device(ctx);
+  if (!ctx->stream) {
+    // the legacy default stream cannot be captured into a graph: use our own
+    if (!ctx->own_stream) CU(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+    ctx->stream = ctx->own_stream;
+  }
+  ctx->arena = (char*)dev_ptr;
+  const amrmhd::Hierarchy& H = ctx->H;
+  const int np = (int)H.p.size(), nlev = H.nlev;
+  cudaError_t e = cudaSuccess;
+  // patch table
+  std::vector<DPatch> hp(np);
+  for (int q = 0; q < np; ++q) {
+    DPatch& P = hp[q];
+    for (int d = 0; d < 3; ++d) { P.lo[d] = H.p[q].lo[d]; P.n[d] = H.p[q].n[d]; P.ext[d] = H.p[q].ext[d]; }
+    P.level = H.p[q].level;
+    P.off = ctx->off[q];
+    P.fs = ctx->fs[q];
+    P.soff = ctx->soff[q];
+  }
+  ctx->dP = dbuf<DPatch>(ctx, np, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  CU(cudaMemcpy(ctx->dP, hp.data(), sizeof(DPatch) * np, cudaMemcpyHostToDevice));
+  std::vector<int> iota(np);
+  for (int q = 0; q < np; ++q) iota[q] = q;
+  ctx->d_iota = dbuf<int>(ctx, np, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  CU(cudaMemcpy(ctx->d_iota, iota.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+  for (int k = 0; k < 4; ++k) {
+    ctx->d_poff[k] = dbuf<long long>(ctx, np, &e);
+    if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+    CU(cudaMemcpy(ctx->d_poff[k], ctx->poff[k].data(), sizeof(long long) * np, cudaMemcpyHostToDevice));
+  }
+  ctx->d_scal = dbuf<double>(ctx, 2 + nlev, &e);
+  ctx->d_slots = dbuf<unsigned long long>(ctx, nlev + 1, &e);
+  ctx->d_err = dbuf<unsigned int>(ctx, 1, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+  CU(cudaMemset(ctx->d_slots, 0, sizeof(unsigned long long) * (nlev + 1)));
+  CU(cudaMemset(ctx->d_scal, 0, sizeof(double) * (2 + nlev)));
+  ctx->hist_cap = kHistCap;
+  ctx->d_hist = dbuf<double>(ctx, kHistCap, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  // per-level lists
+  ctx->lev.assign(nlev, LevelDev());
+  auto upload = [&](const std::vector<int32_t>& v, DevList& out, int width) -> bool {
+    out.n = (int64_t)v.size() / width;
+    if (v.empty()) { out.p = nullptr; return true; }
+    out.p = dbuf<int>(ctx, v.size(), &e);
+    if (e != cudaSuccess) return false;
+    e = cudaMemcpy(out.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice);
+    return e == cudaSuccess;
+  };
+  for (int l = 0; l < nlev; ++l) {
+    LevelDev& L = ctx->lev[l];
+    const std::vector<int>& ids = H.level_patches[l];
+    L.npatch = (int)ids.size();
+    for (int d = 0; d < 3; ++d) {
+      L.maxn[d] = 1;
+      for (int q : ids) L.maxn[d] = std::max(L.maxn[d], H.p[q].n[d]);
+      ctx->maxn_all[d] = std::max(ctx->maxn_all[d], L.maxn[d]);
+    }
+    L.ids = dbuf<int>(ctx, ids.size(), &e);
+    if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+    CU(cudaMemcpy(L.ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+    // ghost lists of this level's patches, split by kind
+    std::vector<int32_t> sc, pc, sf, pf;
+    for (size_t r = 0; r < H.ghost_cells.size(); r += 5) {
+      const int32_t* g = &H.ghost_cells[r];
+      if (H.p[g[0]].level != l) continue;
+      std::vector<int32_t>& v = g[2] == 0 ? sc : pc;
+      v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[3]); v.push_back(g[4]);
+    }
+    for (size_t r = 0; r < H.ghost_faces.size(); r += 6) {
+      const int32_t* g = &H.ghost_faces[r];
+      if (H.p[g[0]].level != l) continue;
+      std::vector<int32_t>& v = g[3] == 0 ? sf : pf;
+      v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[2]); v.push_back(g[4]); v.push_back(g[5]);
+    }
+    bool ok = upload(sc, L.same_cells, 4) && upload(pc, L.prol_cells, 4) && upload(sf, L.same_faces, 5) &&
+              upload(pf, L.prol_faces, 5);
+    if (l > 0 && ok) {
+      auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
+        return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);
+      };
+      ok = upload(slice(H.cf_faces, H.rng_cf_faces[l], 7), L.cf_faces, 7) &&
+           upload(slice(H.cf_edges, H.rng_cf_edges[l], 6), L.cf_edges, 6) &&
+           upload(slice(H.emf_faces, H.rng_emf_faces[l], 8), L.emf_faces, 8) &&
+           upload(slice(H.restrict_cells, H.rng_restrict_cells[l], 5), L.restrict_cells, 5) &&
+           upload(slice(H.restrict_faces, H.rng_restrict_faces[l], 6), L.restrict_faces, 6) &&
+           upload(slice(H.reflux_cells, H.rng_reflux_cells[l], 9), L.reflux_cells, 9);
+      L.cf_face0 = H.rng_cf_faces[l][0];
+      L.cf_edge0 = H.rng_cf_edges[l][0];
+    }
+    if (!ok) return fail(ctx, AMRMHD_ECUDA, std::string("map upload: ") + cudaGetErrorString(e));
+  }
+  ctx->cur.assign(nlev, 0);
+  ctx->start.assign(nlev, 0);
+  ctx->bound = true;
+  return AMRMHD_OK;
+}
+
+static amrmhd_status io_one(amrmhd_ctx* ctx, int32_t patch, int32_t field, void* buf, int32_t on_device,
+                            int to_state, bool packed) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  const amrmhd::Hierarchy& H = ctx->H;
+  if (field < 0 || field > 7) return fail(ctx, AMRMHD_EINVAL, "bad field");
+  if (!packed && (patch < 0 || patch >= (int)H.p.size())) return fail(ctx, AMRMHD_EINVAL, "bad patch");
+  int kind = (field >= 5 && !(H.dim == 2 && field == 7)) ? field - 4 : 0;
+  long long count;
+  if (packed) count = ctx->ptotal[kind];
+  else {
+    count = 1;
+    for (int d = 0; d < H.dim; ++d) count *= H.p[patch].n[d] + (kind == d + 1 ? 1 : 0);
+  }
+  double* stage = (double*)(ctx->arena + ctx->o_stage);
+  double* dev = on_device ? (double*)buf : stage;
+  // the I/O kernel addresses packed[poff[pid] + t]; for a single patch shift the base
+  double* kbase = packed ? dev : dev - ctx->poff[kind][patch];
+  const int* ids = packed ? ctx->d_iota : ctx->d_iota + patch;
+  const int npatch = packed ? (int)H.p.size() : 1;
+  const int* maxn = packed ? ctx->maxn_all : H.p[patch].n;
+  void* state = state_buf(ctx, ctx->cur[H.p[packed ? 0 : patch].level]);
+  if (packed) {
+    // patches of different levels may sit in different buffers: one launch per level
+    if (to_state && !on_device) CU(cudaMemcpyAsync(stage, buf, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    for (int l = 0; l < H.nlev; ++l) {
+      const LevelDev& L = ctx->lev[l];
+      int lm[3] = {L.maxn[0], L.maxn[1], L.maxn[2]};
+      int nl = 0;
+      ctx->ops->io(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev, ctx->d_poff[kind], field, to_state,
+                   ctx->stream, &nl);
+    }
+    if (!to_state && !on_device) {
+      CU(cudaMemcpyAsync(buf, stage, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CU(cudaStreamSynchronize(ctx->stream));
+    }
+    CU(cudaGetLastError());
+    return AMRMHD_OK;
+  }
+  if (to_state && !on_device) CU(cudaMemcpyAsync(stage, buf, count * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  int nl = 0;
+  ctx->ops->io(ctx->dP, ids, npatch, maxn, state, kbase, ctx->d_poff[kind], field, to_state, ctx->stream, &nl);
+  if (!to_state && !on_device) {
+    CU(cudaMemcpyAsync(buf, stage, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  CU(cudaGetLastError());
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_set_state(amrmhd_ctx* ctx, int32_t patch, int32_t field, const void* src, int32_t on_device) {
+  if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
+  return io_one(ctx, patch, field, (void*)src, on_device, 1, false);
+}
+
+amrmhd_status amrmhd_get_state(amrmhd_ctx* ctx, int32_t patch, int32_t field, void* dst, int32_t on_device) {
+  if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
+  return io_one(ctx, patch, field, dst, on_device, 0, false);
+}
+
+amrmhd_status amrmhd_packed_size(amrmhd_ctx* ctx, int32_t field, int64_t* count) {
+  if (!ctx || !count) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  if (field < 0 || field > 7) return fail(ctx, AMRMHD_EINVAL, "bad field");
+  int kind = (field >= 5 && !(ctx->H.dim == 2 && field == 7)) ? field - 4 : 0;
+  *count = ctx->ptotal[kind];
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_set_state_packed(amrmhd_ctx* ctx, int32_t field, const double* src, int32_t on_device) {
+  if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
+  return io_one(ctx, 0, field, (void*)src, on_device, 1, true);
+}
+
+amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* dst, int32_t on_device) {
+  if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
+  return io_one(ctx, 0, field, dst, on_device, 0, true);
+}
+
+amrmhd_status amrmhd_export_map(amrmhd_ctx* ctx, int32_t which, int32_t* dst, int64_t cap, int64_t* len,
+                                int32_t* width) {
+  if (!ctx || !len) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  std::vector<int32_t> tmp;
+  const std::vector<int32_t>* v = nullptr;
+  int w = 0;
+  if (which == AMRMHD_MAP_NEIGHBORS) {
+    w = 5;
+    for (size_t q = 0; q < ctx->H.nbr.size(); ++q)
+      for (const amrmhd::Nbr& x : ctx->H.nbr[q]) {
+        tmp.push_back((int32_t)q); tmp.push_back(x.q); tmp.push_back(x.s[0]); tmp.push_back(x.s[1]); tmp.push_back(x.s[2]);
+      }
+    v = &tmp;
+  } else {
+    v = map_vec(ctx, which, &w);
+    if (!v) return fail(ctx, AMRMHD_EINVAL, "unknown map");
+  }
+  *len = (int64_t)v->size();
+  if (width) *width = w;
+  if (dst && cap > 0) std::memcpy(dst, v->data(), sizeof(int32_t) * (size_t)std::min<int64_t>(cap, *len));
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_fill_ghosts(amrmhd_ctx* ctx, int32_t level, int32_t substep) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (level < 0 || level >= ctx->H.nlev || (substep != 1 && substep != 2)) return fail(ctx, AMRMHD_EINVAL, "bad level/substep");
+  int nl = 0;
+  op_fill(ctx, level, substep, &nl);
+  ctx->launches += nl;
+  CU(cudaGetLastError());
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_advance_level(amrmhd_ctx* ctx, int32_t level, double dt, int32_t substep) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (level < 0 || level >= ctx->H.nlev || (substep != 1 && substep != 2) || !(dt >= 0.0))
+    return fail(ctx, AMRMHD_EINVAL, "bad level/substep/dt");
+  int nl = 1;
+  double* slot = ctx->d_scal + 1 + level;
+  amrk::launch_set_scalar(slot, dt, ctx->stream);
+  op_advance(ctx, level, slot, 1.0, substep, &nl);
+  ctx->launches += nl;
+  CU(cudaGetLastError());
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_reflux_restrict(amrmhd_ctx* ctx, int32_t fine_level) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (fine_level < 1 || fine_level >= ctx->H.nlev) return fail(ctx, AMRMHD_EINVAL, "bad fine level");
+  int nl = 0;
+  op_reflux_restrict(ctx, fine_level, &nl);
+  ctx->launches += nl;
+  CU(cudaGetLastError());
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  int nl = 0;
+  op_cfl(ctx, nullptr, &nl);
+  ctx->launches += nl;
+  double v = 0;
+  unsigned int err = 0;
+  CU(cudaMemcpyAsync(&v, ctx->d_scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(&err, ctx->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (err) {
+    CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
+  }
+  if (dt0) *dt0 = v;
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (n_coarse < 0) return fail(ctx, AMRMHD_EINVAL, "negative step count");
+  if (n_coarse == 0) return AMRMHD_OK;
+  const int nlev = ctx->H.nlev;
+  for (int32_t done = 0; done < n_coarse;) {
+    const int32_t chunk = (int32_t)std::min<int64_t>(kHistCap, n_coarse - done);
+    CU(cudaMemsetAsync(ctx->d_slots + nlev, 0, sizeof(unsigned long long), ctx->stream));
+    for (int it = 0; it < chunk; ++it) {
+      if (ctx->opt_graph) {
+        const int par = ctx->cur[0];
+        if (!ctx->gexec[par]) {
+          std::vector<int> c0 = ctx->cur, s0 = ctx->start;
+          cudaGraph_t g = nullptr;
+          CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+          int nl = 0;
+          op_coarse_step(ctx, &nl);
+          cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+          if (ce != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+          ce = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
+          cudaGraphDestroy(g);
+          if (ce != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+          ctx->g_cur_after[par] = ctx->cur;
+          ctx->g_start_after[par] = ctx->start;
+          ctx->g_launches[par] = nl;
+          ctx->cur = c0;
+          ctx->start = s0;
+        }
+        CU(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
+        ctx->cur = ctx->g_cur_after[par];
+        ctx->start = ctx->g_start_after[par];
+        ctx->launches += ctx->g_launches[par];
+      } else {
+        int nl = 0;
+        op_coarse_step(ctx, &nl);
+        ctx->launches += nl;
+        CU(cudaGetLastError());
+      }
+    }
+    if (dt_used)
+      CU(cudaMemcpyAsync(dt_used + done, ctx->d_hist, sizeof(double) * chunk, cudaMemcpyDeviceToHost, ctx->stream));
+    done += chunk;
+  }
+  unsigned int err = 0;
+  CU(cudaMemcpyAsync(&err, ctx->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (err) {
+    CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
+  }
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
+  if (!ctx || !value) return AMRMHD_EINVAL;
+  if (what == AMRMHD_Q_KERNEL_LAUNCHES) { *value = ctx->launches; return AMRMHD_OK; }
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  const amrmhd::Hierarchy& H = ctx->H;
+  switch (what) {
+    case AMRMHD_Q_NPATCH: *value = (int64_t)H.p.size(); return AMRMHD_OK;
+    case AMRMHD_Q_NLEVEL: *value = H.nlev; return AMRMHD_OK;
+    case AMRMHD_Q_CELLS:
+    case AMRMHD_Q_CELL_UPDATES_PER_STEP: {
+      int64_t t = 0;
+      for (const auto& P : H.p) {
+        int64_t c = (int64_t)P.n[0] * P.n[1] * P.n[2];
+        t += what == AMRMHD_Q_CELLS ? c : (c << P.level);
+      }
+      *value = t;
+      return AMRMHD_OK;
+    }
+    case AMRMHD_Q_ARENA_BYTES: *value = (int64_t)ctx->arena_bytes; return AMRMHD_OK;
+    default: return fail(ctx, AMRMHD_EINVAL, "unknown query");
+  }
+}
+
+const char* amrmhd_last_error(const amrmhd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Host-side patch hierarchy: validation, neighbour lists by inheritance and
+// the integer maps the kernels consume (ghost fill, prolongation, registers,
+// restriction). Plain C++, no CUDA.
+#pragma once
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace amrmhd {
+
+struct HPatch {
+  int level;
+  int lo[3], hi[3];
+  int n[3];    // interior extent
+  int ext[3];  // ghosted storage extent n+9 (1 on inactive z)
+};
+
+struct Nbr {
+  int q;
+  int s[3];
+  bool operator<(const Nbr& o) const {
+    if (q != o.q) return q < o.q;
+    if (s[0] != o.s[0]) return s[0] < o.s[0];
+    if (s[1] != o.s[1]) return s[1] < o.s[1];
+    return s[2] < o.s[2];
+  }
+  bool operator==(const Nbr& o) const { return q == o.q && s[0] == o.s[0] && s[1] == o.s[1] && s[2] == o.s[2]; }
+};
+
+struct Hierarchy {
+  int dim = 2;
+  int base[3] = {1, 1, 1};
+  int max_level = 0;
+  int nlev = 0;
+  std::vector<HPatch> p;
+  std::vector<std::vector<int>> level_patches;  // ids per level, ascending
+  std::vector<std::vector<Nbr>> nbr;            // per patch, sorted by (q, shift)
+  std::vector<std::vector<int>> parents, children;
+
+  // maps, rows of fixed width (see amrmhd.h for the row formats)
+  std::vector<int32_t> ghost_cells;     // 5
+  std::vector<int32_t> ghost_faces;     // 6
+  std::vector<int32_t> cf_faces;        // 7
+  std::vector<int32_t> cf_edges;        // 6
+  std::vector<int32_t> emf_faces;       // 8
+  std::vector<int32_t> restrict_cells;  // 5
+  std::vector<int32_t> restrict_faces;  // 6
+  std::vector<int32_t> reflux_cells;    // 9
+  // per level row ranges [begin, end) of each list (rows are grouped by level:
+  // ghost lists by the patch's level, register lists by the fine level l)
+  std::vector<std::array<int64_t, 2>> rng_ghost_cells, rng_ghost_faces, rng_cf_faces, rng_cf_edges,
+      rng_emf_faces, rng_restrict_cells, rng_restrict_faces, rng_reflux_cells;
+  std::string err;
+
+  int N(int l, int d) const { return d < dim ? (base[d] << l) : 1; }
+  int loc(int q, int a, int b, int c) const;  // local index of level position (a,b,c)
+  // Returns 0 or a negative amrmhd_status; fills err.
+  int build(const int32_t* rows7, int n);
+};
+
+}  // namespace amrmhd

@@ -1,0 +1,97 @@
+// Launch interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace amrk {
+
+// Per-patch descriptor in device memory.
+struct DPatch {
+  int lo[3], n[3], ext[3];
+  int level;
+  long long off;   // element offset of field 0 in a state buffer
+  long long fs;    // elements per field array (padded)
+  long long soff;  // element offset of the patch's scratch block
+};
+
+// Scratch arrays per patch (each fs elements): W (8), Wh (8), S[d] (3x8),
+// Ref (3), F[d] (3x8), E (3).
+enum { SC_W = 0, SC_WH = 8, SC_S = 16, SC_REF = 40, SC_F = 43, SC_E = 67, SC_N = 70 };
+
+struct LevelArgs {
+  const DPatch* P;
+  const int* ids;  // patch ids of this launch
+  int npatch;
+  int maxn[3];     // largest interior extent among them
+  void* cur;       // state buffer read (base of all patches)
+  void* nxt;       // state buffer written by the update
+  void* scr;       // scratch base
+  const double* dtp;
+  double dtscale;  // dt = *dtp * dtscale
+  double idx[3];   // 1/dx of this level
+  double gamma;
+  int w;           // extra ghost layers updated (0 or 2)
+};
+
+struct RowArgs {
+  const DPatch* P;
+  const int* rows;
+  int64_t nrows;
+  void* fbuf;        // buffer of the fine level (read)
+  void* cbuf;        // buffer of the coarse level (written / read)
+  void* scr;
+  double* creg;      // coarse flux registers (row x 6)
+  double* freg;      // fine flux registers (row x 2 x 6)
+  double* ecreg;     // coarse EMF registers
+  double* efreg;     // fine EMF registers (row x 2)
+  const double* dtp;
+  double dtscale;
+  double idx[3];     // coarse level 1/dx
+  double ratio[3][3];  // dx_n/dx_t on the coarse level
+  int substep;       // 1 or 2
+  const double* flux_rows;  // unused
+};
+
+struct CflArgs {
+  const DPatch* P;
+  const int* ids;
+  int npatch;
+  int maxn[3];
+  const void* cur;
+  double idx[3];
+  double gamma;
+  unsigned long long* slot;  // per-level max (bits of a non-negative double)
+  unsigned int* err;
+};
+
+enum Variant { V_FP64 = 0, V_FP64_STRICT = 1, V_MIXED = 2 };
+
+struct Ops {
+  void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
+  void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
+  void (*reg_fine)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
+  void (*fill_same_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*fill_same_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*reflux_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*reflux_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*restrict_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*restrict_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*cfl)(const CflArgs&, cudaStream_t, int* launches);
+  // packed I/O of one field: to_state = 1 copies packed -> state
+  void (*io)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
+             const long long* poff, int field, int to_state, cudaStream_t, int* launches);
+  size_t elem;  // bytes per stored value
+};
+
+const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED
+const Ops* ops_strict(int dim);               // V_FP64_STRICT
+
+void launch_set_scalar(double* p, double v, cudaStream_t s);
+void launch_cfl_finalize(const unsigned long long* slots, int nlev, double cfl, double* dt_out, double* hist,
+                         unsigned int* err, cudaStream_t s);
+void launch_zero_u64(unsigned long long* p, int n, cudaStream_t s);
+
+}  // namespace amrk

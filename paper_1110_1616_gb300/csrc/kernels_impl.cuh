@@ -1,0 +1,667 @@
+// Staged level-advance kernels and the ghost-fill, prolongation, register,
+// reflux, restriction, CFL and I/O kernels. Included by one translation unit
+// per compilation mode with AMRK_NS set to a distinct namespace.
+//
+// Work decomposition: every launch batches all patches of a level: blockIdx.y
+// selects the patch, blockIdx.x/threadIdx.x the cell (or face/edge) of that
+// patch's region; patches of uneven size leave surplus blocks idle. Map-driven
+// kernels run one thread per map row, each row writing one destination value
+// set (no atomics, deterministic).
+#include "kernels.hpp"
+#include "mhd_device.cuh"
+
+#ifndef AMRK_NS
+#error "AMRK_NS must name the instantiation namespace"
+#endif
+
+namespace AMRK_NS {
+using namespace amrk;
+using namespace amrdev;
+
+constexpr int TPB = 256;
+
+__host__ __device__ __forceinline__ int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
+
+// region = interior widened by m layers; thread t -> local storage coords
+template <int DIM>
+__device__ __forceinline__ bool region_cell(const DPatch& P, int m, int t, int& i, int& j, int& k) {
+  const int rx = P.n[0] + 2 * m, ry = P.n[1] + 2 * m, rz = DIM == 3 ? P.n[2] + 2 * m : 1;
+  if (t >= rx * ry * rz) return false;
+  i = 4 - m + t % rx;
+  j = 4 - m + (t / rx) % ry;
+  k = DIM == 3 ? 4 - m + t / (rx * ry) : 0;
+  return true;
+}
+
+__device__ __forceinline__ int lidx(const DPatch& P, int i, int j, int k) { return i + P.ext[0] * (j + P.ext[1] * k); }
+
+template <int DIM> __device__ __forceinline__ int stride_of(const DPatch& P, int d) {
+  return d == 0 ? 1 : (d == 1 ? P.ext[0] : P.ext[0] * P.ext[1]);
+}
+
+// ------------------------------------------------------------------ advance stages
+template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_prim(LevelArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  if (!region_cell<DIM>(P, a.w + 2, blockIdx.x * TPB + threadIdx.x, i, j, k)) return;
+  const int L = lidx(P, i, j, k);
+  const long long fs = P.fs;
+  const T* U = (const T*)a.cur + P.off;
+  double u[5], bc[3], w[8];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) u[f] = (double)U[f * fs + L];
+  bc[0] = 0.5 * ((double)U[5 * fs + L] + (double)U[5 * fs + L + 1]);
+  bc[1] = 0.5 * ((double)U[6 * fs + L] + (double)U[6 * fs + L + P.ext[0]]);
+  if (DIM == 3) bc[2] = 0.5 * ((double)U[7 * fs + L] + (double)U[7 * fs + L + P.ext[0] * P.ext[1]]);
+  else bc[2] = (double)U[7 * fs + L];
+  recover(u, bc, a.gamma - 1.0, w);
+  T* W = (T*)a.scr + P.soff + SC_W * fs;
+#pragma unroll
+  for (int f = 0; f < 8; ++f) W[f * fs + L] = (T)w[f];
+}
+
+template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_predict(LevelArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  if (!region_cell<DIM>(P, a.w + 1, blockIdx.x * TPB + threadIdx.x, i, j, k)) return;
+  const int L = lidx(P, i, j, k);
+  const long long fs = P.fs;
+  const T* U = (const T*)a.cur + P.off;
+  T* S = (T*)a.scr + P.soff;
+  const T* W = S + SC_W * fs;
+  const double dt = *a.dtp * a.dtscale;
+  T w[8], s[3][8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) w[f] = W[f * fs + L];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int sd = stride_of<DIM>(P, d);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f == BX + d) s[d][f] = U[(BX + d) * fs + L + sd] - U[(BX + d) * fs + L];
+      else s[d][f] = mm(w[f] - W[f * fs + L - sd], W[f * fs + L + sd] - w[f]);
+      S[(SC_S + 8 * d + f) * fs + L] = s[d][f];
+    }
+  }
+  const T ir = T(1) / w[0];
+  const T gamma = (T)a.gamma;
+  T wh[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) wh[f] = w[f];
+  {
+    T dw[8];
+    const T h0 = (T)(0.5 * dt * a.idx[0]);
+    prim_terms<T, 0>(w, s[0], gamma, ir, dw);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h0 * dw[f];
+    const T h1 = (T)(0.5 * dt * a.idx[1]);
+    prim_terms<T, 1>(w, s[1], gamma, ir, dw);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h1 * dw[f];
+    if (DIM == 3) {
+      const T h2 = (T)(0.5 * dt * a.idx[2]);
+      prim_terms<T, 2>(w, s[2], gamma, ir, dw);
+#pragma unroll
+      for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h2 * dw[f];
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 8; ++f) S[(SC_WH + f) * fs + L] = wh[f];
+  S[(SC_REF + 0) * fs + L] = wh[3] * wh[6] - wh[2] * wh[7];
+  S[(SC_REF + 1) * fs + L] = wh[1] * wh[7] - wh[3] * wh[5];
+  S[(SC_REF + 2) * fs + L] = wh[2] * wh[5] - wh[1] * wh[6];
+}
+
+// d-faces with normal index in [4-w, n+4+w] and transverse cells in
+// [4-w-1, n+4+w+1); face stored at the cell on its high side.
+template <class T, int DIM, int D> __global__ void __launch_bounds__(TPB) k_flux(LevelArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  const int w = a.w;
+  int r[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r[e] = e >= DIM ? 1 : (e == D ? P.n[e] + 2 * w + 1 : P.n[e] + 2 * w + 2);
+  const int t = blockIdx.x * TPB + threadIdx.x;
+  if (t >= r[0] * r[1] * r[2]) return;
+  int c[3] = {t % r[0], (t / r[0]) % r[1], t / (r[0] * r[1])};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) c[e] = e >= DIM ? 0 : c[e] + (e == D ? 4 - w : 3 - w);
+  const int L = lidx(P, c[0], c[1], c[2]);
+  const int Ll = L - stride_of<DIM>(P, D);
+  const long long fs = P.fs;
+  T* S = (T*)a.scr + P.soff;
+  T wl[8], wr[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    wl[f] = S[(SC_WH + f) * fs + Ll] + T(0.5) * S[(SC_S + 8 * D + f) * fs + Ll];
+    wr[f] = S[(SC_WH + f) * fs + L] - T(0.5) * S[(SC_S + 8 * D + f) * fs + L];
+  }
+  constexpr int n = D, tt = (D + 1) % 3, uu = (D + 2) % 3;
+  const T bn = T(0.5) * (wl[5 + n] + wr[5 + n]);
+  const T ql[7] = {wl[0], wl[1 + n], wl[1 + tt], wl[1 + uu], wl[4], wl[5 + tt], wl[5 + uu]};
+  const T qr[7] = {wr[0], wr[1 + n], wr[1 + tt], wr[1 + uu], wr[4], wr[5 + tt], wr[5 + uu]};
+  T fr[7];
+  hlld_flux<T>(ql, qr, bn, (T)a.gamma, fr);
+  T* F = S + (SC_F + 8 * D) * fs;
+  F[RHO * fs + L] = fr[0];
+  F[(MX + n) * fs + L] = fr[1];
+  F[(MX + tt) * fs + L] = fr[2];
+  F[(MX + uu) * fs + L] = fr[3];
+  F[EN * fs + L] = fr[4];
+  F[(BX + tt) * fs + L] = fr[5];
+  F[(BX + uu) * fs + L] = fr[6];
+  F[(BX + n) * fs + L] = T(0);
+}
+
+// c-edges: c-coordinate cells in [4-w, n+4+w), a,b in [4-w, n+4+w]
+template <class T, int DIM, int C> __global__ void __launch_bounds__(TPB) k_emf(LevelArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  const int w = a.w;
+  int r[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r[e] = e >= DIM ? 1 : (e == C ? P.n[e] + 2 * w : P.n[e] + 2 * w + 1);
+  const int t = blockIdx.x * TPB + threadIdx.x;
+  if (t >= r[0] * r[1] * r[2]) return;
+  int c[3] = {t % r[0], (t / r[0]) % r[1], t / (r[0] * r[1])};
+#pragma unroll
+  for (int e = 0; e < 3; ++e) c[e] = e >= DIM ? 0 : c[e] + 4 - w;
+  constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+  const int L = lidx(P, c[0], c[1], c[2]);
+  const int sa = stride_of<DIM>(P, A), sb = stride_of<DIM>(P, B);
+  const long long fs = P.fs;
+  T* S = (T*)a.scr + P.soff;
+  const T* Fa = S + (SC_F + 8 * A) * fs;
+  const T* Fb = S + (SC_F + 8 * B) * fs;
+  const T* R = S + (SC_REF + C) * fs;
+  const int q11 = L, q01 = L - sa, q10 = L - sb, q00 = L - sa - sb;
+  const T ea_hi = -Fa[(BX + B) * fs + q11], ea_lo = -Fa[(BX + B) * fs + q10];
+  const T eb_hi = Fb[(BX + A) * fs + q11], eb_lo = Fb[(BX + A) * fs + q01];
+  S[(SC_E + C) * fs + L] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, R[q00], R[q10], R[q01], R[q11], Fa[q10], Fa[q11],
+                                     Fb[q01], Fb[q11]);
+}
+
+template <class T, int DIM>
+__device__ __forceinline__ T face_update(const T* S, long long fs, const DPatch& P, int d, int L, T v, const T* dtd) {
+  const T* E0 = S + (SC_E + 0) * fs;
+  const T* E1 = S + (SC_E + 1) * fs;
+  const T* E2 = S + (SC_E + 2) * fs;
+  const int sx = 1, sy = P.ext[0], sz = P.ext[0] * P.ext[1];
+  if (DIM == 2) {
+    if (d == 0) v = v - dtd[1] * (E2[L + sy] - E2[L]);
+    else v = v + dtd[0] * (E2[L + sx] - E2[L]);
+  } else {
+    if (d == 0) {
+      v = v - dtd[1] * (E2[L + sy] - E2[L]);
+      v = v + dtd[2] * (E1[L + sz] - E1[L]);
+    } else if (d == 1) {
+      v = v - dtd[2] * (E0[L + sz] - E0[L]);
+      v = v + dtd[0] * (E2[L + sx] - E2[L]);
+    } else {
+      v = v - dtd[0] * (E1[L + sx] - E1[L]);
+      v = v + dtd[1] * (E0[L + sy] - E0[L]);
+    }
+  }
+  return v;
+}
+
+template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_update(LevelArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  if (!region_cell<DIM>(P, a.w, blockIdx.x * TPB + threadIdx.x, i, j, k)) return;
+  const int L = lidx(P, i, j, k);
+  const long long fs = P.fs;
+  const T* U = (const T*)a.cur + P.off;
+  T* V = (T*)a.nxt + P.off;
+  const T* S = (const T*)a.scr + P.soff;
+  const double dt = *a.dtp * a.dtscale;
+  T dtd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dtd[d] = (T)(dt * a.idx[d]);
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    T v = U[f * fs + L];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T* F = S + (SC_F + 8 * d + f) * fs;
+      v = v - dtd[d] * (F[L + stride_of<DIM>(P, d)] - F[L]);
+    }
+    V[f * fs + L] = v;
+  }
+  const int hi[3] = {P.n[0] + 4 + a.w - 1, P.n[1] + 4 + a.w - 1, DIM == 3 ? P.n[2] + 4 + a.w - 1 : 0};
+  const int cc[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    V[(BX + d) * fs + L] = face_update<T, DIM>(S, fs, P, d, L, U[(BX + d) * fs + L], dtd);
+    if (cc[d] == hi[d]) {
+      const int L2 = L + stride_of<DIM>(P, d);
+      V[(BX + d) * fs + L2] = face_update<T, DIM>(S, fs, P, d, L2, U[(BX + d) * fs + L2], dtd);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ registers
+// coarse side: rows (l, qc, d, Lface, side, pf, Lfine) -> creg = dt F_c
+template <class T, int DIM> __global__ void k_reg_coarse_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 7 * r;
+  const DPatch P = a.P[row[1]];
+  const int d = row[2], L = row[3];
+  const double dt = *a.dtp * a.dtscale;
+  const T* F = (const T*)a.scr + P.soff + (SC_F + 8 * d) * P.fs;
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    a.creg[r * 6 + n] = dt * (double)F[f * P.fs + L];
+  }
+}
+
+template <class T, int DIM> __global__ void k_reg_coarse_edges(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch P = a.P[row[1]];
+  const int c = row[2], L = row[3];
+  const double dt = *a.dtp * a.dtscale;
+  const T* E = (const T*)a.scr + P.soff + (SC_E + c) * P.fs;
+  a.ecreg[r] = dt * (double)E[L];
+}
+
+// fine side, one sub-step: freg[s] = dt 2^-(dim-1) * tree sum of the sub-faces
+template <class T, int DIM> __global__ void k_reg_fine_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 7 * r;
+  const DPatch P = a.P[row[5]];
+  const int d = row[2], L = row[6];
+  const double dt = *a.dtp * a.dtscale;
+  const double af = dt * (DIM == 3 ? 0.25 : 0.5);
+  const T* F = (const T*)a.scr + P.soff + (SC_F + 8 * d) * P.fs;
+  const int sx = 1, sy = P.ext[0], sz = P.ext[0] * P.ext[1];
+  int o[4];
+  if (DIM == 2) {
+    o[0] = 0; o[1] = d == 0 ? sy : sx;
+  } else if (d == 0) {
+    o[0] = 0; o[1] = sy; o[2] = sz; o[3] = sy + sz;
+  } else if (d == 1) {
+    o[0] = 0; o[1] = sx; o[2] = sz; o[3] = sx + sz;
+  } else {
+    o[0] = 0; o[1] = sx; o[2] = sy; o[3] = sx + sy;
+  }
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+  double* out = a.freg + (r * 2 + (a.substep - 1)) * 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    const T* G = F + f * P.fs + L;
+    double s;
+    if (DIM == 2) s = tree2((double)G[o[0]], (double)G[o[1]]);
+    else s = tree4((double)G[o[0]], (double)G[o[1]], (double)G[o[2]], (double)G[o[3]]);
+    out[n] = af * s;
+  }
+}
+
+template <class T, int DIM> __global__ void k_reg_fine_edges(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch P = a.P[row[4]];
+  const int c = row[2], L = row[5];
+  const double dt = *a.dtp * a.dtscale;
+  const T* E = (const T*)a.scr + P.soff + (SC_E + c) * P.fs;
+  double v;
+  if (DIM == 3) {
+    const int sc = c == 0 ? 1 : (c == 1 ? P.ext[0] : P.ext[0] * P.ext[1]);
+    v = (dt * 0.5) * tree2((double)E[L], (double)E[L + sc]);
+  } else {
+    v = dt * (double)E[L];
+  }
+  a.efreg[r * 2 + (a.substep - 1)] = v;
+}
+
+// ------------------------------------------------------------------ ghost fill
+// same-level cell copies: rows (dst, Ldst, src, Lsrc)
+template <class T, int DIM> __global__ void k_fill_same_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 4 * r;
+  const DPatch D = a.P[row[0]], S = a.P[row[2]];
+  T* dst = (T*)a.fbuf + D.off + row[1];
+  const T* src = (const T*)a.fbuf + S.off + row[3];
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    dst[f * D.fs] = src[f * S.fs];
+  }
+}
+
+// same-level face copies: rows (dst, d, Ldst, src, Lsrc)
+template <class T, int DIM> __global__ void k_fill_same_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 5 * r;
+  const DPatch D = a.P[row[0]], S = a.P[row[3]];
+  const int f = BX + row[1];
+  ((T*)a.fbuf)[D.off + f * D.fs + row[2]] = ((const T*)a.fbuf)[S.off + f * S.fs + row[4]];
+}
+
+template <int DIM> __device__ __forceinline__ void global_pos(const DPatch& P, int L, int* g) {
+  const int a = L % P.ext[0];
+  const int b = (L / P.ext[0]) % P.ext[1];
+  const int c = L / (P.ext[0] * P.ext[1]);
+  g[0] = P.lo[0] + a - 4;
+  g[1] = P.lo[1] + b - 4;
+  g[2] = DIM == 3 ? P.lo[2] + c - 4 : 0;
+}
+
+// prolonged ghost cells: rows (dst, Ldst, srcC, Lsrc); coarse data from cbuf
+// (the parent level's state at the start of its current sub-step)
+template <class T, int DIM> __global__ void k_prolong_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 4 * r;
+  const DPatch D = a.P[row[0]], C = a.P[row[2]];
+  int g[3];
+  global_pos<DIM>(D, row[1], g);
+  T* dst = (T*)a.fbuf + D.off + row[1];
+  const T* src = (const T*)a.cbuf + C.off + row[3];
+  const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    const T* u = src + f * C.fs;
+    const T u0 = u[0];
+    T v = u0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T sl = mm(u0 - u[-st[d]], u[st[d]] - u0);
+      v = v + sl * ((g[d] & 1) ? T(0.25) : T(-0.25));
+    }
+    dst[f * D.fs] = v;
+  }
+}
+
+// B_n on the coarse n-face at b (pointer to that face), prolonged to the fine
+// sub-face with transverse parities par
+template <class T, int DIM>
+__device__ __forceinline__ T coincident(const T* b, const int* st, int n, const int* par) {
+  const T b0 = b[0];
+  T v = b0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    if (d == n) continue;
+    const T sl = mm(b0 - b[-st[d]], b[st[d]] - b0);
+    v = v + sl * (par[d] ? T(0.25) : T(-0.25));
+  }
+  return v;
+}
+
+// prolonged ghost faces: rows (dst, d, Ldst, srcC, Lsrc)
+template <class T, int DIM> __global__ void k_prolong_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 5 * r;
+  const DPatch D = a.P[row[0]], C = a.P[row[3]];
+  const int n = row[1];
+  int g[3];
+  global_pos<DIM>(D, row[2], g);
+  const int par[3] = {g[0] & 1, g[1] & 1, DIM == 3 ? (g[2] & 1) : 0};
+  const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
+  const T* cb = (const T*)a.cbuf + C.off;
+  const T* bn = cb + (BX + n) * C.fs + row[4];
+  T v;
+  if (!par[n]) {
+    v = coincident<T, DIM>(bn, st, n, par);
+  } else {
+    const T lo_v = coincident<T, DIM>(bn, st, n, par);
+    const T hi_v = coincident<T, DIM>(bn + st[n], st, n, par);
+    T corr = T(0);
+    bool first = true;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == n) continue;
+      const T* bt_lo = cb + (BX + t) * C.fs + row[4];
+      const T* bt_hi = bt_lo + st[t];
+      const T s_hi = mm(bt_hi[0] - bt_hi[-st[n]], bt_hi[st[n]] - bt_hi[0]);
+      const T s_lo = mm(bt_lo[0] - bt_lo[-st[n]], bt_lo[st[n]] - bt_lo[0]);
+      const T term = (T)a.ratio[n][t] * (s_hi - s_lo);
+      corr = first ? (T(0) + term) : (corr + term);
+      first = false;
+    }
+    v = T(0.5) * (lo_v + hi_v) + T(0.125) * corr;
+  }
+  ((T*)a.fbuf)[D.off + (BX + n) * D.fs + row[2]] = v;
+}
+
+// ------------------------------------------------------------------ reflux and restriction
+// rows (l, qc, Lcell, f0..f5); R = (S1 + S2) - C per C/F face, applied in slot order
+template <class T, int DIM> __global__ void k_reflux_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 9 * r;
+  const DPatch P = a.P[row[1]];
+  T* U = (T*)a.cbuf + P.off + row[2];
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    double v = (double)U[f * P.fs];
+    for (int slot = 0; slot < 2 * DIM; ++slot) {
+      const int e = row[3 + slot];
+      if (e < 0) continue;
+      const double R = (a.freg[(2 * (long long)e) * 6 + n] + a.freg[(2 * (long long)e + 1) * 6 + n]) - a.creg[(long long)e * 6 + n];
+      if (slot & 1) v = v - R * a.idx[slot >> 1];
+      else v = v + R * a.idx[slot >> 1];
+    }
+    U[f * P.fs] = (T)v;
+  }
+}
+
+// rows (l, qc, d, Lface, e0..e3): B += +e0/dx_t1 - e1/dx_t1 - e2/dx_t2 + e3/dx_t2
+template <class T, int DIM> __global__ void k_reflux_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 8 * r;
+  const DPatch P = a.P[row[1]];
+  const int d = row[2];
+  T* B = (T*)a.cbuf + P.off + (BX + d) * P.fs + row[3];
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  double v = (double)B[0];
+#pragma unroll
+  for (int slot = 0; slot < 4; ++slot) {
+    const int e = row[4 + slot];
+    if (e < 0) continue;
+    const double RE = (a.efreg[2 * (long long)e] + a.efreg[2 * (long long)e + 1]) - a.ecreg[e];
+    const double coef = slot == 0 ? a.idx[t1] : slot == 1 ? -a.idx[t1] : slot == 2 ? -a.idx[t2] : a.idx[t2];
+    v = v + coef * RE;
+  }
+  B[0] = (T)v;
+}
+
+// rows (l, qc, Lcell, pf, Lchild0)
+template <class T, int DIM> __global__ void k_restrict_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 5 * r;
+  const DPatch C = a.P[row[1]], F = a.P[row[3]];
+  T* dst = (T*)a.cbuf + C.off + row[2];
+  const T* src = (const T*)a.fbuf + F.off + row[4];
+  const int sy = F.ext[0], sz = F.ext[0] * F.ext[1];
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    const T* c = src + f * F.fs;
+    double s;
+    if (DIM == 2) {
+      s = tree4((double)c[0], (double)c[1], (double)c[sy], (double)c[sy + 1]) * 0.25;
+    } else {
+      const double v[8] = {(double)c[0], (double)c[1], (double)c[sy], (double)c[sy + 1],
+                           (double)c[sz], (double)c[sz + 1], (double)c[sz + sy], (double)c[sz + sy + 1]};
+      s = tree8(v) * 0.125;
+    }
+    dst[f * C.fs] = (T)s;
+  }
+}
+
+// rows (l, qc, d, Lface, pf, Lfine0)
+template <class T, int DIM> __global__ void k_restrict_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch C = a.P[row[1]], F = a.P[row[4]];
+  const int d = row[2];
+  const T* c = (const T*)a.fbuf + F.off + (BX + d) * F.fs + row[5];
+  const int sx = 1, sy = F.ext[0], sz = F.ext[0] * F.ext[1];
+  double s;
+  if (DIM == 2) {
+    s = tree2((double)c[0], (double)c[d == 0 ? sy : sx]) * 0.5;
+  } else {
+    int o1, o2;
+    if (d == 0) { o1 = sy; o2 = sz; }
+    else if (d == 1) { o1 = sx; o2 = sz; }
+    else { o1 = sx; o2 = sy; }
+    s = tree4((double)c[0], (double)c[o1], (double)c[o2], (double)c[o1 + o2]) * 0.25;
+  }
+  ((T*)a.cbuf)[C.off + (BX + d) * C.fs + row[3]] = (T)s;
+}
+
+// ------------------------------------------------------------------ CFL
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs a) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  double rate = 0.0;
+  bool bad = false;
+  if (region_cell<DIM>(P, 0, blockIdx.x * TPB + threadIdx.x, i, j, k)) {
+    const int L = lidx(P, i, j, k);
+    const long long fs = P.fs;
+    const T* U = (const T*)a.cur + P.off;
+    double u[5], bc[3], w[8];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) u[f] = (double)U[f * fs + L];
+    bc[0] = 0.5 * ((double)U[5 * fs + L] + (double)U[5 * fs + L + 1]);
+    bc[1] = 0.5 * ((double)U[6 * fs + L] + (double)U[6 * fs + L + P.ext[0]]);
+    if (DIM == 3) bc[2] = 0.5 * ((double)U[7 * fs + L] + (double)U[7 * fs + L + P.ext[0] * P.ext[1]]);
+    else bc[2] = (double)U[7 * fs + L];
+    recover(u, bc, a.gamma - 1.0, w);
+    if (!(w[0] > 0.0) || !(w[4] > 0.0)) bad = true;
+    else {
+      double rr = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const int t = (d + 1) % 3, uu = (d + 2) % 3;
+        const double cf = cfast<double>(w[0], w[4], w[5 + d], w[5 + t], w[5 + uu], a.gamma);
+        rr = rr + (fabs(w[1 + d]) + cf) * a.idx[d];
+      }
+      if (!(rr == rr) || rr > 1.79e308) bad = true;
+      else rate = rr;
+    }
+  }
+  if (bad) atomicOr(a.err, 1u);
+  rate = warp_max(rate);
+  __shared__ double red[TPB / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < TPB / 32 ? red[threadIdx.x] : 0.0;
+    v = warp_max(v);
+    if (threadIdx.x == 0) atomicMax(a.slot, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// ------------------------------------------------------------------ packed I/O
+template <class T, int DIM>
+__global__ void __launch_bounds__(TPB) k_io(const DPatch* PP, const int* ids, void* state, double* packed,
+                                            const long long* poff, int field, int to_state) {
+  const int pid = ids[blockIdx.y];
+  const DPatch P = PP[pid];
+  const int fd = (field >= BX && !(DIM == 2 && field == BZ)) ? field - BX : -1;
+  int r[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r[e] = e >= DIM ? 1 : P.n[e] + (e == fd ? 1 : 0);
+  const int t = blockIdx.x * TPB + threadIdx.x;
+  if (t >= r[0] * r[1] * r[2]) return;
+  const int i = t % r[0], j = (t / r[0]) % r[1], k = t / (r[0] * r[1]);
+  const int L = lidx(P, i + 4, j + 4, DIM == 3 ? k + 4 : 0);
+  T* s = (T*)state + P.off + field * P.fs + L;
+  double* q = packed + poff[pid] + t;
+  if (to_state) *s = (T)*q;
+  else *q = (double)*s;
+}
+
+// ------------------------------------------------------------------ launchers
+template <class T, int DIM> struct Impl {
+  static dim3 grid_region(const LevelArgs& a, int m, int extra) {
+    long long n = 1;
+    for (int d = 0; d < DIM; ++d) n *= a.maxn[d] + 2 * m + extra;
+    return dim3(cdiv(n, TPB), a.npatch);
+  }
+  static void advance(const LevelArgs& a, cudaStream_t s, int* nl) {
+    k_prim<T, DIM><<<grid_region(a, a.w + 2, 0), TPB, 0, s>>>(a);
+    k_predict<T, DIM><<<grid_region(a, a.w + 1, 0), TPB, 0, s>>>(a);
+    k_flux<T, DIM, 0><<<grid_region(a, a.w + 1, 0), TPB, 0, s>>>(a);
+    k_flux<T, DIM, 1><<<grid_region(a, a.w + 1, 0), TPB, 0, s>>>(a);
+    if (DIM == 3) k_flux<T, DIM, 2><<<grid_region(a, a.w + 1, 0), TPB, 0, s>>>(a);
+    if (DIM == 3) {
+      k_emf<T, DIM, 0><<<grid_region(a, a.w, 1), TPB, 0, s>>>(a);
+      k_emf<T, DIM, 1><<<grid_region(a, a.w, 1), TPB, 0, s>>>(a);
+    }
+    k_emf<T, DIM, 2><<<grid_region(a, a.w, 1), TPB, 0, s>>>(a);
+    k_update<T, DIM><<<grid_region(a, a.w, 0), TPB, 0, s>>>(a);
+    if (nl) *nl += DIM == 3 ? 9 : 6;
+  }
+  static void reg_coarse(const RowArgs& f, const RowArgs& e, cudaStream_t s, int* nl) {
+    if (f.nrows) { k_reg_coarse_faces<T, DIM><<<cdiv(f.nrows, TPB), TPB, 0, s>>>(f); if (nl) ++*nl; }
+    if (e.nrows) { k_reg_coarse_edges<T, DIM><<<cdiv(e.nrows, TPB), TPB, 0, s>>>(e); if (nl) ++*nl; }
+  }
+  static void reg_fine(const RowArgs& f, const RowArgs& e, cudaStream_t s, int* nl) {
+    if (f.nrows) { k_reg_fine_faces<T, DIM><<<cdiv(f.nrows, TPB), TPB, 0, s>>>(f); if (nl) ++*nl; }
+    if (e.nrows) { k_reg_fine_edges<T, DIM><<<cdiv(e.nrows, TPB), TPB, 0, s>>>(e); if (nl) ++*nl; }
+  }
+#define AMRK_ROWS(NAME)                                                                 \
+  static void NAME(const RowArgs& a, cudaStream_t s, int* nl) {                         \
+    if (!a.nrows) return;                                                               \
+    k_##NAME<T, DIM><<<cdiv(a.nrows, TPB), TPB, 0, s>>>(a);                             \
+    if (nl) ++*nl;                                                                      \
+  }
+  AMRK_ROWS(fill_same_cells)
+  AMRK_ROWS(fill_same_faces)
+  AMRK_ROWS(prolong_cells)
+  AMRK_ROWS(prolong_faces)
+  AMRK_ROWS(reflux_cells)
+  AMRK_ROWS(reflux_faces)
+  AMRK_ROWS(restrict_cells)
+  AMRK_ROWS(restrict_faces)
+#undef AMRK_ROWS
+  static void cfl(const CflArgs& a, cudaStream_t s, int* nl) {
+    long long n = 1;
+    for (int d = 0; d < DIM; ++d) n *= a.maxn[d];
+    k_cfl<T, DIM><<<dim3(cdiv(n, TPB), a.npatch), TPB, 0, s>>>(a);
+    if (nl) ++*nl;
+  }
+  static void io(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
+                 const long long* poff, int field, int to_state, cudaStream_t s, int* nl) {
+    long long n = 1;
+    for (int d = 0; d < DIM; ++d) n *= maxn[d] + 1;
+    k_io<T, DIM><<<dim3(cdiv(n, TPB), npatch), TPB, 0, s>>>(P, ids, state, packed, poff, field, to_state);
+    if (nl) ++*nl;
+  }
+  static const Ops* ops() {
+    static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, prolong_cells,
+                          prolong_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
+                          sizeof(T)};
+    return &o;
+  }
+};
+
+}  // namespace AMRK_NS

@@ -290,8 +290,9 @@ def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
                 if phi - plo < 2:
                     ok = False
                     break
+                wmax = 10 if l - 1 == 0 else 6
                 a = int(rng.integers(plo, phi - 1))
-                b = int(rng.integers(a + 1, min(phi, a + 6) + 1))
+                b = int(rng.integers(min(a + 4, phi) if l - 1 == 0 else a + 1, min(phi, a + wmax) + 1))
                 lo.append(2 * a)
                 hi.append(2 * b)
             if not ok:

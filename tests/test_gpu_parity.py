@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the
+same seeded inputs, plus properties that hold at any size.
+
+Tolerances: FP64 (strict build, no FMA contraction) must match the oracle to
+1e-12 relative L1 per field (it is expected to be bitwise identical; the dt
+sequence must be bitwise identical since the CFL maximum is order-free). The
+mixed FP32 path must be within 1e-5 relative L1 per field on smooth problems.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import compare_states, gpu_level_arrays, max_err, oracle_for, rel_l1
+from paper_1110_1616_gb300 import amrmhd as A
+from paper_1110_1616_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_1616_gb300 import build
+    build.build()
+
+
+def gpu_for(pb, precision=A.FP64, strict=True, graph=True, baseline=False):
+    import torch
+    s = torch.cuda.Stream()
+    ctx = A.context_for(pb, precision=precision, strict_fp64=strict, stream=s.cuda_stream)
+    if not graph:
+        ctx.set_option(A.OPT_GRAPH, 0)
+    if baseline:
+        ctx.set_option(A.OPT_ADVANCE, 1)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    ctx.load_state(pb.state)
+    return ctx
+
+
+def run_both(pb, nsteps, precision=A.FP64, strict=True):
+    ctx = gpu_for(pb, precision, strict)
+    dts = ctx.step(nsteps)
+    o = oracle_for(pb)
+    odts = np.array([o.step() for _ in range(nsteps)])
+    return ctx, dts, o, odts
+
+
+def test_ot_amr_fp64_config1_full():
+    """2D Orszag-Tang, 64^2 base in 16^2 patches + one refined level over the
+    central 32^2 base cells, seeded noise 1e-3, 50 coarse steps, FP64."""
+    pb = inputs.orszag_tang(64, 16, refine=True, noise=1e-3, seed=1)
+    ctx, dts, o, odts = run_both(pb, 50)
+    assert np.array_equal(dts, odts), np.abs(dts - odts).max()
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+def test_blast3d_fp64_reduced():
+    """3D blast (config-2 physics) at 32^3 in 16^3 patches, 30 steps, FP64."""
+    pb = inputs.blast_3d(32, 16)
+    ctx, dts, o, odts = run_both(pb, 30)
+    assert np.array_equal(dts, odts)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+def test_3d_amr_fp64():
+    base = (16, 16, 16)
+    patches = inputs.tile(0, (0, 0, 0), base, 8, 3) + inputs.tile(1, (8, 8, 8), (24, 16, 24), 8, 3) \
+        + inputs.tile(1, (8, 16, 8), (16, 24, 16), 8, 3)
+    st = {0: inputs.blast_3d(16, 8).state[0], 1: inputs.blast_3d(32, 8).state[0]}
+    pb = inputs.Problem("blast3d_amr", 3, base, patches, 2, st)
+    ctx, dts, o, odts = run_both(pb, 8)
+    assert np.array_equal(dts, odts)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_hierarchy_2d_fp64(seed):
+    patches = inputs.random_hierarchy(2, seed, base=32, nlev=3)
+    nlev = max(p[0] for p in patches) + 1
+    pb = inputs.Problem("rand2d", 2, (32, 32, 1), patches, nlev, inputs.random_smooth_2d(32, nlev, seed=seed))
+    ctx, dts, o, odts = run_both(pb, 6)
+    assert np.array_equal(dts, odts)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+def test_random_hierarchy_3d_fp64():
+    patches = inputs.random_hierarchy(3, 10, base=16, nlev=2)
+    st = {0: inputs.blast_3d(16, 8).state[0], 1: inputs.blast_3d(32, 8).state[0]}
+    pb = inputs.Problem("rand3d", 3, (16, 16, 16), patches, 2, st)
+    ctx, dts, o, odts = run_both(pb, 4)
+    assert np.array_equal(dts, odts)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+def test_ot_amr_fp64_fast_build():
+    """FP64 with FMA contraction allowed: still within 1e-12 of the oracle."""
+    pb = inputs.orszag_tang(64, 16, refine=True)
+    ctx, dts, o, odts = run_both(pb, 20, strict=False)
+    assert np.allclose(dts, odts, rtol=1e-13, atol=0)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
+def test_mixed_smooth_amr_within_1e5():
+    """Mixed precision (FP32 stencil, FP64 recovery/registers/dt) against the
+    FP64 oracle on a smooth 2D problem with a refined quadrant across the
+    periodic seam: relative L1 per field <= 1e-5."""
+    base = (64, 64, 1)
+    patches = inputs.tile(0, (0, 0, 0), base, 16, 2) + inputs.tile(1, (0, 0, 0), (64, 64, 1), 16, 2)
+    pb = inputs.Problem("smooth_quadrant", 2, base, patches, 2, inputs.random_smooth_2d(64, 2, seed=3))
+    ctx, dts, o, odts = run_both(pb, 20, precision=A.MIXED)
+    assert np.allclose(dts, odts, rtol=1e-5)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-5, res
+
+
+def test_mixed_alfven_within_1e5():
+    pb = inputs.alfven_2d(64, 16, amp=1e-2)
+    ctx, dts, o, odts = run_both(pb, 40, precision=A.MIXED)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-5, res
+
+
+@pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
+def test_uniform_state_preserved(precision):
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    pb.state = inputs.uniform_state(2, pb.base, pb.patches, pb.nlev, seed=4)
+    ctx = gpu_for(pb, precision)
+    ctx.step(3)
+    g = gpu_level_arrays(ctx, pb)
+    for l in range(pb.nlev):
+        for f in range(8):
+            a = g[l][f]
+            v = pb.state[l][f].flat[0]
+            if precision == A.MIXED:
+                v = np.float32(v)
+            assert np.all(a[~np.isnan(a)] == v), (l, f)
+
+
+def composite(ctx, pb):
+    g = gpu_level_arrays(ctx, pb)[0]
+    vol = 1.0 / g[0].size
+    return np.array([np.nansum(g[f]) * vol for f in range(5)])
+
+
+def test_conservation_across_cf_boundaries_fp64():
+    pb = inputs.orszag_tang(64, 16, refine=True)
+    ctx = gpu_for(pb, A.FP64, strict=False)
+    ctx.step(1)
+    ref = composite(ctx, pb)
+    ctx.step(10)
+    tot = composite(ctx, pb)
+    scale = np.abs(ref).max()
+    assert np.all(np.abs(tot - ref) <= 1e-13 * scale), tot - ref
+
+
+def test_divb_roundoff_gpu():
+    pb = inputs.orszag_tang(64, 16, refine=True)
+    for precision, tol in ((A.FP64, 1e-13), (A.MIXED, 1e-5)):
+        ctx = gpu_for(pb, precision)
+        ctx.step(10)
+        per = ctx.read_state()
+        for p, (l, lo, hi) in enumerate(pb.patches):
+            bx, by = per[5][p][0], per[6][p][0]
+            n = 64 << l
+            d = (bx[:, 1:] - bx[:, :-1]) * n + (by[1:, :] - by[:-1, :]) * n
+            bmax = max(np.abs(bx).max(), np.abs(by).max())
+            assert np.abs(d).max() <= tol * bmax * n, (precision, p)
+
+
+def test_graph_equals_direct_calls():
+    """The captured coarse step equals the same sequence of C-ABI calls
+    (fill, advance, reflux/restrict in the order 0,1,1) bitwise."""
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    a = gpu_for(pb, A.FP64)
+    a.step(3)
+    b = gpu_for(pb, A.FP64)
+    for _ in range(3):
+        dt = b.cfl_dt()
+        b.fill_ghosts(0, 1)
+        b.advance_level(0, dt, 1)
+        b.fill_ghosts(1, 1)
+        b.advance_level(1, dt * 0.5, 1)
+        b.fill_ghosts(1, 2)
+        b.advance_level(1, dt * 0.5, 2)
+        b.reflux_restrict(1)
+    sa, sb = a.read_state(), b.read_state()
+    for f in range(8):
+        for p in range(len(pb.patches)):
+            assert np.array_equal(sa[f][p], sb[f][p]), (f, p)
+
+
+def test_one_patch_per_launch_baseline_equals_batched():
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    a = gpu_for(pb, A.FP64)
+    a.step(3)
+    b = gpu_for(pb, A.FP64, baseline=True, graph=False)
+    b.step(3)
+    sa, sb = a.read_state(), b.read_state()
+    for f in range(8):
+        for p in range(len(pb.patches)):
+            assert np.array_equal(sa[f][p], sb[f][p]), (f, p)
+
+
+def test_nonphysical_state_reported():
+    pb = inputs.orszag_tang(32, 8, refine=False)
+    pb.state[0][4] = pb.state[0][4].copy()
+    pb.state[0][4][0, 3, 3] = -1.0  # negative total energy -> negative pressure
+    ctx = gpu_for(pb, A.FP64)
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx.cfl_dt()
+    assert e.value.status == A.ENONPHYS
+
+
+@pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
+def test_blast3d_full_size_sampled(precision):
+    """Config-2 size (128^3, 512 patches of 16^3) in the launch configuration
+    the benchmark times: after one graph step, sampled cells (interior, patch
+    corners and edges, across the periodic seam) equal the oracle's one-by-one
+    update of those cells from the same state and dt."""
+    pb = inputs.blast_3d(128, 16)
+    ctx = gpu_for(pb, precision, strict=True)
+    dt = ctx.step(1)[0]
+    g = gpu_level_arrays(ctx, pb)[0]
+    rng = np.random.default_rng(0)
+    pts = [(0, 0, 0), (127, 127, 127), (15, 16, 17), (63, 64, 64), (64, 63, 50), (31, 0, 127), (50, 50, 50)]
+    pts += [tuple(int(x) for x in rng.integers(0, 128, 3)) for _ in range(40)]
+    o = oracle_for(pb)
+    o.step_targets(dt, pts)
+    ost = o.get_state()[0]
+    tol = 1e-12 if precision == A.FP64 else 1e-5
+    for (i, j, k) in pts:
+        for f in range(5):
+            ov, gv = ost[f][k, j, i], g[f][k, j, i]
+            assert abs(gv - ov) <= tol * (abs(ov) + 1e-30) + (0 if precision == A.FP64 else 1e-6), (i, j, k, f, gv, ov)
+        for f, (a, b, c) in ((5, (i, j, k)), (6, (i, j, k)), (7, (i, j, k))):
+            ov, gv = ost[f][c, b, a], g[f][c, b, a]
+            assert abs(gv - ov) <= tol * (abs(ov) + 1e-30) + (0 if precision == A.FP64 else 1e-6), (i, j, k, f, gv, ov)

@@ -1,0 +1,134 @@
+"""CPU-only checks of the C-ABI library: it builds, loads and exports every
+entry point the header declares; the host-side hierarchy builder (neighbours by
+inheritance, Sec. 3.1) reproduces the oracle's brute-force integer maps bit for
+bit; malformed hierarchies return the documented error codes. No kernel runs."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import build_map
+from paper_1110_1616_gb300 import amrmhd as A
+from paper_1110_1616_gb300 import build as B
+from paper_1110_1616_gb300 import inputs
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_exports_every_declared_symbol():
+    names = A.declared_symbols()
+    assert len(names) >= 18
+    L = ctypes.CDLL(A.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def ctx_for(dim, base, patches, max_level=10):
+    cfg = A.make_config(dim, base, max_level=max_level)
+    c = A.Context(cfg)
+    c.set_hierarchy(patches)
+    return c
+
+
+def hierarchies():
+    out = [
+        ("ot_amr", 2, (32, 32, 1), inputs.orszag_tang(32, 8, refine=True).patches),
+        ("seam_quadrant", 2, (32, 32, 1), inputs.tile(0, (0, 0, 0), (32, 32, 1), 8, 2) + inputs.tile(1, (0, 0, 0), (32, 32, 1), 8, 2)),
+        ("single_patch_levels", 2, (16, 16, 1), [(0, (0, 0, 0), (16, 16, 1)), (1, (8, 8, 0), (24, 24, 1))]),
+        ("everywhere_refined", 2, (16, 16, 1), inputs.tile(0, (0, 0, 0), (16, 16, 1), 8, 2) + [(1, (0, 0, 0), (32, 32, 1))]),
+        ("3d_two_boxes", 3, (16, 16, 16), inputs.tile(0, (0, 0, 0), (16, 16, 16), 8, 3)
+         + inputs.tile(1, (8, 8, 8), (24, 16, 24), 8, 3) + inputs.tile(1, (8, 16, 8), (16, 24, 16), 8, 3)),
+    ]
+    for seed in range(4):
+        out.append(("rand2d_%d" % seed, 2, (32, 32, 1), inputs.random_hierarchy(2, seed, base=32, nlev=3)))
+    for seed in range(2):
+        out.append(("rand3d_%d" % seed, 3, (16, 16, 16), inputs.random_hierarchy(3, 10 + seed, base=16, nlev=2)))
+    return out
+
+
+HIERS = hierarchies()
+
+
+@pytest.mark.parametrize("name,dim,base,patches", HIERS, ids=[h[0] for h in HIERS])
+def test_maps_bit_exact_vs_oracle(name, dim, base, patches):
+    c = ctx_for(dim, base, patches)
+    for which in A.MAPS:
+        got = c.export_map(which)
+        exp = build_map(dim, base, patches, which)
+        assert got.shape == exp.shape, (which, got.shape, exp.shape)
+        assert np.array_equal(got, exp), which
+
+
+def test_error_codes():
+    base = (32, 32, 1)
+    lvl0 = inputs.tile(0, (0, 0, 0), base, 16, 2)
+    # misaligned fine patch
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(2, base, lvl0 + [(1, (21, 20, 0), (30, 30, 1))])
+    assert e.value.status == A.EINVAL
+    # overlap on level 1
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(2, base, lvl0 + [(1, (20, 20, 0), (30, 30, 1)), (1, (24, 24, 0), (34, 34, 1))])
+    assert e.value.status == A.EOVERLAP
+    # nesting: level 2 box touching the edge of the level-1 region
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(2, base, lvl0 + [(1, (20, 20, 0), (40, 40, 1)), (2, (40, 40, 0), (48, 48, 1))])
+    assert e.value.status == A.ENEST
+    # level 0 must tile the domain
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(2, base, lvl0[:-1])
+    assert e.value.status == A.EINVAL
+    # level gap
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(2, base, lvl0 + [(2, (40, 40, 0), (48, 48, 1))])
+    assert e.value.status == A.EINVAL
+    # calls out of order
+    c = A.Context(A.make_config(2, base))
+    with pytest.raises(A.AmrmhdError) as e:
+        c.fill_ghosts(0, 1)
+    assert e.value.status == A.ESTATE
+    c.set_hierarchy(lvl0)
+    with pytest.raises(A.AmrmhdError) as e:
+        c.advance_level(0, 1e-3, 1)
+    assert e.value.status == A.ESTATE
+
+
+def test_nesting_matches_oracle_validation():
+    """The library's nesting check and the oracle's agree on random boxes."""
+    from oracle import OracleSim
+    rng = np.random.default_rng(5)
+    base = (32, 32, 1)
+    lvl0 = inputs.tile(0, (0, 0, 0), base, 16, 2)
+    l1 = [(1, (16, 16, 0), (48, 48, 1))]
+    agree = 0
+    for _ in range(40):
+        a = int(rng.integers(14, 44)) * 2
+        b = int(rng.integers(14, 44)) * 2
+        w = int(rng.integers(2, 8)) * 2
+        p2 = [(2, (a, b, 0), (min(a + w, 128), min(b + w, 128), 1))]
+        try:
+            OracleSim(2, base, lvl0 + l1 + p2)
+            ok_o = True
+        except ValueError:
+            ok_o = False
+        try:
+            ctx_for(2, base, lvl0 + l1 + p2)
+            ok_l = True
+        except A.AmrmhdError:
+            ok_l = False
+        assert ok_o == ok_l, p2
+        agree += 1
+    assert agree == 40
+
+
+def test_query_counts():
+    pb = inputs.orszag_tang(64, 16, refine=True)
+    c = A.context_for(pb)
+    assert c.query(A.Q_NPATCH) == 32
+    assert c.query(A.Q_NLEVEL) == 2
+    assert c.query(A.Q_CELLS) == 64 * 64 + 64 * 64
+    assert c.query(A.Q_CELL_UPDATES_PER_STEP) == 64 * 64 + 2 * 64 * 64
+    assert c.query(A.Q_ARENA_BYTES) > 0
