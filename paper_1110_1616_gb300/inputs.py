@@ -88,9 +88,13 @@ def _cell_b_from_faces(bx, by, bz, dim):
 
 
 def _b_from_az_2d(az_corner, n, dx, dy):
-    """Face B from a corner vector potential A_z of shape (Ny+1, Nx+1)."""
+    """Face B from a corner vector potential A_z of shape (Ny+1, Nx+1). The
+    periodic copy (entry N along the face normal) is set to entry 0 exactly,
+    so that both stored copies of a seam face agree bit for bit."""
     bx = (az_corner[1:, :] - az_corner[:-1, :]) / dy  # (Ny, Nx+1)
     by = -(az_corner[:, 1:] - az_corner[:, :-1]) / dx  # (Ny+1, Nx)
+    bx[:, -1] = bx[:, 0]
+    by[-1, :] = by[0, :]
     return bx[None], by[None]
 
 
