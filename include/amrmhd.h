@@ -203,6 +203,32 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx);
 
+/* Advance of ONE patch that allocates no device memory (no counterpart in the
+ * paper: it exists for callers that cannot call cudaMalloc, e.g. code running
+ * under a memory pool that forbids new allocations, a real-time loop that must
+ * not enter the allocator, or a library handed only the state pointers).
+ * Mixed precision (FP32 stencil, FP64 primitive recovery), the same staged
+ * kernels as advance_level. Its intermediate arrays live in one fixed device
+ * array of 256 B + 70 x 16384 x 4 B (about 4.6 MB) that every GPU loading the
+ * library holds until the process exits.
+ *  u_in:  device pointer, 8 consecutive float arrays (rho, mx, my, mz, E, Bx,
+ *         By, Bz), each over the ghosted box of extent (n_x+9)(n_y+9)(n_z+9)
+ *         (2D: (n_x+9)(n_y+9)), x fastest, index as in the state layout above;
+ *         the caller fills the 4 ghost layers (cells and faces).
+ *  u_out: device pointer, same layout; the cells of the interior widened by w
+ *         layers and their faces are written, nothing else.
+ *  dim 2 or 3; n[dim] interior extents; dx[dim] cell sizes; gamma; dt; w = 0
+ *  (interior) or 2 (interior + 2 ghost layers); cuda_stream (NULL = legacy
+ *  default stream). Returns AMRMHD_EINVAL for bad arguments or when
+ *  (n_x+9)(n_y+9)(n_z+9) > 16384 (e.g. 3D patches above 16^3), AMRMHD_ECUDA if
+ *  a CUDA call fails. The first call on a device looks up the array's device
+ *  address (once per device, with that device current): make that first call
+ *  before any stream capture. Every call shares the array and it keeps the last
+ *  call's contents (every entry read is written earlier in the same call, so
+ *  nothing needs clearing); calls that overlap on the GPU race on it. */
+amrmhd_status amrmhd_advance_patch_noalloc(const float* u_in, float* u_out, int32_t dim, const int32_t* n,
+                                           const double* dx, double gamma, double dt, int32_t w, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.amrmhd_advance_patch_noalloc.argtypes = [vp, vp, i32, C.POINTER(i32), C.POINTER(dbl), dbl, dbl, i32, vp]
+        L.amrmhd_advance_patch_noalloc.restype = C.c_int
         L.amrmhd_last_error.argtypes = [vp]
         L.amrmhd_last_error.restype = C.c_char_p
         _lib = L
@@ -262,6 +264,17 @@ class Context:
         self._check(lib().amrmhd_export_map(self.h, which, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n),
                                             C.byref(w)), "export_map")
         return out[: n.value].reshape(-1, w.value)
+
+
+def advance_patch_noalloc(u_in, u_out, dim, n, dx, gamma, dt, w=0, stream=None):
+    """One-patch advance that allocates nothing (see include/amrmhd.h):
+    u_in/u_out are device float tensors in the ghosted single-patch layout."""
+    ni = (C.c_int32 * 3)(*(list(n) + [1] * (3 - len(n))))
+    dd = (C.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    st = lib().amrmhd_advance_patch_noalloc(C.c_void_p(u_in.data_ptr()), C.c_void_p(u_out.data_ptr()), dim, ni, dd,
+                                             float(gamma), float(dt), w, C.c_void_p(stream or 0))
+    if st != OK:
+        raise AmrmhdError(st, "advance_patch_noalloc")
 
 
 def context_for(problem, precision=FP64, strict_fp64=True, stream=None):

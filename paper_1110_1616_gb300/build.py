@@ -14,6 +14,7 @@ UNITS = [
     ("api.cu", []),
     ("kernels_fast.cu", []),
     ("kernels_strict.cu", ["--fmad=false"]),
+    ("noalloc.cu", []),
 ]
 HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "mhd_device.cuh"]
 
