@@ -330,7 +330,7 @@ def main():
                    "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "precision": "mixed",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (arena %.2f GB: ping-pong state and stage scratch)" % arena_gb},
-        "roofline": {"bound": "hbm", "kernel": "advance_level (staged: prim, predict, 3 flux, 3 emf, update)",
+        "roofline": {"bound": "hbm", "kernel": "k_advance3d_fused<float> (one launch per level advance)",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
                      "traffic": None, "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_adv},

@@ -195,9 +195,13 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
 
 /* Options (set before set_hierarchy): AMRMHD_OPT_* */
 enum {
-  AMRMHD_OPT_ADVANCE = 0,  /* 0: staged kernels batched over a level (default); 1: the
-                              same kernels launched one patch at a time (baseline) */
-  AMRMHD_OPT_GRAPH = 1     /* 1 (default): amrmhd_step replays a CUDA graph; 0: plain launches */
+  AMRMHD_OPT_ADVANCE = 0,  /* 0 (default): in 3D one fused kernel per level advance (no
+                              scratch), in 2D the staged kernels batched over the level;
+                              1: the staged kernels launched one patch at a time (baseline);
+                              2: the staged kernels batched over the level */
+  AMRMHD_OPT_GRAPH = 1,    /* 1 (default): amrmhd_step replays a CUDA graph; 0: plain launches */
+  AMRMHD_OPT_TILE = 2      /* fused 3D advance tile: -1 default (16x8 FP32, 8x8 FP64), 0: 16x16 tile
+                              with 256 threads, 1: 16x16 / 512, 2: 16x8 / 256, 3: 8x8 / 256 */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

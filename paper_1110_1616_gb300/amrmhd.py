@@ -19,7 +19,7 @@ MAPS = {
     "emf_faces": 5, "restrict_cells": 6, "restrict_faces": 7, "reflux_cells": 8,
 }
 Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
-OPT_ADVANCE, OPT_GRAPH = 0, 1
+OPT_ADVANCE, OPT_GRAPH, OPT_TILE = 0, 1, 2
 
 
 class AmrmhdError(RuntimeError):

@@ -43,7 +43,8 @@ struct amrmhd_ctx {
   bool have_h = false, bound = false;
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
-  int64_t opt_advance = 0, opt_graph = 1;
+  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1;
+  bool fused() const { return cfg.dim == 3 && opt_advance == 0; }
   // arena layout (bytes)
   std::vector<long long> off, fs, soff;
   long long state_elems = 0, scr_elems = 0;
@@ -186,9 +187,17 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   }
 }
 
+void level_idx(amrmhd_ctx* ctx, int l, double* idx) {
+  for (int d = 0; d < 3; ++d) {
+    int N = d < ctx->cfg.dim ? (ctx->cfg.base[d] << l) : 1;
+    idx[d] = 1.0 / (d < ctx->cfg.dim ? (ctx->cfg.hi[d] - ctx->cfg.lo[d]) / N : 1.0);
+  }
+}
+
 void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, int* nl) {
   const int w = (l == 0) ? 0 : (s == 1 ? 2 : 0);
   LevelArgs a = level_args(ctx, l, dtp, dtscale, w);
+  const bool fused = ctx->fused();
   if (ctx->opt_advance == 1) {
     // one launch sequence per patch (baseline)
     const LevelDev& L = ctx->lev[l];
@@ -198,6 +207,9 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
       b.npatch = 1;
       ctx->ops->advance(b, ctx->stream, nl);
     }
+  } else if (fused) {
+    const int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
+    ctx->ops->advance_fused(a, v, ctx->stream, nl);
   } else {
     ctx->ops->advance(a, ctx->stream, nl);
   }
@@ -208,10 +220,17 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
     offset_regs(ctx, f, l + 1);
     f.dtp = dtp;
     f.dtscale = dtscale;
+    f.fbuf = state_buf(ctx, ctx->cur[l]);
     RowArgs e = f;
     e.rows = F.cf_edges.p;
     e.nrows = F.cf_edges.n;
-    ctx->ops->reg_coarse(f, e, ctx->stream, nl);
+    if (fused) {
+      double idx[3];
+      level_idx(ctx, l, idx);
+      ctx->ops->reg_coarse_rc(f, e, idx, ctx->cfg.gamma, ctx->stream, nl);
+    } else {
+      ctx->ops->reg_coarse(f, e, ctx->stream, nl);
+    }
   }
   if (l > 0) {
     const LevelDev& F = ctx->lev[l];
@@ -220,10 +239,17 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
     f.dtp = dtp;
     f.dtscale = dtscale;
     f.substep = s;
+    f.fbuf = state_buf(ctx, ctx->cur[l]);
     RowArgs e = f;
     e.rows = F.cf_edges.p;
     e.nrows = F.cf_edges.n;
-    ctx->ops->reg_fine(f, e, ctx->stream, nl);
+    if (fused) {
+      double idx[3];
+      level_idx(ctx, l, idx);
+      ctx->ops->reg_fine_rc(f, e, idx, ctx->cfg.gamma, ctx->stream, nl);
+    } else {
+      ctx->ops->reg_fine(f, e, ctx->stream, nl);
+    }
   }
   ctx->cur[l] ^= 1;
 }
@@ -344,8 +370,9 @@ amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx) {
 
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) {
   if (!ctx) return AMRMHD_EINVAL;
-  if (option == AMRMHD_OPT_ADVANCE && (value == 0 || value == 1)) ctx->opt_advance = value;
+  if (option == AMRMHD_OPT_ADVANCE && (value == 0 || value == 1 || value == 2)) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
+  else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 3) ctx->opt_tile = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -382,7 +409,7 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
       ctx->off[q] = acc;
       acc += 8 * f;
       ctx->soff[q] = sacc;
-      sacc += amrk::SC_N * f;
+      if (!ctx->fused()) sacc += amrk::SC_N * f;
     }
   ctx->state_elems = acc;
   ctx->scr_elems = sacc;
@@ -519,6 +546,8 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
   }
   ctx->cur.assign(nlev, 0);
   ctx->start.assign(nlev, 0);
+  ctx->ops->prepare();
+  CU(cudaGetLastError());
   ctx->bound = true;
   return AMRMHD_OK;
 }

@@ -84,6 +84,13 @@ struct Ops {
   void (*io)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
              const long long* poff, int field, int to_state, cudaStream_t, int* launches);
   size_t elem;  // bytes per stored value
+  // fused path (3D): one kernel per level advance, registers recomputed from the input state
+  void (*prepare)();
+  void (*advance_fused)(const LevelArgs&, int variant, cudaStream_t, int* launches);
+  void (*reg_coarse_rc)(const RowArgs& faces, const RowArgs& edges, const double* idx, double gamma, cudaStream_t,
+                        int* launches);
+  void (*reg_fine_rc)(const RowArgs& faces, const RowArgs& edges, const double* idx, double gamma, cudaStream_t,
+                      int* launches);
 };
 
 const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED

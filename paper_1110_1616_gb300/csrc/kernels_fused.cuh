@@ -1,0 +1,449 @@
+// Fused 3D level advance: one CTA per (patch, x-y tile), marching along z with
+// rolling plane buffers in shared memory, so that primitives, slopes,
+// predicted states, HLLD fluxes and CT EMFs never leave the SM. Only the state
+// is read and written in HBM. Included by kernels_impl.cuh inside AMRK_NS.
+//
+// Pipeline per iteration t (planes in patch-local storage coordinates; the
+// output z range is [zlo, zhi) = [4-w, n_z+4+w)):
+//   S1  W at plane t                     (tile + 2 halo)        -> ring of 3
+//   S2  slopes, predictor, reference EMF at plane p = t-1 (tile + 1 halo)
+//   S3  HLLD fluxes: x- and y-faces of plane p, z-faces of face plane p
+//   S4  edge EMFs: E_z at plane p, E_x and E_y at edge plane p
+//   S5  update of cell plane q = p-1: cells, B_x and B_y of plane q, B_z of face
+//       plane q (and the top face plane zhi on the last plane)
+// followed in the next iteration by S1 without a barrier (S5 touches no buffer
+// S1 writes). Buffers that span iterations are 2- or 3-slot rings by plane.
+
+// Tile variants (x-y output tile and threads per CTA), chosen by the
+// autotuning option: 0 = 16x16 / 256, 1 = 16x16 / 512, 2 = 16x8 / 256,
+// 3 = 8x8 / 256.
+template <int V> struct FusedCfg;
+template <> struct FusedCfg<0> { static constexpr int TX = 16, TY = 16, NT = 256; };
+template <> struct FusedCfg<1> { static constexpr int TX = 16, TY = 16, NT = 512; };
+template <> struct FusedCfg<2> { static constexpr int TX = 16, TY = 8, NT = 256; };
+template <> struct FusedCfg<3> { static constexpr int TX = 8, TY = 8, NT = 256; };
+
+template <class T, int TX_, int TY_> struct FusedSmem {
+  static constexpr int TX = TX_, TY = TY_;
+  static constexpr int PX = TX + 4, PY = TY + 4, P = PX * PY;  // W region
+  static constexpr int QX = TX + 2, QY = TY + 2, Q = QX * QY;  // predict / flux / EMF region
+  T w[3][8][P];
+  T wh[2][8][Q];
+  T sz[2][8][Q];
+  T sx[8][Q];
+  T sy[8][Q];
+  T ref[2][3][Q];
+  T fx[2][8][Q];
+  T fy[2][8][Q];
+  T fz[2][8][Q];
+  T ez[2][Q];
+  T ex[2][Q];
+  T ey[2][Q];
+};
+
+template <class T>
+__device__ __forceinline__ void hlld_face(const T* wl, const T* wr, int D, T gamma, T* out8) {
+  const int n = D, t = (D + 1) % 3, u = (D + 2) % 3;
+  const T bn = T(0.5) * (wl[5 + n] + wr[5 + n]);
+  const T ql[7] = {wl[0], wl[1 + n], wl[1 + t], wl[1 + u], wl[4], wl[5 + t], wl[5 + u]};
+  const T qr[7] = {wr[0], wr[1 + n], wr[1 + t], wr[1 + u], wr[4], wr[5 + t], wr[5 + u]};
+  T fr[7];
+  hlld_flux<T>(ql, qr, bn, gamma, fr);
+  out8[RHO] = fr[0];
+  out8[MX + n] = fr[1];
+  out8[MX + t] = fr[2];
+  out8[MX + u] = fr[3];
+  out8[EN] = fr[4];
+  out8[BX + t] = fr[5];
+  out8[BX + u] = fr[6];
+  out8[BX + n] = T(0);
+}
+
+template <class T>
+__device__ __forceinline__ void load_recover(const T* U, long long fs, int L, int sy, int sz, double gm1, T* w) {
+  T u[5], bl[3], br[3];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) u[f] = U[f * fs + L];
+  bl[0] = U[5 * fs + L]; br[0] = U[5 * fs + L + 1];
+  bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + sy];
+  bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + sz];
+  recover_t(u, bl, br, gm1, w);
+}
+
+template <class T, int VAR>
+__global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelArgs a, int ntx) {
+  using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
+  constexpr int TX = S::TX, TY = S::TY, PX = S::PX, QX = S::QX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S& sm = *reinterpret_cast<S*>(smem_raw);
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  const int w = a.w;
+  const int xlo = 4 - w, xhi = P.n[0] + 4 + w, ylo = 4 - w, yhi = P.n[1] + 4 + w;
+  const int zlo = 4 - w, zhi = P.n[2] + 4 + w;
+  const int tile = blockIdx.x;
+  const int x0 = xlo + (tile % ntx) * TX, y0 = ylo + (tile / ntx) * TY;
+  if (x0 >= xhi || y0 >= yhi) return;
+  const int tx = min(TX, xhi - x0), ty = min(TY, yhi - y0);
+  const bool last_x = x0 + tx == xhi, last_y = y0 + ty == yhi;
+  const long long fs = P.fs;
+  const int sy = P.ext[0], sz = P.ext[0] * P.ext[1];
+  const T* U = (const T*)a.cur + P.off;
+  T* V = (T*)a.nxt + P.off;
+  const double gm1 = a.gamma - 1.0;
+  const T gamma = (T)a.gamma;
+  const double dt = *a.dtp * a.dtscale;
+  const T h0 = (T)(0.5 * dt * a.idx[0]), h1 = (T)(0.5 * dt * a.idx[1]), h2 = (T)(0.5 * dt * a.idx[2]);
+  const T dtd[3] = {(T)(dt * a.idx[0]), (T)(dt * a.idx[1]), (T)(dt * a.idx[2])};
+  const int nth = blockDim.x;
+  // W region columns: x in [x0-2, x0+tx+2), y in [y0-2, y0+ty+2); Q region: +-1
+  const int wx = tx + 4, wy = ty + 4, qx = tx + 2, qy = ty + 2;
+  auto widx = [&](int x, int y) { return (x - (x0 - 2)) + PX * (y - (y0 - 2)); };
+  auto qidx = [&](int x, int y) { return (x - (x0 - 1)) + QX * (y - (y0 - 1)); };
+
+  for (int t = zlo - 2; t <= zhi + 1; ++t) {
+    // ---------------- S1: primitives of plane t
+    if (t <= zhi + 1) {
+      const int slot = (t + 3) % 3;
+      for (int c = threadIdx.x; c < wx * wy; c += nth) {
+        const int x = x0 - 2 + c % wx, y = y0 - 2 + c / wx;
+        T wv[8];
+        load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv);
+        const int i = widx(x, y);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) sm.w[slot][f][i] = wv[f];
+      }
+    }
+    __syncthreads();
+    const int p = t - 1;
+    // ---------------- S2: slopes and predictor of plane p
+    if (p >= zlo - 1 && p <= zhi) {
+      const int sm1 = (p - 1 + 3) % 3, s0 = (p + 3) % 3, sp1 = (p + 1 + 3) % 3;
+      const int r2 = (p + 2) % 2;
+      for (int c = threadIdx.x; c < qx * qy; c += nth) {
+        const int x = x0 - 1 + c % qx, y = y0 - 1 + c / qx;
+        const int i = widx(x, y);
+        const int L = x + sy * y + sz * p;
+        T wc[8], s[3][8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wc[f] = sm.w[s0][f][i];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          s[0][f] = f == BX ? U[BX * fs + L + 1] - U[BX * fs + L] : mm(wc[f] - sm.w[s0][f][i - 1], sm.w[s0][f][i + 1] - wc[f]);
+          s[1][f] = f == BY ? U[BY * fs + L + sy] - U[BY * fs + L]
+                            : mm(wc[f] - sm.w[s0][f][i - PX], sm.w[s0][f][i + PX] - wc[f]);
+          s[2][f] = f == BZ ? U[BZ * fs + L + sz] - U[BZ * fs + L] : mm(wc[f] - sm.w[sm1][f][i], sm.w[sp1][f][i] - wc[f]);
+        }
+        const T ir = T(1) / wc[0];
+        T wh[8], dw[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wh[f] = wc[f];
+        prim_terms<T, 0>(wc, s[0], gamma, ir, dw);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h0 * dw[f];
+        prim_terms<T, 1>(wc, s[1], gamma, ir, dw);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h1 * dw[f];
+        prim_terms<T, 2>(wc, s[2], gamma, ir, dw);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h2 * dw[f];
+        const int q = qidx(x, y);
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          sm.wh[r2][f][q] = wh[f];
+          sm.sx[f][q] = s[0][f];
+          sm.sy[f][q] = s[1][f];
+          sm.sz[r2][f][q] = s[2][f];
+        }
+        sm.ref[r2][0][q] = wh[3] * wh[6] - wh[2] * wh[7];
+        sm.ref[r2][1][q] = wh[1] * wh[7] - wh[3] * wh[5];
+        sm.ref[r2][2][q] = wh[2] * wh[5] - wh[1] * wh[6];
+      }
+    }
+    __syncthreads();
+    // ---------------- S3: fluxes (x, y faces of plane p; z faces of face plane p)
+    if (p >= zlo - 1 && p <= zhi) {
+      const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
+      const int nfx = (tx + 1) * (ty + 2), nfy = (tx + 2) * (ty + 1);
+      const int nfz = p >= zlo ? (tx + 2) * (ty + 2) : 0;
+      for (int c = threadIdx.x; c < nfx + nfy + nfz; c += nth) {
+        T wl[8], wr[8], out[8];
+        int q;
+        if (c < nfx) {  // x-face at x (cells x-1, x), y in [y0-1, y0+ty+1)
+          const int x = x0 + c % (tx + 1), y = y0 - 1 + c / (tx + 1);
+          q = qidx(x, y);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            wl[f] = sm.wh[r2][f][q - 1] + T(0.5) * sm.sx[f][q - 1];
+            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sx[f][q];
+          }
+          hlld_face<T>(wl, wr, 0, gamma, out);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) sm.fx[r2][f][q] = out[f];
+        } else if (c < nfx + nfy) {  // y-face at y (cells y-1, y), x in [x0-1, x0+tx+1)
+          const int cc = c - nfx;
+          const int x = x0 - 1 + cc % (tx + 2), y = y0 + cc / (tx + 2);
+          q = qidx(x, y);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            wl[f] = sm.wh[r2][f][q - QX] + T(0.5) * sm.sy[f][q - QX];
+            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sy[f][q];
+          }
+          hlld_face<T>(wl, wr, 1, gamma, out);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) sm.fy[r2][f][q] = out[f];
+        } else {  // z-face at face plane p (cells p-1, p)
+          const int cc = c - nfx - nfy;
+          const int x = x0 - 1 + cc % (tx + 2), y = y0 - 1 + cc / (tx + 2);
+          q = qidx(x, y);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            wl[f] = sm.wh[rm][f][q] + T(0.5) * sm.sz[rm][f][q];
+            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sz[r2][f][q];
+          }
+          hlld_face<T>(wl, wr, 2, gamma, out);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) sm.fz[r2][f][q] = out[f];
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- S4: edge EMFs
+    if (p >= zlo && p <= zhi) {
+      const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
+      const int nez = p < zhi ? (tx + 1) * (ty + 1) : 0;
+      const int nex = tx * (ty + 1), ney = (tx + 1) * ty;
+      for (int c = threadIdx.x; c < nez + nex + ney; c += nth) {
+        if (c < nez) {  // E_z at corner (x-1/2, y-1/2) of plane p: a = x, b = y
+          const int x = x0 + c % (tx + 1), y = y0 + c / (tx + 1);
+          const int q11 = qidx(x, y), q01 = q11 - 1, q10 = q11 - QX, q00 = q11 - 1 - QX;
+          const T ea_hi = -sm.fx[r2][BY][q11], ea_lo = -sm.fx[r2][BY][q10];
+          const T eb_hi = sm.fy[r2][BX][q11], eb_lo = sm.fy[r2][BX][q01];
+          sm.ez[r2][q11] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[r2][2][q00], sm.ref[r2][2][q10],
+                                     sm.ref[r2][2][q01], sm.ref[r2][2][q11], sm.fx[r2][RHO][q10], sm.fx[r2][RHO][q11],
+                                     sm.fy[r2][RHO][q01], sm.fy[r2][RHO][q11]);
+        } else if (c < nez + nex) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
+          const int cc = c - nez;
+          const int x = x0 + cc % tx, y = y0 + cc / tx;
+          const int q = qidx(x, y), qm = q - QX;
+          // a-faces = y-faces at rows z = p-1, p; b-faces = z-faces at columns y-1, y
+          const T ea_lo = -sm.fy[rm][BZ][q], ea_hi = -sm.fy[r2][BZ][q];
+          const T eb_lo = sm.fz[r2][BY][qm], eb_hi = sm.fz[r2][BY][q];
+          sm.ex[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][0][qm], sm.ref[rm][0][q], sm.ref[r2][0][qm],
+                                   sm.ref[r2][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
+                                   sm.fz[r2][RHO][q]);
+        } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
+          const int cc = c - nez - nex;
+          const int x = x0 + cc % (tx + 1), y = y0 + cc / (tx + 1);
+          const int q = qidx(x, y), qm = q - 1;
+          // a-faces = z-faces at rows x-1, x; b-faces = x-faces at columns z = p-1, p
+          const T ea_lo = -sm.fz[r2][BX][qm], ea_hi = -sm.fz[r2][BX][q];
+          const T eb_lo = sm.fx[rm][BZ][q], eb_hi = sm.fx[r2][BZ][q];
+          // references: r00 = (z p-1, x-1), r10 = (z p, x-1), r01 = (z p-1, x), r11 = (z p, x)
+          sm.ey[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][1][qm], sm.ref[r2][1][qm], sm.ref[rm][1][q],
+                                   sm.ref[r2][1][q], sm.fz[r2][RHO][qm], sm.fz[r2][RHO][q], sm.fx[rm][RHO][q],
+                                   sm.fx[r2][RHO][q]);
+        }
+      }
+    }
+    __syncthreads();
+    // ---------------- S5: update cell plane q = p-1
+    const int qz = p - 1;
+    if (qz >= zlo && qz < zhi) {
+      const int rq = (qz + 2) % 2, rp = (p + 2) % 2;
+      const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
+      for (int c = threadIdx.x; c < nx * ny; c += nth) {
+        const int x = x0 + c % nx, y = y0 + c / nx;
+        const bool in_x = x < x0 + tx, in_y = y < y0 + ty;
+        const int L = x + sy * y + sz * qz;
+        const int q = qidx(x, y);
+        if (in_x && in_y) {
+#pragma unroll
+          for (int n = 0; n < 5; ++n) {
+            T v = U[n * fs + L];
+            v = v - dtd[0] * (sm.fx[rq][n][q + 1] - sm.fx[rq][n][q]);
+            v = v - dtd[1] * (sm.fy[rq][n][q + QX] - sm.fy[rq][n][q]);
+            v = v - dtd[2] * (sm.fz[rp][n][q] - sm.fz[rq][n][q]);
+            V[n * fs + L] = v;
+          }
+          // B_z of face plane qz (and the top face plane on the last plane)
+          {
+            T v = U[BZ * fs + L];
+            v = v - dtd[0] * (sm.ey[rq][q + 1] - sm.ey[rq][q]);
+            v = v + dtd[1] * (sm.ex[rq][q + QX] - sm.ex[rq][q]);
+            V[BZ * fs + L] = v;
+          }
+          if (qz == zhi - 1) {
+            T v = U[BZ * fs + L + sz];
+            v = v - dtd[0] * (sm.ey[rp][q + 1] - sm.ey[rp][q]);
+            v = v + dtd[1] * (sm.ex[rp][q + QX] - sm.ex[rp][q]);
+            V[BZ * fs + L + sz] = v;
+          }
+        }
+        if (in_y) {  // B_x at (x, y, qz)
+          T v = U[BX * fs + L];
+          v = v - dtd[1] * (sm.ez[rq][q + QX] - sm.ez[rq][q]);
+          v = v + dtd[2] * (sm.ey[rp][q] - sm.ey[rq][q]);
+          V[BX * fs + L] = v;
+        }
+        if (in_x) {  // B_y at (x, y, qz)
+          T v = U[BY * fs + L];
+          v = v - dtd[2] * (sm.ex[rp][q] - sm.ex[rq][q]);
+          v = v + dtd[0] * (sm.ez[rq][q + 1] - sm.ez[rq][q]);
+          V[BY * fs + L] = v;
+        }
+      }
+    }
+    // no barrier: the next S1 writes only the W ring slot that S2 no longer reads
+  }
+}
+
+// ------------------------------------------------------------------ register recompute
+// Registers for the fused path, recomputed from the state the advance read:
+// the same formulas as the fused kernel, evaluated at the listed faces/edges.
+template <class T>
+__device__ void predict_at(const T* U, const DPatch& P, int L, double dt, const double* idx, double gamma, T* wh,
+                           T* sd /* 3 x 8 */) {
+  const long long fs = P.fs;
+  const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
+  const double gm1 = gamma - 1.0;
+  T wc[8], wm[8], wp[8];
+  load_recover(U, fs, L, st[1], st[2], gm1, wc);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    load_recover(U, fs, L - st[d], st[1], st[2], gm1, wm);
+    load_recover(U, fs, L + st[d], st[1], st[2], gm1, wp);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      if (f == BX + d) sd[8 * d + f] = U[(BX + d) * fs + L + st[d]] - U[(BX + d) * fs + L];
+      else sd[8 * d + f] = mm(wc[f] - wm[f], wp[f] - wc[f]);
+    }
+  }
+  const T ir = T(1) / wc[0];
+  const T g = (T)gamma;
+  T dw[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) wh[f] = wc[f];
+  const T h0 = (T)(0.5 * dt * idx[0]), h1 = (T)(0.5 * dt * idx[1]), h2 = (T)(0.5 * dt * idx[2]);
+  prim_terms<T, 0>(wc, sd, g, ir, dw);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h0 * dw[f];
+  prim_terms<T, 1>(wc, sd + 8, g, ir, dw);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h1 * dw[f];
+  prim_terms<T, 2>(wc, sd + 16, g, ir, dw);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h2 * dw[f];
+}
+
+// flux through the d-face stored at L (cells L - st[d] and L), global field order
+template <class T>
+__device__ void face_flux_at(const T* U, const DPatch& P, int d, int L, double dt, const double* idx, double gamma,
+                             T* out8) {
+  const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
+  T whl[8], whr[8], sl[24], sr[24], wl[8], wr[8];
+  predict_at(U, P, L - st[d], dt, idx, gamma, whl, sl);
+  predict_at(U, P, L, dt, idx, gamma, whr, sr);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    wl[f] = whl[f] + T(0.5) * sl[8 * d + f];
+    wr[f] = whr[f] - T(0.5) * sr[8 * d + f];
+  }
+  hlld_face<T>(wl, wr, d, (T)gamma, out8);
+}
+
+// E_c at the c-edge stored at L (the low a,b corner of cell L), (a,b,c) cyclic
+template <class T>
+__device__ T edge_emf_at(const T* U, const DPatch& P, int c, int L, double dt, const double* idx, double gamma) {
+  const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
+  const int a = (c + 1) % 3, b = (c + 2) % 3;
+  const int Lc[4] = {L - st[a] - st[b], L - st[b], L - st[a], L};  // (a-1,b-1), (a,b-1), (a-1,b), (a,b)
+  T wh[4][8], sd[4][24];
+  for (int k = 0; k < 4; ++k) predict_at(U, P, Lc[k], dt, idx, gamma, wh[k], sd[k]);
+  T wl[8], wr[8], fa_lo[8], fa_hi[8], fb_lo[8], fb_hi[8];
+  const T g = (T)gamma;
+  // a-faces at rows b-1 (cells 0 -> 1) and b (cells 2 -> 3)
+#pragma unroll
+  for (int f = 0; f < 8; ++f) { wl[f] = wh[0][f] + T(0.5) * sd[0][8 * a + f]; wr[f] = wh[1][f] - T(0.5) * sd[1][8 * a + f]; }
+  hlld_face<T>(wl, wr, a, g, fa_lo);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) { wl[f] = wh[2][f] + T(0.5) * sd[2][8 * a + f]; wr[f] = wh[3][f] - T(0.5) * sd[3][8 * a + f]; }
+  hlld_face<T>(wl, wr, a, g, fa_hi);
+  // b-faces at columns a-1 (cells 0 -> 2) and a (cells 1 -> 3)
+#pragma unroll
+  for (int f = 0; f < 8; ++f) { wl[f] = wh[0][f] + T(0.5) * sd[0][8 * b + f]; wr[f] = wh[2][f] - T(0.5) * sd[2][8 * b + f]; }
+  hlld_face<T>(wl, wr, b, g, fb_lo);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) { wl[f] = wh[1][f] + T(0.5) * sd[1][8 * b + f]; wr[f] = wh[3][f] - T(0.5) * sd[3][8 * b + f]; }
+  hlld_face<T>(wl, wr, b, g, fb_hi);
+  T r[4];
+  for (int k = 0; k < 4; ++k) {
+    const T* h = wh[k];
+    r[k] = c == 0 ? h[3] * h[6] - h[2] * h[7] : (c == 1 ? h[1] * h[7] - h[3] * h[5] : h[2] * h[5] - h[1] * h[6]);
+  }
+  return gs_emf<T>(-fa_lo[BX + b], -fa_hi[BX + b], fb_lo[BX + a], fb_hi[BX + a], r[0], r[1], r[2], r[3], fa_lo[RHO],
+                   fa_hi[RHO], fb_lo[RHO], fb_hi[RHO]);
+}
+
+// RowArgs.fbuf = the state the level's advance read (for the coarse side the
+// coarse level, for the fine side the fine level); dt = *dtp * dtscale.
+template <class T> __global__ void k_regrc_coarse_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 7 * r;
+  const DPatch P = a.P[row[1]];
+  const double dt = *a.dtp * a.dtscale;
+  const double idx[3] = {ix, iy, iz};
+  T f8[8];
+  face_flux_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma, f8);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) a.creg[r * 6 + n] = dt * (double)f8[n];
+}
+
+template <class T> __global__ void k_regrc_coarse_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch P = a.P[row[1]];
+  const double dt = *a.dtp * a.dtscale;
+  const double idx[3] = {ix, iy, iz};
+  a.ecreg[r] = dt * (double)edge_emf_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma);
+}
+
+template <class T> __global__ void k_regrc_fine_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 7 * r;
+  const DPatch P = a.P[row[5]];
+  const int d = row[2], L = row[6];
+  const double dt = *a.dtp * a.dtscale;
+  const double idx[3] = {ix, iy, iz};
+  const double af = dt * 0.25;
+  const int sx = 1, sy = P.ext[0], sz = P.ext[0] * P.ext[1];
+  int o1, o2;
+  if (d == 0) { o1 = sy; o2 = sz; }
+  else if (d == 1) { o1 = sx; o2 = sz; }
+  else { o1 = sx; o2 = sy; }
+  const int off[4] = {0, o1, o2, o1 + o2};
+  T f[4][8];
+  const T* U = (const T*)a.fbuf + P.off;
+  for (int k = 0; k < 4; ++k) face_flux_at<T>(U, P, d, L + off[k], dt, idx, gamma, f[k]);
+  double* out = a.freg + (r * 2 + (a.substep - 1)) * 6;
+#pragma unroll
+  for (int n = 0; n < 5; ++n)
+    out[n] = af * tree4((double)f[0][n], (double)f[1][n], (double)f[2][n], (double)f[3][n]);
+}
+
+template <class T> __global__ void k_regrc_fine_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch P = a.P[row[4]];
+  const int c = row[2], L = row[5];
+  const double dt = *a.dtp * a.dtscale;
+  const double idx[3] = {ix, iy, iz};
+  const int sc = c == 0 ? 1 : (c == 1 ? P.ext[0] : P.ext[0] * P.ext[1]);
+  const T* U = (const T*)a.fbuf + P.off;
+  const T e0 = edge_emf_at<T>(U, P, c, L, dt, idx, gamma);
+  const T e1 = edge_emf_at<T>(U, P, c, L + sc, dt, idx, gamma);
+  a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)e0, (double)e1);
+}

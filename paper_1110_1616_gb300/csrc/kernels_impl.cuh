@@ -537,6 +537,9 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// per-cell rate sum_d (|v_d| + c_f,d)/dx_d; FP64 path: all FP64 (bitwise with a
+// plain FP64 evaluation); mixed path: the FP64-balanced recovery of
+// recover_t and FP32 fast speeds, the maximum carried in FP64
 template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs a) {
   const DPatch P = a.P[a.ids[blockIdx.y]];
   int i, j, k;
@@ -546,25 +549,26 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
     const int L = lidx(P, i, j, k);
     const long long fs = P.fs;
     const T* U = (const T*)a.cur + P.off;
-    double u[5], bc[3], w[8];
+    T u[5], bl[3], br[3], w[8];
 #pragma unroll
-    for (int f = 0; f < 5; ++f) u[f] = (double)U[f * fs + L];
-    bc[0] = 0.5 * ((double)U[5 * fs + L] + (double)U[5 * fs + L + 1]);
-    bc[1] = 0.5 * ((double)U[6 * fs + L] + (double)U[6 * fs + L + P.ext[0]]);
-    if (DIM == 3) bc[2] = 0.5 * ((double)U[7 * fs + L] + (double)U[7 * fs + L + P.ext[0] * P.ext[1]]);
-    else bc[2] = (double)U[7 * fs + L];
-    recover(u, bc, a.gamma - 1.0, w);
-    if (!(w[0] > 0.0) || !(w[4] > 0.0)) bad = true;
+    for (int f = 0; f < 5; ++f) u[f] = U[f * fs + L];
+    bl[0] = U[5 * fs + L]; br[0] = U[5 * fs + L + 1];
+    bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + P.ext[0]];
+    if (DIM == 3) { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + P.ext[0] * P.ext[1]]; }
+    else { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L]; }
+    recover_t(u, bl, br, a.gamma - 1.0, w);
+    if (!(w[0] > T(0)) || !(w[4] > T(0))) bad = true;
     else {
-      double rr = 0.0;
+      T rr = T(0);
+      const T g = (T)a.gamma;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int t = (d + 1) % 3, uu = (d + 2) % 3;
-        const double cf = cfast<double>(w[0], w[4], w[5 + d], w[5 + t], w[5 + uu], a.gamma);
-        rr = rr + (fabs(w[1 + d]) + cf) * a.idx[d];
+        const T cf = cfast<T>(w[0], w[4], w[5 + d], w[5 + t], w[5 + uu], g);
+        rr = rr + (dabs(w[1 + d]) + cf) * (T)a.idx[d];
       }
-      if (!(rr == rr) || rr > 1.79e308) bad = true;
-      else rate = rr;
+      if (!(rr == rr) || (double)rr > 1.79e308) bad = true;
+      else rate = (double)rr;
     }
   }
   if (bad) atomicOr(a.err, 1u);
@@ -598,6 +602,8 @@ __global__ void __launch_bounds__(TPB) k_io(const DPatch* PP, const int* ids, vo
   if (to_state) *s = (T)*q;
   else *q = (double)*s;
 }
+
+#include "kernels_fused.cuh"
 
 // ------------------------------------------------------------------ launchers
 template <class T, int DIM> struct Impl {
@@ -656,10 +662,53 @@ template <class T, int DIM> struct Impl {
     k_io<T, DIM><<<dim3(cdiv(n, TPB), npatch), TPB, 0, s>>>(P, ids, state, packed, poff, field, to_state);
     if (nl) ++*nl;
   }
+  // fused 3D advance (2D falls back to the staged kernels)
+  template <int V> static size_t fused_smem() {
+    return sizeof(FusedSmem<T, FusedCfg<V>::TX, FusedCfg<V>::TY>);
+  }
+  template <int V> static bool fused_fits() { return fused_smem<V>() <= 227 * 1024; }
+  template <int V> static void prepare_v() {
+    if (fused_fits<V>())
+      cudaFuncSetAttribute(k_advance3d_fused<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<V>());
+  }
+  static void prepare() {
+    if (DIM == 3) { prepare_v<0>(); prepare_v<1>(); prepare_v<2>(); prepare_v<3>(); }
+  }
+  template <int V> static void launch_fused(const LevelArgs& a, cudaStream_t s) {
+    constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
+    const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
+    const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
+    k_advance3d_fused<T, V><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+  }
+  static void advance_fused(const LevelArgs& a, int variant, cudaStream_t s, int* nl) {
+    if (DIM != 3) {
+      advance(a, s, nl);
+      return;
+    }
+    // variants whose shared memory does not fit fall back to the 8x8 tile
+    if (variant == 0 && fused_fits<0>()) launch_fused<0>(a, s);
+    else if (variant == 1 && fused_fits<1>()) launch_fused<1>(a, s);
+    else if (variant == 2 && fused_fits<2>()) launch_fused<2>(a, s);
+    else launch_fused<3>(a, s);
+    if (nl) ++*nl;
+  }
+  // registers recomputed from the state read by the advance (fused path, 3D)
+  static void reg_coarse_rc(const RowArgs& f, const RowArgs& e, const double* idx, double gamma, cudaStream_t s,
+                            int* nl) {
+    if (DIM != 3) return;
+    if (f.nrows) { k_regrc_coarse_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+    if (e.nrows) { k_regrc_coarse_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+  }
+  static void reg_fine_rc(const RowArgs& f, const RowArgs& e, const double* idx, double gamma, cudaStream_t s,
+                          int* nl) {
+    if (DIM != 3) return;
+    if (f.nrows) { k_regrc_fine_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+    if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+  }
   static const Ops* ops() {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, prolong_cells,
                           prolong_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
-                          sizeof(T)};
+                          sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc};
     return &o;
   }
 };

@@ -67,6 +67,84 @@ __device__ __forceinline__ void recover(const double* u, const double* bc, doubl
   w[5] = bc[0]; w[6] = bc[1]; w[7] = bc[2];
 }
 
+// Error-free FP32 transformations (Knuth two-sum, FMA two-product): a pair
+// (hi, lo) represents hi + lo exactly or to ~2^-46 relative.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+// (ah, al) + (bh, bl)
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+// (ah, al)^2
+__device__ __forceinline__ void df_sq(float ah, float al, float& h, float& l) {
+  float p, e;
+  two_prod(ah, ah, p, e);
+  e = fmaf(2.0f * ah, al, e);
+  h = p + e;
+  l = e - (h - p);
+}
+
+// Recovery of one cell from stored values in the working type T. For T =
+// double this is recover() exactly. For the mixed path (T = float) the energy
+// balance p = (g-1)(E - ke - me) is evaluated in FP64, with
+// ke = |m|^2 / (2 rho) and me = |B_c|^2 / 2 formed from the FP32 inputs by
+// error-free FP32 transformations (squares, sums, face means and the division
+// by rho carried as hi + lo pairs, ~2^-46 relative), so that the FP64 pipe
+// only does the final subtraction; v = m / rho and B_c are FP32.
+__device__ __forceinline__ void recover_t(const double* u, const double* bl, const double* br, double gm1, double* w) {
+  double bc[3] = {0.5 * (bl[0] + br[0]), 0.5 * (bl[1] + br[1]), 0.5 * (bl[2] + br[2])};
+  recover(u, bc, gm1, w);
+}
+__device__ __forceinline__ void recover_t(const float* u, const float* bl, const float* br, double gm1, float* w) {
+  const float r = u[0];
+  const float irf = 1.0f / r;
+  // |m|^2 as a pair
+  float mh, ml, th, tl;
+  two_prod(u[1], u[1], mh, ml);
+  two_prod(u[2], u[2], th, tl);
+  df_add(mh, ml, th, tl, mh, ml);
+  two_prod(u[3], u[3], th, tl);
+  df_add(mh, ml, th, tl, mh, ml);
+  // ke = 0.5 |m|^2 / rho as a pair: q = mh/r, remainder (mh - q r + ml)/r
+  const float q = mh * irf;
+  const float q1 = (fmaf(-q, r, mh) + ml) * irf;
+  const float q2 = (fmaf(-q1, r, fmaf(-q, r, mh) + ml)) * irf;
+  float kh, kl;
+  two_sum(q, q1 + q2, kh, kl);
+  // |bl + br|^2 summed over components as a pair (me = that / 8)
+  float bh = 0.0f, blo = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float sh, se, qh, ql;
+    two_sum(bl[c], br[c], sh, se);
+    df_sq(sh, se, qh, ql);
+    df_add(bh, blo, qh, ql, bh, blo);
+  }
+  // (ke + me) = 0.5 (kh, kl) + 0.125 (bh, blo): exact power-of-two scalings
+  float eh, el;
+  df_add(0.5f * kh, 0.5f * kl, 0.125f * bh, 0.125f * blo, eh, el);
+  const double p = gm1 * ((double)u[4] - ((double)eh + (double)el));
+  w[0] = r;
+  w[1] = u[1] * irf;
+  w[2] = u[2] * irf;
+  w[3] = u[3] * irf;
+  w[4] = (float)p;
+  w[5] = 0.5f * (bl[0] + br[0]);
+  w[6] = 0.5f * (bl[1] + br[1]);
+  w[7] = 0.5f * (bl[2] + br[2]);
+}
+
 // A_d(W) s for the primitive predictor, direction d (n = d, t = d+1, u = d+2 mod 3)
 template <class T, int D> __device__ __forceinline__ void prim_terms(const T* w, const T* s, T gamma, T ir, T* dw) {
   constexpr int n = D, t = (D + 1) % 3, u = (D + 2) % 3;
