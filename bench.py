@@ -26,6 +26,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MHD cell-updates/s on 1 GB300 (FP32 vs FP64) and achieved HBM GB/s vs peak"
 UNIT = "cell-updates/s"
+# Algorithmic FP operations of one 3D cell update (recovery, slopes, predictor,
+# face states, 3 HLLD solves, reference and 3 GS edge EMFs, updates), counted
+# by running the oracle's per-cell formulas with a counting scalar type
+# (oracle/opcount.cpp, 2000 subsonic samples, seed 1; tests/test_oracle_opcount.py).
+FLOPS_PER_CELL_UPDATE_3D = 1504.0
+# FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock
+SMS, FP32_LANES = 152, 128
 
 
 def parse():
@@ -286,6 +293,9 @@ def main():
     alg_bytes = 16 * 4 * cells_step
     achieved = alg_bytes / (t_adv / 1e3) / 1e9
     arena_gb = ctx.query(A.Q_ARENA_BYTES) / 1e9
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    flops_achieved = FLOPS_PER_CELL_UPDATE_3D * cells_step / (t_adv / 1e3) / 1e12
     del ctx
     torch.cuda.empty_cache()
 
@@ -330,10 +340,15 @@ def main():
                    "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "precision": "mixed",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (arena %.2f GB: ping-pong state and stage scratch)" % arena_gb},
-        "roofline": {"bound": "hbm", "kernel": "k_advance3d_fused<float> (one launch per level advance)",
-                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
-                     "traffic": None, "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_adv},
+        "roofline": {"bound": "alu", "kernel": "k_advance3d_fused<float,16x8> (one launch per level advance)",
+                     "achieved": flops_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": flops_achieved / fp32_peak,
+                     "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (SMS, FP32_LANES, sm_max),
+                     "traffic": None, "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
+                     "ms_per_launch": t_adv},
+        "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
+                "alg_bytes_per_launch": alg_bytes},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

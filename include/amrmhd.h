@@ -53,7 +53,12 @@ typedef enum {
 } amrmhd_status;
 
 enum { AMRMHD_FP64 = 0, AMRMHD_MIXED = 1 };
-enum { AMRMHD_BC_PERIODIC = 0 };
+/* Boundary kinds per side of a dimension. A dimension is periodic with
+ * AMRMHD_BC_PERIODIC on both sides. Otherwise each side is a zero-gradient
+ * outflow (ghost cells copy the nearest domain cell; a ghost face normal to the
+ * boundary copies the boundary face) or a fixed inflow (ghost cells and faces
+ * take cfg.inflow). */
+enum { AMRMHD_BC_PERIODIC = 0, AMRMHD_BC_OUTFLOW = 1, AMRMHD_BC_INFLOW = 2 };
 
 typedef struct {
   int32_t dim;         /* 2 or 3 */
@@ -64,11 +69,12 @@ typedef struct {
   int32_t max_level;   /* highest level index allowed (levels 0..max_level) */
   int32_t precision;   /* AMRMHD_FP64: all FP64; AMRMHD_MIXED: FP32 stencil, FP64
                           primitive recovery, registers, dt and CFL */
-  int32_t bc[3][2];    /* AMRMHD_BC_PERIODIC on every side (only periodic is built) */
+  int32_t bc[3][2];    /* AMRMHD_BC_* per dimension and side (low, high) */
   double gamma;        /* ratio of specific heats */
   double cfl;          /* Courant number of the sum-form rate (e.g. 0.4) */
   int32_t strict_fp64; /* 1: FP64 kernels compiled without FMA contraction (bitwise
                           reproducible parity build); 0: contraction allowed */
+  double inflow[8];    /* conserved inflow state (rho, mx, my, mz, E, Bx, By, Bz) */
 } amrmhd_config;
 
 /* A patch: level and half-open box [lo, hi) in level-l cell indices, inside
@@ -128,7 +134,8 @@ amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* ds
  *                 shifted interior meets p's ghosted box; sorted.
  *  GHOST_CELLS    (p, Ldst, kind, src, Lsrc) for every ghost cell of p in z,y,x
  *                 order; kind 0 = same-level copy, 1 = prolongation from the parent
- *                 cell Lsrc of coarse patch src.
+ *                 cell Lsrc of coarse patch src, 2 = boundary copy from p's own
+ *                 Lsrc (the nearest domain position), 3 = inflow (src = Lsrc = -1).
  *  GHOST_FACES    (p, d, Ldst, kind, src, Lsrc), faces not owned by p; the
  *                 same-level source is the owner with the smallest (id, index).
  *  CF_FACES       (l, qc, d, Lface, side, pf, Lfine): coarse faces between a
@@ -195,10 +202,11 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
 
 /* Options (set before set_hierarchy): AMRMHD_OPT_* */
 enum {
-  AMRMHD_OPT_ADVANCE = 0,  /* 0 (default): in 3D one fused kernel per level advance (no
-                              scratch), in 2D the staged kernels batched over the level;
-                              1: the staged kernels launched one patch at a time (baseline);
-                              2: the staged kernels batched over the level */
+  AMRMHD_OPT_ADVANCE = 0,  /* 0 (default): mixed precision in 3D uses one fused kernel per
+                              level advance (no scratch); FP64 and 2D use the staged kernels
+                              batched over the level; 1: the staged kernels launched one
+                              patch at a time (baseline); 2: the staged kernels batched;
+                              3: the fused kernel (3D) in either precision */
   AMRMHD_OPT_GRAPH = 1,    /* 1 (default): amrmhd_step replays a CUDA graph; 0: plain launches */
   AMRMHD_OPT_TILE = 2      /* fused 3D advance tile: -1 default (16x8 FP32, 8x8 FP64), 0: 16x16 tile
                               with 256 threads, 1: 16x16 / 512, 2: 16x8 / 256, 3: 8x8 / 256 */

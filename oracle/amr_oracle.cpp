@@ -26,7 +26,10 @@
 // ghosted boxes behaves exactly like the band of width 4 around the region.
 // This keeps the oracle free of any patch bookkeeping.
 //
-// Only periodic boundaries are implemented.
+// Boundaries: periodic, or (per dimension) a fixed inflow state on one side
+// and zero-gradient outflow on the other (reading R17). A non-periodic
+// dimension carries a margin of 4 cells outside the domain, filled by the
+// boundary conditions before every sub-step.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -41,8 +44,13 @@ static const int G = 4;  // ghost width
 
 struct Patch { int level, lo[3], hi[3]; };
 
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
+
 struct Level {
   int N[3] = {1, 1, 1};  // cells per dimension
+  int M[3] = {0, 0, 0};  // margin (4 in a non-periodic dimension)
+  int X[3] = {1, 1, 1};  // storage extent: N (periodic) or N + 2M + 1
+  bool per[3] = {true, true, true};
   double dx[3] = {1, 1, 1}, idx[3] = {1, 1, 1};
   size_t ncell = 0;
   std::vector<double> u[NFIELD];      // cell fields and face fields, index (k*Ny + j)*Nx + i
@@ -69,24 +77,66 @@ struct Sim {
   std::vector<Patch> patches;
   std::vector<Level> lev;
   long long cell_updates = 0;
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  double inflow[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
   int flags = 0;  // test-only switches: bit 0 skips the cell reflux (a planted
-                  // mistake); bit 1 replaces minmod by the unlimited centred slope
+                  // mistake); bit 1 replaces minmod by the unlimited centred slope;
+                  // bit 2 plants an off-by-one in the high-side boundary faces
 };
 
 // ---------------------------------------------------------------- indexing
 static inline int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+static inline int mapi(const Level& L, int d, int i) { return L.per[d] ? wrapi(i, L.N[d]) : i + L.M[d]; }
 static inline size_t at(const Level& L, int i, int j, int k) {
-  return ((size_t)wrapi(k, L.N[2]) * L.N[1] + wrapi(j, L.N[1])) * L.N[0] + wrapi(i, L.N[0]);
+  return ((size_t)mapi(L, 2, k) * L.X[1] + mapi(L, 1, j)) * L.X[0] + mapi(L, 0, i);
+}
+// cell (i,j,k) stored (margin included)?
+static inline bool in_storage(const Level& L, int i, int j, int k) {
+  const int o[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d)
+    if (!L.per[d] && (o[d] < -L.M[d] || o[d] >= L.N[d] + L.M[d])) return false;
+  return true;
+}
+static inline bool in_domain(const Level& L, int i, int j, int k) {
+  const int o[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d)
+    if (!L.per[d] && (o[d] < 0 || o[d] >= L.N[d])) return false;
+  return true;
 }
 static inline size_t atd(const Level& L, int i, int j, int k, int d, int s) {
   int o[3] = {i, j, k};
   o[d] += s;
   return at(L, o[0], o[1], o[2]);
 }
+// cells of the domain
 template <class F> static void for_cells(const Level& L, F f) {
   for (int k = 0; k < L.N[2]; ++k)
     for (int j = 0; j < L.N[1]; ++j)
       for (int i = 0; i < L.N[0]; ++i) f(i, j, k);
+}
+// cells of the domain and of the margins
+template <class F> static void for_all(const Level& L, F f) {
+  for (int k = -L.M[2]; k < L.N[2] + L.M[2]; ++k)
+    for (int j = -L.M[1]; j < L.N[1] + L.M[1]; ++j)
+      for (int i = -L.M[0]; i < L.N[0] + L.M[0]; ++i) f(i, j, k);
+}
+// positions of the d-faces of the domain (the face at the high end of a
+// non-periodic dimension included; periodic faces wrap)
+template <class F> static void for_face_pos(const Level& L, int d, F f) {
+  int hi[3] = {L.N[0], L.N[1], L.N[2]};
+  if (!L.per[d]) hi[d] += 1;
+  for (int k = 0; k < hi[2]; ++k)
+    for (int j = 0; j < hi[1]; ++j)
+      for (int i = 0; i < hi[0]; ++i) f(i, j, k);
+}
+// positions of the c-edges of the domain
+template <class F> static void for_edge_pos(const Level& L, int c, F f) {
+  int hi[3] = {L.N[0], L.N[1], L.N[2]};
+  for (int e = 0; e < 3; ++e)
+    if (e != c && !L.per[e]) hi[e] += 1;
+  for (int k = 0; k < hi[2]; ++k)
+    for (int j = 0; j < hi[1]; ++j)
+      for (int i = 0; i < hi[0]; ++i) f(i, j, k);
 }
 
 // Cell-field list: in 3D rho, m, E; in 2D also Bz, which is cell-centred and
@@ -104,13 +154,16 @@ static void dilate(const Sim& S, const Level& L, std::vector<int8_t>& d) {
   const int kz = S.dim == 3 ? 1 : 0;
   for (int r = 1; r <= G; ++r) {
     std::vector<int8_t> nd = d;
-    for_cells(L, [&](int i, int j, int k) {
+    for_all(L, [&](int i, int j, int k) {
       size_t q = at(L, i, j, k);
       if (d[q] >= 0) return;
       for (int c = -kz; c <= kz; ++c)
         for (int b = -1; b <= 1; ++b)
           for (int a = -1; a <= 1; ++a)
-            if (d[at(L, i + a, j + b, k + c)] == r - 1) { nd[q] = (int8_t)r; return; }
+            if (in_storage(L, i + a, j + b, k + c) && d[at(L, i + a, j + b, k + c)] == r - 1) {
+              nd[q] = (int8_t)r;
+              return;
+            }
     });
     d.swap(nd);
   }
@@ -127,8 +180,11 @@ static int validate_and_build(Sim& S) {
       L.N[d] = d < S.dim ? (S.base[d] << l) : 1;
       L.dx[d] = d < S.dim ? (S.hi[d] - S.lo[d]) / L.N[d] : 1.0;
       L.idx[d] = 1.0 / L.dx[d];
+      L.per[d] = d >= S.dim || S.bc[d][0] == BC_PERIODIC;
+      L.M[d] = L.per[d] ? 0 : G;
+      L.X[d] = L.per[d] ? L.N[d] : L.N[d] + 2 * G + 1;
     }
-    L.ncell = (size_t)L.N[0] * L.N[1] * L.N[2];
+    L.ncell = (size_t)L.X[0] * L.X[1] * L.X[2];
     for (int f = 0; f < NFIELD; ++f) { L.u[f].assign(L.ncell, 0.0); L.start[f].assign(L.ncell, 0.0); }
     L.dist.assign(L.ncell, -1);
     L.cov.assign(L.ncell, 0);
@@ -150,8 +206,13 @@ static int validate_and_build(Sim& S) {
           L.dist[q] = 0;
         }
   }
-  for (size_t q = 0; q < S.lev[0].ncell; ++q)
-    if (S.lev[0].dist[q] != 0) return -1;  // level 0 must tile the domain
+  {
+    bool tiled = true;
+    for_cells(S.lev[0], [&](int i, int j, int k) {
+      if (S.lev[0].dist[at(S.lev[0], i, j, k)] != 0) tiled = false;
+    });
+    if (!tiled) return -1;  // level 0 must tile the domain
+  }
   for (int l = 1; l < S.nlev; ++l) {
     Level& F = S.lev[l];
     Level& C = S.lev[l - 1];
@@ -167,7 +228,7 @@ static int validate_and_build(Sim& S) {
       for (int c = -kz; c <= kz; ++c)
         for (int b = -3; b <= 3; ++b)
           for (int a = -3; a <= 3; ++a)
-            if (C.dist[at(C, i + a, j + b, k + c)] != 0) ok = false;
+            if (in_domain(C, i + a, j + b, k + c) && C.dist[at(C, i + a, j + b, k + c)] != 0) ok = false;
     });
     if (!ok) return -2;
   }
@@ -183,25 +244,32 @@ static int validate_and_build(Sim& S) {
       F.remf[d].assign(C.ncell, 0.0);
       F.remfc[d].assign(C.ncell, 0.0);
     }
-    for_cells(C, [&](int i, int j, int k) {
-      size_t q = at(C, i, j, k);
-      for (int d = 0; d < S.dim; ++d)
-        if (C.cov[atd(C, i, j, k, d, -1)] != C.cov[q]) F.cf_face[d][q] = 1;
-      // edges along c with the (a,b) plane: 4 surrounding cells
-      for (int c = 0; c < 3; ++c) {
-        if (S.dim == 2 && c != 2) continue;
-        int a = (c + 1) % 3, b = (c + 2) % 3;
-        int o[3] = {i, j, k};
+    // a C/F face lies between a covered and an uncovered cell of the domain; a
+    // C/F edge has 1..3 covered cells around it (cells outside the domain count
+    // as uncovered)
+    for (int d = 0; d < S.dim; ++d)
+      for_face_pos(C, d, [&](int i, int j, int k) {
+        int m[3] = {i, j, k};
+        m[d] -= 1;
+        if (!in_domain(C, i, j, k) || !in_domain(C, m[0], m[1], m[2])) return;
+        size_t q = at(C, i, j, k);
+        if (C.cov[at(C, m[0], m[1], m[2])] != C.cov[q]) F.cf_face[d][q] = 1;
+      });
+    for (int c = 0; c < 3; ++c) {
+      if (S.dim == 2 && c != 2) continue;
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      for_edge_pos(C, c, [&](int i, int j, int k) {
         int n = 0;
         for (int sb = -1; sb <= 0; ++sb)
           for (int sa = -1; sa <= 0; ++sa) {
-            int p[3] = {o[0], o[1], o[2]};
-            p[a] += sa; p[b] += sb;
-            n += C.cov[at(C, p[0], p[1], p[2])];
+            int p[3] = {i, j, k};
+            p[a] += sa;
+            p[b] += sb;
+            if (in_domain(C, p[0], p[1], p[2])) n += C.cov[at(C, p[0], p[1], p[2])];
           }
-        if (n >= 1 && n <= 3) F.cf_edge[c][q] = 1;
-      }
-    });
+        if (n >= 1 && n <= 3) F.cf_edge[c][at(C, i, j, k)] = 1;
+      });
+    }
   }
   return 0;
 }
@@ -241,9 +309,11 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   const int dim = S.dim;
   const std::vector<int8_t>& tm = L.tmask;
   auto in = [&](size_t q, int r) { return tm[q] >= 0 && tm[q] <= r; };
+  // the same test for a cell given by coordinates (false outside the storage)
+  auto inc = [&](int i, int j, int k, int r) { return in_storage(L, i, j, k) && in(at(L, i, j, k), r); };
   const double gamma = S.gamma;
   // primitives
-  for_cells(L, [&](int i, int j, int k) {
+  for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
     if (!in(q, 2)) return;
     double w[8];
@@ -253,7 +323,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   // slopes and half-step predictor (R1, R2)
   double h[3];
   for (int d = 0; d < 3; ++d) h[d] = 0.5 * dt * L.idx[d];
-  for_cells(L, [&](int i, int j, int k) {
+  for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
     if (!in(q, 1)) return;
     double w[8], s[3][8];
@@ -284,9 +354,11 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   // HLLD fluxes at d-faces (R3, R4); face stored at the cell on its high side
   for (int d = 0; d < dim; ++d) {
     const int t = (d + 1) % 3, u = (d + 2) % 3;
-    for_cells(L, [&](int i, int j, int k) {
-      size_t qr = at(L, i, j, k), ql = atd(L, i, j, k, d, -1);
-      if (!in(qr, 1) || !in(ql, 1)) return;
+    for_all(L, [&](int i, int j, int k) {
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      if (!inc(i, j, k, 1) || !inc(m[0], m[1], m[2], 1)) return;
+      size_t qr = at(L, i, j, k), ql = at(L, m[0], m[1], m[2]);
       double wl[8], wr[8];
       for (int f = 0; f < 8; ++f) {
         wl[f] = L.Wh[f][ql] + 0.5 * L.S[d][f][ql];
@@ -311,14 +383,18 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   for (int c = 0; c < 3; ++c) {
     if (dim == 2 && c != 2) continue;
     const int a = (c + 1) % 3, b = (c + 2) % 3;
-    for_cells(L, [&](int i, int j, int k) {
-      size_t q11 = at(L, i, j, k);
-      size_t q01 = atd(L, i, j, k, a, -1);
-      size_t q10 = atd(L, i, j, k, b, -1);
-      int o[3] = {i, j, k};
+    for_all(L, [&](int i, int j, int k) {
+      int o[3] = {i, j, k}, oa[3] = {i, j, k}, ob[3] = {i, j, k};
       o[a] -= 1; o[b] -= 1;
+      oa[a] -= 1;
+      ob[b] -= 1;
+      if (!inc(i, j, k, 1) || !inc(oa[0], oa[1], oa[2], 1) || !inc(ob[0], ob[1], ob[2], 1) ||
+          !inc(o[0], o[1], o[2], 1))
+        return;
+      size_t q11 = at(L, i, j, k);
+      size_t q01 = at(L, oa[0], oa[1], oa[2]);
+      size_t q10 = at(L, ob[0], ob[1], ob[2]);
       size_t q00 = at(L, o[0], o[1], o[2]);
-      if (!in(q11, 1) || !in(q01, 1) || !in(q10, 1) || !in(q00, 1)) return;
       // E_c on an a-face is -F_a[B_b]; on a b-face it is +F_b[B_a].
       double ea_hi = -L.F[a][BX + b][q11], ea_lo = -L.F[a][BX + b][q10];
       double eb_hi = L.F[b][BX + a][q11], eb_lo = L.F[b][BX + a][q01];
@@ -334,7 +410,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   for (int d = 0; d < 3; ++d) dtd[d] = dt * L.idx[d];
   std::vector<double> nu[NFIELD];
   for (int f = 0; f < NFIELD; ++f) nu[f] = L.u[f];
-  for_cells(L, [&](int i, int j, int k) {
+  for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
     // cell update
     if (in(q, 0)) {
@@ -348,8 +424,9 @@ static void advance_masked(Sim& S, Level& L, double dt) {
     }
     // face updates: d-face stored at q (between q-e_d and q)
     for (int d = 0; d < dim; ++d) {
-      size_t qm = atd(L, i, j, k, d, -1);
-      if (!in(q, 0) && !in(qm, 0)) continue;
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      if (!in(q, 0) && !inc(m[0], m[1], m[2], 0)) continue;
       double v = L.u[BX + d][q];
       if (dim == 2) {
         if (d == 0) v = v - dtd[1] * (L.E[2][atd(L, i, j, k, 1, 1)] - L.E[2][q]);
@@ -449,21 +526,85 @@ static void prolong_band(Sim& S, int l) {
   const int ncf = cell_fields(S, cf);
   for_cells(F, [&](int i, int j, int k) {
     size_t q = at(F, i, j, k);
-    int8_t dd = F.dist[q];
-    if (dd >= 1) {
+    if (F.dist[q] >= 1) {
       for (int n = 0; n < ncf; ++n)
         F.u[cf[n]][q] = prolong_cell(S, C, cf[n], i >> 1, j >> 1, S.dim == 3 ? k >> 1 : 0, i & 1, j & 1, S.dim == 3 ? (k & 1) : 0);
     }
-    // d-face between q-e_d and q: band face if not owned (no adjacent region
-    // cell) and adjacent to a band cell
-    for (int d = 0; d < S.dim; ++d) {
-      size_t qm = atd(F, i, j, k, d, -1);
-      int8_t dm = F.dist[qm];
-      if (dd == 0 || dm == 0) continue;
-      if (dd < 0 && dm < 0) continue;
-      F.u[BX + d][q] = prolong_face(S, C, F, d, i, j, k);
-    }
   });
+  // d-face between cells q-e_d and q of the domain closure: prolonged if not
+  // owned (no adjacent region cell) and adjacent to a band cell
+  for (int d = 0; d < S.dim; ++d)
+    for_face_pos(F, d, [&](int i, int j, int k) {
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      int8_t dd = in_storage(F, i, j, k) ? F.dist[at(F, i, j, k)] : -1;
+      int8_t dm = in_storage(F, m[0], m[1], m[2]) ? F.dist[at(F, m[0], m[1], m[2])] : -1;
+      if (dd == 0 || dm == 0) return;
+      if (dd < 0 && dm < 0) return;
+      F.u[BX + d][at(F, i, j, k)] = prolong_face(S, C, F, d, i, j, k);
+    });
+}
+
+// Physical boundaries (R17): margin cells and faces outside the domain. Cells
+// copy the nearest domain cell (zero-gradient outflow) or take the inflow
+// state; a face whose normal index lies beyond the boundary face copies that
+// boundary face, a face of a margin cell along another dimension copies the
+// face of the nearest domain cell; inflow faces take the inflow field.
+static bool outside_kind(const Sim& S, const Level& L, const int* o, int* clamped) {
+  bool inflow = false;
+  for (int d = 0; d < 3; ++d) {
+    clamped[d] = o[d];
+    if (L.per[d]) continue;
+    if (o[d] < 0) { clamped[d] = 0; inflow |= S.bc[d][0] == BC_INFLOW; }
+    else if (o[d] >= L.N[d]) { clamped[d] = L.N[d] - 1; inflow |= S.bc[d][1] == BC_INFLOW; }
+  }
+  return inflow;
+}
+
+static void fill_bc(Sim& S, int l) {
+  Level& L = S.lev[l];
+  bool any = false;
+  for (int d = 0; d < S.dim; ++d) any |= !L.per[d];
+  if (!any) return;
+  int cf[6];
+  const int ncf = cell_fields(S, cf);
+  for_all(L, [&](int i, int j, int k) {
+    const int o[3] = {i, j, k};
+    if (in_domain(L, i, j, k)) return;
+    int c[3];
+    const bool inflow = outside_kind(S, L, o, c);
+    size_t q = at(L, i, j, k), qs = at(L, c[0], c[1], c[2]);
+    for (int n = 0; n < ncf; ++n) L.u[cf[n]][q] = inflow ? S.inflow[cf[n]] : L.u[cf[n]][qs];
+  });
+  for (int d = 0; d < S.dim; ++d) {
+    // d-face positions of the storage: along a non-periodic d one beyond the cells
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+      lo[e] = -L.M[e];
+      hi[e] = L.N[e] + L.M[e] + ((e == d && !L.per[e]) ? 1 : 0);
+    }
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) {
+          const int o[3] = {i, j, k};
+          bool out = false, inflow = false;
+          int c[3] = {i, j, k};
+          for (int e = 0; e < 3; ++e) {
+            if (L.per[e]) continue;
+            const int top = e == d ? L.N[e] : L.N[e] - 1;
+            if (o[e] < 0) { out = true; c[e] = 0; inflow |= S.bc[e][0] == BC_INFLOW; }
+            else if (o[e] > top) {
+              out = true;
+              // bit 2 of flags: a planted off-by-one (the high-side normal face
+              // copies the face one cell inside) for the mirror-pair control
+              c[e] = (e == d && (S.flags & 4)) ? top - 1 : top;
+              inflow |= S.bc[e][1] == BC_INFLOW;
+            }
+          }
+          if (!out) continue;
+          L.u[BX + d][at(L, i, j, k)] = inflow ? S.inflow[BX + d] : L.u[BX + d][at(L, c[0], c[1], c[2])];
+        }
+  }
 }
 
 // ---------------------------------------------------------------- registers, reflux, restriction (R9)
@@ -503,10 +644,10 @@ static void add_fine_registers(Sim& S, int l, double dt) {
   const int ncf = cell_fields(S, cf);
   const double af = dt * (S.dim == 3 ? 0.25 : 0.5);
   const double ae = dt * (S.dim == 3 ? 0.5 : 1.0);
-  for_cells(C, [&](int i, int j, int k) {
-    size_t q = at(C, i, j, k);
-    for (int d = 0; d < S.dim; ++d) {
-      if (!F.cf_face[d][q]) continue;
+  for (int d = 0; d < S.dim; ++d)
+    for_face_pos(C, d, [&](int i, int j, int k) {
+      size_t q = at(C, i, j, k);
+      if (!F.cf_face[d][q]) return;
       size_t qf[4];
       int m = 0;
       for (int c2 = 0; c2 < 2; ++c2)
@@ -522,10 +663,12 @@ static void add_fine_registers(Sim& S, int l, double dt) {
         for (int s = 0; s < m; ++s) v[s] = F.F[d][cf[n]][qf[s]];
         F.rflux[d][cf[n]][q] += af * tree_sum(v, m);
       }
-    }
-    for (int c = 0; c < 3; ++c) {
-      if (S.dim == 2 && c != 2) continue;
-      if (!F.cf_edge[c][q]) continue;
+    });
+  for (int c = 0; c < 3; ++c) {
+    if (S.dim == 2 && c != 2) continue;
+    for_edge_pos(C, c, [&](int i, int j, int k) {
+      size_t q = at(C, i, j, k);
+      if (!F.cf_edge[c][q]) return;
       int nsub = S.dim == 3 ? 2 : 1;
       double v[2];
       for (int sidx = 0; sidx < nsub; ++sidx) {
@@ -534,8 +677,8 @@ static void add_fine_registers(Sim& S, int l, double dt) {
         v[sidx] = F.E[c][at(F, o[0], o[1], o[2])];
       }
       F.remf[c][q] += ae * tree_sum(v, nsub);
-    }
-  });
+    });
+  }
 }
 
 static void restrict_cell(const Sim& S, Level& C, const Level& F, int i, int j, int k, double wc) {
@@ -587,45 +730,50 @@ static void reflux_and_restrict(Sim& S, int l) {
           C.u[cf[n]][q] = C.u[cf[n]][q] - (F.rflux[d][cf[n]][qhi] - F.rcoarse[d][cf[n]][qhi]) * C.idx[d];
     }
   });
-  // EMF correction on uncovered coarse faces adjacent to C/F edges
-  for_cells(C, [&](int i, int j, int k) {
-    size_t q = at(C, i, j, k);
-    for (int d = 0; d < S.dim; ++d) {
-      size_t qm = atd(C, i, j, k, d, -1);
-      if (C.cov[q] || C.cov[qm]) continue;
+  // EMF correction on uncovered coarse faces adjacent to C/F edges (a cell
+  // outside the domain counts as uncovered)
+  auto covered = [&](int i, int j, int k) { return in_domain(C, i, j, k) && C.cov[at(C, i, j, k)]; };
+  for (int d = 0; d < S.dim; ++d)
+    for_face_pos(C, d, [&](int i, int j, int k) {
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      if (covered(i, j, k) || covered(m[0], m[1], m[2])) return;
+      size_t q = at(C, i, j, k);
       double v = C.u[BX + d][q];
-      auto add = [&](int c, size_t qe, double coef) {
-        if (F.cf_edge[c][qe]) v = v + coef * (F.remf[c][qe] - F.remfc[c][qe]);
+      auto add = [&](int c, int si, int sj, int sk, double coef) {
+        int e[3] = {i + si, j + sj, k + sk};
+        size_t qe = at(C, e[0], e[1], e[2]);
+        if (in_storage(C, e[0], e[1], e[2]) && F.cf_edge[c][qe]) v = v + coef * (F.remf[c][qe] - F.remfc[c][qe]);
       };
       if (S.dim == 2) {
-        if (d == 0) { add(2, q, C.idx[1]); add(2, atd(C, i, j, k, 1, 1), -C.idx[1]); }
-        else        { add(2, q, -C.idx[0]); add(2, atd(C, i, j, k, 0, 1), C.idx[0]); }
+        if (d == 0) { add(2, 0, 0, 0, C.idx[1]); add(2, 0, 1, 0, -C.idx[1]); }
+        else        { add(2, 0, 0, 0, -C.idx[0]); add(2, 1, 0, 0, C.idx[0]); }
       } else if (d == 0) {
-        add(2, q, C.idx[1]); add(2, atd(C, i, j, k, 1, 1), -C.idx[1]);
-        add(1, q, -C.idx[2]); add(1, atd(C, i, j, k, 2, 1), C.idx[2]);
+        add(2, 0, 0, 0, C.idx[1]); add(2, 0, 1, 0, -C.idx[1]);
+        add(1, 0, 0, 0, -C.idx[2]); add(1, 0, 0, 1, C.idx[2]);
       } else if (d == 1) {
-        add(0, q, C.idx[2]); add(0, atd(C, i, j, k, 2, 1), -C.idx[2]);
-        add(2, q, -C.idx[0]); add(2, atd(C, i, j, k, 0, 1), C.idx[0]);
+        add(0, 0, 0, 0, C.idx[2]); add(0, 0, 0, 1, -C.idx[2]);
+        add(2, 0, 0, 0, -C.idx[0]); add(2, 1, 0, 0, C.idx[0]);
       } else {
-        add(1, q, C.idx[0]); add(1, atd(C, i, j, k, 0, 1), -C.idx[0]);
-        add(0, q, -C.idx[1]); add(0, atd(C, i, j, k, 1, 1), C.idx[1]);
+        add(1, 0, 0, 0, C.idx[0]); add(1, 1, 0, 0, -C.idx[0]);
+        add(0, 0, 0, 0, -C.idx[1]); add(0, 0, 1, 0, C.idx[1]);
       }
       C.u[BX + d][q] = v;
-    }
-  });
+    });
   // R: restriction of covered cells and of faces in the closure of the fine
   // region: pairwise sums in z,y,x child order times 2^-dim (2^-(dim-1)).
   const double wc = S.dim == 3 ? 0.125 : 0.25;
   const double wf = S.dim == 3 ? 0.25 : 0.5;
   for_cells(C, [&](int i, int j, int k) {
-    size_t q = at(C, i, j, k);
-    if (C.cov[q]) restrict_cell(S, C, F, i, j, k, wc);
-    for (int d = 0; d < S.dim; ++d) {
-      size_t qm = atd(C, i, j, k, d, -1);
-      if (!C.cov[q] && !C.cov[qm]) continue;
-      restrict_face(S, C, F, d, i, j, k, wf);
-    }
+    if (C.cov[at(C, i, j, k)]) restrict_cell(S, C, F, i, j, k, wc);
   });
+  for (int d = 0; d < S.dim; ++d)
+    for_face_pos(C, d, [&](int i, int j, int k) {
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      if (!covered(i, j, k) && !covered(m[0], m[1], m[2])) return;
+      restrict_face(S, C, F, d, i, j, k, wf);
+    });
 }
 
 // ---------------------------------------------------------------- CFL (R6)
@@ -667,6 +815,7 @@ static void level_substep(Sim& S, int l, int s, double dt) {
   Level& L = S.lev[l];
   const int w = (l == 0) ? 0 : (s == 1 ? 2 : 0);
   if (l > 0 && s == 1) prolong_band(S, l);  // P
+  fill_bc(S, l);
   for (int f = 0; f < NFIELD; ++f) L.start[f] = L.u[f];
   L.tmask.assign(L.ncell, -1);
   for (size_t q = 0; q < L.ncell; ++q)
@@ -700,6 +849,18 @@ void* oc_new(int dim, const int* base, const double* lo, const double* hi, int n
   s->nlev = nlev;
   s->gamma = gamma;
   s->cfl = cfl;
+  return s;
+}
+
+// bc: 6 ints (x-low, x-high, y-low, y-high, z-low, z-high): 0 periodic,
+// 1 outflow, 2 inflow; a dimension is periodic only with both sides 0.
+// inflow: the conserved inflow state (rho, mx, my, mz, E, Bx, By, Bz).
+void* oc_new2(int dim, const int* base, const double* lo, const double* hi, int nlev, double gamma, double cfl,
+              const int* bc, const double* inflow) {
+  Sim* s = (Sim*)oc_new(dim, base, lo, hi, nlev, gamma, cfl);
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 2; ++e) s->bc[d][e] = d < dim ? bc[2 * d + e] : 0;
+  for (int f = 0; f < NFIELD; ++f) s->inflow[f] = inflow[f];
   return s;
 }
 
@@ -739,9 +900,13 @@ int oc_set_field(void* h, int level, int field, const double* a) {
   Level& L = s->lev[level];
   int n[3];
   field_shape(*s, level, field, n);
-  for (int k = 0; k < L.N[2]; ++k)
-    for (int j = 0; j < L.N[1]; ++j)
-      for (int i = 0; i < L.N[0]; ++i) L.u[field][at(L, i, j, k)] = a[((size_t)k * n[1] + j) * n[0] + i];
+  // a periodic dimension stores the face at N as the face at 0; a bounded one
+  // stores both domain faces
+  int m[3];
+  for (int d = 0; d < 3; ++d) m[d] = L.per[d] ? L.N[d] : n[d];
+  for (int k = 0; k < m[2]; ++k)
+    for (int j = 0; j < m[1]; ++j)
+      for (int i = 0; i < m[0]; ++i) L.u[field][at(L, i, j, k)] = a[((size_t)k * n[1] + j) * n[0] + i];
   return 0;
 }
 
@@ -775,7 +940,14 @@ void oc_set_flags(void* h, int flags) { ((Sim*)h)->flags = flags; }
 int oc_get_masks(void* h, int level, signed char* dist, signed char* cov) {
   Sim* s = (Sim*)h;
   Level& L = s->lev[level];
-  for (size_t q = 0; q < L.ncell; ++q) { dist[q] = L.dist[q]; cov[q] = L.cov[q]; }
+  size_t o = 0;
+  for (int k = 0; k < L.N[2]; ++k)
+    for (int j = 0; j < L.N[1]; ++j)
+      for (int i = 0; i < L.N[0]; ++i, ++o) {
+        const size_t q = at(L, i, j, k);
+        dist[o] = L.dist[q];
+        cov[o] = L.cov[q];
+      }
   return 0;
 }
 

@@ -9,7 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SOURCES = ["amr_oracle.cpp", "maps_oracle.cpp"]
+SOURCES = ["amr_oracle.cpp", "maps_oracle.cpp", "opcount.cpp"]
 
 
 def build(force=False):

@@ -19,7 +19,12 @@
 //  * Face-copy lists (EMF_FACES, RESTRICT_FACES) hold every stored copy of a
 //    face: each owner patch and, for a patch spanning the periodic domain, each
 //    of its two representatives of the seam face.
-//  * Kinds: 0 same-level copy, 1 prolongation from the parent level.
+//  * Kinds: 0 same-level copy, 1 prolongation from the parent level,
+//    2 boundary copy (zero-gradient outflow: src is the patch itself, Lsrc the
+//    nearest position inside the domain), 3 boundary inflow (src = Lsrc = -1).
+//    A ghost cell outside the domain of a non-periodic dimension is a boundary
+//    entry; so is a ghost face whose normal index lies beyond the boundary
+//    face or whose cell lies outside along another dimension.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -32,6 +37,8 @@ struct P { int level, lo[3], hi[3]; };
 struct H {
   int dim;
   int base[3];
+  bool per[3] = {true, true, true};
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   std::vector<P> p;
   int N(int l, int d) const { return d < dim ? (base[d] << l) : 1; }
   int ext(int q, int d) const { return d < dim ? (p[q].hi[d] - p[q].lo[d]) + 9 : 1; }
@@ -57,12 +64,14 @@ static bool face_owned(const P& q, const int* g, int d, int dim) {
   return true;
 }
 
-// all shift vectors in {-1,0,1}^dim, lexicographic (x most significant)
+// all shift vectors in {-1,0,1} per periodic dimension (0 otherwise),
+// lexicographic (x most significant)
+static const bool* g_per = nullptr;
 static std::vector<std::vector<int>> shifts(int dim) {
   std::vector<std::vector<int>> out;
-  int nz = dim == 3 ? 1 : 0;
-  for (int sx = -1; sx <= 1; ++sx)
-    for (int sy = -1; sy <= 1; ++sy)
+  const int nx = g_per[0] ? 1 : 0, ny = g_per[1] ? 1 : 0, nz = (dim == 3 && g_per[2]) ? 1 : 0;
+  for (int sx = -nx; sx <= nx; ++sx)
+    for (int sy = -ny; sy <= ny; ++sy)
       for (int sz = -nz; sz <= nz; ++sz) out.push_back({sx, sy, sz});
   return out;
 }
@@ -133,9 +142,17 @@ static int find_edge(const H& h, int l, const int* g, int c, int* L) {
   return best;
 }
 
+static bool in_domain(const H& h, int l, const int* g) {
+  for (int d = 0; d < h.dim; ++d)
+    if (!h.per[d] && (g[d] < 0 || g[d] >= h.N(l, d))) return false;
+  return true;
+}
+static int wrapd(const H& h, int l, int d, int i) { return h.per[d] ? wrapi(i, h.N(l, d)) : i; }
+
 static bool covered(const H& h, int l, const int* gc) {
-  // coarse cell gc on level l is covered by level l+1
-  int g[3] = {2 * wrapi(gc[0], h.N(l, 0)), 2 * wrapi(gc[1], h.N(l, 1)), h.dim == 3 ? 2 * wrapi(gc[2], h.N(l, 2)) : 0};
+  // coarse cell gc on level l is covered by level l+1 (never outside the domain)
+  if (!in_domain(h, l, gc)) return false;
+  int g[3] = {2 * wrapd(h, l, 0, gc[0]), 2 * wrapd(h, l, 1, gc[1]), h.dim == 3 ? 2 * wrapd(h, l, 2, gc[2]) : 0};
   int L;
   return find_cell(h, l + 1, g, &L) >= 0;
 }
@@ -158,11 +175,17 @@ enum {
 
 // Builds map `which` for the hierarchy; rows of int32 appended to out (up to
 // cap ints); *len receives the total number of ints. Returns the row width.
-int oc_build_map(int dim, const int* base, const int* patches, int n, int which, int* out, long long cap,
-                 long long* len) {
+int oc_build_map2(int dim, const int* base, const int* bc, const int* patches, int n, int which, int* out,
+                  long long cap, long long* len) {
   H h;
   h.dim = dim;
-  for (int d = 0; d < 3; ++d) h.base[d] = d < dim ? base[d] : 1;
+  for (int d = 0; d < 3; ++d) {
+    h.base[d] = d < dim ? base[d] : 1;
+    h.bc[d][0] = d < dim ? bc[2 * d] : 0;
+    h.bc[d][1] = d < dim ? bc[2 * d + 1] : 0;
+    h.per[d] = d >= dim || h.bc[d][0] == 0;
+  }
+  g_per = h.per;
   for (int i = 0; i < n; ++i) {
     P q;
     q.level = patches[7 * i];
@@ -207,14 +230,39 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
               if (own) continue;
               int Ld = h.loc(a, g);
               int Ls = -1, src = -1, kind;
+              // outside the domain of a non-periodic dimension: boundary entry
+              bool out = false, inflow = false;
+              int gc[3] = {g[0], g[1], g[2]};
+              for (int e = 0; e < dim; ++e) {
+                if (h.per[e]) continue;
+                const int top = (which == MAP_GHOST_FACES && e == d) ? h.N(l, e) : h.N(l, e) - 1;
+                if (g[e] < 0) { out = true; gc[e] = 0; inflow |= h.bc[e][0] == 2; }
+                else if (g[e] > top) { out = true; gc[e] = top; inflow |= h.bc[e][1] == 2; }
+              }
+              if (out) {
+                if (inflow) { kind = 3; src = -1; Ls = -1; }
+                else { kind = 2; src = a; Ls = h.loc(a, gc); }
+                if (which == MAP_GHOST_CELLS) emit({a, Ld, kind, src, Ls});
+                else emit({a, d, Ld, kind, src, Ls});
+                continue;
+              }
               if (which == MAP_GHOST_CELLS) src = find_cell(h, l, g, &Ls);
               else src = find_face(h, l, g, d, &Ls);
               if (src >= 0) kind = 0;
               else {
                 kind = 1;
                 int gc[3];
-                for (int e = 0; e < 3; ++e) gc[e] = e < dim ? (wrapi(g[e], h.N(l, e)) >> 1) : 0;
+                for (int e = 0; e < 3; ++e) gc[e] = e < dim ? (wrapd(h, l, e, g[e]) >> 1) : 0;
+                // a face on the high side of a non-periodic domain lies on the
+                // high face of the last coarse cell: search that cell, index the
+                // coarse face position one past it
+                const bool top_face = which == MAP_GHOST_FACES && !h.per[d] && g[d] == h.N(l, d);
+                if (top_face) gc[d] -= 1;
                 src = find_cell(h, l - 1, gc, &Ls);
+                if (top_face && src >= 0) {
+                  gc[d] += 1;
+                  Ls = h.loc(src, gc);
+                }
               }
               if (which == MAP_GHOST_CELLS) emit({a, Ld, kind, src, Ls});
               else emit({a, d, Ld, kind, src, Ls});
@@ -244,13 +292,14 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
                   if (side == 1) gf[d] += 1;
                   // children of the covered cell, in the fine patch's frame
                   int ch[3];
-                  for (int e = 0; e < 3; ++e) ch[e] = e < dim ? 2 * wrapi(gn[e], h.N(l - 1, e)) : 0;
+                  for (int e = 0; e < 3; ++e) ch[e] = e < dim ? 2 * wrapd(h, l - 1, e, gn[e]) : 0;
                   int Lc;
                   int pf = find_cell(h, l, ch, &Lc);
                   int ff[3] = {ch[0], ch[1], ch[2]};
                   if (side == 0) ff[d] += 2;  // covered cell on the low side: its high face
                   // ff is in pf's frame up to a period: bring it into pf's closure
                   for (int e = 0; e < dim; ++e) {
+                    if (!h.per[e]) continue;
                     int Ne = h.N(l, e);
                     while (ff[e] > h.p[pf].hi[e]) ff[e] -= Ne;
                     while (ff[e] < h.p[pf].lo[e]) ff[e] += Ne;
@@ -267,9 +316,12 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
         if (dim == 2 && ce != 2) continue;
         int a = (ce + 1) % 3, b = (ce + 2) % 3;
         int Nc[3] = {h.N(l - 1, 0), h.N(l - 1, 1), h.N(l - 1, 2)};
-        for (int k = 0; k < Nc[2]; ++k)
-          for (int j = 0; j < Nc[1]; ++j)
-            for (int i = 0; i < Nc[0]; ++i) {
+        int Ne[3] = {Nc[0], Nc[1], Nc[2]};
+        for (int e = 0; e < dim; ++e)
+          if (e != ce && !h.per[e]) Ne[e] += 1;
+        for (int k = 0; k < Ne[2]; ++k)
+          for (int j = 0; j < Ne[1]; ++j)
+            for (int i = 0; i < Ne[0]; ++i) {
               int g[3] = {i, j, k};
               int ncov = 0, cpf = -1;
               int firstcov[3] = {0, 0, 0};
@@ -335,7 +387,7 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
       for (int l = 1; l < nl; ++l) {
         int Nc[3] = {h.N(l - 1, 0), h.N(l - 1, 1), h.N(l - 1, 2)};
         auto edge_row = [&](int c, const int* g) {
-          int w[3] = {wrapi(g[0], Nc[0]), wrapi(g[1], Nc[1]), dim == 3 ? wrapi(g[2], Nc[2]) : 0};
+          int w[3] = {wrapd(h, l - 1, 0, g[0]), wrapd(h, l - 1, 1, g[1]), dim == 3 ? wrapd(h, l - 1, 2, g[2]) : 0};
           int Le;
           int qc = find_edge(h, l - 1, w, c, &Le);
           for (size_t r = 0; r < edges.size(); ++r)
@@ -343,9 +395,9 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
           return -1;
         };
         for (int d = 0; d < dim; ++d)
-          for (int k = 0; k < Nc[2]; ++k)
-            for (int j = 0; j < Nc[1]; ++j)
-              for (int i = 0; i < Nc[0]; ++i) {
+          for (int k = 0; k < Nc[2] + ((d == 2 && !h.per[2]) ? 1 : 0); ++k)
+            for (int j = 0; j < Nc[1] + ((d == 1 && !h.per[1]) ? 1 : 0); ++j)
+              for (int i = 0; i < Nc[0] + ((d == 0 && !h.per[0]) ? 1 : 0); ++i) {
                 int g[3] = {i, j, k};
                 int gm[3] = {i, j, k};
                 gm[d] -= 1;
@@ -390,9 +442,9 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
         }
       } else {
         for (int d = 0; d < dim; ++d)
-          for (int k = 0; k < Nc[2]; ++k)
-            for (int j = 0; j < Nc[1]; ++j)
-              for (int i = 0; i < Nc[0]; ++i) {
+          for (int k = 0; k < Nc[2] + ((d == 2 && !h.per[2]) ? 1 : 0); ++k)
+            for (int j = 0; j < Nc[1] + ((d == 1 && !h.per[1]) ? 1 : 0); ++j)
+              for (int i = 0; i < Nc[0] + ((d == 0 && !h.per[0]) ? 1 : 0); ++i) {
                 int g[3] = {i, j, k};
                 int gm[3] = {i, j, k};
                 gm[d] -= 1;
@@ -415,6 +467,12 @@ int oc_build_map(int dim, const int* base, const int* patches, int n, int which,
   long long m = std::min<long long>(cap, (long long)v.size());
   if (out && m > 0) std::memcpy(out, v.data(), sizeof(int) * (size_t)m);
   return width;
+}
+
+int oc_build_map(int dim, const int* base, const int* patches, int n, int which, int* out, long long cap,
+                 long long* len) {
+  const int bc[6] = {0, 0, 0, 0, 0, 0};
+  return oc_build_map2(dim, base, bc, patches, n, which, out, cap, len);
 }
 
 }  // extern "C"

@@ -22,6 +22,8 @@ def lib():
         L = C.CDLL(_build.build())
         L.oc_new.restype = C.c_void_p
         L.oc_new.argtypes = [C.c_int, _ip, _dp, _dp, C.c_int, C.c_double, C.c_double]
+        L.oc_new2.restype = C.c_void_p
+        L.oc_new2.argtypes = [C.c_int, _ip, _dp, _dp, C.c_int, C.c_double, C.c_double, _ip, _dp]
         L.oc_free.argtypes = [C.c_void_p]
         L.oc_set_patches.argtypes = [C.c_void_p, _ip, C.c_int]
         L.oc_field_size.restype = C.c_longlong
@@ -48,9 +50,15 @@ def lib():
         L.oc_gs_edge.argtypes = [_dp]
         L.oc_prolong_all.argtypes = [C.c_void_p, C.c_void_p]
         L.oc_restrict_all.argtypes = [C.c_void_p, C.c_void_p]
+        L.oc_flops_per_cell_update.restype = C.c_double
+        L.oc_flops_per_cell_update.argtypes = [C.c_int, C.c_int, C.c_uint]
+        L.oc_flops_recovery.restype = C.c_longlong
         L.oc_build_map.restype = C.c_int
         L.oc_build_map.argtypes = [C.c_int, _ip, _ip, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
                                    C.POINTER(C.c_longlong)]
+        L.oc_build_map2.restype = C.c_int
+        L.oc_build_map2.argtypes = [C.c_int, _ip, _ip, _ip, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
+                                    C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
 
@@ -67,15 +75,19 @@ def patch_array(patches):
 class OracleSim:
     """One hierarchy held by the oracle; fields are whole-level numpy arrays."""
 
-    def __init__(self, dim, base, patches, nlev=None, lo=(0, 0, 0), hi=(1, 1, 1), gamma=5.0 / 3.0, cfl=0.4):
+    def __init__(self, dim, base, patches, nlev=None, lo=(0, 0, 0), hi=(1, 1, 1), gamma=5.0 / 3.0, cfl=0.4,
+                 bc=None, inflow=None):
         self.dim = dim
         self.base = tuple(base) + (1,) * (3 - len(base))
         pa = patch_array(patches)
         if nlev is None:
             nlev = int(pa[:, 0].max()) + 1
         self.nlev = nlev
-        self.h = lib().oc_new(dim, np.array(self.base, dtype=np.int32), np.array(lo, dtype=np.float64),
-                              np.array(hi, dtype=np.float64), nlev, gamma, cfl)
+        bca = np.zeros(6, dtype=np.int32) if bc is None else np.ascontiguousarray(np.asarray(bc, dtype=np.int32).ravel())
+        inf = np.zeros(8) if inflow is None else np.ascontiguousarray(np.asarray(inflow, dtype=np.float64))
+        self.bc = bca
+        self.h = lib().oc_new2(dim, np.array(self.base, dtype=np.int32), np.array(lo, dtype=np.float64),
+                               np.array(hi, dtype=np.float64), nlev, gamma, cfl, bca, inf)
         self.status = lib().oc_set_patches(self.h, pa, len(pa))
         if self.status != 0:
             raise ValueError("oracle rejected the hierarchy: status %d" % self.status)
@@ -137,17 +149,28 @@ class OracleSim:
         lib().oc_step_targets(self.h, float(dt), ijk.ravel(), len(ijk))
 
 
-def build_map(dim, base, patches, which):
-    """Brute-force integer map; returns an (n_rows, width) int32 array."""
+def build_map(dim, base, patches, which, bc=None):
+    """Brute-force integer map; returns an (n_rows, width) int32 array. bc: 6
+    ints (x-low, x-high, ...): 0 periodic, 1 outflow, 2 inflow."""
     if isinstance(which, str):
         which = MAPS[which]
     pa = patch_array(patches)
     b = np.array(tuple(base) + (1,) * (3 - len(base)), dtype=np.int32)
+    bca = np.zeros(6, dtype=np.int32) if bc is None else np.ascontiguousarray(np.asarray(bc, dtype=np.int32).ravel())
     n = C.c_longlong(0)
-    w = lib().oc_build_map(dim, b, pa, len(pa), which, None, 0, C.byref(n))
+    w = lib().oc_build_map2(dim, b, bca, pa, len(pa), which, None, 0, C.byref(n))
     out = np.zeros(max(n.value, 1), dtype=np.int32)
-    lib().oc_build_map(dim, b, pa, len(pa), which, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n))
+    lib().oc_build_map2(dim, b, bca, pa, len(pa), which, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n))
     return out[: n.value].reshape(-1, w)
+
+
+def flops_per_cell_update(dim=3, nsample=2000, seed=1):
+    """Algorithmic FP operation count of one cell update (see opcount.cpp)."""
+    return lib().oc_flops_per_cell_update(dim, nsample, seed)
+
+
+def flops_recovery():
+    return lib().oc_flops_recovery()
 
 
 def hlld(ql, qr, bn, gamma=5.0 / 3.0, eps=1e-12):

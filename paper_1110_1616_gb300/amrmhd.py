@@ -33,6 +33,7 @@ class Config(C.Structure):
         ("dim", C.c_int32), ("base", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
         ("nghost", C.c_int32), ("ratio", C.c_int32), ("max_level", C.c_int32), ("precision", C.c_int32),
         ("bc", (C.c_int32 * 2) * 3), ("gamma", C.c_double), ("cfl", C.c_double), ("strict_fp64", C.c_int32),
+        ("inflow", C.c_double * 8),
     ]
 
 
@@ -90,7 +91,8 @@ def declared_symbols():
 
 
 def make_config(dim, base, precision=FP64, max_level=10, gamma=5.0 / 3.0, cfl=0.4, lo=(0, 0, 0), hi=(1, 1, 1),
-                strict_fp64=True):
+                strict_fp64=True, bc=None, inflow=None):
+    """bc: 6 ints (x-low, x-high, y-low, ...), 0 periodic, 1 outflow, 2 inflow."""
     c = Config()
     c.dim = dim
     b = tuple(base) + (1,) * (3 - len(base))
@@ -99,6 +101,10 @@ def make_config(dim, base, precision=FP64, max_level=10, gamma=5.0 / 3.0, cfl=0.
         c.lo[d] = lo[d]
         c.hi[d] = hi[d]
         c.bc[d][0] = c.bc[d][1] = 0
+        if bc is not None and d < dim:
+            c.bc[d][0], c.bc[d][1] = int(bc[2 * d]), int(bc[2 * d + 1])
+    for f in range(8):
+        c.inflow[f] = 0.0 if inflow is None else float(inflow[f])
     c.nghost, c.ratio, c.max_level, c.precision = 4, 2, max_level, precision
     c.gamma, c.cfl, c.strict_fp64 = gamma, cfl, 1 if strict_fp64 else 0
     return c
@@ -280,7 +286,7 @@ def advance_patch_noalloc(u_in, u_out, dim, n, dx, gamma, dt, w=0, stream=None):
 def context_for(problem, precision=FP64, strict_fp64=True, stream=None):
     """Context + hierarchy for an inputs.Problem (no device memory yet)."""
     cfg = make_config(problem.dim, problem.base, precision=precision, gamma=problem.gamma, cfl=problem.cfl,
-                      lo=problem.lo, hi=problem.hi, strict_fp64=strict_fp64)
+                      lo=problem.lo, hi=problem.hi, strict_fp64=strict_fp64, bc=problem.bc, inflow=problem.inflow)
     ctx = Context(cfg, stream)
     ctx.set_hierarchy(problem.patches)
     return ctx

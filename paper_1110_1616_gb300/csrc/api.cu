@@ -28,6 +28,7 @@ struct LevelDev {
   int npatch = 0;
   int maxn[3] = {1, 1, 1};
   DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
+  DevList bc_cells, bc_faces;                               // physical boundaries (kinds 2, 3)
   DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
   int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
 };
@@ -44,7 +45,11 @@ struct amrmhd_ctx {
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
   int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1;
-  bool fused() const { return cfg.dim == 3 && opt_advance == 0; }
+  // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
+  // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
+  bool fused() const {
+    return cfg.dim == 3 && (opt_advance == 3 || (opt_advance == 0 && cfg.precision == AMRMHD_MIXED));
+  }
   // arena layout (bytes)
   std::vector<long long> off, fs, soff;
   long long state_elems = 0, scr_elems = 0;
@@ -184,6 +189,16 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
     b.rows = L.prol_faces.p;
     b.nrows = L.prol_faces.n;
     ctx->ops->prolong_faces(b, ctx->stream, nl);
+  }
+  // physical boundaries last: their sources are domain cells filled above
+  if (L.bc_cells.n || L.bc_faces.n) {
+    RowArgs c = row_args(ctx, L.bc_cells, l);
+    c.fbuf = state_buf(ctx, ctx->cur[l]);
+    for (int f = 0; f < 8; ++f) c.inflow[f] = ctx->cfg.inflow[f];
+    ctx->ops->fill_bc_cells(c, ctx->stream, nl);
+    c.rows = L.bc_faces.p;
+    c.nrows = L.bc_faces.n;
+    ctx->ops->fill_bc_faces(c, ctx->stream, nl);
   }
 }
 
@@ -347,8 +362,10 @@ amrmhd_status amrmhd_create(const amrmhd_config* cfg, void* cuda_stream, amrmhd_
   for (int d = 0; d < 3; ++d) {
     if (d < cfg->dim && (cfg->base[d] < 8 || !(cfg->hi[d] > cfg->lo[d]))) return AMRMHD_EINVAL;
     if (d >= cfg->dim && cfg->base[d] != 1) return AMRMHD_EINVAL;
+    if (d >= cfg->dim) continue;
     for (int s = 0; s < 2; ++s)
-      if (d < cfg->dim && cfg->bc[d][s] != AMRMHD_BC_PERIODIC) return AMRMHD_EINVAL;
+      if (cfg->bc[d][s] < AMRMHD_BC_PERIODIC || cfg->bc[d][s] > AMRMHD_BC_INFLOW) return AMRMHD_EINVAL;
+    if ((cfg->bc[d][0] == AMRMHD_BC_PERIODIC) != (cfg->bc[d][1] == AMRMHD_BC_PERIODIC)) return AMRMHD_EINVAL;
   }
   amrmhd_ctx* ctx = new amrmhd_ctx();
   ctx->cfg = *cfg;
@@ -370,7 +387,7 @@ amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx) {
 
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) {
   if (!ctx) return AMRMHD_EINVAL;
-  if (option == AMRMHD_OPT_ADVANCE && (value == 0 || value == 1 || value == 2)) ctx->opt_advance = value;
+  if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 3) ctx->opt_tile = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
@@ -385,7 +402,12 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
   ctx->have_h = false;
   amrmhd::Hierarchy& H = ctx->H;
   H.dim = ctx->cfg.dim;
-  for (int d = 0; d < 3; ++d) H.base[d] = ctx->cfg.base[d];
+  for (int d = 0; d < 3; ++d) {
+    H.base[d] = ctx->cfg.base[d];
+    H.bc[d][0] = d < H.dim ? ctx->cfg.bc[d][0] : 0;
+    H.bc[d][1] = d < H.dim ? ctx->cfg.bc[d][1] : 0;
+    H.per[d] = d >= H.dim || H.bc[d][0] == AMRMHD_BC_PERIODIC;
+  }
   H.max_level = ctx->cfg.max_level;
   std::vector<int32_t> rows(7 * (size_t)n);
   for (int i = 0; i < n; ++i) {
@@ -514,21 +536,29 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
     CU(cudaMemcpy(L.ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
     // ghost lists of this level's patches, split by kind
-    std::vector<int32_t> sc, pc, sf, pf;
+    std::vector<int32_t> sc, pc, sf, pf, bcc, bcf;
     for (size_t r = 0; r < H.ghost_cells.size(); r += 5) {
       const int32_t* g = &H.ghost_cells[r];
       if (H.p[g[0]].level != l) continue;
+      if (g[2] >= 2) {
+        bcc.insert(bcc.end(), g, g + 5);
+        continue;
+      }
       std::vector<int32_t>& v = g[2] == 0 ? sc : pc;
       v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[3]); v.push_back(g[4]);
     }
     for (size_t r = 0; r < H.ghost_faces.size(); r += 6) {
       const int32_t* g = &H.ghost_faces[r];
       if (H.p[g[0]].level != l) continue;
+      if (g[3] >= 2) {
+        bcf.insert(bcf.end(), g, g + 6);
+        continue;
+      }
       std::vector<int32_t>& v = g[3] == 0 ? sf : pf;
       v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[2]); v.push_back(g[4]); v.push_back(g[5]);
     }
     bool ok = upload(sc, L.same_cells, 4) && upload(pc, L.prol_cells, 4) && upload(sf, L.same_faces, 5) &&
-              upload(pf, L.prol_faces, 5);
+              upload(pf, L.prol_faces, 5) && upload(bcc, L.bc_cells, 5) && upload(bcf, L.bc_faces, 6);
     if (l > 0 && ok) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
         return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);

@@ -31,11 +31,13 @@ namespace {
 // Uniform bins over one level, for the level-0 neighbour search and the parent search.
 struct Bins {
   int N[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, B = 16, dim = 2;
+  bool per[3] = {true, true, true};
   std::vector<std::vector<int>> bin;
   std::vector<int> stamp;
   int tick = 0;
   void init(const Hierarchy& h, int l, int B_) {
     dim = h.dim;
+    for (int d = 0; d < 3; ++d) per[d] = h.per[d];
     B = B_;
     for (int d = 0; d < 3; ++d) {
       N[d] = h.N(l, d);
@@ -57,9 +59,9 @@ struct Bins {
   }
   // All (q, s) whose interior shifted by s*N meets [lo, hi) (unwrapped).
   void query(const Hierarchy& h, const int* lo, const int* hi, bool only_zero_shift, std::vector<Nbr>& out) {
-    int zs = dim == 3 ? 1 : 0;
-    for (int sx = -1; sx <= 1; ++sx)
-      for (int sy = -1; sy <= 1; ++sy)
+    const int xs = per[0] ? 1 : 0, ys = per[1] ? 1 : 0, zs = (dim == 3 && per[2]) ? 1 : 0;
+    for (int sx = -xs; sx <= xs; ++sx)
+      for (int sy = -ys; sy <= ys; ++sy)
         for (int sz = -zs; sz <= zs; ++sz) {
           int s[3] = {sx, sy, sz};
           if (only_zero_shift && (sx || sy || sz)) continue;
@@ -217,7 +219,8 @@ int Hierarchy::build(const int32_t* rows7, int n) {
         if (d >= dim) { lo[d] = 0; hi[d] = 1; continue; }
         lo[d] = p[q].lo[d] / 2 - 3;
         hi[d] = p[q].hi[d] / 2 + 3;
-        if (hi[d] - lo[d] >= N(l - 1, d)) { lo[d] = 0; hi[d] = N(l - 1, d); }
+        if (!per[d]) { lo[d] = std::max(lo[d], 0); hi[d] = std::min(hi[d], N(l - 1, d)); }
+        else if (hi[d] - lo[d] >= N(l - 1, d)) { lo[d] = 0; hi[d] = N(l - 1, d); }
         need *= hi[d] - lo[d];
       }
       std::vector<Nbr> cov;
@@ -250,14 +253,23 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     }
     std::sort(cc.begin(), cc.end());
     cc.erase(std::unique(cc.begin(), cc.end()), cc.end());
-    auto coarse_src = [&](const int* g, int* L) {
+    // parent cell of fine position g; for a d-face (dn >= 0) on the high side
+    // of a non-periodic domain the parent is the last coarse cell and L indexes
+    // the coarse face one past it
+    auto coarse_src = [&](const int* g, int* L, int dn) {
       int c[3];
-      for (int d = 0; d < 3; ++d) c[d] = d < dim ? (wrapi(g[d], N(l, d)) >> 1) : 0;
+      for (int d = 0; d < 3; ++d) c[d] = d < dim ? (wrapd(l, d, g[d]) >> 1) : 0;
+      const bool top = dn >= 0 && !per[dn] && g[dn] == N(l, dn);
+      if (top) c[dn] -= 1;
       for (int Q : cc) {
         bool in = true;
         for (int d = 0; d < dim; ++d)
           if (c[d] < p[Q].lo[d] || c[d] >= p[Q].hi[d]) in = false;
-        if (in) { *L = loc(Q, c[0], c[1], c[2]); return Q; }
+        if (in) {
+          if (top) c[dn] += 1;
+          *L = loc(Q, c[0], c[1], c[2]);
+          return Q;
+        }
       }
       return -1;
     };
@@ -290,14 +302,32 @@ int Hierarchy::build(const int32_t* rows7, int n) {
             bool inner = a >= P.lo[0] && a < P.hi[0] && b >= P.lo[1] && b < P.hi[1] &&
                          (dim == 2 || (c >= P.lo[2] && c < P.hi[2]));
             if (inner) continue;
+            {
+              // outside the domain of a non-periodic dimension: boundary entry
+              int g[3] = {a, b, c}, gc[3] = {a, b, c};
+              bool out = false, inflow = false;
+              for (int e = 0; e < dim; ++e) {
+                if (per[e]) continue;
+                if (g[e] < 0) { out = true; gc[e] = 0; inflow |= bc[e][0] == 2; }
+                else if (g[e] > N(l, e) - 1) { out = true; gc[e] = N(l, e) - 1; inflow |= bc[e][1] == 2; }
+              }
+              if (out) {
+                int row[5] = {q, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q, inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
+                ghost_cells.insert(ghost_cells.end(), row, row + 5);
+                continue;
+              }
+            }
             size_t t = idx(a, b, c);
             int kind = 0, src = sq[t], L = sl[t];
             if (src < 0) {
               if (l == 0) { err = "level-0 ghost cell without a source"; return AMRMHD_EINVAL; }
               int g[3] = {a, b, c};
               kind = 1;
-              src = coarse_src(g, &L);
-              if (src < 0) { err = "no parent-level source for a ghost cell of patch " + std::to_string(q); return AMRMHD_ENEST; }
+              src = coarse_src(g, &L, -1);
+              if (src < 0) { err = "no parent-level source for the ghost cell (" + std::to_string(a) + ", " + std::to_string(b) + ", " +
+                      std::to_string(c) + ") of patch " + std::to_string(q);
+                return AMRMHD_ENEST;
+              }
             }
             int row[5] = {q, loc(q, a, b, c), kind, src, L};
             ghost_cells.insert(ghost_cells.end(), row, row + 5);
@@ -342,13 +372,32 @@ int Hierarchy::build(const int32_t* rows7, int n) {
               else if (g[e] < P.lo[e] || g[e] >= P.hi[e]) own = false;
             }
             if (own) continue;
+            {
+              int gc[3] = {a, b, c};
+              bool out = false, inflow = false;
+              for (int e = 0; e < dim; ++e) {
+                if (per[e]) continue;
+                const int top = e == d ? N(l, e) : N(l, e) - 1;
+                if (g[e] < 0) { out = true; gc[e] = 0; inflow |= bc[e][0] == 2; }
+                else if (g[e] > top) { out = true; gc[e] = top; inflow |= bc[e][1] == 2; }
+              }
+              if (out) {
+                int row[6] = {q, d, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q,
+                              inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
+                ghost_faces.insert(ghost_faces.end(), row, row + 6);
+                continue;
+              }
+            }
             size_t t = idx(a, b, c);
             int kind = 0, src = sq[t], L = sl[t];
             if (src < 0) {
               if (l == 0) { err = "level-0 ghost face without a source"; return AMRMHD_EINVAL; }
               kind = 1;
-              src = coarse_src(g, &L);
-              if (src < 0) { err = "no parent-level source for a ghost face of patch " + std::to_string(q); return AMRMHD_ENEST; }
+              src = coarse_src(g, &L, d);
+              if (src < 0) { err = "no parent-level source for the ghost face (" + std::to_string(d) + "; " + std::to_string(a) + ", " +
+                      std::to_string(b) + ", " + std::to_string(c) + ") of patch " + std::to_string(q);
+                return AMRMHD_ENEST;
+              }
             }
             int row[6] = {q, d, loc(q, a, b, c), kind, src, L};
             ghost_faces.insert(ghost_faces.end(), row, row + 6);
@@ -493,7 +542,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
                   if (bf < 0 || v.c < bf || (v.c == bf && Lf < bl)) { bf = v.c; bl = Lf; }
                 }
               if (ncov < 1 || ncov > 3) continue;
-              Key key{c, wrapi(i, N(lc, 0)), wrapi(j, N(lc, 1)), dim == 3 ? wrapi(k, N(lc, 2)) : 0};
+              Key key{c, wrapd(lc, 0, i), wrapd(lc, 1, j), dim == 3 ? wrapd(lc, 2, k) : 0};
               int Le = loc(qc, i, j, k);
               auto it = edge_best.find(key);
               if (it == edge_best.end()) edge_best[key] = {qc, Le, bf, bl};
@@ -572,7 +621,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
                   if (dim == 2 && comp != 2) continue;
                   int gs[3] = {i, j, k};
                   gs[slot < 2 ? t1 : t2] += slot & 1;
-                  Key key{comp, wrapi(gs[0], N(lc, 0)), wrapi(gs[1], N(lc, 1)), dim == 3 ? wrapi(gs[2], N(lc, 2)) : 0};
+                  Key key{comp, wrapd(lc, 0, gs[0]), wrapd(lc, 1, gs[1]), dim == 3 ? wrapd(lc, 2, gs[2]) : 0};
                   auto it = edge_row.find(key);
                   if (it != edge_row.end()) { e[slot] = it->second; any = true; }
                 }

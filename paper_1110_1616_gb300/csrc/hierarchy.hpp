@@ -31,6 +31,8 @@ struct Nbr {
 struct Hierarchy {
   int dim = 2;
   int base[3] = {1, 1, 1};
+  bool per[3] = {true, true, true};        // periodic dimension
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // 0 periodic, 1 outflow, 2 inflow
   int max_level = 0;
   int nlev = 0;
   std::vector<HPatch> p;
@@ -54,6 +56,11 @@ struct Hierarchy {
   std::string err;
 
   int N(int l, int d) const { return d < dim ? (base[d] << l) : 1; }
+  int wrapd(int l, int d, int i) const {
+    if (!per[d]) return i;
+    int n = N(l, d), r = i % n;
+    return r < 0 ? r + n : r;
+  }
   int loc(int q, int a, int b, int c) const;  // local index of level position (a,b,c)
   // Returns 0 or a negative amrmhd_status; fills err.
   int build(const int32_t* rows7, int n);

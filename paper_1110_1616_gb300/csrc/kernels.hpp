@@ -50,7 +50,7 @@ struct RowArgs {
   double idx[3];     // coarse level 1/dx
   double ratio[3][3];  // dx_n/dx_t on the coarse level
   int substep;       // 1 or 2
-  const double* flux_rows;  // unused
+  double inflow[8];  // conserved inflow state (boundary fill)
 };
 
 struct CflArgs {
@@ -75,6 +75,8 @@ struct Ops {
   void (*fill_same_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*fill_bc_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*fill_bc_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*reflux_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*reflux_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*restrict_cells)(const RowArgs&, cudaStream_t, int* launches);

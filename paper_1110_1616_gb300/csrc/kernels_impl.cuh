@@ -348,6 +348,42 @@ template <class T, int DIM> __global__ void k_fill_same_faces(RowArgs a) {
   ((T*)a.fbuf)[D.off + f * D.fs + row[2]] = ((const T*)a.fbuf)[S.off + f * S.fs + row[4]];
 }
 
+// physical boundary cells: rows (dst, Ldst, kind, src, Lsrc); kind 2 copies
+// the patch's own nearest domain cell, kind 3 sets the inflow state
+template <class T, int DIM> __global__ void k_fill_bc_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 5 * r;
+  const DPatch D = a.P[row[0]];
+  T* dst = (T*)a.fbuf + D.off + row[1];
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+  if (row[2] == 3) {
+#pragma unroll
+    for (int n = 0; n < NCF; ++n) {
+      const int f = n < 5 ? n : BZ;
+      dst[f * D.fs] = (T)a.inflow[f];
+    }
+  } else {
+    const T* src = (const T*)a.fbuf + D.off + row[4];
+#pragma unroll
+    for (int n = 0; n < NCF; ++n) {
+      const int f = n < 5 ? n : BZ;
+      dst[f * D.fs] = src[f * D.fs];
+    }
+  }
+}
+
+// physical boundary faces: rows (dst, d, Ldst, kind, src, Lsrc)
+template <class T, int DIM> __global__ void k_fill_bc_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch D = a.P[row[0]];
+  const int f = BX + row[1];
+  T* B = (T*)a.fbuf + D.off + f * D.fs;
+  B[row[2]] = row[3] == 3 ? (T)a.inflow[f] : B[row[5]];
+}
+
 template <int DIM> __device__ __forceinline__ void global_pos(const DPatch& P, int L, int* g) {
   const int a = L % P.ext[0];
   const int b = (L / P.ext[0]) % P.ext[1];
@@ -644,6 +680,8 @@ template <class T, int DIM> struct Impl {
   AMRK_ROWS(fill_same_faces)
   AMRK_ROWS(prolong_cells)
   AMRK_ROWS(prolong_faces)
+  AMRK_ROWS(fill_bc_cells)
+  AMRK_ROWS(fill_bc_faces)
   AMRK_ROWS(reflux_cells)
   AMRK_ROWS(reflux_faces)
   AMRK_ROWS(restrict_cells)
@@ -707,7 +745,7 @@ template <class T, int DIM> struct Impl {
   }
   static const Ops* ops() {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, prolong_cells,
-                          prolong_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
+                          prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc};
     return &o;
   }

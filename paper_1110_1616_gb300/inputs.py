@@ -5,10 +5,15 @@ draws); it contains none of the advance's arithmetic. Both the CUDA path and the
 CPU oracle take their inputs from here, so each sees identical arrays.
 
 State format: ``{level: [rho, mx, my, mz, E, bx, by, bz]}``; each entry is a
-whole-level numpy float64 array over the periodic domain at that level's
-resolution, x fastest: cell fields have shape (Nz, Ny, Nx); the face field
-along d has one extra entry along d (entry N_d repeats entry 0). In 2D, Nz = 1
-and bz is a cell field.
+whole-level numpy float64 array over the domain at that level's resolution,
+x fastest: cell fields have shape (Nz, Ny, Nx); the face field along d has one
+extra entry along d (in a periodic dimension entry N_d repeats entry 0; in a
+bounded one it is the high boundary face). In 2D, Nz = 1 and bz is a cell
+field.
+
+Boundaries: ``Problem.bc`` lists (x-low, x-high, y-low, y-high, z-low,
+z-high) with 0 periodic, 1 zero-gradient outflow, 2 fixed inflow of the
+conserved state ``Problem.inflow``; None means periodic everywhere.
 
 Patches are ``(level, lo, hi)`` with half-open level-l cell index boxes
 (2D: lo[2] = 0, hi[2] = 1). Patch ids are list positions.
@@ -34,6 +39,8 @@ class Problem:
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (1.0, 1.0, 1.0)
     meta: dict = field(default_factory=dict)
+    bc: tuple = None      # 6 ints (x-low, x-high, ...): 0 periodic, 1 outflow, 2 inflow
+    inflow: tuple = None  # conserved inflow state (rho, mx, my, mz, E, Bx, By, Bz)
 
     def level_n(self, level):
         return tuple(self.base[d] << level if d < self.dim else 1 for d in range(3))
@@ -87,14 +94,17 @@ def _cell_b_from_faces(bx, by, bz, dim):
     return bcx, bcy, bcz
 
 
-def _b_from_az_2d(az_corner, n, dx, dy):
-    """Face B from a corner vector potential A_z of shape (Ny+1, Nx+1). The
-    periodic copy (entry N along the face normal) is set to entry 0 exactly,
-    so that both stored copies of a seam face agree bit for bit."""
+def _b_from_az_2d(az_corner, n, dx, dy, periodic=(True, True)):
+    """Face B from a corner vector potential A_z of shape (Ny+1, Nx+1). In a
+    periodic dimension the copy (entry N along the face normal) is set to
+    entry 0 exactly, so that both stored copies of a seam face agree bit for
+    bit."""
     bx = (az_corner[1:, :] - az_corner[:-1, :]) / dy  # (Ny, Nx+1)
     by = -(az_corner[:, 1:] - az_corner[:, :-1]) / dx  # (Ny+1, Nx)
-    bx[:, -1] = bx[:, 0]
-    by[-1, :] = by[0, :]
+    if periodic[0]:
+        bx[:, -1] = bx[:, 0]
+    if periodic[1]:
+        by[-1, :] = by[0, :]
     return bx[None], by[None]
 
 
@@ -247,6 +257,139 @@ def random_smooth_2d(n, nlev, seed=0, amp=0.05, gamma=GAMMA):
         bx, by = _b_from_az_2d(az, nn, dx, dx)
         state[l] = _state_2d(nn, rho, vx, vy, vz, p, bx, by, bz, gamma)
     return state
+
+
+def conserved(prim, gamma=GAMMA):
+    """Conserved vector (rho, mx, my, mz, E, Bx, By, Bz) of one primitive state
+    (rho, vx, vy, vz, p, Bx, By, Bz)."""
+    rho, vx, vy, vz, p, bx, by, bz = [float(v) for v in prim]
+    return (rho, rho * vx, rho * vy, rho * vz, _energy(rho, vx, vy, vz, p, bx, by, bz, gamma), bx, by, bz)
+
+
+def rankine_hugoniot(mach, rho1=1.0, p1=None, gamma=GAMMA):
+    """Hydrodynamic normal-shock jump in the shock frame for an upstream state
+    of sound speed 1 (p1 = rho1 / gamma unless given): returns (rho1, u1, p1,
+    rho2, u2, p2). A field along the shock normal leaves the jump unchanged."""
+    if p1 is None:
+        p1 = rho1 / gamma
+    c1 = math.sqrt(gamma * p1 / rho1)
+    u1 = mach * c1
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    u2 = u1 * rho1 / rho2
+    return rho1, u1, p1, rho2, u2, p2
+
+
+def _fill_level(n, dim, cells, faces):
+    """Whole-level arrays of a state given per-cell primitive arrays
+    (rho, vx, vy, vz, p, bz-cell in 2D) and per-face normal B arrays."""
+    rho, vx, vy, vz, p = cells[:5]
+    bx, by, bz = faces
+    bcx, bcy, bcz = _cell_b_from_faces(bx, by, bz, dim)
+    e = _energy(rho, vx, vy, vz, p, bcx, bcy, bcz, gamma=cells[5])
+    return [rho, rho * vx, rho * vy, rho * vz, e, bx, by, bz]
+
+
+def stationary_shock(dim=2, n=64, mach=10.0, bn=0.2, refine=True, psize=8, gamma=GAMMA):
+    """A stationary planar shock at x = 1/2 (a face of every level) on
+    [0,1] x [0,1/8] (x [0,1/8] in 3D): supersonic inflow of the upstream
+    state (rho 1, sound speed 1, velocity +mach) at x-low, zero-gradient
+    outflow at x-high, periodic in y and z; the downstream state is the
+    Rankine-Hugoniot jump; uniform normal field Bx = bn. With refine, level 1
+    covers the shock and both x boundaries."""
+    rho1, u1, p1, rho2, u2, p2 = rankine_hugoniot(mach, gamma=gamma)
+    m = n // 8
+    base = (n, m, m if dim == 3 else 1)
+    hi = (1.0, 1.0 / 8.0, 1.0 / 8.0 if dim == 3 else 1.0)
+    patches = tile(0, (0, 0, 0), base, psize, dim)
+    nlev = 1
+    if refine:
+        fy = (2 * base[1], 2 * base[2] if dim == 3 else 1)
+        for x0, x1 in ((0, n // 4), (n - n // 4, n + n // 4), (2 * n - n // 4, 2 * n)):
+            patches += tile(1, (x0, 0, 0), (x1, fy[0], fy[1]), psize, dim)
+        nlev = 2
+    state = {}
+    for l in range(nlev):
+        nn = tuple(base[d] << l if d < dim else 1 for d in range(3))
+        x, _, _ = _cell_centres(nn, (0, 0, 0), hi, dim)
+        up = x < 0.5
+        rho = np.where(up, rho1, rho2)
+        vx = np.where(up, u1, u2)
+        p = np.where(up, p1, p2)
+        zero = np.zeros_like(x)
+        bx = np.full((nn[2], nn[1], nn[0] + 1), bn)
+        by = np.zeros((nn[2], nn[1] + 1, nn[0]))
+        bz = np.zeros((nn[2] + 1, nn[1], nn[0])) if dim == 3 else zero.copy()
+        state[l] = _fill_level(nn, dim, (rho, vx, zero, zero.copy(), p, gamma), (bx, by, bz))
+    bc = (2, 1, 0, 0, 0, 0)
+    return Problem("stationary_shock_%dd" % dim, dim, base, patches, nlev, state, gamma=gamma, hi=hi, bc=bc,
+                   inflow=conserved((rho1, u1, 0, 0, p1, bn, 0, 0), gamma),
+                   meta={"mach": mach, "downstream": (rho2, u2, p2), "upstream": (rho1, u1, p1)})
+
+
+def uniform_flow(dim, base, patches, nlev, bc, seed=0, gamma=GAMMA):
+    """A random constant state with a non-zero velocity on every level; the
+    inflow state (used on inflow sides) is that same state."""
+    rng = np.random.default_rng(seed)
+    prim = (rng.uniform(0.5, 2.0), *rng.uniform(0.3, 1.0, size=3) * rng.choice([-1, 1], size=3),
+            rng.uniform(0.2, 2.0), *rng.uniform(-1, 1, size=3))
+    u = conserved(prim, gamma)
+    state = {}
+    for l in range(nlev):
+        n = tuple(base[d] << l if d < dim else 1 for d in range(3))
+        shp = (n[2], n[1], n[0])
+        one = np.ones(shp)
+        bx = np.full((n[2], n[1], n[0] + 1), u[5])
+        by = np.full((n[2], n[1] + 1, n[0]), u[6])
+        bz = np.full((n[2] + 1, n[1], n[0]), u[7]) if dim == 3 else one * u[7]
+        state[l] = [one * u[0], one * u[1], one * u[2], one * u[3], one * u[4], bx, by, bz]
+    return Problem("uniform_flow_%dd" % dim, dim, tuple(base), patches, nlev, state, gamma=gamma, bc=tuple(bc),
+                   inflow=u)
+
+
+def smooth_bounded_2d(n=32, refine=True, seed=0, mirrored=False, gamma=GAMMA):
+    """A smooth random 2D flow through a box bounded in x (outflow on both x
+    sides, periodic y) with vx in [0.3, 0.9] and vy in [0.15, 0.45], so no face
+    mass flux changes sign. mirrored=True gives the exact mirror image about
+    x = 1/2 (vx and Bx negated, cells and faces reversed in x), which flows the
+    other way. Level 1 covers both x boundaries and the centre, a layout that
+    is its own mirror image."""
+    rng = np.random.default_rng(seed)
+    patches = tile(0, (0, 0, 0), (n, n, 1), 8, 2)
+    nlev = 1
+    if refine:
+        for x0, x1 in ((0, n // 2), (n - n // 4, n + n // 4), (2 * n - n // 2, 2 * n)):
+            patches += tile(1, (x0, 0, 0), (x1, 2 * n, 1), 8, 2)
+        nlev = 2
+    k = [(int(rng.integers(1, 3)), int(rng.integers(1, 3)), rng.uniform(0, 2 * math.pi)) for _ in range(7)]
+    a = rng.uniform(0.05, 0.1, size=7)
+
+    def f(c, X, Y):
+        kx, ky, ph = k[c]
+        return a[c] * np.sin(2 * math.pi * (kx * X + ky * Y) + ph)
+
+    state = {}
+    for l in range(nlev):
+        nn = (n << l, n << l, 1)
+        dx = 1.0 / nn[0]
+        x, y, _ = _cell_centres(nn, (0, 0, 0), (1, 1, 1), 2)
+        rho = 1.0 + 2.0 * f(0, x, y)
+        p = 1.0 + 2.0 * f(1, x, y)
+        vx = 0.6 + 3.0 * f(2, x, y)
+        vy = 0.3 + 1.5 * f(3, x, y)
+        vz = f(4, x, y)
+        bz = 0.3 + f(5, x, y)
+        Y, X = np.meshgrid(np.arange(nn[1] + 1) * dx, np.arange(nn[0] + 1) * dx, indexing="ij")
+        az = 0.4 * Y - 0.2 * X + f(6, X, Y) / (2 * math.pi)
+        bx, by = _b_from_az_2d(az, nn, dx, dx, periodic=(False, True))
+        st = _state_2d(nn, rho, vx, vy, vz, p, bx, by, bz, gamma)
+        if mirrored:
+            sign = (1, -1, 1, 1, 1, -1, 1, 1)
+            st = [sign[i] * v[..., ::-1] for i, v in enumerate(st)]
+        state[l] = [np.ascontiguousarray(v) for v in st]
+    return Problem("smooth_bounded_2d", 2, (n, n, 1), patches, nlev, state, gamma=gamma, bc=(1, 1, 0, 0, 0, 0),
+                   meta={"seed": seed, "mirrored": mirrored})
 
 
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):

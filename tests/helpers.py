@@ -6,7 +6,8 @@ from oracle import OracleSim
 
 
 def oracle_for(pb):
-    s = OracleSim(pb.dim, pb.base, pb.patches, pb.nlev, lo=pb.lo, hi=pb.hi, gamma=pb.gamma, cfl=pb.cfl)
+    s = OracleSim(pb.dim, pb.base, pb.patches, pb.nlev, lo=pb.lo, hi=pb.hi, gamma=pb.gamma, cfl=pb.cfl,
+                  bc=pb.bc, inflow=pb.inflow)
     s.set_state(pb.state)
     return s
 

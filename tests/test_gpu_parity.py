@@ -251,7 +251,7 @@ def test_blast3d_full_size_sampled(precision):
 
 @pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
 def test_fused_equals_staged_3d_amr(precision):
-    """The fused 3D advance (default) and the staged kernels (option 2) give
+    """The fused 3D advance (option 3) and the staged kernels (option 2) give
     the same result on a 3D AMR hierarchy: bitwise in the strict FP64 build
     (registers recomputed from the state vs read from the staged scratch),
     within FP32 rounding in mixed precision."""
@@ -262,7 +262,7 @@ def test_fused_equals_staged_3d_amr(precision):
     pb = inputs.Problem("blast3d_amr", 3, base, patches, 2, st)
     import torch
     out = []
-    for opt in (0, 2):
+    for opt in (3, 2):
         s = torch.cuda.Stream()
         ctx = A.Context(A.make_config(3, base, precision=precision, strict_fp64=True), s.cuda_stream)
         ctx.set_option(A.OPT_ADVANCE, opt)

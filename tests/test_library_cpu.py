@@ -26,8 +26,8 @@ def test_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
-def ctx_for(dim, base, patches, max_level=10):
-    cfg = A.make_config(dim, base, max_level=max_level)
+def ctx_for(dim, base, patches, max_level=10, bc=None):
+    cfg = A.make_config(dim, base, max_level=max_level, bc=bc)
     c = A.Context(cfg)
     c.set_hierarchy(patches)
     return c
@@ -49,17 +49,52 @@ def hierarchies():
     return out
 
 
-HIERS = hierarchies()
+def boundary_hierarchies():
+    """Hierarchies whose fine patches touch non-periodic domain sides; bc is
+    (x-low, x-high, y-low, y-high, z-low, z-high) with 0 periodic, 1 outflow,
+    2 inflow."""
+    edge2 = inputs.tile(0, (0, 0, 0), (32, 32, 1), 8, 2) + [
+        (1, (0, 8, 0), (16, 40, 1)), (1, (48, 0, 0), (64, 24, 1)), (2, (0, 24, 0), (16, 56, 1))]
+    corner3 = inputs.tile(0, (0, 0, 0), (16, 16, 16), 8, 3) + [
+        (1, (0, 0, 0), (16, 16, 16)), (1, (16, 0, 16), (32, 8, 32)), (1, (24, 24, 0), (32, 32, 8))]
+    out = [
+        ("edge2_inflow_outflow", 2, (32, 32, 1), edge2, (2, 1, 0, 0, 0, 0)),
+        ("edge2_all_outflow", 2, (32, 32, 1), edge2, (1, 1, 1, 1, 0, 0)),
+        ("edge2_y_inflow", 2, (32, 32, 1), edge2, (1, 2, 2, 1, 0, 0)),
+        ("corner3_mixed", 3, (16, 16, 16), corner3, (2, 1, 1, 1, 0, 0)),
+        ("corner3_all", 3, (16, 16, 16), corner3, (1, 2, 2, 1, 1, 2)),
+    ]
+    for seed in range(3):
+        out.append(("rand2d_bc_%d" % seed, 2, (32, 32, 1), inputs.random_hierarchy(2, 20 + seed, base=32, nlev=3),
+                    (2, 1, 1, 1, 0, 0)))
+    out.append(("rand3d_bc", 3, (16, 16, 16), inputs.random_hierarchy(3, 30, base=16, nlev=2), (2, 1, 0, 0, 1, 1)))
+    return out
 
 
-@pytest.mark.parametrize("name,dim,base,patches", HIERS, ids=[h[0] for h in HIERS])
-def test_maps_bit_exact_vs_oracle(name, dim, base, patches):
-    c = ctx_for(dim, base, patches)
+HIERS = [h + (None,) for h in hierarchies()] + boundary_hierarchies()
+
+
+@pytest.mark.parametrize("name,dim,base,patches,bc", HIERS, ids=[h[0] for h in HIERS])
+def test_maps_bit_exact_vs_oracle(name, dim, base, patches, bc):
+    c = ctx_for(dim, base, patches, bc=bc)
     for which in A.MAPS:
         got = c.export_map(which)
-        exp = build_map(dim, base, patches, which)
+        exp = build_map(dim, base, patches, which, bc=bc)
         assert got.shape == exp.shape, (which, got.shape, exp.shape)
         assert np.array_equal(got, exp), which
+    if bc is not None:
+        g = c.export_map("ghost_cells")
+        assert (g[:, 2] >= 2).any()
+        assert ((g[:, 2] == 3).any()) == (2 in bc[:2 * dim])
+
+
+def test_boundary_config_errors():
+    base = (32, 32, 1)
+    lvl0 = inputs.tile(0, (0, 0, 0), base, 16, 2)
+    for bad in [(0, 1, 0, 0, 0, 0), (3, 1, 0, 0, 0, 0), (-1, -1, 0, 0, 0, 0)]:
+        with pytest.raises(A.AmrmhdError) as e:
+            ctx_for(2, base, lvl0, bc=bad)
+        assert e.value.status == A.EINVAL
 
 
 def test_error_codes():
