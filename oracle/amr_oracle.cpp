@@ -36,6 +36,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ad.hpp"
 #include "mhd_core.hpp"
 
 namespace oracle {
@@ -46,28 +47,31 @@ struct Patch { int level, lo[3], hi[3]; };
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW = 2 };
 
-struct Level {
+// Value type R: double for the forward oracle; the differentiation types of
+// oracle/adjoint.cpp (a reverse-mode tape entry, a forward-mode tangent) for the
+// adjoint pins.
+template <class R> struct LevelT {
   int N[3] = {1, 1, 1};  // cells per dimension
   int M[3] = {0, 0, 0};  // margin (4 in a non-periodic dimension)
   int X[3] = {1, 1, 1};  // storage extent: N (periodic) or N + 2M + 1
   bool per[3] = {true, true, true};
   double dx[3] = {1, 1, 1}, idx[3] = {1, 1, 1};
   size_t ncell = 0;
-  std::vector<double> u[NFIELD];      // cell fields and face fields, index (k*Ny + j)*Nx + i
-  std::vector<double> start[NFIELD];  // state at the start of the latest sub-step
+  std::vector<R> u[NFIELD];      // cell fields and face fields, index (k*Ny + j)*Nx + i
+  std::vector<R> start[NFIELD];  // state at the start of the latest sub-step
   std::vector<int8_t> dist;           // Chebyshev distance to the region, -1 if > 4
   std::vector<int8_t> cov;            // cell covered by the next finer level
   // work arrays
-  std::vector<double> W[NFIELD], Wh[NFIELD], S[3][NFIELD], ref[3], F[3][NFIELD], E[3];
+  std::vector<R> W[NFIELD], Wh[NFIELD], S[3][NFIELD], ref[3], F[3][NFIELD], E[3];
   std::vector<int8_t> tmask;          // target distance map used by one advance
   // registers of this level's C/F boundary with its parent (indexed on the parent level)
-  std::vector<double> rflux[3][NFIELD];    // per parent face: fine time-integrated flux (S1 + S2)
-  std::vector<double> rcoarse[3][NFIELD];  // per parent face: coarse time-integrated flux C
-  std::vector<double> remf[3], remfc[3];   // the same for the EMF of parent edges
+  std::vector<R> rflux[3][NFIELD];    // per parent face: fine time-integrated flux (S1 + S2)
+  std::vector<R> rcoarse[3][NFIELD];  // per parent face: coarse time-integrated flux C
+  std::vector<R> remf[3], remfc[3];   // the same for the EMF of parent edges
   std::vector<int8_t> cf_face[3], cf_edge[3];
 };
 
-struct Sim {
+template <class R> struct SimT {
   int dim = 2;
   int base[3] = {1, 1, 1};
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
@@ -75,7 +79,7 @@ struct Sim {
   double eps = 1e-12;
   int nlev = 1;
   std::vector<Patch> patches;
-  std::vector<Level> lev;
+  std::vector<LevelT<R>> lev;
   long long cell_updates = 0;
   int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   double inflow[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -86,43 +90,43 @@ struct Sim {
 
 // ---------------------------------------------------------------- indexing
 static inline int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
-static inline int mapi(const Level& L, int d, int i) { return L.per[d] ? wrapi(i, L.N[d]) : i + L.M[d]; }
-static inline size_t at(const Level& L, int i, int j, int k) {
+template <class LV> static inline int mapi(const LV& L, int d, int i) { return L.per[d] ? wrapi(i, L.N[d]) : i + L.M[d]; }
+template <class LV> static inline size_t at(const LV& L, int i, int j, int k) {
   return ((size_t)mapi(L, 2, k) * L.X[1] + mapi(L, 1, j)) * L.X[0] + mapi(L, 0, i);
 }
 // cell (i,j,k) stored (margin included)?
-static inline bool in_storage(const Level& L, int i, int j, int k) {
+template <class LV> static inline bool in_storage(const LV& L, int i, int j, int k) {
   const int o[3] = {i, j, k};
   for (int d = 0; d < 3; ++d)
     if (!L.per[d] && (o[d] < -L.M[d] || o[d] >= L.N[d] + L.M[d])) return false;
   return true;
 }
-static inline bool in_domain(const Level& L, int i, int j, int k) {
+template <class LV> static inline bool in_domain(const LV& L, int i, int j, int k) {
   const int o[3] = {i, j, k};
   for (int d = 0; d < 3; ++d)
     if (!L.per[d] && (o[d] < 0 || o[d] >= L.N[d])) return false;
   return true;
 }
-static inline size_t atd(const Level& L, int i, int j, int k, int d, int s) {
+template <class LV> static inline size_t atd(const LV& L, int i, int j, int k, int d, int s) {
   int o[3] = {i, j, k};
   o[d] += s;
   return at(L, o[0], o[1], o[2]);
 }
 // cells of the domain
-template <class F> static void for_cells(const Level& L, F f) {
+template <class LV, class F> static void for_cells(const LV& L, F f) {
   for (int k = 0; k < L.N[2]; ++k)
     for (int j = 0; j < L.N[1]; ++j)
       for (int i = 0; i < L.N[0]; ++i) f(i, j, k);
 }
 // cells of the domain and of the margins
-template <class F> static void for_all(const Level& L, F f) {
+template <class LV, class F> static void for_all(const LV& L, F f) {
   for (int k = -L.M[2]; k < L.N[2] + L.M[2]; ++k)
     for (int j = -L.M[1]; j < L.N[1] + L.M[1]; ++j)
       for (int i = -L.M[0]; i < L.N[0] + L.M[0]; ++i) f(i, j, k);
 }
 // positions of the d-faces of the domain (the face at the high end of a
 // non-periodic dimension included; periodic faces wrap)
-template <class F> static void for_face_pos(const Level& L, int d, F f) {
+template <class LV, class F> static void for_face_pos(const LV& L, int d, F f) {
   int hi[3] = {L.N[0], L.N[1], L.N[2]};
   if (!L.per[d]) hi[d] += 1;
   for (int k = 0; k < hi[2]; ++k)
@@ -130,7 +134,7 @@ template <class F> static void for_face_pos(const Level& L, int d, F f) {
       for (int i = 0; i < hi[0]; ++i) f(i, j, k);
 }
 // positions of the c-edges of the domain
-template <class F> static void for_edge_pos(const Level& L, int c, F f) {
+template <class LV, class F> static void for_edge_pos(const LV& L, int c, F f) {
   int hi[3] = {L.N[0], L.N[1], L.N[2]};
   for (int e = 0; e < 3; ++e)
     if (e != c && !L.per[e]) hi[e] += 1;
@@ -141,16 +145,16 @@ template <class F> static void for_edge_pos(const Level& L, int c, F f) {
 
 // Cell-field list: in 3D rho, m, E; in 2D also Bz, which is cell-centred and
 // advanced by its fluxes there.
-static int cell_fields(const Sim& S, int* f) {
+template <class R> static int cell_fields(const SimT<R>& S, int* f) {
   int n = 0;
   f[n++] = RHO; f[n++] = MX; f[n++] = MY; f[n++] = MZ; f[n++] = EN;
   if (S.dim == 2) f[n++] = BZ;
   return n;
 }
-static inline bool is_face_field(const Sim& S, int f) { return f == BX || f == BY || (f == BZ && S.dim == 3); }
+template <class R> static inline bool is_face_field(const SimT<R>& S, int f) { return f == BX || f == BY || (f == BZ && S.dim == 3); }
 
 // Chebyshev dilation of a distance map (0 = seed) up to 4, with periodic wrap.
-static void dilate(const Sim& S, const Level& L, std::vector<int8_t>& d) {
+template <class R> static void dilate(const SimT<R>& S, const LevelT<R>& L, std::vector<int8_t>& d) {
   const int kz = S.dim == 3 ? 1 : 0;
   for (int r = 1; r <= G; ++r) {
     std::vector<int8_t> nd = d;
@@ -170,12 +174,12 @@ static void dilate(const Sim& S, const Level& L, std::vector<int8_t>& d) {
 }
 
 // ---------------------------------------------------------------- setup
-static int validate_and_build(Sim& S) {
+template <class R> static int validate_and_build(SimT<R>& S) {
   // Sec. 2: levels l>0 nested in level l-1 with ratio 2; patches aligned to
   // parent cells; no same-level overlap; level 0 tiles the domain.
-  S.lev.assign(S.nlev, Level());
+  S.lev.assign(S.nlev, LevelT<R>());
   for (int l = 0; l < S.nlev; ++l) {
-    Level& L = S.lev[l];
+    LevelT<R>& L = S.lev[l];
     for (int d = 0; d < 3; ++d) {
       L.N[d] = d < S.dim ? (S.base[d] << l) : 1;
       L.dx[d] = d < S.dim ? (S.hi[d] - S.lo[d]) / L.N[d] : 1.0;
@@ -191,7 +195,7 @@ static int validate_and_build(Sim& S) {
   }
   for (const Patch& p : S.patches) {
     if (p.level < 0 || p.level >= S.nlev) return -1;
-    Level& L = S.lev[p.level];
+    LevelT<R>& L = S.lev[p.level];
     for (int d = 0; d < 3; ++d) {
       int lo = p.lo[d], hi = p.hi[d];
       if (d >= S.dim) { if (lo != 0 || hi != 1) return -1; continue; }
@@ -214,8 +218,8 @@ static int validate_and_build(Sim& S) {
     if (!tiled) return -1;  // level 0 must tile the domain
   }
   for (int l = 1; l < S.nlev; ++l) {
-    Level& F = S.lev[l];
-    Level& C = S.lev[l - 1];
+    LevelT<R>& F = S.lev[l];
+    LevelT<R>& C = S.lev[l - 1];
     // covered coarse cells and proper nesting (R11): every coarse cell within
     // Chebyshev distance 3 of a covered cell lies in the coarse region.
     for_cells(F, [&](int i, int j, int k) {
@@ -235,8 +239,8 @@ static int validate_and_build(Sim& S) {
   for (int l = 0; l < S.nlev; ++l) dilate(S, S.lev[l], S.lev[l].dist);
   // C/F faces and edges of level l (>0) on its parent level.
   for (int l = 1; l < S.nlev; ++l) {
-    Level& F = S.lev[l];
-    Level& C = S.lev[l - 1];
+    LevelT<R>& F = S.lev[l];
+    LevelT<R>& C = S.lev[l - 1];
     for (int d = 0; d < 3; ++d) {
       F.cf_face[d].assign(C.ncell, 0);
       F.cf_edge[d].assign(C.ncell, 0);
@@ -274,7 +278,7 @@ static int validate_and_build(Sim& S) {
   return 0;
 }
 
-static void alloc_work(const Sim& S, Level& L) {
+template <class R> static void alloc_work(const SimT<R>& S, LevelT<R>& L) {
   if (L.W[0].size() == L.ncell) return;
   for (int f = 0; f < NFIELD; ++f) {
     L.W[f].assign(L.ncell, 0.0); L.Wh[f].assign(L.ncell, 0.0);
@@ -285,26 +289,26 @@ static void alloc_work(const Sim& S, Level& L) {
 }
 
 // ---------------------------------------------------------------- advance
-static inline void cell_bc(const Sim& S, const Level& L, int i, int j, int k, double* bc) {
+template <class R> static inline void cell_bc(const SimT<R>& S, const LevelT<R>& L, int i, int j, int k, R* bc) {
   size_t q = at(L, i, j, k);
   bc[0] = 0.5 * (L.u[BX][q] + L.u[BX][atd(L, i, j, k, 0, 1)]);
   bc[1] = 0.5 * (L.u[BY][q] + L.u[BY][atd(L, i, j, k, 1, 1)]);
   bc[2] = S.dim == 3 ? 0.5 * (L.u[BZ][q] + L.u[BZ][atd(L, i, j, k, 2, 1)]) : L.u[BZ][q];
 }
 
-static void prim_at(const Sim& S, const Level& L, int i, int j, int k, double* w) {
+template <class R> static void prim_at(const SimT<R>& S, const LevelT<R>& L, int i, int j, int k, R* w) {
   size_t q = at(L, i, j, k);
-  double u[5] = {L.u[RHO][q], L.u[MX][q], L.u[MY][q], L.u[MZ][q], L.u[EN][q]};
-  double bc[3];
+  R u[5] = {L.u[RHO][q], L.u[MX][q], L.u[MY][q], L.u[MZ][q], L.u[EN][q]};
+  R bc[3];
   cell_bc(S, L, i, j, k, bc);
-  cons_to_prim(u, bc, S.gamma - 1.0, w);
+  cons_to_prim<R>(u, bc, R(S.gamma - 1.0), w);
 }
 
 // One level update with time step dt of the target cell set T = {dist_t <= 0}
 // where dist_t is L.tmask (Chebyshev distance to the target, -1 beyond 4):
 // W on T+2, predictor on T+1, fluxes between T+1 cells, EMFs at edges whose 4
 // cells are in T+1, then cells of T and faces touching T are updated.
-static void advance_masked(Sim& S, Level& L, double dt) {
+template <class R> static void advance_masked(SimT<R>& S, LevelT<R>& L, double dt) {
   alloc_work(S, L);
   const int dim = S.dim;
   const std::vector<int8_t>& tm = L.tmask;
@@ -316,7 +320,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
     if (!in(q, 2)) return;
-    double w[8];
+    R w[8];
     prim_at(S, L, i, j, k, w);
     for (int f = 0; f < 8; ++f) L.W[f][q] = w[f];
   });
@@ -326,7 +330,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
     if (!in(q, 1)) return;
-    double w[8], s[3][8];
+    R w[8], s[3][8];
     for (int f = 0; f < 8; ++f) w[f] = L.W[f][q];
     for (int d = 0; d < dim; ++d) {
       size_t qm = atd(L, i, j, k, d, -1), qp = atd(L, i, j, k, d, 1);
@@ -337,12 +341,12 @@ static void advance_masked(Sim& S, Level& L, double dt) {
         L.S[d][f][q] = s[d][f];
       }
     }
-    double ir = 1.0 / w[0];
-    double wh[8];
+    R ir = R(1.0) / w[0];
+    R wh[8];
     for (int f = 0; f < 8; ++f) wh[f] = w[f];
     for (int d = 0; d < dim; ++d) {
-      double dw[8];
-      prim_rhs(w, s[d], d, gamma, ir, dw);
+      R dw[8];
+      prim_rhs<R>(w, s[d], d, R(gamma), ir, dw);
       for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h[d] * dw[f];
     }
     for (int f = 0; f < 8; ++f) L.Wh[f][q] = wh[f];
@@ -359,16 +363,16 @@ static void advance_masked(Sim& S, Level& L, double dt) {
       m[d] -= 1;
       if (!inc(i, j, k, 1) || !inc(m[0], m[1], m[2], 1)) return;
       size_t qr = at(L, i, j, k), ql = at(L, m[0], m[1], m[2]);
-      double wl[8], wr[8];
+      R wl[8], wr[8];
       for (int f = 0; f < 8; ++f) {
         wl[f] = L.Wh[f][ql] + 0.5 * L.S[d][f][ql];
         wr[f] = L.Wh[f][qr] - 0.5 * L.S[d][f][qr];
       }
-      double bn = 0.5 * (wl[5 + d] + wr[5 + d]);
-      double rl[7] = {wl[0], wl[1 + d], wl[1 + t], wl[1 + u], wl[4], wl[5 + t], wl[5 + u]};
-      double rr[7] = {wr[0], wr[1 + d], wr[1 + t], wr[1 + u], wr[4], wr[5 + t], wr[5 + u]};
-      double fr[7];
-      hlld(rl, rr, bn, gamma, S.eps, fr);
+      R bn = 0.5 * (wl[5 + d] + wr[5 + d]);
+      R rl[7] = {wl[0], wl[1 + d], wl[1 + t], wl[1 + u], wl[4], wl[5 + t], wl[5 + u]};
+      R rr[7] = {wr[0], wr[1 + d], wr[1 + t], wr[1 + u], wr[4], wr[5 + t], wr[5 + u]};
+      R fr[7];
+      hlld<R>(rl, rr, bn, R(gamma), R(S.eps), fr);
       L.F[d][RHO][qr] = fr[0];
       L.F[d][MX + d][qr] = fr[1];
       L.F[d][MX + t][qr] = fr[2];
@@ -396,8 +400,8 @@ static void advance_masked(Sim& S, Level& L, double dt) {
       size_t q10 = at(L, ob[0], ob[1], ob[2]);
       size_t q00 = at(L, o[0], o[1], o[2]);
       // E_c on an a-face is -F_a[B_b]; on a b-face it is +F_b[B_a].
-      double ea_hi = -L.F[a][BX + b][q11], ea_lo = -L.F[a][BX + b][q10];
-      double eb_hi = L.F[b][BX + a][q11], eb_lo = L.F[b][BX + a][q01];
+      R ea_hi = -L.F[a][BX + b][q11], ea_lo = -L.F[a][BX + b][q10];
+      R eb_hi = L.F[b][BX + a][q11], eb_lo = L.F[b][BX + a][q01];
       L.E[c][q11] = gs_edge_emf(ea_lo, ea_hi, eb_lo, eb_hi, L.ref[c][q00], L.ref[c][q10],
                                 L.ref[c][q01], L.ref[c][q11], L.F[a][RHO][q10], L.F[a][RHO][q11],
                                 L.F[b][RHO][q01], L.F[b][RHO][q11]);
@@ -408,7 +412,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
   const int ncf = cell_fields(S, cf);
   double dtd[3];
   for (int d = 0; d < 3; ++d) dtd[d] = dt * L.idx[d];
-  std::vector<double> nu[NFIELD];
+  std::vector<R> nu[NFIELD];
   for (int f = 0; f < NFIELD; ++f) nu[f] = L.u[f];
   for_all(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
@@ -417,7 +421,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
       if (L.dist[q] == 0) S.cell_updates++;
       for (int n = 0; n < ncf; ++n) {
         int f = cf[n];
-        double v = L.u[f][q];
+        R v = L.u[f][q];
         for (int d = 0; d < dim; ++d) v = v - dtd[d] * (L.F[d][f][atd(L, i, j, k, d, 1)] - L.F[d][f][q]);
         nu[f][q] = v;
       }
@@ -427,7 +431,7 @@ static void advance_masked(Sim& S, Level& L, double dt) {
       int m[3] = {i, j, k};
       m[d] -= 1;
       if (!in(q, 0) && !inc(m[0], m[1], m[2], 0)) continue;
-      double v = L.u[BX + d][q];
+      R v = L.u[BX + d][q];
       if (dim == 2) {
         if (d == 0) v = v - dtd[1] * (L.E[2][atd(L, i, j, k, 1, 1)] - L.E[2][q]);
         else        v = v + dtd[0] * (L.E[2][atd(L, i, j, k, 0, 1)] - L.E[2][q]);
@@ -456,14 +460,14 @@ static void advance_masked(Sim& S, Level& L, double dt) {
 // reconstruction (Balsara 2001): mean of the two bracketing fine faces plus
 // (dx_n/8) sum over the transverse t of (d/dn-slope of B_t on the high t-face
 // - the same on the low t-face) / dx_t.
-static double prolong_cell(const Sim& S, const Level& C, int f, int ci, int cj, int ck, int oa, int ob, int oc) {
-  const std::vector<double>& u = C.start[f];
+template <class R> static R prolong_cell(const SimT<R>& S, const LevelT<R>& C, int f, int ci, int cj, int ck, int oa, int ob, int oc) {
+  const std::vector<R>& u = C.start[f];
   size_t q = at(C, ci, cj, ck);
-  double v = u[q];
+  R v = u[q];
   const int off[3] = {oa, ob, oc};
-  double r = u[q];
+  R r = u[q];
   for (int d = 0; d < S.dim; ++d) {
-    double sl = minmod(u[q] - u[atd(C, ci, cj, ck, d, -1)], u[atd(C, ci, cj, ck, d, 1)] - u[q]);
+    R sl = minmod(u[q] - u[atd(C, ci, cj, ck, d, -1)], u[atd(C, ci, cj, ck, d, 1)] - u[q]);
     r = r + sl * (off[d] ? 0.25 : -0.25);
   }
   (void)v;
@@ -472,27 +476,27 @@ static double prolong_cell(const Sim& S, const Level& C, int f, int ci, int cj, 
 
 // Fine value of B_n on the coarse n-face stored at coarse cell (ci,cj,ck),
 // at the fine sub-face with transverse offsets given by fine parities.
-static double prolong_coincident(const Sim& S, const Level& C, int n, int ci, int cj, int ck, const int* par) {
-  const std::vector<double>& b = C.start[BX + n];
+template <class R> static R prolong_coincident(const SimT<R>& S, const LevelT<R>& C, int n, int ci, int cj, int ck, const int* par) {
+  const std::vector<R>& b = C.start[BX + n];
   size_t q = at(C, ci, cj, ck);
-  double v = b[q];
+  R v = b[q];
   for (int d = 0; d < S.dim; ++d) {
     if (d == n) continue;
-    double sl = minmod(b[q] - b[atd(C, ci, cj, ck, d, -1)], b[atd(C, ci, cj, ck, d, 1)] - b[q]);
+    R sl = minmod(b[q] - b[atd(C, ci, cj, ck, d, -1)], b[atd(C, ci, cj, ck, d, 1)] - b[q]);
     v = v + sl * (par[d] ? 0.25 : -0.25);
   }
   return v;
 }
 
 // Transverse slope along direction d of B_t on the coarse t-face stored at (ci,cj,ck).
-static double face_slope(const Level& C, int t, int d, int ci, int cj, int ck) {
-  const std::vector<double>& b = C.start[BX + t];
+template <class R> static R face_slope(const LevelT<R>& C, int t, int d, int ci, int cj, int ck) {
+  const std::vector<R>& b = C.start[BX + t];
   size_t q = at(C, ci, cj, ck);
   return minmod(b[q] - b[atd(C, ci, cj, ck, d, -1)], b[atd(C, ci, cj, ck, d, 1)] - b[q]);
 }
 
 // Fine n-face at fine index (fi,fj,fk) (position fi-1/2 etc. along n).
-static double prolong_face(const Sim& S, const Level& C, const Level& F, int n, int fi, int fj, int fk) {
+template <class R> static R prolong_face(const SimT<R>& S, const LevelT<R>& C, const LevelT<R>& F, int n, int fi, int fj, int fk) {
   int fidx[3] = {fi, fj, fk};
   int cidx[3], par[3];
   for (int d = 0; d < 3; ++d) {
@@ -503,15 +507,15 @@ static double prolong_face(const Sim& S, const Level& C, const Level& F, int n, 
   // interior face of coarse cell cidx: bracketing coincident fine faces
   int hi[3] = {cidx[0], cidx[1], cidx[2]};
   hi[n] += 1;
-  double lo_v = prolong_coincident(S, C, n, cidx[0], cidx[1], cidx[2], par);
-  double hi_v = prolong_coincident(S, C, n, hi[0], hi[1], hi[2], par);
-  double corr = 0.0;
+  R lo_v = prolong_coincident(S, C, n, cidx[0], cidx[1], cidx[2], par);
+  R hi_v = prolong_coincident(S, C, n, hi[0], hi[1], hi[2], par);
+  R corr = 0.0;
   for (int t = 0; t < S.dim; ++t) {
     if (t == n) continue;
     int th[3] = {cidx[0], cidx[1], cidx[2]};
     th[t] += 1;
-    double s_hi = face_slope(C, t, n, th[0], th[1], th[2]);
-    double s_lo = face_slope(C, t, n, cidx[0], cidx[1], cidx[2]);
+    R s_hi = face_slope(C, t, n, th[0], th[1], th[2]);
+    R s_lo = face_slope(C, t, n, cidx[0], cidx[1], cidx[2]);
     corr = corr + (C.dx[n] / C.dx[t]) * (s_hi - s_lo);
   }
   (void)F;
@@ -519,9 +523,9 @@ static double prolong_face(const Sim& S, const Level& C, const Level& F, int n, 
 }
 
 // P: fill the band (1 <= dist <= 4) of level l from level l-1's start state.
-static void prolong_band(Sim& S, int l) {
-  Level& F = S.lev[l];
-  const Level& C = S.lev[l - 1];
+template <class R> static void prolong_band(SimT<R>& S, int l) {
+  LevelT<R>& F = S.lev[l];
+  const LevelT<R>& C = S.lev[l - 1];
   int cf[6];
   const int ncf = cell_fields(S, cf);
   for_cells(F, [&](int i, int j, int k) {
@@ -550,7 +554,7 @@ static void prolong_band(Sim& S, int l) {
 // state; a face whose normal index lies beyond the boundary face copies that
 // boundary face, a face of a margin cell along another dimension copies the
 // face of the nearest domain cell; inflow faces take the inflow field.
-static bool outside_kind(const Sim& S, const Level& L, const int* o, int* clamped) {
+template <class R> static bool outside_kind(const SimT<R>& S, const LevelT<R>& L, const int* o, int* clamped) {
   bool inflow = false;
   for (int d = 0; d < 3; ++d) {
     clamped[d] = o[d];
@@ -561,8 +565,8 @@ static bool outside_kind(const Sim& S, const Level& L, const int* o, int* clampe
   return inflow;
 }
 
-static void fill_bc(Sim& S, int l) {
-  Level& L = S.lev[l];
+template <class R> static void fill_bc(SimT<R>& S, int l) {
+  LevelT<R>& L = S.lev[l];
   bool any = false;
   for (int d = 0; d < S.dim; ++d) any |= !L.per[d];
   if (!any) return;
@@ -574,7 +578,7 @@ static void fill_bc(Sim& S, int l) {
     int c[3];
     const bool inflow = outside_kind(S, L, o, c);
     size_t q = at(L, i, j, k), qs = at(L, c[0], c[1], c[2]);
-    for (int n = 0; n < ncf; ++n) L.u[cf[n]][q] = inflow ? S.inflow[cf[n]] : L.u[cf[n]][qs];
+    for (int n = 0; n < ncf; ++n) L.u[cf[n]][q] = inflow ? R(S.inflow[cf[n]]) : L.u[cf[n]][qs];
   });
   for (int d = 0; d < S.dim; ++d) {
     // d-face positions of the storage: along a non-periodic d one beyond the cells
@@ -602,15 +606,15 @@ static void fill_bc(Sim& S, int l) {
             }
           }
           if (!out) continue;
-          L.u[BX + d][at(L, i, j, k)] = inflow ? S.inflow[BX + d] : L.u[BX + d][at(L, c[0], c[1], c[2])];
+          L.u[BX + d][at(L, i, j, k)] = inflow ? R(S.inflow[BX + d]) : L.u[BX + d][at(L, c[0], c[1], c[2])];
         }
   }
 }
 
 // ---------------------------------------------------------------- registers, reflux, restriction (R9)
-static void record_coarse_registers(Sim& S, int l, double dt) {
-  Level& C = S.lev[l];
-  Level& F = S.lev[l + 1];
+template <class R> static void record_coarse_registers(SimT<R>& S, int l, double dt) {
+  LevelT<R>& C = S.lev[l];
+  LevelT<R>& F = S.lev[l + 1];
   int cf[6];
   const int ncf = cell_fields(S, cf);
   for (int d = 0; d < S.dim; ++d)
@@ -627,7 +631,7 @@ static void record_coarse_registers(Sim& S, int l, double dt) {
 
 // Pairwise sum of 2, 4 or 8 values in the given order: ((v0+v1)+(v2+v3))+...
 // (R9: exact for equal values, so uniform states stay bitwise uniform).
-static double tree_sum(const double* v, int n) {
+template <class V> static V tree_sum(const V* v, int n) {
   if (n == 1) return v[0];
   if (n == 2) return v[0] + v[1];
   if (n == 4) return (v[0] + v[1]) + (v[2] + v[3]);
@@ -637,9 +641,9 @@ static double tree_sum(const double* v, int n) {
 // Fine side of the registers after one fine sub-step of dt: per C/F coarse
 // face R += (dt 2^-(dim-1)) * tree_sum(fine sub-face fluxes in z,y,x order);
 // per C/F coarse edge R += (dt 2^-(dim-2)) * tree_sum(fine sub-edges along it).
-static void add_fine_registers(Sim& S, int l, double dt) {
-  Level& F = S.lev[l];
-  Level& C = S.lev[l - 1];
+template <class R> static void add_fine_registers(SimT<R>& S, int l, double dt) {
+  LevelT<R>& F = S.lev[l];
+  LevelT<R>& C = S.lev[l - 1];
   int cf[6];
   const int ncf = cell_fields(S, cf);
   const double af = dt * (S.dim == 3 ? 0.25 : 0.5);
@@ -659,7 +663,7 @@ static void add_fine_registers(Sim& S, int l, double dt) {
             qf[m++] = at(F, 2 * i + o[0], 2 * j + o[1], S.dim == 3 ? 2 * k + o[2] : 0);
           }
       for (int n = 0; n < ncf; ++n) {
-        double v[4];
+        R v[4];
         for (int s = 0; s < m; ++s) v[s] = F.F[d][cf[n]][qf[s]];
         F.rflux[d][cf[n]][q] += af * tree_sum(v, m);
       }
@@ -670,7 +674,7 @@ static void add_fine_registers(Sim& S, int l, double dt) {
       size_t q = at(C, i, j, k);
       if (!F.cf_edge[c][q]) return;
       int nsub = S.dim == 3 ? 2 : 1;
-      double v[2];
+      R v[2];
       for (int sidx = 0; sidx < nsub; ++sidx) {
         int o[3] = {2 * i, 2 * j, S.dim == 3 ? 2 * k : 0};
         o[c] += sidx;
@@ -681,13 +685,13 @@ static void add_fine_registers(Sim& S, int l, double dt) {
   }
 }
 
-static void restrict_cell(const Sim& S, Level& C, const Level& F, int i, int j, int k, double wc) {
+template <class R> static void restrict_cell(const SimT<R>& S, LevelT<R>& C, const LevelT<R>& F, int i, int j, int k, double wc) {
   int cf[6];
   const int ncf = cell_fields(S, cf);
   const int kz = S.dim == 3 ? 2 : 1;
   size_t q = at(C, i, j, k);
   for (int n = 0; n < ncf; ++n) {
-    double v[8];
+    R v[8];
     int m = 0;
     for (int c = 0; c < kz; ++c)
       for (int b = 0; b < 2; ++b)
@@ -696,9 +700,9 @@ static void restrict_cell(const Sim& S, Level& C, const Level& F, int i, int j, 
   }
 }
 
-static void restrict_face(const Sim& S, Level& C, const Level& F, int d, int i, int j, int k, double wf) {
+template <class R> static void restrict_face(const SimT<R>& S, LevelT<R>& C, const LevelT<R>& F, int d, int i, int j, int k, double wf) {
   const int kz = S.dim == 3 ? 2 : 1;
-  double v[4];
+  R v[4];
   int m = 0;
   for (int c = 0; c < kz; ++c)
     for (int b = 0; b < 2; ++b)
@@ -710,10 +714,10 @@ static void restrict_face(const Sim& S, Level& C, const Level& F, int d, int i, 
   C.u[BX + d][at(C, i, j, k)] = tree_sum(v, m) * wf;
 }
 
-static void reflux_and_restrict(Sim& S, int l) {
+template <class R> static void reflux_and_restrict(SimT<R>& S, int l) {
   // level l is the fine level; corrections go to level l-1
-  Level& F = S.lev[l];
-  Level& C = S.lev[l - 1];
+  LevelT<R>& F = S.lev[l];
+  LevelT<R>& C = S.lev[l - 1];
   int cf[6];
   const int ncf = cell_fields(S, cf);
   // S: cell reflux on uncovered coarse cells, faces in order x-,x+,y-,y+,z-,z+
@@ -739,7 +743,7 @@ static void reflux_and_restrict(Sim& S, int l) {
       m[d] -= 1;
       if (covered(i, j, k) || covered(m[0], m[1], m[2])) return;
       size_t q = at(C, i, j, k);
-      double v = C.u[BX + d][q];
+      R v = C.u[BX + d][q];
       auto add = [&](int c, int si, int sj, int sk, double coef) {
         int e[3] = {i + si, j + sj, k + sk};
         size_t qe = at(C, e[0], e[1], e[2]);
@@ -777,7 +781,7 @@ static void reflux_and_restrict(Sim& S, int l) {
 }
 
 // ---------------------------------------------------------------- CFL (R6)
-static double level_rate(const Sim& S, const Level& L) {
+template <class R> static double level_rate(const SimT<R>& S, const LevelT<R>& L) {
   double m = 0.0;
   for_cells(L, [&](int i, int j, int k) {
     size_t q = at(L, i, j, k);
@@ -798,7 +802,7 @@ static double level_rate(const Sim& S, const Level& L) {
   return m;
 }
 
-static double cfl_dt(const Sim& S) {
+template <class R> static double cfl_dt(const SimT<R>& S) {
   double mmax = 0.0;
   double scale = 1.0;
   for (int l = 0; l < S.nlev; ++l) {
@@ -811,8 +815,8 @@ static double cfl_dt(const Sim& S) {
 }
 
 // ---------------------------------------------------------------- recursion (Sec. 4)
-static void level_substep(Sim& S, int l, int s, double dt) {
-  Level& L = S.lev[l];
+template <class R> static void level_substep(SimT<R>& S, int l, int s, double dt) {
+  LevelT<R>& L = S.lev[l];
   const int w = (l == 0) ? 0 : (s == 1 ? 2 : 0);
   if (l > 0 && s == 1) prolong_band(S, l);  // P
   fill_bc(S, l);
@@ -835,6 +839,8 @@ static void level_substep(Sim& S, int l, int s, double dt) {
 
 // ================================================================ C API
 using namespace oracle;
+using Level = LevelT<double>;
+using Sim = SimT<double>;
 
 extern "C" {
 
@@ -961,6 +967,131 @@ int oc_step_targets(void* h, double dt, const int* ijk, int n) {
   for (int m = 0; m < n; ++m) L.tmask[at(L, ijk[3 * m], ijk[3 * m + 1], ijk[3 * m + 2])] = 0;
   dilate(*s, L, L.tmask);
   advance_masked(*s, L, dt);
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- adjoint pins
+// A copy of the simulation s (configuration, hierarchy, state) with value type
+// R; the domain entries of every level's state (those oc_set_field writes)
+// become the independent variables through make_input.
+template <class R, class MakeInput>
+static SimT<R>* clone_as(const Sim& s, MakeInput make_input) {
+  SimT<R>* a = new SimT<R>();
+  a->dim = s.dim;
+  for (int d = 0; d < 3; ++d) {
+    a->base[d] = s.base[d];
+    a->lo[d] = s.lo[d];
+    a->hi[d] = s.hi[d];
+    a->bc[d][0] = s.bc[d][0];
+    a->bc[d][1] = s.bc[d][1];
+  }
+  a->gamma = s.gamma;
+  a->cfl = s.cfl;
+  a->eps = s.eps;
+  a->nlev = s.nlev;
+  a->patches = s.patches;
+  a->flags = s.flags;
+  for (int f = 0; f < NFIELD; ++f) a->inflow[f] = s.inflow[f];
+  validate_and_build(*a);
+  size_t off = 0;
+  for (int l = 0; l < s.nlev; ++l) {
+    const Level& L = s.lev[l];
+    LevelT<R>& A = a->lev[l];
+    for (int f = 0; f < NFIELD; ++f) {
+      for (size_t q = 0; q < L.ncell; ++q) A.u[f][q] = R(L.u[f][q]);
+      int n[3];
+      field_shape(s, l, f, n);
+      int m[3];
+      for (int d = 0; d < 3; ++d) m[d] = L.per[d] ? L.N[d] : n[d];
+      for (int k = 0; k < m[2]; ++k)
+        for (int j = 0; j < m[1]; ++j)
+          for (int i = 0; i < m[0]; ++i) {
+            const size_t q = at(L, i, j, k);
+            A.u[f][q] = make_input(L.u[f][q], off + ((size_t)k * n[1] + j) * n[0] + i);
+          }
+      off += (size_t)n[0] * n[1] * n[2];
+    }
+  }
+  return a;
+}
+
+// Visits every level-array entry (the oc_get_field layout, levels then fields,
+// periodic face copies included) with its storage value.
+template <class R, class Visit> static void visit_state(const Sim& s, const SimT<R>& a, Visit visit) {
+  size_t off = 0;
+  for (int l = 0; l < s.nlev; ++l) {
+    const LevelT<R>& A = a.lev[l];
+    for (int f = 0; f < NFIELD; ++f) {
+      int n[3];
+      field_shape(s, l, f, n);
+      for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+          for (int i = 0; i < n[0]; ++i) visit(A.u[f][at(A, i, j, k)], off + ((size_t)k * n[1] + j) * n[0] + i);
+      off += (size_t)n[0] * n[1] * n[2];
+    }
+  }
+}
+
+extern "C" {
+
+long long oc_state_size(void* h) {
+  Sim* s = (Sim*)h;
+  long long t = 0;
+  for (int l = 0; l < s->nlev; ++l)
+    for (int f = 0; f < NFIELD; ++f) t += oc_field_size(h, l, f);
+  return t;
+}
+
+// Reverse mode: lam0 = (dU_final/dU0)^T lam_final for nsteps coarse steps of the
+// given dts (dt is a constant of the differentiated map). Both vectors hold
+// every level array in the oc_get_field layout, levels then fields; the entry
+// N of a periodic face array is the entry 0 (seeds at both add, and both
+// receive the same adjoint). The simulation's own state is not changed.
+long long oc_backward(void* h, int nsteps, const double* dts, const double* lam_final, double* lam0) {
+  Sim* s = (Sim*)h;
+  Tape& T = tape();
+  T.clear();
+  std::vector<int32_t> input_node((size_t)oc_state_size(h), -1);
+  SimT<Rev>* a = clone_as<Rev>(*s, [&](double v, size_t pos) {
+    Rev r(v);
+    r.i = T.input();
+    input_node[pos] = r.i;
+    return r;
+  });
+  for (int i = 0; i < nsteps; ++i) level_substep(*a, 0, 1, dts[i]);
+  std::vector<double> adj(T.size(), 0.0);
+  visit_state(*s, *a, [&](const Rev& r, size_t pos) {
+    if (r.i >= 0) adj[r.i] += lam_final[pos];
+  });
+  const long long nodes = (long long)T.size();
+  T.sweep(adj);
+  // every output entry reads the adjoint of the storage input behind it
+  SimT<Rev>* b = clone_as<Rev>(*s, [&](double v, size_t pos) {
+    Rev r(v);
+    r.i = input_node[pos];
+    return r;
+  });
+  visit_state(*s, *b, [&](const Rev& r, size_t pos) { lam0[pos] = r.i >= 0 ? adj[r.i] : 0.0; });
+  delete a;
+  delete b;
+  T.clear();
+  std::vector<int32_t>().swap(T.pa);
+  std::vector<int32_t>().swap(T.pb);
+  std::vector<double>().swap(T.da);
+  std::vector<double>().swap(T.db);
+  return nodes;
+}
+
+// Forward mode: jv = (dU_final/dU0) v0, same layouts (entries N of periodic
+// face arrays are ignored in v0, as in oc_set_field).
+int oc_tangent(void* h, int nsteps, const double* dts, const double* v0, double* jv) {
+  Sim* s = (Sim*)h;
+  SimT<Tan>* a = clone_as<Tan>(*s, [&](double v, size_t pos) { return Tan(v, v0[pos]); });
+  for (int i = 0; i < nsteps; ++i) level_substep(*a, 0, 1, dts[i]);
+  visit_state(*s, *a, [&](const Tan& t, size_t pos) { jv[pos] = t.d; });
+  delete a;
   return 0;
 }
 

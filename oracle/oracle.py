@@ -56,6 +56,12 @@ def lib():
         L.oc_build_map.restype = C.c_int
         L.oc_build_map.argtypes = [C.c_int, _ip, _ip, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
                                    C.POINTER(C.c_longlong)]
+        L.oc_state_size.restype = C.c_longlong
+        L.oc_state_size.argtypes = [C.c_void_p]
+        L.oc_backward.restype = C.c_longlong
+        L.oc_backward.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
+        L.oc_tangent.restype = C.c_int
+        L.oc_tangent.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
         L.oc_build_map2.restype = C.c_int
         L.oc_build_map2.argtypes = [C.c_int, _ip, _ip, _ip, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
                                     C.POINTER(C.c_longlong)]
@@ -143,6 +149,41 @@ class OracleSim:
         c = np.zeros_like(d)
         lib().oc_get_masks(self.h, level, d, c)
         return d.reshape(n[2], n[1], n[0]), c.reshape(n[2], n[1], n[0])
+
+    # ---- adjoint pins: the state as one vector (levels, then fields, each
+    # array in the get_field layout; periodic face copies included)
+    def flatten(self, state):
+        return np.concatenate([np.ascontiguousarray(state[l][f], dtype=np.float64).ravel()
+                               for l in range(self.nlev) for f in range(8)])
+
+    def unflatten(self, vec):
+        out, o = {}, 0
+        for l in range(self.nlev):
+            out[l] = []
+            for f in range(8):
+                shp = self.field_shape(l, f)
+                n = int(np.prod(shp))
+                out[l].append(vec[o:o + n].reshape(shp))
+                o += n
+        return out
+
+    def backward(self, dts, lam_final):
+        """(dU_final/dU0)^T lam_final over len(dts) coarse steps of the given
+        dts, by a reverse sweep of the oracle's own operation tape; the
+        simulation's state is left unchanged. Dicts {level: [8 arrays]}."""
+        dts = np.ascontiguousarray(dts, dtype=np.float64)
+        lam = self.flatten(lam_final)
+        out = np.zeros_like(lam)
+        lib().oc_backward(self.h, len(dts), dts, lam, out)
+        return self.unflatten(out)
+
+    def tangent(self, dts, v0):
+        """(dU_final/dU0) v0 by forward-mode differentiation of the oracle."""
+        dts = np.ascontiguousarray(dts, dtype=np.float64)
+        v = self.flatten(v0)
+        out = np.zeros_like(v)
+        lib().oc_tangent(self.h, len(dts), dts, v, out)
+        return self.unflatten(out)
 
     def step_targets(self, dt, ijk):
         ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
