@@ -193,6 +193,38 @@ amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0);
  * values. Synchronises the stream at the end and reports device errors. */
 amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used);
 
+/* n_coarse coarse steps with the prescribed dt0 sequence dt_seq (host, n_coarse
+ * positive values; level l steps with dt0 2^-l) instead of the CFL dt, with
+ * plain launches: the forward map that amrmhd_backward differentiates.
+ * Synchronises the stream. */
+amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq);
+
+/* Discrete adjoint of n_coarse coarse steps with the dt0 sequence dt_seq (host;
+ * dt is a constant of the map, not differentiated). The paper's level advance
+ * (Sec. 4: prolongation, advance, reflux and restriction of the recursive
+ * level order) is differentiated exactly: the call returns
+ *   dL_dU0 = (dU_final / dU0)^T dL_dUfinal
+ * where U0 is the context's state at the call and U_final the state after the
+ * steps. Both are DEVICE arrays of float64 in the packed state layout of all
+ * 8 fields one after the other (field 0's packed array, then field 1's, ...;
+ * each as amrmhd_set_state_packed: patches in id order, a patch's interior
+ * cells, or its own faces along the field's direction, x fastest). A face
+ * stored by two patches has one entry per copy: dL_dUfinal may split the
+ * derivative of a shared face among its copies in any way, and dL_dU0 gives
+ * each copy its own partial derivative (the derivative with respect to the
+ * face value is their sum).
+ * The forward is run once storing a checkpoint of every level's state every
+ * ckpt_every coarse steps, then each segment is recomputed storing the filled
+ * state of every level sub-step, and swept backwards. Branches (minmod, HLLD
+ * cases, upwinding) take the forward's decisions. Adjoint arithmetic is FP64;
+ * in mixed precision it is evaluated on the mixed-precision trajectory.
+ * The first call (and any call needing more checkpoint or snapshot room) allocates
+ * device memory owned by the context: about state + 70 scratch arrays per patch
+ * in FP64, n_coarse/ckpt_every checkpoints and ckpt_every x (2^nlevels - 1)
+ * level snapshots. On return the context holds U0 again. Synchronises the stream. */
+amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
+                              const double* dL_dUfinal, double* dL_dU0);
+
 /* Integer queries: AMRMHD_Q_* */
 enum {
   AMRMHD_Q_NPATCH = 0, AMRMHD_Q_NLEVEL = 1, AMRMHD_Q_CELLS = 2, AMRMHD_Q_CELL_UPDATES_PER_STEP = 3,

@@ -69,6 +69,8 @@ def lib():
             "amrmhd_reflux_restrict": [vp, i32],
             "amrmhd_cfl_dt": [vp, C.POINTER(dbl)],
             "amrmhd_step": [vp, i32, vp],
+            "amrmhd_step_dt": [vp, i32, vp],
+            "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
             "amrmhd_set_option": [vp, i32, i64],
         }
@@ -252,6 +254,50 @@ class Context:
         buf = np.zeros(max(n, 1), dtype=np.float64) if want_dt else None
         self._check(lib().amrmhd_step(self.h, n, buf.ctypes.data_as(C.c_void_p) if want_dt else None), "step")
         return buf
+
+    def step_dt(self, dts):
+        """Coarse steps with the prescribed dt0 sequence (the map the adjoint differentiates)."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(lib().amrmhd_step_dt(self.h, len(d), d.ctypes.data_as(C.c_void_p)), "step_dt")
+
+    # ---- the full state as one packed vector (8 fields one after the other)
+    def packed_total(self):
+        return sum(self.packed_size(f) for f in range(8))
+
+    def field_offsets(self):
+        o, out = 0, []
+        for f in range(8):
+            out.append(o)
+            o += self.packed_size(f)
+        return out
+
+    def load_packed_all(self, vec):
+        """vec: a float64 CUDA tensor (or numpy array) holding all 8 packed fields."""
+        offs = self.field_offsets()
+        for f in range(8):
+            n = self.packed_size(f)
+            if hasattr(vec, "data_ptr"):
+                self._check(lib().amrmhd_set_state_packed(self.h, f, C.c_void_p(vec.data_ptr() + 8 * offs[f]), 1),
+                            "set_state_packed")
+            else:
+                self.set_field_packed(f, vec[offs[f]:offs[f] + n])
+
+    def read_packed_all(self, out):
+        """Fills out (a float64 CUDA tensor of packed_total() entries)."""
+        offs = self.field_offsets()
+        for f in range(8):
+            self._check(lib().amrmhd_get_state_packed(self.h, f, C.c_void_p(out.data_ptr() + 8 * offs[f]), 1),
+                        "get_state_packed")
+        return out
+
+    def backward(self, dts, g_final, g0, ckpt_every=20):
+        """dL/dU0 = (dU_final/dU0)^T dL/dU_final over len(dts) coarse steps with
+        the dt0 sequence dts, starting from the current state (kept). g_final and
+        g0 are float64 CUDA tensors in the packed_total() layout."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(lib().amrmhd_backward(self.h, len(d), d.ctypes.data_as(C.c_void_p), int(ckpt_every),
+                                          C.c_void_p(g_final.data_ptr()), C.c_void_p(g0.data_ptr())), "backward")
+        return g0
 
     def query(self, what):
         v = C.c_int64(0)

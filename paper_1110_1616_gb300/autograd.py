@@ -1,0 +1,51 @@
+"""torch.autograd integration of the discrete adjoint: the coarse steps of a
+context as a differentiable function of the packed initial state.
+
+    u_final = advance(ctx, u0, dts, ckpt_every)
+
+u0 and u_final are float64 CUDA tensors holding all 8 packed fields (the
+amrmhd_backward layout). The forward runs amrmhd_step_dt with the fixed dt0
+sequence dts (dt is not differentiated); the backward reloads u0 and calls
+amrmhd_backward, which recomputes the forward from checkpoints every ckpt_every
+coarse steps. Every step of both passes runs in the library's CUDA kernels.
+"""
+import torch
+
+from . import amrmhd as A
+
+
+class AdvanceFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, u0, ctx, dts, ckpt_every):
+        if not u0.is_cuda or u0.dtype != torch.float64:
+            raise TypeError("u0 must be a float64 CUDA tensor")
+        u0 = u0.contiguous()
+        out = torch.empty_like(u0)
+        # the library runs on its own stream: order it after torch's work and back
+        torch.cuda.synchronize()
+        ctx.load_packed_all(u0)
+        ctx.step_dt(dts)
+        ctx.read_packed_all(out)
+        torch.cuda.synchronize()
+        fctx.save_for_backward(u0)
+        fctx.amr = ctx
+        fctx.dts = list(dts)
+        fctx.ckpt = int(ckpt_every)
+        return out
+
+    @staticmethod
+    def backward(fctx, g):
+        (u0,) = fctx.saved_tensors
+        ctx = fctx.amr
+        g = g.contiguous().to(torch.float64)
+        g0 = torch.empty_like(u0)
+        torch.cuda.synchronize()
+        ctx.load_packed_all(u0)
+        ctx.backward(fctx.dts, g, g0, fctx.ckpt)
+        torch.cuda.synchronize()
+        return g0, None, None, None
+
+
+def advance(ctx: "A.Context", u0: torch.Tensor, dts, ckpt_every: int = 20) -> torch.Tensor:
+    """Differentiable len(dts) coarse steps of ctx from the packed state u0."""
+    return AdvanceFunction.apply(u0, ctx, dts, ckpt_every)

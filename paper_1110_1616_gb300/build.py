@@ -16,8 +16,11 @@ UNITS = [
     ("kernels_fast.cu", ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]),
     ("kernels_strict.cu", ["--fmad=false"]),
     ("noalloc.cu", []),
+    # no FMA contraction: the adjoint re-evaluates the forward's formulas (with
+    # dual numbers) and must take the same branches as the strict FP64 forward
+    ("adjoint.cu", ["--fmad=false"]),
 ]
-HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "mhd_device.cuh"]
+HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp"]
 
 
 def _sources():

@@ -8,79 +8,14 @@
 #include <string>
 #include <vector>
 
-#include "../../include/amrmhd.h"
-#include "hierarchy.hpp"
-#include "kernels.hpp"
+#include "ctx.hpp"
 
 using amrk::DPatch;
 using amrk::LevelArgs;
 using amrk::RowArgs;
+using namespace amrapi;
 
-namespace {
-
-struct DevList {  // a device int list with its row count
-  int* p = nullptr;
-  int64_t n = 0;
-};
-
-struct LevelDev {
-  int* ids = nullptr;  // patch ids of the level (device)
-  int npatch = 0;
-  int maxn[3] = {1, 1, 1};
-  DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
-  DevList bc_cells, bc_faces;                               // physical boundaries (kinds 2, 3)
-  DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
-  int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
-};
-
-}  // namespace
-
-struct amrmhd_ctx {
-  amrmhd_config cfg;
-  cudaStream_t stream = nullptr;
-  cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
-  std::string err;
-  amrmhd::Hierarchy H;
-  bool have_h = false, bound = false;
-  int variant = amrk::V_FP64;
-  const amrk::Ops* ops = nullptr;
-  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1;
-  // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
-  // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
-  bool fused() const {
-    return cfg.dim == 3 && (opt_advance == 3 || (opt_advance == 0 && cfg.precision == AMRMHD_MIXED));
-  }
-  // arena layout (bytes)
-  std::vector<long long> off, fs, soff;
-  long long state_elems = 0, scr_elems = 0;
-  size_t o_state[2] = {0, 0}, o_scr = 0, o_creg = 0, o_freg = 0, o_ecreg = 0, o_efreg = 0, o_stage = 0;
-  size_t arena_bytes = 0;
-  char* arena = nullptr;
-  int64_t ncf = 0, nce = 0, stage_elems = 0;
-  // packed I/O offsets: kind 0 cells, 1..3 faces along x,y,z
-  std::vector<long long> poff[4];
-  long long ptotal[4] = {0, 0, 0, 0};
-  // library-owned device memory
-  std::vector<void*> dev_allocs;
-  DPatch* dP = nullptr;
-  int* d_iota = nullptr;
-  long long* d_poff[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* d_scal = nullptr;              // [0] CFL dt0, [1 + l] dt given to advance_level(l)
-  unsigned long long* d_slots = nullptr;  // per-level CFL maxima + step counter
-  unsigned int* d_err = nullptr;
-  double* d_hist = nullptr;
-  int64_t hist_cap = 0;
-  std::vector<LevelDev> lev;
-  std::vector<int> cur, start;
-  int maxn_all[3] = {1, 1, 1};
-  // graphs, one per parity of level 0's buffer
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  std::vector<int> g_cur_after[2], g_start_after[2];
-  int g_launches[2] = {0, 0};
-  long long launches = 0;
-};
-
-namespace {
+namespace amrapi {
 
 amrmhd_status fail(amrmhd_ctx* c, amrmhd_status s, const std::string& m) {
   if (c) c->err = m;
@@ -99,6 +34,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int64_t kHistCap = 4096;
 
 void free_device(amrmhd_ctx* ctx) {
+  adj_free(ctx);
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
   for (void* p : ctx->dev_allocs) cudaFree(p);
@@ -313,6 +249,7 @@ void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
 // the recursive order 0,1,2,2,1,2,2 of Sec. 4 with P, A, S, R
 void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl) {
   op_fill(ctx, l, s, nl);
+  if (ctx->after_fill) ctx->after_fill(ctx, l, s);
   op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, nl);
   if (l + 1 < ctx->H.nlev) {
     op_level_step(ctx, l + 1, 1, nl);
@@ -348,7 +285,7 @@ const std::vector<int32_t>* map_vec(amrmhd_ctx* ctx, int which, int* width) {
   }
 }
 
-}  // namespace
+}  // namespace amrapi
 
 extern "C" {
 
@@ -752,6 +689,12 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
     for (int it = 0; it < chunk; ++it) {
       if (ctx->opt_graph) {
         const int par = ctx->cur[0];
+        // a graph bakes in every level's buffer choice: recapture when direct
+        // level calls have changed the finer levels' buffers since the capture
+        if (ctx->gexec[par] && ctx->g_cur_before[par] != ctx->cur) {
+          cudaGraphExecDestroy(ctx->gexec[par]);
+          ctx->gexec[par] = nullptr;
+        }
         if (!ctx->gexec[par]) {
           std::vector<int> c0 = ctx->cur, s0 = ctx->start;
           cudaGraph_t g = nullptr;
@@ -763,6 +706,7 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
           ce = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
           cudaGraphDestroy(g);
           if (ce != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+          ctx->g_cur_before[par] = c0;
           ctx->g_cur_after[par] = ctx->cur;
           ctx->g_start_after[par] = ctx->start;
           ctx->g_launches[par] = nl;

@@ -1,0 +1,99 @@
+// Internal view of the library context, shared by the translation units of
+// the C ABI (api.cu: forward path; adjoint.cu: discrete adjoint).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amrmhd.h"
+#include "hierarchy.hpp"
+#include "kernels.hpp"
+
+namespace amrapi {
+
+struct DevList {  // a device int list with its row count
+  int* p = nullptr;
+  int64_t n = 0;
+};
+
+struct LevelDev {
+  int* ids = nullptr;  // patch ids of the level (device)
+  int npatch = 0;
+  int maxn[3] = {1, 1, 1};
+  DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
+  DevList bc_cells, bc_faces;                               // physical boundaries (kinds 2, 3)
+  DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
+  int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
+};
+
+struct AdjWork;  // discrete-adjoint workspace (adjoint.cu)
+
+}  // namespace amrapi
+
+struct amrmhd_ctx {
+  amrmhd_config cfg;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
+  std::string err;
+  amrmhd::Hierarchy H;
+  bool have_h = false, bound = false;
+  int variant = amrk::V_FP64;
+  const amrk::Ops* ops = nullptr;
+  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1;
+  // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
+  // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
+  bool fused() const {
+    return cfg.dim == 3 && (opt_advance == 3 || (opt_advance == 0 && cfg.precision == AMRMHD_MIXED));
+  }
+  // arena layout (bytes)
+  std::vector<long long> off, fs, soff;
+  long long state_elems = 0, scr_elems = 0;
+  size_t o_state[2] = {0, 0}, o_scr = 0, o_creg = 0, o_freg = 0, o_ecreg = 0, o_efreg = 0, o_stage = 0;
+  size_t arena_bytes = 0;
+  char* arena = nullptr;
+  int64_t ncf = 0, nce = 0, stage_elems = 0;
+  // packed I/O offsets: kind 0 cells, 1..3 faces along x,y,z
+  std::vector<long long> poff[4];
+  long long ptotal[4] = {0, 0, 0, 0};
+  // library-owned device memory
+  std::vector<void*> dev_allocs;
+  amrk::DPatch* dP = nullptr;
+  int* d_iota = nullptr;
+  long long* d_poff[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* d_scal = nullptr;              // [0] CFL dt0, [1 + l] dt given to advance_level(l)
+  unsigned long long* d_slots = nullptr;  // per-level CFL maxima + step counter
+  unsigned int* d_err = nullptr;
+  double* d_hist = nullptr;
+  int64_t hist_cap = 0;
+  std::vector<amrapi::LevelDev> lev;
+  std::vector<int> cur, start;
+  int maxn_all[3] = {1, 1, 1};
+  // graphs, one per parity of level 0's buffer
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<int> g_cur_before[2], g_cur_after[2], g_start_after[2];
+  int g_launches[2] = {0, 0};
+  long long launches = 0;
+  // called after every ghost fill of op_level_step (level, sub-step): the
+  // adjoint records the filled states there
+  void (*after_fill)(amrmhd_ctx*, int, int) = nullptr;
+  amrapi::AdjWork* adj = nullptr;
+};
+
+namespace amrapi {
+
+amrmhd_status fail(amrmhd_ctx* c, amrmhd_status s, const std::string& m);
+size_t align256(size_t x);
+void* state_buf(amrmhd_ctx* ctx, int b);
+amrk::LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int w);
+amrk::RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level);
+void offset_regs(amrmhd_ctx* ctx, amrk::RowArgs& a, int l);
+void level_idx(amrmhd_ctx* ctx, int l, double* idx);
+void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl);
+void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, int* nl);
+void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl);
+void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl);
+amrmhd_status check_bound(amrmhd_ctx* ctx);
+void adj_free(amrmhd_ctx* ctx);  // adjoint.cu
+
+}  // namespace amrapi
