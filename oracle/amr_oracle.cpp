@@ -85,7 +85,8 @@ template <class R> struct SimT {
   double inflow[NFIELD] = {0, 0, 0, 0, 0, 0, 0, 0};
   int flags = 0;  // test-only switches: bit 0 skips the cell reflux (a planted
                   // mistake); bit 1 replaces minmod by the unlimited centred slope;
-                  // bit 2 plants an off-by-one in the high-side boundary faces
+                  // bit 2 plants an off-by-one in the high-side boundary faces;
+                  // bit 3 skips the divergence-free closure of the regrid
 };
 
 // ---------------------------------------------------------------- indexing
@@ -835,12 +836,267 @@ template <class R> static void level_substep(SimT<R>& S, int l, int s, double dt
   }
 }
 
+// ---------------------------------------------------------------- regrid (reading R18)
+// Every level above 0 is rebuilt from the flags of the level below, coarse to
+// fine: flag, buffer by 2 cells, mark the aligned blocks of 4 x 4 (x 4) level-l
+// cells holding a buffered flag, keep the blocks whose 3-cell surroundings lie
+// in the level-l region (proper nesting), merge them greedily in z,y,x order
+// into boxes of at most 4 blocks per side, refine the boxes by 2. New fine data
+// are copied from the old fine level where it covered the parent cell, else
+// prolonged; fine faces on a coarse face next to copied data are copied, and the
+// interior faces of a prolonged coarse cell then get the smallest correction
+// that makes every child divergence-free.
+using Level = LevelT<double>;
+using Sim = SimT<double>;
+
+static const int RG_B = 4;     // block edge in parent cells
+static const int RG_MAXB = 4;  // blocks per box side at most
+
+static bool rg_old(const Sim& S, int l, int ci, int cj, int ck) {
+  // coarse cell (ci,cj,ck) of level l covered by the old level l+1
+  if (S.nlev <= l + 1) return false;
+  const Level& F = S.lev[l + 1];
+  if (!in_domain(S.lev[l], ci, cj, ck)) return false;
+  return F.dist[at(F, 2 * ci, 2 * cj, S.dim == 3 ? 2 * ck : 0)] == 0;
+}
+
+// least-norm correction of the interior faces of a coarse cell so that every
+// child has zero discrete divergence; faces ordered d, then transverse children
+// in z,y,x order; r: child divergences (children in z,y,x order)
+static void rg_closure(int dim, const double* idx, const double* r, double* delta) {
+  const int nc = dim == 3 ? 8 : 4;
+  const int nt = dim == 3 ? 4 : 2;
+  const int nf = dim * nt;
+  double M[8][12] = {};
+  int f = 0;
+  for (int d = 0; d < dim; ++d)
+    for (int t = 0; t < nt; ++t, ++f) {
+      // transverse child offsets of this face
+      int o[3] = {0, 0, 0}, b = 0;
+      for (int e = 0; e < dim; ++e) {
+        if (e == d) continue;
+        o[e] = (t >> b) & 1;
+        ++b;
+      }
+      int lo[3] = {o[0], o[1], o[2]}, hi[3] = {o[0], o[1], o[2]};
+      lo[d] = 0;
+      hi[d] = 1;
+      const int clo = lo[0] + 2 * lo[1] + 4 * lo[2], chi = hi[0] + 2 * hi[1] + 4 * hi[2];
+      M[clo][f] += idx[d];   // the face is the high face of the low child
+      M[chi][f] -= idx[d];   // and the low face of the high child
+    }
+  // (M M^T + 1 1^T) y = -r, delta = M^T y
+  double A[8][9];
+  for (int i = 0; i < nc; ++i) {
+    for (int j = 0; j < nc; ++j) {
+      double s = 1.0;
+      for (int k = 0; k < nf; ++k) s += M[i][k] * M[j][k];
+      A[i][j] = s;
+    }
+    A[i][nc] = -r[i];
+  }
+  for (int c = 0; c < nc; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < nc; ++i)
+      if (std::fabs(A[i][c]) > std::fabs(A[piv][c])) piv = i;
+    for (int j = 0; j <= nc; ++j) std::swap(A[c][j], A[piv][j]);
+    for (int i = 0; i < nc; ++i) {
+      if (i == c) continue;
+      const double m = A[i][c] / A[c][c];
+      for (int j = c; j <= nc; ++j) A[i][j] -= m * A[c][j];
+    }
+  }
+  double y[8];
+  for (int i = 0; i < nc; ++i) y[i] = A[i][nc] / A[i][i];
+  for (int k = 0; k < nf; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < nc; ++i) s += M[i][k] * y[i];
+    delta[k] = s;
+  }
+}
+
+// new level l+1 boxes (fine coordinates) from the flags of level l of N
+static std::vector<Patch> rg_boxes(const Sim& N, int l, double theta) {
+  const Level& L = N.lev[l];
+  const int dim = N.dim;
+  std::vector<int8_t> fl(L.ncell, -1);  // 0 = flagged (seed of the dilation)
+  for_cells(L, [&](int i, int j, int k) {
+    const size_t q = at(L, i, j, k);
+    if (L.dist[q] != 0) return;
+    const double r = L.u[RHO][q];
+    double m = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double g = std::fabs(L.u[RHO][atd(L, i, j, k, d, 1)] - L.u[RHO][atd(L, i, j, k, d, -1)]) / (2.0 * r);
+      if (g > m) m = g;
+    }
+    if (m > theta) fl[q] = 0;
+  });
+  // buffer of 2 cells (Chebyshev), inside the domain and the level region
+  const int kz = dim == 3 ? 1 : 0;
+  std::vector<char> buf(L.ncell, 0);
+  for_cells(L, [&](int i, int j, int k) {
+    if (fl[at(L, i, j, k)] != 0) return;
+    for (int c = -2 * kz; c <= 2 * kz; ++c)
+      for (int b = -2; b <= 2; ++b)
+        for (int a = -2; a <= 2; ++a) {
+          if (!in_domain(L, i + a, j + b, k + c)) continue;
+          const size_t q = at(L, i + a, j + b, k + c);
+          if (L.dist[q] == 0) buf[q] = 1;
+        }
+  });
+  int nb[3];
+  for (int d = 0; d < 3; ++d) nb[d] = d < dim ? L.N[d] / RG_B : 1;
+  const size_t nblk = (size_t)nb[0] * nb[1] * nb[2];
+  std::vector<char> ok(nblk, 0);
+  auto bidx = [&](int a, int b, int c) { return ((size_t)c * nb[1] + b) * nb[0] + a; };
+  for (int bk = 0; bk < nb[2]; ++bk)
+    for (int bj = 0; bj < nb[1]; ++bj)
+      for (int bi = 0; bi < nb[0]; ++bi) {
+        const int lo[3] = {bi * RG_B, bj * RG_B, dim == 3 ? bk * RG_B : 0};
+        const int hi[3] = {lo[0] + RG_B, lo[1] + RG_B, dim == 3 ? lo[2] + RG_B : 1};
+        bool want = false;
+        for (int k = lo[2]; k < hi[2]; ++k)
+          for (int j = lo[1]; j < hi[1]; ++j)
+            for (int i = lo[0]; i < hi[0]; ++i) want |= buf[at(L, i, j, k)] != 0;
+        if (!want) continue;
+        bool allowed = true;
+        const int g = 3;
+        for (int k = lo[2] - g * kz; k < hi[2] + g * kz && allowed; ++k)
+          for (int j = lo[1] - g; j < hi[1] + g && allowed; ++j)
+            for (int i = lo[0] - g; i < hi[0] + g && allowed; ++i) {
+              if (!in_domain(L, i, j, k)) continue;
+              if (L.dist[at(L, i, j, k)] != 0) allowed = false;
+            }
+        if (allowed) ok[bidx(bi, bj, bk)] = 1;
+      }
+  std::vector<Patch> out;
+  for (int bk = 0; bk < nb[2]; ++bk)
+    for (int bj = 0; bj < nb[1]; ++bj)
+      for (int bi = 0; bi < nb[0]; ++bi) {
+        if (!ok[bidx(bi, bj, bk)]) continue;
+        int nx = 1, ny = 1, nz = 1;
+        while (nx < RG_MAXB && bi + nx < nb[0] && ok[bidx(bi + nx, bj, bk)]) ++nx;
+        auto row_ok = [&](int b, int c) {
+          for (int t = 0; t < nx; ++t)
+            if (!ok[bidx(bi + t, b, c)]) return false;
+          return true;
+        };
+        while (ny < RG_MAXB && bj + ny < nb[1] && row_ok(bj + ny, bk)) ++ny;
+        if (dim == 3) {
+          auto slab_ok = [&](int c) {
+            for (int u = 0; u < ny; ++u)
+              if (!row_ok(bj + u, c)) return false;
+            return true;
+          };
+          while (nz < RG_MAXB && bk + nz < nb[2] && slab_ok(bk + nz)) ++nz;
+        }
+        for (int c = 0; c < nz; ++c)
+          for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) ok[bidx(bi + a, bj + b, bk + c)] = 0;
+        Patch p;
+        p.level = l + 1;
+        p.lo[0] = 2 * RG_B * bi; p.hi[0] = 2 * RG_B * (bi + nx);
+        p.lo[1] = 2 * RG_B * bj; p.hi[1] = 2 * RG_B * (bj + ny);
+        p.lo[2] = dim == 3 ? 2 * RG_B * bk : 0;
+        p.hi[2] = dim == 3 ? 2 * RG_B * (bk + nz) : 1;
+        out.push_back(p);
+      }
+  return out;
+}
+
+// band fill of level l of N (prolongation from l-1 and boundaries), then start = u
+static void rg_fill(Sim& N, int l) {
+  if (l > 0) {
+    for (int f = 0; f < NFIELD; ++f) N.lev[l - 1].start[f] = N.lev[l - 1].u[f];
+    prolong_band(N, l);
+  }
+  fill_bc(N, l);
+  for (int f = 0; f < NFIELD; ++f) N.lev[l].start[f] = N.lev[l].u[f];
+}
+
+// level l+1 of N from the old simulation S and level l of N
+static void rg_transfer(const Sim& S, Sim& N, int l) {
+  const int dim = N.dim;
+  const Level& C = N.lev[l];
+  Level& F = N.lev[l + 1];
+  const Level* O = S.nlev > l + 1 ? &S.lev[l + 1] : nullptr;
+  int cf[6];
+  const int ncf = cell_fields(N, cf);
+  for_cells(F, [&](int i, int j, int k) {
+    const size_t q = at(F, i, j, k);
+    if (F.dist[q] != 0) return;
+    if (rg_old(S, l, i >> 1, j >> 1, k >> 1)) {
+      for (int n = 0; n < ncf; ++n) F.u[cf[n]][q] = O->u[cf[n]][at(*O, i, j, k)];
+    } else {
+      for (int n = 0; n < ncf; ++n)
+        F.u[cf[n]][q] = prolong_cell(N, C, cf[n], i >> 1, j >> 1, dim == 3 ? k >> 1 : 0, i & 1, j & 1,
+                                     dim == 3 ? (k & 1) : 0);
+    }
+  });
+  // faces in the closure of the new region
+  for (int d = 0; d < dim; ++d)
+    for_face_pos(F, d, [&](int i, int j, int k) {
+      int m[3] = {i, j, k};
+      m[d] -= 1;
+      const bool rq = in_storage(F, i, j, k) && F.dist[at(F, i, j, k)] == 0;
+      const bool rm = in_storage(F, m[0], m[1], m[2]) && F.dist[at(F, m[0], m[1], m[2])] == 0;
+      if (!rq && !rm) return;
+      const int pq[3] = {i >> 1, j >> 1, dim == 3 ? k >> 1 : 0};
+      const int pm[3] = {m[0] >> 1, m[1] >> 1, dim == 3 ? m[2] >> 1 : 0};
+      const bool interior = pq[d] == pm[d];
+      const bool copy = interior ? rg_old(S, l, pq[0], pq[1], pq[2])
+                                 : (rg_old(S, l, pq[0], pq[1], pq[2]) || rg_old(S, l, pm[0], pm[1], pm[2]));
+      const size_t q = at(F, i, j, k);
+      if (copy) F.u[BX + d][q] = O->u[BX + d][at(*O, i, j, k)];
+      else F.u[BX + d][q] = prolong_face(N, C, F, d, i, j, k);
+    });
+  // divergence-free closure of prolonged coarse cells touching copied faces
+  // (bit 3 of flags skips it: a planted mistake for the div B control)
+  if (N.flags & 8) return;
+  for_cells(C, [&](int ci, int cj, int ck) {
+    const int f0[3] = {2 * ci, 2 * cj, dim == 3 ? 2 * ck : 0};
+    if (F.dist[at(F, f0[0], f0[1], f0[2])] != 0) return;  // not in the new fine region
+    if (rg_old(S, l, ci, cj, ck)) return;
+    bool touches = false;
+    for (int d = 0; d < dim; ++d)
+      for (int s = -1; s <= 1; s += 2) {
+        int nbc[3] = {ci, cj, ck};
+        nbc[d] += s;
+        touches |= rg_old(S, l, nbc[0], nbc[1], nbc[2]);
+      }
+    if (!touches) return;
+    const int nc = dim == 3 ? 8 : 4;
+    double r[8];
+    for (int c = 0; c < nc; ++c) {
+      const int o[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+      const int x = f0[0] + o[0], y = f0[1] + o[1], z = dim == 3 ? f0[2] + o[2] : 0;
+      double div = 0.0;
+      for (int d = 0; d < dim; ++d)
+        div += (F.u[BX + d][atd(F, x, y, z, d, 1)] - F.u[BX + d][at(F, x, y, z)]) * F.idx[d];
+      r[c] = div;
+    }
+    double delta[12];
+    rg_closure(dim, F.idx, r, delta);
+    const int nt = dim == 3 ? 4 : 2;
+    int fi = 0;
+    for (int d = 0; d < dim; ++d)
+      for (int t = 0; t < nt; ++t, ++fi) {
+        int o[3] = {0, 0, 0}, b = 0;
+        for (int e = 0; e < dim; ++e) {
+          if (e == d) continue;
+          o[e] = (t >> b) & 1;
+          ++b;
+        }
+        o[d] = 1;  // the interior face is the low face of the high child
+        F.u[BX + d][at(F, f0[0] + o[0], f0[1] + o[1], dim == 3 ? f0[2] + o[2] : 0)] += delta[fi];
+      }
+  });
+}
+
 }  // namespace oracle
 
 // ================================================================ C API
 using namespace oracle;
-using Level = LevelT<double>;
-using Sim = SimT<double>;
 
 extern "C" {
 
@@ -938,6 +1194,57 @@ double oc_step(void* h, double dt0) {
 }
 
 long long oc_cell_updates(void* h) { return ((Sim*)h)->cell_updates; }
+
+// Regrid (reading R18) with density-gradient threshold theta: every level
+// above 0 is rebuilt, coarse to fine, up to max_levels levels; the first level
+// left without boxes ends the hierarchy. out: the new patch list (n x 7, as
+// oc_set_patches, levels ascending, level 0 first), *n its length. Returns 0,
+// -4 if cap is too small.
+int oc_regrid(void* h, double theta, int max_levels, int* out, int cap, int* n) {
+  Sim* s = (Sim*)h;
+  Sim* N = new Sim();
+  N->dim = s->dim;
+  for (int d = 0; d < 3; ++d) {
+    N->base[d] = s->base[d]; N->lo[d] = s->lo[d]; N->hi[d] = s->hi[d];
+    N->bc[d][0] = s->bc[d][0]; N->bc[d][1] = s->bc[d][1];
+  }
+  N->gamma = s->gamma; N->cfl = s->cfl; N->eps = s->eps; N->flags = s->flags;
+  for (int f = 0; f < NFIELD; ++f) N->inflow[f] = s->inflow[f];
+  std::vector<Patch> ps;
+  for (const Patch& p : s->patches)
+    if (p.level == 0) ps.push_back(p);
+  N->patches = ps;
+  N->nlev = 1;
+  validate_and_build(*N);
+  for (int f = 0; f < NFIELD; ++f) N->lev[0].u[f] = s->lev[0].u[f];
+  for (int l = 0; l + 1 < max_levels; ++l) {
+    rg_fill(*N, l);
+    std::vector<Patch> nb = rg_boxes(*N, l, theta);
+    if (nb.empty()) break;
+    // the new hierarchy with one more level; earlier levels keep their data
+    Sim* M = new Sim(*N);
+    M->patches.insert(M->patches.end(), nb.begin(), nb.end());
+    M->nlev = l + 2;
+    validate_and_build(*M);
+    for (int q = 0; q <= l; ++q)
+      for (int f = 0; f < NFIELD; ++f) M->lev[q].u[f] = N->lev[q].u[f];
+    rg_fill(*M, l);
+    rg_transfer(*s, *M, l);
+    delete N;
+    N = M;
+  }
+  if ((int)N->patches.size() > cap) { delete N; return -4; }
+  *n = (int)N->patches.size();
+  for (int i = 0; i < *n; ++i) {
+    const Patch& p = N->patches[i];
+    out[7 * i] = p.level;
+    for (int d = 0; d < 3; ++d) { out[7 * i + 1 + d] = p.lo[d]; out[7 * i + 4 + d] = p.hi[d]; }
+  }
+  N->cell_updates = s->cell_updates;
+  *s = *N;
+  delete N;
+  return 0;
+}
 
 // Test-only planted mistakes (controls showing that a pin can fail).
 void oc_set_flags(void* h, int flags) { ((Sim*)h)->flags = flags; }

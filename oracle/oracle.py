@@ -62,6 +62,8 @@ def lib():
         L.oc_backward.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
         L.oc_tangent.restype = C.c_int
         L.oc_tangent.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
+        L.oc_regrid.restype = C.c_int
+        L.oc_regrid.argtypes = [C.c_void_p, C.c_double, C.c_int, _ip, C.c_int, C.POINTER(C.c_int)]
         L.oc_build_map2.restype = C.c_int
         L.oc_build_map2.argtypes = [C.c_int, _ip, _ip, _ip, C.c_int, C.c_int, C.c_void_p, C.c_longlong,
                                     C.POINTER(C.c_longlong)]
@@ -184,6 +186,24 @@ class OracleSim:
         out = np.zeros_like(v)
         lib().oc_tangent(self.h, len(dts), dts, v, out)
         return self.unflatten(out)
+
+    def regrid(self, theta, max_levels=None):
+        """Rebuilds every level above 0 from density-gradient flags (threshold
+        theta), coarse to fine up to max_levels levels (default: the current
+        count), with the data transfer; returns the new patch list
+        [(level, lo, hi)] and updates nlev."""
+        if max_levels is None:
+            max_levels = self.nlev
+        cap = 1 << 20
+        out = np.zeros(7 * cap, dtype=np.int32)
+        n = C.c_int(0)
+        st = lib().oc_regrid(self.h, float(theta), int(max_levels), out, cap, C.byref(n))
+        if st != 0:
+            raise ValueError("oracle regrid failed: %d" % st)
+        rows = out[:7 * n.value].reshape(-1, 7)
+        patches = [(int(r[0]), (int(r[1]), int(r[2]), int(r[3])), (int(r[4]), int(r[5]), int(r[6]))) for r in rows]
+        self.nlev = max(p[0] for p in patches) + 1
+        return patches
 
     def step_targets(self, dt, ijk):
         ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))

@@ -392,6 +392,110 @@ def smooth_bounded_2d(n=32, refine=True, seed=0, mirrored=False, gamma=GAMMA):
                    meta={"seed": seed, "mirrored": mirrored})
 
 
+def clump_centres(dim, n_clumps=8, seed=3, lo=0.15, hi=0.85):
+    """Uniformly placed seeded clump centres (kept away from the periodic seam)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(lo, hi, size=(n_clumps, 3))
+    if dim == 2:
+        c[:, 2] = 0.5
+    return c
+
+
+def clump_cells(x, y, z, dim, centres, radius, rho_clump=100.0, rho_amb=1.0, p=1.0, v=(1.0, 0.0, 0.0),
+                gamma=GAMMA):
+    """Cell-centred primitive fields of dense clumps in pressure equilibrium in
+    a uniform flow: rho = rho_clump inside any clump (cell centre strictly
+    within the radius), rho_amb outside."""
+    inside = np.zeros(x.shape, bool)
+    for c in centres:
+        r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2 + ((z - c[2]) ** 2 if dim == 3 else 0.0)
+        inside |= r2 < radius * radius
+    rho = np.where(inside, rho_clump, rho_amb)
+    return rho, np.full(x.shape, v[0]), np.full(x.shape, v[1]), np.full(x.shape, v[2]), np.full(x.shape, p)
+
+
+def clump_boxes(dim, base, nlev, centres, radius, margin=6, block=8):
+    """A properly nested static hierarchy around the clumps: on the finest
+    level one box per clump covering its radius plus margin cells, aligned to
+    block fine cells; each coarser level holds the coarsened finer boxes grown
+    by margin cells; overlapping boxes are merged into their bounding box; boxes
+    are split into pieces of at most 32 cells per side."""
+    def merge(boxes):
+        boxes = [list(map(list, b)) for b in boxes]
+        changed = True
+        while changed:
+            changed = False
+            for i in range(len(boxes)):
+                for j in range(i + 1, len(boxes)):
+                    a, b = boxes[i], boxes[j]
+                    if all(a[0][d] < b[1][d] and b[0][d] < a[1][d] for d in range(dim)):
+                        boxes[i] = [[min(a[0][d], b[0][d]) for d in range(3)], [max(a[1][d], b[1][d]) for d in range(3)]]
+                        del boxes[j]
+                        changed = True
+                        break
+                if changed:
+                    break
+        return boxes
+
+    def align(lo, hi, n):
+        lo = [max(0, (v // block) * block) for v in lo]
+        hi = [min(n[d], -((-v) // block) * block) for d, v in enumerate(hi)]
+        return lo, hi
+
+    levels = {}
+    for l in range(nlev - 1, 0, -1):
+        n = [base[d] << l if d < dim else 1 for d in range(3)]
+        boxes = []
+        for c in centres:
+            lo = [int(np.floor((c[d] - radius) * n[d])) - margin if d < dim else 0 for d in range(3)]
+            hi = [int(np.ceil((c[d] + radius) * n[d])) + margin if d < dim else 1 for d in range(3)]
+            boxes.append(align(lo, hi, n))
+        if l + 1 in levels:
+            for (lo, hi) in levels[l + 1]:
+                clo = [(lo[d] // 2) - margin if d < dim else 0 for d in range(3)]
+                chi = [(hi[d] + 1) // 2 + margin if d < dim else 1 for d in range(3)]
+                boxes.append(align(clo, chi, n))
+        for b in boxes:
+            if dim == 2:
+                b[0][2], b[1][2] = 0, 1
+        levels[l] = merge(boxes)
+    patches = []
+    for l in range(1, nlev):
+        for (lo, hi) in levels[l]:
+            for k0 in range(lo[2], hi[2], 32 if dim == 3 else 1):
+                for j0 in range(lo[1], hi[1], 32):
+                    for i0 in range(lo[0], hi[0], 32):
+                        patches.append((l, (i0, j0, k0), (min(i0 + 32, hi[0]), min(j0 + 32, hi[1]),
+                                                          min(k0 + 32, hi[2]) if dim == 3 else 1)))
+    return patches
+
+
+def clumps_2d(n=32, nlev=3, n_clumps=4, radius=0.06, seed=3, psize=8, b_pert=0.0, gamma=GAMMA):
+    """2D version of the clump workload (whole-level arrays on every level):
+    dense clumps (contrast 100) in pressure equilibrium advected by a uniform
+    flow v = (1, 0) along a uniform field B = (sqrt 2, 0) (plasma beta 1), plus
+    optionally a divergence-free perturbation of amplitude b_pert from the
+    vector potential b_pert sin(2 pi x) sin(2 pi y) / (2 pi)."""
+    centres = clump_centres(2, n_clumps, seed)
+    base = (n, n, 1)
+    patches = tile(0, (0, 0, 0), base, psize, 2) + clump_boxes(2, base, nlev, centres, radius)
+    b0 = math.sqrt(2.0)
+    state = {}
+    for l in range(nlev):
+        nn = (n << l, n << l, 1)
+        x, y, z = _cell_centres(nn, (0, 0, 0), (1, 1, 1), 2)
+        rho, vx, vy, vz, p = clump_cells(x, y, z, 2, centres, radius)
+        dx = 1.0 / nn[0]
+        Y, X = np.meshgrid(np.arange(nn[1] + 1) * dx, np.arange(nn[0] + 1) * dx, indexing="ij")
+        az = b_pert * np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y) / (2 * math.pi)
+        bx, by = _b_from_az_2d(az, nn, dx, dx)
+        bx = bx + b0
+        bz = np.zeros_like(x)
+        state[l] = _state_2d(nn, rho, vx, vy, vz, p, bx, by, bz, gamma)
+    return Problem("clumps_2d", 2, base, patches, nlev, state, gamma=gamma,
+                   meta={"centres": centres, "radius": radius, "seed": seed})
+
+
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
     """A random properly nested periodic hierarchy: level 0 tiled by patches
     of random widths; finer levels a few random boxes aligned to parent cells,
