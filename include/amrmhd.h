@@ -225,6 +225,41 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
 amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
                               const double* dL_dUfinal, double* dL_dU0);
 
+/* Regrid: rebuilds every level above 0, coarse to fine, up to max_levels
+ * levels (Sec. 2: the grids follow the flagged regions; a new grid takes its
+ * data from the preceding overlapping grid of its level, else from the coarser
+ * level). For each level l < max_levels - 1, in order:
+ *  1. flag the level-l cells with max_d |rho(i+1) - rho(i-1)| / (2 rho) > theta
+ *     (FP64 from the stored values, ghosts filled first);
+ *  2. buffer the flags by 2 cells inside the level-l region;
+ *  3. mark the aligned blocks of 4^dim level-l cells that hold a buffered flag
+ *     and whose surrounding 3 cells lie in the level-l region (proper nesting);
+ *  4. merge the marked blocks greedily in z,y,x order (runs along x, then y,
+ *     then z, at most 4 blocks per side) and refine by 2: new level-(l+1)
+ *     patches of 8..32 cells per side, aligned to 8 fine cells;
+ *  5. fill the new level: cells and faces copied from the old level l+1 where
+ *     it covered the parent cell, else prolonged from level l; where copied and
+ *     prolonged fine faces meet on a coarse face, the interior faces of the
+ *     prolonged coarse cell get the least-norm correction that makes every
+ *     child divergence-free.
+ * The first level without boxes ends the hierarchy. Level 0 is kept. Patch ids
+ * of the result: level 0 as before, then each level's boxes in creation order
+ * (amrmhd_get_patches). After the call the context owns a new arena allocated
+ * with cudaMalloc (a caller's arena is no longer referenced); the adjoint
+ * workspace and captured graphs are released. Base sizes must be divisible by 4.
+ * Synchronises the stream. */
+amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels);
+
+/* Steps 2-4 of amrmhd_regrid alone on the context's hierarchy (host only, no
+ * device work): the level+1 boxes (n x 7 int32: level, lo[3], hi[3]) from the
+ * flagged level cells given as nflags (x, y, z) triples; flags outside the
+ * level's region are ignored. out may be NULL to query *n. */
+amrmhd_status amrmhd_regrid_boxes(amrmhd_ctx* ctx, int32_t level, const int32_t* flags, int64_t nflags,
+                                  int32_t* out, int32_t cap, int32_t* n);
+
+/* The current patch list (ids in order); out may be NULL to query *n. */
+amrmhd_status amrmhd_get_patches(amrmhd_ctx* ctx, amrmhd_patch* out, int32_t cap, int32_t* n);
+
 /* Integer queries: AMRMHD_Q_* */
 enum {
   AMRMHD_Q_NPATCH = 0, AMRMHD_Q_NLEVEL = 1, AMRMHD_Q_CELLS = 2, AMRMHD_Q_CELL_UPDATES_PER_STEP = 3,

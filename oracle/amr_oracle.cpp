@@ -915,22 +915,28 @@ static void rg_closure(int dim, const double* idx, const double* r, double* delt
   }
 }
 
-// new level l+1 boxes (fine coordinates) from the flags of level l of N
-static std::vector<Patch> rg_boxes(const Sim& N, int l, double theta) {
+// flags of level l of N: region cells with max_d |rho(i+1) - rho(i-1)| / (2 rho) > theta
+static std::vector<int8_t> rg_flags(const Sim& N, int l, double theta) {
   const Level& L = N.lev[l];
-  const int dim = N.dim;
-  std::vector<int8_t> fl(L.ncell, -1);  // 0 = flagged (seed of the dilation)
+  std::vector<int8_t> fl(L.ncell, -1);  // 0 = flagged
   for_cells(L, [&](int i, int j, int k) {
     const size_t q = at(L, i, j, k);
     if (L.dist[q] != 0) return;
     const double r = L.u[RHO][q];
     double m = 0.0;
-    for (int d = 0; d < dim; ++d) {
+    for (int d = 0; d < N.dim; ++d) {
       const double g = std::fabs(L.u[RHO][atd(L, i, j, k, d, 1)] - L.u[RHO][atd(L, i, j, k, d, -1)]) / (2.0 * r);
       if (g > m) m = g;
     }
     if (m > theta) fl[q] = 0;
   });
+  return fl;
+}
+
+// new level l+1 boxes (fine coordinates) from the flag map fl of level l of N
+static std::vector<Patch> rg_boxes(const Sim& N, int l, const std::vector<int8_t>& fl) {
+  const Level& L = N.lev[l];
+  const int dim = N.dim;
   // buffer of 2 cells (Chebyshev), inside the domain and the level region
   const int kz = dim == 3 ? 1 : 0;
   std::vector<char> buf(L.ncell, 0);
@@ -1195,6 +1201,28 @@ double oc_step(void* h, double dt0) {
 
 long long oc_cell_updates(void* h) { return ((Sim*)h)->cell_updates; }
 
+// The clustering alone: new level l+1 boxes from the given flagged level-l
+// cells (x, y, z triples; cells outside the level-l region are ignored).
+int oc_regrid_boxes(void* h, int l, const int* flags, long long nflags, int* out, int cap, int* n) {
+  Sim* s = (Sim*)h;
+  const Level& L = s->lev[l];
+  std::vector<int8_t> fl(L.ncell, -1);
+  for (long long f = 0; f < nflags; ++f) {
+    const int* c = flags + 3 * f;
+    if (!in_domain(L, c[0], c[1], c[2])) continue;
+    const size_t q = at(L, c[0], c[1], c[2]);
+    if (L.dist[q] == 0) fl[q] = 0;
+  }
+  std::vector<Patch> b = rg_boxes(*s, l, fl);
+  if ((int)b.size() > cap) return -4;
+  *n = (int)b.size();
+  for (int i = 0; i < *n; ++i) {
+    out[7 * i] = b[i].level;
+    for (int d = 0; d < 3; ++d) { out[7 * i + 1 + d] = b[i].lo[d]; out[7 * i + 4 + d] = b[i].hi[d]; }
+  }
+  return 0;
+}
+
 // Regrid (reading R18) with density-gradient threshold theta: every level
 // above 0 is rebuilt, coarse to fine, up to max_levels levels; the first level
 // left without boxes ends the hierarchy. out: the new patch list (n x 7, as
@@ -1219,7 +1247,7 @@ int oc_regrid(void* h, double theta, int max_levels, int* out, int cap, int* n) 
   for (int f = 0; f < NFIELD; ++f) N->lev[0].u[f] = s->lev[0].u[f];
   for (int l = 0; l + 1 < max_levels; ++l) {
     rg_fill(*N, l);
-    std::vector<Patch> nb = rg_boxes(*N, l, theta);
+    std::vector<Patch> nb = rg_boxes(*N, l, rg_flags(*N, l, theta));
     if (nb.empty()) break;
     // the new hierarchy with one more level; earlier levels keep their data
     Sim* M = new Sim(*N);

@@ -62,6 +62,8 @@ def lib():
         L.oc_backward.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
         L.oc_tangent.restype = C.c_int
         L.oc_tangent.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
+        L.oc_regrid_boxes.restype = C.c_int
+        L.oc_regrid_boxes.argtypes = [C.c_void_p, C.c_int, _ip, C.c_longlong, _ip, C.c_int, C.POINTER(C.c_int)]
         L.oc_regrid.restype = C.c_int
         L.oc_regrid.argtypes = [C.c_void_p, C.c_double, C.c_int, _ip, C.c_int, C.POINTER(C.c_int)]
         L.oc_build_map2.restype = C.c_int
@@ -204,6 +206,17 @@ class OracleSim:
         patches = [(int(r[0]), (int(r[1]), int(r[2]), int(r[3])), (int(r[4]), int(r[5]), int(r[6]))) for r in rows]
         self.nlev = max(p[0] for p in patches) + 1
         return patches
+
+    def regrid_boxes(self, level, flags):
+        """The clustering alone: level+1 boxes from flagged level cells (n x 3)."""
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.int32).reshape(-1, 3))
+        cap = 1 << 16
+        out = np.zeros(7 * cap, dtype=np.int32)
+        n = C.c_int(0)
+        st = lib().oc_regrid_boxes(self.h, level, f.ravel(), len(f), out, cap, C.byref(n))
+        if st != 0:
+            raise ValueError("oracle clustering failed: %d" % st)
+        return out[:7 * n.value].reshape(-1, 7).copy()
 
     def step_targets(self, dt, ijk):
         ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))

@@ -71,6 +71,9 @@ def lib():
             "amrmhd_step": [vp, i32, vp],
             "amrmhd_step_dt": [vp, i32, vp],
             "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
+            "amrmhd_regrid": [vp, dbl, i32],
+            "amrmhd_get_patches": [vp, vp, i32, C.POINTER(i32)],
+            "amrmhd_regrid_boxes": [vp, i32, vp, i64, vp, i32, C.POINTER(i32)],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
             "amrmhd_set_option": [vp, i32, i64],
         }
@@ -254,6 +257,33 @@ class Context:
         buf = np.zeros(max(n, 1), dtype=np.float64) if want_dt else None
         self._check(lib().amrmhd_step(self.h, n, buf.ctypes.data_as(C.c_void_p) if want_dt else None), "step")
         return buf
+
+    def regrid(self, theta, max_levels):
+        """Rebuilds the levels above 0 from density-gradient flags (threshold
+        theta) up to max_levels levels; the context then owns its arena.
+        Returns the new patch list [(level, lo, hi)]."""
+        self._check(lib().amrmhd_regrid(self.h, float(theta), int(max_levels)), "regrid")
+        self.arena = None
+        self.patches = self.get_patches()
+        return self.patches
+
+    def regrid_boxes(self, level, flags):
+        """The clustering alone (host): level+1 boxes (n x 7) from flagged cells (n x 3)."""
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.int32).reshape(-1, 3))
+        n = C.c_int32(0)
+        self._check(lib().amrmhd_regrid_boxes(self.h, level, f.ctypes.data_as(C.c_void_p), len(f), None, 0,
+                                              C.byref(n)), "regrid_boxes")
+        out = np.zeros(7 * max(n.value, 1), dtype=np.int32)
+        self._check(lib().amrmhd_regrid_boxes(self.h, level, f.ctypes.data_as(C.c_void_p), len(f),
+                                              out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)), "regrid_boxes")
+        return out[:7 * n.value].reshape(-1, 7)
+
+    def get_patches(self):
+        n = C.c_int32(0)
+        self._check(lib().amrmhd_get_patches(self.h, None, 0, C.byref(n)), "get_patches")
+        arr = (Patch * max(n.value, 1))()
+        self._check(lib().amrmhd_get_patches(self.h, arr, n.value, C.byref(n)), "get_patches")
+        return [(arr[i].level, tuple(arr[i].lo), tuple(arr[i].hi)) for i in range(n.value)]
 
     def step_dt(self, dts):
         """Coarse steps with the prescribed dt0 sequence (the map the adjoint differentiates)."""

@@ -19,12 +19,15 @@ UNITS = [
     # no FMA contraction: the adjoint re-evaluates the forward's formulas (with
     # dual numbers) and must take the same branches as the strict FP64 forward
     ("adjoint.cu", ["--fmad=false"]),
+    ("regrid_api.cu", []),
 ]
-HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp"]
+HOST_UNITS = ["hierarchy.cpp", "regrid.cpp"]
+HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp",
+           "regrid.hpp"]
 
 
 def _sources():
-    s = [os.path.join(CSRC, u) for u, _ in UNITS] + [os.path.join(CSRC, "hierarchy.cpp")]
+    s = [os.path.join(CSRC, u) for u, _ in UNITS] + [os.path.join(CSRC, u) for u in HOST_UNITS]
     s += [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "amrmhd.h")]
     return s
 
@@ -46,8 +49,9 @@ def build(force=False, verbose=False):
         cmd = [NVCC, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *extra, "-c",
                os.path.join(CSRC, unit), "-o", obj]
         jobs.append((cmd, obj))
-    hobj = os.path.join(OUT, "hierarchy.o")
-    jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-c", os.path.join(CSRC, "hierarchy.cpp"), "-o", hobj], hobj))
+    for unit in HOST_UNITS:
+        hobj = os.path.join(OUT, unit.replace(".cpp", ".o"))
+        jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-c", os.path.join(CSRC, unit), "-o", hobj], hobj))
     with cf.ThreadPoolExecutor(len(jobs)) as ex:
         futs = [ex.submit(subprocess.run, cmd, capture_output=True, text=True) for cmd, _ in jobs]
         for (cmd, _), f in zip(jobs, futs):

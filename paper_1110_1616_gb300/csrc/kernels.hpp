@@ -51,6 +51,11 @@ struct RowArgs {
   double ratio[3][3];  // dx_n/dx_t on the coarse level
   int substep;       // 1 or 2
   double inflow[8];  // conserved inflow state (boundary fill)
+  // regrid transfer: the old hierarchy's patch table and state buffer, and the
+  // closure matrix (12 x 8)
+  const DPatch* P2;
+  const void* obuf;
+  const double* K;
 };
 
 struct CflArgs {
@@ -93,6 +98,12 @@ struct Ops {
                         int* launches);
   void (*reg_fine_rc)(const RowArgs& faces, const RowArgs& edges, const double* idx, double gamma, cudaStream_t,
                       int* launches);
+  // regrid: flagged cells of a level (global indices appended to out), the
+  // transfer of a new fine level and its divergence-free closure
+  void (*flag)(const LevelArgs&, double theta, int* out, unsigned long long* count, long long cap, cudaStream_t);
+  void (*transfer_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*transfer_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*closure)(const RowArgs&, cudaStream_t, int* launches);
 };
 
 const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED

@@ -473,6 +473,162 @@ template <class T, int DIM> __global__ void k_prolong_faces(RowArgs a) {
   ((T*)a.fbuf)[D.off + (BX + n) * D.fs + row[2]] = v;
 }
 
+// ------------------------------------------------------------------ regrid
+// flagged cells of a level: max_d |rho(i+1) - rho(i-1)| / (2 rho) > theta in
+// FP64 from the stored values; global indices appended (order is arbitrary)
+template <class T, int DIM>
+__global__ void __launch_bounds__(TPB) k_flag(LevelArgs a, double theta, int* out, unsigned long long* count,
+                                              long long cap) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  if (!region_cell<DIM>(P, 0, blockIdx.x * TPB + threadIdx.x, i, j, k)) return;
+  const int L = lidx(P, i, j, k);
+  const T* R = (const T*)a.cur + P.off;
+  const double r = (double)R[L];
+  double m = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int sd = stride_of<DIM>(P, d);
+    const double g = fabs((double)R[L + sd] - (double)R[L - sd]) / (2.0 * r);
+    if (g > m) m = g;
+  }
+  if (!(m > theta)) return;
+  const unsigned long long n = atomicAdd(count, 1ULL);
+  if ((long long)n >= cap) return;
+  out[3 * n] = P.lo[0] + i - 4;
+  out[3 * n + 1] = P.lo[1] + j - 4;
+  out[3 * n + 2] = DIM == 3 ? P.lo[2] + k - 4 : 0;
+}
+
+// new fine cells: rows (dst, Ldst, kind, src, Lsrc); kind 0 copies the old fine
+// patch src of the old hierarchy (P2, obuf), kind 1 prolongs from the coarse
+// patch src (cbuf) as for a ghost cell
+template <class T, int DIM> __global__ void k_transfer_cells(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 5 * r;
+  const DPatch D = a.P[row[0]];
+  T* dst = (T*)a.fbuf + D.off + row[1];
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+  if (row[2] == 0) {
+    const DPatch O = a.P2[row[3]];
+    const T* src = (const T*)a.obuf + O.off + row[4];
+#pragma unroll
+    for (int n = 0; n < NCF; ++n) {
+      const int f = n < 5 ? n : BZ;
+      dst[f * D.fs] = src[f * O.fs];
+    }
+    return;
+  }
+  const DPatch C = a.P[row[3]];
+  int g[3];
+  global_pos<DIM>(D, row[1], g);
+  const T* src = (const T*)a.cbuf + C.off + row[4];
+  const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    const T* u = src + f * C.fs;
+    const T u0 = u[0];
+    T v = u0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T sl = mm(u0 - u[-st[d]], u[st[d]] - u0);
+      v = v + sl * ((g[d] & 1) ? T(0.25) : T(-0.25));
+    }
+    dst[f * D.fs] = v;
+  }
+}
+
+// new fine own faces: rows (dst, d, Ldst, kind, src, Lsrc); kind 0 copies the
+// old fine face, kind 1 prolongs (coincident or interior, by the parity)
+template <class T, int DIM> __global__ void k_transfer_faces(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch D = a.P[row[0]];
+  const int n = row[1];
+  T* out = (T*)a.fbuf + D.off + (BX + n) * D.fs + row[2];
+  if (row[3] == 0) {
+    const DPatch O = a.P2[row[4]];
+    *out = ((const T*)a.obuf)[O.off + (BX + n) * O.fs + row[5]];
+    return;
+  }
+  const DPatch C = a.P[row[4]];
+  int g[3];
+  global_pos<DIM>(D, row[2], g);
+  const int par[3] = {g[0] & 1, g[1] & 1, DIM == 3 ? (g[2] & 1) : 0};
+  const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
+  const T* cb = (const T*)a.cbuf + C.off;
+  const T* bn = cb + (BX + n) * C.fs + row[5];
+  if (!par[n]) {
+    *out = coincident<T, DIM>(bn, st, n, par);
+    return;
+  }
+  const T lo_v = coincident<T, DIM>(bn, st, n, par);
+  const T hi_v = coincident<T, DIM>(bn + st[n], st, n, par);
+  T corr = T(0);
+  bool first = true;
+#pragma unroll
+  for (int t = 0; t < DIM; ++t) {
+    if (t == n) continue;
+    const T* bt_lo = cb + (BX + t) * C.fs + row[5];
+    const T* bt_hi = bt_lo + st[t];
+    const T s_hi = mm(bt_hi[0] - bt_hi[-st[n]], bt_hi[st[n]] - bt_hi[0]);
+    const T s_lo = mm(bt_lo[0] - bt_lo[-st[n]], bt_lo[st[n]] - bt_lo[0]);
+    const T term = (T)a.ratio[n][t] * (s_hi - s_lo);
+    corr = first ? (T(0) + term) : (corr + term);
+    first = false;
+  }
+  *out = T(0.5) * (lo_v + hi_v) + T(0.125) * corr;
+}
+
+// divergence-free closure: rows (dst, L of the first child) of a prolonged
+// coarse cell; the children's divergences r, delta = K r added to the interior
+// faces (faces by direction, then transverse children in z,y,x bit order);
+// idx = fine 1/dx
+template <class T, int DIM> __global__ void k_closure(RowArgs a) {
+  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 2 * r;
+  const DPatch D = a.P[row[0]];
+  const int L0 = row[1];
+  T* B = (T*)a.fbuf + D.off;
+  const int st[3] = {1, D.ext[0], D.ext[0] * D.ext[1]};
+  constexpr int NC = DIM == 3 ? 8 : 4, NT = DIM == 3 ? 4 : 2;
+  double res[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int x = L0 + (c & 1) * st[0] + ((c >> 1) & 1) * st[1] + (DIM == 3 ? ((c >> 2) & 1) * st[2] : 0);
+    double div = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const T* b = B + (BX + d) * D.fs;
+      div = div + ((double)b[x + st[d]] - (double)b[x]) * a.idx[d];
+    }
+    res[c] = div;
+  }
+  int f = 0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d)
+#pragma unroll
+    for (int t = 0; t < NT; ++t, ++f) {
+      int o[3] = {0, 0, 0}, bit = 0;
+#pragma unroll
+      for (int e = 0; e < DIM; ++e) {
+        if (e == d) continue;
+        o[e] = (t >> bit) & 1;
+        ++bit;
+      }
+      o[d] = 1;
+      double delta = 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) delta += a.K[f * 8 + c] * res[c];
+      T* face = B + (BX + d) * D.fs + L0 + o[0] * st[0] + o[1] * st[1] + (DIM == 3 ? o[2] * st[2] : 0);
+      *face = (T)((double)*face + delta);
+    }
+}
+
 // ------------------------------------------------------------------ reflux and restriction
 // rows (l, qc, Lcell, f0..f5); R = (S1 + S2) - C per C/F face, applied in slot order
 template <class T, int DIM> __global__ void k_reflux_cells(RowArgs a) {
@@ -682,6 +838,9 @@ template <class T, int DIM> struct Impl {
   AMRK_ROWS(prolong_faces)
   AMRK_ROWS(fill_bc_cells)
   AMRK_ROWS(fill_bc_faces)
+  AMRK_ROWS(transfer_cells)
+  AMRK_ROWS(transfer_faces)
+  AMRK_ROWS(closure)
   AMRK_ROWS(reflux_cells)
   AMRK_ROWS(reflux_faces)
   AMRK_ROWS(restrict_cells)
@@ -692,6 +851,10 @@ template <class T, int DIM> struct Impl {
     for (int d = 0; d < DIM; ++d) n *= a.maxn[d];
     k_cfl<T, DIM><<<dim3(cdiv(n, TPB), a.npatch), TPB, 0, s>>>(a);
     if (nl) ++*nl;
+  }
+  static void flag(const LevelArgs& a, double theta, int* out, unsigned long long* count, long long cap,
+                   cudaStream_t s) {
+    k_flag<T, DIM><<<grid_region(a, 0, 0), TPB, 0, s>>>(a, theta, out, count, cap);
   }
   static void io(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
                  const long long* poff, int field, int to_state, cudaStream_t s, int* nl) {
@@ -746,7 +909,8 @@ template <class T, int DIM> struct Impl {
   static const Ops* ops() {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
-                          sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc};
+                          sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
+                          transfer_faces, closure};
     return &o;
   }
 };

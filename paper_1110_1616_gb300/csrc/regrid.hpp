@@ -1,0 +1,34 @@
+// Regrid host logic (regrid.cpp): block clustering and transfer maps.
+#pragma once
+#include <array>
+#include <cstdint>
+#include <vector>
+
+#include "hierarchy.hpp"
+
+namespace amrmhd {
+
+// New level-(l+1) boxes (level, lo[3], hi[3] in level-(l+1) cells) from the
+// flagged level-l cells (x, y, z triples, global level-l indices): buffer the
+// flags by 2 cells inside the level-l region, mark the aligned 4^dim blocks of
+// level-l cells holding a buffered flag whose 3-cell surroundings lie in the
+// region, merge them greedily in z,y,x order (x runs, then y, then z, at most 4
+// blocks per side) and refine by 2.
+std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags);
+
+struct TransferMaps {
+  std::vector<int32_t> cells;    // (dst, Ldst, kind, src, Lsrc): 0 copy from old patch src, 1 prolong from coarse src
+  std::vector<int32_t> faces;    // (dst, d, Ldst, kind, src, Lsrc)
+  std::vector<int32_t> closure;  // (dst, L of the first child) of prolonged coarse cells next to copied ones
+};
+
+// Maps filling level lf of the new hierarchy Hn from level lf of the old
+// hierarchy Ho and level lf-1 of Hn. Returns 0, or < 0 if a source is missing.
+int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps& out);
+
+// K (12 x 8, row-major, faces x children): the least-norm correction of the
+// interior fine faces of a coarse cell that cancels the children's
+// divergences r, delta = K r; idx: fine 1/dx per dimension.
+void closure_matrix(int dim, const double* idx, double* K);
+
+}  // namespace amrmhd

@@ -1,0 +1,283 @@
+// C-ABI of the regrid (amrmhd_regrid, amrmhd_get_patches): every level above 0
+// is rebuilt coarse to fine. Each stage is a context holding the levels built
+// so far plus the new level: its coarser levels are copied from the previous
+// stage, the new level is transferred from the old hierarchy (copy where the
+// old fine level covered the parent cell, else prolongation, then the
+// divergence-free closure), its ghosts are filled and its cells flagged for
+// the next stage. The last stage's hierarchy and arena replace the context's.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ctx.hpp"
+#include "regrid.hpp"
+
+using namespace amrapi;
+
+namespace {
+
+#define CUR(call)                                                                                  \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// flagged cells of level l of context c (ghosts of l filled): host triples
+amrmhd_status flag_level(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta, std::vector<int32_t>& out) {
+  long long cap = 1 << 16;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    int* d_out = nullptr;
+    unsigned long long* d_cnt = nullptr;
+    CUR(cudaMalloc((void**)&d_out, sizeof(int) * 3 * cap));
+    CUR(cudaMalloc((void**)&d_cnt, sizeof(unsigned long long)));
+    CUR(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream));
+    amrk::LevelArgs a = level_args(c, l, c->d_scal, 1.0, 0);
+    c->ops->flag(a, theta, d_out, d_cnt, cap, c->stream);
+    unsigned long long n = 0;
+    CUR(cudaMemcpyAsync(&n, d_cnt, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    CUR(cudaStreamSynchronize(c->stream));
+    if ((long long)n <= cap) {
+      out.resize(3 * n);
+      if (n) CUR(cudaMemcpy(out.data(), d_out, sizeof(int) * 3 * n, cudaMemcpyDeviceToHost));
+      cudaFree(d_out);
+      cudaFree(d_cnt);
+      return AMRMHD_OK;
+    }
+    cudaFree(d_out);
+    cudaFree(d_cnt);
+    cap = (long long)n;
+  }
+  return fail(ctx, AMRMHD_ENOMEM, "flag list did not fit");
+}
+
+// a stage context with the given patches, a library-owned arena and the
+// option settings of ctx
+amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, amrmhd_ctx** out) {
+  amrmhd_ctx* c = nullptr;
+  amrmhd_status st = amrmhd_create(&ctx->cfg, ctx->stream, &c);
+  if (st) return fail(ctx, st, "regrid: create");
+  c->opt_advance = ctx->opt_advance;
+  c->opt_graph = ctx->opt_graph;
+  c->opt_tile = ctx->opt_tile;
+  size_t bytes = 0;
+  st = amrmhd_set_hierarchy(c, ps.data(), (int32_t)ps.size(), &bytes);
+  if (st) {
+    std::string m = c->err;
+    amrmhd_destroy(c);
+    return fail(ctx, st, "regrid: new hierarchy rejected: " + m);
+  }
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, std::max<size_t>(bytes, 256));
+  if (e != cudaSuccess) {
+    amrmhd_destroy(c);
+    return fail(ctx, AMRMHD_ENOMEM, std::string("regrid: arena: ") + cudaGetErrorString(e));
+  }
+  st = amrmhd_bind_arena(c, mem, bytes);
+  c->dev_allocs.push_back(mem);
+  if (st) {
+    std::string m = c->err;
+    amrmhd_destroy(c);
+    return fail(ctx, st, "regrid: bind: " + m);
+  }
+  *out = c;
+  return AMRMHD_OK;
+}
+
+// levels 0..l of src (same patches, same order) into buffer 0 of dst
+amrmhd_status copy_levels(amrmhd_ctx* ctx, amrmhd_ctx* src, amrmhd_ctx* dst, int l) {
+  const size_t elem = dst->ops->elem;
+  for (int q = 0; q <= l; ++q) {
+    const std::vector<int>& ids = dst->H.level_patches[q];
+    const long long b = dst->off[ids.front()];
+    const long long e = dst->off[ids.back()] + 8 * dst->fs[ids.back()];
+    if (src->off[src->H.level_patches[q].front()] != b) return fail(ctx, AMRMHD_EINVAL, "regrid: layout mismatch");
+    CUR(cudaMemcpyAsync((char*)state_buf(dst, 0) + b * elem, (char*)state_buf(src, src->cur[q]) + b * elem,
+                        (size_t)(e - b) * elem, cudaMemcpyDeviceToDevice, dst->stream));
+    dst->cur[q] = 0;
+  }
+  return AMRMHD_OK;
+}
+
+amrmhd_status upload_rows(amrmhd_ctx* ctx, const std::vector<int32_t>& v, int** p) {
+  *p = nullptr;
+  if (v.empty()) return AMRMHD_OK;
+  CUR(cudaMalloc((void**)p, sizeof(int32_t) * v.size()));
+  CUR(cudaMemcpy(*p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
+  return AMRMHD_OK;
+}
+
+// transfer of level lf of stage S from the old context O
+amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
+  amrmhd::TransferMaps m;
+  const int rc = amrmhd::transfer_maps(S->H, O->H, lf, m);
+  if (rc) return fail(ctx, AMRMHD_EINVAL, "regrid: transfer map without a source");
+  int *dc = nullptr, *df = nullptr, *dk = nullptr;
+  double* dK = nullptr;
+  amrmhd_status st = upload_rows(ctx, m.cells, &dc);
+  if (!st) st = upload_rows(ctx, m.faces, &df);
+  if (!st) st = upload_rows(ctx, m.closure, &dk);
+  double idx[3], K[96] = {0};
+  level_idx(S, lf, idx);
+  amrmhd::closure_matrix(S->cfg.dim, idx, K);
+  if (!st) {
+    cudaError_t e = cudaMalloc((void**)&dK, sizeof(K));
+    if (e == cudaSuccess) e = cudaMemcpy(dK, K, sizeof(K), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, "regrid: closure matrix");
+  }
+  if (!st) {
+    amrk::RowArgs a = row_args(S, DevList{dc, (int64_t)m.cells.size() / 5}, lf - 1);
+    a.fbuf = state_buf(S, S->cur[lf]);
+    a.cbuf = state_buf(S, S->cur[lf - 1]);
+    a.P2 = O->dP;
+    a.obuf = O->H.nlev > lf ? state_buf(O, O->cur[lf]) : nullptr;
+    int nl = 0;
+    S->ops->transfer_cells(a, S->stream, &nl);
+    a.rows = df;
+    a.nrows = (int64_t)m.faces.size() / 6;
+    S->ops->transfer_faces(a, S->stream, &nl);
+    a.rows = dk;
+    a.nrows = (int64_t)m.closure.size() / 2;
+    for (int d = 0; d < 3; ++d) a.idx[d] = idx[d];
+    a.K = dK;
+    S->ops->closure(a, S->stream, &nl);
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer: ") + cudaGetErrorString(e));
+  }
+  cudaFree(dc);
+  cudaFree(df);
+  cudaFree(dk);
+  cudaFree(dK);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (max_levels < 1 || max_levels > ctx->cfg.max_level + 1) return fail(ctx, AMRMHD_EINVAL, "bad max_levels");
+  for (int d = 0; d < ctx->cfg.dim; ++d)
+    if (ctx->cfg.base[d] % 4) return fail(ctx, AMRMHD_EINVAL, "regrid needs base sizes divisible by 4");
+  std::vector<amrmhd_patch> ps;
+  for (int q : ctx->H.level_patches[0]) {
+    amrmhd_patch p;
+    p.level = 0;
+    for (int d = 0; d < 3; ++d) { p.lo[d] = ctx->H.p[q].lo[d]; p.hi[d] = ctx->H.p[q].hi[d]; }
+    ps.push_back(p);
+  }
+  // level 0 of the old context: fill and flag
+  int nl = 0;
+  op_fill(ctx, 0, 1, &nl);
+  std::vector<int32_t> flags;
+  st = flag_level(ctx, ctx, 0, theta, flags);
+  if (st) return st;
+  amrmhd_ctx* prev = ctx;
+  const amrmhd::Hierarchy* prevH = &ctx->H;
+  for (int l = 0; l + 1 < max_levels; ++l) {
+    std::vector<std::array<int, 7>> boxes = amrmhd::regrid_boxes(*prevH, l, flags);
+    if (boxes.empty()) break;
+    std::vector<amrmhd_patch> next = ps;
+    for (const auto& b : boxes) {
+      amrmhd_patch p;
+      p.level = b[0];
+      for (int d = 0; d < 3; ++d) { p.lo[d] = b[1 + d]; p.hi[d] = b[4 + d]; }
+      next.push_back(p);
+    }
+    amrmhd_ctx* S = nullptr;
+    st = make_stage(ctx, next, &S);
+    if (!st) st = copy_levels(ctx, prev, S, l);
+    if (!st) {
+      for (int q = 0; q <= l; ++q) op_fill(S, q, 1, &nl);
+      st = transfer(ctx, S, ctx, l + 1);
+    }
+    if (!st) {
+      op_fill(S, l + 1, 1, &nl);
+      flags.clear();
+      if (l + 2 < max_levels) st = flag_level(ctx, S, l + 1, theta, flags);
+    }
+    if (st) {
+      if (S) amrmhd_destroy(S);
+      if (prev != ctx) amrmhd_destroy(prev);
+      return st;
+    }
+    if (prev != ctx) amrmhd_destroy(prev);
+    prev = S;
+    prevH = &S->H;
+    ps = next;
+  }
+  if (prev == ctx) {
+    // no level above 0: a context with level 0 only
+    amrmhd_ctx* S = nullptr;
+    st = make_stage(ctx, ps, &S);
+    if (!st) st = copy_levels(ctx, ctx, S, 0);
+    if (st) {
+      if (S) amrmhd_destroy(S);
+      return st;
+    }
+    prev = S;
+  }
+  CUR(cudaStreamSynchronize(ctx->stream));
+  // the context takes the last stage's hierarchy and arena; the stage object
+  // then holds (and frees) the old ones
+  std::swap(*ctx, *prev);
+  std::swap(ctx->own_stream, prev->own_stream);
+  ctx->launches += prev->launches;
+  amrmhd_destroy(prev);
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_regrid_boxes(amrmhd_ctx* ctx, int32_t level, const int32_t* flags, int64_t nflags,
+                                  int32_t* out, int32_t cap, int32_t* n) {
+  if (!ctx || !n || nflags < 0 || (nflags && !flags)) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  if (level < 0 || level >= ctx->H.nlev) return fail(ctx, AMRMHD_EINVAL, "bad level");
+  std::vector<int32_t> f;
+  f.reserve(3 * (size_t)nflags);
+  const amrmhd::Hierarchy& H = ctx->H;
+  for (int64_t i = 0; i < nflags; ++i) {
+    const int32_t* c = flags + 3 * i;
+    bool inside = true;
+    for (int d = 0; d < H.dim; ++d)
+      if (c[d] < 0 || c[d] >= H.N(level, d)) inside = false;
+    if (!inside) continue;
+    bool in_region = false;
+    for (int q : H.level_patches[level]) {
+      const amrmhd::HPatch& P = H.p[q];
+      bool in = true;
+      for (int d = 0; d < H.dim; ++d)
+        if (c[d] < P.lo[d] || c[d] >= P.hi[d]) in = false;
+      if (in) { in_region = true; break; }
+    }
+    if (in_region) f.insert(f.end(), c, c + 3);
+  }
+  std::vector<std::array<int, 7>> b = amrmhd::regrid_boxes(H, level, f);
+  *n = (int32_t)b.size();
+  if (!out) return AMRMHD_OK;
+  if (cap < *n) return fail(ctx, AMRMHD_EINVAL, "box buffer too small");
+  for (size_t i = 0; i < b.size(); ++i)
+    for (int k = 0; k < 7; ++k) out[7 * i + k] = b[i][k];
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_get_patches(amrmhd_ctx* ctx, amrmhd_patch* out, int32_t cap, int32_t* n) {
+  if (!ctx || !n) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  const int np = (int)ctx->H.p.size();
+  *n = np;
+  if (!out) return AMRMHD_OK;
+  if (cap < np) return fail(ctx, AMRMHD_EINVAL, "patch buffer too small");
+  for (int q = 0; q < np; ++q) {
+    out[q].level = ctx->H.p[q].level;
+    for (int d = 0; d < 3; ++d) { out[q].lo[d] = ctx->H.p[q].lo[d]; out[q].hi[d] = ctx->H.p[q].hi[d]; }
+  }
+  return AMRMHD_OK;
+}
+
+}  // extern "C"

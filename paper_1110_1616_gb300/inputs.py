@@ -496,6 +496,35 @@ def clumps_2d(n=32, nlev=3, n_clumps=4, radius=0.06, seed=3, psize=8, b_pert=0.0
                    meta={"centres": centres, "radius": radius, "seed": seed})
 
 
+def clumps_3d_small(n=16, nlev=2, n_clumps=3, radius=0.1, seed=3, b_pert=0.3, gamma=GAMMA):
+    """3D clumps as whole-level arrays on every level (small sizes, for parity
+    tests): contrast 100, pressure equilibrium, v = (1, 0, 0), B = (sqrt 2, 0, 0)
+    plus a perturbation from the vector potential A_z = b_pert sin(2 pi x)
+    sin(2 pi y) / (2 pi)."""
+    centres = clump_centres(3, n_clumps, seed, lo=0.3, hi=0.7)
+    base = (n, n, n)
+    patches = tile(0, (0, 0, 0), base, 8, 3) + clump_boxes(3, base, nlev, centres, radius, margin=4)
+    b0 = math.sqrt(2.0)
+    state = {}
+    for l in range(nlev):
+        m = n << l
+        x, y, z = _cell_centres((m, m, m), (0, 0, 0), (1, 1, 1), 3)
+        rho, vx, vy, vz, p = clump_cells(x, y, z, 3, centres, radius)
+        dx = 1.0 / m
+        ax = np.arange(m + 1) * dx
+        Y, X = np.meshgrid(ax, ax, indexing="ij")
+        az = b_pert * np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y) / (2 * math.pi)
+        bx2, by2 = _b_from_az_2d(az, (m, m, 1), dx, dx)
+        bx = np.broadcast_to(bx2 + b0, (m, m, m + 1)).copy()
+        by = np.broadcast_to(by2, (m, m + 1, m)).copy()
+        bz = np.zeros((m + 1, m, m))
+        bcx, bcy, bcz = _cell_b_from_faces(bx, by, bz, 3)
+        e = _energy(rho, vx, vy, vz, p, bcx, bcy, bcz, gamma)
+        state[l] = [rho, rho * vx, rho * vy, rho * vz, e, bx, by, bz]
+    return Problem("clumps_3d_small", 3, base, patches, nlev, state, gamma=gamma,
+                   meta={"centres": centres, "radius": radius})
+
+
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
     """A random properly nested periodic hierarchy: level 0 tiled by patches
     of random widths; finer levels a few random boxes aligned to parent cells,

@@ -167,3 +167,43 @@ def test_query_counts():
     assert c.query(A.Q_CELLS) == 64 * 64 + 64 * 64
     assert c.query(A.Q_CELL_UPDATES_PER_STEP) == 64 * 64 + 2 * 64 * 64
     assert c.query(A.Q_ARENA_BYTES) > 0
+
+
+def regrid_cases():
+    out = []
+    rng = np.random.default_rng(12)
+    for seed in range(3):
+        patches = inputs.random_hierarchy(2, 40 + seed, base=32, nlev=3)
+        out.append(("rand2d_%d" % seed, 2, (32, 32, 1), patches, None))
+    out.append(("clumps2d", 2, (32, 32, 1), inputs.clumps_2d(32, 3).patches, None))
+    out.append(("bounded2d", 2, (32, 32, 1), inputs.clumps_2d(32, 3).patches, (2, 1, 1, 1, 0, 0)))
+    out.append(("rand3d", 3, (16, 16, 16), inputs.random_hierarchy(3, 50, base=16, nlev=2), None))
+    return out
+
+
+@pytest.mark.parametrize("name,dim,base,patches,bc", regrid_cases(), ids=[c[0] for c in regrid_cases()])
+def test_regrid_clustering_bit_exact_vs_oracle(name, dim, base, patches, bc):
+    """The library's host clustering (steps 2-4 of the regrid) and the oracle's
+    give the same boxes, in the same order, for the same flagged cells: random
+    sparse flags, clustered flags and all-flagged levels."""
+    from oracle import OracleSim
+    c = ctx_for(dim, base, patches, bc=bc)
+    o = OracleSim(dim, base, patches, bc=bc)
+    nlev = max(p[0] for p in patches) + 1
+    rng = np.random.default_rng(hash(name) % 1000)
+    for l in range(nlev):
+        n = [base[d] << l if d < dim else 1 for d in range(3)]
+        sets = [np.stack([rng.integers(0, n[d], size=40) for d in range(3)], axis=1)]
+        centre = [rng.integers(0, n[d]) for d in range(3)]
+        blob = np.array([[(centre[0] + a) % n[0], (centre[1] + b) % n[1], (centre[2] + cc) % n[2] if dim == 3 else 0]
+                         for a in range(-6, 7) for b in range(-6, 7) for cc in (range(-3, 4) if dim == 3 else [0])])
+        sets.append(blob)
+        full = np.array([[i, j, k] for k in range(n[2]) for j in range(n[1]) for i in range(n[0])])
+        sets.append(full)
+        for fl in sets:
+            fl = fl.astype(np.int32)
+            if dim == 2:
+                fl[:, 2] = 0
+            got = c.regrid_boxes(l, fl)
+            exp = o.regrid_boxes(l, fl)
+            assert np.array_equal(got, exp), (l, got[:4], exp[:4])
