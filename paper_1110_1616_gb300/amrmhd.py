@@ -19,7 +19,7 @@ MAPS = {
     "emf_faces": 5, "restrict_cells": 6, "restrict_faces": 7, "reflux_cells": 8,
 }
 Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
-OPT_ADVANCE, OPT_GRAPH, OPT_TILE = 0, 1, 2
+OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT = 0, 1, 2, 3
 
 
 class AmrmhdError(RuntimeError):
@@ -72,6 +72,7 @@ def lib():
             "amrmhd_step_dt": [vp, i32, vp],
             "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
             "amrmhd_regrid": [vp, dbl, i32],
+            "amrmhd_autotune": [vp, i32, vp],
             "amrmhd_get_patches": [vp, vp, i32, C.POINTER(i32)],
             "amrmhd_regrid_boxes": [vp, i32, vp, i64, vp, i32, C.POINTER(i32)],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
@@ -257,6 +258,13 @@ class Context:
         buf = np.zeros(max(n, 1), dtype=np.float64) if want_dt else None
         self._check(lib().amrmhd_step(self.h, n, buf.ctypes.data_as(C.c_void_p) if want_dt else None), "step")
         return buf
+
+    def autotune(self, trials=5):
+        """Per-level fused-tile choice by timing (see amrmhd_autotune)."""
+        n = self.query(Q_NLEVEL)
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        self._check(lib().amrmhd_autotune(self.h, int(trials), out.ctypes.data_as(C.c_void_p)), "autotune")
+        return out[:n].tolist()
 
     def regrid(self, theta, max_levels):
         """Rebuilds the levels above 0 from density-gradient flags (threshold

@@ -35,6 +35,13 @@ constexpr int64_t kHistCap = 4096;
 
 void free_device(amrmhd_ctx* ctx) {
   adj_free(ctx);
+  for (cudaStream_t st : ctx->side) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ctx->ev_fork) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->ev_join) cudaEventDestroy(e);
+  ctx->side.clear();
+  ctx->ev_fork.clear();
+  ctx->ev_join.clear();
+  ctx->tile_level.clear();
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
   for (void* p : ctx->dev_allocs) cudaFree(p);
@@ -159,7 +166,8 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
       ctx->ops->advance(b, ctx->stream, nl);
     }
   } else if (fused) {
-    const int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
+    int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
+    if (ctx->opt_tile < 0 && (int)ctx->tile_level.size() > l && ctx->tile_level[l] >= 0) v = ctx->tile_level[l];
     ctx->ops->advance_fused(a, v, ctx->stream, nl);
   } else {
     ctx->ops->advance(a, ctx->stream, nl);
@@ -247,11 +255,32 @@ void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
 }
 
 // the recursive order 0,1,2,2,1,2,2 of Sec. 4 with P, A, S, R
+// With concurrency on, the two sub-steps of level l+1 run on a side stream
+// while level l advances: level l+1 reads only level l's filled state at the
+// start of the step (prolongation, extended ghost zones) and the registers
+// of both sides are separate arrays, so the two are joined only before the
+// reflux and restriction (Sec. 4: finer levels need not wait for the coarser
+// level's advance).
 void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl) {
   op_fill(ctx, l, s, nl);
   if (ctx->after_fill) ctx->after_fill(ctx, l, s);
+  const bool kids = l + 1 < ctx->H.nlev;
+  if (kids && ctx->opt_concurrent && (int)ctx->side.size() > l) {
+    cudaStream_t main = ctx->stream, side = ctx->side[l];
+    cudaEventRecord(ctx->ev_fork[l], main);
+    cudaStreamWaitEvent(side, ctx->ev_fork[l], 0);
+    op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, nl);
+    ctx->stream = side;
+    op_level_step(ctx, l + 1, 1, nl);
+    op_level_step(ctx, l + 1, 2, nl);
+    cudaEventRecord(ctx->ev_join[l], side);
+    ctx->stream = main;
+    cudaStreamWaitEvent(main, ctx->ev_join[l], 0);
+    op_reflux_restrict(ctx, l + 1, nl);
+    return;
+  }
   op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, nl);
-  if (l + 1 < ctx->H.nlev) {
+  if (kids) {
     op_level_step(ctx, l + 1, 1, nl);
     op_level_step(ctx, l + 1, 2, nl);
     op_reflux_restrict(ctx, l + 1, nl);
@@ -327,6 +356,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 3) ctx->opt_tile = value;
+  else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -513,6 +543,17 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
   }
   ctx->cur.assign(nlev, 0);
   ctx->start.assign(nlev, 0);
+  for (int l = 0; l + 1 < nlev; ++l) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    ctx->side.push_back(st);
+    ctx->ev_fork.push_back(a);
+    ctx->ev_join.push_back(b);
+  }
+  ctx->tile_level.assign(nlev, -1);
   ctx->ops->prepare();
   CU(cudaGetLastError());
   ctx->bound = true;
@@ -735,6 +776,58 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
     CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
     return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
   }
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (trials < 1) return fail(ctx, AMRMHD_EINVAL, "trials must be positive");
+  const int nlev = ctx->H.nlev;
+  if (!ctx->fused()) {
+    if (tiles)
+      for (int l = 0; l < nlev; ++l) tiles[l] = -1;
+    return AMRMHD_OK;
+  }
+  // a CFL dt for the timed advances (the state is not changed: an advance
+  // reads the current buffer and writes the other one)
+  int nl = 0;
+  op_cfl(ctx, nullptr, &nl);
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const int64_t keep = ctx->opt_tile;
+  ctx->opt_tile = -1;
+  for (int l = 0; l < nlev; ++l) {
+    float best = 0.0f;
+    int bv = -1;
+    for (int v = 0; v < 4; ++v) {
+      ctx->tile_level[l] = v;
+      const int c0 = ctx->cur[l];
+      op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), 1, &nl);  // warm-up
+      ctx->cur[l] = c0;
+      if (cudaGetLastError() != cudaSuccess) continue;
+      CU(cudaEventRecord(e0, ctx->stream));
+      for (int t = 0; t < trials; ++t) {
+        op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), 1, &nl);
+        ctx->cur[l] = c0;
+      }
+      CU(cudaEventRecord(e1, ctx->stream));
+      CU(cudaEventSynchronize(e1));
+      if (cudaGetLastError() != cudaSuccess) continue;
+      float ms = 0.0f;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (bv < 0 || ms < best) { best = ms; bv = v; }
+    }
+    ctx->tile_level[l] = bv;
+    if (tiles) tiles[l] = bv;
+  }
+  ctx->opt_tile = keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
+  CU(cudaStreamSynchronize(ctx->stream));
   return AMRMHD_OK;
 }
 

@@ -40,7 +40,8 @@ struct amrmhd_ctx {
   bool have_h = false, bound = false;
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
-  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1;
+  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1;
+  std::vector<int> tile_level;  // autotuned fused tile per level (-1: none)
   // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
   // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
   bool fused() const {
@@ -74,6 +75,9 @@ struct amrmhd_ctx {
   std::vector<int> g_cur_before[2], g_cur_after[2], g_start_after[2];
   int g_launches[2] = {0, 0};
   long long launches = 0;
+  // inter-level concurrency: side stream and fork/join events per level
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev_fork, ev_join;
   // called after every ghost fill of op_level_step (level, sub-step): the
   // adjoint records the filled states there
   void (*after_fill)(amrmhd_ctx*, int, int) = nullptr;

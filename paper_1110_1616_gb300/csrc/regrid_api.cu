@@ -63,6 +63,7 @@ amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, a
   c->opt_advance = ctx->opt_advance;
   c->opt_graph = ctx->opt_graph;
   c->opt_tile = ctx->opt_tile;
+  c->opt_concurrent = ctx->opt_concurrent;
   size_t bytes = 0;
   st = amrmhd_set_hierarchy(c, ps.data(), (int32_t)ps.size(), &bytes);
   if (st) {

@@ -279,3 +279,53 @@ def test_fused_equals_staged_3d_amr(precision):
                 assert np.array_equal(a, b), (f, p, np.abs(a - b).max())
             else:
                 assert np.abs(a - b).sum() <= 1e-5 * np.abs(b).sum() + 1e-12, (f, p)
+
+
+def run_opts(pb, precision, steps, **opts):
+    import torch
+    s = torch.cuda.Stream()
+    ctx = A.context_for(pb, precision=precision, strict_fp64=True, stream=s.cuda_stream)
+    for k, v in opts.items():
+        ctx.set_option(getattr(A, k), v)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    ctx.load_state(pb.state)
+    return ctx
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_concurrent_levels_equal_serial(graph):
+    """Running each finer level's sub-steps concurrently with the coarser
+    advance (side streams, joined before the reflux) changes nothing, bitwise:
+    3-level 2D FP64 and 2-level 3D mixed precision."""
+    patches = inputs.random_hierarchy(2, 1, base=32, nlev=3)
+    nlev = max(p[0] for p in patches) + 1
+    pb2 = inputs.Problem("rand3", 2, (32, 32, 1), patches, nlev, inputs.random_smooth_2d(32, nlev, seed=2))
+    base = (16, 16, 16)
+    p3 = inputs.tile(0, (0, 0, 0), base, 8, 3) + inputs.tile(1, (8, 8, 8), (24, 16, 24), 8, 3)
+    pb3 = inputs.Problem("b3", 3, base, p3, 2, {0: inputs.blast_3d(16, 8).state[0], 1: inputs.blast_3d(32, 8).state[0]})
+    for pb, prec in ((pb2, A.FP64), (pb3, A.MIXED)):
+        a = run_opts(pb, prec, 4, OPT_CONCURRENT=1, OPT_GRAPH=graph)
+        b = run_opts(pb, prec, 4, OPT_CONCURRENT=0, OPT_GRAPH=graph)
+        a.step(4)
+        b.step(4)
+        sa, sb = a.read_state(), b.read_state()
+        for f in range(8):
+            for p in range(len(pb.patches)):
+                assert np.array_equal(sa[f][p], sb[f][p]), (pb.name, f, p)
+
+
+def test_autotune_picks_a_tile_per_level_and_keeps_results():
+    base = (16, 16, 16)
+    p3 = inputs.tile(0, (0, 0, 0), base, 8, 3) + inputs.tile(1, (8, 8, 8), (24, 16, 24), 8, 3)
+    pb = inputs.Problem("b3", 3, base, p3, 2, {0: inputs.blast_3d(16, 8).state[0], 1: inputs.blast_3d(32, 8).state[0]})
+    a = run_opts(pb, A.MIXED, 3)
+    tiles = a.autotune(3)
+    assert len(tiles) == 2 and all(0 <= t <= 3 for t in tiles)
+    b = run_opts(pb, A.MIXED, 3)
+    a.step(3)
+    b.step(3)
+    sa, sb = a.read_state(), b.read_state()
+    for f in range(8):
+        for p in range(len(pb.patches)):
+            assert np.array_equal(sa[f][p], sb[f][p]), (f, p)
