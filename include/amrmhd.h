@@ -263,7 +263,12 @@ amrmhd_status amrmhd_get_patches(amrmhd_ctx* ctx, amrmhd_patch* out, int32_t cap
 /* Integer queries: AMRMHD_Q_* */
 enum {
   AMRMHD_Q_NPATCH = 0, AMRMHD_Q_NLEVEL = 1, AMRMHD_Q_CELLS = 2, AMRMHD_Q_CELL_UPDATES_PER_STEP = 3,
-  AMRMHD_Q_ARENA_BYTES = 4, AMRMHD_Q_KERNEL_LAUNCHES = 5
+  AMRMHD_Q_ARENA_BYTES = 4, AMRMHD_Q_KERNEL_LAUNCHES = 5,
+  /* host wall time of the last amrmhd_regrid in microseconds: flagging (fill,
+   * flag kernel, list copy), clustering, building the stage hierarchies, maps
+   * and arenas, and the data transfer */
+  AMRMHD_Q_REGRID_FLAG_US = 6, AMRMHD_Q_REGRID_CLUSTER_US = 7, AMRMHD_Q_REGRID_BUILD_US = 8,
+  AMRMHD_Q_REGRID_TRANSFER_US = 9
 };
 amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
 

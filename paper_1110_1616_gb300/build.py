@@ -51,7 +51,8 @@ def build(force=False, verbose=False):
         jobs.append((cmd, obj))
     for unit in HOST_UNITS:
         hobj = os.path.join(OUT, unit.replace(".cpp", ".o"))
-        jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-c", os.path.join(CSRC, unit), "-o", hobj], hobj))
+        jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-fopenmp", "-c", os.path.join(CSRC, unit), "-o", hobj],
+                     hobj))
     with cf.ThreadPoolExecutor(len(jobs)) as ex:
         futs = [ex.submit(subprocess.run, cmd, capture_output=True, text=True) for cmd, _ in jobs]
         for (cmd, _), f in zip(jobs, futs):
@@ -61,7 +62,7 @@ def build(force=False, verbose=False):
             if verbose:
                 print(r.stdout + r.stderr)
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs] + ["-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stderr))

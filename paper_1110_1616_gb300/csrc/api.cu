@@ -850,6 +850,10 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
       return AMRMHD_OK;
     }
     case AMRMHD_Q_ARENA_BYTES: *value = (int64_t)ctx->arena_bytes; return AMRMHD_OK;
+    case AMRMHD_Q_REGRID_FLAG_US:
+    case AMRMHD_Q_REGRID_CLUSTER_US:
+    case AMRMHD_Q_REGRID_BUILD_US:
+    case AMRMHD_Q_REGRID_TRANSFER_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
     default: return fail(ctx, AMRMHD_EINVAL, "unknown query");
   }
 }

@@ -75,6 +75,9 @@ struct amrmhd_ctx {
   std::vector<int> g_cur_before[2], g_cur_after[2], g_start_after[2];
   int g_launches[2] = {0, 0};
   long long launches = 0;
+  // host wall time of the last regrid, microseconds: flagging, clustering,
+  // hierarchy and map building with the stage arenas, data transfer
+  long long regrid_us[4] = {0, 0, 0, 0};
   // inter-level concurrency: side stream and fork/join events per level
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_fork, ev_join;

@@ -7,6 +7,8 @@
 // finer level's candidates come from its parents' neighbour lists.
 #include "hierarchy.hpp"
 
+#include <unordered_map>
+
 #include <algorithm>
 #include <map>
 #include <tuple>
@@ -99,6 +101,21 @@ struct Bins {
 struct Key {
   int c, a, b, z;
   bool operator<(const Key& o) const { return std::tie(c, a, b, z) < std::tie(o.c, o.a, o.b, o.z); }
+  bool operator==(const Key& o) const { return c == o.c && a == o.a && b == o.b && z == o.z; }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = (uint64_t)(uint32_t)k.c * 0x9E3779B97F4A7C15ull;
+    h ^= (uint64_t)(uint32_t)k.a + 0x7F4A7C159E3779B9ull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)(uint32_t)k.b + 0x94D049BB133111EBull + (h << 6) + (h >> 2);
+    h ^= (uint64_t)(uint32_t)k.z + 0xBF58476D1CE4E5B9ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+struct PairHash {
+  size_t operator()(const std::pair<int, int>& k) const {
+    return (size_t)(((uint64_t)(uint32_t)k.first << 32) ^ (uint64_t)(uint32_t)k.second) * 0x9E3779B97F4A7C15ull;
+  }
 };
 
 }  // namespace
@@ -239,10 +256,13 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     }
   }
 
-  // ---------------- ghost maps
+  // ---------------- ghost maps (patches in parallel, rows concatenated in patch order)
   rng_ghost_cells.assign(nlev, {0, 0});
   rng_ghost_faces.assign(nlev, {0, 0});
-  for (int q = 0; q < np; ++q) {
+  std::vector<std::vector<int32_t>> gc_rows(np), gf_rows(np);
+  std::vector<std::string> gerr(np);
+  std::vector<int> gst(np, 0);
+  auto ghost_patch = [&](int q, std::vector<int32_t>& gcq, std::vector<int32_t>& gfq, std::string& errq) -> int {
     const HPatch& P = p[q];
     const int l = P.level;
     // coarse candidates for prolongation sources
@@ -256,22 +276,26 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     // parent cell of fine position g; for a d-face (dn >= 0) on the high side
     // of a non-periodic domain the parent is the last coarse cell and L indexes
     // the coarse face one past it
+    int last_src = -1;
     auto coarse_src = [&](const int* g, int* L, int dn) {
       int c[3];
       for (int d = 0; d < 3; ++d) c[d] = d < dim ? (wrapd(l, d, g[d]) >> 1) : 0;
       const bool top = dn >= 0 && !per[dn] && g[dn] == N(l, dn);
       if (top) c[dn] -= 1;
-      for (int Q : cc) {
-        bool in = true;
+      auto inside = [&](int Q) {
         for (int d = 0; d < dim; ++d)
-          if (c[d] < p[Q].lo[d] || c[d] >= p[Q].hi[d]) in = false;
-        if (in) {
-          if (top) c[dn] += 1;
-          *L = loc(Q, c[0], c[1], c[2]);
-          return Q;
-        }
-      }
-      return -1;
+          if (c[d] < p[Q].lo[d] || c[d] >= p[Q].hi[d]) return false;
+        return true;
+      };
+      // consecutive positions usually share the parent patch: try the last one first
+      int hit = (last_src >= 0 && inside(last_src)) ? last_src : -1;
+      for (size_t i = 0; hit < 0 && i < cc.size(); ++i)
+        if (inside(cc[i])) hit = cc[i];
+      if (hit < 0) return -1;
+      last_src = hit;
+      if (top) c[dn] += 1;
+      *L = loc(hit, c[0], c[1], c[2]);
+      return hit;
     };
     // cells
     {
@@ -313,24 +337,24 @@ int Hierarchy::build(const int32_t* rows7, int n) {
               }
               if (out) {
                 int row[5] = {q, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q, inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
-                ghost_cells.insert(ghost_cells.end(), row, row + 5);
+                gcq.insert(gcq.end(), row, row + 5);
                 continue;
               }
             }
             size_t t = idx(a, b, c);
             int kind = 0, src = sq[t], L = sl[t];
             if (src < 0) {
-              if (l == 0) { err = "level-0 ghost cell without a source"; return AMRMHD_EINVAL; }
+              if (l == 0) { errq = "level-0 ghost cell without a source"; return AMRMHD_EINVAL; }
               int g[3] = {a, b, c};
               kind = 1;
               src = coarse_src(g, &L, -1);
-              if (src < 0) { err = "no parent-level source for the ghost cell (" + std::to_string(a) + ", " + std::to_string(b) + ", " +
+              if (src < 0) { errq = "no parent-level source for the ghost cell (" + std::to_string(a) + ", " + std::to_string(b) + ", " +
                       std::to_string(c) + ") of patch " + std::to_string(q);
                 return AMRMHD_ENEST;
               }
             }
             int row[5] = {q, loc(q, a, b, c), kind, src, L};
-            ghost_cells.insert(ghost_cells.end(), row, row + 5);
+            gcq.insert(gcq.end(), row, row + 5);
           }
     }
     // faces
@@ -384,24 +408,41 @@ int Hierarchy::build(const int32_t* rows7, int n) {
               if (out) {
                 int row[6] = {q, d, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q,
                               inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
-                ghost_faces.insert(ghost_faces.end(), row, row + 6);
+                gfq.insert(gfq.end(), row, row + 6);
                 continue;
               }
             }
             size_t t = idx(a, b, c);
             int kind = 0, src = sq[t], L = sl[t];
             if (src < 0) {
-              if (l == 0) { err = "level-0 ghost face without a source"; return AMRMHD_EINVAL; }
+              if (l == 0) { errq = "level-0 ghost face without a source"; return AMRMHD_EINVAL; }
               kind = 1;
               src = coarse_src(g, &L, d);
-              if (src < 0) { err = "no parent-level source for the ghost face (" + std::to_string(d) + "; " + std::to_string(a) + ", " +
+              if (src < 0) { errq = "no parent-level source for the ghost face (" + std::to_string(d) + "; " + std::to_string(a) + ", " +
                       std::to_string(b) + ", " + std::to_string(c) + ") of patch " + std::to_string(q);
                 return AMRMHD_ENEST;
               }
             }
             int row[6] = {q, d, loc(q, a, b, c), kind, src, L};
-            ghost_faces.insert(ghost_faces.end(), row, row + 6);
+            gfq.insert(gfq.end(), row, row + 6);
           }
+    }
+      return 0;
+  };
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int q = 0; q < np; ++q) gst[q] = ghost_patch(q, gc_rows[q], gf_rows[q], gerr[q]);
+  for (int q = 0; q < np; ++q)
+    if (gst[q]) { err = gerr[q]; return gst[q]; }
+  {
+    size_t nc = 0, nf = 0;
+    for (int q = 0; q < np; ++q) { nc += gc_rows[q].size(); nf += gf_rows[q].size(); }
+    ghost_cells.reserve(nc);
+    ghost_faces.reserve(nf);
+    for (int q = 0; q < np; ++q) {
+      ghost_cells.insert(ghost_cells.end(), gc_rows[q].begin(), gc_rows[q].end());
+      ghost_faces.insert(ghost_faces.end(), gf_rows[q].begin(), gf_rows[q].end());
+      std::vector<int32_t>().swap(gc_rows[q]);
+      std::vector<int32_t>().swap(gf_rows[q]);
     }
   }
 
@@ -422,7 +463,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     rng_reflux_cells[l][0] = (int64_t)reflux_cells.size() / 9;
     // per coarse patch: cover map over its cells widened by one, entry (fine patch, shift)
     struct Cov { int c = -1; int s[3] = {0, 0, 0}; };
-    std::map<Key, std::array<int, 4>> edge_best;  // key -> (qc, Le, pf, Lf)
+    std::unordered_map<Key, std::array<int, 4>, KeyHash> edge_best;  // key -> (qc, Le, pf, Lf)
     std::vector<std::vector<std::array<int, 7>>> face_rows(np);
     std::vector<std::vector<std::array<int, 5>>> rcell_rows(np);
     std::vector<std::vector<std::array<int, 6>>> rface_rows(np);
@@ -464,9 +505,12 @@ int Hierarchy::build(const int32_t* rows7, int n) {
       if (add_d >= 0) f[add_d] += add;
       return loc(v.c, f[0], f[1], f[2]);
     };
-    const int zlo = 0;
-    (void)zlo;
-    for (int qc : level_patches[lc]) {
+    // per coarse patch: candidate owners of its C/F edges (merged below)
+    std::vector<std::vector<std::pair<Key, std::array<int, 4>>>> edge_cand(np);
+    const std::vector<int>& lpc = level_patches[lc];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (size_t ip = 0; ip < lpc.size(); ++ip) {
+      const int qc = lpc[ip];
       const HPatch& C = p[qc];
       const int k0 = dim == 3 ? C.lo[2] : 0, k1 = dim == 3 ? C.hi[2] : 1;
       // C/F faces and restricted cells
@@ -543,20 +587,26 @@ int Hierarchy::build(const int32_t* rows7, int n) {
                 }
               if (ncov < 1 || ncov > 3) continue;
               Key key{c, wrapd(lc, 0, i), wrapd(lc, 1, j), dim == 3 ? wrapd(lc, 2, k) : 0};
-              int Le = loc(qc, i, j, k);
-              auto it = edge_best.find(key);
-              if (it == edge_best.end()) edge_best[key] = {qc, Le, bf, bl};
-              else {
-                auto& v = it->second;
-                if (qc < v[0] || (qc == v[0] && Le < v[1])) { v[0] = qc; v[1] = Le; }
-                if (bf < v[2] || (bf == v[2] && bl < v[3])) { v[2] = bf; v[3] = bl; }
-              }
+              edge_cand[qc].push_back({key, {qc, loc(qc, i, j, k), bf, bl}});
             }
       }
     }
+    // the smallest (coarse patch, local index) and (fine patch, local index) per edge
+    for (int qc : lpc)
+      for (const auto& kc : edge_cand[qc]) {
+        const Key& key = kc.first;
+        const int Le = kc.second[1], bf = kc.second[2], bl = kc.second[3];
+        auto it = edge_best.find(key);
+        if (it == edge_best.end()) edge_best[key] = kc.second;
+        else {
+          auto& v = it->second;
+          if (qc < v[0] || (qc == v[0] && Le < v[1])) { v[0] = qc; v[1] = Le; }
+          if (bf < v[2] || (bf == v[2] && bl < v[3])) { v[2] = bf; v[3] = bl; }
+        }
+      }
     // emit C/F faces (qc ascending, then (d, Lface)), reflux cells, restriction lists
     std::vector<std::array<int, 9>> rrows;
-    std::map<std::pair<int, int>, size_t> rrow_of;  // (qc, Lcell) -> index in rrows
+    std::unordered_map<std::pair<int, int>, size_t, PairHash> rrow_of;  // (qc, Lcell) -> index in rrows
     for (int qc : level_patches[lc]) {
       auto& v = face_rows[qc];
       std::sort(v.begin(), v.end());
@@ -595,17 +645,38 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     std::vector<std::pair<std::array<int, 6>, Key>> erows;
     for (auto& kv : edge_best) erows.push_back({{l, kv.second[0], kv.first.c, kv.second[1], kv.second[2], kv.second[3]}, kv.first});
     std::sort(erows.begin(), erows.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    std::map<Key, int> edge_row;
+    std::unordered_map<Key, int, KeyHash> edge_row;
     for (auto& e : erows) {
       edge_row[e.second] = (int)(cf_edges.size() / 6);
       cf_edges.insert(cf_edges.end(), e.first.begin(), e.first.end());
     }
     // EMF-corrected faces: every stored copy of an uncovered face touching a C/F edge
     {
-      std::vector<std::array<int, 8>> all;
-      for (int qc : level_patches[lc]) {
+      std::vector<std::vector<std::array<int, 8>>> per(np);
+#pragma omp parallel for schedule(dynamic, 1)
+      for (size_t ip = 0; ip < lpc.size(); ++ip) {
+        const int qc = lpc[ip];
         const HPatch& C = p[qc];
         const int k0 = dim == 3 ? C.lo[2] : 0, k1 = dim == 3 ? C.hi[2] : 1;
+        // cells within one cell of a covered cell: only faces touching one can
+        // touch a C/F edge
+        const int e0 = C.n[0] + 2, e1 = C.n[1] + 2, e2 = dim == 3 ? C.n[2] + 2 : 1;
+        std::vector<char> near((size_t)e0 * e1 * e2, 0);
+        for (int z = 0; z < e2; ++z)
+          for (int y = 0; y < e1; ++y)
+            for (int x = 0; x < e0; ++x) {
+              if (covmaps[qc][((size_t)z * e1 + y) * e0 + x].c < 0) continue;
+              for (int cz = (dim == 3 ? z - 1 : 0); cz <= (dim == 3 ? z + 1 : 0); ++cz)
+                for (int cy = y - 1; cy <= y + 1; ++cy)
+                  for (int cx = x - 1; cx <= x + 1; ++cx)
+                    if (cz >= 0 && cz < e2 && cy >= 0 && cy < e1 && cx >= 0 && cx < e0)
+                      near[((size_t)cz * e1 + cy) * e0 + cx] = 1;
+            }
+        auto near_at = [&](const int* g) {
+          const int z = dim == 3 ? g[2] - C.lo[2] + 1 : 0;
+          return near[((size_t)z * e1 + (g[1] - C.lo[1] + 1)) * e0 + (g[0] - C.lo[0] + 1)] != 0;
+        };
+        std::vector<std::array<int, 8>>& all = per[qc];
         for (int d = 0; d < dim; ++d) {
           const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
           for (int k = k0; k < k1 + (d == 2 ? 1 : 0); ++k)
@@ -613,6 +684,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
               for (int i = C.lo[0]; i < C.hi[0] + (d == 0 ? 1 : 0); ++i) {
                 int g[3] = {i, j, k}, gm[3] = {i, j, k};
                 gm[d] -= 1;
+                if (!near_at(g) && !near_at(gm)) continue;
                 if (cov_at(qc, g).c >= 0 || cov_at(qc, gm).c >= 0) continue;
                 int e[4] = {-1, -1, -1, -1};
                 bool any = false;
@@ -630,6 +702,8 @@ int Hierarchy::build(const int32_t* rows7, int n) {
               }
         }
       }
+      std::vector<std::array<int, 8>> all;
+      for (int qc : lpc) all.insert(all.end(), per[qc].begin(), per[qc].end());
       std::sort(all.begin(), all.end());
       for (auto& r : all) emf_faces.insert(emf_faces.end(), r.begin(), r.end());
     }

@@ -57,17 +57,26 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
   int nb[3];
   for (int d = 0; d < 3; ++d) nb[d] = d < dim ? region.n[d] / kBlock : 1;
   auto bi = [&](int a, int b, int c) { return ((size_t)c * nb[1] + b) * nb[0] + a; };
+  // blocks holding a buffered flag (found from the flags' neighbourhoods)
+  std::vector<uint8_t> want((size_t)nb[0] * nb[1] * nb[2], 0);
+  std::vector<size_t> wanted;
+  for (size_t f = 0; f + 2 < flags.size(); f += 3)
+    for (int c = -2 * kz; c <= 2 * kz; ++c)
+      for (int b = -2; b <= 2; ++b)
+        for (int a = -2; a <= 2; ++a) {
+          int p[3] = {flags[f] + a, flags[f + 1] + b, dim == 3 ? flags[f + 2] + c : 0};
+          if (!inside(p)) continue;
+          if (!buf.v[buf.at(p[0], p[1], p[2])]) continue;
+          const size_t w = bi(p[0] / kBlock, p[1] / kBlock, dim == 3 ? p[2] / kBlock : 0);
+          if (!want[w]) { want[w] = 1; wanted.push_back(w); }
+        }
+  std::sort(wanted.begin(), wanted.end());
   std::vector<uint8_t> ok((size_t)nb[0] * nb[1] * nb[2], 0);
-  for (int c = 0; c < nb[2]; ++c)
-    for (int b = 0; b < nb[1]; ++b)
-      for (int a = 0; a < nb[0]; ++a) {
+  for (size_t w : wanted) {
+    const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
+    {
         const int lo[3] = {a * kBlock, b * kBlock, dim == 3 ? c * kBlock : 0};
         const int hi[3] = {lo[0] + kBlock, lo[1] + kBlock, dim == 3 ? lo[2] + kBlock : 1};
-        bool want = false;
-        for (int k = lo[2]; k < hi[2] && !want; ++k)
-          for (int j = lo[1]; j < hi[1] && !want; ++j)
-            for (int i = lo[0]; i < hi[0] && !want; ++i) want = buf.v[buf.at(i, j, k)] != 0;
-        if (!want) continue;
         // proper nesting: every cell within 3 of the block is in the region
         bool allowed = true;
         for (int k = lo[2] - 3 * kz; k < hi[2] + 3 * kz && allowed; ++k)
@@ -78,12 +87,13 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
               if (!region.v[region.at(p[0], p[1], p[2])]) allowed = false;
             }
         if (allowed) ok[bi(a, b, c)] = 1;
-      }
+    }
+  }
   std::vector<std::array<int, 7>> out;
-  for (int c = 0; c < nb[2]; ++c)
-    for (int b = 0; b < nb[1]; ++b)
-      for (int a = 0; a < nb[0]; ++a) {
-        if (!ok[bi(a, b, c)]) continue;
+  for (size_t w : wanted) {
+    const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
+    {
+        if (!ok[w]) continue;
         int sx = 1, sy = 1, sz = 1;
         while (sx < kMaxBlocks && a + sx < nb[0] && ok[bi(a + sx, b, c)]) ++sx;
         auto row = [&](int bb, int cc) {
@@ -112,7 +122,8 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
         p[5] = 2 * kBlock * (b + sy);
         p[6] = dim == 3 ? 2 * kBlock * (c + sz) : 1;
         out.push_back(p);
-      }
+    }
+  }
   return out;
 }
 
@@ -190,9 +201,26 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
     }
     return -1;
   };
+  const std::vector<int> all_old = oldp;
   for (int q : Hn.level_patches[lf]) {
     const HPatch& P = Hn.p[q];
     const int kz = dim == 3 ? 1 : 0;
+    // old fine patches meeting this patch grown by 2 cells (periodic images included)
+    oldp.clear();
+    for (int o : all_old) {
+      const HPatch& Q = Ho.p[o];
+      bool meet = true;
+      for (int d = 0; d < dim && meet; ++d) {
+        const int n = Hn.N(lf, d);
+        bool m = false;
+        for (int sft = -1; sft <= 1; ++sft) {
+          if (!Hn.per[d] && sft != 0) continue;
+          if (Q.lo[d] + sft * n < P.hi[d] + 2 && P.lo[d] - 2 < Q.hi[d] + sft * n) m = true;
+        }
+        meet = m;
+      }
+      if (meet) oldp.push_back(o);
+    }
     // cells
     for (int k = P.lo[2]; k < P.hi[2]; ++k)
       for (int j = P.lo[1]; j < P.hi[1]; ++j)

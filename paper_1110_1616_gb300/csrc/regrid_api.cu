@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -19,6 +20,11 @@
 using namespace amrapi;
 
 namespace {
+
+long long now_us() {
+  return std::chrono::duration_cast<std::chrono::microseconds>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 #define CUR(call)                                                                                  \
   do {                                                                                             \
@@ -173,16 +179,20 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     for (int d = 0; d < 3; ++d) { p.lo[d] = ctx->H.p[q].lo[d]; p.hi[d] = ctx->H.p[q].hi[d]; }
     ps.push_back(p);
   }
+  long long us[4] = {0, 0, 0, 0}, t0 = now_us();
   // level 0 of the old context: fill and flag
   int nl = 0;
   op_fill(ctx, 0, 1, &nl);
   std::vector<int32_t> flags;
   st = flag_level(ctx, ctx, 0, theta, flags);
   if (st) return st;
+  us[0] += now_us() - t0;
   amrmhd_ctx* prev = ctx;
   const amrmhd::Hierarchy* prevH = &ctx->H;
   for (int l = 0; l + 1 < max_levels; ++l) {
+    t0 = now_us();
     std::vector<std::array<int, 7>> boxes = amrmhd::regrid_boxes(*prevH, l, flags);
+    us[1] += now_us() - t0;
     if (boxes.empty()) break;
     std::vector<amrmhd_patch> next = ps;
     for (const auto& b : boxes) {
@@ -192,16 +202,22 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
       next.push_back(p);
     }
     amrmhd_ctx* S = nullptr;
+    t0 = now_us();
     st = make_stage(ctx, next, &S);
+    us[2] += now_us() - t0;
+    t0 = now_us();
     if (!st) st = copy_levels(ctx, prev, S, l);
     if (!st) {
       for (int q = 0; q <= l; ++q) op_fill(S, q, 1, &nl);
       st = transfer(ctx, S, ctx, l + 1);
     }
+    us[3] += now_us() - t0;
     if (!st) {
+      t0 = now_us();
       op_fill(S, l + 1, 1, &nl);
       flags.clear();
       if (l + 2 < max_levels) st = flag_level(ctx, S, l + 1, theta, flags);
+      us[0] += now_us() - t0;
     }
     if (st) {
       if (S) amrmhd_destroy(S);
@@ -231,6 +247,7 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
   std::swap(ctx->own_stream, prev->own_stream);
   ctx->launches += prev->launches;
   amrmhd_destroy(prev);
+  for (int i = 0; i < 4; ++i) ctx->regrid_us[i] = us[i];
   return AMRMHD_OK;
 }
 

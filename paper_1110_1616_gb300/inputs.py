@@ -525,6 +525,43 @@ def clumps_3d_small(n=16, nlev=2, n_clumps=3, radius=0.1, seed=3, b_pert=0.3, ga
                    meta={"centres": centres, "radius": radius})
 
 
+def clumps_3d(base=32, nlev=6, n_clumps=8, radius=0.02, seed=3, margin=6, gamma=GAMMA):
+    """The deep clump workload: 3D, base^3 level 0 in 16^3 patches, nlev
+    levels around 8 seeded dense clumps (contrast 100, radius 0.02, uniformly
+    placed) in pressure equilibrium (p = 1), advected by v = (1, 0, 0) along
+    B = (sqrt 2, 0, 0) (plasma beta 1). The state is given per patch
+    (packed_clumps): whole-level arrays of the finest levels would not fit."""
+    centres = clump_centres(3, n_clumps, seed)
+    b = (base, base, base)
+    patches = tile(0, (0, 0, 0), b, 16, 3) + clump_boxes(3, b, nlev, centres, radius, margin=margin)
+    return Problem("clumps_3d", 3, b, patches, nlev, None, gamma=gamma,
+                   meta={"centres": centres, "radius": radius, "seed": seed})
+
+
+def packed_clumps(pb, patches=None):
+    """The 8 packed field arrays (field-major; patches in id order; a patch's
+    interior cells, or its own faces along the field's direction, x fastest)
+    of the clump state of pb on the given patch list."""
+    patches = pb.patches if patches is None else patches
+    centres, radius = pb.meta["centres"], pb.meta["radius"]
+    b0 = math.sqrt(2.0)
+    out = [[] for _ in range(8)]
+    for (l, lo, hi) in patches:
+        n = [pb.base[d] << l for d in range(3)]
+        xs = [(np.arange(lo[d], hi[d]) + 0.5) / n[d] for d in range(3)]
+        z, y, x = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+        rho, vx, vy, vz, p = clump_cells(x, y, z, 3, centres, radius)
+        e = _energy(rho, vx, vy, vz, p, b0, 0.0, 0.0, pb.gamma)
+        for f, a in enumerate((rho, rho * vx, rho * vy, rho * vz, e)):
+            out[f].append(a.ravel())
+        shp = [hi[d] - lo[d] for d in range(3)]
+        for d, val in ((0, b0), (1, 0.0), (2, 0.0)):
+            s = list(shp)
+            s[d] += 1
+            out[5 + d].append(np.full(int(np.prod(s)), val))
+    return [np.concatenate(a) for a in out]
+
+
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
     """A random properly nested periodic hierarchy: level 0 tiled by patches
     of random widths; finer levels a few random boxes aligned to parent cells,
