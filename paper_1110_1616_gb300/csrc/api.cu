@@ -118,12 +118,17 @@ void offset_regs(amrmhd_ctx* ctx, RowArgs& a, int l) {
 void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   ctx->start[l] = ctx->cur[l];
   const LevelDev& L = ctx->lev[l];
-  RowArgs a = row_args(ctx, L.same_cells, l);
+  // an advance of the interior alone (w = 0) reads ghosts 2 cells deep
+  const bool near = l == 0 || s == 2;
+  RowArgs a = row_args(ctx, near ? L.run_cells2 : L.run_cells, l);
   a.fbuf = state_buf(ctx, ctx->cur[l]);
-  ctx->ops->fill_same_cells(a, ctx->stream, nl);
-  a.rows = L.same_faces.p;
-  a.nrows = L.same_faces.n;
-  ctx->ops->fill_same_faces(a, ctx->stream, nl);
+  a.chunks = near ? L.chunk_cells2.p : L.chunk_cells.p;
+  a.nrows = near ? L.chunk_cells2.n : L.chunk_cells.n;
+  ctx->ops->fill_runs_cells(a, ctx->stream, nl);
+  a.rows = near ? L.run_faces2.p : L.run_faces.p;
+  a.chunks = near ? L.chunk_faces2.p : L.chunk_faces.p;
+  a.nrows = near ? L.chunk_faces2.n : L.chunk_faces.n;
+  ctx->ops->fill_runs_faces(a, ctx->stream, nl);
   if (s == 1 && l > 0) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
     b.fbuf = state_buf(ctx, ctx->cur[l]);
@@ -134,13 +139,15 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
     ctx->ops->prolong_faces(b, ctx->stream, nl);
   }
   // physical boundaries last: their sources are domain cells filled above
-  if (L.bc_cells.n || L.bc_faces.n) {
-    RowArgs c = row_args(ctx, L.bc_cells, l);
+  const DevList& bcc = near ? L.bc_cells2 : L.bc_cells;
+  const DevList& bcf = near ? L.bc_faces2 : L.bc_faces;
+  if (bcc.n || bcf.n) {
+    RowArgs c = row_args(ctx, bcc, l);
     c.fbuf = state_buf(ctx, ctx->cur[l]);
     for (int f = 0; f < 8; ++f) c.inflow[f] = ctx->cfg.inflow[f];
     ctx->ops->fill_bc_cells(c, ctx->stream, nl);
-    c.rows = L.bc_faces.p;
-    c.nrows = L.bc_faces.n;
+    c.rows = bcf.p;
+    c.nrows = bcf.n;
     ctx->ops->fill_bc_faces(c, ctx->stream, nl);
   }
 }
@@ -526,6 +533,113 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     }
     bool ok = upload(sc, L.same_cells, 4) && upload(pc, L.prol_cells, 4) && upload(sf, L.same_faces, 5) &&
               upload(pf, L.prol_faces, 5) && upload(bcc, L.bc_cells, 5) && upload(bcf, L.bc_faces, 6);
+    // the same-level copies as boxes: rows grouped by (destination, [face
+    // direction,] source, coordinate shift) and each group's positions merged
+    // greedily into boxes (x runs, then y, then z); blocks take chunks of at
+    // most 64 cells of one box
+    auto make_boxes = [&](const std::vector<int32_t>& rows, int w, std::vector<int32_t>& boxes,
+                          std::vector<int32_t>& chunks) {
+      const bool faces = w == 5;
+      std::vector<std::array<int, 9>> cells;  // dst, d, src, da, db, dc, a, b, c
+      cells.reserve(rows.size() / w);
+      for (size_t r = 0; r < rows.size(); r += w) {
+        const int32_t* x = &rows[r];
+        const int dst = x[0], d = faces ? x[1] : 0, Ld = x[faces ? 2 : 1], src = x[faces ? 3 : 2],
+                  Ls = x[faces ? 4 : 3];
+        const amrmhd::HPatch &D = H.p[dst], &S = H.p[src];
+        const int a0 = Ld % D.ext[0], b0 = (Ld / D.ext[0]) % D.ext[1], c0 = Ld / (D.ext[0] * D.ext[1]);
+        const int a1 = Ls % S.ext[0], b1 = (Ls / S.ext[0]) % S.ext[1], c1 = Ls / (S.ext[0] * S.ext[1]);
+        cells.push_back({dst, d, src, a1 - a0, b1 - b0, c1 - c0, a0, b0, c0});
+      }
+      std::sort(cells.begin(), cells.end(), [](const std::array<int, 9>& u, const std::array<int, 9>& v) {
+        for (int k = 0; k < 6; ++k)
+          if (u[k] != v[k]) return u[k] < v[k];
+        if (u[8] != v[8]) return u[8] < v[8];
+        if (u[7] != v[7]) return u[7] < v[7];
+        return u[6] < v[6];
+      });
+      for (size_t g0 = 0; g0 < cells.size();) {
+        size_t g1 = g0;
+        while (g1 < cells.size() && std::equal(cells[g1].begin(), cells[g1].begin() + 6, cells[g0].begin())) ++g1;
+        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+        for (size_t i = g0; i < g1; ++i)
+          for (int e = 0; e < 3; ++e) {
+            lo[e] = std::min(lo[e], cells[i][6 + e]);
+            hi[e] = std::max(hi[e], cells[i][6 + e] + 1);
+          }
+        const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+        std::vector<uint8_t> m((size_t)ex * ey * ez, 0);  // 1 present, 2 assigned
+        auto at = [&](int x, int y, int z) -> uint8_t& { return m[((size_t)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])]; };
+        for (size_t i = g0; i < g1; ++i) at(cells[i][6], cells[i][7], cells[i][8]) = 1;
+        const std::array<int, 9>& k = cells[g0];
+        const amrmhd::HPatch &D = H.p[k[0]], &S = H.p[k[2]];
+        for (size_t i = g0; i < g1; ++i) {
+          const int x0 = cells[i][6], y0 = cells[i][7], z0 = cells[i][8];
+          if (at(x0, y0, z0) != 1) continue;
+          int nx = 1, ny = 1, nz = 1;
+          while (x0 + nx < hi[0] && at(x0 + nx, y0, z0) == 1) ++nx;
+          auto row_ok = [&](int y, int z) {
+            for (int t = 0; t < nx; ++t)
+              if (at(x0 + t, y, z) != 1) return false;
+            return true;
+          };
+          while (y0 + ny < hi[1] && row_ok(y0 + ny, z0)) ++ny;
+          auto slab_ok = [&](int z) {
+            for (int u = 0; u < ny; ++u)
+              if (!row_ok(y0 + u, z)) return false;
+            return true;
+          };
+          while (z0 + nz < hi[2] && slab_ok(z0 + nz)) ++nz;
+          for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+              for (int x = 0; x < nx; ++x) at(x0 + x, y0 + y, z0 + z) = 2;
+          const int Ld = x0 + D.ext[0] * (y0 + D.ext[1] * z0);
+          const int Ls = (x0 + k[3]) + S.ext[0] * ((y0 + k[4]) + S.ext[1] * (z0 + k[5]));
+          const int bi = (int)(boxes.size() / (faces ? 8 : 7));
+          if (faces) boxes.insert(boxes.end(), {k[0], k[1], Ld, k[2], Ls, nx, ny, nz});
+          else boxes.insert(boxes.end(), {k[0], Ld, k[2], Ls, nx, ny, nz});
+          for (int c = 0; c < nx * ny * nz; c += 64) {
+            chunks.push_back(bi);
+            chunks.push_back(c);
+          }
+        }
+        g0 = g1;
+      }
+    };
+    std::vector<int32_t> rc, cc, rf, cf;
+    make_boxes(sc, 4, rc, cc);
+    make_boxes(sf, 5, rf, cf);
+    // rows of ghosts within 2 cells of the interior (faces: either adjacent cell)
+    auto depth = [&](int q, int L, int dshift) {  // Chebyshev depth of local cell L (shifted by -1 along dshift)
+      const amrmhd::HPatch& P = H.p[q];
+      int c[3] = {L % P.ext[0], (L / P.ext[0]) % P.ext[1], L / (P.ext[0] * P.ext[1])};
+      if (dshift >= 0) c[dshift] -= 1;
+      int dep = 0;
+      for (int e = 0; e < H.dim; ++e) {
+        if (c[e] < 4) dep = std::max(dep, 4 - c[e]);
+        if (c[e] >= P.n[e] + 4) dep = std::max(dep, c[e] - (P.n[e] + 3));
+      }
+      return dep;
+    };
+    auto near_rows = [&](const std::vector<int32_t>& rows, int w, bool face) {
+      std::vector<int32_t> out;
+      for (size_t r = 0; r < rows.size(); r += w) {
+        const int32_t* x = &rows[r];
+        bool keep;
+        if (!face) keep = depth(x[0], x[1], -1) <= 2;
+        else keep = std::min(depth(x[0], x[2], -1), depth(x[0], x[2], x[1])) <= 2;
+        if (keep) out.insert(out.end(), x, x + w);
+      }
+      return out;
+    };
+    std::vector<int32_t> rc2, cc2, rf2, cf2;
+    make_boxes(near_rows(sc, 4, false), 4, rc2, cc2);
+    make_boxes(near_rows(sf, 5, true), 5, rf2, cf2);
+    ok = ok && upload(rc2, L.run_cells2, 7) && upload(cc2, L.chunk_cells2, 2) && upload(rf2, L.run_faces2, 8) &&
+         upload(cf2, L.chunk_faces2, 2) && upload(near_rows(bcc, 5, false), L.bc_cells2, 5) &&
+         upload(near_rows(bcf, 6, true), L.bc_faces2, 6);
+    ok = ok && upload(rc, L.run_cells, 7) && upload(cc, L.chunk_cells, 2) && upload(rf, L.run_faces, 8) &&
+         upload(cf, L.chunk_faces, 2);
     if (l > 0 && ok) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
         return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);

@@ -23,6 +23,11 @@ struct LevelDev {
   int maxn[3] = {1, 1, 1};
   DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
   DevList bc_cells, bc_faces;                               // physical boundaries (kinds 2, 3)
+  DevList run_cells, run_faces;      // same-level copies as boxes (7 / 8 ints per box)
+  DevList chunk_cells, chunk_faces;  // (box, first cell) per block of at most 64 cells
+  // the same for the ghosts within 2 cells of the interior (all that an advance
+  // of the interior alone reads): used for sub-steps with w = 0
+  DevList run_cells2, run_faces2, chunk_cells2, chunk_faces2, bc_cells2, bc_faces2;
   DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
   int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
 };

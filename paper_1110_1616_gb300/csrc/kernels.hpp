@@ -56,6 +56,8 @@ struct RowArgs {
   const DPatch* P2;
   const void* obuf;
   const double* K;
+  // box copies: chunk table (box, first cell) per block
+  const int* chunks;
 };
 
 struct CflArgs {
@@ -78,6 +80,9 @@ struct Ops {
   void (*reg_fine)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
   void (*fill_same_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_same_faces)(const RowArgs&, cudaStream_t, int* launches);
+  // the same copies as boxes (rows = boxes, nrows = chunks of at most 256 cells)
+  void (*fill_runs_cells)(const RowArgs&, cudaStream_t, int* launches);
+  void (*fill_runs_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_bc_cells)(const RowArgs&, cudaStream_t, int* launches);

@@ -348,6 +348,53 @@ template <class T, int DIM> __global__ void k_fill_same_faces(RowArgs a) {
   ((T*)a.fbuf)[D.off + f * D.fs + row[2]] = ((const T*)a.fbuf)[S.off + f * S.fs + row[4]];
 }
 
+// Same-level copies as boxes: box records (dst, Ldst0, src, Lsrc0, nx, ny, nz)
+// for cells, (dst, d, Ldst0, src, Lsrc0, nx, ny, nz) for faces: the box of nx x
+// ny x nz positions starting at Ldst0 in patch dst takes the positions starting
+// at Lsrc0 in patch src (strides of each patch's own storage). chunks[2c],
+// chunks[2c+1] = (box, first cell) of block c (at most FILL_TPB cells of one box;
+// small blocks keep the threads busy on boxes of ~100 cells).
+constexpr int FILL_TPB = 64;
+template <int W>
+__device__ __forceinline__ bool box_cell(const int* boxes, const int* chunks, const DPatch* P, const int*& box,
+                                         long long& Ld, long long& Ls) {
+  const int bi = chunks[2 * blockIdx.x];
+  const int c = chunks[2 * blockIdx.x + 1] + threadIdx.x;
+  box = boxes + W * bi;
+  const int nx = box[W - 3], ny = box[W - 2], nz = box[W - 1];
+  if (c >= nx * ny * nz) return false;
+  const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+  const DPatch& D = P[box[0]];
+  const DPatch& S = P[box[W - 5]];
+  Ld = box[W - 6] + x + (long long)D.ext[0] * (y + (long long)D.ext[1] * z);
+  Ls = box[W - 4] + x + (long long)S.ext[0] * (y + (long long)S.ext[1] * z);
+  return true;
+}
+
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_cells(RowArgs a) {
+  const int* box;
+  long long Ld, Ls;
+  if (!box_cell<7>(a.rows, a.chunks, a.P, box, Ld, Ls)) return;
+  const DPatch D = a.P[box[0]], S = a.P[box[2]];
+  T* dst = (T*)a.fbuf + D.off + Ld;
+  const T* src = (const T*)a.fbuf + S.off + Ls;
+  constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+  for (int n = 0; n < NCF; ++n) {
+    const int f = n < 5 ? n : BZ;
+    dst[f * D.fs] = src[f * S.fs];
+  }
+}
+
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_faces(RowArgs a) {
+  const int* box;
+  long long Ld, Ls;
+  if (!box_cell<8>(a.rows, a.chunks, a.P, box, Ld, Ls)) return;
+  const DPatch D = a.P[box[0]], S = a.P[box[3]];
+  const int f = BX + box[1];
+  ((T*)a.fbuf)[D.off + f * D.fs + Ld] = ((const T*)a.fbuf)[S.off + f * S.fs + Ls];
+}
+
 // physical boundary cells: rows (dst, Ldst, kind, src, Lsrc); kind 2 copies
 // the patch's own nearest domain cell, kind 3 sets the inflow state
 template <class T, int DIM> __global__ void k_fill_bc_cells(RowArgs a) {
@@ -732,12 +779,17 @@ __device__ __forceinline__ double warp_max(double v) {
 // per-cell rate sum_d (|v_d| + c_f,d)/dx_d; FP64 path: all FP64 (bitwise with a
 // plain FP64 evaluation); mixed path: the FP64-balanced recovery of
 // recover_t and FP32 fast speeds, the maximum carried in FP64
+// cells per thread of the CFL reduction: one atomic per block of TPB x CFL_CPT
+// cells (a single address takes every block's atomic)
+constexpr int CFL_CPT = 4;
+
 template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs a) {
   const DPatch P = a.P[a.ids[blockIdx.y]];
   int i, j, k;
-  double rate = 0.0;
+  T tmax = T(0);  // per-thread maximum in the working type; the reduction is FP64
   bool bad = false;
-  if (region_cell<DIM>(P, 0, blockIdx.x * TPB + threadIdx.x, i, j, k)) {
+  for (int tc = blockIdx.x * TPB + threadIdx.x;; tc += gridDim.x * TPB) {
+    if (!region_cell<DIM>(P, 0, tc, i, j, k)) break;
     const int L = lidx(P, i, j, k);
     const long long fs = P.fs;
     const T* U = (const T*)a.cur + P.off;
@@ -759,12 +811,12 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
         const T cf = cfast<T>(w[0], w[4], w[5 + d], w[5 + t], w[5 + uu], g);
         rr = rr + (dabs(w[1 + d]) + cf) * (T)a.idx[d];
       }
-      if (!(rr == rr) || (double)rr > 1.79e308) bad = true;
-      else rate = (double)rr;
+      if (!(rr < (T)INFINITY)) bad = true;  // NaN or infinite
+      else if (rr > tmax) tmax = rr;
     }
   }
   if (bad) atomicOr(a.err, 1u);
-  rate = warp_max(rate);
+  double rate = warp_max((double)tmax);
   __shared__ double red[TPB / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
   __syncthreads();
@@ -838,6 +890,16 @@ template <class T, int DIM> struct Impl {
   AMRK_ROWS(prolong_faces)
   AMRK_ROWS(fill_bc_cells)
   AMRK_ROWS(fill_bc_faces)
+  static void fill_runs_cells(const RowArgs& a, cudaStream_t s, int* nl) {
+    if (!a.nrows) return;
+    k_fill_box_cells<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
+    if (nl) ++*nl;
+  }
+  static void fill_runs_faces(const RowArgs& a, cudaStream_t s, int* nl) {
+    if (!a.nrows) return;
+    k_fill_box_faces<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
+    if (nl) ++*nl;
+  }
   AMRK_ROWS(transfer_cells)
   AMRK_ROWS(transfer_faces)
   AMRK_ROWS(closure)
@@ -849,7 +911,7 @@ template <class T, int DIM> struct Impl {
   static void cfl(const CflArgs& a, cudaStream_t s, int* nl) {
     long long n = 1;
     for (int d = 0; d < DIM; ++d) n *= a.maxn[d];
-    k_cfl<T, DIM><<<dim3(cdiv(n, TPB), a.npatch), TPB, 0, s>>>(a);
+    k_cfl<T, DIM><<<dim3(cdiv(n, TPB * CFL_CPT), a.npatch), TPB, 0, s>>>(a);
     if (nl) ++*nl;
   }
   static void flag(const LevelArgs& a, double theta, int* out, unsigned long long* count, long long cap,
@@ -907,7 +969,8 @@ template <class T, int DIM> struct Impl {
     if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
   }
   static const Ops* ops() {
-    static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, prolong_cells,
+    static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, fill_runs_cells,
+                          fill_runs_faces, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
                           transfer_faces, closure};
