@@ -31,6 +31,10 @@ UNIT = "cell-updates/s"
 # by running the oracle's per-cell formulas with a counting scalar type
 # (oracle/opcount.cpp, 2000 subsonic samples, seed 1; tests/test_oracle_opcount.py).
 FLOPS_PER_CELL_UPDATE_3D = 1504.0
+# DRAM bytes (read + write) of one launch of the fused advance on the 128^3
+# blast in 16^3 patches, mixed precision, from one ncu capture of that launch
+# (224.92 MB read + 75.82 MB written; profiles/k_advance3d_fused_blast3d_128.md)
+FUSED_TRAFFIC_BYTES = 300.74e6
 # FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock
 SMS, FP32_LANES = 152, 128
 
@@ -176,26 +180,22 @@ def advance_alone(ctx, stream, reps):
 
 
 def e2e_run(pb, precision, k):
-    """Through the C ABI with host buffers: every step uploads the state from
-    pinned host memory, advances one coarse step and reads the state back."""
+    """Through the C ABI with host buffers: every step uploads the whole state
+    from pinned host memory (one copy), advances one coarse step and reads the
+    whole state back (one copy)."""
     import numpy as np
     import torch
-    ctx, stream = make_ctx(pb, precision)
-    host_in = []
-    for f in range(8):
-        a = torch.from_numpy(ctx.pack(pb.state, f)).pin_memory()
-        host_in.append(a)
-    host_out = [torch.empty_like(a).pin_memory() for a in host_in]
-    from paper_1110_1616_gb300 import amrmhd as A
-    lib = A.lib()
     import ctypes as C
+    from paper_1110_1616_gb300 import amrmhd as A
+    ctx, stream = make_ctx(pb, precision)
+    host_in = torch.from_numpy(np.concatenate([ctx.pack(pb.state, f) for f in range(8)])).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    lib = A.lib()
 
     def one():
-        for f in range(8):
-            ctx._check(lib.amrmhd_set_state_packed(ctx.h, f, C.c_void_p(host_in[f].data_ptr()), 0), "set")
+        ctx._check(lib.amrmhd_set_state_all(ctx.h, C.c_void_p(host_in.data_ptr()), 0), "set_all")
         ctx.step(1, want_dt=False)
-        for f in range(8):
-            ctx._check(lib.amrmhd_get_state_packed(ctx.h, f, C.c_void_p(host_out[f].data_ptr()), 0), "get")
+        ctx._check(lib.amrmhd_get_state_all(ctx.h, C.c_void_p(host_out.data_ptr()), 0), "get_all")
 
     one()
     torch.cuda.synchronize()
@@ -204,12 +204,121 @@ def e2e_run(pb, precision, k):
         one()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
-    nbytes = sum(a.numel() * 8 for a in host_in)
+    nbytes = host_in.numel() * 8
     cells = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
     del ctx
     torch.cuda.empty_cache()
-    _ = np
     return cells * k / t, nbytes
+
+
+def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
+    """The deep clump workload (3D, 32^3 base, 6 levels around 8 dense clumps):
+    mixed precision, concurrent levels, autotuned tiles; a regrid every
+    regrid_every coarse steps. Steps are timed with CUDA events on the
+    launching stream; the regrid (host clustering and map building, device
+    flagging and transfer) with the host clock."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    pb = inputs.clumps_3d()
+    stream = torch.cuda.Stream()
+    ctx = A.Context(A.make_config(3, pb.base, precision=A.MIXED, gamma=pb.gamma, cfl=pb.cfl), stream.cuda_stream)
+    ctx.set_hierarchy(pb.patches)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    for f, a in enumerate(inputs.packed_clumps(pb)):
+        ctx.set_field_packed(f, a)
+    ctx.regrid(theta, pb.nlev)
+    tiles = ctx.autotune(3)
+    ctx.step(1, want_dt=False)
+    updates, t_steps, t_regrid, breakdown = 0, 0.0, 0.0, [0, 0, 0, 0]
+    nreg = 0
+    for i in range(0, steps, regrid_every):
+        k = min(regrid_every, steps - i)
+        per = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
+        ms, _ = timed_steps(ctx, stream, k)
+        t_steps += ms / 1e3
+        updates += per * k
+        if i + k < steps:
+            t0 = time.perf_counter()
+            ctx.regrid(theta, pb.nlev)
+            t_regrid += time.perf_counter() - t0
+            nreg += 1
+            for q in range(4):
+                breakdown[q] += ctx.query(A.Q_REGRID_FLAG_US + q)
+            ctx.autotune(2)
+    ms_c, _ = timed_steps(ctx, stream, 2)
+    ctx.set_option(A.OPT_CONCURRENT, 0)
+    ctx.step(1, want_dt=False)
+    ms_s, _ = timed_steps(ctx, stream, 2)
+    cells = {}
+    for (l, lo, hi) in ctx.get_patches():
+        cells[l] = cells.get(l, 0) + (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
+    out = {"value": updates / t_steps, "unit": UNIT, "with_regrid": updates / (t_steps + t_regrid),
+           "steps": steps, "regrid_every": regrid_every, "theta": theta, "regrids": nreg,
+           "regrid_ms_mean": 1e3 * t_regrid / max(nreg, 1),
+           "regrid_host_us_mean": {k: v / max(nreg, 1) for k, v in
+                                   zip(("flag", "cluster", "build", "transfer"), breakdown)},
+           "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
+           "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
+           "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_leg(steps=200, ckpt=20):
+    """The adjoint workload (2D, 256^2 base in 32^2 patches + refined quadrant):
+    forward amrmhd_step_dt and amrmhd_backward with checkpoints every ckpt
+    coarse steps for a fixed dt sequence, FP64 and mixed precision; the seed is
+    the derivative of 0.5 sum (rho - rho_target)^2 over the level-0 cells with
+    rho_target the final density of a second seed's forward run."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    pb = inputs.adjoint_2d(seed=4)
+    pt = inputs.adjoint_2d(seed=5)
+    out = {"workload": "adjoint_2d_256_q: 256^2 base + refined quadrant, Alfven wave + smooth dv, %d steps, "
+                       "checkpoint every %d" % (steps, ckpt)}
+    for name, prec in (("fp64", A.FP64), ("mixed", A.MIXED)):
+        stream = torch.cuda.Stream()
+        ctx = A.context_for(pb, precision=prec, strict_fp64=False, stream=stream.cuda_stream)
+        ctx.alloc_arena()
+        torch.cuda.synchronize()
+        ctx.load_state(pb.state)
+        dts = [0.8 * ctx.cfl_dt()] * steps
+        n0 = sum((hi[0] - lo[0]) * (hi[1] - lo[1]) for (l, lo, hi) in pb.patches if l == 0)
+        tgt = A.context_for(pt, precision=prec, strict_fp64=False, stream=stream.cuda_stream)
+        tgt.alloc_arena()
+        torch.cuda.synchronize()
+        tgt.load_state(pt.state)
+        tgt.step_dt(dts)
+        rho_t = tgt.get_field_packed(0)[:n0]
+        del tgt
+        import numpy as np
+        u0 = torch.tensor(np.concatenate([ctx.pack(pb.state, f) for f in range(8)]), dtype=torch.float64,
+                          device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_dt(dts)
+        t_fwd = time.perf_counter() - t0
+        uf = torch.empty_like(u0)
+        ctx.read_packed_all(uf)
+        torch.cuda.synchronize()
+        g = torch.zeros_like(u0)
+        g[:n0] = uf[:n0] - torch.tensor(rho_t, dtype=torch.float64, device="cuda")
+        ctx.load_packed_all(u0)
+        g0 = torch.empty_like(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.backward(dts, g, g0, ckpt)
+        t_bwd = time.perf_counter() - t0
+        per = pb.cells_per_coarse_step()
+        out[name] = {"forward_cell_updates_per_s": per * steps / t_fwd, "forward_s": t_fwd, "backward_s": t_bwd,
+                     "backward_over_forward": t_bwd / t_fwd, "grad_norm": float(g0.norm())}
+        del ctx
+        torch.cuda.empty_cache()
+    return out
 
 
 def cpu_oracle_rate(pb, steps=1):
@@ -319,6 +428,8 @@ def main():
         extras["speedup_vs_fp64_one_patch_per_launch"] = value / world / vb
         del ctxb
         torch.cuda.empty_cache()
+        extras["deep_amr_clumps3d"] = deep_amr_leg()
+        extras["adjoint_2d"] = adjoint_leg()
     e2e = None
     if not args.skip_extras:
         ke = max(3, args.steps // 10)
@@ -344,7 +455,10 @@ def main():
                      "achieved": flops_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": flops_achieved / fp32_peak,
                      "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (SMS, FP32_LANES, sm_max),
-                     "traffic": None, "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
+                     "traffic": FUSED_TRAFFIC_BYTES if args.n == 128 and args.psize == 16 else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
+                                       "this kernel on this workload (profiles/k_advance3d_fused_blast3d_128.md)",
+                     "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
                      "ms_per_launch": t_adv},
         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",

@@ -127,6 +127,15 @@ amrmhd_status amrmhd_packed_size(amrmhd_ctx* ctx, int32_t field, int64_t* count)
 amrmhd_status amrmhd_set_state_packed(amrmhd_ctx* ctx, int32_t field, const double* src, int32_t src_on_device);
 amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* dst, int32_t dst_on_device);
 
+/* The whole state as one packed array: the 8 packed fields of
+ * amrmhd_set_state_packed one after the other (field 0's array, then field
+ * 1's, ...; the amrmhd_backward layout). With a host pointer the data moves in
+ * one copy per direction through a library-owned staging buffer (allocated on
+ * first use) and the call synchronises the stream; with a device pointer it is
+ * stream-ordered. */
+amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device);
+amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_device);
+
 /* Exports integer map `which` (AMRMHD_MAP_*) as rows of int32; *width receives
  * the row width, *len the total int count; up to cap ints are written to dst
  * (host memory; dst may be NULL to query the size). Host-only. Row formats:

@@ -71,6 +71,8 @@ def lib():
             "amrmhd_cfl_dt": [vp, C.POINTER(dbl)],
             "amrmhd_step": [vp, i32, vp],
             "amrmhd_step_dt": [vp, i32, vp],
+            "amrmhd_set_state_all": [vp, vp, i32],
+            "amrmhd_get_state_all": [vp, vp, i32],
             "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
             "amrmhd_regrid": [vp, dbl, i32],
             "amrmhd_autotune": [vp, i32, vp],

@@ -11,7 +11,7 @@ LIB = os.path.join(OUT, "libamrmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 UNITS = [
-    ("api.cu", []),
+    ("api.cu", ["-Xcompiler", "-fopenmp"]),
     # FP32 division and square root without IEEE rounding (FP64 code is unaffected)
     ("kernels_fast.cu", ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]),
     ("kernels_strict.cu", ["--fmad=false"]),

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ctx.hpp"
@@ -46,6 +47,7 @@ void free_device(amrmhd_ctx* ctx) {
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
   for (void* p : ctx->dev_allocs) cudaFree(p);
   ctx->dev_allocs.clear();
+  ctx->d_stage_all = nullptr;
   ctx->lev.clear();
   ctx->bound = false;
 }
@@ -540,70 +542,102 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     auto make_boxes = [&](const std::vector<int32_t>& rows, int w, std::vector<int32_t>& boxes,
                           std::vector<int32_t>& chunks) {
       const bool faces = w == 5;
-      std::vector<std::array<int, 9>> cells;  // dst, d, src, da, db, dc, a, b, c
-      cells.reserve(rows.size() / w);
-      for (size_t r = 0; r < rows.size(); r += w) {
-        const int32_t* x = &rows[r];
-        const int dst = x[0], d = faces ? x[1] : 0, Ld = x[faces ? 2 : 1], src = x[faces ? 3 : 2],
-                  Ls = x[faces ? 4 : 3];
-        const amrmhd::HPatch &D = H.p[dst], &S = H.p[src];
-        const int a0 = Ld % D.ext[0], b0 = (Ld / D.ext[0]) % D.ext[1], c0 = Ld / (D.ext[0] * D.ext[1]);
-        const int a1 = Ls % S.ext[0], b1 = (Ls / S.ext[0]) % S.ext[1], c1 = Ls / (S.ext[0] * S.ext[1]);
-        cells.push_back({dst, d, src, a1 - a0, b1 - b0, c1 - c0, a0, b0, c0});
-      }
-      std::sort(cells.begin(), cells.end(), [](const std::array<int, 9>& u, const std::array<int, 9>& v) {
-        for (int k = 0; k < 6; ++k)
-          if (u[k] != v[k]) return u[k] < v[k];
-        if (u[8] != v[8]) return u[8] < v[8];
-        if (u[7] != v[7]) return u[7] < v[7];
-        return u[6] < v[6];
-      });
-      for (size_t g0 = 0; g0 < cells.size();) {
-        size_t g1 = g0;
-        while (g1 < cells.size() && std::equal(cells[g1].begin(), cells[g1].begin() + 6, cells[g0].begin())) ++g1;
-        int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
-        for (size_t i = g0; i < g1; ++i)
-          for (int e = 0; e < 3; ++e) {
-            lo[e] = std::min(lo[e], cells[i][6 + e]);
-            hi[e] = std::max(hi[e], cells[i][6 + e] + 1);
+      const int bw = faces ? 8 : 7;
+      // rows come grouped by destination patch: one segment per patch
+      std::vector<size_t> seg;
+      for (size_t r = 0; r < rows.size(); r += w)
+        if (r == 0 || rows[r] != rows[r - w]) seg.push_back(r);
+      seg.push_back(rows.size());
+      const int nseg = (int)seg.size() - 1;
+      std::vector<std::vector<int32_t>> out(std::max(nseg, 0));
+#pragma omp parallel for schedule(dynamic, 1)
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        // groups by (direction, source, coordinate shift), in order of first appearance;
+        // rows arrive in z,y,x order, so every group is too
+        std::vector<std::array<int, 5>> keys;
+        std::vector<std::vector<std::array<int, 3>>> pos;
+        std::unordered_map<uint64_t, int> gid;
+        for (size_t r = seg[sgi]; r < seg[sgi + 1]; r += w) {
+          const int32_t* x = &rows[r];
+          const int dst = x[0], d = faces ? x[1] : 0, Ld = x[faces ? 2 : 1], src = x[faces ? 3 : 2],
+                    Ls = x[faces ? 4 : 3];
+          const amrmhd::HPatch &D = H.p[dst], &S = H.p[src];
+          const int a0 = Ld % D.ext[0], b0 = (Ld / D.ext[0]) % D.ext[1], c0 = Ld / (D.ext[0] * D.ext[1]);
+          const int a1 = Ls % S.ext[0], b1 = (Ls / S.ext[0]) % S.ext[1], c1 = Ls / (S.ext[0] * S.ext[1]);
+          const std::array<int, 5> k = {d, src, a1 - a0, b1 - b0, c1 - c0};
+          uint64_t h = 1469598103934665603ull;
+          for (int v : k) h = (h ^ (uint32_t)v) * 1099511628211ull;
+          auto it = gid.find(h);
+          int g = -1;
+          if (it != gid.end() && keys[it->second] == k) g = it->second;
+          if (g < 0) {
+            for (size_t t = 0; t < keys.size() && g < 0; ++t)
+              if (keys[t] == k) g = (int)t;  // hash collision: fall back to a scan
+            if (g < 0) {
+              g = (int)keys.size();
+              keys.push_back(k);
+              pos.emplace_back();
+              gid[h] = g;
+            }
           }
-        const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-        std::vector<uint8_t> m((size_t)ex * ey * ez, 0);  // 1 present, 2 assigned
-        auto at = [&](int x, int y, int z) -> uint8_t& { return m[((size_t)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])]; };
-        for (size_t i = g0; i < g1; ++i) at(cells[i][6], cells[i][7], cells[i][8]) = 1;
-        const std::array<int, 9>& k = cells[g0];
-        const amrmhd::HPatch &D = H.p[k[0]], &S = H.p[k[2]];
-        for (size_t i = g0; i < g1; ++i) {
-          const int x0 = cells[i][6], y0 = cells[i][7], z0 = cells[i][8];
-          if (at(x0, y0, z0) != 1) continue;
-          int nx = 1, ny = 1, nz = 1;
-          while (x0 + nx < hi[0] && at(x0 + nx, y0, z0) == 1) ++nx;
-          auto row_ok = [&](int y, int z) {
-            for (int t = 0; t < nx; ++t)
-              if (at(x0 + t, y, z) != 1) return false;
-            return true;
+          pos[g].push_back({a0, b0, c0});
+        }
+        const int dst = rows[seg[sgi]];
+        const amrmhd::HPatch& D = H.p[dst];
+        std::vector<int32_t>& ob = out[sgi];
+        for (size_t g = 0; g < keys.size(); ++g) {
+          const std::array<int, 5>& k = keys[g];
+          const amrmhd::HPatch& S = H.p[k[1]];
+          int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+          for (const auto& c : pos[g])
+            for (int e = 0; e < 3; ++e) {
+              lo[e] = std::min(lo[e], c[e]);
+              hi[e] = std::max(hi[e], c[e] + 1);
+            }
+          const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+          std::vector<uint8_t> m((size_t)ex * ey * ez, 0);  // 1 present, 2 assigned
+          auto at = [&](int x, int y, int z) -> uint8_t& {
+            return m[((size_t)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])];
           };
-          while (y0 + ny < hi[1] && row_ok(y0 + ny, z0)) ++ny;
-          auto slab_ok = [&](int z) {
-            for (int u = 0; u < ny; ++u)
-              if (!row_ok(y0 + u, z)) return false;
-            return true;
-          };
-          while (z0 + nz < hi[2] && slab_ok(z0 + nz)) ++nz;
-          for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-              for (int x = 0; x < nx; ++x) at(x0 + x, y0 + y, z0 + z) = 2;
-          const int Ld = x0 + D.ext[0] * (y0 + D.ext[1] * z0);
-          const int Ls = (x0 + k[3]) + S.ext[0] * ((y0 + k[4]) + S.ext[1] * (z0 + k[5]));
-          const int bi = (int)(boxes.size() / (faces ? 8 : 7));
-          if (faces) boxes.insert(boxes.end(), {k[0], k[1], Ld, k[2], Ls, nx, ny, nz});
-          else boxes.insert(boxes.end(), {k[0], Ld, k[2], Ls, nx, ny, nz});
-          for (int c = 0; c < nx * ny * nz; c += 64) {
+          for (const auto& c : pos[g]) at(c[0], c[1], c[2]) = 1;
+          for (const auto& c : pos[g]) {
+            const int x0 = c[0], y0 = c[1], z0 = c[2];
+            if (at(x0, y0, z0) != 1) continue;
+            int nx = 1, ny = 1, nz = 1;
+            while (x0 + nx < hi[0] && at(x0 + nx, y0, z0) == 1) ++nx;
+            auto row_ok = [&](int y, int z) {
+              for (int t = 0; t < nx; ++t)
+                if (at(x0 + t, y, z) != 1) return false;
+              return true;
+            };
+            while (y0 + ny < hi[1] && row_ok(y0 + ny, z0)) ++ny;
+            auto slab_ok = [&](int z) {
+              for (int u = 0; u < ny; ++u)
+                if (!row_ok(y0 + u, z)) return false;
+              return true;
+            };
+            while (z0 + nz < hi[2] && slab_ok(z0 + nz)) ++nz;
+            for (int z = 0; z < nz; ++z)
+              for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) at(x0 + x, y0 + y, z0 + z) = 2;
+            const int Ld = x0 + D.ext[0] * (y0 + D.ext[1] * z0);
+            const int Ls = (x0 + k[2]) + S.ext[0] * ((y0 + k[3]) + S.ext[1] * (z0 + k[4]));
+            if (faces) ob.insert(ob.end(), {dst, k[0], Ld, k[1], Ls, nx, ny, nz});
+            else ob.insert(ob.end(), {dst, Ld, k[1], Ls, nx, ny, nz});
+          }
+        }
+      }
+      for (int sgi = 0; sgi < nseg; ++sgi) {
+        const int first = (int)(boxes.size() / bw);
+        boxes.insert(boxes.end(), out[sgi].begin(), out[sgi].end());
+        for (int bi = first; bi < (int)(boxes.size() / bw); ++bi) {
+          const int* bx = &boxes[(size_t)bi * bw];
+          const int vol = bx[bw - 3] * bx[bw - 2] * bx[bw - 1];
+          for (int c = 0; c < vol; c += 64) {
             chunks.push_back(bi);
             chunks.push_back(c);
           }
         }
-        g0 = g1;
       }
     };
     std::vector<int32_t> rc, cc, rf, cf;
@@ -751,6 +785,53 @@ amrmhd_status amrmhd_set_state_packed(amrmhd_ctx* ctx, int32_t field, const doub
 amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* dst, int32_t on_device) {
   if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
   return io_one(ctx, 0, field, dst, on_device, 0, true);
+}
+
+// all 8 packed fields one after the other (the amrmhd_backward layout)
+static amrmhd_status io_all(amrmhd_ctx* ctx, double* buf, int32_t on_device, int to_state) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  const amrmhd::Hierarchy& H = ctx->H;
+  long long total = 0, off[8];
+  for (int f = 0; f < 8; ++f) {
+    const int kind = (f >= 5 && !(H.dim == 2 && f == 7)) ? f - 4 : 0;
+    off[f] = total;
+    total += ctx->ptotal[kind];
+  }
+  double* dev = buf;
+  if (!on_device) {
+    if (!ctx->d_stage_all) {
+      cudaError_t e = cudaSuccess;
+      ctx->d_stage_all = dbuf<double>(ctx, (size_t)total, &e);
+      if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, "staging buffer");
+    }
+    dev = ctx->d_stage_all;
+    if (to_state) CU(cudaMemcpyAsync(dev, buf, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  for (int f = 0; f < 8; ++f) {
+    const int kind = (f >= 5 && !(H.dim == 2 && f == 7)) ? f - 4 : 0;
+    for (int l = 0; l < H.nlev; ++l) {
+      const LevelDev& L = ctx->lev[l];
+      int lm[3] = {L.maxn[0], L.maxn[1], L.maxn[2]};
+      int nl = 0;
+      ctx->ops->io(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev + off[f], ctx->d_poff[kind], f,
+                   to_state, ctx->stream, &nl);
+    }
+  }
+  if (!to_state && !on_device)
+    CU(cudaMemcpyAsync(buf, dev, total * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device) {
+  if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
+  return io_all(ctx, (double*)src, on_device, 1);
+}
+
+amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_device) {
+  if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
+  return io_all(ctx, dst, on_device, 0);
 }
 
 amrmhd_status amrmhd_export_map(amrmhd_ctx* ctx, int32_t which, int32_t* dst, int64_t cap, int64_t* len,

@@ -71,6 +71,7 @@ struct amrmhd_ctx {
   unsigned long long* d_slots = nullptr;  // per-level CFL maxima + step counter
   unsigned int* d_err = nullptr;
   double* d_hist = nullptr;
+  double* d_stage_all = nullptr;  // staging of the whole packed state (lazy)
   int64_t hist_cap = 0;
   std::vector<amrapi::LevelDev> lev;
   std::vector<int> cur, start;

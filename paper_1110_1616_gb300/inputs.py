@@ -562,6 +562,43 @@ def packed_clumps(pb, patches=None):
     return [np.concatenate(a) for a in out]
 
 
+def adjoint_2d(n=256, psize=32, seed=4, amp=1e-4, kmax=8, rms=1e-4, gamma=GAMMA):
+    """The adjoint workload: n^2 periodic base in psize^2 patches plus one
+    refined level over the quadrant [0, 1/2)^2 (its C/F boundary crosses the
+    periodic seam); the circularly polarised Alfven wave of amplitude amp plus
+    a seeded smooth velocity perturbation sum_{|k| <= kmax} a_k cos(2 pi k.x +
+    phi_k) per component (a_k ~ N(0,1), phi_k ~ U[0, 2 pi)), rescaled to an rms
+    of rms."""
+    rng = np.random.default_rng(seed)
+    ks = [(kx, ky) for kx in range(-kmax, kmax + 1) for ky in range(-kmax, kmax + 1)
+          if 0 < kx * kx + ky * ky <= kmax * kmax]
+    coef = rng.normal(size=(len(ks), 3))
+    phase = rng.uniform(0, 2 * math.pi, size=(len(ks), 3))
+    base = (n, n, 1)
+    patches = tile(0, (0, 0, 0), base, psize, 2) + tile(1, (0, 0, 0), (n, n, 1), psize, 2)
+    state = {}
+    scale = None
+    for l in range(2):
+        m = n << l
+        st = alfven_2d_state(m, amp, 0.0, gamma)
+        x, y, _ = _cell_centres((m, m, 1), (0, 0, 0), (1, 1, 1), 2)
+        dv = np.zeros((3,) + x.shape)
+        for i, (kx, ky) in enumerate(ks):
+            for c in range(3):
+                dv[c] += coef[i, c] * np.cos(2 * math.pi * (kx * x + ky * y) + phase[i, c])
+        if scale is None:
+            scale = rms / np.sqrt((dv ** 2).mean())
+        dv *= scale
+        rho = st[0]
+        v = [st[1 + c] / rho + dv[c] for c in range(3)]
+        ke_old = 0.5 * (st[1] ** 2 + st[2] ** 2 + st[3] ** 2) / rho
+        for c in range(3):
+            st[1 + c] = rho * v[c]
+        st[4] = st[4] - ke_old + 0.5 * rho * (v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+        state[l] = st
+    return Problem("adjoint_2d", 2, base, patches, 2, state, gamma=gamma, meta={"seed": seed})
+
+
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
     """A random properly nested periodic hierarchy: level 0 tiled by patches
     of random widths; finer levels a few random boxes aligned to parent cells,

@@ -329,3 +329,19 @@ def test_autotune_picks_a_tile_per_level_and_keeps_results():
     for f in range(8):
         for p in range(len(pb.patches)):
             assert np.array_equal(sa[f][p], sb[f][p]), (f, p)
+
+
+def test_whole_state_packed_io_round_trip():
+    """amrmhd_set_state_all / get_state_all (host pointers) move the same
+    values as the per-field packed calls."""
+    import ctypes as C
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    ctx = gpu_for(pb, A.FP64)
+    ref = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    out = np.empty_like(ref)
+    ctx._check(A.lib().amrmhd_get_state_all(ctx.h, out.ctypes.data_as(C.c_void_p), 0), "get_all")
+    assert np.array_equal(out, ref)
+    new = ref * 1.5
+    ctx._check(A.lib().amrmhd_set_state_all(ctx.h, new.ctypes.data_as(C.c_void_p), 0), "set_all")
+    back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    assert np.array_equal(back, new)
