@@ -267,6 +267,49 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     return out
 
 
+def shock_clump_leg(steps=10, theta=0.1):
+    """The shock-clump workload (3D, 64^3 base, 5 levels, Mach-10 shock into a
+    lognormal fractal clump, inflow at x-low and outflow elsewhere), mixed
+    precision: the state is generated per patch on the nested initial boxes,
+    one regrid (theta) builds the flagged hierarchy (its host time reported),
+    then `steps` coarse steps are timed with CUDA events."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    pb = inputs.shock_clump_3d()
+    fields = inputs.packed_shock_clump(pb)
+    stream = torch.cuda.Stream()
+    cfg = A.make_config(3, pb.base, precision=A.MIXED, gamma=pb.gamma, cfl=pb.cfl, bc=pb.bc, inflow=pb.inflow)
+    ctx = A.Context(cfg, stream.cuda_stream)
+    ctx.set_hierarchy(pb.patches)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    for f, a in enumerate(fields):
+        ctx.set_field_packed(f, a)
+    ctx.step(1, want_dt=False)
+    t0 = time.perf_counter()
+    ctx.regrid(theta, pb.nlev)
+    t_regrid = time.perf_counter() - t0
+    tiles = ctx.autotune(2)
+    ctx.step(1, want_dt=False)
+    per = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
+    ms, launches = timed_steps(ctx, stream, steps)
+    cells = {}
+    for (l, lo, hi) in ctx.get_patches():
+        cells[l] = cells.get(l, 0) + (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
+    out = {"value": per * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+           "cells_per_level": [cells[l] for l in sorted(cells)], "patches": ctx.query(A.Q_NPATCH),
+           "arena_gb": ctx.query(A.Q_ARENA_BYTES) / 1e9, "regrid_s": t_regrid,
+           "regrid_host_us": {k: ctx.query(A.Q_REGRID_FLAG_US + i)
+                              for i, k in enumerate(("flag", "cluster", "build", "transfer"))},
+           "tiles": tiles,
+           "workload": "shock_clump3d_64_5lev: Mach-10 shock into a lognormal (sigma 1, slope -11/3, contrast 10) "
+                       "clump r 0.15; B (sqrt2,0,0); inflow x-low, outflow elsewhere; mixed precision"}
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
 def adjoint_leg(steps=200, ckpt=20):
     """The adjoint workload (2D, 256^2 base in 32^2 patches + refined quadrant):
     forward amrmhd_step_dt and amrmhd_backward with checkpoints every ckpt
@@ -318,6 +361,46 @@ def adjoint_leg(steps=200, ckpt=20):
                      "backward_over_forward": t_bwd / t_fwd, "grad_norm": float(g0.norm())}
         del ctx
         torch.cuda.empty_cache()
+    return out
+
+
+def mixed_error_leg():
+    """Relative L1 error per field of the mixed path against the strict FP64
+    path (which matches the oracle to 1e-12), per config, with the same dt
+    sequence: Orszag-Tang (config-1 hierarchy, 50 coarse steps), the 3D blast at
+    64^3 (20 steps), the finite-amplitude Alfven wave (40 steps)."""
+    import numpy as np
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    names = ["rho", "mx", "my", "mz", "E", "bx", "by", "bz"]
+    cases = [("orszag_tang_64_amr", inputs.orszag_tang(64, 16, refine=True, noise=1e-3, seed=1), 50),
+             ("blast3d_64", inputs.blast_3d(64, 16), 20),
+             ("alfven_2d_64_amp0.1", inputs.alfven_2d(64, 16, amp=1e-1), 40)]
+    out = {}
+    for name, pb, steps in cases:
+        res = {}
+        ref, dts = None, None
+        for prec in (A.FP64, A.MIXED):
+            stream = torch.cuda.Stream()
+            ctx = A.context_for(pb, precision=prec, strict_fp64=True, stream=stream.cuda_stream)
+            ctx.alloc_arena()
+            torch.cuda.synchronize()
+            ctx.load_state(pb.state)
+            if dts is None:
+                dts = list(ctx.step(steps))
+            else:
+                ctx.step_dt(dts)
+            st = [ctx.get_field_packed(f) for f in range(8)]
+            if ref is None:
+                ref = st
+            else:
+                for f in range(8):
+                    den = np.abs(ref[f]).sum()
+                    res[names[f]] = float(np.abs(st[f] - ref[f]).sum() / den) if den > 0 else float(np.abs(st[f]).sum())
+            del ctx
+            torch.cuda.empty_cache()
+        out[name] = res
     return out
 
 
@@ -428,8 +511,10 @@ def main():
         extras["speedup_vs_fp64_one_patch_per_launch"] = value / world / vb
         del ctxb
         torch.cuda.empty_cache()
+        extras["mixed_rel_l1_vs_fp64"] = mixed_error_leg()
         extras["deep_amr_clumps3d"] = deep_amr_leg()
         extras["adjoint_2d"] = adjoint_leg()
+        extras["shock_clump3d"] = shock_clump_leg()
     e2e = None
     if not args.skip_extras:
         ke = max(3, args.steps // 10)

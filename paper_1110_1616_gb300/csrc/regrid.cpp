@@ -27,10 +27,13 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
   const int dim = H.dim;
   Dense region, buf;
   for (int d = 0; d < 3; ++d) region.n[d] = buf.n[d] = H.N(l, d);
-  region.v.assign((size_t)region.n[0] * region.n[1] * region.n[2], 0);
-  buf.v.assign(region.v.size(), 0);
-  for (int q : H.level_patches[l]) {
-    const HPatch& P = H.p[q];
+  const size_t ncell = (size_t)region.n[0] * region.n[1] * region.n[2];
+  region.v.assign(ncell, 0);
+  buf.v.assign(ncell, 0);
+  const std::vector<int>& lp = H.level_patches[l];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (size_t ip = 0; ip < lp.size(); ++ip) {  // patches are disjoint: no shared writes
+    const HPatch& P = H.p[lp[ip]];
     for (int k = P.lo[2]; k < P.hi[2]; ++k)
       for (int j = P.lo[1]; j < P.hi[1]; ++j)
         for (int i = P.lo[0]; i < P.hi[0]; ++i) region.v[region.at(i, j, k)] = 1;
@@ -44,51 +47,63 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
     return true;
   };
   const int kz = dim == 3 ? 1 : 0;
-  for (size_t f = 0; f + 2 < flags.size(); f += 3) {
-    for (int c = -2 * kz; c <= 2 * kz; ++c)
-      for (int b = -2; b <= 2; ++b)
-        for (int a = -2; a <= 2; ++a) {
-          int p[3] = {flags[f] + a, flags[f + 1] + b, dim == 3 ? flags[f + 2] + c : 0};
-          if (!inside(p)) continue;
-          const size_t q = region.at(p[0], p[1], p[2]);
-          if (region.v[q]) buf.v[q] = 1;
+  // buffer of 2 cells: the flags dilated (Chebyshev) along x, then y, then z,
+  // then restricted to the region
+  for (size_t f = 0; f + 2 < flags.size(); f += 3) buf.v[buf.at(flags[f], flags[f + 1], dim == 3 ? flags[f + 2] : 0)] = 1;
+  for (int d = 0; d < dim; ++d) {
+    const int n = region.n[d];
+    const size_t st = d == 0 ? 1 : (d == 1 ? (size_t)region.n[0] : (size_t)region.n[0] * region.n[1]);
+    const size_t lines = ncell / n;
+    std::vector<uint8_t> src = buf.v;
+#pragma omp parallel for schedule(static)
+    for (long long li = 0; li < (long long)lines; ++li) {
+      // the line's first element: li enumerates the other two coordinates
+      size_t base;
+      if (d == 0) base = (size_t)li * n;
+      else if (d == 1) base = ((size_t)li / region.n[0]) * region.n[0] * n + (size_t)li % region.n[0];
+      else base = (size_t)li;
+      for (int x = 0; x < n; ++x) {
+        if (!src[base + x * st]) continue;
+        for (int o = -2; o <= 2; ++o) {
+          int y = x + o;
+          if (H.per[d]) y = (y % n + n) % n;
+          else if (y < 0 || y >= n) continue;
+          buf.v[base + y * st] = 1;
         }
+      }
+    }
   }
+#pragma omp parallel for schedule(static)
+  for (long long c = 0; c < (long long)ncell; ++c) buf.v[c] &= region.v[c];
   int nb[3];
   for (int d = 0; d < 3; ++d) nb[d] = d < dim ? region.n[d] / kBlock : 1;
   auto bi = [&](int a, int b, int c) { return ((size_t)c * nb[1] + b) * nb[0] + a; };
-  // blocks holding a buffered flag (found from the flags' neighbourhoods)
-  std::vector<uint8_t> want((size_t)nb[0] * nb[1] * nb[2], 0);
-  std::vector<size_t> wanted;
-  for (size_t f = 0; f + 2 < flags.size(); f += 3)
-    for (int c = -2 * kz; c <= 2 * kz; ++c)
-      for (int b = -2; b <= 2; ++b)
-        for (int a = -2; a <= 2; ++a) {
-          int p[3] = {flags[f] + a, flags[f + 1] + b, dim == 3 ? flags[f + 2] + c : 0};
-          if (!inside(p)) continue;
-          if (!buf.v[buf.at(p[0], p[1], p[2])]) continue;
-          const size_t w = bi(p[0] / kBlock, p[1] / kBlock, dim == 3 ? p[2] / kBlock : 0);
-          if (!want[w]) { want[w] = 1; wanted.push_back(w); }
-        }
-  std::sort(wanted.begin(), wanted.end());
-  std::vector<uint8_t> ok((size_t)nb[0] * nb[1] * nb[2], 0);
-  for (size_t w : wanted) {
+  const size_t nblk = (size_t)nb[0] * nb[1] * nb[2];
+  std::vector<uint8_t> ok(nblk, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long long w = 0; w < (long long)nblk; ++w) {
     const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
-    {
-        const int lo[3] = {a * kBlock, b * kBlock, dim == 3 ? c * kBlock : 0};
-        const int hi[3] = {lo[0] + kBlock, lo[1] + kBlock, dim == 3 ? lo[2] + kBlock : 1};
-        // proper nesting: every cell within 3 of the block is in the region
-        bool allowed = true;
-        for (int k = lo[2] - 3 * kz; k < hi[2] + 3 * kz && allowed; ++k)
-          for (int j = lo[1] - 3; j < hi[1] + 3 && allowed; ++j)
-            for (int i = lo[0] - 3; i < hi[0] + 3 && allowed; ++i) {
-              int p[3] = {i, j, k};
-              if (!inside(p)) continue;
-              if (!region.v[region.at(p[0], p[1], p[2])]) allowed = false;
-            }
-        if (allowed) ok[bi(a, b, c)] = 1;
-    }
+    const int lo[3] = {a * kBlock, b * kBlock, dim == 3 ? c * kBlock : 0};
+    const int hi[3] = {lo[0] + kBlock, lo[1] + kBlock, dim == 3 ? lo[2] + kBlock : 1};
+    bool want = false;
+    for (int k = lo[2]; k < hi[2] && !want; ++k)
+      for (int j = lo[1]; j < hi[1] && !want; ++j)
+        for (int i = lo[0]; i < hi[0] && !want; ++i) want = buf.v[buf.at(i, j, k)] != 0;
+    if (!want) continue;
+    // proper nesting: every cell within 3 of the block is in the region
+    bool allowed = true;
+    for (int k = lo[2] - 3 * kz; k < hi[2] + 3 * kz && allowed; ++k)
+      for (int j = lo[1] - 3; j < hi[1] + 3 && allowed; ++j)
+        for (int i = lo[0] - 3; i < hi[0] + 3 && allowed; ++i) {
+          int p[3] = {i, j, k};
+          if (!inside(p)) continue;
+          if (!region.v[region.at(p[0], p[1], p[2])]) allowed = false;
+        }
+    if (allowed) ok[w] = 1;
   }
+  std::vector<size_t> wanted;
+  for (size_t w = 0; w < nblk; ++w)
+    if (ok[w]) wanted.push_back(w);
   std::vector<std::array<int, 7>> out;
   for (size_t w : wanted) {
     const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
@@ -134,119 +149,118 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
   out.faces.clear();
   out.closure.clear();
   const bool have_old = Ho.nlev > lf;
-  // old fine patches as boxes
-  std::vector<int> oldp;
-  if (have_old) oldp = Ho.level_patches[lf];
-  auto old_cell = [&](const int* g, int* Lo) -> int {  // old fine patch holding fine cell g
-    for (int q : oldp) {
-      const HPatch& P = Ho.p[q];
-      bool in = true;
-      for (int d = 0; d < dim; ++d)
-        if (g[d] < P.lo[d] || g[d] >= P.hi[d]) in = false;
-      if (in) {
-        if (Lo) *Lo = Ho.loc(q, g[0], g[1], g[2]);
-        return q;
-      }
-    }
-    return -1;
-  };
-  auto oldcov = [&](const int* c) -> bool {  // coarse cell c covered by the old fine level
-    if (!have_old) return false;
-    for (int d = 0; d < dim; ++d)
-      if (!Hn.per[d] && (c[d] < 0 || c[d] >= Hn.N(lc, d))) return false;
-    int g[3];
-    for (int d = 0; d < 3; ++d) g[d] = d < dim ? 2 * Hn.wrapd(lc, d, c[d]) : 0;
-    return old_cell(g, nullptr) >= 0;
-  };
-  // owner of fine d-face g in the old fine level: smallest (patch, local index)
-  auto old_face = [&](int d, const int* g, int* Lo) -> int {
-    int best = -1, bl = 0;
-    for (int q : oldp) {
-      const HPatch& P = Ho.p[q];
-      bool in = true;
-      for (int e = 0; e < dim; ++e) {
-        if (e == d) { if (g[e] < P.lo[e] || g[e] > P.hi[e]) in = false; }
-        else if (g[e] < P.lo[e] || g[e] >= P.hi[e]) in = false;
-      }
-      if (!in) continue;
-      const int L = Ho.loc(q, g[0], g[1], g[2]);
-      if (best < 0 || q < best || (q == best && L < bl)) { best = q; bl = L; }
-    }
-    *Lo = bl;
-    return best;
-  };
-  // new coarse patch holding coarse cell c (after periodic wrap)
-  auto coarse = [&](int qf, int* c, int* Lc) -> int {
-    int w[3];
-    for (int d = 0; d < 3; ++d) w[d] = d < dim ? Hn.wrapd(lc, d, c[d]) : 0;
-    for (int Q : Hn.parents[qf]) {
-      const HPatch& P = Hn.p[Q];
-      bool in = true;
-      for (int d = 0; d < dim; ++d)
-        if (w[d] < P.lo[d] || w[d] >= P.hi[d]) in = false;
-      if (in) {
-        *Lc = Hn.loc(Q, w[0], w[1], w[2]);
-        return Q;
-      }
-    }
-    for (int Q : Hn.level_patches[lc]) {
-      const HPatch& P = Hn.p[Q];
-      bool in = true;
-      for (int d = 0; d < dim; ++d)
-        if (w[d] < P.lo[d] || w[d] >= P.hi[d]) in = false;
-      if (in) {
-        *Lc = Hn.loc(Q, w[0], w[1], w[2]);
-        return Q;
-      }
-    }
-    return -1;
-  };
-  const std::vector<int> all_old = oldp;
-  for (int q : Hn.level_patches[lf]) {
+  const std::vector<int> empty;
+  const std::vector<int>& oldp = have_old ? Ho.level_patches[lf] : empty;
+  const std::vector<int>& newp = Hn.level_patches[lf];
+  const int np = (int)newp.size();
+  std::vector<TransferMaps> per(np);
+  std::vector<int> status(np, 0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int ip = 0; ip < np; ++ip) {
+    const int q = newp[ip];
     const HPatch& P = Hn.p[q];
-    const int kz = dim == 3 ? 1 : 0;
-    // old fine patches meeting this patch grown by 2 cells (periodic images included)
-    oldp.clear();
-    for (int o : all_old) {
-      const HPatch& Q = Ho.p[o];
-      bool meet = true;
-      for (int d = 0; d < dim && meet; ++d) {
-        const int n = Hn.N(lf, d);
-        bool m = false;
-        for (int sft = -1; sft <= 1; ++sft) {
-          if (!Hn.per[d] && sft != 0) continue;
-          if (Q.lo[d] + sft * n < P.hi[d] + 2 && P.lo[d] - 2 < Q.hi[d] + sft * n) m = true;
-        }
-        meet = m;
-      }
-      if (meet) oldp.push_back(o);
+    TransferMaps& o = per[ip];
+    // owner map over the patch grown by 2 fine cells (unwrapped positions):
+    // the old fine patch (and its periodic shift) holding each fine cell
+    int glo[3], gex[3];
+    for (int d = 0; d < 3; ++d) {
+      glo[d] = d < dim ? P.lo[d] - 2 : 0;
+      gex[d] = d < dim ? P.n[d] + 4 : 1;
     }
+    const size_t gsz = (size_t)gex[0] * gex[1] * gex[2];
+    std::vector<int> own(gsz, -1), shf(gsz, 0);
+    auto gi = [&](const int* g) -> long long {
+      for (int d = 0; d < 3; ++d)
+        if (g[d] < glo[d] || g[d] >= glo[d] + gex[d]) return -1;
+      return ((long long)(g[2] - glo[2]) * gex[1] + (g[1] - glo[1])) * gex[0] + (g[0] - glo[0]);
+    };
+    for (int oq : oldp) {
+      const HPatch& Q = Ho.p[oq];
+      int sr[3][2];
+      for (int d = 0; d < 3; ++d) {
+        const bool per = d < dim && Hn.per[d];
+        sr[d][0] = per ? -1 : 0;
+        sr[d][1] = per ? 1 : 0;
+      }
+      for (int sz = sr[2][0]; sz <= sr[2][1]; ++sz)
+        for (int sy = sr[1][0]; sy <= sr[1][1]; ++sy)
+          for (int sx = sr[0][0]; sx <= sr[0][1]; ++sx) {
+            const int s3[3] = {sx, sy, sz};
+            int a0[3], a1[3];
+            bool any = true;
+            for (int d = 0; d < 3; ++d) {
+              const int off = d < dim ? s3[d] * Hn.N(lf, d) : 0;
+              a0[d] = std::max(glo[d], (d < dim ? Q.lo[d] : 0) + off);
+              a1[d] = std::min(glo[d] + gex[d], (d < dim ? Q.hi[d] : 1) + off);
+              if (a1[d] <= a0[d]) any = false;
+            }
+            if (!any) continue;
+            const int code = (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1);
+            for (int z = a0[2]; z < a1[2]; ++z)
+              for (int y = a0[1]; y < a1[1]; ++y)
+                for (int x = a0[0]; x < a1[0]; ++x) {
+                  const int g[3] = {x, y, z};
+                  const long long k = gi(g);
+                  if (own[k] < 0) { own[k] = oq; shf[k] = code; }
+                }
+          }
+    }
+    // local index in the old patch of the position g seen through the owner's shift
+    auto old_loc = [&](long long k, const int* g) {
+      const int code = shf[k];
+      const int s3[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+      int w[3];
+      for (int d = 0; d < 3; ++d) w[d] = d < dim ? g[d] - s3[d] * Hn.N(lf, d) : 0;
+      return Ho.loc(own[k], w[0], w[1], w[2]);
+    };
+    auto oldcov = [&](const int* c) -> bool {  // coarse cell c covered by the old fine level
+      if (!have_old) return false;
+      int g[3];
+      for (int d = 0; d < 3; ++d) g[d] = d < dim ? 2 * c[d] : 0;
+      const long long k = gi(g);
+      return k >= 0 && own[k] >= 0;
+    };
+    // new coarse patch holding coarse cell c (after periodic wrap)
+    auto coarse = [&](int* c, int* Lc) -> int {
+      int w[3];
+      for (int d = 0; d < 3; ++d) w[d] = d < dim ? Hn.wrapd(lc, d, c[d]) : 0;
+      auto inside = [&](int Q) {
+        const HPatch& C = Hn.p[Q];
+        for (int d = 0; d < dim; ++d)
+          if (w[d] < C.lo[d] || w[d] >= C.hi[d]) return false;
+        return true;
+      };
+      for (int Q : Hn.parents[q])
+        if (inside(Q)) { *Lc = Hn.loc(Q, w[0], w[1], w[2]); return Q; }
+      for (int Q : Hn.level_patches[lc])
+        if (inside(Q)) { *Lc = Hn.loc(Q, w[0], w[1], w[2]); return Q; }
+      return -1;
+    };
     // cells
     for (int k = P.lo[2]; k < P.hi[2]; ++k)
       for (int j = P.lo[1]; j < P.hi[1]; ++j)
         for (int i = P.lo[0]; i < P.hi[0]; ++i) {
-          int g[3] = {i, j, k};
+          const int g[3] = {i, j, k};
           int c[3] = {i >> 1, j >> 1, dim == 3 ? k >> 1 : 0};
           const int L = Hn.loc(q, i, j, k);
           if (oldcov(c)) {
-            int Lo = 0;
-            const int o = old_cell(g, &Lo);
-            out.cells.insert(out.cells.end(), {q, L, 0, o, Lo});
+            const long long kk = gi(g);
+            o.cells.insert(o.cells.end(), {q, L, 0, own[kk], old_loc(kk, g)});
           } else {
             int Lc = 0;
-            const int Q = coarse(q, c, &Lc);
-            if (Q < 0) return -1;
-            out.cells.insert(out.cells.end(), {q, L, 1, Q, Lc});
+            const int Q = coarse(c, &Lc);
+            if (Q < 0) { status[ip] = -1; break; }
+            o.cells.insert(o.cells.end(), {q, L, 1, Q, Lc});
           }
         }
     // own faces
-    for (int d = 0; d < dim; ++d) {
+    for (int d = 0; d < dim && !status[ip]; ++d) {
       int hi[3] = {P.hi[0], P.hi[1], P.hi[2]};
       hi[d] += 1;
       for (int k = P.lo[2]; k < hi[2]; ++k)
         for (int j = P.lo[1]; j < hi[1]; ++j)
           for (int i = P.lo[0]; i < hi[0]; ++i) {
-            int g[3] = {i, j, k};
+            const int g[3] = {i, j, k};
             int m[3] = {i, j, k};
             m[d] -= 1;
             int pq[3] = {i >> 1, j >> 1, dim == 3 ? k >> 1 : 0};
@@ -255,34 +269,31 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
             const bool copy = interior ? oldcov(pq) : (oldcov(pq) || oldcov(pm));
             const int L = Hn.loc(q, i, j, k);
             if (copy) {
-              int gw[3];
-              for (int e = 0; e < 3; ++e) gw[e] = e < dim ? g[e] : 0;
-              // the face as stored: wrap a periodic position into the domain
-              for (int e = 0; e < dim; ++e)
-                if (Hn.per[e] && (e != d || gw[e] != Hn.N(lf, e))) gw[e] = Hn.wrapd(lf, e, gw[e]);
-              int Lo = 0;
-              int o = old_face(d, gw, &Lo);
-              if (o < 0 && Hn.per[d] && (gw[d] == 0 || gw[d] == Hn.N(lf, d))) {
-                gw[d] = gw[d] == 0 ? Hn.N(lf, d) : 0;  // the other stored position of the seam face
-                o = old_face(d, gw, &Lo);
+              // owners of the face: the old patches holding the cells on its two sides;
+              // the smallest (patch, local index) as for ghost faces
+              int best = -1, bl = 0;
+              const long long k1 = gi(g), k0 = gi(m);
+              if (k1 >= 0 && own[k1] >= 0) { best = own[k1]; bl = old_loc(k1, g); }
+              if (k0 >= 0 && own[k0] >= 0) {
+                const int Lo = old_loc(k0, g);  // the same face position, in the low cell's patch
+                if (best < 0 || own[k0] < best || (own[k0] == best && Lo < bl)) { best = own[k0]; bl = Lo; }
               }
-              if (o < 0) return -2;
-              out.faces.insert(out.faces.end(), {q, d, L, 0, o, Lo});
+              if (best < 0) { status[ip] = -2; break; }
+              o.faces.insert(o.faces.end(), {q, d, L, 0, best, bl});
             } else {
-              // parent cell of the face position (the top face of a bounded domain
-              // indexes one past the last coarse cell)
               int c[3] = {pq[0], pq[1], pq[2]};
               const bool top = !Hn.per[d] && g[d] == Hn.N(lf, d);
               if (top) c[d] -= 1;
               int Lc = 0;
-              const int Q = coarse(q, c, &Lc);
-              if (Q < 0) return -1;
+              const int Q = coarse(c, &Lc);
+              if (Q < 0) { status[ip] = -1; break; }
               if (top) Lc += d == 0 ? 1 : (d == 1 ? Hn.p[Q].ext[0] : Hn.p[Q].ext[0] * Hn.p[Q].ext[1]);
-              out.faces.insert(out.faces.end(), {q, d, L, 1, Q, Lc});
+              o.faces.insert(o.faces.end(), {q, d, L, 1, Q, Lc});
             }
           }
     }
     // closure rows: prolonged coarse cells with an old-covered face neighbour
+    const int kz = dim == 3 ? 1 : 0;
     for (int ck = P.lo[2] >> kz; ck < (dim == 3 ? P.hi[2] >> 1 : 1); ++ck)
       for (int cj = P.lo[1] >> 1; cj < P.hi[1] >> 1; ++cj)
         for (int ci = P.lo[0] >> 1; ci < P.hi[0] >> 1; ++ci) {
@@ -290,15 +301,25 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
           if (oldcov(c)) continue;
           bool touches = false;
           for (int d = 0; d < dim; ++d)
-            for (int s = -1; s <= 1; s += 2) {
-              int n[3] = {ci, cj, ck};
-              n[d] += s;
-              touches |= oldcov(n);
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+              int nb[3] = {ci, cj, ck};
+              nb[d] += sgn;
+              // a neighbour outside a bounded domain is never covered
+              bool in = true;
+              for (int e = 0; e < dim; ++e)
+                if (!Hn.per[e] && (nb[e] < 0 || nb[e] >= Hn.N(lc, e))) in = false;
+              touches |= in && oldcov(nb);
             }
           if (!touches) continue;
-          out.closure.push_back(q);
-          out.closure.push_back(Hn.loc(q, 2 * ci, 2 * cj, dim == 3 ? 2 * ck : 0));
+          o.closure.push_back(q);
+          o.closure.push_back(Hn.loc(q, 2 * ci, 2 * cj, dim == 3 ? 2 * ck : 0));
         }
+  }
+  for (int ip = 0; ip < np; ++ip) {
+    if (status[ip]) return status[ip];
+    out.cells.insert(out.cells.end(), per[ip].cells.begin(), per[ip].cells.end());
+    out.faces.insert(out.faces.end(), per[ip].faces.begin(), per[ip].faces.end());
+    out.closure.insert(out.closure.end(), per[ip].closure.begin(), per[ip].closure.end());
   }
   return 0;
 }

@@ -599,6 +599,96 @@ def adjoint_2d(n=256, psize=32, seed=4, amp=1e-4, kmax=8, rms=1e-4, gamma=GAMMA)
     return Problem("adjoint_2d", 2, base, patches, 2, state, gamma=gamma, meta={"seed": seed})
 
 
+def fractal_field(n=256, slope=-11.0 / 3.0, seed=7):
+    """A periodic Gaussian random field on an n^3 grid with power spectrum
+    P(k) ~ k^slope (zero mean, unit variance), by filtering white noise in
+    Fourier space."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(n) * n
+    kz, ky, kx = np.meshgrid(k, k, np.fft.rfftfreq(n) * n, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(kk)
+    amp[kk > 0] = kk[kk > 0] ** (slope / 2.0)
+    noise = np.fft.rfftn(rng.normal(size=(n, n, n)))
+    g = np.fft.irfftn(noise * amp, s=(n, n, n))
+    g -= g.mean()
+    return g / g.std()
+
+
+def _trilinear(g, x, y, z):
+    """Periodic trilinear sample of the grid g (cell-centred on [0,1]^3) at points."""
+    n = g.shape[0]
+    fx, fy, fz = x * n - 0.5, y * n - 0.5, z * n - 0.5
+    i0, j0, k0 = np.floor(fx).astype(int), np.floor(fy).astype(int), np.floor(fz).astype(int)
+    tx, ty, tz = fx - i0, fy - j0, fz - k0
+    out = 0.0
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                wgt = (tx if di else 1 - tx) * (ty if dj else 1 - ty) * (tz if dk else 1 - tz)
+                out = out + wgt * g[(k0 + dk) % n, (j0 + dj) % n, (i0 + di) % n]
+    return out
+
+
+def shock_clump_3d(base=64, nlev=5, radius=0.15, centre=(0.5, 0.5, 0.5), mach=10.0, sigma=1.0, contrast=10.0,
+                   shock_x=0.1, seed=7, fft_n=256, margin=4, gamma=GAMMA):
+    """The shock-clump workload: a Mach-10 planar shock (hydrodynamic
+    Rankine-Hugoniot jump; the field B = (sqrt 2, 0, 0) lies along the normal,
+    plasma beta 1 with p = 1) at x = shock_x moving into a clump of radius
+    0.15 whose density is lognormal, rho = contrast exp(sigma G) / <exp(sigma G)>
+    with G a Gaussian random field of spectral slope -11/3 (sampled
+    trilinearly from an fft_n^3 grid), in an ambient rho = 1, p = 1 at rest.
+    Inflow of the post-shock state at x-low, outflow on every other side.
+    Level 0 in 16^3 patches; nested boxes around the clump on the finer levels.
+    The state is given per patch (packed_shock_clump)."""
+    b = (base, base, base)
+    patches = tile(0, (0, 0, 0), b, 16, 3) + clump_boxes(3, b, nlev, [centre], radius, margin=margin)
+    c1 = math.sqrt(gamma * 1.0 / 1.0)
+    rho1, u1, p1, rho2, u2, p2 = rankine_hugoniot(mach, rho1=1.0, p1=1.0, gamma=gamma)
+    us = mach * c1                  # shock speed into the gas at rest
+    u2lab = us * (1.0 - rho1 / rho2)  # post-shock gas velocity in the lab frame
+    b0 = math.sqrt(2.0)
+    post = conserved((rho2, u2lab, 0.0, 0.0, p2, b0, 0.0, 0.0), gamma)
+    return Problem("shock_clump_3d", 3, b, patches, nlev, None, gamma=gamma,
+                   bc=(2, 1, 1, 1, 1, 1), inflow=post,
+                   meta={"radius": radius, "centre": centre, "sigma": sigma, "contrast": contrast, "seed": seed,
+                         "fft_n": fft_n, "shock_x": shock_x, "post": (rho2, u2lab, p2), "b0": b0})
+
+
+def packed_shock_clump(pb, patches=None, field=None):
+    """The 8 packed field arrays of the shock-clump state of pb on the given
+    patch list (layout as packed_clumps)."""
+    patches = pb.patches if patches is None else patches
+    m = pb.meta
+    g = field if field is not None else fractal_field(m["fft_n"], seed=m["seed"])
+    mean_exp = np.exp(m["sigma"] * g).mean()
+    rho2, u2, p2 = m["post"]
+    b0 = m["b0"]
+    out = [[] for _ in range(8)]
+    for (l, lo, hi) in patches:
+        n = [pb.base[d] << l for d in range(3)]
+        xs = [(np.arange(lo[d], hi[d]) + 0.5) / n[d] for d in range(3)]
+        z, y, x = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+        r2 = (x - m["centre"][0]) ** 2 + (y - m["centre"][1]) ** 2 + (z - m["centre"][2]) ** 2
+        rho = np.ones_like(x)
+        inside = r2 < m["radius"] ** 2
+        if inside.any():
+            rho[inside] = m["contrast"] * np.exp(m["sigma"] * _trilinear(g, x[inside], y[inside], z[inside])) / mean_exp
+        p = np.ones_like(x)
+        vx = np.zeros_like(x)
+        shocked = x < m["shock_x"]
+        rho[shocked], vx[shocked], p[shocked] = rho2, u2, p2
+        e = _energy(rho, vx, 0.0, 0.0, p, b0, 0.0, 0.0, pb.gamma)
+        for f, a in enumerate((rho, rho * vx, np.zeros_like(x), np.zeros_like(x), e)):
+            out[f].append(a.ravel())
+        shp = [hi[d] - lo[d] for d in range(3)]
+        for d, val in ((0, b0), (1, 0.0), (2, 0.0)):
+            sh = list(shp)
+            sh[d] += 1
+            out[5 + d].append(np.full(int(np.prod(sh)), val))
+    return [np.concatenate(a) for a in out]
+
+
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
     """A random properly nested periodic hierarchy: level 0 tiled by patches
     of random widths; finer levels a few random boxes aligned to parent cells,
