@@ -1430,6 +1430,62 @@ int oc_tangent(void* h, int nsteps, const double* dts, const double* v0, double*
   return 0;
 }
 
+// Transposed Jacobians of single formulas by the tape (Rev): gx = J^T g.
+// The HLLD flux (R4) with x = (ql[7], qr[7], bn).
+void oc_hlld_vjp(const double* x, double gamma, double eps, const double* g, double* gx) {
+  Tape& T = tape();
+  T.clear();
+  Rev in[15];
+  for (int i = 0; i < 15; ++i) {
+    in[i] = Rev(x[i]);
+    in[i].i = T.input();
+  }
+  Rev f[7];
+  hlld<Rev>(in, in + 7, in[14], Rev(gamma), Rev(eps), f);
+  std::vector<double> adj(T.size(), 0.0);
+  for (int o = 0; o < 7; ++o)
+    if (f[o].i >= 0) adj[f[o].i] += g[o];
+  T.sweep(adj);
+  for (int i = 0; i < 15; ++i) gx[i] = adj[in[i].i];
+  T.clear();
+}
+
+// The half-step predictor of one cell (R1): wh = w - sum_d h_d A_d(w) s_d with
+// x = (w[8], s_0[8], .., s_{dim-1}[8]), as the advance forms it.
+}  // extern "C"
+template <class R> static void predict_cell(int dim, const R* x, double gamma, const double* h, R* wh) {
+  const R* w = x;
+  R ir = R(1.0) / w[0];
+  for (int f = 0; f < 8; ++f) wh[f] = w[f];
+  for (int d = 0; d < dim; ++d) {
+    R dw[8];
+    prim_rhs<R>(w, x + 8 + 8 * d, d, R(gamma), ir, dw);
+    for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h[d] * dw[f];
+  }
+}
+extern "C" {
+void oc_predict(int dim, const double* x, double gamma, const double* h, double* wh) {
+  predict_cell<double>(dim, x, gamma, h, wh);
+}
+void oc_predict_vjp(int dim, const double* x, double gamma, const double* h, const double* g, double* gx) {
+  Tape& T = tape();
+  T.clear();
+  const int nin = 8 + 8 * dim;
+  Rev in[32];
+  for (int i = 0; i < nin; ++i) {
+    in[i] = Rev(x[i]);
+    in[i].i = T.input();
+  }
+  Rev wh[8];
+  predict_cell<Rev>(dim, in, gamma, h, wh);
+  std::vector<double> adj(T.size(), 0.0);
+  for (int o = 0; o < 8; ++o)
+    if (wh[o].i >= 0) adj[wh[o].i] += g[o];
+  T.sweep(adj);
+  for (int i = 0; i < nin; ++i) gx[i] = adj[in[i].i];
+  T.clear();
+}
+
 // Stand-alone kernels for pins.
 void oc_hlld(const double* ql, const double* qr, double bn, double gamma, double eps, double* f) {
   hlld(ql, qr, bn, gamma, eps, f);

@@ -41,6 +41,9 @@ def lib():
                                    np.ctypeslib.ndpointer(dtype=np.int8)]
         L.oc_step_targets.argtypes = [C.c_void_p, C.c_double, _ip, C.c_int]
         L.oc_hlld.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, _dp]
+        L.oc_hlld_vjp.argtypes = [_dp, C.c_double, C.c_double, _dp, _dp]
+        L.oc_predict.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp]
+        L.oc_predict_vjp.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp]
         L.oc_flux.argtypes = [_dp, C.c_double, C.c_double, _dp]
         L.oc_minmod.restype = C.c_double
         L.oc_minmod.argtypes = [C.c_double, C.c_double]
@@ -251,6 +254,31 @@ def hlld(ql, qr, bn, gamma=5.0 / 3.0, eps=1e-12):
     f = np.zeros(7)
     lib().oc_hlld(np.asarray(ql, dtype=np.float64), np.asarray(qr, dtype=np.float64), bn, gamma, eps, f)
     return f
+
+
+def hlld_vjp(x, g, gamma=5.0 / 3.0, eps=1e-12):
+    """J^T g of the HLLD flux at x = (ql[7], qr[7], bn), by the oracle's tape."""
+    gx = np.zeros(15)
+    lib().oc_hlld_vjp(np.ascontiguousarray(x, dtype=np.float64), gamma, eps,
+                      np.ascontiguousarray(g, dtype=np.float64), gx)
+    return gx
+
+
+def predict(dim, x, h, gamma=5.0 / 3.0):
+    """Half-step predictor wh = w - sum_d h_d A_d(w) s_d of one cell, x = (w, s_0, .., s_{dim-1})."""
+    wh = np.zeros(8)
+    lib().oc_predict(dim, np.ascontiguousarray(x, dtype=np.float64), gamma,
+                     np.ascontiguousarray(np.resize(np.asarray(h, dtype=np.float64), 3)), wh)
+    return wh
+
+
+def predict_vjp(dim, x, h, g, gamma=5.0 / 3.0):
+    """J^T g of the half-step predictor of one cell, by the oracle's tape."""
+    gx = np.zeros(8 + 8 * dim)
+    lib().oc_predict_vjp(dim, np.ascontiguousarray(x, dtype=np.float64), gamma,
+                         np.ascontiguousarray(np.resize(np.asarray(h, dtype=np.float64), 3)),
+                         np.ascontiguousarray(g, dtype=np.float64), gx)
+    return gx
 
 
 def mhd_flux(q, bn, gamma=5.0 / 3.0):
