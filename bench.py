@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--n", type=int, default=128)
     p.add_argument("--psize", type=int, default=16)
     p.add_argument("--skip-extras", action="store_true", help="headline only (no FP64/baseline/e2e/oracle legs)")
+    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error"],
+                   help="run one extra leg alone and print its JSON (for profiling)")
+    p.add_argument("--leg-steps", type=int, default=None, help="coarse steps of the --leg run")
     return p.parse_args()
 
 
@@ -463,6 +466,15 @@ def main():
     if rank == 0 or not os.path.exists(B.LIB):
         B.build()
     barrier(world)
+    if args.leg:
+        kw = {} if args.leg_steps is None else {"steps": args.leg_steps}
+        if args.leg == "adjoint" and args.leg_steps is not None:
+            kw["ckpt"] = max(1, args.leg_steps // 2)
+        fn = {"adjoint": adjoint_leg, "deep": deep_amr_leg, "shockclump": shock_clump_leg,
+              "error": mixed_error_leg}[args.leg]
+        if rank == 0:
+            print(json.dumps({"leg": args.leg, "result": fn(**kw) if args.leg != "error" else fn()}), flush=True)
+        return
     pb = inputs.blast_3d(args.n, args.psize)
     cells_step = pb.cells_per_coarse_step()
     pk = peaks()

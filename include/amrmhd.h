@@ -225,14 +225,39 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
  * The forward is run once storing a checkpoint of every level's state every
  * ckpt_every coarse steps, then each segment is recomputed storing the filled
  * state of every level sub-step, and swept backwards. Branches (minmod, HLLD
- * cases, upwinding) take the forward's decisions. Adjoint arithmetic is FP64;
- * in mixed precision it is evaluated on the mixed-precision trajectory.
+ * cases, upwinding) take the forward's decisions. Adjoint accumulation is FP64;
+ * the local Jacobians of the HLLD flux and the half-step predictor are
+ * evaluated in the forward's compute type (FP64, or FP32 in mixed precision, on
+ * the mixed-precision trajectory), the others in FP64.
  * The first call (and any call needing more checkpoint or snapshot room) allocates
  * device memory owned by the context: about state + 70 scratch arrays per patch
  * in FP64, n_coarse/ckpt_every checkpoints and ckpt_every x (2^nlevels - 1)
  * level snapshots. On return the context holds U0 again. Synchronises the stream. */
 amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
                               const double* dL_dUfinal, double* dL_dU0);
+
+/* The local transposed Jacobians that amrmhd_backward applies at every face
+ * and cell, exposed for verification: gx = J^T g at n points, FP64, one point
+ * per row, all arrays HOST, row-major.
+ *  which 0: the HLLD flux (Sec. 4's hyperbolic advance; Miyoshi-Kusano) of a
+ *           rotated face, x = (rho, u_n, u_t, u_u, p, B_t, B_u) of the left
+ *           state, the same of the right state, then B_n (15 per row);
+ *           g = the 7 flux components (rho, m_n, m_t, m_u, E, B_t, B_u);
+ *           dim is ignored.
+ *  which 1: the half-step primitive predictor of one cell, wh = w -
+ *           sum_d h[d] A_d(w) s_d, x = (w[8], s_0[8], .., s_{dim-1}[8]) with
+ *           w = (rho, vx, vy, vz, p, Bx, By, Bz) and s_d its slopes along d
+ *           (8 + 8 dim per row); g = 8 per row; h[dim] the factors dt/(2 dx_d).
+ *  method 0: the hand-written transposes amrmhd_backward uses in FP64; 1: the
+ *            same formulas evaluated with forward-mode dual numbers (FP64);
+ *            2: the hand-written transposes in FP32 (x, g and h rounded to
+ *            FP32), as the mixed-precision adjoint applies them.
+ * Branches are the ones the forward takes at x. Allocates and frees device
+ * memory for the call and synchronises the device. Errors: AMRMHD_EINVAL for a
+ * bad which/dim/method, a negative n, NULL arrays or gamma <= 1; AMRMHD_ECUDA if
+ * an allocation, copy or launch fails. */
+amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const double* x, const double* g, double gamma,
+                               const double* h, int32_t method, double* gx);
 
 /* Regrid: rebuilds every level above 0, coarse to fine, up to max_levels
  * levels (Sec. 2: the grids follow the flagged regions; a new grid takes its

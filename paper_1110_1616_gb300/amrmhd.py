@@ -80,6 +80,7 @@ def lib():
             "amrmhd_regrid_boxes": [vp, i32, vp, i64, vp, i32, C.POINTER(i32)],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
             "amrmhd_set_option": [vp, i32, i64],
+            "amrmhd_local_vjp": [i32, i32, i64, vp, vp, dbl, vp, i32, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -91,6 +92,25 @@ def lib():
         L.amrmhd_last_error.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def local_vjp(which, x, g, gamma=5.0 / 3.0, dim=3, h=None, method=0):
+    """gx = J^T g at every row of x (numpy float64, host) for the HLLD flux
+    (which 0: rows of 15 inputs, 7 outputs) or the half-step predictor (which 1:
+    rows of 8 + 8 dim inputs, 8 outputs, h = dt/(2 dx_d)); method 0 the
+    hand-written transposes of the adjoint in FP64, 1 forward-mode dual numbers,
+    2 the hand-written transposes in FP32 (the mixed-precision adjoint's)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n = x.shape[0]
+    gx = np.zeros_like(x)
+    hh = np.ascontiguousarray(np.zeros(3) if h is None else np.asarray(h, dtype=np.float64).reshape(-1))
+    st = lib().amrmhd_local_vjp(int(which), int(dim), n, x.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p),
+                                float(gamma), hh.ctypes.data_as(C.c_void_p), int(method),
+                                gx.ctypes.data_as(C.c_void_p))
+    if st != 0:
+        raise RuntimeError("amrmhd_local_vjp failed: status %d" % st)
+    return gx
 
 
 def declared_symbols():

@@ -12,11 +12,13 @@
 // transposes: of reflux/restriction (scatter to the registers and the fine
 // level), of the advance stage by stage (update, EMF, HLLD, predictor and
 // slopes, recovery), and of the fill (scatter-add of every copied or
-// prolonged ghost value to its sources). Local Jacobians of the pointwise
-// formulas (HLLD, the predictor, the recovery, the edge EMF) come from the
-// same templated device formulas as the forward evaluated with forward-mode
-// dual numbers; branches (minmod, HLLD cases, upwinding) take the forward's
-// decisions. Adjoint arithmetic is FP64 in both precision modes, at the forward
+// prolonged ghost value to its sources). The transposed Jacobians of the two
+// costliest pointwise formulas (HLLD and the half-step predictor) are written
+// by hand (adjoint_local.cuh); those of the recovery and the edge EMF come from
+// the same templated device formulas as the forward evaluated with
+// forward-mode dual numbers (also kept for HLLD and the predictor, as the
+// cross-check of amrmhd_local_vjp); branches (minmod, HLLD cases, upwinding)
+// take the forward's decisions. Adjoint arithmetic is FP64 in both precision modes, at the forward
 // trajectory of the context's precision.
 #include <cuda_runtime.h>
 
@@ -26,6 +28,7 @@
 
 #include "ctx.hpp"
 #include "mhd_device.cuh"
+#include "adjoint_local.cuh"
 
 // ------------------------------------------------------------------ dual numbers
 namespace amrdev {
@@ -385,11 +388,13 @@ template <class T, int DIM, int D> __global__ void __launch_bounds__(TPB) k_adj_
     wr[f] = S[(SC_WH + f) * fs + L] - T(0.5) * S[(SC_S + 8 * D + f) * fs + L];
   }
   const T bn = T(0.5) * (wl[5 + n] + wr[5 + n]);
-  const double x[15] = {(double)wl[0], (double)wl[1 + n], (double)wl[1 + tt], (double)wl[1 + uu], (double)wl[4],
-                        (double)wl[5 + tt], (double)wl[5 + uu], (double)wr[0], (double)wr[1 + n], (double)wr[1 + tt],
-                        (double)wr[1 + uu], (double)wr[4], (double)wr[5 + tt], (double)wr[5 + uu], (double)bn};
-  double gx[15];
-  vjp<15, 7, 5>(x, g, gx, HlldFn{a.gamma});
+  // local Jacobian in the forward's compute type T (FP32 in mixed precision)
+  const T x[15] = {wl[0], wl[1 + n], wl[1 + tt], wl[1 + uu], wl[4], wl[5 + tt], wl[5 + uu],
+                   wr[0], wr[1 + n], wr[1 + tt], wr[1 + uu], wr[4], wr[5 + tt], wr[5 + uu], bn};
+  T gt[7], gx[15];
+#pragma unroll
+  for (int o = 0; o < 7; ++o) gt[o] = (T)g[o];
+  hlld_vjp<T>(x, gt, (T)a.gamma, gx);
   double gl[8], gr[8];
   gl[0] = gx[0]; gl[1 + n] = gx[1]; gl[1 + tt] = gx[2]; gl[1 + uu] = gx[3]; gl[4] = gx[4];
   gl[5 + tt] = gx[5]; gl[5 + uu] = gx[6]; gl[5 + n] = 0.5 * gx[14];
@@ -454,24 +459,32 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_adj_predict
     gwh[5] += -r1 * wh[3] + r2 * wh[2];
   }
   constexpr int NIN = 8 + 8 * DIM;
-  double x[NIN], gx[NIN];
+  // local Jacobian in the forward's compute type T (FP32 in mixed precision)
+  T x[NIN], gxt[NIN], gt[8];
+  double gx[NIN];
 #pragma unroll
-  for (int f = 0; f < 8; ++f) x[f] = (double)S[(SC_W + f) * fs + L];
+  for (int f = 0; f < 8; ++f) x[f] = S[(SC_W + f) * fs + L];
 #pragma unroll
   for (int d = 0; d < DIM; ++d)
 #pragma unroll
-    for (int f = 0; f < 8; ++f) x[8 + 8 * d + f] = (double)S[(SC_S + 8 * d + f) * fs + L];
+    for (int f = 0; f < 8; ++f) x[8 + 8 * d + f] = S[(SC_S + 8 * d + f) * fs + L];
   bool any = false;
 #pragma unroll
-  for (int f = 0; f < 8; ++f) any |= gwh[f] != 0.0;
+  for (int f = 0; f < 8; ++f) {
+    any |= gwh[f] != 0.0;
+    gt[f] = (T)gwh[f];
+  }
   const double dt = *a.dtp * a.dtscale;
-  PredFn<DIM> fn;
-  fn.gamma = a.gamma;
-  for (int d = 0; d < 3; ++d) fn.h[d] = (double)(T)(0.5 * dt * a.idx[d]);
-  if (any) vjp<NIN, 8, 8>(x, gwh, gx, fn);
-  else
+  T h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (T)(0.5 * dt * a.idx[d]);
+  if (any) {
+    predict_vjp<DIM, T>(x, gt, (T)a.gamma, h, gxt);
+#pragma unroll
+    for (int q = 0; q < NIN; ++q) gx[q] = (double)gxt[q];
+  } else {
 #pragma unroll
     for (int q = 0; q < NIN; ++q) gx[q] = 0.0;
+  }
   // W of the cell
   double* lW = lS + SC_W * fs;
 #pragma unroll
@@ -955,6 +968,49 @@ const AdjOps* adj_ops(bool fp32, int dim) {
   return dim == 3 ? AImpl<double, 3>::ops() : AImpl<double, 2>::ops();
 }
 
+// one thread per point: gx = J^T g of HLLD (WHICH 0; x = ql[7], qr[7], bn) or
+// of the half-step predictor (WHICH 1; x = w[8], s_0[8], .., s_{DIM-1}[8]), by
+// the hand-written transposes in FP64 (METHOD 0) or FP32 (METHOD 2, inputs
+// rounded to FP32), or forward-mode dual numbers (METHOD 1)
+template <int WHICH, int DIM, int METHOD>
+__global__ void __launch_bounds__(TPB) k_local_vjp(long long n, const double* x, const double* g, double gamma,
+                                                   double h0, double h1, double h2, double* gx) {
+  const long long i = blockIdx.x * (long long)TPB + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NIN = WHICH == 0 ? 15 : 8 + 8 * DIM;
+  constexpr int NOUT = WHICH == 0 ? 7 : 8;
+  double xi[NIN], gi[NOUT], o[NIN];
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) xi[q] = x[i * NIN + q];
+#pragma unroll
+  for (int q = 0; q < NOUT; ++q) gi[q] = g[i * NOUT + q];
+  float xf[NIN], gf[NOUT], of[NIN];
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) xf[q] = (float)xi[q];
+#pragma unroll
+  for (int q = 0; q < NOUT; ++q) gf[q] = (float)gi[q];
+  if (WHICH == 0) {
+    if (METHOD == 0) hlld_vjp<double>(xi, gi, gamma, o);
+    else if (METHOD == 1) vjp<NIN, NOUT, 5>(xi, gi, o, HlldFn{gamma});
+    else hlld_vjp<float>(xf, gf, (float)gamma, of);
+  } else {
+    const double h[3] = {h0, h1, h2};
+    const float hf[3] = {(float)h0, (float)h1, (float)h2};
+    if (METHOD == 0) {
+      predict_vjp<DIM, double>(xi, gi, gamma, h, o);
+    } else if (METHOD == 2) {
+      predict_vjp<DIM, float>(xf, gf, (float)gamma, hf, of);
+    } else {
+      PredFn<DIM> fn;
+      fn.gamma = gamma;
+      for (int d = 0; d < 3; ++d) fn.h[d] = h[d];
+      vjp<NIN, NOUT, 8>(xi, gi, o, fn);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) gx[i * NIN + q] = METHOD == 2 ? (double)of[q] : o[q];
+}
+
 }  // namespace amradj
 
 // ================================================================== host side
@@ -1366,6 +1422,53 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
   CUA(cudaStreamSynchronize(ctx->stream));
   CUA(cudaGetLastError());
   return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const double* x, const double* g, double gamma,
+                               const double* h, int32_t method, double* gx) {
+  if (which < 0 || which > 1 || (which == 1 && dim != 2 && dim != 3) || n < 0 || method < 0 || method > 2 ||
+      (n > 0 && (!x || !g || !gx || (which == 1 && !h))) || !(gamma > 1.0))
+    return AMRMHD_EINVAL;
+  if (n == 0) return AMRMHD_OK;
+  const int nin = which == 0 ? 15 : 8 + 8 * dim, nout = which == 0 ? 7 : 8;
+  double *dx = nullptr, *dg = nullptr, *dgx = nullptr;
+  amrmhd_status st = AMRMHD_OK;
+  const double hh[3] = {which == 1 ? h[0] : 0.0, which == 1 ? h[1] : 0.0, which == 1 && dim == 3 ? h[2] : 0.0};
+  if (cudaMalloc(&dx, sizeof(double) * n * nin) != cudaSuccess || cudaMalloc(&dg, sizeof(double) * n * nout) != cudaSuccess ||
+      cudaMalloc(&dgx, sizeof(double) * n * nin) != cudaSuccess) {
+    st = AMRMHD_ECUDA;
+  } else if (cudaMemcpy(dx, x, sizeof(double) * n * nin, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dg, g, sizeof(double) * n * nout, cudaMemcpyHostToDevice) != cudaSuccess) {
+    st = AMRMHD_ECUDA;
+  } else {
+    using namespace amradj;
+    const unsigned nb = (unsigned)((n + TPB - 1) / TPB);
+    const int key = which * 100 + (which == 1 ? dim : 0) * 10 + method;
+#define AMRMHD_LVJP(W, D, M) \
+  case W * 100 + (W == 1 ? D : 0) * 10 + M: \
+    k_local_vjp<W, D, M><<<nb, TPB>>>(n, dx, dg, gamma, hh[0], hh[1], hh[2], dgx); \
+    break;
+    switch (key) {
+      AMRMHD_LVJP(0, 3, 0)
+      AMRMHD_LVJP(0, 3, 1)
+      AMRMHD_LVJP(0, 3, 2)
+      AMRMHD_LVJP(1, 2, 0)
+      AMRMHD_LVJP(1, 2, 1)
+      AMRMHD_LVJP(1, 2, 2)
+      AMRMHD_LVJP(1, 3, 0)
+      AMRMHD_LVJP(1, 3, 1)
+      AMRMHD_LVJP(1, 3, 2)
+      default: break;
+    }
+#undef AMRMHD_LVJP
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(gx, dgx, sizeof(double) * n * nin, cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = AMRMHD_ECUDA;
+  }
+  cudaFree(dx);
+  cudaFree(dg);
+  cudaFree(dgx);
+  return st;
 }
 
 }  // extern "C"
