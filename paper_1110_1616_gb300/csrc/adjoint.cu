@@ -1067,6 +1067,8 @@ void preorder(int nlev, int l, std::vector<int>& out) {
 
 amrmhd_status adj_setup(amrmhd_ctx* ctx) {
   if (ctx->adj) return AMRMHD_OK;
+  amrmhd_status rst = upload_fill_rows(ctx);
+  if (rst) return rst;
   AdjWork* A = new AdjWork();
   ctx->adj = A;
   const amrmhd::Hierarchy& H = ctx->H;
@@ -1306,17 +1308,17 @@ void adj_fill(const Rev& R, int l, int s, int parent_slot) {
   amrmhd_ctx* ctx = R.ctx;
   AdjWork* A = ctx->adj;
   const LevelDev& L = ctx->lev[l];
-  amradj::AdjRows c = adj_rows(ctx, L.bc_cells, l), f = adj_rows(ctx, L.bc_faces, l);
+  amradj::AdjRows c = adj_rows(ctx, L.row_bc_cells, l), f = adj_rows(ctx, L.row_bc_faces, l);
   A->ops->bc_t(c, f, ctx->stream);
   if (s == 1 && l > 0) {
-    c = adj_rows(ctx, L.prol_cells, l - 1);
-    f = adj_rows(ctx, L.prol_faces, l - 1);
+    c = adj_rows(ctx, L.row_prol_cells, l - 1);
+    f = adj_rows(ctx, L.row_prol_faces, l - 1);
     c.lamc = f.lamc = A->lamx;
     c.Xc = f.Xc = snap_base(ctx, R.step, parent_slot);
     A->ops->prolong_t(c, f, ctx->stream);
   }
-  c = adj_rows(ctx, L.same_cells, l);
-  f = adj_rows(ctx, L.same_faces, l);
+  c = adj_rows(ctx, L.row_same_cells, l);
+  f = adj_rows(ctx, L.row_same_faces, l);
   A->ops->same_t(c, f, ctx->stream);
 }
 

@@ -135,21 +135,29 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
     b.fbuf = state_buf(ctx, ctx->cur[l]);
     b.cbuf = state_buf(ctx, ctx->start[l - 1]);
+    b.chunks = L.chunk_pcells.p;
+    b.nrows = L.chunk_pcells.n;
     ctx->ops->prolong_cells(b, ctx->stream, nl);
     b.rows = L.prol_faces.p;
-    b.nrows = L.prol_faces.n;
+    b.chunks = L.chunk_pfaces.p;
+    b.nrows = L.chunk_pfaces.n;
     ctx->ops->prolong_faces(b, ctx->stream, nl);
   }
   // physical boundaries last: their sources are domain cells filled above
   const DevList& bcc = near ? L.bc_cells2 : L.bc_cells;
   const DevList& bcf = near ? L.bc_faces2 : L.bc_faces;
-  if (bcc.n || bcf.n) {
+  const DevList& bch = near ? L.chunk_bcells2 : L.chunk_bcells;
+  const DevList& bfh = near ? L.chunk_bfaces2 : L.chunk_bfaces;
+  if (bch.n || bfh.n) {
     RowArgs c = row_args(ctx, bcc, l);
     c.fbuf = state_buf(ctx, ctx->cur[l]);
     for (int f = 0; f < 8; ++f) c.inflow[f] = ctx->cfg.inflow[f];
+    c.chunks = bch.p;
+    c.nrows = bch.n;
     ctx->ops->fill_bc_cells(c, ctx->stream, nl);
     c.rows = bcf.p;
-    c.nrows = bcf.n;
+    c.chunks = bfh.p;
+    c.nrows = bfh.n;
     ctx->ops->fill_bc_faces(c, ctx->stream, nl);
   }
 }
@@ -301,6 +309,52 @@ void op_coarse_step(amrmhd_ctx* ctx, int* nl) {
   op_level_step(ctx, 0, 1, nl);
 }
 
+// the ghost fills as one row per position (the ghost maps' rows split by kind:
+// same-level (dst, [d,] Ld, src, Ls), prolongation (dst, [d,] Ld, srcC, Lc),
+// boundaries as the map rows), per level, for the adjoint's transposed fills
+amrmhd_status upload_fill_rows(amrmhd_ctx* ctx) {
+  amrmhd::Hierarchy& H = ctx->H;
+  H.expand_ghost_rows();
+  cudaError_t e = cudaSuccess;
+  auto upload = [&](const std::vector<int32_t>& v, DevList& out, int width) -> bool {
+    out.n = (int64_t)v.size() / width;
+    if (v.empty()) { out.p = nullptr; return true; }
+    out.p = dbuf<int>(ctx, v.size(), &e);
+    if (e != cudaSuccess) return false;
+    e = cudaMemcpy(out.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice);
+    return e == cudaSuccess;
+  };
+  std::vector<std::vector<int32_t>> sc(H.nlev), pc(H.nlev), sf(H.nlev), pf(H.nlev), bcc(H.nlev), bcf(H.nlev);
+  for (size_t r = 0; r < H.ghost_cells.size(); r += 5) {
+    const int32_t* g = &H.ghost_cells[r];
+    const int l = H.p[g[0]].level;
+    if (g[2] >= 2) {
+      bcc[l].insert(bcc[l].end(), g, g + 5);
+      continue;
+    }
+    std::vector<int32_t>& v = g[2] == 0 ? sc[l] : pc[l];
+    v.insert(v.end(), {g[0], g[1], g[3], g[4]});
+  }
+  for (size_t r = 0; r < H.ghost_faces.size(); r += 6) {
+    const int32_t* g = &H.ghost_faces[r];
+    const int l = H.p[g[0]].level;
+    if (g[3] >= 2) {
+      bcf[l].insert(bcf[l].end(), g, g + 6);
+      continue;
+    }
+    std::vector<int32_t>& v = g[3] == 0 ? sf[l] : pf[l];
+    v.insert(v.end(), {g[0], g[1], g[2], g[4], g[5]});
+  }
+  for (int l = 0; l < H.nlev; ++l) {
+    LevelDev& L = ctx->lev[l];
+    const bool ok = upload(sc[l], L.row_same_cells, 4) && upload(pc[l], L.row_prol_cells, 4) &&
+                    upload(sf[l], L.row_same_faces, 5) && upload(pf[l], L.row_prol_faces, 5) &&
+                    upload(bcc[l], L.row_bc_cells, 5) && upload(bcf[l], L.row_bc_faces, 6);
+    if (!ok) return fail(ctx, AMRMHD_ECUDA, std::string("fill row upload: ") + cudaGetErrorString(e));
+  }
+  return AMRMHD_OK;
+}
+
 amrmhd_status check_bound(amrmhd_ctx* ctx) {
   if (!ctx) return AMRMHD_EINVAL;
   if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
@@ -309,7 +363,8 @@ amrmhd_status check_bound(amrmhd_ctx* ctx) {
 }
 
 const std::vector<int32_t>* map_vec(amrmhd_ctx* ctx, int which, int* width) {
-  const amrmhd::Hierarchy& H = ctx->H;
+  amrmhd::Hierarchy& H = ctx->H;
+  if (which == AMRMHD_MAP_GHOST_CELLS || which == AMRMHD_MAP_GHOST_FACES) H.expand_ghost_rows();
   switch (which) {
     case AMRMHD_MAP_GHOST_CELLS: *width = 5; return &H.ghost_cells;
     case AMRMHD_MAP_GHOST_FACES: *width = 6; return &H.ghost_faces;
@@ -511,169 +566,69 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     L.ids = dbuf<int>(ctx, ids.size(), &e);
     if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
     CU(cudaMemcpy(L.ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
-    // ghost lists of this level's patches, split by kind
-    std::vector<int32_t> sc, pc, sf, pf, bcc, bcf;
-    for (size_t r = 0; r < H.ghost_cells.size(); r += 5) {
-      const int32_t* g = &H.ghost_cells[r];
-      if (H.p[g[0]].level != l) continue;
-      if (g[2] >= 2) {
-        bcc.insert(bcc.end(), g, g + 5);
-        continue;
-      }
-      std::vector<int32_t>& v = g[2] == 0 ? sc : pc;
-      v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[3]); v.push_back(g[4]);
-    }
-    for (size_t r = 0; r < H.ghost_faces.size(); r += 6) {
-      const int32_t* g = &H.ghost_faces[r];
-      if (H.p[g[0]].level != l) continue;
-      if (g[3] >= 2) {
-        bcf.insert(bcf.end(), g, g + 6);
-        continue;
-      }
-      std::vector<int32_t>& v = g[3] == 0 ? sf : pf;
-      v.push_back(g[0]); v.push_back(g[1]); v.push_back(g[2]); v.push_back(g[4]); v.push_back(g[5]);
-    }
-    bool ok = upload(sc, L.same_cells, 4) && upload(pc, L.prol_cells, 4) && upload(sf, L.same_faces, 5) &&
-              upload(pf, L.prol_faces, 5) && upload(bcc, L.bc_cells, 5) && upload(bcf, L.bc_faces, 6);
-    // the same-level copies as boxes: rows grouped by (destination, [face
-    // direction,] source, coordinate shift) and each group's positions merged
-    // greedily into boxes (x runs, then y, then z); blocks take chunks of at
-    // most 64 cells of one box
-    auto make_boxes = [&](const std::vector<int32_t>& rows, int w, std::vector<int32_t>& boxes,
-                          std::vector<int32_t>& chunks) {
-      const bool faces = w == 5;
-      const int bw = faces ? 8 : 7;
-      // rows come grouped by destination patch: one segment per patch
-      std::vector<size_t> seg;
-      for (size_t r = 0; r < rows.size(); r += w)
-        if (r == 0 || rows[r] != rows[r - w]) seg.push_back(r);
-      seg.push_back(rows.size());
-      const int nseg = (int)seg.size() - 1;
-      std::vector<std::vector<int32_t>> out(std::max(nseg, 0));
-#pragma omp parallel for schedule(dynamic, 1)
-      for (int sgi = 0; sgi < nseg; ++sgi) {
-        // groups by (direction, source, coordinate shift), in order of first appearance;
-        // rows arrive in z,y,x order, so every group is too
-        std::vector<std::array<int, 5>> keys;
-        std::vector<std::vector<std::array<int, 3>>> pos;
-        std::unordered_map<uint64_t, int> gid;
-        for (size_t r = seg[sgi]; r < seg[sgi + 1]; r += w) {
-          const int32_t* x = &rows[r];
-          const int dst = x[0], d = faces ? x[1] : 0, Ld = x[faces ? 2 : 1], src = x[faces ? 3 : 2],
-                    Ls = x[faces ? 4 : 3];
-          const amrmhd::HPatch &D = H.p[dst], &S = H.p[src];
-          const int a0 = Ld % D.ext[0], b0 = (Ld / D.ext[0]) % D.ext[1], c0 = Ld / (D.ext[0] * D.ext[1]);
-          const int a1 = Ls % S.ext[0], b1 = (Ls / S.ext[0]) % S.ext[1], c1 = Ls / (S.ext[0] * S.ext[1]);
-          const std::array<int, 5> k = {d, src, a1 - a0, b1 - b0, c1 - c0};
-          uint64_t h = 1469598103934665603ull;
-          for (int v : k) h = (h ^ (uint32_t)v) * 1099511628211ull;
-          auto it = gid.find(h);
-          int g = -1;
-          if (it != gid.end() && keys[it->second] == k) g = it->second;
-          if (g < 0) {
-            for (size_t t = 0; t < keys.size() && g < 0; ++t)
-              if (keys[t] == k) g = (int)t;  // hash collision: fall back to a scan
-            if (g < 0) {
-              g = (int)keys.size();
-              keys.push_back(k);
-              pos.emplace_back();
-              gid[h] = g;
-            }
-          }
-          pos[g].push_back({a0, b0, c0});
-        }
-        const int dst = rows[seg[sgi]];
-        const amrmhd::HPatch& D = H.p[dst];
-        std::vector<int32_t>& ob = out[sgi];
-        for (size_t g = 0; g < keys.size(); ++g) {
-          const std::array<int, 5>& k = keys[g];
-          const amrmhd::HPatch& S = H.p[k[1]];
-          int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
-          for (const auto& c : pos[g])
-            for (int e = 0; e < 3; ++e) {
-              lo[e] = std::min(lo[e], c[e]);
-              hi[e] = std::max(hi[e], c[e] + 1);
-            }
-          const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
-          std::vector<uint8_t> m((size_t)ex * ey * ez, 0);  // 1 present, 2 assigned
-          auto at = [&](int x, int y, int z) -> uint8_t& {
-            return m[((size_t)(z - lo[2]) * ey + (y - lo[1])) * ex + (x - lo[0])];
-          };
-          for (const auto& c : pos[g]) at(c[0], c[1], c[2]) = 1;
-          for (const auto& c : pos[g]) {
-            const int x0 = c[0], y0 = c[1], z0 = c[2];
-            if (at(x0, y0, z0) != 1) continue;
-            int nx = 1, ny = 1, nz = 1;
-            while (x0 + nx < hi[0] && at(x0 + nx, y0, z0) == 1) ++nx;
-            auto row_ok = [&](int y, int z) {
-              for (int t = 0; t < nx; ++t)
-                if (at(x0 + t, y, z) != 1) return false;
-              return true;
-            };
-            while (y0 + ny < hi[1] && row_ok(y0 + ny, z0)) ++ny;
-            auto slab_ok = [&](int z) {
-              for (int u = 0; u < ny; ++u)
-                if (!row_ok(y0 + u, z)) return false;
-              return true;
-            };
-            while (z0 + nz < hi[2] && slab_ok(z0 + nz)) ++nz;
-            for (int z = 0; z < nz; ++z)
-              for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) at(x0 + x, y0 + y, z0 + z) = 2;
-            const int Ld = x0 + D.ext[0] * (y0 + D.ext[1] * z0);
-            const int Ls = (x0 + k[2]) + S.ext[0] * ((y0 + k[3]) + S.ext[1] * (z0 + k[4]));
-            if (faces) ob.insert(ob.end(), {dst, k[0], Ld, k[1], Ls, nx, ny, nz});
-            else ob.insert(ob.end(), {dst, Ld, k[1], Ls, nx, ny, nz});
-          }
-        }
-      }
-      for (int sgi = 0; sgi < nseg; ++sgi) {
-        const int first = (int)(boxes.size() / bw);
-        boxes.insert(boxes.end(), out[sgi].begin(), out[sgi].end());
-        for (int bi = first; bi < (int)(boxes.size() / bw); ++bi) {
-          const int* bx = &boxes[(size_t)bi * bw];
-          const int vol = bx[bw - 3] * bx[bw - 2] * bx[bw - 1];
-          for (int c = 0; c < vol; c += 64) {
-            chunks.push_back(bi);
-            chunks.push_back(c);
-          }
-        }
+    // ghost fill lists of this level from the hierarchy's boxes (see LevelDev)
+    std::vector<int32_t> rc, cc, rf, cf, pcb, pcc, pfb, pfc, bcb, bcc, bfb, bfc;
+    std::vector<int32_t> rc2, cc2, rf2, cf2, bcb2, bcc2, bfb2, bfc2;
+    auto chunks_of = [](std::vector<int32_t>& ch, int bi, int vol) {
+      for (int c = 0; c < vol; c += amrk::FILL_CHUNK) {
+        ch.push_back(bi);
+        ch.push_back(c);
       }
     };
-    std::vector<int32_t> rc, cc, rf, cf;
-    make_boxes(sc, 4, rc, cc);
-    make_boxes(sf, 5, rf, cf);
-    // rows of ghosts within 2 cells of the interior (faces: either adjacent cell)
-    auto depth = [&](int q, int L, int dshift) {  // Chebyshev depth of local cell L (shifted by -1 along dshift)
-      const amrmhd::HPatch& P = H.p[q];
-      int c[3] = {L % P.ext[0], (L / P.ext[0]) % P.ext[1], L / (P.ext[0] * P.ext[1])};
-      if (dshift >= 0) c[dshift] -= 1;
-      int dep = 0;
+    // a box clipped to the ghosts within 2 cells of the interior (faces: either
+    // adjacent cell within 2); false if nothing is left
+    auto clip_near = [&](const int32_t* b, int32_t* o) {
+      const amrmhd::HPatch& P = H.p[b[0]];
+      std::copy(b, b + amrmhd::GHOST_BOX_W, o);
       for (int e = 0; e < H.dim; ++e) {
-        if (c[e] < 4) dep = std::max(dep, 4 - c[e]);
-        if (c[e] >= P.n[e] + 4) dep = std::max(dep, c[e] - (P.n[e] + 3));
+        const int lo = std::max(b[4 + e], 2), hi = std::min(b[4 + e] + b[7 + e], P.n[e] + 6 + (e == b[1] ? 1 : 0));
+        if (hi <= lo) return false;
+        o[4 + e] = lo;
+        o[7 + e] = hi - lo;
       }
-      return dep;
+      return true;
     };
-    auto near_rows = [&](const std::vector<int32_t>& rows, int w, bool face) {
-      std::vector<int32_t> out;
-      for (size_t r = 0; r < rows.size(); r += w) {
-        const int32_t* x = &rows[r];
-        bool keep;
-        if (!face) keep = depth(x[0], x[1], -1) <= 2;
-        else keep = std::min(depth(x[0], x[2], -1), depth(x[0], x[2], x[1])) <= 2;
-        if (keep) out.insert(out.end(), x, x + w);
+    // a same-level box as (dst, [d,] Ld, src, Ls, nx, ny, nz)
+    auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
+      const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
+      const int Ld = b[4] + D.ext[0] * (b[5] + D.ext[1] * b[6]);
+      const int Ls = (b[4] + b[10]) + S.ext[0] * ((b[5] + b[11]) + S.ext[1] * (b[6] + b[12]));
+      const int bi = (int)(boxes.size() / (b[1] < 0 ? 7 : 8));
+      if (b[1] < 0) boxes.insert(boxes.end(), {b[0], Ld, b[3], Ls, b[7], b[8], b[9]});
+      else boxes.insert(boxes.end(), {b[0], b[1], Ld, b[3], Ls, b[7], b[8], b[9]});
+      chunks_of(ch, bi, b[7] * b[8] * b[9]);
+    };
+    auto add_box = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
+      const int bi = (int)(boxes.size() / amrmhd::GHOST_BOX_W);
+      boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
+      chunks_of(ch, bi, b[7] * b[8] * b[9]);
+    };
+    for (int faces = 0; faces < 2; ++faces) {
+      const std::vector<int32_t>& gb = faces ? H.ghost_box_faces : H.ghost_box_cells;
+      for (size_t r = 0; r < gb.size(); r += amrmhd::GHOST_BOX_W) {
+        const int32_t* b = &gb[r];
+        if (H.p[b[0]].level != l) continue;
+        int32_t nb[amrmhd::GHOST_BOX_W];
+        const bool near = clip_near(b, nb);
+        if (b[2] == 0) {
+          add_run(b, faces ? rf : rc, faces ? cf : cc);
+          if (near) add_run(nb, faces ? rf2 : rc2, faces ? cf2 : cc2);
+        } else if (b[2] == 1) {
+          add_box(b, faces ? pfb : pcb, faces ? pfc : pcc);
+        } else {
+          add_box(b, faces ? bfb : bcb, faces ? bfc : bcc);
+          if (near) add_box(nb, faces ? bfb2 : bcb2, faces ? bfc2 : bcc2);
+        }
       }
-      return out;
-    };
-    std::vector<int32_t> rc2, cc2, rf2, cf2;
-    make_boxes(near_rows(sc, 4, false), 4, rc2, cc2);
-    make_boxes(near_rows(sf, 5, true), 5, rf2, cf2);
+    }
+    const int GW = amrmhd::GHOST_BOX_W;
+    bool ok = upload(rc, L.run_cells, 7) && upload(cc, L.chunk_cells, 2) && upload(rf, L.run_faces, 8) &&
+              upload(cf, L.chunk_faces, 2) && upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
+              upload(pfb, L.prol_faces, GW) && upload(pfc, L.chunk_pfaces, 2) && upload(bcb, L.bc_cells, GW) &&
+              upload(bcc, L.chunk_bcells, 2) && upload(bfb, L.bc_faces, GW) && upload(bfc, L.chunk_bfaces, 2);
     ok = ok && upload(rc2, L.run_cells2, 7) && upload(cc2, L.chunk_cells2, 2) && upload(rf2, L.run_faces2, 8) &&
-         upload(cf2, L.chunk_faces2, 2) && upload(near_rows(bcc, 5, false), L.bc_cells2, 5) &&
-         upload(near_rows(bcf, 6, true), L.bc_faces2, 6);
-    ok = ok && upload(rc, L.run_cells, 7) && upload(cc, L.chunk_cells, 2) && upload(rf, L.run_faces, 8) &&
-         upload(cf, L.chunk_faces, 2);
+         upload(cf2, L.chunk_faces2, 2) && upload(bcb2, L.bc_cells2, GW) && upload(bcc2, L.chunk_bcells2, 2) &&
+         upload(bfb2, L.bc_faces2, GW) && upload(bfc2, L.chunk_bfaces2, 2);
     if (l > 0 && ok) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
         return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);

@@ -21,13 +21,19 @@ struct LevelDev {
   int* ids = nullptr;  // patch ids of the level (device)
   int npatch = 0;
   int maxn[3] = {1, 1, 1};
-  DevList same_cells, same_faces, prol_cells, prol_faces;  // ghost fill of this level
-  DevList bc_cells, bc_faces;                               // physical boundaries (kinds 2, 3)
-  DevList run_cells, run_faces;      // same-level copies as boxes (7 / 8 ints per box)
-  DevList chunk_cells, chunk_faces;  // (box, first cell) per block of at most 64 cells
-  // the same for the ghosts within 2 cells of the interior (all that an advance
-  // of the interior alone reads): used for sub-steps with w = 0
-  DevList run_cells2, run_faces2, chunk_cells2, chunk_faces2, bc_cells2, bc_faces2;
+  // ghost fill of this level as boxes, each list with its chunks (box, first
+  // position) per block of at most 64 positions: same-level copies (7 / 8 ints
+  // per box), prolongation and physical boundaries (GHOST_BOX_W ints per box)
+  DevList run_cells, run_faces, chunk_cells, chunk_faces;
+  DevList prol_cells, prol_faces, chunk_pcells, chunk_pfaces;
+  DevList bc_cells, bc_faces, chunk_bcells, chunk_bfaces;
+  // the same clipped to the ghosts within 2 cells of the interior (all that an
+  // advance of the interior alone reads): used for sub-steps with w = 0
+  DevList run_cells2, run_faces2, chunk_cells2, chunk_faces2;
+  DevList bc_cells2, bc_faces2, chunk_bcells2, chunk_bfaces2;
+  // one row per ghost position of the same fills (rows of amrmhd.h's ghost maps
+  // split by kind), uploaded on demand for the adjoint's transposed fills
+  DevList row_same_cells, row_same_faces, row_prol_cells, row_prol_faces, row_bc_cells, row_bc_faces;
   DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
   int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
 };
@@ -107,6 +113,7 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
 void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl);
 void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl);
 amrmhd_status check_bound(amrmhd_ctx* ctx);
+amrmhd_status upload_fill_rows(amrmhd_ctx* ctx);
 void adj_free(amrmhd_ctx* ctx);  // adjoint.cu
 
 }  // namespace amrapi

@@ -13,6 +13,8 @@
 #include <map>
 #include <tuple>
 
+#include <parallel/algorithm>
+
 #include "../../include/amrmhd.h"
 
 namespace amrmhd {
@@ -118,12 +120,20 @@ struct PairHash {
   }
 };
 
+// sort in parallel (OpenMP) above a size where it pays
+template <class It, class Cmp> void psort(It a, It b, Cmp cmp) {
+  if (b - a > (1 << 16)) __gnu_parallel::sort(a, b, cmp);
+  else std::sort(a, b, cmp);
+}
+
 }  // namespace
 
 int Hierarchy::build(const int32_t* rows7, int n) {
   err.clear();
   p.clear();
-  ghost_cells.clear(); ghost_faces.clear(); cf_faces.clear(); cf_edges.clear();
+  ghost_cells.clear(); ghost_faces.clear(); ghost_box_cells.clear(); ghost_box_faces.clear();
+  ghost_rows_ready = false;
+  cf_faces.clear(); cf_edges.clear();
   emf_faces.clear(); restrict_cells.clear(); restrict_faces.clear(); reflux_cells.clear();
   if (n <= 0) { err = "empty patch list"; return AMRMHD_EINVAL; }
   for (int d = 0; d < dim; ++d)
@@ -256,13 +266,27 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     }
   }
 
-  // ---------------- ghost maps (patches in parallel, rows concatenated in patch order)
-  rng_ghost_cells.assign(nlev, {0, 0});
-  rng_ghost_faces.assign(nlev, {0, 0});
-  std::vector<std::vector<int32_t>> gc_rows(np), gf_rows(np);
+  // ---------------- ghost fill boxes (patches in parallel, concatenated in patch order)
+  // Every ghost position of a patch (cells: the ghosted box minus the interior;
+  // d-faces: the face box minus the patch's own faces) gets a label: kind 0 a
+  // copy from a same-level patch at a constant local offset, kind 1 a
+  // prolongation from the coarse patch holding the parent cell (with the
+  // periodic wrap of the fine position), kind 2 a copy of the patch's own
+  // position clamped into the domain, kind 3 the inflow state. Positions with
+  // equal labels are merged greedily into boxes (x runs, then y, then z), so
+  // the work per position is a label and a comparison, and the device lists
+  // hold boxes, not positions.
+  ghost_rows_ready = false;
+  std::vector<std::vector<int32_t>> gbc(np), gbf(np);
   std::vector<std::string> gerr(np);
   std::vector<int> gst(np, 0);
-  auto ghost_patch = [&](int q, std::vector<int32_t>& gcq, std::vector<int32_t>& gfq, std::string& errq) -> int {
+  struct Lab {
+    int kind, src, aux[3];
+    bool operator==(const Lab& o) const {
+      return kind == o.kind && src == o.src && aux[0] == o.aux[0] && aux[1] == o.aux[1] && aux[2] == o.aux[2];
+    }
+  };
+  auto ghost_patch = [&](int q, std::vector<int32_t>& outc, std::vector<int32_t>& outf, std::string& errq) -> int {
     const HPatch& P = p[q];
     const int l = P.level;
     // coarse candidates for prolongation sources
@@ -273,176 +297,201 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     }
     std::sort(cc.begin(), cc.end());
     cc.erase(std::unique(cc.begin(), cc.end()), cc.end());
-    // parent cell of fine position g; for a d-face (dn >= 0) on the high side
-    // of a non-periodic domain the parent is the last coarse cell and L indexes
-    // the coarse face one past it
-    int last_src = -1;
-    auto coarse_src = [&](const int* g, int* L, int dn) {
-      int c[3];
-      for (int d = 0; d < 3; ++d) c[d] = d < dim ? (wrapd(l, d, g[d]) >> 1) : 0;
-      const bool top = dn >= 0 && !per[dn] && g[dn] == N(l, dn);
-      if (top) c[dn] -= 1;
-      auto inside = [&](int Q) {
-        for (int d = 0; d < dim; ++d)
-          if (c[d] < p[Q].lo[d] || c[d] >= p[Q].hi[d]) return false;
-        return true;
-      };
-      // consecutive positions usually share the parent patch: try the last one first
-      int hit = (last_src >= 0 && inside(last_src)) ? last_src : -1;
-      for (size_t i = 0; hit < 0 && i < cc.size(); ++i)
-        if (inside(cc[i])) hit = cc[i];
-      if (hit < 0) return -1;
-      last_src = hit;
-      if (top) c[dn] += 1;
-      *L = loc(hit, c[0], c[1], c[2]);
-      return hit;
+    // labels are few per patch: positions hold an index into a small table
+    std::vector<Lab> labs;
+    int last_id = -1;
+    auto label_id = [&](const Lab& k) {
+      if (last_id >= 0 && labs[last_id] == k) return last_id;
+      for (size_t i = 0; i < labs.size(); ++i)
+        if (labs[i] == k) return last_id = (int)i;
+      labs.push_back(k);
+      return last_id = (int)labs.size() - 1;
     };
-    // cells
-    {
-      int e[3];
-      for (int d = 0; d < 3; ++d) e[d] = d < dim ? P.n[d] + 8 : 1;
-      size_t tot = (size_t)e[0] * e[1] * e[2];
-      std::vector<int> sq(tot, -1), sl(tot, 0);
-      auto idx = [&](int a, int b, int c) { return ((size_t)(c - (dim == 3 ? P.lo[2] - 4 : 0)) * e[1] + (b - P.lo[1] + 4)) * e[0] + (a - P.lo[0] + 4); };
-      for (const Nbr& x : nbr[q]) {
-        const HPatch& Q = p[x.q];
-        int a0[3], a1[3];
-        for (int d = 0; d < 3; ++d) {
-          if (d >= dim) { a0[d] = 0; a1[d] = 1; continue; }
-          a0[d] = std::max(P.lo[d] - 4, Q.lo[d] + x.s[d] * N(l, d));
-          a1[d] = std::min(P.hi[d] + 4, Q.hi[d] + x.s[d] * N(l, d));
-        }
-        for (int c = a0[2]; c < a1[2]; ++c)
-          for (int b = a0[1]; b < a1[1]; ++b)
-            for (int a = a0[0]; a < a1[0]; ++a) {
-              size_t t = idx(a, b, c);
-              sq[t] = x.q;
-              sl[t] = loc(x.q, a - x.s[0] * N(l, 0), b - x.s[1] * N(l, 1), c - x.s[2] * N(l, 2));
-            }
-      }
-      for (int c = (dim == 3 ? P.lo[2] - 4 : 0); c < (dim == 3 ? P.hi[2] + 4 : 1); ++c)
-        for (int b = P.lo[1] - 4; b < P.hi[1] + 4; ++b)
-          for (int a = P.lo[0] - 4; a < P.hi[0] + 4; ++a) {
-            bool inner = a >= P.lo[0] && a < P.hi[0] && b >= P.lo[1] && b < P.hi[1] &&
-                         (dim == 2 || (c >= P.lo[2] && c < P.hi[2]));
-            if (inner) continue;
-            {
-              // outside the domain of a non-periodic dimension: boundary entry
-              int g[3] = {a, b, c}, gc[3] = {a, b, c};
-              bool out = false, inflow = false;
-              for (int e = 0; e < dim; ++e) {
-                if (per[e]) continue;
-                if (g[e] < 0) { out = true; gc[e] = 0; inflow |= bc[e][0] == 2; }
-                else if (g[e] > N(l, e) - 1) { out = true; gc[e] = N(l, e) - 1; inflow |= bc[e][1] == 2; }
-              }
-              if (out) {
-                int row[5] = {q, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q, inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
-                gcq.insert(gcq.end(), row, row + 5);
-                continue;
-              }
-            }
-            size_t t = idx(a, b, c);
-            int kind = 0, src = sq[t], L = sl[t];
-            if (src < 0) {
-              if (l == 0) { errq = "level-0 ghost cell without a source"; return AMRMHD_EINVAL; }
-              int g[3] = {a, b, c};
-              kind = 1;
-              src = coarse_src(g, &L, -1);
-              if (src < 0) { errq = "no parent-level source for the ghost cell (" + std::to_string(a) + ", " + std::to_string(b) + ", " +
-                      std::to_string(c) + ") of patch " + std::to_string(q);
-                return AMRMHD_ENEST;
-              }
-            }
-            int row[5] = {q, loc(q, a, b, c), kind, src, L};
-            gcq.insert(gcq.end(), row, row + 5);
-          }
-    }
-    // faces
-    for (int d = 0; d < dim; ++d) {
-      int lo[3], hi[3];  // face box (inclusive-exclusive per dim)
+    static thread_local std::vector<int> lid, sl;
+    static thread_local std::vector<uint8_t> state;  // 0 not a ghost, 1 to assign, 2 assigned
+    for (int d = -1; d < dim; ++d) {  // -1: cells, else the d-faces
+      int ex[3], g0[3], own0[3], own1[3];
       for (int e = 0; e < 3; ++e) {
-        if (e >= dim) { lo[e] = 0; hi[e] = 1; continue; }
-        lo[e] = P.lo[e] - 4;
-        hi[e] = P.hi[e] + 4 + (e == d ? 1 : 0);
+        ex[e] = e < dim ? P.n[e] + 8 + (e == d ? 1 : 0) : 1;
+        g0[e] = e < dim ? P.lo[e] - 4 : 0;  // global position of local coordinate 0
+        // the patch's own cells (faces) in local coordinates
+        own0[e] = e < dim ? 4 : 0;
+        own1[e] = e < dim ? P.n[e] + 4 + (e == d ? 1 : 0) : 1;
       }
-      int ex[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
-      size_t tot = (size_t)ex[0] * ex[1] * ex[2];
-      std::vector<int> sq(tot, -1), sl(tot, 0);
-      auto idx = [&](int a, int b, int c) { return ((size_t)(c - lo[2]) * ex[1] + (b - lo[1])) * ex[0] + (a - lo[0]); };
+      const size_t tot = (size_t)ex[0] * ex[1] * ex[2];
+      lid.assign(tot, -1);
+      sl.resize(tot);
+      state.assign(tot, 0);
+      labs.clear();
+      last_id = -1;
+      auto at = [&](int a, int b, int c) { return ((size_t)c * ex[1] + b) * ex[0] + a; };
+      // the ghost positions of row (b, c): all of it, or the two ends when the
+      // row passes through the patch's own positions
+      auto for_ghosts = [&](auto&& f) {
+        for (int c = 0; c < ex[2]; ++c)
+          for (int b = 0; b < ex[1]; ++b) {
+            const bool through = b >= own0[1] && b < own1[1] && c >= own0[2] && c < own1[2];
+            if (!through) {
+              for (int a = 0; a < ex[0]; ++a) f(a, b, c);
+            } else {
+              for (int a = 0; a < own0[0]; ++a) f(a, b, c);
+              for (int a = own1[0]; a < ex[0]; ++a) f(a, b, c);
+            }
+          }
+      };
+      // same-level sources: the neighbour (with its periodic shift) whose
+      // interior (or own faces) holds the position; on a face stored by two
+      // neighbours the smaller (patch, local index) wins
       for (const Nbr& x : nbr[q]) {
         const HPatch& Q = p[x.q];
-        int a0[3], a1[3];
+        int a0[3], a1[3], delta[3] = {0, 0, 0};
+        bool empty = false;
         for (int e = 0; e < 3; ++e) {
           if (e >= dim) { a0[e] = 0; a1[e] = 1; continue; }
-          int qlo = Q.lo[e] + x.s[e] * N(l, e), qhi = Q.hi[e] + x.s[e] * N(l, e) + (e == d ? 1 : 0);
-          a0[e] = std::max(lo[e], qlo);
-          a1[e] = std::min(hi[e], qhi);
+          const int qlo = Q.lo[e] + x.s[e] * N(l, e), qhi = Q.hi[e] + x.s[e] * N(l, e) + (e == d ? 1 : 0);
+          a0[e] = std::max(0, qlo - g0[e]);
+          a1[e] = std::min(ex[e], qhi - g0[e]);
+          if (a1[e] <= a0[e]) empty = true;
+          delta[e] = P.lo[e] - Q.lo[e] - x.s[e] * N(l, e);
         }
+        if (empty) continue;
+        const int id = label_id(Lab{0, x.q, {delta[0], delta[1], delta[2]}});
         for (int c = a0[2]; c < a1[2]; ++c)
           for (int b = a0[1]; b < a1[1]; ++b)
             for (int a = a0[0]; a < a1[0]; ++a) {
-              size_t t = idx(a, b, c);
-              int L = loc(x.q, a - x.s[0] * N(l, 0), b - x.s[1] * N(l, 1), c - x.s[2] * N(l, 2));
-              if (sq[t] < 0 || x.q < sq[t] || (x.q == sq[t] && L < sl[t])) { sq[t] = x.q; sl[t] = L; }
+              const size_t t = at(a, b, c);
+              const int L = (a + delta[0]) + Q.ext[0] * ((b + delta[1]) + Q.ext[1] * (c + delta[2]));
+              const int cur = lid[t];
+              if (d < 0 || cur < 0 || x.q < labs[cur].src || (x.q == labs[cur].src && L < sl[t])) {
+                lid[t] = id;
+                sl[t] = L;
+              }
             }
       }
-      for (int c = lo[2]; c < hi[2]; ++c)
-        for (int b = lo[1]; b < hi[1]; ++b)
-          for (int a = lo[0]; a < hi[0]; ++a) {
-            int g[3] = {a, b, c};
-            bool own = true;
-            for (int e = 0; e < dim; ++e) {
-              if (e == d) { if (g[e] < P.lo[e] || g[e] > P.hi[e]) own = false; }
-              else if (g[e] < P.lo[e] || g[e] >= P.hi[e]) own = false;
-            }
-            if (own) continue;
-            {
-              int gc[3] = {a, b, c};
-              bool out = false, inflow = false;
-              for (int e = 0; e < dim; ++e) {
-                if (per[e]) continue;
-                const int top = e == d ? N(l, e) : N(l, e) - 1;
-                if (g[e] < 0) { out = true; gc[e] = 0; inflow |= bc[e][0] == 2; }
-                else if (g[e] > top) { out = true; gc[e] = top; inflow |= bc[e][1] == 2; }
-              }
-              if (out) {
-                int row[6] = {q, d, loc(q, a, b, c), inflow ? 3 : 2, inflow ? -1 : q,
-                              inflow ? -1 : loc(q, gc[0], gc[1], gc[2])};
-                gfq.insert(gfq.end(), row, row + 6);
-                continue;
-              }
-            }
-            size_t t = idx(a, b, c);
-            int kind = 0, src = sq[t], L = sl[t];
-            if (src < 0) {
-              if (l == 0) { errq = "level-0 ghost face without a source"; return AMRMHD_EINVAL; }
-              kind = 1;
-              src = coarse_src(g, &L, d);
-              if (src < 0) { errq = "no parent-level source for the ghost face (" + std::to_string(d) + "; " + std::to_string(a) + ", " +
-                      std::to_string(b) + ", " + std::to_string(c) + ") of patch " + std::to_string(q);
-                return AMRMHD_ENEST;
-              }
-            }
-            int row[6] = {q, d, loc(q, a, b, c), kind, src, L};
-            gfq.insert(gfq.end(), row, row + 6);
+      // prolongation: each coarse candidate, at each periodic image w, is the
+      // source of the positions whose wrapped parent cell (g + w N) >> 1 it
+      // holds; along a non-periodic d the face at the domain's top belongs to
+      // the coarse patch holding the last cell
+      if (l > 0) {
+        for (int Cq : cc) {
+          const HPatch& Cp = p[Cq];
+          int wlo[3], whi[3];
+          for (int e = 0; e < 3; ++e) {
+            wlo[e] = (e < dim && per[e]) ? -1 : 0;
+            whi[e] = (e < dim && per[e]) ? 1 : 0;
           }
+          for (int wz = wlo[2]; wz <= whi[2]; ++wz)
+            for (int wy = wlo[1]; wy <= whi[1]; ++wy)
+              for (int wx = wlo[0]; wx <= whi[0]; ++wx) {
+                const int w[3] = {wx, wy, wz};
+                int a0[3], a1[3], aux[3] = {0, 0, 0};
+                bool empty = false;
+                for (int e = 0; e < 3; ++e) {
+                  if (e >= dim) { a0[e] = 0; a1[e] = 1; continue; }
+                  aux[e] = w[e] * N(l, e);
+                  const int top = (e == d && !per[e] && Cp.hi[e] == N(l - 1, e)) ? 1 : 0;
+                  a0[e] = std::max(0, 2 * Cp.lo[e] - aux[e] - g0[e]);
+                  a1[e] = std::min(ex[e], 2 * Cp.hi[e] + top - aux[e] - g0[e]);
+                  if (a1[e] <= a0[e]) empty = true;
+                }
+                if (empty) continue;
+                const int id = label_id(Lab{1, Cq, {aux[0], aux[1], aux[2]}});
+                for (int c = a0[2]; c < a1[2]; ++c)
+                  for (int b = a0[1]; b < a1[1]; ++b)
+                    for (int a = a0[0]; a < a1[0]; ++a) {
+                      const size_t t = at(a, b, c);
+                      if (lid[t] < 0) lid[t] = id;
+                    }
+              }
+        }
+      }
+      // physical boundaries (outside the domain of a non-periodic dimension),
+      // then a check that every ghost position has a source
+      bool touches = false;
+      for (int e = 0; e < dim; ++e)
+        if (!per[e] && (g0[e] < 0 || g0[e] + ex[e] - 1 > (e == d ? N(l, e) : N(l, e) - 1))) touches = true;
+      int fail = 0;
+      for_ghosts([&](int a, int b, int c) {
+        if (fail) return;
+        const size_t t = at(a, b, c);
+        state[t] = 1;
+        const int g[3] = {g0[0] + a, g0[1] + b, g0[2] + c};
+        if (touches) {
+          Lab bl{2, q, {-1, -1, -1}};
+          bool out = false, inflow = false;
+          for (int e = 0; e < dim; ++e) {
+            if (per[e]) continue;
+            const int top = e == d ? N(l, e) : N(l, e) - 1;
+            if (g[e] < 0) { out = true; bl.aux[e] = 0; inflow |= bc[e][0] == 2; }
+            else if (g[e] > top) { out = true; bl.aux[e] = top; inflow |= bc[e][1] == 2; }
+          }
+          if (out) {
+            lid[t] = label_id(inflow ? Lab{3, -1, {0, 0, 0}} : bl);
+            return;
+          }
+        }
+        if (lid[t] >= 0) return;
+        if (l == 0) {
+          errq = d < 0 ? "level-0 ghost cell without a source" : "level-0 ghost face without a source";
+          fail = AMRMHD_EINVAL;
+          return;
+        }
+        errq = d < 0 ? "no parent-level source for the ghost cell (" + std::to_string(g[0]) + ", " +
+                           std::to_string(g[1]) + ", " + std::to_string(g[2]) + ") of patch " + std::to_string(q)
+                     : "no parent-level source for the ghost face (" + std::to_string(d) + "; " +
+                           std::to_string(g[0]) + ", " + std::to_string(g[1]) + ", " + std::to_string(g[2]) +
+                           ") of patch " + std::to_string(q);
+        fail = AMRMHD_ENEST;
+      });
+      if (fail) return fail;
+      // greedy boxes of equal labels
+      std::vector<int32_t>& out = d < 0 ? outc : outf;
+      for_ghosts([&](int a, int b, int c) {
+        const size_t t0 = at(a, b, c);
+        if (state[t0] != 1) return;
+        const int k = lid[t0];
+        auto same = [&](int x, int y, int z) {
+          const size_t t = at(x, y, z);
+          return state[t] == 1 && lid[t] == k;
+        };
+        int nx = 1, ny = 1, nz = 1;
+        while (a + nx < ex[0] && same(a + nx, b, c)) ++nx;
+        auto row_ok = [&](int y, int z) {
+          for (int i = 0; i < nx; ++i)
+            if (!same(a + i, y, z)) return false;
+          return true;
+        };
+        while (b + ny < ex[1] && row_ok(b + ny, c)) ++ny;
+        auto slab_ok = [&](int z) {
+          for (int j = 0; j < ny; ++j)
+            if (!row_ok(b + j, z)) return false;
+          return true;
+        };
+        while (c + nz < ex[2] && slab_ok(c + nz)) ++nz;
+        for (int z = 0; z < nz; ++z)
+          for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) state[at(a + x, b + y, c + z)] = 2;
+        const Lab& kk = labs[k];
+        const int32_t row[GHOST_BOX_W] = {q, d, kk.kind, kk.src, a, b, c, nx, ny, nz, kk.aux[0], kk.aux[1], kk.aux[2]};
+        out.insert(out.end(), row, row + GHOST_BOX_W);
+      });
     }
-      return 0;
+    return 0;
   };
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int q = 0; q < np; ++q) gst[q] = ghost_patch(q, gc_rows[q], gf_rows[q], gerr[q]);
+  for (int q = 0; q < np; ++q) gst[q] = ghost_patch(q, gbc[q], gbf[q], gerr[q]);
   for (int q = 0; q < np; ++q)
     if (gst[q]) { err = gerr[q]; return gst[q]; }
   {
     size_t nc = 0, nf = 0;
-    for (int q = 0; q < np; ++q) { nc += gc_rows[q].size(); nf += gf_rows[q].size(); }
-    ghost_cells.reserve(nc);
-    ghost_faces.reserve(nf);
+    for (int q = 0; q < np; ++q) { nc += gbc[q].size(); nf += gbf[q].size(); }
+    ghost_box_cells.clear();
+    ghost_box_faces.clear();
+    ghost_box_cells.reserve(nc);
+    ghost_box_faces.reserve(nf);
     for (int q = 0; q < np; ++q) {
-      ghost_cells.insert(ghost_cells.end(), gc_rows[q].begin(), gc_rows[q].end());
-      ghost_faces.insert(ghost_faces.end(), gf_rows[q].begin(), gf_rows[q].end());
-      std::vector<int32_t>().swap(gc_rows[q]);
-      std::vector<int32_t>().swap(gf_rows[q]);
+      ghost_box_cells.insert(ghost_box_cells.end(), gbc[q].begin(), gbc[q].end());
+      ghost_box_faces.insert(ghost_box_faces.end(), gbf[q].begin(), gbf[q].end());
     }
   }
 
@@ -463,18 +512,21 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     rng_reflux_cells[l][0] = (int64_t)reflux_cells.size() / 9;
     // per coarse patch: cover map over its cells widened by one, entry (fine patch, shift)
     struct Cov { int c = -1; int s[3] = {0, 0, 0}; };
-    std::unordered_map<Key, std::array<int, 4>, KeyHash> edge_best;  // key -> (qc, Le, pf, Lf)
     std::vector<std::vector<std::array<int, 7>>> face_rows(np);
     std::vector<std::vector<std::array<int, 5>>> rcell_rows(np);
     std::vector<std::vector<std::array<int, 6>>> rface_rows(np);
     std::vector<std::vector<Cov>> covmaps(np);
+    const std::vector<int>& lpc = level_patches[lc];
+    const int npc = (int)lpc.size();
     auto covidx = [&](int qc, int a, int b, int c) {
       const HPatch& C = p[qc];
       int e0 = C.n[0] + 2, e1 = C.n[1] + 2;
       int z = dim == 3 ? c - C.lo[2] + 1 : 0;
       return ((size_t)z * e1 + (b - C.lo[1] + 1)) * e0 + (a - C.lo[0] + 1);
     };
-    for (int qc : level_patches[lc]) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ip = 0; ip < npc; ++ip) {
+      const int qc = lpc[ip];
       const HPatch& C = p[qc];
       std::vector<Cov>& cm = covmaps[qc];
       cm.assign((size_t)(C.n[0] + 2) * (C.n[1] + 2) * (dim == 3 ? C.n[2] + 2 : 1), Cov());
@@ -505,11 +557,13 @@ int Hierarchy::build(const int32_t* rows7, int n) {
       if (add_d >= 0) f[add_d] += add;
       return loc(v.c, f[0], f[1], f[2]);
     };
-    // per coarse patch: candidate owners of its C/F edges (merged below)
-    std::vector<std::vector<std::pair<Key, std::array<int, 4>>>> edge_cand(np);
-    const std::vector<int>& lpc = level_patches[lc];
+    // per coarse patch: C/F faces (sorted by (d, Lface)), restricted cells and
+    // faces (generated in (d,) local index order), candidate owners of its C/F
+    // edges (merged below)
+    struct ECand { Key key; int qc, Le, bf, bl; };
+    std::vector<std::vector<ECand>> edge_cand(np);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (size_t ip = 0; ip < lpc.size(); ++ip) {
+    for (int ip = 0; ip < npc; ++ip) {
       const int qc = lpc[ip];
       const HPatch& C = p[qc];
       const int k0 = dim == 3 ? C.lo[2] : 0, k1 = dim == 3 ? C.hi[2] : 1;
@@ -587,74 +641,109 @@ int Hierarchy::build(const int32_t* rows7, int n) {
                 }
               if (ncov < 1 || ncov > 3) continue;
               Key key{c, wrapd(lc, 0, i), wrapd(lc, 1, j), dim == 3 ? wrapd(lc, 2, k) : 0};
-              edge_cand[qc].push_back({key, {qc, loc(qc, i, j, k), bf, bl}});
+              edge_cand[qc].push_back({key, qc, loc(qc, i, j, k), bf, bl});
             }
       }
+      std::sort(face_rows[qc].begin(), face_rows[qc].end());
     }
-    // the smallest (coarse patch, local index) and (fine patch, local index) per edge
-    for (int qc : lpc)
-      for (const auto& kc : edge_cand[qc]) {
-        const Key& key = kc.first;
-        const int Le = kc.second[1], bf = kc.second[2], bl = kc.second[3];
-        auto it = edge_best.find(key);
-        if (it == edge_best.end()) edge_best[key] = kc.second;
-        else {
-          auto& v = it->second;
-          if (qc < v[0] || (qc == v[0] && Le < v[1])) { v[0] = qc; v[1] = Le; }
-          if (bf < v[2] || (bf == v[2] && bl < v[3])) { v[2] = bf; v[3] = bl; }
-        }
+    // row offsets of each coarse patch's rows in the level's lists
+    std::vector<size_t> o_face(npc + 1, 0), o_rcell(npc + 1, 0), o_rface(npc + 1, 0), o_ecand(npc + 1, 0);
+    for (int ip = 0; ip < npc; ++ip) {
+      const int qc = lpc[ip];
+      o_face[ip + 1] = o_face[ip] + face_rows[qc].size();
+      o_rcell[ip + 1] = o_rcell[ip] + rcell_rows[qc].size();
+      o_rface[ip + 1] = o_rface[ip] + rface_rows[qc].size();
+      o_ecand[ip + 1] = o_ecand[ip] + edge_cand[qc].size();
+    }
+    // C/F edges: the candidates sorted by edge; per edge the smallest (coarse
+    // patch, local index) and (fine patch, local index)
+    std::vector<ECand> ec(o_ecand[npc]);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ip = 0; ip < npc; ++ip)
+      std::copy(edge_cand[lpc[ip]].begin(), edge_cand[lpc[ip]].end(), ec.begin() + o_ecand[ip]);
+    std::vector<std::vector<ECand>>().swap(edge_cand);
+    psort(ec.begin(), ec.end(), [](const ECand& x, const ECand& y) { return x.key < y.key; });
+    std::vector<std::pair<std::array<int, 6>, Key>> erows;
+    for (size_t i = 0; i < ec.size();) {
+      size_t j = i;
+      std::array<int, 4> v = {ec[i].qc, ec[i].Le, ec[i].bf, ec[i].bl};
+      for (; j < ec.size() && ec[j].key == ec[i].key; ++j) {
+        const ECand& x = ec[j];
+        if (x.qc < v[0] || (x.qc == v[0] && x.Le < v[1])) { v[0] = x.qc; v[1] = x.Le; }
+        if (x.bf < v[2] || (x.bf == v[2] && x.bl < v[3])) { v[2] = x.bf; v[3] = x.bl; }
       }
-    // emit C/F faces (qc ascending, then (d, Lface)), reflux cells, restriction lists
-    std::vector<std::array<int, 9>> rrows;
-    std::unordered_map<std::pair<int, int>, size_t, PairHash> rrow_of;  // (qc, Lcell) -> index in rrows
-    for (int qc : level_patches[lc]) {
-      auto& v = face_rows[qc];
-      std::sort(v.begin(), v.end());
-      for (auto& r : v) {
-        int64_t row = (int64_t)cf_faces.size() / 7;
-        cf_faces.insert(cf_faces.end(), r.begin(), r.end());
+      erows.push_back({{l, v[0], ec[i].key.c, v[1], v[2], v[3]}, ec[i].key});
+      i = j;
+    }
+    std::vector<ECand>().swap(ec);
+    // C/F edges sorted by (qc, c, Le); their row numbers by key (sorted for lookup)
+    psort(erows.begin(), erows.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    const int64_t erow0 = (int64_t)cf_edges.size() / 6;
+    std::vector<std::pair<Key, int>> edge_row((size_t)erows.size());
+    cf_edges.resize(cf_edges.size() + 6 * erows.size());
+#pragma omp parallel for
+    for (int64_t i = 0; i < (int64_t)erows.size(); ++i) {
+      std::copy(erows[i].first.begin(), erows[i].first.end(), cf_edges.begin() + 6 * (erow0 + i));
+      edge_row[i] = {erows[i].second, (int)(erow0 + i)};
+    }
+    std::vector<std::pair<std::array<int, 6>, Key>>().swap(erows);
+    psort(edge_row.begin(), edge_row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    auto edge_row_of = [&](const Key& k) {
+      auto it = std::lower_bound(edge_row.begin(), edge_row.end(), k,
+                                 [](const std::pair<Key, int>& x, const Key& y) { return x.first < y; });
+      return (it != edge_row.end() && it->first == k) ? it->second : -1;
+    };
+    // emit C/F faces (qc ascending, then (d, Lface)), reflux cells (per
+    // uncovered cell with a C/F face: the rows of its faces by slot), restriction lists
+    const int64_t frow0 = (int64_t)cf_faces.size() / 7;
+    cf_faces.resize(cf_faces.size() + 7 * o_face[npc]);
+    const size_t rc0 = restrict_cells.size(), rf0 = restrict_faces.size();
+    restrict_cells.resize(rc0 + 5 * o_rcell[npc]);
+    restrict_faces.resize(rf0 + 6 * o_rface[npc]);
+    std::vector<std::vector<std::array<int, 9>>> rrows(npc);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ip = 0; ip < npc; ++ip) {
+      const int qc = lpc[ip];
+      const auto& v = face_rows[qc];
+      std::vector<std::array<int, 3>> cells;  // (Lcell, slot, row)
+      cells.reserve(v.size());
+      for (size_t k = 0; k < v.size(); ++k) {
+        const auto& r = v[k];
+        const int64_t row = frow0 + (int64_t)(o_face[ip] + k);
+        std::copy(r.begin(), r.end(), cf_faces.begin() + 7 * row);
         // the uncovered cell this face belongs to, and the face's slot in it
-        int d = r[2], Lf = r[3], side = r[4];
+        const int d = r[2], Lf = r[3], side = r[4];
         int sd = 1;
         for (int e = 0; e < d; ++e) sd *= p[qc].ext[e];
-        int Lcell = side == 1 ? Lf : Lf - sd;
-        int slot = 2 * d + (side == 1 ? 0 : 1);
-        auto it = rrow_of.find({qc, Lcell});
-        if (it == rrow_of.end()) {
-          std::array<int, 9> rr = {l, qc, Lcell, -1, -1, -1, -1, -1, -1};
-          rr[3 + slot] = (int)row;
-          rrow_of[{qc, Lcell}] = rrows.size();
-          rrows.push_back(rr);
-        } else {
-          rrows[it->second][3 + slot] = (int)row;
-        }
+        cells.push_back({side == 1 ? Lf : Lf - sd, 2 * d + (side == 1 ? 0 : 1), (int)row});
+      }
+      std::sort(cells.begin(), cells.end());
+      for (size_t k = 0; k < cells.size();) {
+        std::array<int, 9> rr = {l, qc, cells[k][0], -1, -1, -1, -1, -1, -1};
+        size_t m = k;
+        for (; m < cells.size() && cells[m][0] == cells[k][0]; ++m) rr[3 + cells[m][1]] = cells[m][2];
+        rrows[ip].push_back(rr);
+        k = m;
+      }
+      size_t o = rc0 + 5 * o_rcell[ip];
+      for (const auto& r : rcell_rows[qc]) {
+        std::copy(r.begin(), r.end(), restrict_cells.begin() + o);
+        o += 5;
+      }
+      o = rf0 + 6 * o_rface[ip];
+      for (const auto& r : rface_rows[qc]) {
+        std::copy(r.begin(), r.end(), restrict_faces.begin() + o);
+        o += 6;
       }
     }
-    std::sort(rrows.begin(), rrows.end());
-    for (auto& r : rrows) reflux_cells.insert(reflux_cells.end(), r.begin(), r.end());
-    for (int qc : level_patches[lc]) {
-      for (auto& r : rcell_rows[qc]) restrict_cells.insert(restrict_cells.end(), r.begin(), r.end());
-    }
-    {
-      std::vector<std::array<int, 6>> all;
-      for (int qc : level_patches[lc]) all.insert(all.end(), rface_rows[qc].begin(), rface_rows[qc].end());
-      std::sort(all.begin(), all.end());
-      for (auto& r : all) restrict_faces.insert(restrict_faces.end(), r.begin(), r.end());
-    }
-    // C/F edges sorted by (qc, c, Le); remember their row numbers by key
-    std::vector<std::pair<std::array<int, 6>, Key>> erows;
-    for (auto& kv : edge_best) erows.push_back({{l, kv.second[0], kv.first.c, kv.second[1], kv.second[2], kv.second[3]}, kv.first});
-    std::sort(erows.begin(), erows.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    std::unordered_map<Key, int, KeyHash> edge_row;
-    for (auto& e : erows) {
-      edge_row[e.second] = (int)(cf_edges.size() / 6);
-      cf_edges.insert(cf_edges.end(), e.first.begin(), e.first.end());
-    }
-    // EMF-corrected faces: every stored copy of an uncovered face touching a C/F edge
+    for (int ip = 0; ip < npc; ++ip)
+      for (const auto& r : rrows[ip]) reflux_cells.insert(reflux_cells.end(), r.begin(), r.end());
+    // EMF-corrected faces: every stored copy of an uncovered face touching a C/F
+    // edge, generated per coarse patch in (d, local index) order
     {
       std::vector<std::vector<std::array<int, 8>>> per(np);
 #pragma omp parallel for schedule(dynamic, 1)
-      for (size_t ip = 0; ip < lpc.size(); ++ip) {
+      for (int ip = 0; ip < npc; ++ip) {
         const int qc = lpc[ip];
         const HPatch& C = p[qc];
         const int k0 = dim == 3 ? C.lo[2] : 0, k1 = dim == 3 ? C.hi[2] : 1;
@@ -694,18 +783,16 @@ int Hierarchy::build(const int32_t* rows7, int n) {
                   int gs[3] = {i, j, k};
                   gs[slot < 2 ? t1 : t2] += slot & 1;
                   Key key{comp, wrapd(lc, 0, gs[0]), wrapd(lc, 1, gs[1]), dim == 3 ? wrapd(lc, 2, gs[2]) : 0};
-                  auto it = edge_row.find(key);
-                  if (it != edge_row.end()) { e[slot] = it->second; any = true; }
+                  const int row = edge_row_of(key);
+                  if (row >= 0) { e[slot] = row; any = true; }
                 }
                 if (!any) continue;
                 all.push_back({l, qc, d, loc(qc, i, j, k), e[0], e[1], e[2], e[3]});
               }
         }
       }
-      std::vector<std::array<int, 8>> all;
-      for (int qc : lpc) all.insert(all.end(), per[qc].begin(), per[qc].end());
-      std::sort(all.begin(), all.end());
-      for (auto& r : all) emf_faces.insert(emf_faces.end(), r.begin(), r.end());
+      for (int qc : lpc)
+        for (const auto& r : per[qc]) emf_faces.insert(emf_faces.end(), r.begin(), r.end());
     }
     rng_cf_faces[l][1] = (int64_t)cf_faces.size() / 7;
     rng_cf_edges[l][1] = (int64_t)cf_edges.size() / 6;
@@ -715,6 +802,64 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     rng_reflux_cells[l][1] = (int64_t)reflux_cells.size() / 9;
   }
   return AMRMHD_OK;
+}
+
+void Hierarchy::expand_ghost_rows() {
+  if (ghost_rows_ready) return;
+  const int np = (int)p.size();
+  // positions of every box, per patch, sorted into the row order (patch; cells
+  // by local index; faces by direction, then local index)
+  std::vector<std::vector<std::array<int64_t, 2>>> keyc(np), keyf(np);  // (sort key, row start)
+  std::vector<int32_t> rc, rf;
+  auto emit = [&](const std::vector<int32_t>& boxes, bool faces) {
+    for (size_t r = 0; r < boxes.size(); r += GHOST_BOX_W) {
+      const int32_t* b = &boxes[r];
+      const int q = b[0], d = b[1], kind = b[2], src = b[3];
+      const HPatch& P = p[q];
+      for (int z = b[6]; z < b[6] + b[9]; ++z)
+        for (int y = b[5]; y < b[5] + b[8]; ++y)
+          for (int x = b[4]; x < b[4] + b[7]; ++x) {
+            const int Ld = x + P.ext[0] * (y + P.ext[1] * z);
+            const int g[3] = {P.lo[0] + x - 4, P.lo[1] + y - 4, dim == 3 ? P.lo[2] + z - 4 : 0};
+            int Ls = -1;
+            if (kind == 0) {
+              const HPatch& S = p[src];
+              Ls = (x + b[10]) + S.ext[0] * ((y + b[11]) + S.ext[1] * (z + b[12]));
+            } else if (kind == 1) {
+              int c[3];
+              for (int e = 0; e < 3; ++e) c[e] = e < dim ? (g[e] + b[10 + e]) >> 1 : 0;
+              Ls = loc(src, c[0], c[1], c[2]);
+            } else if (kind == 2) {
+              int gc[3];
+              for (int e = 0; e < 3; ++e) gc[e] = b[10 + e] >= 0 ? b[10 + e] : g[e];
+              Ls = loc(q, gc[0], gc[1], gc[2]);
+            }
+            std::vector<int32_t>& v = faces ? rf : rc;
+            if (faces) {
+              keyf[q].push_back({(int64_t)d << 40 | Ld, (int64_t)v.size()});
+              const int32_t row[6] = {q, d, Ld, kind, src, Ls};
+              v.insert(v.end(), row, row + 6);
+            } else {
+              keyc[q].push_back({(int64_t)Ld, (int64_t)v.size()});
+              const int32_t row[5] = {q, Ld, kind, src, Ls};
+              v.insert(v.end(), row, row + 5);
+            }
+          }
+    }
+  };
+  emit(ghost_box_cells, false);
+  emit(ghost_box_faces, true);
+  ghost_cells.clear();
+  ghost_faces.clear();
+  ghost_cells.reserve(rc.size());
+  ghost_faces.reserve(rf.size());
+  for (int q = 0; q < np; ++q) {
+    std::sort(keyc[q].begin(), keyc[q].end());
+    for (const auto& k : keyc[q]) ghost_cells.insert(ghost_cells.end(), rc.begin() + k[1], rc.begin() + k[1] + 5);
+    std::sort(keyf[q].begin(), keyf[q].end());
+    for (const auto& k : keyf[q]) ghost_faces.insert(ghost_faces.end(), rf.begin() + k[1], rf.begin() + k[1] + 6);
+  }
+  ghost_rows_ready = true;
 }
 
 }  // namespace amrmhd

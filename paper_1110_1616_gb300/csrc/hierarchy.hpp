@@ -9,6 +9,8 @@
 
 namespace amrmhd {
 
+constexpr int GHOST_BOX_W = 13;
+
 struct HPatch {
   int level;
   int lo[3], hi[3];
@@ -40,9 +42,20 @@ struct Hierarchy {
   std::vector<std::vector<Nbr>> nbr;            // per patch, sorted by (q, shift)
   std::vector<std::vector<int>> parents, children;
 
-  // maps, rows of fixed width (see amrmhd.h for the row formats)
+  // ghost fill as boxes of GHOST_BOX_W ints: (dst patch, d (-1 cells, else the
+  // d-faces), kind, src, lo[3], n[3], aux[3]) with lo in dst's local (ghosted,
+  // 0-based) coordinates. kind 0: copy from patch src at local offset aux;
+  // kind 1: prolongation from coarse patch src, parent of the wrapped fine
+  // position (global g + aux) >> 1; kind 2: copy of dst's own position with
+  // the coordinates aux[e] >= 0 replaced by aux[e] (clamped into the domain);
+  // kind 3: the inflow state. Boxes of one patch cover its ghost positions once.
+  std::vector<int32_t> ghost_box_cells, ghost_box_faces;
+  // the same as one row per position (amrmhd.h row formats), made on demand by
+  // expand_ghost_rows() (map export, the adjoint's transposed fills)
   std::vector<int32_t> ghost_cells;     // 5
   std::vector<int32_t> ghost_faces;     // 6
+  bool ghost_rows_ready = false;
+  // maps, rows of fixed width (see amrmhd.h for the row formats)
   std::vector<int32_t> cf_faces;        // 7
   std::vector<int32_t> cf_edges;        // 6
   std::vector<int32_t> emf_faces;       // 8
@@ -51,7 +64,7 @@ struct Hierarchy {
   std::vector<int32_t> reflux_cells;    // 9
   // per level row ranges [begin, end) of each list (rows are grouped by level:
   // ghost lists by the patch's level, register lists by the fine level l)
-  std::vector<std::array<int64_t, 2>> rng_ghost_cells, rng_ghost_faces, rng_cf_faces, rng_cf_edges,
+  std::vector<std::array<int64_t, 2>> rng_cf_faces, rng_cf_edges,
       rng_emf_faces, rng_restrict_cells, rng_restrict_faces, rng_reflux_cells;
   std::string err;
 
@@ -64,6 +77,7 @@ struct Hierarchy {
   int loc(int q, int a, int b, int c) const;  // local index of level position (a,b,c)
   // Returns 0 or a negative amrmhd_status; fills err.
   int build(const int32_t* rows7, int n);
+  void expand_ghost_rows();
 };
 
 }  // namespace amrmhd

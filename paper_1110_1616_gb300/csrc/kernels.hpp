@@ -74,13 +74,17 @@ struct CflArgs {
 
 enum Variant { V_FP64 = 0, V_FP64_STRICT = 1, V_MIXED = 2 };
 
+// positions per chunk (= threads per block) of the box-list fill kernels
+constexpr int FILL_CHUNK = 64;
+
 struct Ops {
   void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
   void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
   void (*reg_fine)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
-  void (*fill_same_cells)(const RowArgs&, cudaStream_t, int* launches);
-  void (*fill_same_faces)(const RowArgs&, cudaStream_t, int* launches);
-  // the same copies as boxes (rows = boxes, nrows = chunks of at most 256 cells)
+  // ghost fill, all as boxes: rows = the box list, chunks = (box, first
+  // position) per block of at most 64 positions, nrows = the number of chunks.
+  // Same-level copies (7 / 8-int boxes), then prolongation and physical
+  // boundaries (ghost boxes of amrmhd::GHOST_BOX_W ints)
   void (*fill_runs_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_runs_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);

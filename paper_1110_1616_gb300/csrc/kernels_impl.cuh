@@ -7,6 +7,7 @@
 // patch's region; patches of uneven size leave surplus blocks idle. Map-driven
 // kernels run one thread per map row, each row writing one destination value
 // set (no atomics, deterministic).
+#include "hierarchy.hpp"
 #include "kernels.hpp"
 #include "mhd_device.cuh"
 
@@ -322,39 +323,13 @@ template <class T, int DIM> __global__ void k_reg_fine_edges(RowArgs a) {
 }
 
 // ------------------------------------------------------------------ ghost fill
-// same-level cell copies: rows (dst, Ldst, src, Lsrc)
-template <class T, int DIM> __global__ void k_fill_same_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 4 * r;
-  const DPatch D = a.P[row[0]], S = a.P[row[2]];
-  T* dst = (T*)a.fbuf + D.off + row[1];
-  const T* src = (const T*)a.fbuf + S.off + row[3];
-  constexpr int NCF = DIM == 3 ? 5 : 6;
-#pragma unroll
-  for (int n = 0; n < NCF; ++n) {
-    const int f = n < 5 ? n : BZ;
-    dst[f * D.fs] = src[f * S.fs];
-  }
-}
-
-// same-level face copies: rows (dst, d, Ldst, src, Lsrc)
-template <class T, int DIM> __global__ void k_fill_same_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 5 * r;
-  const DPatch D = a.P[row[0]], S = a.P[row[3]];
-  const int f = BX + row[1];
-  ((T*)a.fbuf)[D.off + f * D.fs + row[2]] = ((const T*)a.fbuf)[S.off + f * S.fs + row[4]];
-}
-
 // Same-level copies as boxes: box records (dst, Ldst0, src, Lsrc0, nx, ny, nz)
 // for cells, (dst, d, Ldst0, src, Lsrc0, nx, ny, nz) for faces: the box of nx x
 // ny x nz positions starting at Ldst0 in patch dst takes the positions starting
 // at Lsrc0 in patch src (strides of each patch's own storage). chunks[2c],
 // chunks[2c+1] = (box, first cell) of block c (at most FILL_TPB cells of one box;
 // small blocks keep the threads busy on boxes of ~100 cells).
-constexpr int FILL_TPB = 64;
+constexpr int FILL_TPB = FILL_CHUNK;
 template <int W>
 __device__ __forceinline__ bool box_cell(const int* boxes, const int* chunks, const DPatch* P, const int*& box,
                                          long long& Ld, long long& Ls) {
@@ -395,23 +370,51 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_b
   ((T*)a.fbuf)[D.off + f * D.fs + Ld] = ((const T*)a.fbuf)[S.off + f * S.fs + Ls];
 }
 
-// physical boundary cells: rows (dst, Ldst, kind, src, Lsrc); kind 2 copies
-// the patch's own nearest domain cell, kind 3 sets the inflow state
-template <class T, int DIM> __global__ void k_fill_bc_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 5 * r;
-  const DPatch D = a.P[row[0]];
-  T* dst = (T*)a.fbuf + D.off + row[1];
+// Prolongation and physical-boundary fills as ghost boxes of GHOST_BOX_W
+// ints (dst, d, kind, src, lo[3], n[3], aux[3]), lo in dst's local ghosted
+// coordinates; chunks as for the same-level boxes. gbox_pos gives the local
+// coordinates x of this thread's position and its global position g.
+constexpr int GBW = amrmhd::GHOST_BOX_W;
+template <int DIM>
+__device__ __forceinline__ bool gbox_pos(const RowArgs& a, const int*& box, int* x, int* g) {
+  const int bi = a.chunks[2 * blockIdx.x];
+  const int c = a.chunks[2 * blockIdx.x + 1] + threadIdx.x;
+  box = a.rows + GBW * bi;
+  const int nx = box[7], ny = box[8], nz = box[9];
+  if (c >= nx * ny * nz) return false;
+  x[0] = box[4] + c % nx;
+  x[1] = box[5] + (c / nx) % ny;
+  x[2] = box[6] + c / (nx * ny);
+  const DPatch& D = a.P[box[0]];
+  g[0] = D.lo[0] + x[0] - 4;
+  g[1] = D.lo[1] + x[1] - 4;
+  g[2] = DIM == 3 ? D.lo[2] + x[2] - 4 : 0;
+  return true;
+}
+__device__ __forceinline__ int local_of(const DPatch& P, const int* g) {
+  return (g[0] - P.lo[0] + 4) + P.ext[0] * ((g[1] - P.lo[1] + 4) + P.ext[1] * (P.ext[2] > 1 ? g[2] - P.lo[2] + 4 : 0));
+}
+
+// physical boundary cells: kind 2 copies the patch's own position clamped into
+// the domain (the coordinates aux[e] >= 0 replaced), kind 3 sets the inflow state
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_bc_cells(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]];
+  T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
   constexpr int NCF = DIM == 3 ? 5 : 6;
-  if (row[2] == 3) {
+  if (box[2] == 3) {
 #pragma unroll
     for (int n = 0; n < NCF; ++n) {
       const int f = n < 5 ? n : BZ;
       dst[f * D.fs] = (T)a.inflow[f];
     }
   } else {
-    const T* src = (const T*)a.fbuf + D.off + row[4];
+    int gc[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gc[e] = box[10 + e] >= 0 ? box[10 + e] : g[e];
+    const T* src = (const T*)a.fbuf + D.off + local_of(D, gc);
 #pragma unroll
     for (int n = 0; n < NCF; ++n) {
       const int f = n < 5 ? n : BZ;
@@ -420,37 +423,45 @@ template <class T, int DIM> __global__ void k_fill_bc_cells(RowArgs a) {
   }
 }
 
-// physical boundary faces: rows (dst, d, Ldst, kind, src, Lsrc)
-template <class T, int DIM> __global__ void k_fill_bc_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 6 * r;
-  const DPatch D = a.P[row[0]];
-  const int f = BX + row[1];
+// physical boundary faces (the box's d-faces)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_bc_faces(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]];
+  const int f = BX + box[1];
   T* B = (T*)a.fbuf + D.off + f * D.fs;
-  B[row[2]] = row[3] == 3 ? (T)a.inflow[f] : B[row[5]];
+  const int Ld = x[0] + D.ext[0] * (x[1] + D.ext[1] * x[2]);
+  if (box[2] == 3) {
+    B[Ld] = (T)a.inflow[f];
+  } else {
+    int gc[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) gc[e] = box[10 + e] >= 0 ? box[10 + e] : g[e];
+    B[Ld] = B[local_of(D, gc)];
+  }
 }
 
-template <int DIM> __device__ __forceinline__ void global_pos(const DPatch& P, int L, int* g) {
-  const int a = L % P.ext[0];
-  const int b = (L / P.ext[0]) % P.ext[1];
-  const int c = L / (P.ext[0] * P.ext[1]);
-  g[0] = P.lo[0] + a - 4;
-  g[1] = P.lo[1] + b - 4;
-  g[2] = DIM == 3 ? P.lo[2] + c - 4 : 0;
+// the coarse patch's local index of the parent of fine position g: the box's
+// aux is the periodic wrap of g, so (g + aux) >> 1 is the parent cell (for a
+// d-face, the coarse face coincident with or below the fine one)
+template <int DIM> __device__ __forceinline__ int parent_local(const DPatch& C, const int* g, const int* aux) {
+  int c[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) c[e] = e < DIM ? (g[e] + aux[e]) >> 1 : 0;
+  return local_of(C, c);
 }
 
-// prolonged ghost cells: rows (dst, Ldst, srcC, Lsrc); coarse data from cbuf
-// (the parent level's state at the start of its current sub-step)
-template <class T, int DIM> __global__ void k_prolong_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 4 * r;
-  const DPatch D = a.P[row[0]], C = a.P[row[2]];
-  int g[3];
-  global_pos<DIM>(D, row[1], g);
-  T* dst = (T*)a.fbuf + D.off + row[1];
-  const T* src = (const T*)a.cbuf + C.off + row[3];
+// prolonged ghost cells (Sec. 2 prolongation): minmod-limited linear
+// reconstruction of the parent cell at the child's centre; coarse data from
+// cbuf (the parent level's state at the start of its current sub-step)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolong_cells(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]], C = a.P[box[3]];
+  T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
+  const T* src = (const T*)a.cbuf + C.off + parent_local<DIM>(C, g, box + 10);
   const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
   constexpr int NCF = DIM == 3 ? 5 : 6;
 #pragma unroll
@@ -483,19 +494,19 @@ __device__ __forceinline__ T coincident(const T* b, const int* st, int n, const 
   return v;
 }
 
-// prolonged ghost faces: rows (dst, d, Ldst, srcC, Lsrc)
-template <class T, int DIM> __global__ void k_prolong_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 5 * r;
-  const DPatch D = a.P[row[0]], C = a.P[row[3]];
-  const int n = row[1];
-  int g[3];
-  global_pos<DIM>(D, row[2], g);
+// prolonged ghost faces (the box's n-faces): divergence-free (Balsara) from the
+// coarse faces
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolong_faces(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]], C = a.P[box[3]];
+  const int n = box[1];
+  const int Lc = parent_local<DIM>(C, g, box + 10);
   const int par[3] = {g[0] & 1, g[1] & 1, DIM == 3 ? (g[2] & 1) : 0};
   const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
   const T* cb = (const T*)a.cbuf + C.off;
-  const T* bn = cb + (BX + n) * C.fs + row[4];
+  const T* bn = cb + (BX + n) * C.fs + Lc;
   T v;
   if (!par[n]) {
     v = coincident<T, DIM>(bn, st, n, par);
@@ -507,7 +518,7 @@ template <class T, int DIM> __global__ void k_prolong_faces(RowArgs a) {
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
       if (t == n) continue;
-      const T* bt_lo = cb + (BX + t) * C.fs + row[4];
+      const T* bt_lo = cb + (BX + t) * C.fs + Lc;
       const T* bt_hi = bt_lo + st[t];
       const T s_hi = mm(bt_hi[0] - bt_hi[-st[n]], bt_hi[st[n]] - bt_hi[0]);
       const T s_lo = mm(bt_lo[0] - bt_lo[-st[n]], bt_lo[st[n]] - bt_lo[0]);
@@ -517,7 +528,16 @@ template <class T, int DIM> __global__ void k_prolong_faces(RowArgs a) {
     }
     v = T(0.5) * (lo_v + hi_v) + T(0.125) * corr;
   }
-  ((T*)a.fbuf)[D.off + (BX + n) * D.fs + row[2]] = v;
+  ((T*)a.fbuf)[D.off + (BX + n) * D.fs + x[0] + D.ext[0] * (x[1] + D.ext[1] * x[2])] = v;
+}
+
+template <int DIM> __device__ __forceinline__ void global_pos(const DPatch& P, int L, int* g) {
+  const int a = L % P.ext[0];
+  const int b = (L / P.ext[0]) % P.ext[1];
+  const int c = L / (P.ext[0] * P.ext[1]);
+  g[0] = P.lo[0] + a - 4;
+  g[1] = P.lo[1] + b - 4;
+  g[2] = DIM == 3 ? P.lo[2] + c - 4 : 0;
 }
 
 // ------------------------------------------------------------------ regrid
@@ -884,12 +904,17 @@ template <class T, int DIM> struct Impl {
     k_##NAME<T, DIM><<<cdiv(a.nrows, TPB), TPB, 0, s>>>(a);                             \
     if (nl) ++*nl;                                                                      \
   }
-  AMRK_ROWS(fill_same_cells)
-  AMRK_ROWS(fill_same_faces)
-  AMRK_ROWS(prolong_cells)
-  AMRK_ROWS(prolong_faces)
-  AMRK_ROWS(fill_bc_cells)
-  AMRK_ROWS(fill_bc_faces)
+#define AMRK_BOXES(NAME)                                                                \
+  static void NAME(const RowArgs& a, cudaStream_t s, int* nl) {                         \
+    if (!a.nrows) return;                                                               \
+    k_##NAME<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);                          \
+    if (nl) ++*nl;                                                                      \
+  }
+  AMRK_BOXES(prolong_cells)
+  AMRK_BOXES(prolong_faces)
+  AMRK_BOXES(fill_bc_cells)
+  AMRK_BOXES(fill_bc_faces)
+#undef AMRK_BOXES
   static void fill_runs_cells(const RowArgs& a, cudaStream_t s, int* nl) {
     if (!a.nrows) return;
     k_fill_box_cells<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
@@ -969,7 +994,7 @@ template <class T, int DIM> struct Impl {
     if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
   }
   static const Ops* ops() {
-    static const Ops o = {advance, reg_coarse, reg_fine, fill_same_cells, fill_same_faces, fill_runs_cells,
+    static const Ops o = {advance, reg_coarse, reg_fine, fill_runs_cells,
                           fill_runs_faces, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
