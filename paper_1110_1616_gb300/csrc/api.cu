@@ -440,6 +440,8 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
     H.per[d] = d >= H.dim || H.bc[d][0] == AMRMHD_BC_PERIODIC;
   }
   H.max_level = ctx->cfg.max_level;
+  H.ghost_from = ctx->stage_light ? ctx->stage_ghost_from : 0;
+  H.with_registers = !ctx->stage_light;
   std::vector<int32_t> rows(7 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     rows[7 * i] = patches[i].level;
@@ -462,7 +464,7 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
       ctx->off[q] = acc;
       acc += 8 * f;
       ctx->soff[q] = sacc;
-      if (!ctx->fused()) sacc += amrk::SC_N * f;
+      if (!ctx->fused() && !ctx->stage_light) sacc += amrk::SC_N * f;
     }
   ctx->state_elems = acc;
   ctx->scr_elems = sacc;

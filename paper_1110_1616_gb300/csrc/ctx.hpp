@@ -49,6 +49,11 @@ struct amrmhd_ctx {
   std::string err;
   amrmhd::Hierarchy H;
   bool have_h = false, bound = false;
+  // an intermediate regrid stage: ghost boxes only from level stage_ghost_from
+  // on, no register maps and no advance scratch (it is filled, flagged and
+  // copied, never advanced)
+  bool stage_light = false;
+  int stage_ghost_from = 0;
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
   int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1;

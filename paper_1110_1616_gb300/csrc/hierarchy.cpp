@@ -479,7 +479,8 @@ int Hierarchy::build(const int32_t* rows7, int n) {
     return 0;
   };
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int q = 0; q < np; ++q) gst[q] = ghost_patch(q, gbc[q], gbf[q], gerr[q]);
+  for (int q = 0; q < np; ++q)
+    if (p[q].level >= ghost_from) gst[q] = ghost_patch(q, gbc[q], gbf[q], gerr[q]);
   for (int q = 0; q < np; ++q)
     if (gst[q]) { err = gerr[q]; return gst[q]; }
   {
@@ -502,7 +503,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
   rng_restrict_cells.assign(nlev, {0, 0});
   rng_restrict_faces.assign(nlev, {0, 0});
   rng_reflux_cells.assign(nlev, {0, 0});
-  for (int l = 1; l < nlev; ++l) {
+  for (int l = 1; l < nlev && with_registers; ++l) {
     const int lc = l - 1;
     rng_cf_faces[l][0] = (int64_t)cf_faces.size() / 7;
     rng_cf_edges[l][0] = (int64_t)cf_edges.size() / 6;

@@ -37,6 +37,11 @@ struct Hierarchy {
   int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // 0 periodic, 1 outflow, 2 inflow
   int max_level = 0;
   int nlev = 0;
+  // partial builds (a regrid's intermediate stages): ghost boxes only for the
+  // patches of levels >= ghost_from, register/reflux/restriction maps only
+  // with with_registers; validation and neighbour lists are always complete
+  int ghost_from = 0;
+  bool with_registers = true;
   std::vector<HPatch> p;
   std::vector<std::vector<int>> level_patches;  // ids per level, ascending
   std::vector<std::vector<Nbr>> nbr;            // per patch, sorted by (q, shift)

@@ -25,33 +25,70 @@ struct Dense {  // a byte per cell of one level's domain
 
 std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags) {
   const int dim = H.dim;
+  const std::vector<int>& lp = H.level_patches[l];
+  // the dense arrays cover the level region's bounding box, aligned to blocks
+  // and widened by the 3-cell nesting margin; a dimension whose widened box
+  // reaches around the domain (periodic) or is bounded keeps the whole level
+  // extent, so wrapped neighbours are found as before
+  int off[3] = {0, 0, 0}, N[3], full[3];
+  for (int d = 0; d < 3; ++d) {
+    N[d] = H.N(l, d);
+    full[d] = 1;
+    if (d >= dim || lp.empty()) continue;
+    int lo = N[d], hi = 0;
+    for (int q : lp) {
+      lo = std::min(lo, H.p[q].lo[d]);
+      hi = std::max(hi, H.p[q].hi[d]);
+    }
+    lo = (lo / kBlock) * kBlock - 2 * kBlock;
+    hi = ((hi + kBlock - 1) / kBlock) * kBlock + 2 * kBlock;
+    if (lo >= 0 && hi <= N[d]) {
+      full[d] = 0;
+      off[d] = lo;
+      N[d] = hi - lo;
+    }
+  }
   Dense region, buf;
-  for (int d = 0; d < 3; ++d) region.n[d] = buf.n[d] = H.N(l, d);
+  for (int d = 0; d < 3; ++d) region.n[d] = buf.n[d] = N[d];
   const size_t ncell = (size_t)region.n[0] * region.n[1] * region.n[2];
   region.v.assign(ncell, 0);
   buf.v.assign(ncell, 0);
-  const std::vector<int>& lp = H.level_patches[l];
 #pragma omp parallel for schedule(dynamic, 1)
   for (size_t ip = 0; ip < lp.size(); ++ip) {  // patches are disjoint: no shared writes
     const HPatch& P = H.p[lp[ip]];
     for (int k = P.lo[2]; k < P.hi[2]; ++k)
       for (int j = P.lo[1]; j < P.hi[1]; ++j)
-        for (int i = P.lo[0]; i < P.hi[0]; ++i) region.v[region.at(i, j, k)] = 1;
+        for (int i = P.lo[0]; i < P.hi[0]; ++i) region.v[region.at(i - off[0], j - off[1], k - off[2])] = 1;
   }
-  // position inside the domain (periodic wrap), false if outside a bounded side
-  auto inside = [&](int* c) {
+  // a local position inside the level domain (periodic wrap in a whole-extent
+  // dimension), false if outside a bounded side; a position of a bounding-box
+  // dimension outside the box is outside the region
+  auto inside = [&](int* c, bool* in_box) {
+    *in_box = true;
     for (int d = 0; d < dim; ++d) {
-      if (H.per[d]) c[d] = H.wrapd(l, d, c[d]);
-      else if (c[d] < 0 || c[d] >= region.n[d]) return false;
+      if (full[d]) {
+        if (H.per[d]) c[d] = H.wrapd(l, d, c[d]);
+        else if (c[d] < 0 || c[d] >= region.n[d]) return false;
+      } else {
+        const int g = c[d] + off[d];
+        if (!H.per[d] && (g < 0 || g >= H.N(l, d))) return false;
+        if (c[d] < 0 || c[d] >= region.n[d]) *in_box = false;
+      }
     }
     return true;
   };
   const int kz = dim == 3 ? 1 : 0;
   // buffer of 2 cells: the flags dilated (Chebyshev) along x, then y, then z,
   // then restricted to the region
-  for (size_t f = 0; f + 2 < flags.size(); f += 3) buf.v[buf.at(flags[f], flags[f + 1], dim == 3 ? flags[f + 2] : 0)] = 1;
+  for (size_t f = 0; f + 2 < flags.size(); f += 3) {
+    int c[3] = {flags[f] - off[0], flags[f + 1] - off[1], dim == 3 ? flags[f + 2] - off[2] : 0};
+    bool ok = true;
+    for (int d = 0; d < 3; ++d) ok = ok && c[d] >= 0 && c[d] < region.n[d];
+    if (ok) buf.v[buf.at(c[0], c[1], c[2])] = 1;
+  }
   for (int d = 0; d < dim; ++d) {
     const int n = region.n[d];
+    const bool wrap = full[d] && H.per[d];
     const size_t st = d == 0 ? 1 : (d == 1 ? (size_t)region.n[0] : (size_t)region.n[0] * region.n[1]);
     const size_t lines = ncell / n;
     std::vector<uint8_t> src = buf.v;
@@ -66,7 +103,7 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
         if (!src[base + x * st]) continue;
         for (int o = -2; o <= 2; ++o) {
           int y = x + o;
-          if (H.per[d]) y = (y % n + n) % n;
+          if (wrap) y = (y % n + n) % n;
           else if (y < 0 || y >= n) continue;
           buf.v[base + y * st] = 1;
         }
@@ -96,48 +133,44 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
       for (int j = lo[1] - 3; j < hi[1] + 3 && allowed; ++j)
         for (int i = lo[0] - 3; i < hi[0] + 3 && allowed; ++i) {
           int p[3] = {i, j, k};
-          if (!inside(p)) continue;
-          if (!region.v[region.at(p[0], p[1], p[2])]) allowed = false;
+          bool in_box;
+          if (!inside(p, &in_box)) continue;
+          if (!in_box || !region.v[region.at(p[0], p[1], p[2])]) allowed = false;
         }
     if (allowed) ok[w] = 1;
   }
-  std::vector<size_t> wanted;
-  for (size_t w = 0; w < nblk; ++w)
-    if (ok[w]) wanted.push_back(w);
   std::vector<std::array<int, 7>> out;
-  for (size_t w : wanted) {
+  for (size_t w = 0; w < nblk; ++w) {
+    if (!ok[w]) continue;
     const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
-    {
-        if (!ok[w]) continue;
-        int sx = 1, sy = 1, sz = 1;
-        while (sx < kMaxBlocks && a + sx < nb[0] && ok[bi(a + sx, b, c)]) ++sx;
-        auto row = [&](int bb, int cc) {
-          for (int t = 0; t < sx; ++t)
-            if (!ok[bi(a + t, bb, cc)]) return false;
-          return true;
-        };
-        while (sy < kMaxBlocks && b + sy < nb[1] && row(b + sy, c)) ++sy;
-        if (dim == 3) {
-          auto slab = [&](int cc) {
-            for (int u = 0; u < sy; ++u)
-              if (!row(b + u, cc)) return false;
-            return true;
-          };
-          while (sz < kMaxBlocks && c + sz < nb[2] && slab(c + sz)) ++sz;
-        }
-        for (int z = 0; z < sz; ++z)
-          for (int y = 0; y < sy; ++y)
-            for (int x = 0; x < sx; ++x) ok[bi(a + x, b + y, c + z)] = 0;
-        std::array<int, 7> p;
-        p[0] = l + 1;
-        p[1] = 2 * kBlock * a;
-        p[2] = 2 * kBlock * b;
-        p[3] = dim == 3 ? 2 * kBlock * c : 0;
-        p[4] = 2 * kBlock * (a + sx);
-        p[5] = 2 * kBlock * (b + sy);
-        p[6] = dim == 3 ? 2 * kBlock * (c + sz) : 1;
-        out.push_back(p);
+    int sx = 1, sy = 1, sz = 1;
+    while (sx < kMaxBlocks && a + sx < nb[0] && ok[bi(a + sx, b, c)]) ++sx;
+    auto row = [&](int bb, int cc) {
+      for (int t = 0; t < sx; ++t)
+        if (!ok[bi(a + t, bb, cc)]) return false;
+      return true;
+    };
+    while (sy < kMaxBlocks && b + sy < nb[1] && row(b + sy, c)) ++sy;
+    if (dim == 3) {
+      auto slab = [&](int cc) {
+        for (int u = 0; u < sy; ++u)
+          if (!row(b + u, cc)) return false;
+        return true;
+      };
+      while (sz < kMaxBlocks && c + sz < nb[2] && slab(c + sz)) ++sz;
     }
+    for (int z = 0; z < sz; ++z)
+      for (int y = 0; y < sy; ++y)
+        for (int x = 0; x < sx; ++x) ok[bi(a + x, b + y, c + z)] = 0;
+    std::array<int, 7> p;
+    p[0] = l + 1;
+    p[1] = 2 * (kBlock * a + off[0]);
+    p[2] = 2 * (kBlock * b + off[1]);
+    p[3] = dim == 3 ? 2 * (kBlock * c + off[2]) : 0;
+    p[4] = 2 * (kBlock * (a + sx) + off[0]);
+    p[5] = 2 * (kBlock * (b + sy) + off[1]);
+    p[6] = dim == 3 ? 2 * (kBlock * (c + sz) + off[2]) : 1;
+    out.push_back(p);
   }
   return out;
 }

@@ -61,11 +61,14 @@ amrmhd_status flag_level(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta, st
 }
 
 // a stage context with the given patches, a library-owned arena and the
-// option settings of ctx
-amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, amrmhd_ctx** out) {
+// option settings of ctx; a light stage (ghost_from >= 0) has the fill maps of
+// the levels from ghost_from on only, no register maps and no scratch
+amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, int ghost_from, amrmhd_ctx** out) {
   amrmhd_ctx* c = nullptr;
   amrmhd_status st = amrmhd_create(&ctx->cfg, ctx->stream, &c);
   if (st) return fail(ctx, st, "regrid: create");
+  c->stage_light = ghost_from >= 0;
+  c->stage_ghost_from = std::max(ghost_from, 0);
   c->opt_advance = ctx->opt_advance;
   c->opt_graph = ctx->opt_graph;
   c->opt_tile = ctx->opt_tile;
@@ -201,16 +204,15 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
       for (int d = 0; d < 3; ++d) { p.lo[d] = b[1 + d]; p.hi[d] = b[4 + d]; }
       next.push_back(p);
     }
+    // a light stage: levels 0..l as in prev (copied with their filled ghosts),
+    // the new level l+1 transferred, filled and flagged
     amrmhd_ctx* S = nullptr;
     t0 = now_us();
-    st = make_stage(ctx, next, &S);
+    st = make_stage(ctx, next, l + 1, &S);
     us[2] += now_us() - t0;
     t0 = now_us();
     if (!st) st = copy_levels(ctx, prev, S, l);
-    if (!st) {
-      for (int q = 0; q <= l; ++q) op_fill(S, q, 1, &nl);
-      st = transfer(ctx, S, ctx, l + 1);
-    }
+    if (!st) st = transfer(ctx, S, ctx, l + 1);
     us[3] += now_us() - t0;
     if (!st) {
       t0 = now_us();
@@ -229,15 +231,23 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     prevH = &S->H;
     ps = next;
   }
-  if (prev == ctx) {
-    // no level above 0: a context with level 0 only
+  {
+    // the final context: the whole hierarchy with all its maps, every level's
+    // data (with filled ghosts) from the last stage
     amrmhd_ctx* S = nullptr;
-    st = make_stage(ctx, ps, &S);
-    if (!st) st = copy_levels(ctx, ctx, S, 0);
+    t0 = now_us();
+    st = make_stage(ctx, ps, -1, &S);
+    us[2] += now_us() - t0;
+    t0 = now_us();
+    const int top = (int)S->H.nlev - 1;
+    if (!st) st = copy_levels(ctx, prev, S, top);
+    us[3] += now_us() - t0;
     if (st) {
       if (S) amrmhd_destroy(S);
+      if (prev != ctx) amrmhd_destroy(prev);
       return st;
     }
+    if (prev != ctx) amrmhd_destroy(prev);
     prev = S;
   }
   CUR(cudaStreamSynchronize(ctx->stream));

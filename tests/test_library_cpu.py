@@ -178,6 +178,10 @@ def regrid_cases():
     out.append(("clumps2d", 2, (32, 32, 1), inputs.clumps_2d(32, 3).patches, None))
     out.append(("bounded2d", 2, (32, 32, 1), inputs.clumps_2d(32, 3).patches, (2, 1, 1, 1, 0, 0)))
     out.append(("rand3d", 3, (16, 16, 16), inputs.random_hierarchy(3, 50, base=16, nlev=2), None))
+    # fine levels well inside the domain: the clustering works on the region's
+    # bounding box there
+    out.append(("clumps3d", 3, (32, 32, 32), inputs.clumps_3d_small(32, 3).patches, None))
+    out.append(("clumps3d_bounded", 3, (32, 32, 32), inputs.clumps_3d_small(32, 3).patches, (1, 1, 2, 1, 1, 1)))
     return out
 
 
