@@ -234,7 +234,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     ctx.regrid(theta, pb.nlev)
     tiles = ctx.autotune(3)
     ctx.step(1, want_dt=False)
-    updates, t_steps, t_regrid, breakdown = 0, 0.0, 0.0, [0, 0, 0, 0]
+    updates, t_steps, t_regrid, breakdown = 0, 0.0, 0.0, [0, 0, 0, 0, 0]
     nreg = 0
     for i in range(0, steps, regrid_every):
         k = min(regrid_every, steps - i)
@@ -247,7 +247,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
             ctx.regrid(theta, pb.nlev)
             t_regrid += time.perf_counter() - t0
             nreg += 1
-            for q in range(4):
+            for q in range(5):
                 breakdown[q] += ctx.query(A.Q_REGRID_FLAG_US + q)
             ctx.autotune(2)
     ms_c, _ = timed_steps(ctx, stream, 2)
@@ -261,7 +261,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
            "steps": steps, "regrid_every": regrid_every, "theta": theta, "regrids": nreg,
            "regrid_ms_mean": 1e3 * t_regrid / max(nreg, 1),
            "regrid_host_us_mean": {k: v / max(nreg, 1) for k, v in
-                                   zip(("flag", "cluster", "build", "transfer"), breakdown)},
+                                   zip(("flag", "cluster", "build", "transfer", "build_host_maps"), breakdown)},
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
            "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
            "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}

@@ -302,7 +302,10 @@ enum {
    * flag kernel, list copy), clustering, building the stage hierarchies, maps
    * and arenas, and the data transfer */
   AMRMHD_Q_REGRID_FLAG_US = 6, AMRMHD_Q_REGRID_CLUSTER_US = 7, AMRMHD_Q_REGRID_BUILD_US = 8,
-  AMRMHD_Q_REGRID_TRANSFER_US = 9
+  AMRMHD_Q_REGRID_TRANSFER_US = 9,
+  /* of AMRMHD_Q_REGRID_BUILD_US, the host building of hierarchies and maps
+   * (the rest is device memory and map upload) */
+  AMRMHD_Q_REGRID_MAPS_US = 10
 };
 amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
 

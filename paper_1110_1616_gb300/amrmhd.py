@@ -19,7 +19,7 @@ MAPS = {
     "emf_faces": 5, "restrict_cells": 6, "restrict_faces": 7, "reflux_cells": 8,
 }
 Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
-Q_REGRID_FLAG_US, Q_REGRID_CLUSTER_US, Q_REGRID_BUILD_US, Q_REGRID_TRANSFER_US = range(6, 10)
+Q_REGRID_FLAG_US, Q_REGRID_CLUSTER_US, Q_REGRID_BUILD_US, Q_REGRID_TRANSFER_US, Q_REGRID_MAPS_US = range(6, 11)
 OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT = 0, 1, 2, 3
 
 

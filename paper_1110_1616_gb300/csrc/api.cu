@@ -546,16 +546,22 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
   ctx->hist_cap = kHistCap;
   ctx->d_hist = dbuf<double>(ctx, kHistCap, &e);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-  // per-level lists
+  // per-level lists: gathered into one host image (each list 256-byte aligned),
+  // then one device allocation and one copy
   ctx->lev.assign(nlev, LevelDev());
+  std::vector<int32_t> pack;
+  std::vector<std::pair<DevList*, size_t>> pend;  // list -> element offset in pack
   auto upload = [&](const std::vector<int32_t>& v, DevList& out, int width) -> bool {
     out.n = (int64_t)v.size() / width;
-    if (v.empty()) { out.p = nullptr; return true; }
-    out.p = dbuf<int>(ctx, v.size(), &e);
-    if (e != cudaSuccess) return false;
-    e = cudaMemcpy(out.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice);
-    return e == cudaSuccess;
+    out.p = nullptr;
+    if (v.empty()) return true;
+    const size_t o = (pack.size() + 63) / 64 * 64;
+    pack.resize(o + v.size());
+    std::copy(v.begin(), v.end(), pack.begin() + o);
+    pend.push_back({&out, o});
+    return true;
   };
+  std::vector<DevList> id_lists(nlev);
   for (int l = 0; l < nlev; ++l) {
     LevelDev& L = ctx->lev[l];
     const std::vector<int>& ids = H.level_patches[l];
@@ -565,9 +571,7 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       for (int q : ids) L.maxn[d] = std::max(L.maxn[d], H.p[q].n[d]);
       ctx->maxn_all[d] = std::max(ctx->maxn_all[d], L.maxn[d]);
     }
-    L.ids = dbuf<int>(ctx, ids.size(), &e);
-    if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-    CU(cudaMemcpy(L.ids, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice));
+    upload(ids, id_lists[l], 1);
     // ghost fill lists of this level from the hierarchy's boxes (see LevelDev)
     std::vector<int32_t> rc, cc, rf, cf, pcb, pcc, pfb, pfc, bcb, bcc, bfb, bfc;
     std::vector<int32_t> rc2, cc2, rf2, cf2, bcb2, bcc2, bfb2, bfc2;
@@ -646,9 +650,17 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     }
     if (!ok) return fail(ctx, AMRMHD_ECUDA, std::string("map upload: ") + cudaGetErrorString(e));
   }
+  if (!pack.empty()) {
+    int* dlists = dbuf<int>(ctx, pack.size(), &e);
+    if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+    CU(cudaMemcpy(dlists, pack.data(), sizeof(int) * pack.size(), cudaMemcpyHostToDevice));
+    for (auto& pr : pend) pr.first->p = dlists + pr.second;
+  }
+  for (int l = 0; l < nlev; ++l) ctx->lev[l].ids = id_lists[l].p;
   ctx->cur.assign(nlev, 0);
   ctx->start.assign(nlev, 0);
-  for (int l = 0; l + 1 < nlev; ++l) {
+  // side streams for concurrent levels (a regrid's light stages never step)
+  for (int l = 0; l + 1 < nlev && !ctx->stage_light; ++l) {
     cudaStream_t st = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1005,7 +1017,8 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
     case AMRMHD_Q_REGRID_FLAG_US:
     case AMRMHD_Q_REGRID_CLUSTER_US:
     case AMRMHD_Q_REGRID_BUILD_US:
-    case AMRMHD_Q_REGRID_TRANSFER_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
+    case AMRMHD_Q_REGRID_TRANSFER_US:
+    case AMRMHD_Q_REGRID_MAPS_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
     default: return fail(ctx, AMRMHD_EINVAL, "unknown query");
   }
 }

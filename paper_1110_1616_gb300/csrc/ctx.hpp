@@ -94,7 +94,7 @@ struct amrmhd_ctx {
   long long launches = 0;
   // host wall time of the last regrid, microseconds: flagging, clustering,
   // hierarchy and map building with the stage arenas, data transfer
-  long long regrid_us[4] = {0, 0, 0, 0};
+  long long regrid_us[5] = {0, 0, 0, 0, 0};
   // inter-level concurrency: side stream and fork/join events per level
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_fork, ev_join;

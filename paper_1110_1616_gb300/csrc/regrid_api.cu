@@ -63,7 +63,8 @@ amrmhd_status flag_level(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta, st
 // a stage context with the given patches, a library-owned arena and the
 // option settings of ctx; a light stage (ghost_from >= 0) has the fill maps of
 // the levels from ghost_from on only, no register maps and no scratch
-amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, int ghost_from, amrmhd_ctx** out) {
+amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, int ghost_from, amrmhd_ctx** out,
+                         long long* maps_us) {
   amrmhd_ctx* c = nullptr;
   amrmhd_status st = amrmhd_create(&ctx->cfg, ctx->stream, &c);
   if (st) return fail(ctx, st, "regrid: create");
@@ -74,7 +75,9 @@ amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, i
   c->opt_tile = ctx->opt_tile;
   c->opt_concurrent = ctx->opt_concurrent;
   size_t bytes = 0;
+  const long long t0 = now_us();
   st = amrmhd_set_hierarchy(c, ps.data(), (int32_t)ps.size(), &bytes);
+  *maps_us += now_us() - t0;
   if (st) {
     std::string m = c->err;
     amrmhd_destroy(c);
@@ -182,7 +185,7 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     for (int d = 0; d < 3; ++d) { p.lo[d] = ctx->H.p[q].lo[d]; p.hi[d] = ctx->H.p[q].hi[d]; }
     ps.push_back(p);
   }
-  long long us[4] = {0, 0, 0, 0}, t0 = now_us();
+  long long us[5] = {0, 0, 0, 0, 0}, t0 = now_us();
   // level 0 of the old context: fill and flag
   int nl = 0;
   op_fill(ctx, 0, 1, &nl);
@@ -208,7 +211,7 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     // the new level l+1 transferred, filled and flagged
     amrmhd_ctx* S = nullptr;
     t0 = now_us();
-    st = make_stage(ctx, next, l + 1, &S);
+    st = make_stage(ctx, next, l + 1, &S, &us[4]);
     us[2] += now_us() - t0;
     t0 = now_us();
     if (!st) st = copy_levels(ctx, prev, S, l);
@@ -236,7 +239,7 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     // data (with filled ghosts) from the last stage
     amrmhd_ctx* S = nullptr;
     t0 = now_us();
-    st = make_stage(ctx, ps, -1, &S);
+    st = make_stage(ctx, ps, -1, &S, &us[4]);
     us[2] += now_us() - t0;
     t0 = now_us();
     const int top = (int)S->H.nlev - 1;
@@ -257,7 +260,7 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
   std::swap(ctx->own_stream, prev->own_stream);
   ctx->launches += prev->launches;
   amrmhd_destroy(prev);
-  for (int i = 0; i < 4; ++i) ctx->regrid_us[i] = us[i];
+  for (int i = 0; i < 5; ++i) ctx->regrid_us[i] = us[i];
   return AMRMHD_OK;
 }
 
