@@ -6,6 +6,8 @@
 // Pipeline per iteration t (planes in patch-local storage coordinates; the
 // output z range is [zlo, zhi) = [4-w, n_z+4+w)):
 //   S1  W at plane t                     (tile + 2 halo)        -> ring of 3
+//       (and the normal-B differences of the tile + 1 halo; then cp.async
+//       prefetch of the stored values of the plane S5 updates)
 //   S2  slopes, predictor, reference EMF at plane p = t-1 (tile + 1 halo)
 //   S3  HLLD fluxes: x- and y-faces of plane p, z-faces of face plane p
 //   S4  edge EMFs: E_z at plane p, E_x and E_y at edge plane p
@@ -39,7 +41,18 @@ template <class T, int TX_, int TY_> struct FusedSmem {
   T ez[2][Q];
   T ex[2][Q];
   T ey[2][Q];
+  T db[2][3][Q];                 // normal-B face differences of the Q region (slopes of B_d along d)
+  T up[9][(TX + 1) * (TY + 1)];  // the update plane's stored values (8 fields, then B_z one plane up)
 };
+
+// asynchronous 4- or 8-byte global -> shared copy (cp.async, no registers)
+template <class T> __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <class T>
 __device__ __forceinline__ void hlld_face(const T* wl, const T* wr, int D, T gamma, T* out8) {
@@ -60,7 +73,8 @@ __device__ __forceinline__ void hlld_face(const T* wl, const T* wr, int D, T gam
 }
 
 template <class T>
-__device__ __forceinline__ void load_recover(const T* U, long long fs, int L, int sy, int sz, double gm1, T* w) {
+__device__ __forceinline__ void load_recover(const T* U, long long fs, int L, int sy, int sz, double gm1, T* w,
+                                             T* dB = nullptr) {
   T u[5], bl[3], br[3];
 #pragma unroll
   for (int f = 0; f < 5; ++f) u[f] = U[f * fs + L];
@@ -68,6 +82,10 @@ __device__ __forceinline__ void load_recover(const T* U, long long fs, int L, in
   bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + sy];
   bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + sz];
   recover_t(u, bl, br, gm1, w);
+  if (dB) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dB[d] = br[d] - bl[d];
+  }
 }
 
 template <class T, int VAR>
@@ -104,17 +122,40 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
     // ---------------- S1: primitives of plane t
     if (t <= zhi + 1) {
       const int slot = (t + 3) % 3;
+      const int r2t = (t + 2) % 2;
       for (int c = threadIdx.x; c < wx * wy; c += nth) {
         const int x = x0 - 2 + c % wx, y = y0 - 2 + c / wx;
-        T wv[8];
-        load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv);
+        T wv[8], dB[3];
+        load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB);
         const int i = widx(x, y);
 #pragma unroll
         for (int f = 0; f < 8; ++f) sm.w[slot][f][i] = wv[f];
+        if (x >= x0 - 1 && x < x0 + tx + 1 && y >= y0 - 1 && y < y0 + ty + 1) {
+          const int q = qidx(x, y);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) sm.db[r2t][d][q] = dB[d];
+        }
       }
     }
     __syncthreads();
     const int p = t - 1;
+    // prefetch of the stored values the update of plane p-1 (S5) reads: every
+    // thread has left the previous S5, and the copies land before S5's barrier
+    {
+      const int qz = p - 1;
+      if (qz >= zlo && qz < zhi) {
+        const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
+        const int nf = qz == zhi - 1 ? 9 : 8;
+        for (int c = threadIdx.x; c < nf * nx * ny; c += nth) {
+          const int f = c / (nx * ny), cc = c % (nx * ny);
+          const int x = x0 + cc % nx, y = y0 + cc / nx;
+          const int L = x + sy * y + sz * qz;
+          const T* src = f < 8 ? U + f * fs + L : U + BZ * fs + L + sz;
+          cp_async_elem<T>(&sm.up[f][(x - x0) + (TX + 1) * (y - y0)], src);
+        }
+      }
+      cp_async_commit();
+    }
     // ---------------- S2: slopes and predictor of plane p
     if (p >= zlo - 1 && p <= zhi) {
       const int sm1 = (p - 1 + 3) % 3, s0 = (p + 3) % 3, sp1 = (p + 1 + 3) % 3;
@@ -122,16 +163,15 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
       for (int c = threadIdx.x; c < qx * qy; c += nth) {
         const int x = x0 - 1 + c % qx, y = y0 - 1 + c / qx;
         const int i = widx(x, y);
-        const int L = x + sy * y + sz * p;
         T wc[8], s[3][8];
+        const int qd = qidx(x, y);
 #pragma unroll
         for (int f = 0; f < 8; ++f) wc[f] = sm.w[s0][f][i];
 #pragma unroll
         for (int f = 0; f < 8; ++f) {
-          s[0][f] = f == BX ? U[BX * fs + L + 1] - U[BX * fs + L] : mm(wc[f] - sm.w[s0][f][i - 1], sm.w[s0][f][i + 1] - wc[f]);
-          s[1][f] = f == BY ? U[BY * fs + L + sy] - U[BY * fs + L]
-                            : mm(wc[f] - sm.w[s0][f][i - PX], sm.w[s0][f][i + PX] - wc[f]);
-          s[2][f] = f == BZ ? U[BZ * fs + L + sz] - U[BZ * fs + L] : mm(wc[f] - sm.w[sm1][f][i], sm.w[sp1][f][i] - wc[f]);
+          s[0][f] = f == BX ? sm.db[r2][0][qd] : mm(wc[f] - sm.w[s0][f][i - 1], sm.w[s0][f][i + 1] - wc[f]);
+          s[1][f] = f == BY ? sm.db[r2][1][qd] : mm(wc[f] - sm.w[s0][f][i - PX], sm.w[s0][f][i + PX] - wc[f]);
+          s[2][f] = f == BZ ? sm.db[r2][2][qd] : mm(wc[f] - sm.w[sm1][f][i], sm.w[sp1][f][i] - wc[f]);
         }
         const T ir = T(1) / wc[0];
         T wh[8], dw[8];
@@ -245,6 +285,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
         }
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     // ---------------- S5: update cell plane q = p-1
     const int qz = p - 1;
@@ -256,10 +297,11 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
         const bool in_x = x < x0 + tx, in_y = y < y0 + ty;
         const int L = x + sy * y + sz * qz;
         const int q = qidx(x, y);
+        const int u = (x - x0) + (TX + 1) * (y - y0);
         if (in_x && in_y) {
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
-            T v = U[n * fs + L];
+            T v = sm.up[n][u];
             v = v - dtd[0] * (sm.fx[rq][n][q + 1] - sm.fx[rq][n][q]);
             v = v - dtd[1] * (sm.fy[rq][n][q + QX] - sm.fy[rq][n][q]);
             v = v - dtd[2] * (sm.fz[rp][n][q] - sm.fz[rq][n][q]);
@@ -267,26 +309,26 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
           }
           // B_z of face plane qz (and the top face plane on the last plane)
           {
-            T v = U[BZ * fs + L];
+            T v = sm.up[BZ][u];
             v = v - dtd[0] * (sm.ey[rq][q + 1] - sm.ey[rq][q]);
             v = v + dtd[1] * (sm.ex[rq][q + QX] - sm.ex[rq][q]);
             V[BZ * fs + L] = v;
           }
           if (qz == zhi - 1) {
-            T v = U[BZ * fs + L + sz];
+            T v = sm.up[8][u];
             v = v - dtd[0] * (sm.ey[rp][q + 1] - sm.ey[rp][q]);
             v = v + dtd[1] * (sm.ex[rp][q + QX] - sm.ex[rp][q]);
             V[BZ * fs + L + sz] = v;
           }
         }
         if (in_y) {  // B_x at (x, y, qz)
-          T v = U[BX * fs + L];
+          T v = sm.up[BX][u];
           v = v - dtd[1] * (sm.ez[rq][q + QX] - sm.ez[rq][q]);
           v = v + dtd[2] * (sm.ey[rp][q] - sm.ey[rq][q]);
           V[BX * fs + L] = v;
         }
         if (in_x) {  // B_y at (x, y, qz)
-          T v = U[BY * fs + L];
+          T v = sm.up[BY][u];
           v = v - dtd[2] * (sm.ex[rp][q] - sm.ex[rq][q]);
           v = v + dtd[0] * (sm.ez[rq][q + 1] - sm.ez[rq][q]);
           V[BY * fs + L] = v;
