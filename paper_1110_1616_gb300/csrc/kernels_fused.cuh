@@ -88,8 +88,10 @@ __device__ __forceinline__ void load_recover(const T* U, long long fs, int L, in
   }
 }
 
+// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread)
 template <class T, int VAR>
-__global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelArgs a, int ntx) {
+__global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
+    k_advance3d_fused(LevelArgs a, int ntx) {
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
   constexpr int TX = S::TX, TY = S::TY, PX = S::PX, QX = S::QX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -123,8 +125,10 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
     if (t <= zhi + 1) {
       const int slot = (t + 3) % 3;
       const int r2t = (t + 2) % 2;
-      for (int c = threadIdx.x; c < wx * wy; c += nth) {
-        const int x = x0 - 2 + c % wx, y = y0 - 2 + c / wx;
+      for (int c = threadIdx.x; c < PX * S::PY; c += nth) {
+        const int xi = c % PX, yi = c / PX;  // constant divisors; positions beyond a partial tile skip
+        if (xi >= wx || yi >= wy) continue;
+        const int x = x0 - 2 + xi, y = y0 - 2 + yi;
         T wv[8], dB[3];
         load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB);
         const int i = widx(x, y);
@@ -145,13 +149,14 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
       const int qz = p - 1;
       if (qz >= zlo && qz < zhi) {
         const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
-        const int nf = qz == zhi - 1 ? 9 : 8;
-        for (int c = threadIdx.x; c < nf * nx * ny; c += nth) {
-          const int f = c / (nx * ny), cc = c % (nx * ny);
-          const int x = x0 + cc % nx, y = y0 + cc / nx;
-          const int L = x + sy * y + sz * qz;
-          const T* src = f < 8 ? U + f * fs + L : U + BZ * fs + L + sz;
-          cp_async_elem<T>(&sm.up[f][(x - x0) + (TX + 1) * (y - y0)], src);
+        const bool top = qz == zhi - 1;
+        for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
+          const int xi = c % (TX + 1), yi = c / (TX + 1);
+          if (xi >= nx || yi >= ny) continue;
+          const int L = (x0 + xi) + sy * (y0 + yi) + sz * qz;
+#pragma unroll
+          for (int f = 0; f < 8; ++f) cp_async_elem<T>(&sm.up[f][c], U + f * fs + L);
+          if (top) cp_async_elem<T>(&sm.up[8][c], U + BZ * fs + L + sz);
         }
       }
       cp_async_commit();
@@ -160,8 +165,10 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
     if (p >= zlo - 1 && p <= zhi) {
       const int sm1 = (p - 1 + 3) % 3, s0 = (p + 3) % 3, sp1 = (p + 1 + 3) % 3;
       const int r2 = (p + 2) % 2;
-      for (int c = threadIdx.x; c < qx * qy; c += nth) {
-        const int x = x0 - 1 + c % qx, y = y0 - 1 + c / qx;
+      for (int c = threadIdx.x; c < QX * S::QY; c += nth) {
+        const int xi = c % QX, yi = c / QX;
+        if (xi >= qx || yi >= qy) continue;
+        const int x = x0 - 1 + xi, y = y0 - 1 + yi;
         const int i = widx(x, y);
         T wc[8], s[3][8];
         const int qd = qidx(x, y);
@@ -203,67 +210,77 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
     // ---------------- S3: fluxes (x, y faces of plane p; z faces of face plane p)
     if (p >= zlo - 1 && p <= zhi) {
       const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
-      const int nfx = (tx + 1) * (ty + 2), nfy = (tx + 2) * (ty + 1);
-      const int nfz = p >= zlo ? (tx + 2) * (ty + 2) : 0;
-      for (int c = threadIdx.x; c < nfx + nfy + nfz; c += nth) {
-        T wl[8], wr[8], out[8];
-        int q;
-        if (c < nfx) {  // x-face at x (cells x-1, x), y in [y0-1, y0+ty+1)
-          const int x = x0 + c % (tx + 1), y = y0 - 1 + c / (tx + 1);
-          q = qidx(x, y);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) {
-            wl[f] = sm.wh[r2][f][q - 1] + T(0.5) * sm.sx[f][q - 1];
-            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sx[f][q];
-          }
-          hlld_face<T>(wl, wr, 0, gamma, out);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) sm.fx[r2][f][q] = out[f];
-        } else if (c < nfx + nfy) {  // y-face at y (cells y-1, y), x in [x0-1, x0+tx+1)
-          const int cc = c - nfx;
-          const int x = x0 - 1 + cc % (tx + 2), y = y0 + cc / (tx + 2);
-          q = qidx(x, y);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) {
-            wl[f] = sm.wh[r2][f][q - QX] + T(0.5) * sm.sy[f][q - QX];
-            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sy[f][q];
-          }
-          hlld_face<T>(wl, wr, 1, gamma, out);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) sm.fy[r2][f][q] = out[f];
+      constexpr int NFX = (TX + 1) * (S::QY), NFY = (QX) * (TY + 1), NFZ = QX * S::QY, Q = S::Q;
+      const int nf = NFX + NFY + (p >= zlo ? NFZ : 0);
+      for (int c = threadIdx.x; c < nf; c += nth) {
+        // one face: direction D, its high-side cell (x, y) and the offset of its low-side cell
+        int D, x, y, lo;
+        const T *whl, *whr, *sl, *sr;
+        T* fo;
+        if (c < NFX) {  // x-face at x (cells x-1, x), y in [y0-1, y0+ty+1)
+          const int xi = c % (TX + 1), yi = c / (TX + 1);
+          if (xi > tx || yi >= ty + 2) continue;
+          D = 0; x = x0 + xi; y = y0 - 1 + yi; lo = -1;
+          whl = whr = &sm.wh[r2][0][0];
+          sl = sr = &sm.sx[0][0];
+          fo = &sm.fx[r2][0][0];
+        } else if (c < NFX + NFY) {  // y-face at y (cells y-1, y), x in [x0-1, x0+tx+1)
+          const int cc = c - NFX, xi = cc % QX, yi = cc / QX;
+          if (xi >= tx + 2 || yi > ty) continue;
+          D = 1; x = x0 - 1 + xi; y = y0 + yi; lo = -QX;
+          whl = whr = &sm.wh[r2][0][0];
+          sl = sr = &sm.sy[0][0];
+          fo = &sm.fy[r2][0][0];
         } else {  // z-face at face plane p (cells p-1, p)
-          const int cc = c - nfx - nfy;
-          const int x = x0 - 1 + cc % (tx + 2), y = y0 - 1 + cc / (tx + 2);
-          q = qidx(x, y);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) {
-            wl[f] = sm.wh[rm][f][q] + T(0.5) * sm.sz[rm][f][q];
-            wr[f] = sm.wh[r2][f][q] - T(0.5) * sm.sz[r2][f][q];
-          }
-          hlld_face<T>(wl, wr, 2, gamma, out);
-#pragma unroll
-          for (int f = 0; f < 8; ++f) sm.fz[r2][f][q] = out[f];
+          const int cc = c - NFX - NFY, xi = cc % QX, yi = cc / QX;
+          if (xi >= tx + 2 || yi >= ty + 2) continue;
+          D = 2; x = x0 - 1 + xi; y = y0 - 1 + yi; lo = 0;
+          whl = &sm.wh[rm][0][0];
+          whr = &sm.wh[r2][0][0];
+          sl = &sm.sz[rm][0][0];
+          sr = &sm.sz[r2][0][0];
+          fo = &sm.fz[r2][0][0];
         }
+        const int q = qidx(x, y), ql = q + lo;
+        const int n = D, t = D == 2 ? 0 : D + 1, u = D == 0 ? 2 : D - 1;
+        // the predicted face states, read in the face's rotated order (rho, v_n,
+        // v_t, v_u, p, B_t, B_u), and the mean normal field; fluxes stored back by field
+        const int fi[7] = {RHO, MX + n, MX + t, MX + u, EN, BX + t, BX + u};
+        T qlv[7], qrv[7], fr[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          qlv[k] = whl[fi[k] * Q + ql] + T(0.5) * sl[fi[k] * Q + ql];
+          qrv[k] = whr[fi[k] * Q + q] - T(0.5) * sr[fi[k] * Q + q];
+        }
+        const T bnl = whl[(BX + n) * Q + ql] + T(0.5) * sl[(BX + n) * Q + ql];
+        const T bnr = whr[(BX + n) * Q + q] - T(0.5) * sr[(BX + n) * Q + q];
+        hlld_flux<T>(qlv, qrv, T(0.5) * (bnl + bnr), gamma, fr);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) fo[fi[k] * Q + q] = fr[k];
+        fo[(BX + n) * Q + q] = T(0);
       }
     }
     __syncthreads();
     // ---------------- S4: edge EMFs
     if (p >= zlo && p <= zhi) {
       const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
-      const int nez = p < zhi ? (tx + 1) * (ty + 1) : 0;
-      const int nex = tx * (ty + 1), ney = (tx + 1) * ty;
-      for (int c = threadIdx.x; c < nez + nex + ney; c += nth) {
+      constexpr int NEZ = (TX + 1) * (TY + 1), NEX = TX * (TY + 1), NEY = (TX + 1) * TY;
+      const int nez = p < zhi ? NEZ : 0;
+      for (int c = threadIdx.x; c < nez + NEX + NEY; c += nth) {
         if (c < nez) {  // E_z at corner (x-1/2, y-1/2) of plane p: a = x, b = y
-          const int x = x0 + c % (tx + 1), y = y0 + c / (tx + 1);
+          const int xi = c % (TX + 1), yi = c / (TX + 1);
+          if (xi > tx || yi > ty) continue;
+          const int x = x0 + xi, y = y0 + yi;
           const int q11 = qidx(x, y), q01 = q11 - 1, q10 = q11 - QX, q00 = q11 - 1 - QX;
           const T ea_hi = -sm.fx[r2][BY][q11], ea_lo = -sm.fx[r2][BY][q10];
           const T eb_hi = sm.fy[r2][BX][q11], eb_lo = sm.fy[r2][BX][q01];
           sm.ez[r2][q11] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[r2][2][q00], sm.ref[r2][2][q10],
                                      sm.ref[r2][2][q01], sm.ref[r2][2][q11], sm.fx[r2][RHO][q10], sm.fx[r2][RHO][q11],
                                      sm.fy[r2][RHO][q01], sm.fy[r2][RHO][q11]);
-        } else if (c < nez + nex) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
-          const int cc = c - nez;
-          const int x = x0 + cc % tx, y = y0 + cc / tx;
+        } else if (c < nez + NEX) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
+          const int cc = c - nez, xi = cc % TX, yi = cc / TX;
+          if (xi >= tx || yi > ty) continue;
+          const int x = x0 + xi, y = y0 + yi;
           const int q = qidx(x, y), qm = q - QX;
           // a-faces = y-faces at rows z = p-1, p; b-faces = z-faces at columns y-1, y
           const T ea_lo = -sm.fy[rm][BZ][q], ea_hi = -sm.fy[r2][BZ][q];
@@ -272,8 +289,9 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
                                    sm.ref[r2][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
                                    sm.fz[r2][RHO][q]);
         } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
-          const int cc = c - nez - nex;
-          const int x = x0 + cc % (tx + 1), y = y0 + cc / (tx + 1);
+          const int cc = c - nez - NEX, xi = cc % (TX + 1), yi = cc / (TX + 1);
+          if (xi > tx || yi >= ty) continue;
+          const int x = x0 + xi, y = y0 + yi;
           const int q = qidx(x, y), qm = q - 1;
           // a-faces = z-faces at rows x-1, x; b-faces = x-faces at columns z = p-1, p
           const T ea_lo = -sm.fz[r2][BX][qm], ea_hi = -sm.fz[r2][BX][q];
@@ -292,12 +310,14 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, 1) k_advance3d_fused(LevelA
     if (qz >= zlo && qz < zhi) {
       const int rq = (qz + 2) % 2, rp = (p + 2) % 2;
       const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
-      for (int c = threadIdx.x; c < nx * ny; c += nth) {
-        const int x = x0 + c % nx, y = y0 + c / nx;
+      for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
+        const int xi = c % (TX + 1), yi = c / (TX + 1);
+        if (xi >= nx || yi >= ny) continue;
+        const int x = x0 + xi, y = y0 + yi;
         const bool in_x = x < x0 + tx, in_y = y < y0 + ty;
         const int L = x + sy * y + sz * qz;
         const int q = qidx(x, y);
-        const int u = (x - x0) + (TX + 1) * (y - y0);
+        const int u = c;
         if (in_x && in_y) {
 #pragma unroll
           for (int n = 0; n < 5; ++n) {
