@@ -126,11 +126,11 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   a.fbuf = state_buf(ctx, ctx->cur[l]);
   a.chunks = near ? L.chunk_cells2.p : L.chunk_cells.p;
   a.nrows = near ? L.chunk_cells2.n : L.chunk_cells.n;
-  ctx->ops->fill_runs_cells(a, ctx->stream, nl);
-  a.rows = near ? L.run_faces2.p : L.run_faces.p;
-  a.chunks = near ? L.chunk_faces2.p : L.chunk_faces.p;
-  a.nrows = near ? L.chunk_faces2.n : L.chunk_faces.n;
-  ctx->ops->fill_runs_faces(a, ctx->stream, nl);
+  RowArgs af = a;
+  af.rows = near ? L.run_faces2.p : L.run_faces.p;
+  af.chunks = near ? L.chunk_faces2.p : L.chunk_faces.p;
+  af.nrows = near ? L.chunk_faces2.n : L.chunk_faces.n;
+  ctx->ops->fill_runs_both(a, af, ctx->stream, nl);
   if (s == 1 && l > 0) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
     b.fbuf = state_buf(ctx, ctx->cur[l]);

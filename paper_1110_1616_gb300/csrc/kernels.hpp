@@ -87,6 +87,7 @@ struct Ops {
   // boundaries (ghost boxes of amrmhd::GHOST_BOX_W ints)
   void (*fill_runs_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_runs_faces)(const RowArgs&, cudaStream_t, int* launches);
+  void (*fill_runs_both)(const RowArgs& cells, const RowArgs& faces, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_bc_cells)(const RowArgs&, cudaStream_t, int* launches);

@@ -332,9 +332,9 @@ template <class T, int DIM> __global__ void k_reg_fine_edges(RowArgs a) {
 constexpr int FILL_TPB = FILL_CHUNK;
 template <int W>
 __device__ __forceinline__ bool box_cell(const int* boxes, const int* chunks, const DPatch* P, const int*& box,
-                                         long long& Ld, long long& Ls) {
-  const int bi = chunks[2 * blockIdx.x];
-  const int c = chunks[2 * blockIdx.x + 1] + threadIdx.x;
+                                         long long& Ld, long long& Ls, unsigned blk) {
+  const int bi = chunks[2 * blk];
+  const int c = chunks[2 * blk + 1] + threadIdx.x;
   box = boxes + W * bi;
   const int nx = box[W - 3], ny = box[W - 2], nz = box[W - 1];
   if (c >= nx * ny * nz) return false;
@@ -349,7 +349,7 @@ __device__ __forceinline__ bool box_cell(const int* boxes, const int* chunks, co
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_cells(RowArgs a) {
   const int* box;
   long long Ld, Ls;
-  if (!box_cell<7>(a.rows, a.chunks, a.P, box, Ld, Ls)) return;
+  if (!box_cell<7>(a.rows, a.chunks, a.P, box, Ld, Ls, blockIdx.x)) return;
   const DPatch D = a.P[box[0]], S = a.P[box[2]];
   T* dst = (T*)a.fbuf + D.off + Ld;
   const T* src = (const T*)a.fbuf + S.off + Ls;
@@ -364,10 +364,34 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_b
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_faces(RowArgs a) {
   const int* box;
   long long Ld, Ls;
-  if (!box_cell<8>(a.rows, a.chunks, a.P, box, Ld, Ls)) return;
+  if (!box_cell<8>(a.rows, a.chunks, a.P, box, Ld, Ls, blockIdx.x)) return;
   const DPatch D = a.P[box[0]], S = a.P[box[3]];
   const int f = BX + box[1];
   ((T*)a.fbuf)[D.off + f * D.fs + Ld] = ((const T*)a.fbuf)[S.off + f * S.fs + Ls];
+}
+
+// cell and face boxes in one launch: blocks [0, ncell) take the cell chunks of
+// c, the rest the face chunks of f (the two sets are disjoint in memory)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_both(RowArgs c, RowArgs f) {
+  const int* box;
+  long long Ld, Ls;
+  if (blockIdx.x < c.nrows) {
+    if (!box_cell<7>(c.rows, c.chunks, c.P, box, Ld, Ls, blockIdx.x)) return;
+    const DPatch D = c.P[box[0]], S = c.P[box[2]];
+    T* dst = (T*)c.fbuf + D.off + Ld;
+    const T* src = (const T*)c.fbuf + S.off + Ls;
+    constexpr int NCF = DIM == 3 ? 5 : 6;
+#pragma unroll
+    for (int n = 0; n < NCF; ++n) {
+      const int fl = n < 5 ? n : BZ;
+      dst[fl * D.fs] = src[fl * S.fs];
+    }
+  } else {
+    if (!box_cell<8>(f.rows, f.chunks, f.P, box, Ld, Ls, blockIdx.x - (unsigned)c.nrows)) return;
+    const DPatch D = f.P[box[0]], S = f.P[box[3]];
+    const int fl = BX + box[1];
+    ((T*)f.fbuf)[D.off + fl * D.fs + Ld] = ((const T*)f.fbuf)[S.off + fl * S.fs + Ls];
+  }
 }
 
 // Prolongation and physical-boundary fills as ghost boxes of GHOST_BOX_W
@@ -925,6 +949,11 @@ template <class T, int DIM> struct Impl {
     k_fill_box_faces<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
     if (nl) ++*nl;
   }
+  static void fill_runs_both(const RowArgs& c, const RowArgs& f, cudaStream_t s, int* nl) {
+    if (!c.nrows && !f.nrows) return;
+    k_fill_box_both<T, DIM><<<(unsigned)(c.nrows + f.nrows), FILL_TPB, 0, s>>>(c, f);
+    if (nl) ++*nl;
+  }
   AMRK_ROWS(transfer_cells)
   AMRK_ROWS(transfer_faces)
   AMRK_ROWS(closure)
@@ -995,7 +1024,7 @@ template <class T, int DIM> struct Impl {
   }
   static const Ops* ops() {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_runs_cells,
-                          fill_runs_faces, prolong_cells,
+                          fill_runs_faces, fill_runs_both, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
                           transfer_faces, closure};
