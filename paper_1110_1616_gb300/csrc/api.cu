@@ -80,6 +80,7 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
   }
   a.gamma = ctx->cfg.gamma;
   a.w = w;
+  a.bnd = (l > 0 && ctx->bnd_elems > 0) ? (void*)(ctx->arena + ctx->o_bnd) : nullptr;
   return a;
 }
 
@@ -222,6 +223,8 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
     if (fused) {
       double idx[3];
       level_idx(ctx, l, idx);
+      // the fine advance just wrote its boundary fluxes and EMFs (when the fused kernel ran)
+      f.bnd = e.bnd = (ctx->opt_advance != 1 && a.bnd) ? a.bnd : nullptr;
       ctx->ops->reg_fine_rc(f, e, idx, ctx->cfg.gamma, ctx->stream, nl);
     } else {
       ctx->ops->reg_fine(f, e, ctx->stream, nl);
@@ -468,6 +471,17 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
     }
   ctx->state_elems = acc;
   ctx->scr_elems = sacc;
+  // boundary capture blocks of the fused 3D path: fluxes and EMFs on the
+  // boundary planes of every patch above level 0 (read by the fine registers)
+  ctx->boff.assign(np, -1);
+  long long bacc = 0;
+  if (H.dim == 3 && ctx->fused() && !ctx->stage_light)
+    for (int l = 1; l < H.nlev; ++l)
+      for (int q : H.level_patches[l]) {
+        ctx->boff[q] = bacc;
+        bacc += 5 * amrk::bnd_faces_total(H.p[q].n) + amrk::bnd_edges_total(H.p[q].n);
+      }
+  ctx->bnd_elems = bacc;
   ctx->ncf = (int64_t)H.cf_faces.size() / 7;
   ctx->nce = (int64_t)H.cf_edges.size() / 6;
   for (int k = 0; k < 4; ++k) {
@@ -492,6 +506,7 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
   ctx->o_ecreg = o; o = align256(o + (size_t)ctx->nce * sizeof(double));
   ctx->o_efreg = o; o = align256(o + (size_t)ctx->nce * 2 * sizeof(double));
   ctx->o_stage = o; o = align256(o + (size_t)ctx->stage_elems * sizeof(double));
+  ctx->o_bnd = o; o = align256(o + (size_t)ctx->bnd_elems * elem);
   ctx->arena_bytes = o;
   ctx->have_h = true;
   if (arena_bytes) *arena_bytes = o;
@@ -522,6 +537,7 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     P.off = ctx->off[q];
     P.fs = ctx->fs[q];
     P.soff = ctx->soff[q];
+    P.boff = ctx->boff[q];
   }
   ctx->dP = dbuf<DPatch>(ctx, np, &e);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));

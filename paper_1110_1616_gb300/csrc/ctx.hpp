@@ -64,9 +64,10 @@ struct amrmhd_ctx {
     return cfg.dim == 3 && (opt_advance == 3 || (opt_advance == 0 && cfg.precision == AMRMHD_MIXED));
   }
   // arena layout (bytes)
-  std::vector<long long> off, fs, soff;
+  std::vector<long long> off, fs, soff, boff;
   long long state_elems = 0, scr_elems = 0;
-  size_t o_state[2] = {0, 0}, o_scr = 0, o_creg = 0, o_freg = 0, o_ecreg = 0, o_efreg = 0, o_stage = 0;
+  size_t o_state[2] = {0, 0}, o_scr = 0, o_creg = 0, o_freg = 0, o_ecreg = 0, o_efreg = 0, o_stage = 0, o_bnd = 0;
+  long long bnd_elems = 0;  // boundary capture blocks (fused 3D, levels > 0)
   size_t arena_bytes = 0;
   char* arena = nullptr;
   int64_t ncf = 0, nce = 0, stage_elems = 0;

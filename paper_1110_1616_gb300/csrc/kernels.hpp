@@ -13,6 +13,7 @@ struct DPatch {
   long long off;   // element offset of field 0 in a state buffer
   long long fs;    // elements per field array (padded)
   long long soff;  // element offset of the patch's scratch block
+  long long boff;  // element offset of the patch's boundary capture block (fused 3D, levels > 0), or -1
 };
 
 // Scratch arrays per patch (each fs elements): W (8), Wh (8), S[d] (3x8),
@@ -32,6 +33,9 @@ struct LevelArgs {
   double idx[3];   // 1/dx of this level
   double gamma;
   int w;           // extra ghost layers updated (0 or 2)
+  // boundary capture buffer (fused 3D advance of a level > 0): the fluxes and
+  // EMFs of every patch's boundary planes are written at P.boff; nullptr: none
+  void* bnd;
 };
 
 struct RowArgs {
@@ -58,6 +62,9 @@ struct RowArgs {
   const double* K;
   // box copies: chunk table (box, first cell) per block
   const int* chunks;
+  // fine-side registers of the fused path: the boundary capture buffer the fine
+  // level's advance wrote (nullptr: recompute the fluxes and EMFs)
+  const void* bnd;
 };
 
 struct CflArgs {
@@ -71,6 +78,19 @@ struct CflArgs {
   unsigned long long* slot;  // per-level max (bits of a non-negative double)
   unsigned int* err;
 };
+
+// sizes of a patch's boundary capture block (fused 3D path, levels > 0): the
+// faces of its six boundary planes, and the tangential edges of those planes
+__host__ __device__ __forceinline__ long long bnd_faces_total(const int* n) {
+  return 2LL * ((long long)n[1] * n[2] + (long long)n[0] * n[2] + (long long)n[0] * n[1]);
+}
+__host__ __device__ __forceinline__ long long bnd_edges_total(const int* n) {
+  long long t = 0;
+  for (int e = 0; e < 3; ++e)
+    for (int c = 0; c < 3; ++c)
+      if (c != e) t += 2LL * n[c] * (n[3 - c - e] + 1);
+  return t;
+}
 
 enum Variant { V_FP64 = 0, V_FP64_STRICT = 1, V_MIXED = 2 };
 

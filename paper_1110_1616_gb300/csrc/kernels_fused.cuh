@@ -88,8 +88,61 @@ __device__ __forceinline__ void load_recover(const T* U, long long fs, int L, in
   }
 }
 
-// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread)
-template <class T, int VAR>
+// ---------------------------------------------------------------- boundary capture
+// The fluxes and EMFs on the six boundary planes of a fine patch, written by the
+// fused advance and read by the fine-side registers (levels > 0), instead of
+// recomputing them there. Per patch at P.boff (elements of the state type): the
+// 5 conserved-flux components (field-major) of every boundary face, planes in
+// the order x-low, x-high, y-low, y-high, z-low, z-high, a plane of normal e
+// holding n_t1 x n_t2 faces (t1 < t2 the other axes, t1 fastest); then the
+// tangential EMFs of the boundary planes in the same plane order, per plane its
+// two components c != e ascending, each over n_c x (n_o + 1) edges (c fastest,
+// o the remaining axis).
+// slot of the e-face at local (x, y, z) if it lies on a boundary plane, else -1
+__device__ __forceinline__ long long bnd_face_slot(const DPatch& P, int e, int x, int y, int z) {
+  const int pos[3] = {x, y, z};
+  const int side = pos[e] == 4 ? 0 : (pos[e] == P.n[e] + 4 ? 1 : -1);
+  if (side < 0) return -1;
+  const int t1 = e == 0 ? 1 : 0, t2 = e == 2 ? 1 : 2;
+  const int u = pos[t1] - 4, v = pos[t2] - 4;
+  if (u < 0 || u >= P.n[t1] || v < 0 || v >= P.n[t2]) return -1;
+  const long long S0 = (long long)P.n[1] * P.n[2], S1 = (long long)P.n[0] * P.n[2], S2 = (long long)P.n[0] * P.n[1];
+  const long long Se = e == 0 ? S0 : (e == 1 ? S1 : S2);
+  const long long base = (e == 0 ? 0 : (e == 1 ? 2 * S0 : 2 * (S0 + S1))) + side * Se;
+  return base + u + (long long)P.n[t1] * v;
+}
+// slot of the c-edge at local (x, y, z) on the boundary plane of normal e, else -1
+__device__ __forceinline__ long long bnd_edge_slot(const DPatch& P, int c, int e, int x, int y, int z) {
+  const int pos[3] = {x, y, z};
+  const int side = pos[e] == 4 ? 0 : (pos[e] == P.n[e] + 4 ? 1 : -1);
+  if (side < 0) return -1;
+  const int o = 3 - c - e;
+  const int u = pos[c] - 4, v = pos[o] - 4;
+  if (u < 0 || u >= P.n[c] || v < 0 || v > P.n[o]) return -1;
+  long long base = 0;
+  for (int ee = 0; ee < 3; ++ee)
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (int cc = 0; cc < 3; ++cc) {
+        if (cc == ee) continue;
+        if (ee == e && s2 == side && cc == c) return base + u + (long long)P.n[c] * v;
+        base += (long long)P.n[cc] * (P.n[3 - cc - ee] + 1);
+      }
+  return -1;
+}
+template <class T>
+__device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch& P, int c, int x, int y, int z, T v) {
+  T* b = (T*)a.bnd + P.boff + 5 * bnd_faces_total(P.n);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (e == c) continue;
+    const long long sl = bnd_edge_slot(P, c, e, x, y, z);
+    if (sl >= 0) b[sl] = v;
+  }
+}
+
+// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread).
+// CAP: the level's boundary fluxes and EMFs are captured for the fine registers.
+template <class T, int VAR, bool CAP>
 __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
@@ -109,6 +162,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
   const int sy = P.ext[0], sz = P.ext[0] * P.ext[1];
   const T* U = (const T*)a.cur + P.off;
   T* V = (T*)a.nxt + P.off;
+  const bool capture = CAP && P.boff >= 0;
   const double gm1 = a.gamma - 1.0;
   const T gamma = (T)a.gamma;
   const double dt = *a.dtp * a.dtscale;
@@ -258,6 +312,15 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
 #pragma unroll
         for (int k = 0; k < 7; ++k) fo[fi[k] * Q + q] = fr[k];
         fo[(BX + n) * Q + q] = T(0);
+        if (capture) {  // a boundary face of a fine patch: keep its flux for the registers
+          const long long sl = bnd_face_slot(P, D, x, y, p);
+          if (sl >= 0) {
+            T* b = (T*)a.bnd + P.boff;
+            const long long F = bnd_faces_total(P.n);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) b[fi[k] * F + sl] = fr[k];
+          }
+        }
       }
     }
     __syncthreads();
@@ -277,6 +340,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
           sm.ez[r2][q11] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[r2][2][q00], sm.ref[r2][2][q10],
                                      sm.ref[r2][2][q01], sm.ref[r2][2][q11], sm.fx[r2][RHO][q10], sm.fx[r2][RHO][q11],
                                      sm.fy[r2][RHO][q01], sm.fy[r2][RHO][q11]);
+          if (capture) bnd_store_edge<T>(a, P, 2, x, y, p, sm.ez[r2][q11]);
         } else if (c < nez + NEX) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
           const int cc = c - nez, xi = cc % TX, yi = cc / TX;
           if (xi >= tx || yi > ty) continue;
@@ -288,6 +352,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
           sm.ex[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][0][qm], sm.ref[rm][0][q], sm.ref[r2][0][qm],
                                    sm.ref[r2][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
                                    sm.fz[r2][RHO][q]);
+          if (capture) bnd_store_edge<T>(a, P, 0, x, y, p, sm.ex[r2][q]);
         } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
           const int cc = c - nez - NEX, xi = cc % (TX + 1), yi = cc / (TX + 1);
           if (xi > tx || yi >= ty) continue;
@@ -300,6 +365,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
           sm.ey[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][1][qm], sm.ref[r2][1][qm], sm.ref[rm][1][q],
                                    sm.ref[r2][1][q], sm.fz[r2][RHO][qm], sm.fz[r2][RHO][q], sm.fx[rm][RHO][q],
                                    sm.fx[r2][RHO][q]);
+          if (capture) bnd_store_edge<T>(a, P, 1, x, y, p, sm.ey[r2][q]);
         }
       }
     }
@@ -508,4 +574,71 @@ template <class T> __global__ void k_regrc_fine_edges(RowArgs a, double gamma, d
   const T e0 = edge_emf_at<T>(U, P, c, L, dt, idx, gamma);
   const T e1 = edge_emf_at<T>(U, P, c, L + sc, dt, idx, gamma);
   a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)e0, (double)e1);
+}
+
+// fine-side registers from the boundary capture of the fine level's fused
+// advance (the same fluxes and EMFs the recompute kernels above evaluate); a
+// face or edge off the boundary planes (none by construction) is recomputed
+template <class T> __global__ void k_regcap_fine_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 7 * r;
+  const DPatch P = a.P[row[5]];
+  const int d = row[2], L = row[6];
+  const double dt = *a.dtp * a.dtscale;
+  const double af = dt * 0.25;
+  const int sx = 1, sy = P.ext[0], sz = P.ext[0] * P.ext[1];
+  int o1, o2;
+  if (d == 0) { o1 = sy; o2 = sz; }
+  else if (d == 1) { o1 = sx; o2 = sz; }
+  else { o1 = sx; o2 = sy; }
+  const int off[4] = {0, o1, o2, o1 + o2};
+  const T* b = (const T*)a.bnd + P.boff;
+  const long long F = bnd_faces_total(P.n);
+  T f[4][5];
+  for (int k = 0; k < 4; ++k) {
+    const int Lk = L + off[k];
+    const int x = Lk % P.ext[0], y = (Lk / P.ext[0]) % P.ext[1], z = Lk / (P.ext[0] * P.ext[1]);
+    const long long sl = P.boff >= 0 ? bnd_face_slot(P, d, x, y, z) : -1;
+    if (sl >= 0) {
+#pragma unroll
+      for (int n = 0; n < 5; ++n) f[k][n] = b[n * F + sl];
+    } else {
+      const double idx[3] = {ix, iy, iz};
+      T f8[8];
+      face_flux_at<T>((const T*)a.fbuf + P.off, P, d, Lk, dt, idx, gamma, f8);
+#pragma unroll
+      for (int n = 0; n < 5; ++n) f[k][n] = f8[n];
+    }
+  }
+  double* out = a.freg + (r * 2 + (a.substep - 1)) * 6;
+#pragma unroll
+  for (int n = 0; n < 5; ++n)
+    out[n] = af * tree4((double)f[0][n], (double)f[1][n], (double)f[2][n], (double)f[3][n]);
+}
+
+template <class T> __global__ void k_regcap_fine_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
+  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+  if (r >= a.nrows) return;
+  const int* row = a.rows + 6 * r;
+  const DPatch P = a.P[row[4]];
+  const int c = row[2], L = row[5];
+  const double dt = *a.dtp * a.dtscale;
+  const int sc = c == 0 ? 1 : (c == 1 ? P.ext[0] : P.ext[0] * P.ext[1]);
+  const T* b = (const T*)a.bnd + P.boff + 5 * bnd_faces_total(P.n);
+  T ev[2];
+  for (int k = 0; k < 2; ++k) {
+    const int Lk = L + k * sc;
+    const int x = Lk % P.ext[0], y = (Lk / P.ext[0]) % P.ext[1], z = Lk / (P.ext[0] * P.ext[1]);
+    long long sl = -1;
+    for (int e = 0; e < 3 && sl < 0 && P.boff >= 0; ++e)
+      if (e != c) sl = bnd_edge_slot(P, c, e, x, y, z);
+    if (sl >= 0) {
+      ev[k] = b[sl];
+    } else {
+      const double idx[3] = {ix, iy, iz};
+      ev[k] = edge_emf_at<T>((const T*)a.fbuf + P.off, P, c, Lk, dt, idx, gamma);
+    }
+  }
+  a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)ev[0], (double)ev[1]);
 }

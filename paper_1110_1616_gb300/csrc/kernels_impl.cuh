@@ -985,8 +985,12 @@ template <class T, int DIM> struct Impl {
   }
   template <int V> static bool fused_fits() { return fused_smem<V>() <= 227 * 1024; }
   template <int V> static void prepare_v() {
-    if (fused_fits<V>())
-      cudaFuncSetAttribute(k_advance3d_fused<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<V>());
+    if (fused_fits<V>()) {
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<V>());
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<V>());
+    }
   }
   static void prepare() {
     if (DIM == 3) { prepare_v<0>(); prepare_v<1>(); prepare_v<2>(); prepare_v<3>(); }
@@ -995,7 +999,8 @@ template <class T, int DIM> struct Impl {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
     const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
     const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
-    k_advance3d_fused<T, V><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    if (a.bnd) k_advance3d_fused<T, V, true><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    else k_advance3d_fused<T, V, false><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
   }
   static void advance_fused(const LevelArgs& a, int variant, cudaStream_t s, int* nl) {
     if (DIM != 3) {
@@ -1019,6 +1024,11 @@ template <class T, int DIM> struct Impl {
   static void reg_fine_rc(const RowArgs& f, const RowArgs& e, const double* idx, double gamma, cudaStream_t s,
                           int* nl) {
     if (DIM != 3) return;
+    if (f.bnd) {  // from the fine advance's boundary capture
+      if (f.nrows) { k_regcap_fine_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+      if (e.nrows) { k_regcap_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+      return;
+    }
     if (f.nrows) { k_regrc_fine_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
     if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
   }

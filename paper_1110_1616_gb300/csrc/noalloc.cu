@@ -81,6 +81,7 @@ extern "C" amrmhd_status amrmhd_advance_patch_noalloc(const float* u_in, float* 
   h.P.off = 0;
   h.P.fs = fs;
   h.P.soff = 0;
+  h.P.boff = -1;
   h.id = 0;
   h.pad = 0;
   h.dt = dt;
@@ -98,6 +99,7 @@ extern "C" amrmhd_status amrmhd_advance_patch_noalloc(const float* u_in, float* 
   a.dtscale = 1.0;
   for (int d = 0; d < 3; ++d) a.idx[d] = d < dim ? 1.0 / dx[d] : 1.0;
   a.gamma = gamma;
+  a.bnd = nullptr;
   a.w = w;
   if (dim == 3) amrk_noalloc::Impl<float, 3>::advance(a, s, nullptr);
   else amrk_noalloc::Impl<float, 2>::advance(a, s, nullptr);
