@@ -123,15 +123,11 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   const LevelDev& L = ctx->lev[l];
   // an advance of the interior alone (w = 0) reads ghosts 2 cells deep
   const bool near = l == 0 || s == 2;
-  RowArgs a = row_args(ctx, near ? L.run_cells2 : L.run_cells, l);
+  RowArgs a = row_args(ctx, near ? L.runs2 : L.runs, l);
   a.fbuf = state_buf(ctx, ctx->cur[l]);
-  a.chunks = near ? L.chunk_cells2.p : L.chunk_cells.p;
-  a.nrows = near ? L.chunk_cells2.n : L.chunk_cells.n;
-  RowArgs af = a;
-  af.rows = near ? L.run_faces2.p : L.run_faces.p;
-  af.chunks = near ? L.chunk_faces2.p : L.chunk_faces.p;
-  af.nrows = near ? L.chunk_faces2.n : L.chunk_faces.n;
-  ctx->ops->fill_runs_both(a, af, ctx->stream, nl);
+  a.chunks = near ? L.chunk_runs2.p : L.chunk_runs.p;
+  a.nrows = near ? L.chunk_runs2.n : L.chunk_runs.n;
+  ctx->ops->fill_runs(a, ctx->stream, nl);
   if (s == 1 && l > 0) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
     b.fbuf = state_buf(ctx, ctx->cur[l]);
@@ -589,8 +585,8 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     }
     upload(ids, id_lists[l], 1);
     // ghost fill lists of this level from the hierarchy's boxes (see LevelDev)
-    std::vector<int32_t> rc, cc, rf, cf, pcb, pcc, pfb, pfc, bcb, bcc, bfb, bfc;
-    std::vector<int32_t> rc2, cc2, rf2, cf2, bcb2, bcc2, bfb2, bfc2;
+    std::vector<int32_t> rr, cr, pcb, pcc, pfb, pfc, bcb, bcc, bfb, bfc;
+    std::vector<int32_t> rr2, cr2, bcb2, bcc2, bfb2, bfc2;
     auto chunks_of = [](std::vector<int32_t>& ch, int bi, int vol) {
       for (int c = 0; c < vol; c += amrk::FILL_CHUNK) {
         ch.push_back(bi);
@@ -610,14 +606,26 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       }
       return true;
     };
-    // a same-level box as (dst, [d,] Ld, src, Ls, nx, ny, nz)
+    // a same-level box as a self-contained copy record (see k_fill_runs): element
+    // offsets of the first destination and source positions (with the face
+    // field for a face box), both patches' x/y strides and field strides,
+    // extents and the number of fields
     auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
       const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
-      const int Ld = b[4] + D.ext[0] * (b[5] + D.ext[1] * b[6]);
-      const int Ls = (b[4] + b[10]) + S.ext[0] * ((b[5] + b[11]) + S.ext[1] * (b[6] + b[12]));
-      const int bi = (int)(boxes.size() / (b[1] < 0 ? 7 : 8));
-      if (b[1] < 0) boxes.insert(boxes.end(), {b[0], Ld, b[3], Ls, b[7], b[8], b[9]});
-      else boxes.insert(boxes.end(), {b[0], b[1], Ld, b[3], Ls, b[7], b[8], b[9]});
+      const long long Ld = b[4] + (long long)D.ext[0] * (b[5] + (long long)D.ext[1] * b[6]);
+      const long long Ls = (b[4] + b[10]) + (long long)S.ext[0] * ((b[5] + b[11]) + (long long)S.ext[1] * (b[6] + b[12]));
+      const long long fd = ctx->fs[b[0]], fsrc = ctx->fs[b[3]];
+      const int fl = b[1] < 0 ? 0 : 5 + b[1];  // B_x, B_y, B_z are fields 5, 6, 7
+      const long long db = ctx->off[b[0]] + fl * fd + Ld, sb = ctx->off[b[3]] + fl * fsrc + Ls;
+      const int nv = b[1] >= 0 ? 1 : (H.dim == 3 ? 5 : 6);
+      const int bi = (int)(boxes.size() / amrk::FILL_BOX_W);
+      const int32_t rec[amrk::FILL_BOX_W] = {(int32_t)(db & 0xffffffffLL), (int32_t)(db >> 32),
+                                             (int32_t)(sb & 0xffffffffLL), (int32_t)(sb >> 32),
+                                             D.ext[0], D.ext[1], S.ext[0], S.ext[1],
+                                             (int32_t)(fd & 0xffffffffLL), (int32_t)(fd >> 32),
+                                             (int32_t)(fsrc & 0xffffffffLL), (int32_t)(fsrc >> 32),
+                                             b[7], b[8], b[9], nv};
+      boxes.insert(boxes.end(), rec, rec + amrk::FILL_BOX_W);
       chunks_of(ch, bi, b[7] * b[8] * b[9]);
     };
     auto add_box = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
@@ -633,8 +641,8 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
         int32_t nb[amrmhd::GHOST_BOX_W];
         const bool near = clip_near(b, nb);
         if (b[2] == 0) {
-          add_run(b, faces ? rf : rc, faces ? cf : cc);
-          if (near) add_run(nb, faces ? rf2 : rc2, faces ? cf2 : cc2);
+          add_run(b, rr, cr);
+          if (near) add_run(nb, rr2, cr2);
         } else if (b[2] == 1) {
           add_box(b, faces ? pfb : pcb, faces ? pfc : pcc);
         } else {
@@ -644,12 +652,12 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       }
     }
     const int GW = amrmhd::GHOST_BOX_W;
-    bool ok = upload(rc, L.run_cells, 7) && upload(cc, L.chunk_cells, 2) && upload(rf, L.run_faces, 8) &&
-              upload(cf, L.chunk_faces, 2) && upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
+    bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 2) &&
+              upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
               upload(pfb, L.prol_faces, GW) && upload(pfc, L.chunk_pfaces, 2) && upload(bcb, L.bc_cells, GW) &&
               upload(bcc, L.chunk_bcells, 2) && upload(bfb, L.bc_faces, GW) && upload(bfc, L.chunk_bfaces, 2);
-    ok = ok && upload(rc2, L.run_cells2, 7) && upload(cc2, L.chunk_cells2, 2) && upload(rf2, L.run_faces2, 8) &&
-         upload(cf2, L.chunk_faces2, 2) && upload(bcb2, L.bc_cells2, GW) && upload(bcc2, L.chunk_bcells2, 2) &&
+    ok = ok && upload(rr2, L.runs2, amrk::FILL_BOX_W) && upload(cr2, L.chunk_runs2, 2) &&
+         upload(bcb2, L.bc_cells2, GW) && upload(bcc2, L.chunk_bcells2, 2) &&
          upload(bfb2, L.bc_faces2, GW) && upload(bfc2, L.chunk_bfaces2, 2);
     if (l > 0 && ok) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {

@@ -22,14 +22,15 @@ struct LevelDev {
   int npatch = 0;
   int maxn[3] = {1, 1, 1};
   // ghost fill of this level as boxes, each list with its chunks (box, first
-  // position) per block of at most 64 positions: same-level copies (7 / 8 ints
-  // per box), prolongation and physical boundaries (GHOST_BOX_W ints per box)
-  DevList run_cells, run_faces, chunk_cells, chunk_faces;
+  // position) of at most 64 positions: same-level copies (FILL_BOX_W ints per
+  // box, cells and faces in one list), prolongation and physical boundaries
+  // (GHOST_BOX_W ints per box)
+  DevList runs, chunk_runs;
   DevList prol_cells, prol_faces, chunk_pcells, chunk_pfaces;
   DevList bc_cells, bc_faces, chunk_bcells, chunk_bfaces;
   // the same clipped to the ghosts within 2 cells of the interior (all that an
   // advance of the interior alone reads): used for sub-steps with w = 0
-  DevList run_cells2, run_faces2, chunk_cells2, chunk_faces2;
+  DevList runs2, chunk_runs2;
   DevList bc_cells2, bc_faces2, chunk_bcells2, chunk_bfaces2;
   // one row per ghost position of the same fills (rows of amrmhd.h's ghost maps
   // split by kind), uploaded on demand for the adjoint's transposed fills

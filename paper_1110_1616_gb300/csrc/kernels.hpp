@@ -94,20 +94,21 @@ __host__ __device__ __forceinline__ long long bnd_edges_total(const int* n) {
 
 enum Variant { V_FP64 = 0, V_FP64_STRICT = 1, V_MIXED = 2 };
 
-// positions per chunk (= threads per block) of the box-list fill kernels
+// positions per chunk of the box-list fill kernels (= threads per block of the
+// prolongation and boundary kernels), and the ints of a same-level copy box
 constexpr int FILL_CHUNK = 64;
+constexpr int FILL_BOX_W = 16;
 
 struct Ops {
   void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
   void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
   void (*reg_fine)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
   // ghost fill, all as boxes: rows = the box list, chunks = (box, first
-  // position) per block of at most 64 positions, nrows = the number of chunks.
-  // Same-level copies (7 / 8-int boxes), then prolongation and physical
-  // boundaries (ghost boxes of amrmhd::GHOST_BOX_W ints)
-  void (*fill_runs_cells)(const RowArgs&, cudaStream_t, int* launches);
-  void (*fill_runs_faces)(const RowArgs&, cudaStream_t, int* launches);
-  void (*fill_runs_both)(const RowArgs& cells, const RowArgs& faces, cudaStream_t, int* launches);
+  // position) per chunk of at most FILL_CHUNK positions, nrows = the number of
+  // chunks. Same-level copies (FILL_BOX_W-int boxes, cells and faces in one
+  // list), then prolongation and physical boundaries (ghost boxes of
+  // amrmhd::GHOST_BOX_W ints)
+  void (*fill_runs)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_bc_cells)(const RowArgs&, cudaStream_t, int* launches);

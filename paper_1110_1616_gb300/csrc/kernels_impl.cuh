@@ -7,6 +7,8 @@
 // patch's region; patches of uneven size leave surplus blocks idle. Map-driven
 // kernels run one thread per map row, each row writing one destination value
 // set (no atomics, deterministic).
+#include <algorithm>
+
 #include "hierarchy.hpp"
 #include "kernels.hpp"
 #include "mhd_device.cuh"
@@ -323,74 +325,59 @@ template <class T, int DIM> __global__ void k_reg_fine_edges(RowArgs a) {
 }
 
 // ------------------------------------------------------------------ ghost fill
-// Same-level copies as boxes: box records (dst, Ldst0, src, Lsrc0, nx, ny, nz)
-// for cells, (dst, d, Ldst0, src, Lsrc0, nx, ny, nz) for faces: the box of nx x
-// ny x nz positions starting at Ldst0 in patch dst takes the positions starting
-// at Lsrc0 in patch src (strides of each patch's own storage). chunks[2c],
-// chunks[2c+1] = (box, first cell) of block c (at most FILL_TPB cells of one box;
-// small blocks keep the threads busy on boxes of ~100 cells).
+// Same-level copies as boxes, cells and faces in one list. A box record
+// (FILL_BOX_W ints) holds everything a copy needs, so no patch record is read:
+// the destination and source element offsets of its first position (field 0
+// of a cell box, the face field of a face box), the x and y strides of both
+// patches, both field strides, the extents nx, ny, nz and the number of fields
+// nv (5 cells in 3D, 6 in 2D with B_z, 1 for faces). chunks[2c], chunks[2c+1]
+// = (box, first position) of chunk c (at most FILL_CHUNK positions of one box).
 constexpr int FILL_TPB = FILL_CHUNK;
-template <int W>
-__device__ __forceinline__ bool box_cell(const int* boxes, const int* chunks, const DPatch* P, const int*& box,
-                                         long long& Ld, long long& Ls, unsigned blk) {
-  const int bi = chunks[2 * blk];
-  const int c = chunks[2 * blk + 1] + threadIdx.x;
-  box = boxes + W * bi;
-  const int nx = box[W - 3], ny = box[W - 2], nz = box[W - 1];
-  if (c >= nx * ny * nz) return false;
-  const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-  const DPatch& D = P[box[0]];
-  const DPatch& S = P[box[W - 5]];
-  Ld = box[W - 6] + x + (long long)D.ext[0] * (y + (long long)D.ext[1] * z);
-  Ls = box[W - 4] + x + (long long)S.ext[0] * (y + (long long)S.ext[1] * z);
+struct FillPos {
+  long long d, s, dfs, sfs;
+  int nv;
+};
+__device__ __forceinline__ bool fill_pos(const int* boxes, const int* chunks, long long w, FillPos& o) {
+  const long long ch = w / FILL_CHUNK;
+  const int2 cr = reinterpret_cast<const int2*>(chunks)[ch];
+  const int4* br = reinterpret_cast<const int4*>(boxes + FILL_BOX_W * (long long)cr.x);
+  const int4 b3 = br[3];
+  const int k = cr.y + (int)(w % FILL_CHUNK);
+  if (k >= b3.x * b3.y * b3.z) return false;
+  const int4 b0 = br[0], b1 = br[1], b2 = br[2];
+  const int x = k % b3.x, y = (k / b3.x) % b3.y, z = k / (b3.x * b3.y);
+  const long long db = ((long long)(unsigned)b0.x) | ((long long)b0.y << 32);
+  const long long sb = ((long long)(unsigned)b0.z) | ((long long)b0.w << 32);
+  o.dfs = ((long long)(unsigned)b2.x) | ((long long)b2.y << 32);
+  o.sfs = ((long long)(unsigned)b2.z) | ((long long)b2.w << 32);
+  o.d = db + x + (long long)b1.x * (y + (long long)b1.y * z);
+  o.s = sb + x + (long long)b1.z * (y + (long long)b1.w * z);
+  o.nv = b3.w;
   return true;
 }
 
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_cells(RowArgs a) {
-  const int* box;
-  long long Ld, Ls;
-  if (!box_cell<7>(a.rows, a.chunks, a.P, box, Ld, Ls, blockIdx.x)) return;
-  const DPatch D = a.P[box[0]], S = a.P[box[2]];
-  T* dst = (T*)a.fbuf + D.off + Ld;
-  const T* src = (const T*)a.fbuf + S.off + Ls;
-  constexpr int NCF = DIM == 3 ? 5 : 6;
+// persistent grid-stride copy of every position of the box list; each thread
+// keeps two positions' loads in flight before it stores
+template <class T, int DIM> __global__ void __launch_bounds__(256) k_fill_runs(RowArgs a) {
+  T* B = (T*)a.fbuf;
+  const long long total = a.nrows * FILL_CHUNK, stride = (long long)gridDim.x * 256;
+  for (long long w = blockIdx.x * 256LL + threadIdx.x; w < total; w += 2 * stride) {
+    FillPos p0, p1;
+    const bool ok0 = fill_pos(a.rows, a.chunks, w, p0);
+    const bool ok1 = w + stride < total && fill_pos(a.rows, a.chunks, w + stride, p1);
+    T v0[6], v1[6];
 #pragma unroll
-  for (int n = 0; n < NCF; ++n) {
-    const int f = n < 5 ? n : BZ;
-    dst[f * D.fs] = src[f * S.fs];
-  }
-}
-
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_faces(RowArgs a) {
-  const int* box;
-  long long Ld, Ls;
-  if (!box_cell<8>(a.rows, a.chunks, a.P, box, Ld, Ls, blockIdx.x)) return;
-  const DPatch D = a.P[box[0]], S = a.P[box[3]];
-  const int f = BX + box[1];
-  ((T*)a.fbuf)[D.off + f * D.fs + Ld] = ((const T*)a.fbuf)[S.off + f * S.fs + Ls];
-}
-
-// cell and face boxes in one launch: blocks [0, ncell) take the cell chunks of
-// c, the rest the face chunks of f (the two sets are disjoint in memory)
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_box_both(RowArgs c, RowArgs f) {
-  const int* box;
-  long long Ld, Ls;
-  if (blockIdx.x < c.nrows) {
-    if (!box_cell<7>(c.rows, c.chunks, c.P, box, Ld, Ls, blockIdx.x)) return;
-    const DPatch D = c.P[box[0]], S = c.P[box[2]];
-    T* dst = (T*)c.fbuf + D.off + Ld;
-    const T* src = (const T*)c.fbuf + S.off + Ls;
-    constexpr int NCF = DIM == 3 ? 5 : 6;
-#pragma unroll
-    for (int n = 0; n < NCF; ++n) {
+    for (int n = 0; n < 6; ++n) {
       const int fl = n < 5 ? n : BZ;
-      dst[fl * D.fs] = src[fl * S.fs];
+      if (ok0 && n < p0.nv) v0[n] = B[p0.s + fl * p0.sfs];
+      if (ok1 && n < p1.nv) v1[n] = B[p1.s + fl * p1.sfs];
     }
-  } else {
-    if (!box_cell<8>(f.rows, f.chunks, f.P, box, Ld, Ls, blockIdx.x - (unsigned)c.nrows)) return;
-    const DPatch D = f.P[box[0]], S = f.P[box[3]];
-    const int fl = BX + box[1];
-    ((T*)f.fbuf)[D.off + fl * D.fs + Ld] = ((const T*)f.fbuf)[S.off + fl * S.fs + Ls];
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+      const int fl = n < 5 ? n : BZ;
+      if (ok0 && n < p0.nv) B[p0.d + fl * p0.dfs] = v0[n];
+      if (ok1 && n < p1.nv) B[p1.d + fl * p1.dfs] = v1[n];
+    }
   }
 }
 
@@ -939,19 +926,11 @@ template <class T, int DIM> struct Impl {
   AMRK_BOXES(fill_bc_cells)
   AMRK_BOXES(fill_bc_faces)
 #undef AMRK_BOXES
-  static void fill_runs_cells(const RowArgs& a, cudaStream_t s, int* nl) {
+  static void fill_runs(const RowArgs& a, cudaStream_t s, int* nl) {
     if (!a.nrows) return;
-    k_fill_box_cells<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
-    if (nl) ++*nl;
-  }
-  static void fill_runs_faces(const RowArgs& a, cudaStream_t s, int* nl) {
-    if (!a.nrows) return;
-    k_fill_box_faces<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);
-    if (nl) ++*nl;
-  }
-  static void fill_runs_both(const RowArgs& c, const RowArgs& f, cudaStream_t s, int* nl) {
-    if (!c.nrows && !f.nrows) return;
-    k_fill_box_both<T, DIM><<<(unsigned)(c.nrows + f.nrows), FILL_TPB, 0, s>>>(c, f);
+    const long long items = a.nrows * FILL_CHUNK;
+    const long long blocks = std::min<long long>((items + 511) / 512, 152LL * 8);
+    k_fill_runs<T, DIM><<<(unsigned)blocks, 256, 0, s>>>(a);
     if (nl) ++*nl;
   }
   AMRK_ROWS(transfer_cells)
@@ -1033,8 +1012,7 @@ template <class T, int DIM> struct Impl {
     if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
   }
   static const Ops* ops() {
-    static const Ops o = {advance, reg_coarse, reg_fine, fill_runs_cells,
-                          fill_runs_faces, fill_runs_both, prolong_cells,
+    static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
                           transfer_faces, closure};
