@@ -542,15 +542,6 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolon
   ((T*)a.fbuf)[D.off + (BX + n) * D.fs + x[0] + D.ext[0] * (x[1] + D.ext[1] * x[2])] = v;
 }
 
-template <int DIM> __device__ __forceinline__ void global_pos(const DPatch& P, int L, int* g) {
-  const int a = L % P.ext[0];
-  const int b = (L / P.ext[0]) % P.ext[1];
-  const int c = L / (P.ext[0] * P.ext[1]);
-  g[0] = P.lo[0] + a - 4;
-  g[1] = P.lo[1] + b - 4;
-  g[2] = DIM == 3 ? P.lo[2] + c - 4 : 0;
-}
-
 // ------------------------------------------------------------------ regrid
 // flagged cells of a level: max_d |rho(i+1) - rho(i-1)| / (2 rho) > theta in
 // FP64 from the stored values; global indices appended (order is arbitrary)
@@ -578,19 +569,21 @@ __global__ void __launch_bounds__(TPB) k_flag(LevelArgs a, double theta, int* ou
   out[3 * n + 2] = DIM == 3 ? P.lo[2] + k - 4 : 0;
 }
 
-// new fine cells: rows (dst, Ldst, kind, src, Lsrc); kind 0 copies the old fine
-// patch src of the old hierarchy (P2, obuf), kind 1 prolongs from the coarse
-// patch src (cbuf) as for a ghost cell
-template <class T, int DIM> __global__ void k_transfer_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 5 * r;
-  const DPatch D = a.P[row[0]];
-  T* dst = (T*)a.fbuf + D.off + row[1];
+// new fine cells, as transfer boxes (GHOST_BOX_W ints, chunks as for the ghost
+// boxes): kind 0 copies the old fine patch src of the old hierarchy (P2, obuf)
+// at local offset aux, kind 1 prolongs from the coarse patch src (cbuf) as for
+// a ghost cell (the cells lie inside the domain: no periodic wrap)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_transfer_cells(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]];
+  T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
   constexpr int NCF = DIM == 3 ? 5 : 6;
-  if (row[2] == 0) {
-    const DPatch O = a.P2[row[3]];
-    const T* src = (const T*)a.obuf + O.off + row[4];
+  if (box[2] == 0) {
+    const DPatch O = a.P2[box[3]];
+    const T* src = (const T*)a.obuf + O.off + (x[0] + box[10]) +
+                   (long long)O.ext[0] * ((x[1] + box[11]) + (long long)O.ext[1] * (x[2] + box[12]));
 #pragma unroll
     for (int n = 0; n < NCF; ++n) {
       const int f = n < 5 ? n : BZ;
@@ -598,10 +591,8 @@ template <class T, int DIM> __global__ void k_transfer_cells(RowArgs a) {
     }
     return;
   }
-  const DPatch C = a.P[row[3]];
-  int g[3];
-  global_pos<DIM>(D, row[1], g);
-  const T* src = (const T*)a.cbuf + C.off + row[4];
+  const DPatch C = a.P[box[3]];
+  const T* src = (const T*)a.cbuf + C.off + parent_local<DIM>(C, g, box + 10);
   const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
 #pragma unroll
   for (int n = 0; n < NCF; ++n) {
@@ -618,27 +609,28 @@ template <class T, int DIM> __global__ void k_transfer_cells(RowArgs a) {
   }
 }
 
-// new fine own faces: rows (dst, d, Ldst, kind, src, Lsrc); kind 0 copies the
-// old fine face, kind 1 prolongs (coincident or interior, by the parity)
-template <class T, int DIM> __global__ void k_transfer_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 6 * r;
-  const DPatch D = a.P[row[0]];
-  const int n = row[1];
-  T* out = (T*)a.fbuf + D.off + (BX + n) * D.fs + row[2];
-  if (row[3] == 0) {
-    const DPatch O = a.P2[row[4]];
-    *out = ((const T*)a.obuf)[O.off + (BX + n) * O.fs + row[5]];
+// new fine own faces of the box's direction: kind 0 copies the old fine face,
+// kind 1 prolongs (coincident or interior, by the parity) from the coarse face
+// (g + aux) >> 1 of the parent patch (aux: the periodic wrap)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_transfer_faces(RowArgs a) {
+  const int* box;
+  int x[3], g[3];
+  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  const DPatch D = a.P[box[0]];
+  const int n = box[1];
+  T* out = (T*)a.fbuf + D.off + (BX + n) * D.fs + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
+  if (box[2] == 0) {
+    const DPatch O = a.P2[box[3]];
+    *out = ((const T*)a.obuf)[O.off + (BX + n) * O.fs + (x[0] + box[10]) +
+                              (long long)O.ext[0] * ((x[1] + box[11]) + (long long)O.ext[1] * (x[2] + box[12]))];
     return;
   }
-  const DPatch C = a.P[row[4]];
-  int g[3];
-  global_pos<DIM>(D, row[2], g);
+  const DPatch C = a.P[box[3]];
+  const int Lc = parent_local<DIM>(C, g, box + 10);
   const int par[3] = {g[0] & 1, g[1] & 1, DIM == 3 ? (g[2] & 1) : 0};
   const int st[3] = {1, C.ext[0], C.ext[0] * C.ext[1]};
   const T* cb = (const T*)a.cbuf + C.off;
-  const T* bn = cb + (BX + n) * C.fs + row[5];
+  const T* bn = cb + (BX + n) * C.fs + Lc;
   if (!par[n]) {
     *out = coincident<T, DIM>(bn, st, n, par);
     return;
@@ -650,7 +642,7 @@ template <class T, int DIM> __global__ void k_transfer_faces(RowArgs a) {
 #pragma unroll
   for (int t = 0; t < DIM; ++t) {
     if (t == n) continue;
-    const T* bt_lo = cb + (BX + t) * C.fs + row[5];
+    const T* bt_lo = cb + (BX + t) * C.fs + Lc;
     const T* bt_hi = bt_lo + st[t];
     const T s_hi = mm(bt_hi[0] - bt_hi[-st[n]], bt_hi[st[n]] - bt_hi[0]);
     const T s_lo = mm(bt_lo[0] - bt_lo[-st[n]], bt_lo[st[n]] - bt_lo[0]);
@@ -933,8 +925,15 @@ template <class T, int DIM> struct Impl {
     k_fill_runs<T, DIM><<<(unsigned)blocks, 256, 0, s>>>(a);
     if (nl) ++*nl;
   }
-  AMRK_ROWS(transfer_cells)
-  AMRK_ROWS(transfer_faces)
+#define AMRK_BOXES(NAME)                                                                \
+  static void NAME(const RowArgs& a, cudaStream_t s, int* nl) {                         \
+    if (!a.nrows) return;                                                               \
+    k_##NAME<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);                          \
+    if (nl) ++*nl;                                                                      \
+  }
+  AMRK_BOXES(transfer_cells)
+  AMRK_BOXES(transfer_faces)
+#undef AMRK_BOXES
   AMRK_ROWS(closure)
   AMRK_ROWS(reflux_cells)
   AMRK_ROWS(reflux_faces)

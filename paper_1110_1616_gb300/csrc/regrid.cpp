@@ -178,8 +178,7 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
 int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps& out) {
   const int dim = Hn.dim;
   const int lc = lf - 1;
-  out.cells.clear();
-  out.faces.clear();
+  out.boxes.clear();
   out.closure.clear();
   const bool have_old = Ho.nlev > lf;
   const std::vector<int> empty;
@@ -269,30 +268,96 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
         if (inside(Q)) { *Lc = Hn.loc(Q, w[0], w[1], w[2]); return Q; }
       return -1;
     };
-    // cells
-    for (int k = P.lo[2]; k < P.hi[2]; ++k)
-      for (int j = P.lo[1]; j < P.hi[1]; ++j)
-        for (int i = P.lo[0]; i < P.hi[0]; ++i) {
-          const int g[3] = {i, j, k};
-          int c[3] = {i >> 1, j >> 1, dim == 3 ? k >> 1 : 0};
-          const int L = Hn.loc(q, i, j, k);
-          if (oldcov(c)) {
-            const long long kk = gi(g);
-            o.cells.insert(o.cells.end(), {q, L, 0, own[kk], old_loc(kk, g)});
-          } else {
-            int Lc = 0;
-            const int Q = coarse(c, &Lc);
-            if (Q < 0) { status[ip] = -1; break; }
-            o.cells.insert(o.cells.end(), {q, L, 1, Q, Lc});
+    // labels of the new patch's own cells and faces: a copy from old patch src at
+    // local offset delta, or a prolongation from coarse patch src; positions
+    // with equal labels are merged into boxes as for the ghost fill
+    struct TLab {
+      int kind, src, dl[3];
+      bool operator==(const TLab& o) const {
+        return kind == o.kind && src == o.src && dl[0] == o.dl[0] && dl[1] == o.dl[1] && dl[2] == o.dl[2];
+      }
+    };
+    std::vector<TLab> labs;
+    int last_id = -1;
+    auto label_id = [&](const TLab& t) {
+      if (last_id >= 0 && labs[last_id] == t) return last_id;
+      for (size_t i = 0; i < labs.size(); ++i)
+        if (labs[i] == t) return last_id = (int)i;
+      labs.push_back(t);
+      return last_id = (int)labs.size() - 1;
+    };
+    auto copy_label = [&](long long k) {
+      const int code = shf[k];
+      const int s3[3] = {code % 3 - 1, (code / 3) % 3 - 1, code / 9 - 1};
+      const HPatch& O = Ho.p[own[k]];
+      TLab t{0, own[k], {0, 0, 0}};
+      for (int d = 0; d < dim; ++d) t.dl[d] = P.lo[d] - O.lo[d] - s3[d] * Hn.N(lf, d);
+      return t;
+    };
+    std::vector<int> lid;
+    // greedy boxes (x runs, then y, then z) over a grid of label ids; ids are
+    // cleared as positions are taken
+    auto merge = [&](const int* ex, int d) {
+      auto at = [&](int x, int y, int z) { return ((size_t)z * ex[1] + y) * ex[0] + x; };
+      for (int c = 0; c < ex[2]; ++c)
+        for (int b = 0; b < ex[1]; ++b)
+          for (int a = 0; a < ex[0]; ++a) {
+            const int k = lid[at(a, b, c)];
+            if (k < 0) continue;
+            int nx = 1, ny = 1, nz = 1;
+            while (a + nx < ex[0] && lid[at(a + nx, b, c)] == k) ++nx;
+            auto row_ok = [&](int y, int z) {
+              for (int i = 0; i < nx; ++i)
+                if (lid[at(a + i, y, z)] != k) return false;
+              return true;
+            };
+            while (b + ny < ex[1] && row_ok(b + ny, c)) ++ny;
+            auto slab_ok = [&](int z) {
+              for (int j = 0; j < ny; ++j)
+                if (!row_ok(b + j, z)) return false;
+              return true;
+            };
+            while (c + nz < ex[2] && slab_ok(c + nz)) ++nz;
+            for (int z = 0; z < nz; ++z)
+              for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) lid[at(a + x, b + y, c + z)] = -1;
+            const TLab& t = labs[k];
+            const int32_t row[GHOST_BOX_W] = {q, d, t.kind, t.src, 4 + a, 4 + b, dim == 3 ? 4 + c : 0, nx, ny, nz,
+                                              t.dl[0], t.dl[1], t.dl[2]};
+            o.boxes.insert(o.boxes.end(), row, row + GHOST_BOX_W);
           }
-        }
+    };
+    // cells
+    {
+      const int ex[3] = {P.n[0], P.n[1], dim == 3 ? P.n[2] : 1};
+      lid.assign((size_t)ex[0] * ex[1] * ex[2], -1);
+      size_t t = 0;
+      for (int k = P.lo[2]; k < P.hi[2] && !status[ip]; ++k)
+        for (int j = P.lo[1]; j < P.hi[1] && !status[ip]; ++j)
+          for (int i = P.lo[0]; i < P.hi[0]; ++i, ++t) {
+            const int g[3] = {i, j, k};
+            int c[3] = {i >> 1, j >> 1, dim == 3 ? k >> 1 : 0};
+            if (oldcov(c)) {
+              lid[t] = label_id(copy_label(gi(g)));
+            } else {
+              int Lc = 0;
+              const int Q = coarse(c, &Lc);
+              if (Q < 0) { status[ip] = -1; break; }
+              lid[t] = label_id(TLab{1, Q, {0, 0, 0}});
+            }
+          }
+      if (!status[ip]) merge(ex, -1);
+    }
     // own faces
     for (int d = 0; d < dim && !status[ip]; ++d) {
       int hi[3] = {P.hi[0], P.hi[1], P.hi[2]};
       hi[d] += 1;
-      for (int k = P.lo[2]; k < hi[2]; ++k)
-        for (int j = P.lo[1]; j < hi[1]; ++j)
-          for (int i = P.lo[0]; i < hi[0]; ++i) {
+      const int ex[3] = {hi[0] - P.lo[0], hi[1] - P.lo[1], dim == 3 ? hi[2] - P.lo[2] : 1};
+      lid.assign((size_t)ex[0] * ex[1] * ex[2], -1);
+      size_t t = 0;
+      for (int k = P.lo[2]; k < hi[2] && !status[ip]; ++k)
+        for (int j = P.lo[1]; j < hi[1] && !status[ip]; ++j)
+          for (int i = P.lo[0]; i < hi[0]; ++i, ++t) {
             const int g[3] = {i, j, k};
             int m[3] = {i, j, k};
             m[d] -= 1;
@@ -300,19 +365,19 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
             int pm[3] = {m[0] >> 1, m[1] >> 1, dim == 3 ? m[2] >> 1 : 0};
             const bool interior = pq[d] == pm[d];
             const bool copy = interior ? oldcov(pq) : (oldcov(pq) || oldcov(pm));
-            const int L = Hn.loc(q, i, j, k);
             if (copy) {
               // owners of the face: the old patches holding the cells on its two sides;
               // the smallest (patch, local index) as for ghost faces
               int best = -1, bl = 0;
+              long long bk = -1;
               const long long k1 = gi(g), k0 = gi(m);
-              if (k1 >= 0 && own[k1] >= 0) { best = own[k1]; bl = old_loc(k1, g); }
+              if (k1 >= 0 && own[k1] >= 0) { best = own[k1]; bl = old_loc(k1, g); bk = k1; }
               if (k0 >= 0 && own[k0] >= 0) {
                 const int Lo = old_loc(k0, g);  // the same face position, in the low cell's patch
-                if (best < 0 || own[k0] < best || (own[k0] == best && Lo < bl)) { best = own[k0]; bl = Lo; }
+                if (best < 0 || own[k0] < best || (own[k0] == best && Lo < bl)) { best = own[k0]; bl = Lo; bk = k0; }
               }
               if (best < 0) { status[ip] = -2; break; }
-              o.faces.insert(o.faces.end(), {q, d, L, 0, best, bl});
+              lid[t] = label_id(copy_label(bk));
             } else {
               int c[3] = {pq[0], pq[1], pq[2]};
               const bool top = !Hn.per[d] && g[d] == Hn.N(lf, d);
@@ -320,10 +385,14 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
               int Lc = 0;
               const int Q = coarse(c, &Lc);
               if (Q < 0) { status[ip] = -1; break; }
-              if (top) Lc += d == 0 ? 1 : (d == 1 ? Hn.p[Q].ext[0] : Hn.p[Q].ext[0] * Hn.p[Q].ext[1]);
-              o.faces.insert(o.faces.end(), {q, d, L, 1, Q, Lc});
+              // the periodic wrap of the face position (the face at N of a
+              // periodic dimension is the coarse face 0 of the wrapped patch)
+              TLab t1{1, Q, {0, 0, 0}};
+              for (int e = 0; e < dim; ++e) t1.dl[e] = Hn.wrapd(lf, e, g[e]) - g[e];
+              lid[t] = label_id(t1);
             }
           }
+      if (!status[ip]) merge(ex, d);
     }
     // closure rows: prolonged coarse cells with an old-covered face neighbour
     const int kz = dim == 3 ? 1 : 0;
@@ -350,8 +419,7 @@ int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps
   }
   for (int ip = 0; ip < np; ++ip) {
     if (status[ip]) return status[ip];
-    out.cells.insert(out.cells.end(), per[ip].cells.begin(), per[ip].cells.end());
-    out.faces.insert(out.faces.end(), per[ip].faces.begin(), per[ip].faces.end());
+    out.boxes.insert(out.boxes.end(), per[ip].boxes.begin(), per[ip].boxes.end());
     out.closure.insert(out.closure.end(), per[ip].closure.begin(), per[ip].closure.end());
   }
   return 0;

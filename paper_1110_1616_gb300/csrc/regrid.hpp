@@ -17,8 +17,13 @@ namespace amrmhd {
 std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags);
 
 struct TransferMaps {
-  std::vector<int32_t> cells;    // (dst, Ldst, kind, src, Lsrc): 0 copy from old patch src, 1 prolong from coarse src
-  std::vector<int32_t> faces;    // (dst, d, Ldst, kind, src, Lsrc)
+  // boxes of the new patches' own cells (d = -1) and d-faces, GHOST_BOX_W ints
+  // (dst, d, kind, src, lo[3], n[3], aux[3]), lo in dst's local coordinates:
+  // kind 0 copies from old patch src at local offset aux, kind 1 prolongs from
+  // the new coarse patch src holding the parent cell of the wrapped position
+  // g + aux (for a face on the high side of a bounded domain, the last cell;
+  // its coarse face is (g + aux) >> 1)
+  std::vector<int32_t> boxes;
   std::vector<int32_t> closure;  // (dst, L of the first child) of prolonged coarse cells next to copied ones
 };
 

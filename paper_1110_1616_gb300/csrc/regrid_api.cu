@@ -128,10 +128,25 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
   amrmhd::TransferMaps m;
   const int rc = amrmhd::transfer_maps(S->H, O->H, lf, m);
   if (rc) return fail(ctx, AMRMHD_EINVAL, "regrid: transfer map without a source");
-  int *dc = nullptr, *df = nullptr, *dk = nullptr;
+  // cell and face boxes with their chunks (box, first position) of at most FILL_CHUNK positions
+  std::vector<int32_t> cb, cc, fb, fc;
+  for (size_t r = 0; r < m.boxes.size(); r += amrmhd::GHOST_BOX_W) {
+    const int32_t* b = &m.boxes[r];
+    std::vector<int32_t>& boxes = b[1] < 0 ? cb : fb;
+    std::vector<int32_t>& ch = b[1] < 0 ? cc : fc;
+    const int bi = (int)(boxes.size() / amrmhd::GHOST_BOX_W);
+    boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
+    for (int c = 0; c < b[7] * b[8] * b[9]; c += amrk::FILL_CHUNK) {
+      ch.push_back(bi);
+      ch.push_back(c);
+    }
+  }
+  int *dcb = nullptr, *dcc = nullptr, *dfb = nullptr, *dfc = nullptr, *dk = nullptr;
   double* dK = nullptr;
-  amrmhd_status st = upload_rows(ctx, m.cells, &dc);
-  if (!st) st = upload_rows(ctx, m.faces, &df);
+  amrmhd_status st = upload_rows(ctx, cb, &dcb);
+  if (!st) st = upload_rows(ctx, cc, &dcc);
+  if (!st) st = upload_rows(ctx, fb, &dfb);
+  if (!st) st = upload_rows(ctx, fc, &dfc);
   if (!st) st = upload_rows(ctx, m.closure, &dk);
   double idx[3], K[96] = {0};
   level_idx(S, lf, idx);
@@ -142,17 +157,21 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
     if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, "regrid: closure matrix");
   }
   if (!st) {
-    amrk::RowArgs a = row_args(S, DevList{dc, (int64_t)m.cells.size() / 5}, lf - 1);
+    amrk::RowArgs a = row_args(S, DevList{dcb, (int64_t)cb.size() / amrmhd::GHOST_BOX_W}, lf - 1);
     a.fbuf = state_buf(S, S->cur[lf]);
     a.cbuf = state_buf(S, S->cur[lf - 1]);
     a.P2 = O->dP;
     a.obuf = O->H.nlev > lf ? state_buf(O, O->cur[lf]) : nullptr;
     int nl = 0;
+    a.chunks = dcc;
+    a.nrows = (int64_t)cc.size() / 2;
     S->ops->transfer_cells(a, S->stream, &nl);
-    a.rows = df;
-    a.nrows = (int64_t)m.faces.size() / 6;
+    a.rows = dfb;
+    a.chunks = dfc;
+    a.nrows = (int64_t)fc.size() / 2;
     S->ops->transfer_faces(a, S->stream, &nl);
     a.rows = dk;
+    a.chunks = nullptr;
     a.nrows = (int64_t)m.closure.size() / 2;
     for (int d = 0; d < 3; ++d) a.idx[d] = idx[d];
     a.K = dK;
@@ -161,8 +180,10 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer: ") + cudaGetErrorString(e));
   }
-  cudaFree(dc);
-  cudaFree(df);
+  cudaFree(dcb);
+  cudaFree(dcc);
+  cudaFree(dfb);
+  cudaFree(dfc);
   cudaFree(dk);
   cudaFree(dK);
   return st;
