@@ -129,10 +129,12 @@ amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* ds
 
 /* The whole state as one packed array: the 8 packed fields of
  * amrmhd_set_state_packed one after the other (field 0's array, then field
- * 1's, ...; the amrmhd_backward layout). With a host pointer the data moves in
- * one copy per direction through a library-owned staging buffer (allocated on
- * first use) and the call synchronises the stream; with a device pointer it is
- * stream-ordered. */
+ * 1's, ...; the amrmhd_backward layout). With a page-locked host pointer
+ * (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) the packing kernels
+ * read or write the host memory directly; with any other host pointer the data
+ * moves in one copy per direction through a library-owned staging buffer
+ * (allocated on first use); either way the call synchronises the stream. With
+ * a device pointer it is stream-ordered. */
 amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device);
 amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_device);
 

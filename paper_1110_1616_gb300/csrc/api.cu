@@ -548,6 +548,9 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
     CU(cudaMemcpy(ctx->d_poff[k], ctx->poff[k].data(), sizeof(long long) * np, cudaMemcpyHostToDevice));
   }
+  ctx->d_poff_tab = dbuf<const long long*>(ctx, 4, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  CU(cudaMemcpy(ctx->d_poff_tab, ctx->d_poff, sizeof(long long*) * 4, cudaMemcpyHostToDevice));
   ctx->d_scal = dbuf<double>(ctx, 2 + nlev, &e);
   ctx->d_slots = dbuf<unsigned long long>(ctx, nlev + 1, &e);
   ctx->d_err = dbuf<unsigned int>(ctx, 1, &e);
@@ -792,26 +795,35 @@ static amrmhd_status io_all(amrmhd_ctx* ctx, double* buf, int32_t on_device, int
     total += ctx->ptotal[kind];
   }
   double* dev = buf;
+  bool mapped = false;
   if (!on_device) {
-    if (!ctx->d_stage_all) {
-      cudaError_t e = cudaSuccess;
-      ctx->d_stage_all = dbuf<double>(ctx, (size_t)total, &e);
-      if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, "staging buffer");
+    // page-locked host memory mapped into the device address space: the packing
+    // kernels read or write it directly over the host link (one pass, no
+    // staging copy); other host memory goes through a device staging buffer
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, buf) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      dev = (double*)pa.devicePointer;
+      mapped = true;
+    } else {
+      cudaGetLastError();  // an unregistered pointer is not an error here
+      if (!ctx->d_stage_all) {
+        cudaError_t e = cudaSuccess;
+        ctx->d_stage_all = dbuf<double>(ctx, (size_t)total, &e);
+        if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, "staging buffer");
+      }
+      dev = ctx->d_stage_all;
+      if (to_state) CU(cudaMemcpyAsync(dev, buf, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     }
-    dev = ctx->d_stage_all;
-    if (to_state) CU(cudaMemcpyAsync(dev, buf, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   }
-  for (int f = 0; f < 8; ++f) {
-    const int kind = (f >= 5 && !(H.dim == 2 && f == 7)) ? f - 4 : 0;
-    for (int l = 0; l < H.nlev; ++l) {
-      const LevelDev& L = ctx->lev[l];
-      int lm[3] = {L.maxn[0], L.maxn[1], L.maxn[2]};
-      int nl = 0;
-      ctx->ops->io(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev + off[f], ctx->d_poff[kind], f,
-                   to_state, ctx->stream, &nl);
-    }
+  // all 8 fields of a level per launch
+  for (int l = 0; l < H.nlev; ++l) {
+    const LevelDev& L = ctx->lev[l];
+    int lm[3] = {L.maxn[0], L.maxn[1], L.maxn[2]};
+    int nl = 0;
+    ctx->ops->io_all(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev, ctx->d_poff_tab, off, to_state,
+                     ctx->stream, &nl);
   }
-  if (!to_state && !on_device)
+  if (!to_state && !on_device && !mapped)
     CU(cudaMemcpyAsync(buf, dev, total * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
   return AMRMHD_OK;

@@ -80,6 +80,7 @@ struct amrmhd_ctx {
   amrk::DPatch* dP = nullptr;
   int* d_iota = nullptr;
   long long* d_poff[4] = {nullptr, nullptr, nullptr, nullptr};
+  const long long** d_poff_tab = nullptr;  // device copy of d_poff (the 4 pointers)
   double* d_scal = nullptr;              // [0] CFL dt0, [1 + l] dt given to advance_level(l)
   unsigned long long* d_slots = nullptr;  // per-level CFL maxima + step counter
   unsigned int* d_err = nullptr;

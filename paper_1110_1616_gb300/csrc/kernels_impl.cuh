@@ -870,6 +870,31 @@ __global__ void __launch_bounds__(TPB) k_io(const DPatch* PP, const int* ids, vo
   else *q = (double)*s;
 }
 
+// all 8 fields of one level in one launch (blockIdx.z = field); packed + foff[f]
+// is field f's packed array, poff[kind * npatch_total + pid] the patch's offset in it
+struct IoAll {
+  long long foff[8];
+};
+template <class T, int DIM>
+__global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids, void* state, double* packed,
+                                                const long long* const* poff, IoAll io, int to_state) {
+  const int pid = ids[blockIdx.y];
+  const int field = blockIdx.z;
+  const DPatch P = PP[pid];
+  const int fd = (field >= BX && !(DIM == 2 && field == BZ)) ? field - BX : -1;
+  int r[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) r[e] = e >= DIM ? 1 : P.n[e] + (e == fd ? 1 : 0);
+  const int t = blockIdx.x * TPB + threadIdx.x;
+  if (t >= r[0] * r[1] * r[2]) return;
+  const int i = t % r[0], j = (t / r[0]) % r[1], k = t / (r[0] * r[1]);
+  const int L = lidx(P, i + 4, j + 4, DIM == 3 ? k + 4 : 0);
+  T* s = (T*)state + P.off + field * P.fs + L;
+  double* q = packed + io.foff[field] + poff[fd + 1][pid] + t;
+  if (to_state) *s = (T)*q;
+  else *q = (double)*s;
+}
+
 #include "kernels_fused.cuh"
 
 // ------------------------------------------------------------------ launchers
@@ -957,6 +982,15 @@ template <class T, int DIM> struct Impl {
     k_io<T, DIM><<<dim3(cdiv(n, TPB), npatch), TPB, 0, s>>>(P, ids, state, packed, poff, field, to_state);
     if (nl) ++*nl;
   }
+  static void io_all(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
+                     const long long* const* poff, const long long* foff, int to_state, cudaStream_t s, int* nl) {
+    long long n = 1;
+    for (int d = 0; d < DIM; ++d) n *= maxn[d] + 1;
+    IoAll io;
+    for (int f = 0; f < 8; ++f) io.foff[f] = foff[f];
+    k_io_all<T, DIM><<<dim3(cdiv(n, TPB), npatch, 8), TPB, 0, s>>>(P, ids, state, packed, poff, io, to_state);
+    if (nl) ++*nl;
+  }
   // fused 3D advance (2D falls back to the staged kernels)
   template <int V> static size_t fused_smem() {
     return sizeof(FusedSmem<T, FusedCfg<V>::TX, FusedCfg<V>::TY>);
@@ -1013,7 +1047,7 @@ template <class T, int DIM> struct Impl {
   static const Ops* ops() {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
-                          sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
+                          io_all, sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
                           transfer_faces, closure};
     return &o;
   }

@@ -345,3 +345,24 @@ def test_whole_state_packed_io_round_trip():
     ctx._check(A.lib().amrmhd_set_state_all(ctx.h, new.ctypes.data_as(C.c_void_p), 0), "set_all")
     back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
     assert np.array_equal(back, new)
+
+
+@pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
+def test_whole_state_io_page_locked_host_memory(precision):
+    """With page-locked host buffers (read and written by the packing kernels
+    directly, no staging copy) the whole-state I/O moves the same values as
+    with ordinary host memory (through the staging buffer)."""
+    import ctypes as C
+    import torch
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    ctx = gpu_for(pb, precision)
+    ref = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    pinned = torch.empty(ref.size, dtype=torch.float64).pin_memory()
+    ctx._check(A.lib().amrmhd_get_state_all(ctx.h, C.c_void_p(pinned.data_ptr()), 0), "get_all")
+    assert np.array_equal(pinned.numpy(), ref)
+    new = ref * 1.25
+    pinned.copy_(torch.from_numpy(new))
+    ctx._check(A.lib().amrmhd_set_state_all(ctx.h, C.c_void_p(pinned.data_ptr()), 0), "set_all")
+    back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    expect = new if precision == A.FP64 else new.astype(np.float32).astype(np.float64)
+    assert np.array_equal(back, expect)
