@@ -184,21 +184,26 @@ def advance_alone(ctx, stream, reps):
 
 def e2e_run(pb, precision, k):
     """Through the C ABI with host buffers: every step uploads the whole state
-    from pinned host memory (one copy), advances one coarse step and reads the
-    whole state back (one copy)."""
+    from pinned host memory, advances one coarse step and reads the whole state
+    back (amrmhd_set/get_state_all, in the stored element type: float for the
+    mixed-precision context, double for FP64)."""
     import numpy as np
     import torch
     import ctypes as C
     from paper_1110_1616_gb300 import amrmhd as A
     ctx, stream = make_ctx(pb, precision)
-    host_in = torch.from_numpy(np.concatenate([ctx.pack(pb.state, f) for f in range(8)])).pin_memory()
+    f32 = precision == A.MIXED
+    host = np.concatenate([ctx.pack(pb.state, f) for f in range(8)])
+    host_in = torch.from_numpy(host.astype(np.float32) if f32 else host).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     lib = A.lib()
+    set_all = lib.amrmhd_set_state_all_f32 if f32 else lib.amrmhd_set_state_all
+    get_all = lib.amrmhd_get_state_all_f32 if f32 else lib.amrmhd_get_state_all
 
     def one():
-        ctx._check(lib.amrmhd_set_state_all(ctx.h, C.c_void_p(host_in.data_ptr()), 0), "set_all")
+        ctx._check(set_all(ctx.h, C.c_void_p(host_in.data_ptr()), 0), "set_all")
         ctx.step(1, want_dt=False)
-        ctx._check(lib.amrmhd_get_state_all(ctx.h, C.c_void_p(host_out.data_ptr()), 0), "get_all")
+        ctx._check(get_all(ctx.h, C.c_void_p(host_out.data_ptr()), 0), "get_all")
 
     one()
     torch.cuda.synchronize()
@@ -207,7 +212,7 @@ def e2e_run(pb, precision, k):
         one()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
-    nbytes = host_in.numel() * 8
+    nbytes = host_in.numel() * host_in.element_size()
     cells = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
     del ctx
     torch.cuda.empty_cache()

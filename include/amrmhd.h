@@ -138,6 +138,11 @@ amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* ds
 amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device);
 amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_device);
 
+/* The same with float elements (the stored type of AMRMHD_MIXED, so no
+ * rounding there; an FP64 context rounds on the way out and widens on the way in). */
+amrmhd_status amrmhd_set_state_all_f32(amrmhd_ctx* ctx, const float* src, int32_t on_device);
+amrmhd_status amrmhd_get_state_all_f32(amrmhd_ctx* ctx, float* dst, int32_t on_device);
+
 /* Exports integer map `which` (AMRMHD_MAP_*) as rows of int32; *width receives
  * the row width, *len the total int count; up to cap ints are written to dst
  * (host memory; dst may be NULL to query the size). Host-only. Row formats:

@@ -73,6 +73,8 @@ def lib():
             "amrmhd_step_dt": [vp, i32, vp],
             "amrmhd_set_state_all": [vp, vp, i32],
             "amrmhd_get_state_all": [vp, vp, i32],
+            "amrmhd_set_state_all_f32": [vp, vp, i32],
+            "amrmhd_get_state_all_f32": [vp, vp, i32],
             "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
             "amrmhd_regrid": [vp, dbl, i32],
             "amrmhd_autotune": [vp, i32, vp],

@@ -784,17 +784,18 @@ amrmhd_status amrmhd_get_state_packed(amrmhd_ctx* ctx, int32_t field, double* ds
 }
 
 // all 8 packed fields one after the other (the amrmhd_backward layout)
-static amrmhd_status io_all(amrmhd_ctx* ctx, double* buf, int32_t on_device, int to_state) {
+static amrmhd_status io_all(amrmhd_ctx* ctx, void* buf, int32_t on_device, int to_state, int f32) {
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
   const amrmhd::Hierarchy& H = ctx->H;
+  const size_t esz = f32 ? sizeof(float) : sizeof(double);
   long long total = 0, off[8];
   for (int f = 0; f < 8; ++f) {
     const int kind = (f >= 5 && !(H.dim == 2 && f == 7)) ? f - 4 : 0;
     off[f] = total;
     total += ctx->ptotal[kind];
   }
-  double* dev = buf;
+  void* dev = buf;
   bool mapped = false;
   if (!on_device) {
     // page-locked host memory mapped into the device address space: the packing
@@ -802,17 +803,17 @@ static amrmhd_status io_all(amrmhd_ctx* ctx, double* buf, int32_t on_device, int
     // staging copy); other host memory goes through a device staging buffer
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, buf) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
-      dev = (double*)pa.devicePointer;
+      dev = pa.devicePointer;
       mapped = true;
     } else {
       cudaGetLastError();  // an unregistered pointer is not an error here
       if (!ctx->d_stage_all) {
         cudaError_t e = cudaSuccess;
-        ctx->d_stage_all = dbuf<double>(ctx, (size_t)total, &e);
+        ctx->d_stage_all = dbuf<double>(ctx, (size_t)total, &e);  // room for either element type
         if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, "staging buffer");
       }
       dev = ctx->d_stage_all;
-      if (to_state) CU(cudaMemcpyAsync(dev, buf, total * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      if (to_state) CU(cudaMemcpyAsync(dev, buf, total * esz, cudaMemcpyHostToDevice, ctx->stream));
     }
   }
   // all 8 fields of a level per launch
@@ -820,23 +821,33 @@ static amrmhd_status io_all(amrmhd_ctx* ctx, double* buf, int32_t on_device, int
     const LevelDev& L = ctx->lev[l];
     int lm[3] = {L.maxn[0], L.maxn[1], L.maxn[2]};
     int nl = 0;
-    ctx->ops->io_all(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev, ctx->d_poff_tab, off, to_state,
-                     ctx->stream, &nl);
+    ctx->ops->io_all(ctx->dP, L.ids, L.npatch, lm, state_buf(ctx, ctx->cur[l]), dev, f32, ctx->d_poff_tab, off,
+                     to_state, ctx->stream, &nl);
   }
   if (!to_state && !on_device && !mapped)
-    CU(cudaMemcpyAsync(buf, dev, total * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(buf, dev, total * esz, cudaMemcpyDeviceToHost, ctx->stream));
   if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
   return AMRMHD_OK;
 }
 
 amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device) {
   if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
-  return io_all(ctx, (double*)src, on_device, 1);
+  return io_all(ctx, (void*)src, on_device, 1, 0);
 }
 
 amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_device) {
   if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
-  return io_all(ctx, dst, on_device, 0);
+  return io_all(ctx, dst, on_device, 0, 0);
+}
+
+amrmhd_status amrmhd_set_state_all_f32(amrmhd_ctx* ctx, const float* src, int32_t on_device) {
+  if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
+  return io_all(ctx, (void*)src, on_device, 1, 1);
+}
+
+amrmhd_status amrmhd_get_state_all_f32(amrmhd_ctx* ctx, float* dst, int32_t on_device) {
+  if (!dst) return fail(ctx, AMRMHD_EINVAL, "null destination");
+  return io_all(ctx, dst, on_device, 0, 1);
 }
 
 amrmhd_status amrmhd_export_map(amrmhd_ctx* ctx, int32_t which, int32_t* dst, int64_t cap, int64_t* len,

@@ -122,9 +122,11 @@ struct Ops {
   void (*io)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
              const long long* poff, int field, int to_state, cudaStream_t, int* launches);
   // the same for all 8 fields of a level in one launch: poff[kind] per field kind
-  // (device array of 4 device pointers), foff[f] = field f's offset in packed
-  void (*io_all)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
-                 const long long* const* poff, const long long* foff, int to_state, cudaStream_t, int* launches);
+  // (device array of 4 device pointers), foff[f] = field f's offset in packed;
+  // packed holds doubles, or floats if packed_f32
+  void (*io_all)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, void* packed,
+                 int packed_f32, const long long* const* poff, const long long* foff, int to_state, cudaStream_t,
+                 int* launches);
   size_t elem;  // bytes per stored value
   // fused path (3D): one kernel per level advance, registers recomputed from the input state
   void (*prepare)();

@@ -875,8 +875,8 @@ __global__ void __launch_bounds__(TPB) k_io(const DPatch* PP, const int* ids, vo
 struct IoAll {
   long long foff[8];
 };
-template <class T, int DIM>
-__global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids, void* state, double* packed,
+template <class T, int DIM, class Q>
+__global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids, void* state, Q* packed,
                                                 const long long* const* poff, IoAll io, int to_state) {
   const int pid = ids[blockIdx.y];
   const int field = blockIdx.z;
@@ -890,9 +890,9 @@ __global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids
   const int i = t % r[0], j = (t / r[0]) % r[1], k = t / (r[0] * r[1]);
   const int L = lidx(P, i + 4, j + 4, DIM == 3 ? k + 4 : 0);
   T* s = (T*)state + P.off + field * P.fs + L;
-  double* q = packed + io.foff[field] + poff[fd + 1][pid] + t;
+  Q* q = packed + io.foff[field] + poff[fd + 1][pid] + t;
   if (to_state) *s = (T)*q;
-  else *q = (double)*s;
+  else *q = (Q)*s;
 }
 
 #include "kernels_fused.cuh"
@@ -982,13 +982,16 @@ template <class T, int DIM> struct Impl {
     k_io<T, DIM><<<dim3(cdiv(n, TPB), npatch), TPB, 0, s>>>(P, ids, state, packed, poff, field, to_state);
     if (nl) ++*nl;
   }
-  static void io_all(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
-                     const long long* const* poff, const long long* foff, int to_state, cudaStream_t s, int* nl) {
+  static void io_all(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, void* packed,
+                     int packed_f32, const long long* const* poff, const long long* foff, int to_state, cudaStream_t s,
+                     int* nl) {
     long long n = 1;
     for (int d = 0; d < DIM; ++d) n *= maxn[d] + 1;
     IoAll io;
     for (int f = 0; f < 8; ++f) io.foff[f] = foff[f];
-    k_io_all<T, DIM><<<dim3(cdiv(n, TPB), npatch, 8), TPB, 0, s>>>(P, ids, state, packed, poff, io, to_state);
+    const dim3 g(cdiv(n, TPB), npatch, 8);
+    if (packed_f32) k_io_all<T, DIM, float><<<g, TPB, 0, s>>>(P, ids, state, (float*)packed, poff, io, to_state);
+    else k_io_all<T, DIM, double><<<g, TPB, 0, s>>>(P, ids, state, (double*)packed, poff, io, to_state);
     if (nl) ++*nl;
   }
   // fused 3D advance (2D falls back to the staged kernels)

@@ -366,3 +366,26 @@ def test_whole_state_io_page_locked_host_memory(precision):
     back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
     expect = new if precision == A.FP64 else new.astype(np.float32).astype(np.float64)
     assert np.array_equal(back, expect)
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_whole_state_io_float_elements(pinned):
+    """amrmhd_set_state_all_f32 / get_state_all_f32 move the stored FP32 values
+    of a mixed-precision context unchanged (page-locked or ordinary host
+    memory), and round / widen those of an FP64 context."""
+    import ctypes as C
+    import torch
+    pb = inputs.orszag_tang(32, 8, refine=True)
+    for precision in (A.MIXED, A.FP64):
+        ctx = gpu_for(pb, precision)
+        ref = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+        buf = torch.empty(ref.size, dtype=torch.float32)
+        if pinned:
+            buf = buf.pin_memory()
+        ctx._check(A.lib().amrmhd_get_state_all_f32(ctx.h, C.c_void_p(buf.data_ptr()), 0), "get_all_f32")
+        assert np.array_equal(buf.numpy(), ref.astype(np.float32))
+        new = (ref * 1.25).astype(np.float32)
+        buf.copy_(torch.from_numpy(new))
+        ctx._check(A.lib().amrmhd_set_state_all_f32(ctx.h, C.c_void_p(buf.data_ptr()), 0), "set_all_f32")
+        back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+        assert np.array_equal(back, new.astype(np.float64))
