@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--n", type=int, default=128)
     p.add_argument("--psize", type=int, default=16)
     p.add_argument("--skip-extras", action="store_true", help="headline only (no FP64/baseline/e2e/oracle legs)")
-    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error"],
+    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error", "cylinder"],
                    help="run one extra leg alone and print its JSON (for profiling)")
     p.add_argument("--leg-steps", type=int, default=None, help="coarse steps of the --leg run")
     return p.parse_args()
@@ -239,7 +239,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     ctx.regrid(theta, pb.nlev)
     tiles = ctx.autotune(3)
     ctx.step(1, want_dt=False)
-    updates, t_steps, t_regrid, breakdown = 0, 0.0, 0.0, [0, 0, 0, 0, 0]
+    updates, leaves, t_steps, t_regrid, breakdown = 0, 0, 0.0, 0.0, [0, 0, 0, 0, 0]
     nreg = 0
     for i in range(0, steps, regrid_every):
         k = min(regrid_every, steps - i)
@@ -247,6 +247,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
         ms, _ = timed_steps(ctx, stream, k)
         t_steps += ms / 1e3
         updates += per * k
+        leaves += leaf_updates(ctx.get_patches()) * k
         if i + k < steps:
             t0 = time.perf_counter()
             ctx.regrid(theta, pb.nlev)
@@ -263,6 +264,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     for (l, lo, hi) in ctx.get_patches():
         cells[l] = cells.get(l, 0) + (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
     out = {"value": updates / t_steps, "unit": UNIT, "with_regrid": updates / (t_steps + t_regrid),
+           "leaf_cell_updates_per_s": leaves / t_steps,
            "steps": steps, "regrid_every": regrid_every, "theta": theta, "regrids": nreg,
            "regrid_ms_mean": 1e3 * t_regrid / max(nreg, 1),
            "regrid_host_us_mean": {k: v / max(nreg, 1) for k, v in
@@ -270,6 +272,43 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
            "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
            "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
+def leaf_updates(patches, dim=3):
+    """Cell updates per coarse step counting leaf cells only: per level, its
+    cells minus those covered by the next level (each fine cell covers 2^-dim
+    of a coarse cell), times 2^level."""
+    cells = {}
+    for (l, lo, hi) in patches:
+        v = 1
+        for d in range(dim):
+            v *= hi[d] - lo[d]
+        cells[l] = cells.get(l, 0) + v
+    return sum((cells[l] - cells.get(l + 1, 0) // (1 << dim)) << l for l in cells)
+
+
+def cylinder_leg(steps=20):
+    """The paper's workload shape: an advected magnetized cylinder, 64^3 base in
+    16^3 patches and one static refined level over 12.5 % of the volume, mixed
+    precision, concurrent levels, autotuned tiles; coarse steps timed with CUDA
+    events."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    pb = inputs.cylinder_3d()
+    ctx, stream = make_ctx(pb, A.MIXED)
+    tiles = ctx.autotune(3)
+    ctx.step(2, want_dt=False)
+    per = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
+    ms, _ = timed_steps(ctx, stream, steps)
+    leaf = leaf_updates(pb.patches)
+    out = {"value": per * steps / (ms / 1e3), "unit": UNIT, "leaf_cell_updates_per_s": leaf * steps / (ms / 1e3),
+           "ms_per_step": ms / steps, "steps": steps, "cell_updates_per_step": per, "tiles": tiles,
+           "workload": "cylinder3d_64_2lev: magnetized cylinder (contrast 10, r 0.1) advected by v (1, 1/2, 0), "
+                       "B (sqrt2,0,0), level 1 over 12.5 % of the volume; mixed precision"}
     del ctx
     torch.cuda.empty_cache()
     return out
@@ -305,7 +344,9 @@ def shock_clump_leg(steps=10, theta=0.1):
     cells = {}
     for (l, lo, hi) in ctx.get_patches():
         cells[l] = cells.get(l, 0) + (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
-    out = {"value": per * steps / (ms / 1e3), "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+    out = {"value": per * steps / (ms / 1e3), "unit": UNIT,
+           "leaf_cell_updates_per_s": leaf_updates(ctx.get_patches()) * steps / (ms / 1e3),
+           "steps": steps, "ms_per_step": ms / steps,
            "cells_per_level": [cells[l] for l in sorted(cells)], "patches": ctx.query(A.Q_NPATCH),
            "arena_gb": ctx.query(A.Q_ARENA_BYTES) / 1e9, "regrid_s": t_regrid,
            "regrid_host_us": {k: ctx.query(A.Q_REGRID_FLAG_US + i)
@@ -476,7 +517,7 @@ def main():
         if args.leg == "adjoint" and args.leg_steps is not None:
             kw["ckpt"] = max(1, args.leg_steps // 2)
         fn = {"adjoint": adjoint_leg, "deep": deep_amr_leg, "shockclump": shock_clump_leg,
-              "error": mixed_error_leg}[args.leg]
+              "error": mixed_error_leg, "cylinder": cylinder_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(**kw) if args.leg != "error" else fn()}), flush=True)
         return
@@ -532,6 +573,7 @@ def main():
         extras["deep_amr_clumps3d"] = deep_amr_leg()
         extras["adjoint_2d"] = adjoint_leg()
         extras["shock_clump3d"] = shock_clump_leg()
+        extras["cylinder3d_paper_shape"] = cylinder_leg()
     e2e = None
     if not args.skip_extras:
         ke = max(3, args.steps // 10)

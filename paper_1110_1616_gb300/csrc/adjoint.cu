@@ -13,10 +13,10 @@
 // level), of the advance stage by stage (update, EMF, HLLD, predictor and
 // slopes, recovery), and of the fill (scatter-add of every copied or
 // prolonged ghost value to its sources). The transposed Jacobians of the two
-// costliest pointwise formulas (HLLD and the half-step predictor) are written
-// by hand (adjoint_local.cuh); those of the recovery and the edge EMF come from
-// the same templated device formulas as the forward evaluated with
-// forward-mode dual numbers (also kept for HLLD and the predictor, as the
+// costliest pointwise formulas (HLLD, the half-step predictor, the recovery)
+// are written by hand (adjoint_local.cuh); that of the edge EMF comes from the
+// same templated device formula as the forward evaluated with forward-mode
+// dual numbers (dual numbers are also kept for HLLD and the predictor, as the
 // cross-check of amrmhd_local_vjp); branches (minmod, HLLD cases, upwinding)
 // take the forward's decisions. Adjoint arithmetic is FP64 in both precision modes, at the forward
 // trajectory of the context's precision.
@@ -98,18 +98,6 @@ template <int K> __device__ __forceinline__ Dn<K> dabs(const Dn<K>& a) {
 template <int K> struct Eps<Dn<K>> {
   static __device__ __forceinline__ Dn<K> v() { return Dn<K>(1e-12); }
 };
-
-// the FP64 recovery formula of recover(), generic in the value type
-template <class T> __device__ __forceinline__ void recover_g(const T* u, const T* bc, T gm1, T* w) {
-  const T r = u[0];
-  const T ir = T(1.0) / r;
-  const T vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
-  const T ke = T(0.5) * (u[1] * vx + u[2] * vy + u[3] * vz);
-  const T me = T(0.5) * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
-  w[0] = r; w[1] = vx; w[2] = vy; w[3] = vz;
-  w[4] = gm1 * ((u[4] - ke) - me);
-  w[5] = bc[0]; w[6] = bc[1]; w[7] = bc[2];
-}
 
 // J^T g of fn: R^NIN -> R^NOUT at x, by forward-mode chunks of K tangents
 template <int NIN, int NOUT, int K, class Fn>
@@ -521,13 +509,6 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_adj_predict
   (void)U;
 }
 
-struct RecFn {
-  double gm1;
-  template <class V> __device__ __forceinline__ void operator()(const V* x, V* y) const {
-    recover_g<V>(x, x + 5, V(gm1), y);
-  }
-};
-
 // recovery W(U) on region w+2; cell-centred B from the two faces
 template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_adj_prim(AdjArgs a) {
   const DPatch P = a.P[a.ids[blockIdx.y]];
@@ -553,7 +534,7 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_adj_prim(Ad
   if (DIM == 3) x[7] = 0.5 * ((double)U[7 * fs + L] + (double)U[7 * fs + L + P.ext[0] * P.ext[1]]);
   else x[7] = (double)U[7 * fs + L];
   double gx[8];
-  vjp<8, 8, 8>(x, g, gx, RecFn{a.gamma - 1.0});
+  recover_vjp(x, g, a.gamma - 1.0, gx);
   double* lx = a.lamx + P.off;
 #pragma unroll
   for (int f = 0; f < 5; ++f) aadd(lx + f * fs + L, gx[f]);

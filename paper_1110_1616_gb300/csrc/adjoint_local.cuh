@@ -1,6 +1,6 @@
-// Hand-written reverse mode of the two costliest pointwise formulas of the
-// advance: the HLLD flux (hlld_flux) and the half-step primitive predictor
-// (prim_terms summed over directions). Each function returns the exact
+// Hand-written reverse mode of the costliest pointwise formulas of the
+// advance: the HLLD flux (hlld_flux), the half-step primitive predictor
+// (prim_terms summed over directions) and the recovery. Each function returns the exact
 // transposed Jacobian-vector product of the formula in the compute type R
 // (double: the FP64 forward; float: the FP32 stencil of the mixed-precision
 // forward, with its own degenerate-state threshold), taking the branch the
@@ -587,6 +587,27 @@ __device__ __forceinline__ void predict_vjp(const R* x, const R* g, R gamma, con
     prim_terms_vjp<2>(w, x + 24, gamma, ir, G, gx, gx + 24, gir);
   }
   gx[0] -= ir * ir * gir;
+}
+
+// gx[8] = J^T g of the recovery W(U, B_c) (recover_g in adjoint.cu): x = (rho,
+// m_x, m_y, m_z, E, B_cx, B_cy, B_cz), W = (rho, v, p, B_c), p = gm1 ((E - ke) - me)
+__device__ __forceinline__ void recover_vjp(const double* x, const double* g, double gm1, double* gx) {
+  const double r = x[0], ir = 1.0 / r;
+  const double vx = x[1] * ir, vy = x[2] * ir, vz = x[3] * ir;
+  const double gp = g[4];
+  const double gke = -gm1 * gp, gme = -gm1 * gp;
+  // ke = (m_x vx + m_y vy + m_z vz) / 2; v = m ir
+  const double gvx = g[1] + 0.5 * x[1] * gke, gvy = g[2] + 0.5 * x[2] * gke, gvz = g[3] + 0.5 * x[3] * gke;
+  const double gir = x[1] * gvx + x[2] * gvy + x[3] * gvz;
+  gx[0] = g[0] - ir * ir * gir;
+  gx[1] = 0.5 * vx * gke + ir * gvx;
+  gx[2] = 0.5 * vy * gke + ir * gvy;
+  gx[3] = 0.5 * vz * gke + ir * gvz;
+  gx[4] = gm1 * gp;
+  // me = |B_c|^2 / 2
+  gx[5] = g[5] + x[5] * gme;
+  gx[6] = g[6] + x[6] * gme;
+  gx[7] = g[7] + x[7] * gme;
 }
 
 }  // namespace amrdev

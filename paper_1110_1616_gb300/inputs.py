@@ -205,6 +205,34 @@ def blast_3d(n=128, psize=16, gamma=GAMMA):
     return Problem("blast_3d", 3, nn, patches, 1, state, gamma=gamma)
 
 
+def cylinder_3d(n=64, psize=16, contrast=10.0, radius=0.1, gamma=GAMMA):
+    """The paper's workload shape (Sec. 6: an advected magnetized cylinder, one
+    refined level over 12.5 % of the domain): periodic [0,1]^3, a dense
+    cylinder along z through (1/2, 1/2) (density contrast `contrast`, edge
+    smoothed over one coarse cell), pressure 1, flow v = (1, 1/2, 0), uniform
+    field B = (sqrt 2, 0, 0) (plasma beta 1). Level 0 is n^3 in psize^3 patches;
+    level 1 covers the central (n/2)^3 coarse cells (1/8 of the volume) in
+    psize^3 fine patches. Whole-level arrays on both levels."""
+    base = (n, n, n)
+    patches = tile(0, (0, 0, 0), base, psize, 3) + tile(1, (n // 2,) * 3, (3 * n // 2,) * 3, psize, 3)
+    b0 = math.sqrt(2.0)
+    state = {}
+    for l in range(2):
+        m = n << l
+        x, y, z = _cell_centres((m, m, m), (0, 0, 0), (1, 1, 1), 3)
+        r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2)
+        w = 1.0 / n  # smoothing width: one coarse cell
+        rho = 1.0 + (contrast - 1.0) * 0.5 * (1.0 - np.tanh((r - radius) / w))
+        vx, vy = 1.0, 0.5
+        p = np.ones_like(x)
+        bx = np.full((m, m, m + 1), b0)
+        by = np.zeros((m, m + 1, m))
+        bz = np.zeros((m + 1, m, m))
+        e = _energy(rho, vx, vy, 0.0, p, b0, 0.0, 0.0, gamma)
+        state[l] = [rho, rho * vx, rho * vy, np.zeros_like(x), e, bx, by, bz]
+    return Problem("cylinder_3d", 3, base, patches, 2, state, gamma=gamma)
+
+
 def uniform_state(dim, base, patches, nlev, seed=0, gamma=GAMMA):
     """A random constant state on every level."""
     rng = np.random.default_rng(seed)
