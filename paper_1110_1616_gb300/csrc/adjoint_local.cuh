@@ -589,7 +589,7 @@ __device__ __forceinline__ void predict_vjp(const R* x, const R* g, R gamma, con
   gx[0] -= ir * ir * gir;
 }
 
-// gx[8] = J^T g of the recovery W(U, B_c) (recover_g in adjoint.cu): x = (rho,
+// gx[8] = J^T g of the FP64 recovery W(U, B_c) (recover() in mhd_device.cuh): x = (rho,
 // m_x, m_y, m_z, E, B_cx, B_cy, B_cz), W = (rho, v, p, B_c), p = gm1 ((E - ke) - me)
 __device__ __forceinline__ void recover_vjp(const double* x, const double* g, double gm1, double* gx) {
   const double r = x[0], ir = 1.0 / r;
