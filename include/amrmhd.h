@@ -324,23 +324,27 @@ enum {
                               patch at a time (baseline); 2: the staged kernels batched;
                               3: the fused kernel (3D) in either precision */
   AMRMHD_OPT_GRAPH = 1,    /* 1 (default): amrmhd_step replays a CUDA graph; 0: plain launches */
-  AMRMHD_OPT_TILE = 2,     /* fused 3D advance tile: -1 default (the autotuned tile per level after
-                              amrmhd_autotune, else 16x8 FP32, 8x8 FP64), 0: 16x16 tile with 256
-                              threads, 1: 16x16 / 512, 2: 16x8 / 256, 3: 8x8 / 256 */
+  AMRMHD_OPT_TILE = 2,     /* fused 3D advance tile: -1 default (the autotuned tile per level and
+                              sub-step kind after amrmhd_autotune, else 16x8 FP32, 8x8 FP64), 0: 16x16
+                              tile with 256 threads, 1: 16x16 / 512, 2: 16x8 / 256, 3: 8x8 / 256,
+                              4: 12x12 / 256 */
   AMRMHD_OPT_CONCURRENT = 3 /* 1 (default): in a coarse step the two sub-steps of level l+1 run on a
                               side stream concurrently with the advance of level l (they meet
                               before the reflux); 0: one stream, strictly in the recursive order */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 
-/* Autotuner of the fused 3D advance: for every level, times `trials` level
- * advances with each tile variant (AMRMHD_OPT_TILE 0..3) on the current state
- * with CUDA events and keeps the fastest per level (used while
- * AMRMHD_OPT_TILE is -1). The state is not changed: an advance reads the
- * current buffer and writes the other one. tiles (host, may be NULL) receives
- * the chosen variant per level (-1 where the staged kernels are used, i.e. FP64
- * by default and 2D). The variants compute identical results; only the time
- * differs. Synchronises the stream. */
+/* Autotuner of the fused 3D advance: for every level, and separately for its
+ * interior-only advance and (above level 0) its advance with 2 extended ghost
+ * layers (sub-step 1), times `trials` advances with each tile variant
+ * (AMRMHD_OPT_TILE 0..4) on the current state with CUDA events and keeps the
+ * fastest (used while AMRMHD_OPT_TILE is -1). The state is not changed: an
+ * advance reads the current buffer and writes the other one. tiles (host, may
+ * be NULL) receives the interior-only choice per level (-1 where the staged
+ * kernels are used, i.e. FP64 by default and 2D). The variants compute the
+ * same formulas in the same order: identical results in the strict FP64 build,
+ * FP32 rounding differences in mixed precision (where the compiler may
+ * contract multiply-adds differently per variant). Synchronises the stream. */
 amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles);
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx);

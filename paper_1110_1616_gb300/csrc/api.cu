@@ -181,7 +181,8 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
     }
   } else if (fused) {
     int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
-    if (ctx->opt_tile < 0 && (int)ctx->tile_level.size() > l && ctx->tile_level[l] >= 0) v = ctx->tile_level[l];
+    if (ctx->opt_tile < 0 && (int)ctx->tile_level.size() > l && ctx->tile_level[l][w ? 1 : 0] >= 0)
+      v = ctx->tile_level[l][w ? 1 : 0];
     ctx->ops->advance_fused(a, v, ctx->stream, nl);
   } else {
     ctx->ops->advance(a, ctx->stream, nl);
@@ -418,7 +419,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   if (!ctx) return AMRMHD_EINVAL;
   if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
-  else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 3) ctx->opt_tile = value;
+  else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 4) ctx->opt_tile = value;
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
@@ -697,7 +698,7 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     ctx->ev_fork.push_back(a);
     ctx->ev_join.push_back(b);
   }
-  ctx->tile_level.assign(nlev, -1);
+  ctx->tile_level.assign(nlev, {-1, -1});
   ctx->ops->prepare();
   CU(cudaGetLastError());
   ctx->bound = true;
@@ -1010,28 +1011,33 @@ amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {
   const int64_t keep = ctx->opt_tile;
   ctx->opt_tile = -1;
   for (int l = 0; l < nlev; ++l) {
-    float best = 0.0f;
-    int bv = -1;
-    for (int v = 0; v < 4; ++v) {
-      ctx->tile_level[l] = v;
-      const int c0 = ctx->cur[l];
-      op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), 1, &nl);  // warm-up
-      ctx->cur[l] = c0;
-      if (cudaGetLastError() != cudaSuccess) continue;
-      CU(cudaEventRecord(e0, ctx->stream));
-      for (int t = 0; t < trials; ++t) {
-        op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), 1, &nl);
+    // sub-step 1 of a level above 0 advances 2 extended ghost layers, sub-step 2
+    // (and level 0) the interior only: each gets its own tile
+    for (int s = 1; s <= (l > 0 ? 2 : 1); ++s) {
+      const int wi = (l > 0 && s == 1) ? 1 : 0;
+      float best = 0.0f;
+      int bv = -1;
+      for (int v = 0; v < 5; ++v) {
+        ctx->tile_level[l][wi] = v;
+        const int c0 = ctx->cur[l];
+        op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, &nl);  // warm-up
         ctx->cur[l] = c0;
+        if (cudaGetLastError() != cudaSuccess) continue;
+        CU(cudaEventRecord(e0, ctx->stream));
+        for (int t = 0; t < trials; ++t) {
+          op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, &nl);
+          ctx->cur[l] = c0;
+        }
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        if (cudaGetLastError() != cudaSuccess) continue;
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (bv < 0 || ms < best) { best = ms; bv = v; }
       }
-      CU(cudaEventRecord(e1, ctx->stream));
-      CU(cudaEventSynchronize(e1));
-      if (cudaGetLastError() != cudaSuccess) continue;
-      float ms = 0.0f;
-      CU(cudaEventElapsedTime(&ms, e0, e1));
-      if (bv < 0 || ms < best) { best = ms; bv = v; }
+      ctx->tile_level[l][wi] = bv;
+      if (tiles && wi == 0) tiles[l] = bv;
     }
-    ctx->tile_level[l] = bv;
-    if (tiles) tiles[l] = bv;
   }
   ctx->opt_tile = keep;
   cudaEventDestroy(e0);

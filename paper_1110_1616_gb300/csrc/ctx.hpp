@@ -58,7 +58,9 @@ struct amrmhd_ctx {
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
   int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1;
-  std::vector<int> tile_level;  // autotuned fused tile per level (-1: none)
+  // autotuned fused tile per level, for the interior-only advance ([0]) and the
+  // advance with 2 extended ghost layers ([1]) (-1: none)
+  std::vector<std::array<int, 2>> tile_level;
   // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
   // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
   bool fused() const {

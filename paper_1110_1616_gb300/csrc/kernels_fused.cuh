@@ -18,12 +18,13 @@
 
 // Tile variants (x-y output tile and threads per CTA), chosen by the
 // autotuning option: 0 = 16x16 / 256, 1 = 16x16 / 512, 2 = 16x8 / 256,
-// 3 = 8x8 / 256.
+// 3 = 8x8 / 256, 4 = 12x12 / 256 (an 8^3 patch with its 2 extended layers).
 template <int V> struct FusedCfg;
 template <> struct FusedCfg<0> { static constexpr int TX = 16, TY = 16, NT = 256; };
 template <> struct FusedCfg<1> { static constexpr int TX = 16, TY = 16, NT = 512; };
 template <> struct FusedCfg<2> { static constexpr int TX = 16, TY = 8, NT = 256; };
 template <> struct FusedCfg<3> { static constexpr int TX = 8, TY = 8, NT = 256; };
+template <> struct FusedCfg<4> { static constexpr int TX = 12, TY = 12, NT = 256; };
 
 template <class T, int TX_, int TY_> struct FusedSmem {
   static constexpr int TX = TX_, TY = TY_;

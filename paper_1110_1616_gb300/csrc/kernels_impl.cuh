@@ -1008,7 +1008,7 @@ template <class T, int DIM> struct Impl {
     }
   }
   static void prepare() {
-    if (DIM == 3) { prepare_v<0>(); prepare_v<1>(); prepare_v<2>(); prepare_v<3>(); }
+    if (DIM == 3) { prepare_v<0>(); prepare_v<1>(); prepare_v<2>(); prepare_v<3>(); prepare_v<4>(); }
   }
   template <int V> static void launch_fused(const LevelArgs& a, cudaStream_t s) {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
@@ -1026,6 +1026,7 @@ template <class T, int DIM> struct Impl {
     if (variant == 0 && fused_fits<0>()) launch_fused<0>(a, s);
     else if (variant == 1 && fused_fits<1>()) launch_fused<1>(a, s);
     else if (variant == 2 && fused_fits<2>()) launch_fused<2>(a, s);
+    else if (variant == 4 && fused_fits<4>()) launch_fused<4>(a, s);
     else launch_fused<3>(a, s);
     if (nl) ++*nl;
   }
