@@ -492,7 +492,7 @@ def run_reference(args, world, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": "blast3d_%d_p%d" % (args.n, args.psize), "global_batch": 1,
-                       "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "parallelism": "replicas"},
+                       "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "parallelism": "replicas" if world > 1 else "single"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
