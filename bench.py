@@ -126,14 +126,21 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, v):
+def allmax(world, v, device="cuda"):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms_local, device="cuda"):
+    """Whole-job throughput of N replicas (weak scaling): the units all ranks
+    processed over the slowest rank's time; returns (rate per second, max ms)."""
+    ms_max = allmax(world, ms_local, device)
+    return units_per_rank * world / (ms_max / 1e3), ms_max
 
 
 def make_ctx(pb, precision, strict=False, baseline=False, graph=True):
@@ -534,8 +541,7 @@ def main():
     barrier(world)
     ms, launches = timed_steps(ctx, stream, args.steps)
     clk = clocks.stop()
-    ms_max = allmax(world, ms)
-    value = cells_step * args.steps * world / (ms_max / 1e3)
+    value, ms_max = whole_job_rate(world, cells_step * args.steps, ms)
 
     # level advance alone, against the HBM roofline (algorithmic bytes: the 8
     # stored fields read and written once per cell update, 16 x 4 B in FP32)
