@@ -266,6 +266,22 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
 amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const double* x, const double* g, double gamma,
                                const double* h, int32_t method, double* gx);
 
+/* Diagnostic: the FP32 <-> FP64 conversions of the mixed-precision recovery
+ * (Sec. 1 names FP64 for the energy balance p = (gamma-1)(E - ke - me); the
+ * mixed path widens its FP32 operands and rounds the FP64 pressure back to
+ * FP32 with integer operations on the bit patterns). For i < n (host arrays):
+ * x_narrow[i] = x[i] rounded to FP32 (nearest even, results below 2^-126
+ * flushed to a signed zero), y_widen[i] = y[i] widened to FP64 (FP32
+ * subnormals flushed), and x_narrow_hw[i], y_widen_hw[i] the same conversions
+ * by the compiler's casts. on_device 0 evaluates everything on the host CPU;
+ * 1 in a kernel compiled as the mixed path is (FP32 denormals flushed), with
+ * the hardware conversion instructions as the reference. Allocates and frees
+ * device memory for on_device 1 and synchronises the device. Errors:
+ * AMRMHD_EINVAL for on_device not 0/1, n < 0 or NULL arrays with n > 0;
+ * AMRMHD_ECUDA if an allocation, copy or launch fails. */
+amrmhd_status amrmhd_fp_convert(int32_t on_device, int64_t n, const double* x, const float* y, float* x_narrow,
+                                double* y_widen, float* x_narrow_hw, double* y_widen_hw);
+
 /* Regrid: rebuilds every level above 0, coarse to fine, up to max_levels
  * levels (Sec. 2: the grids follow the flagged regions; a new grid takes its
  * data from the preceding overlapping grid of its level, else from the coarser
@@ -330,7 +346,8 @@ enum {
                               4: 12x12 / 256 */
   AMRMHD_OPT_CONCURRENT = 3 /* 1 (default): in a coarse step the two sub-steps of level l+1 run on a
                               side stream concurrently with the advance of level l (they meet
-                              before the reflux); 0: one stream, strictly in the recursive order */
+                              before the reflux), and the CFL reduction runs beside the level-0
+                              ghost fill; 0: one stream, strictly in the recursive order */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

@@ -83,6 +83,7 @@ def lib():
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
             "amrmhd_set_option": [vp, i32, i64],
             "amrmhd_local_vjp": [i32, i32, i64, vp, vp, dbl, vp, i32, vp],
+            "amrmhd_fp_convert": [i32, i64, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -113,6 +114,27 @@ def local_vjp(which, x, g, gamma=5.0 / 3.0, dim=3, h=None, method=0):
     if st != 0:
         raise RuntimeError("amrmhd_local_vjp failed: status %d" % st)
     return gx
+
+
+def fp_convert(x, y, on_device=False):
+    """The mixed recovery's bit-level conversions next to the compiler's casts:
+    returns (narrow(x), widen(y), cast_f32(x), cast_f64(y)) for numpy arrays x
+    (float64) and y (float32) of one length; on_device runs them in a kernel of
+    the mixed-precision unit, else on the host."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    if x.shape != y.shape:
+        raise ValueError("x and y must have one shape")
+    n = x.size
+    xn = np.empty(n, np.float32)
+    xh = np.empty(n, np.float32)
+    yw = np.empty(n, np.float64)
+    yh = np.empty(n, np.float64)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib().amrmhd_fp_convert(int(bool(on_device)), n, p(x), p(y), p(xn), p(yw), p(xh), p(yh))
+    if st != 0:
+        raise RuntimeError("amrmhd_fp_convert failed: status %d" % st)
+    return xn, yw, xh, yh
 
 
 def declared_symbols():

@@ -23,7 +23,7 @@ UNITS = [
 ]
 HOST_UNITS = ["hierarchy.cpp", "regrid.cpp"]
 HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp",
-           "adjoint_local.cuh",
+           "adjoint_local.cuh", "fp_bits.cuh",
            "regrid.hpp"]
 
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ctx.hpp"
+#include "fp_bits.cuh"
 
 using amrk::DPatch;
 using amrk::LevelArgs;
@@ -42,6 +43,11 @@ void free_device(amrmhd_ctx* ctx) {
   ctx->side.clear();
   ctx->ev_fork.clear();
   ctx->ev_join.clear();
+  if (ctx->cfl_stream) cudaStreamDestroy(ctx->cfl_stream);
+  if (ctx->ev_cfl_fork) cudaEventDestroy(ctx->ev_cfl_fork);
+  if (ctx->ev_cfl_join) cudaEventDestroy(ctx->ev_cfl_join);
+  ctx->cfl_stream = nullptr;
+  ctx->ev_cfl_fork = ctx->ev_cfl_join = nullptr;
   ctx->tile_level.clear();
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -278,9 +284,11 @@ void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
 // of both sides are separate arrays, so the two are joined only before the
 // reflux and restriction (Sec. 4: finer levels need not wait for the coarser
 // level's advance).
-void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl) {
-  op_fill(ctx, l, s, nl);
-  if (ctx->after_fill) ctx->after_fill(ctx, l, s);
+void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled) {
+  if (!filled) {
+    op_fill(ctx, l, s, nl);
+    if (ctx->after_fill) ctx->after_fill(ctx, l, s);
+  }
   const bool kids = l + 1 < ctx->H.nlev;
   if (kids && ctx->opt_concurrent && (int)ctx->side.size() > l) {
     cudaStream_t main = ctx->stream, side = ctx->side[l];
@@ -304,7 +312,24 @@ void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl) {
   }
 }
 
+// The CFL reduction reads the interior cells and own faces of every level and
+// the level-0 fill writes only level-0 ghosts, so with concurrency on the two
+// run side by side (both short, latency-bound kernels), joined before the
+// level-0 advance reads dt.
 void op_coarse_step(amrmhd_ctx* ctx, int* nl) {
+  if (ctx->opt_concurrent && ctx->cfl_stream && !ctx->after_fill) {
+    cudaStream_t main = ctx->stream;
+    cudaEventRecord(ctx->ev_cfl_fork, main);
+    cudaStreamWaitEvent(ctx->cfl_stream, ctx->ev_cfl_fork, 0);
+    ctx->stream = ctx->cfl_stream;
+    op_cfl(ctx, ctx->d_hist, nl);
+    cudaEventRecord(ctx->ev_cfl_join, ctx->cfl_stream);
+    ctx->stream = main;
+    op_fill(ctx, 0, 1, nl);
+    cudaStreamWaitEvent(main, ctx->ev_cfl_join, 0);
+    op_level_step(ctx, 0, 1, nl, true);
+    return;
+  }
   op_cfl(ctx, ctx->d_hist, nl);
   op_level_step(ctx, 0, 1, nl);
 }
@@ -460,6 +485,8 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
     for (int q : H.level_patches[l]) {
       const long long e = (long long)H.p[q].ext[0] * H.p[q].ext[1] * H.p[q].ext[2];
       const long long f = (e + 63) / 64 * 64;
+      // the fill records carry field strides (x 8 fields) in 32 bits
+      if (8 * f > INT32_MAX) return fail(ctx, AMRMHD_EINVAL, "patch too large (over 2^28 elements per field)");
       ctx->fs[q] = f;
       ctx->off[q] = acc;
       acc += 8 * f;
@@ -612,8 +639,10 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     };
     // a same-level box as a self-contained copy record (see k_fill_runs): element
     // offsets of the first destination and source positions (with the face
-    // field for a face box), both patches' x/y strides and field strides,
-    // extents and the number of fields
+    // field for a face box), both patches' x/y extents and field strides, the
+    // box's nx, ny, the number of fields, cx = min(nx, 64) and the multipliers
+    // of the lane -> (x, row) and row -> (y, z) divisions; chunks (box, x0,
+    // q0, nrows) of whole rows q = y + ny z of cx positions
     auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
       const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
       const long long Ld = b[4] + (long long)D.ext[0] * (b[5] + (long long)D.ext[1] * b[6]);
@@ -622,15 +651,25 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       const int fl = b[1] < 0 ? 0 : 5 + b[1];  // B_x, B_y, B_z are fields 5, 6, 7
       const long long db = ctx->off[b[0]] + fl * fd + Ld, sb = ctx->off[b[3]] + fl * fsrc + Ls;
       const int nv = b[1] >= 0 ? 1 : (H.dim == 3 ? 5 : 6);
+      const int nx = b[7], ny = b[8], nz = b[9];
+      const int cx = std::min(nx, amrk::FILL_CHUNK);
+      const uint64_t two31 = 1ull << 31;
+      const uint32_t mcx = (uint32_t)((two31 + cx - 1) / cx), mny = (uint32_t)((two31 + ny - 1) / ny);
       const int bi = (int)(boxes.size() / amrk::FILL_BOX_W);
       const int32_t rec[amrk::FILL_BOX_W] = {(int32_t)(db & 0xffffffffLL), (int32_t)(db >> 32),
                                              (int32_t)(sb & 0xffffffffLL), (int32_t)(sb >> 32),
                                              D.ext[0], D.ext[1], S.ext[0], S.ext[1],
-                                             (int32_t)(fd & 0xffffffffLL), (int32_t)(fd >> 32),
-                                             (int32_t)(fsrc & 0xffffffffLL), (int32_t)(fsrc >> 32),
-                                             b[7], b[8], b[9], nv};
+                                             (int32_t)fd, (int32_t)fsrc, nx, ny,
+                                             nv, cx, (int32_t)mcx, (int32_t)mny};
       boxes.insert(boxes.end(), rec, rec + amrk::FILL_BOX_W);
-      chunks_of(ch, bi, b[7] * b[8] * b[9]);
+      const int rows = ny * nz, per = amrk::FILL_CHUNK / cx;
+      for (int q0 = 0; q0 < rows; q0 += per)
+        for (int x0 = 0; x0 < nx; x0 += cx) {
+          ch.push_back(bi);
+          ch.push_back(x0);
+          ch.push_back(q0);
+          ch.push_back(std::min(per, rows - q0));
+        }
     };
     auto add_box = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
       const int bi = (int)(boxes.size() / amrmhd::GHOST_BOX_W);
@@ -656,11 +695,11 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       }
     }
     const int GW = amrmhd::GHOST_BOX_W;
-    bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 2) &&
+    bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 4) &&
               upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
               upload(pfb, L.prol_faces, GW) && upload(pfc, L.chunk_pfaces, 2) && upload(bcb, L.bc_cells, GW) &&
               upload(bcc, L.chunk_bcells, 2) && upload(bfb, L.bc_faces, GW) && upload(bfc, L.chunk_bfaces, 2);
-    ok = ok && upload(rr2, L.runs2, amrk::FILL_BOX_W) && upload(cr2, L.chunk_runs2, 2) &&
+    ok = ok && upload(rr2, L.runs2, amrk::FILL_BOX_W) && upload(cr2, L.chunk_runs2, 4) &&
          upload(bcb2, L.bc_cells2, GW) && upload(bcc2, L.chunk_bcells2, 2) &&
          upload(bfb2, L.bc_faces2, GW) && upload(bfc2, L.chunk_bfaces2, 2);
     if (l > 0 && ok) {
@@ -697,6 +736,11 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     ctx->side.push_back(st);
     ctx->ev_fork.push_back(a);
     ctx->ev_join.push_back(b);
+  }
+  if (!ctx->stage_light) {
+    CU(cudaStreamCreateWithFlags(&ctx->cfl_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&ctx->ev_cfl_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&ctx->ev_cfl_join, cudaEventDisableTiming));
   }
   ctx->tile_level.assign(nlev, {-1, -1});
   ctx->ops->prepare();
@@ -1077,5 +1121,47 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
 }
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+amrmhd_status amrmhd_fp_convert(int32_t on_device, int64_t n, const double* x, const float* y, float* x_narrow,
+                                double* y_widen, float* x_narrow_hw, double* y_widen_hw) {
+  if ((on_device != 0 && on_device != 1) || n < 0 ||
+      (n > 0 && (!x || !y || !x_narrow || !y_widen || !x_narrow_hw || !y_widen_hw)))
+    return AMRMHD_EINVAL;
+  if (n == 0) return AMRMHD_OK;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i) {
+      x_narrow[i] = amrdev::narrow_bits(x[i]);
+      y_widen[i] = amrdev::widen_bits(y[i]);
+      x_narrow_hw[i] = (float)x[i];
+      y_widen_hw[i] = (double)y[i];
+    }
+    return AMRMHD_OK;
+  }
+  // one allocation: x, y_widen, y_widen_hw (doubles), then y, x_narrow, x_narrow_hw
+  char* buf = nullptr;
+  const size_t nd = sizeof(double) * (size_t)n, nf = sizeof(float) * (size_t)n;
+  if (cudaMalloc(&buf, 3 * nd + 3 * nf) != cudaSuccess) return AMRMHD_ECUDA;
+  double* dx = (double*)buf;
+  double* dyw = dx + n;
+  double* dywh = dyw + n;
+  float* dy = (float*)(buf + 3 * nd);
+  float* dxn = dy + n;
+  float* dxnh = dxn + n;
+  amrmhd_status st = AMRMHD_OK;
+  if (cudaMemcpy(dx, x, nd, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dy, y, nf, cudaMemcpyHostToDevice) != cudaSuccess) {
+    st = AMRMHD_ECUDA;
+  } else {
+    amrk::launch_fp_convert(n, dx, dy, dxn, dyw, dxnh, dywh, 0);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(x_narrow, dxn, nf, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(x_narrow_hw, dxnh, nf, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(y_widen, dyw, nd, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(y_widen_hw, dywh, nd, cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = AMRMHD_ECUDA;
+  }
+  cudaFree(buf);
+  return st;
+}
 
 }  // extern "C"

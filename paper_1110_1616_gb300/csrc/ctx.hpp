@@ -21,10 +21,11 @@ struct LevelDev {
   int* ids = nullptr;  // patch ids of the level (device)
   int npatch = 0;
   int maxn[3] = {1, 1, 1};
-  // ghost fill of this level as boxes, each list with its chunks (box, first
-  // position) of at most 64 positions: same-level copies (FILL_BOX_W ints per
-  // box, cells and faces in one list), prolongation and physical boundaries
-  // (GHOST_BOX_W ints per box)
+  // ghost fill of this level as boxes, each list with its chunks of at most
+  // 64 positions: same-level copies (FILL_BOX_W ints per box, cells and faces
+  // in one list, chunks of 4 ints: box, x0, q0, nrows), prolongation and
+  // physical boundaries (GHOST_BOX_W ints per box, chunks of 2 ints: box,
+  // first position)
   DevList runs, chunk_runs;
   DevList prol_cells, prol_faces, chunk_pcells, chunk_pfaces;
   DevList bc_cells, bc_faces, chunk_bcells, chunk_bfaces;
@@ -103,6 +104,9 @@ struct amrmhd_ctx {
   // inter-level concurrency: side stream and fork/join events per level
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_fork, ev_join;
+  // the coarse step's CFL reduction beside the level-0 ghost fill
+  cudaStream_t cfl_stream = nullptr;
+  cudaEvent_t ev_cfl_fork = nullptr, ev_cfl_join = nullptr;
   // called after every ghost fill of op_level_step (level, sub-step): the
   // adjoint records the filled states there
   void (*after_fill)(amrmhd_ctx*, int, int) = nullptr;
@@ -121,7 +125,7 @@ void level_idx(amrmhd_ctx* ctx, int l, double* idx);
 void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl);
 void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, int* nl);
 void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl);
-void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl);
+void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled = false);
 amrmhd_status check_bound(amrmhd_ctx* ctx);
 amrmhd_status upload_fill_rows(amrmhd_ctx* ctx);
 void adj_free(amrmhd_ctx* ctx);  // adjoint.cu

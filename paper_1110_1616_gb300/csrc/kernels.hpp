@@ -103,11 +103,11 @@ struct Ops {
   void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
   void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
   void (*reg_fine)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
-  // ghost fill, all as boxes: rows = the box list, chunks = (box, first
-  // position) per chunk of at most FILL_CHUNK positions, nrows = the number of
-  // chunks. Same-level copies (FILL_BOX_W-int boxes, cells and faces in one
-  // list), then prolongation and physical boundaries (ghost boxes of
-  // amrmhd::GHOST_BOX_W ints)
+  // ghost fill, all as boxes: rows = the box list, chunks of at most
+  // FILL_CHUNK positions, nrows = the number of chunks. Same-level copies
+  // (FILL_BOX_W-int boxes, cells and faces in one list; chunks (box, x0, q0,
+  // nrows) of whole box rows), then prolongation and physical boundaries
+  // (ghost boxes of amrmhd::GHOST_BOX_W ints; chunks (box, first position))
   void (*fill_runs)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
@@ -145,6 +145,8 @@ struct Ops {
 
 const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED
 const Ops* ops_strict(int dim);               // V_FP64_STRICT
+void launch_fp_convert(long long n, const double* x, const float* y, float* xn, double* yw, float* xn_hw,
+                       double* yw_hw, cudaStream_t s);
 
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_cfl_finalize(const unsigned long long* slots, int nlev, double cfl, double* dt_out, double* hist,

@@ -10,6 +10,23 @@ const Ops* ops_fast(int variant, int dim) {
   return dim == 3 ? amrk_fast::Impl<double, 3>::ops() : amrk_fast::Impl<double, 2>::ops();
 }
 
+// the bit-level conversions of the mixed recovery next to the conversion
+// instructions, compiled with this unit's flags (FP32 denormals flushed)
+__global__ void k_fp_convert(long long n, const double* x, const float* y, float* xn, double* yw, float* xn_hw,
+                             double* yw_hw) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  xn[i] = amrdev::narrow_bits(x[i]);
+  yw[i] = amrdev::widen_bits(y[i]);
+  xn_hw[i] = (float)x[i];
+  yw_hw[i] = (double)y[i];
+}
+
+void launch_fp_convert(long long n, const double* x, const float* y, float* xn, double* yw, float* xn_hw,
+                       double* yw_hw, cudaStream_t s) {
+  k_fp_convert<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y, xn, yw, xn_hw, yw_hw);
+}
+
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }

@@ -327,56 +327,70 @@ template <class T, int DIM> __global__ void k_reg_fine_edges(RowArgs a) {
 // ------------------------------------------------------------------ ghost fill
 // Same-level copies as boxes, cells and faces in one list. A box record
 // (FILL_BOX_W ints) holds everything a copy needs, so no patch record is read:
-// the destination and source element offsets of its first position (field 0
-// of a cell box, the face field of a face box), the x and y strides of both
-// patches, both field strides, the extents nx, ny, nz and the number of fields
-// nv (5 cells in 3D, 6 in 2D with B_z, 1 for faces). chunks[2c], chunks[2c+1]
-// = (box, first position) of chunk c (at most FILL_CHUNK positions of one box).
+// the destination and source element offsets of its first position (64-bit;
+// field 0 of a cell box, the face field of a face box), the x and y extents of
+// both patches, both field strides, the box extents nx and ny, the number of
+// fields nv (5 cells in 3D, 6 in 2D with B_z, 1 for faces), cx = min(nx, 64)
+// and the multipliers ceil(2^31 / cx), ceil(2^31 / ny). A box is a list of
+// rows q = y + ny z along x; a chunk (int4: box, x0, q0, nrows) is nrows whole
+// rows of cx positions from (x0, q0), at most FILL_CHUNK positions, so a
+// position's coordinates follow from its lane by two multiply-high divisions:
+// floor(a / n) = hi32(2a ceil(2^31 / n)), exact while a n < 2^31.
 constexpr int FILL_TPB = FILL_CHUNK;
 struct FillPos {
-  long long d, s, dfs, sfs;
-  int nv;
+  long long d, s;
+  int dfs, sfs, nv;
 };
-__device__ __forceinline__ bool fill_pos(const int* boxes, const int* chunks, long long w, FillPos& o) {
-  const long long ch = w / FILL_CHUNK;
-  const int2 cr = reinterpret_cast<const int2*>(chunks)[ch];
+__device__ __forceinline__ bool fill_pos(const int* boxes, const int4* chunks, long long c, int t, FillPos& o) {
+  const int4 cr = chunks[c];
   const int4* br = reinterpret_cast<const int4*>(boxes + FILL_BOX_W * (long long)cr.x);
-  const int4 b3 = br[3];
-  const int k = cr.y + (int)(w % FILL_CHUNK);
-  if (k >= b3.x * b3.y * b3.z) return false;
-  const int4 b0 = br[0], b1 = br[1], b2 = br[2];
-  const int x = k % b3.x, y = (k / b3.x) % b3.y, z = k / (b3.x * b3.y);
+  const int4 b2 = br[2], b3 = br[3];  // (dfs, sfs, nx, ny), (nv, cx, mcx, mny)
+  const unsigned r = __umulhi(2u * (unsigned)t, (unsigned)b3.z);
+  const int x = cr.y + t - (int)r * b3.y;
+  if ((int)r >= cr.w || x >= b2.z) return false;
+  const unsigned q = (unsigned)cr.z + r;
+  const unsigned z = __umulhi(2u * q, (unsigned)b3.w);
+  const int y = (int)(q - z * (unsigned)b2.w);
+  const int4 b0 = br[0], b1 = br[1];  // offsets; (dext0, dext1, sext0, sext1)
   const long long db = ((long long)(unsigned)b0.x) | ((long long)b0.y << 32);
   const long long sb = ((long long)(unsigned)b0.z) | ((long long)b0.w << 32);
-  o.dfs = ((long long)(unsigned)b2.x) | ((long long)b2.y << 32);
-  o.sfs = ((long long)(unsigned)b2.z) | ((long long)b2.w << 32);
-  o.d = db + x + (long long)b1.x * (y + (long long)b1.y * z);
-  o.s = sb + x + (long long)b1.z * (y + (long long)b1.w * z);
-  o.nv = b3.w;
+  o.d = db + (x + b1.x * (y + b1.y * (int)z));
+  o.s = sb + (x + b1.z * (y + b1.w * (int)z));
+  o.dfs = b2.x;
+  o.sfs = b2.y;
+  o.nv = b3.x;
   return true;
 }
 
-// persistent grid-stride copy of every position of the box list; each thread
-// keeps two positions' loads in flight before it stores
-template <class T, int DIM> __global__ void __launch_bounds__(256) k_fill_runs(RowArgs a) {
+// persistent grid-stride copy of the chunk list, FILL_CHUNK threads per chunk;
+// each thread keeps two chunks' loads in flight before it stores
+constexpr int FILL_RUN_TPB = 256;
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_RUN_TPB) k_fill_runs(RowArgs a) {
   T* B = (T*)a.fbuf;
-  const long long total = a.nrows * FILL_CHUNK, stride = (long long)gridDim.x * 256;
-  for (long long w = blockIdx.x * 256LL + threadIdx.x; w < total; w += 2 * stride) {
+  const int4* ch = reinterpret_cast<const int4*>(a.chunks);
+  constexpr int G = FILL_RUN_TPB / FILL_CHUNK;
+  const int t = threadIdx.x % FILL_CHUNK;
+  const long long stride = (long long)gridDim.x * G;
+  for (long long c = (long long)blockIdx.x * G + threadIdx.x / FILL_CHUNK; c < a.nrows; c += 2 * stride) {
     FillPos p0, p1;
-    const bool ok0 = fill_pos(a.rows, a.chunks, w, p0);
-    const bool ok1 = w + stride < total && fill_pos(a.rows, a.chunks, w + stride, p1);
+    const bool ok0 = fill_pos(a.rows, ch, c, t, p0);
+    const bool ok1 = c + stride < a.nrows && fill_pos(a.rows, ch, c + stride, t, p1);
+    const T* s0 = B + p0.s;
+    const T* s1 = B + p1.s;
     T v0[6], v1[6];
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
       const int fl = n < 5 ? n : BZ;
-      if (ok0 && n < p0.nv) v0[n] = B[p0.s + fl * p0.sfs];
-      if (ok1 && n < p1.nv) v1[n] = B[p1.s + fl * p1.sfs];
+      if (ok0 && n < p0.nv) v0[n] = s0[fl * p0.sfs];
+      if (ok1 && n < p1.nv) v1[n] = s1[fl * p1.sfs];
     }
+    T* d0 = B + p0.d;
+    T* d1 = B + p1.d;
 #pragma unroll
     for (int n = 0; n < 6; ++n) {
       const int fl = n < 5 ? n : BZ;
-      if (ok0 && n < p0.nv) B[p0.d + fl * p0.dfs] = v0[n];
-      if (ok1 && n < p1.nv) B[p1.d + fl * p1.dfs] = v1[n];
+      if (ok0 && n < p0.nv) d0[fl * p0.dfs] = v0[n];
+      if (ok1 && n < p1.nv) d1[fl * p1.dfs] = v1[n];
     }
   }
 }
@@ -793,15 +807,19 @@ template <class T, int DIM> __global__ void k_restrict_faces(RowArgs a) {
 }
 
 // ------------------------------------------------------------------ CFL
-__device__ __forceinline__ double warp_max(double v) {
+template <class T> __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const T x = __shfl_xor_sync(0xffffffffu, v, o);
+    v = x > v ? x : v;
+  }
   return v;
 }
 
 // per-cell rate sum_d (|v_d| + c_f,d)/dx_d; FP64 path: all FP64 (bitwise with a
 // plain FP64 evaluation); mixed path: the FP64-balanced recovery of
-// recover_t and FP32 fast speeds, the maximum carried in FP64
+// recover_t and FP32 fast speeds, the maximum taken in FP32 (exact) and
+// carried in FP64 across blocks
 // cells per thread of the CFL reduction: one atomic per block of TPB x CFL_CPT
 // cells (a single address takes every block's atomic)
 constexpr int CFL_CPT = 4;
@@ -839,14 +857,15 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
     }
   }
   if (bad) atomicOr(a.err, 1u);
-  double rate = warp_max((double)tmax);
-  __shared__ double red[TPB / 32];
+  // the maximum is exact in the working type; it is widened once per block
+  const T rate = warp_max(tmax);
+  __shared__ T red[TPB / 32];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < TPB / 32 ? red[threadIdx.x] : 0.0;
+    T v = threadIdx.x < TPB / 32 ? red[threadIdx.x] : T(0);
     v = warp_max(v);
-    if (threadIdx.x == 0) atomicMax(a.slot, (unsigned long long)__double_as_longlong(v));
+    if (threadIdx.x == 0) atomicMax(a.slot, (unsigned long long)__double_as_longlong((double)v));
   }
 }
 
@@ -945,9 +964,17 @@ template <class T, int DIM> struct Impl {
 #undef AMRK_BOXES
   static void fill_runs(const RowArgs& a, cudaStream_t s, int* nl) {
     if (!a.nrows) return;
-    const long long items = a.nrows * FILL_CHUNK;
-    const long long blocks = std::min<long long>((items + 511) / 512, 152LL * 8);
-    k_fill_runs<T, DIM><<<(unsigned)blocks, 256, 0, s>>>(a);
+    constexpr int G = FILL_RUN_TPB / FILL_CHUNK;
+    // one wave: the resident blocks of every SM
+    static const long long resident = [] {
+      int dev = 0, sms = 152, per = 4;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fill_runs<T, DIM>, FILL_RUN_TPB, 0);
+      return (long long)sms * (per > 0 ? per : 1);
+    }();
+    const long long blocks = std::min<long long>((a.nrows + 2 * G - 1) / (2 * G), resident);
+    k_fill_runs<T, DIM><<<(unsigned)blocks, FILL_RUN_TPB, 0, s>>>(a);
     if (nl) ++*nl;
   }
 #define AMRK_BOXES(NAME)                                                                \

@@ -21,6 +21,7 @@
 //    mean of both sides when it is exactly 0).
 #pragma once
 #include <cuda_runtime.h>
+#include "fp_bits.cuh"
 
 namespace amrdev {
 
@@ -101,7 +102,9 @@ __device__ __forceinline__ void df_sq(float ah, float al, float& h, float& l) {
 // ke = |m|^2 / (2 rho) and me = |B_c|^2 / 2 formed from the FP32 inputs by
 // error-free FP32 transformations (squares, sums, face means and the division
 // by rho carried as hi + lo pairs, ~2^-46 relative), so that the FP64 pipe
-// only does the final subtraction; v = m / rho and B_c are FP32.
+// only does the final subtraction and the scaling, its operands widened and
+// its result rounded to FP32 (nearest even) on the integer pipe (fp_bits.cuh);
+// v = m / rho and B_c are FP32.
 __device__ __forceinline__ void recover_t(const double* u, const double* bl, const double* br, double gm1, double* w) {
   double bc[3] = {0.5 * (bl[0] + br[0]), 0.5 * (bl[1] + br[1]), 0.5 * (bl[2] + br[2])};
   recover(u, bc, gm1, w);
@@ -134,12 +137,12 @@ __device__ __forceinline__ void recover_t(const float* u, const float* bl, const
   // (ke + me) = 0.5 (kh, kl) + 0.125 (bh, blo): exact power-of-two scalings
   float eh, el;
   df_add(0.5f * kh, 0.5f * kl, 0.125f * bh, 0.125f * blo, eh, el);
-  const double p = gm1 * ((double)u[4] - ((double)eh + (double)el));
+  const double p = gm1 * (widen_bits(u[4]) - (widen_bits(eh) + widen_bits(el)));
   w[0] = r;
   w[1] = u[1] * irf;
   w[2] = u[2] * irf;
   w[3] = u[3] * irf;
-  w[4] = (float)p;
+  w[4] = narrow_bits(p);
   w[5] = 0.5f * (bl[0] + br[0]);
   w[6] = 0.5f * (bl[1] + br[1]);
   w[7] = 0.5f * (bl[2] + br[2]);
