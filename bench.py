@@ -173,20 +173,24 @@ def timed_steps(ctx, stream, k):
 
 
 def advance_alone(ctx, stream, reps):
-    """CUDA-event time of the level advance alone (fill outside the timed
-    brackets), averaged over reps calls on the launching stream."""
+    """CUDA-event times of the level-0 advance and of its ghost fill, each alone
+    on the launching stream, averaged over reps calls: (advance ms, fill ms)."""
     import torch
     dt = ctx.cfl_dt()
-    tot = 0.0
+    tot = tot_f = 0.0
     for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
         ctx.fill_ghosts(0, 1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e[1].record(stream)
+        e[1].synchronize()
+        e[2].record(stream)
         ctx.advance_level(0, dt, 1)
-        e1.record(stream)
-        e1.synchronize()
-        tot += e0.elapsed_time(e1)
-    return tot / reps
+        e[3].record(stream)
+        e[3].synchronize()
+        tot_f += e[0].elapsed_time(e[1])
+        tot += e[2].elapsed_time(e[3])
+    return tot / reps, tot_f / reps
 
 
 def e2e_run(pb, precision, k):
@@ -545,7 +549,7 @@ def main():
 
     # level advance alone, against the HBM roofline (algorithmic bytes: the 8
     # stored fields read and written once per cell update, 16 x 4 B in FP32)
-    t_adv = advance_alone(ctx, stream, 20)
+    t_adv, t_fill = advance_alone(ctx, stream, 20)
     alg_bytes = 16 * 4 * cells_step
     achieved = alg_bytes / (t_adv / 1e3) / 1e9
     arena_gb = ctx.query(A.Q_ARENA_BYTES) / 1e9
@@ -609,7 +613,7 @@ def main():
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
                                        "this kernel on this workload (profiles/k_advance3d_fused_blast3d_128.md)",
                      "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
-                     "ms_per_launch": t_adv},
+                     "ms_per_launch": t_adv, "fill_ms_per_launch": t_fill},
         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
                 "alg_bytes_per_launch": alg_bytes},

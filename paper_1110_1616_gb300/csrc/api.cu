@@ -133,6 +133,7 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   a.fbuf = state_buf(ctx, ctx->cur[l]);
   a.chunks = near ? L.chunk_runs2.p : L.chunk_runs.p;
   a.nrows = near ? L.chunk_runs2.n : L.chunk_runs.n;
+  a.nsplit = near ? L.runs2_split : L.runs_split;
   ctx->ops->fill_runs(a, ctx->stream, nl);
   if (s == 1 && l > 0) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
@@ -644,6 +645,8 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     // of the lane -> (x, row) and row -> (y, z) divisions; chunks (box, x0,
     // q0, nrows) of whole rows q = y + ny z of cx positions
     auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
+      // every listed box has a chunk: a range of k chunks spans at most k boxes
+      if (b[7] <= 0 || b[8] <= 0 || b[9] <= 0) return;
       const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
       const long long Ld = b[4] + (long long)D.ext[0] * (b[5] + (long long)D.ext[1] * b[6]);
       const long long Ls = (b[4] + b[10]) + (long long)S.ext[0] * ((b[5] + b[11]) + (long long)S.ext[1] * (b[6] + b[12]));
@@ -677,6 +680,10 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       chunks_of(ch, bi, b[7] * b[8] * b[9]);
     };
     for (int faces = 0; faces < 2; ++faces) {
+      if (faces) {
+        L.runs_split = (int64_t)cr.size() / 4;
+        L.runs2_split = (int64_t)cr2.size() / 4;
+      }
       const std::vector<int32_t>& gb = faces ? H.ghost_box_faces : H.ghost_box_cells;
       for (size_t r = 0; r < gb.size(); r += amrmhd::GHOST_BOX_W) {
         const int32_t* b = &gb[r];

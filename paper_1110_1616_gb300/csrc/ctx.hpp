@@ -27,6 +27,7 @@ struct LevelDev {
   // physical boundaries (GHOST_BOX_W ints per box, chunks of 2 ints: box,
   // first position)
   DevList runs, chunk_runs;
+  int64_t runs_split = 0, runs2_split = 0;  // chunks of the cell boxes (listed first)
   DevList prol_cells, prol_faces, chunk_pcells, chunk_pfaces;
   DevList bc_cells, bc_faces, chunk_bcells, chunk_bfaces;
   // the same clipped to the ghosts within 2 cells of the interior (all that an

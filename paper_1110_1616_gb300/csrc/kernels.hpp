@@ -62,6 +62,10 @@ struct RowArgs {
   const double* K;
   // box copies: chunk table (box, first cell) per block
   const int* chunks;
+  // same-level box copies: chunks [0, nsplit) are the cell boxes', the rest the
+  // face boxes'; split_blocks = the blocks given to the cells (set at launch)
+  int64_t nsplit;
+  int split_blocks;
   // fine-side registers of the fused path: the boundary capture buffer the fine
   // level's advance wrote (nullptr: recompute the fluxes and EMFs)
   const void* bnd;

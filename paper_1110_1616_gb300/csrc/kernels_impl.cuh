@@ -341,9 +341,8 @@ struct FillPos {
   long long d, s;
   int dfs, sfs, nv;
 };
-__device__ __forceinline__ bool fill_pos(const int* boxes, const int4* chunks, long long c, int t, FillPos& o) {
-  const int4 cr = chunks[c];
-  const int4* br = reinterpret_cast<const int4*>(boxes + FILL_BOX_W * (long long)cr.x);
+// position t of chunk record cr, box record br (4 int4)
+__device__ __forceinline__ bool fill_pos(const int4 cr, const int4* br, int t, FillPos& o) {
   const int4 b2 = br[2], b3 = br[3];  // (dfs, sfs, nx, ny), (nv, cx, mcx, mny)
   const unsigned r = __umulhi(2u * (unsigned)t, (unsigned)b3.z);
   const int x = cr.y + t - (int)r * b3.y;
@@ -362,37 +361,71 @@ __device__ __forceinline__ bool fill_pos(const int* boxes, const int4* chunks, l
   return true;
 }
 
-// persistent grid-stride copy of the chunk list, FILL_CHUNK threads per chunk;
-// each thread keeps two chunks' loads in flight before it stores
-constexpr int FILL_RUN_TPB = 256;
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_RUN_TPB) k_fill_runs(RowArgs a) {
-  T* B = (T*)a.fbuf;
-  const int4* ch = reinterpret_cast<const int4*>(a.chunks);
+// Each block copies a contiguous range of the chunk list, FILL_CHUNK threads
+// per chunk, in tiles of FILL_TILE chunks whose chunk and box records are
+// first staged in shared memory (a range of chunks spans at most as many
+// boxes, the list being ordered by box), so that the only global loads of the
+// copy loop are the copied values themselves. Each thread loads U chunks'
+// positions (NV fields each) before it stores, so that the face boxes (one
+// field) keep as many loads in flight as the cell boxes.
+constexpr int FILL_RUN_TPB = 256, FILL_TILE = 256;
+constexpr size_t FILL_SMEM = (size_t)FILL_TILE * 5 * sizeof(int4);
+template <class T, int NV, int U>
+__device__ __forceinline__ void fill_range(T* B, const int* boxes, const int4* ch, long long c0, long long c1,
+                                           int4* sch, int4* sbox) {
   constexpr int G = FILL_RUN_TPB / FILL_CHUNK;
-  const int t = threadIdx.x % FILL_CHUNK;
-  const long long stride = (long long)gridDim.x * G;
-  for (long long c = (long long)blockIdx.x * G + threadIdx.x / FILL_CHUNK; c < a.nrows; c += 2 * stride) {
-    FillPos p0, p1;
-    const bool ok0 = fill_pos(a.rows, ch, c, t, p0);
-    const bool ok1 = c + stride < a.nrows && fill_pos(a.rows, ch, c + stride, t, p1);
-    const T* s0 = B + p0.s;
-    const T* s1 = B + p1.s;
-    T v0[6], v1[6];
+  const int t = threadIdx.x % FILL_CHUNK, g = threadIdx.x / FILL_CHUNK;
+  for (long long t0 = c0; t0 < c1; t0 += FILL_TILE) {
+    const int nt = (int)(c1 - t0 < FILL_TILE ? c1 - t0 : FILL_TILE);
+    const int box0 = ch[t0].x, nbox = ch[t0 + nt - 1].x - box0 + 1;
+    __syncthreads();  // the previous tile's records are no longer read
+    for (int i = threadIdx.x; i < nt; i += FILL_RUN_TPB) sch[i] = ch[t0 + i];
+    const int4* gb = reinterpret_cast<const int4*>(boxes) + 4LL * box0;
+    for (int i = threadIdx.x; i < 4 * nbox; i += FILL_RUN_TPB) sbox[i] = gb[i];
+    __syncthreads();
+    for (int c = g; c < nt; c += U * G) {
+      FillPos p[U];
+      bool ok[U];
 #pragma unroll
-    for (int n = 0; n < 6; ++n) {
-      const int fl = n < 5 ? n : BZ;
-      if (ok0 && n < p0.nv) v0[n] = s0[fl * p0.sfs];
-      if (ok1 && n < p1.nv) v1[n] = s1[fl * p1.sfs];
-    }
-    T* d0 = B + p0.d;
-    T* d1 = B + p1.d;
+      for (int u = 0; u < U; ++u) {
+        const int cc = c + u * G;
+        ok[u] = false;
+        if (cc < nt) {
+          const int4 cr = sch[cc];
+          ok[u] = fill_pos(cr, sbox + 4 * (cr.x - box0), t, p[u]);
+        }
+      }
+      T v[U][NV];
 #pragma unroll
-    for (int n = 0; n < 6; ++n) {
-      const int fl = n < 5 ? n : BZ;
-      if (ok0 && n < p0.nv) d0[fl * p0.dfs] = v0[n];
-      if (ok1 && n < p1.nv) d1[fl * p1.dfs] = v1[n];
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+          if (ok[u]) v[u][n] = B[p[u].s + (NV == 1 ? 0 : (n < 5 ? n : BZ)) * p[u].sfs];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int n = 0; n < NV; ++n)
+          if (ok[u]) B[p[u].d + (NV == 1 ? 0 : (n < 5 ? n : BZ)) * p[u].dfs] = v[u][n];
     }
   }
+}
+// the cell boxes' chunks come first in the list (nsplit of them), then the
+// face boxes'; the first split_blocks blocks share the cells' chunks in equal
+// contiguous ranges, the rest the faces'
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_RUN_TPB) k_fill_runs(RowArgs a) {
+  extern __shared__ int4 fill_smem[];
+  int4* sch = fill_smem;
+  int4* sbox = fill_smem + FILL_TILE;
+  T* B = (T*)a.fbuf;
+  const int4* ch = reinterpret_cast<const int4*>(a.chunks);
+  const bool cells = (int)blockIdx.x < a.split_blocks;
+  const long long lo = cells ? 0 : a.nsplit, n = cells ? a.nsplit : a.nrows - a.nsplit;
+  const long long nb = cells ? a.split_blocks : (long long)gridDim.x - a.split_blocks;
+  const long long b = cells ? blockIdx.x : blockIdx.x - a.split_blocks;
+  const long long c0 = lo + n * b / nb, c1 = lo + n * (b + 1) / nb;
+  if (c0 >= c1) return;
+  if (cells) fill_range<T, DIM == 3 ? 5 : 6, 2>(B, a.rows, ch, c0, c1, sch, sbox);
+  else fill_range<T, 1, 4>(B, a.rows, ch, c0, c1, sch, sbox);
 }
 
 // Prolongation and physical-boundary fills as ghost boxes of GHOST_BOX_W
@@ -964,17 +997,26 @@ template <class T, int DIM> struct Impl {
 #undef AMRK_BOXES
   static void fill_runs(const RowArgs& a, cudaStream_t s, int* nl) {
     if (!a.nrows) return;
-    constexpr int G = FILL_RUN_TPB / FILL_CHUNK;
     // one wave: the resident blocks of every SM
     static const long long resident = [] {
       int dev = 0, sms = 152, per = 4;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fill_runs<T, DIM>, FILL_RUN_TPB, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fill_runs<T, DIM>, FILL_RUN_TPB, FILL_SMEM);
       return (long long)sms * (per > 0 ? per : 1);
     }();
-    const long long blocks = std::min<long long>((a.nrows + 2 * G - 1) / (2 * G), resident);
-    k_fill_runs<T, DIM><<<(unsigned)blocks, FILL_RUN_TPB, 0, s>>>(a);
+    // blocks shared between the cell and face chunks by their element counts,
+    // at least 2 x FILL_CHUNK / 4 chunks per block
+    const long long nc = a.nsplit, nf = a.nrows - a.nsplit;
+    const double wc = (double)nc * (DIM == 3 ? 5 : 6), wf = (double)nf;
+    const long long need_c = (nc + 31) / 32, need_f = (nf + 31) / 32;
+    long long bc = std::min(need_c, (long long)(resident * wc / (wc + wf) + 0.5));
+    long long bf = std::min(need_f, resident - bc);
+    if (nc > 0 && bc < 1) bc = 1;
+    if (nf > 0 && bf < 1) bf = 1;
+    RowArgs b = a;
+    b.split_blocks = (int)bc;
+    k_fill_runs<T, DIM><<<(unsigned)(bc + bf), FILL_RUN_TPB, FILL_SMEM, s>>>(b);
     if (nl) ++*nl;
   }
 #define AMRK_BOXES(NAME)                                                                \
