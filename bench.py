@@ -34,7 +34,7 @@ FLOPS_PER_CELL_UPDATE_3D = 1504.0
 # DRAM bytes (read + write) of one launch of the fused advance on the 128^3
 # blast in 16^3 patches, mixed precision, from one ncu capture of that launch
 # (224.92 MB read + 75.82 MB written; profiles/k_advance3d_fused_blast3d_128.md)
-FUSED_TRAFFIC_BYTES = 300.65e6  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)
+FUSED_TRAFFIC_BYTES = 300.44e6  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)
 # FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock
 SMS, FP32_LANES = 152, 128
 
