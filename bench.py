@@ -34,6 +34,7 @@ FLOPS_PER_CELL_UPDATE_3D = 1504.0
 # DRAM bytes (read + write) of one launch of the fused advance on the 128^3
 # blast in 16^3 patches, mixed precision, from one ncu capture of that launch
 # (224.92 MB read + 75.82 MB written; profiles/k_advance3d_fused_blast3d_128.md)
+TILE_NAMES = {0: "16x16", 1: "16x16/512 threads", 2: "16x8", 3: "8x8", 4: "12x12"}
 FUSED_TRAFFIC_BYTES = 300.44e6  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)
 # FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock
 SMS, FP32_LANES = 152, 128
@@ -203,6 +204,7 @@ def e2e_run(pb, precision, k):
     import ctypes as C
     from paper_1110_1616_gb300 import amrmhd as A
     ctx, stream = make_ctx(pb, precision)
+    ctx.autotune(3)
     f32 = precision == A.MIXED
     host = np.concatenate([ctx.pack(pb.state, f) for f in range(8)])
     host_in = torch.from_numpy(host.astype(np.float32) if f32 else host).pin_memory()
@@ -537,9 +539,10 @@ def main():
     pk = peaks()
     hbm_peak = pk.get("hbm_gbs", 6800.0)
 
+    ctx, stream = make_ctx(pb, A.MIXED)
+    tile = ctx.autotune(3)[0]  # the library's autotuner picks the fused tile (state unchanged)
     clocks = Clocks(local)
     clocks.start()
-    ctx, stream = make_ctx(pb, A.MIXED)
     ctx.step(args.warmup, want_dt=False)
     torch.cuda.synchronize()
     barrier(world)
@@ -605,11 +608,13 @@ def main():
                    "cells": args.n ** 3, "patches": (args.n // args.psize) ** 3, "precision": "mixed",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (arena %.2f GB: ping-pong state and stage scratch)" % arena_gb},
-        "roofline": {"bound": "alu", "kernel": "k_advance3d_fused<float,16x8> (one launch per level advance)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_advance3d_fused<float,%s> (one launch per level advance, autotuned tile)"
+                               % TILE_NAMES.get(tile, str(tile)),
                      "achieved": flops_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": flops_achieved / fp32_peak,
                      "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (SMS, FP32_LANES, sm_max),
-                     "traffic": FUSED_TRAFFIC_BYTES if args.n == 128 and args.psize == 16 else None,
+                     "traffic": FUSED_TRAFFIC_BYTES if args.n == 128 and args.psize == 16 and tile == 2 else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
                                        "this kernel on this workload (profiles/k_advance3d_fused_blast3d_128.md)",
                      "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
