@@ -344,10 +344,14 @@ enum {
                               sub-step kind after amrmhd_autotune, else 16x8 FP32, 8x8 FP64), 0: 16x16
                               tile with 256 threads, 1: 16x16 / 512, 2: 16x8 / 256, 3: 8x8 / 256,
                               4: 12x12 / 256 */
-  AMRMHD_OPT_CONCURRENT = 3 /* 1 (default): in a coarse step the two sub-steps of level l+1 run on a
+  AMRMHD_OPT_CONCURRENT = 3, /* 1 (default): in a coarse step the two sub-steps of level l+1 run on a
                               side stream concurrently with the advance of level l (they meet
                               before the reflux), and the CFL reduction runs beside the level-0
                               ghost fill; 0: one stream, strictly in the recursive order */
+  AMRMHD_OPT_HOST_IO = 4    /* whole-state I/O with host buffers (amrmhd_set/get_state_all*): 0 (default):
+                              page-locked buffers are read and written in place by the packing kernels
+                              over the host link, other host memory through a device staging buffer;
+                              1: every host buffer through the staging buffer (copy engine) */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

@@ -447,6 +447,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 4) ctx->opt_tile = value;
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
+  else if (option == AMRMHD_OPT_HOST_IO && (value == 0 || value == 1)) ctx->opt_host_io = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -854,7 +855,8 @@ static amrmhd_status io_all(amrmhd_ctx* ctx, void* buf, int32_t on_device, int t
     // kernels read or write it directly over the host link (one pass, no
     // staging copy); other host memory goes through a device staging buffer
     cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, buf) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+    if (ctx->opt_host_io == 0 && cudaPointerGetAttributes(&pa, buf) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
       dev = pa.devicePointer;
       mapped = true;
     } else {

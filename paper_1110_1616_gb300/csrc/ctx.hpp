@@ -59,7 +59,7 @@ struct amrmhd_ctx {
   int stage_ghost_from = 0;
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
-  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1;
+  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1, opt_host_io = 0;
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;

@@ -395,16 +395,18 @@ def test_whole_state_io_page_locked_host_memory(precision):
     assert np.array_equal(back, expect)
 
 
-@pytest.mark.parametrize("pinned", [False, True])
-def test_whole_state_io_float_elements(pinned):
+@pytest.mark.parametrize("pinned,staged", [(False, 0), (True, 0), (True, 1)])
+def test_whole_state_io_float_elements(pinned, staged):
     """amrmhd_set_state_all_f32 / get_state_all_f32 move the stored FP32 values
     of a mixed-precision context unchanged (page-locked or ordinary host
-    memory), and round / widen those of an FP64 context."""
+    memory, in place or through the staging buffer), and round / widen those
+    of an FP64 context."""
     import ctypes as C
     import torch
     pb = inputs.orszag_tang(32, 8, refine=True)
     for precision in (A.MIXED, A.FP64):
         ctx = gpu_for(pb, precision)
+        ctx.set_option(A.OPT_HOST_IO, staged)
         ref = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
         buf = torch.empty(ref.size, dtype=torch.float32)
         if pinned:
