@@ -59,6 +59,23 @@ def test_ot_amr_fp64_config1_full():
     assert max_err(res) <= 1e-12, res
 
 
+@pytest.mark.parametrize("case", ["ot2d_one_128_patch", "ot2d_amr_64_patches", "blast3d_one_64_patch"])
+def test_wide_patches(case):
+    """Patches wider than a fill chunk (64 positions): ghost rows of more than
+    64 cells are split into several chunks along x, and a single periodic patch
+    is its own neighbour on every side. FP64 strict against the oracle."""
+    if case == "ot2d_one_128_patch":
+        pb, n = inputs.orszag_tang(128, 128, refine=False), 10
+    elif case == "ot2d_amr_64_patches":
+        pb, n = inputs.orszag_tang(128, 64, refine=True), 4
+    else:
+        pb, n = inputs.blast_3d(64, 64), 3
+    ctx, dts, o, odts = run_both(pb, n)
+    assert np.array_equal(dts, odts)
+    res = compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb)
+    assert max_err(res) <= 1e-12, res
+
+
 def test_blast3d_fp64_reduced():
     """3D blast (config-2 physics) at 32^3 in 16^3 patches, 30 steps, FP64."""
     pb = inputs.blast_3d(32, 16)
