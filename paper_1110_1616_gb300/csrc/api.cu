@@ -702,6 +702,17 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
         }
       }
     }
+    // k_fill_runs stages a block's chunk and box records in shared memory and
+    // relies on k chunks spanning at most k boxes: every box listed once, in
+    // order, each followed by its own chunks
+    for (const std::vector<int32_t>* chl : {&cr, &cr2}) {
+      int32_t prev = -1;
+      for (size_t i = 0; i < chl->size(); i += 4) {
+        const int32_t b = (*chl)[i];
+        if (b != prev && b != prev + 1) return fail(ctx, AMRMHD_EINVAL, "internal: same-level fill list out of order");
+        prev = b;
+      }
+    }
     const int GW = amrmhd::GHOST_BOX_W;
     bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 4) &&
               upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
