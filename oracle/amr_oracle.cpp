@@ -86,7 +86,12 @@ template <class R> struct SimT {
   int flags = 0;  // test-only switches: bit 0 skips the cell reflux (a planted
                   // mistake); bit 1 replaces minmod by the unlimited centred slope;
                   // bit 2 plants an off-by-one in the high-side boundary faces;
-                  // bit 3 skips the divergence-free closure of the regrid
+                  // bit 3 skips the divergence-free closure of the regrid;
+                  // bits 4-6 plant mistakes in the half-step predictor (controls
+                  // of its pins): bit 4 p div v for gamma p div v in the pressure
+                  // row; bit 5 the sign of the B_t dv_z/dz terms of the induction
+                  // rows flipped; bit 6 the dp/dz term of the z-momentum row
+                  // dropped (bits 5 and 6 touch the z direction only)
 };
 
 // ---------------------------------------------------------------- indexing
@@ -348,6 +353,12 @@ template <class R> static void advance_masked(SimT<R>& S, LevelT<R>& L, double d
     for (int d = 0; d < dim; ++d) {
       R dw[8];
       prim_rhs<R>(w, s[d], d, R(gamma), ir, dw);
+      if (S.flags & 16) dw[4] = dw[4] - R(gamma - 1.0) * w[4] * s[d][1 + d];  // planted mistake (control)
+      if ((S.flags & 32) && d == 2) {                                          // planted mistake (control)
+        dw[5 + 0] = dw[5 + 0] - R(2.0) * w[5 + 0] * s[d][1 + d];
+        dw[5 + 1] = dw[5 + 1] - R(2.0) * w[5 + 1] * s[d][1 + d];
+      }
+      if ((S.flags & 64) && d == 2) dw[1 + d] = dw[1 + d] - s[d][4] * ir;     // planted mistake (control)
       for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h[d] * dw[f];
     }
     for (int f = 0; f < 8; ++f) L.Wh[f][q] = wh[f];
@@ -1495,6 +1506,11 @@ void oc_flux(const double* q, double bn, double gamma, double* f) {
   mhd_flux(q, bn, 1.0 / (gamma - 1.0), f, u);
 }
 double oc_minmod(double a, double b) { return minmod(a, b); }
+// a3: conservative -> primitive recovery of one cell, u = (rho, mx, my, mz, E),
+// bc = cell-centred B; w = (rho, vx, vy, vz, p, Bx, By, Bz)
+void oc_recover(const double* u, const double* bc, double gamma, double* w) {
+  cons_to_prim<double>(u, bc, gamma - 1.0, w);
+}
 double oc_fast_speed(double rho, double p, double bn, double bt, double bu, double gamma) {
   return fast_speed(rho, p, bn, bt, bu, gamma);
 }

@@ -45,6 +45,7 @@ def lib():
         L.oc_predict.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp]
         L.oc_predict_vjp.argtypes = [C.c_int, _dp, C.c_double, _dp, _dp, _dp]
         L.oc_flux.argtypes = [_dp, C.c_double, C.c_double, _dp]
+        L.oc_recover.argtypes = [_dp, _dp, C.c_double, _dp]
         L.oc_minmod.restype = C.c_double
         L.oc_minmod.argtypes = [C.c_double, C.c_double]
         L.oc_fast_speed.restype = C.c_double
@@ -285,6 +286,15 @@ def mhd_flux(q, bn, gamma=5.0 / 3.0):
     f = np.zeros(7)
     lib().oc_flux(np.asarray(q, dtype=np.float64), bn, gamma, f)
     return f
+
+
+def recover(u, bc, gamma=5.0 / 3.0):
+    """Conservative -> primitive recovery of one cell: u = (rho, mx, my, mz, E),
+    bc = cell-centred B; returns (rho, vx, vy, vz, p, Bx, By, Bz)."""
+    w = np.zeros(8)
+    lib().oc_recover(np.ascontiguousarray(u, dtype=np.float64), np.ascontiguousarray(bc, dtype=np.float64),
+                     float(gamma), w)
+    return w
 
 
 def minmod(a, b):

@@ -185,6 +185,127 @@ def alfven_2d_state(n, amp, t=0.0, gamma=GAMMA):
     return _state_2d((n, n, 1), rho, vx, vy, vz, p, bx, by, bz, gamma)
 
 
+def mhd_wave_mode(family, rho, p, b, khat, v0=(0.0, 0.0, 0.0), sign=1, gamma=GAMMA):
+    """Right eigenvector of the linearised ideal-MHD equations in primitive
+    variables W = (rho, vx, vy, vz, p, Bx, By, Bz) for a plane wave along the
+    unit vector khat through the uniform state (rho, v0, p, b): family
+    'fast', 'slow', 'alfven' or 'entropy'; sign +1 or -1 for the wave moving
+    along +khat or -khat relative to the flow. Returns (lam, r) with lam =
+    khat.v0 + sign c the characteristic speed (c the family's phase speed):
+    W + a r cos(k.x - |k| lam t) solves the linearised equations.
+
+    Closed forms (a^2 = gamma p / rho, b_n = b.khat, b_t the rest of b, t its
+    direction, u = khat x t): fast / slow c^2 = ((a^2 + |b|^2/rho) +- sqrt((a^2 +
+    |b|^2/rho)^2 - 4 a^2 b_n^2 / rho)) / 2, with dv_n = 1, drho = rho / c',
+    dp = gamma p / c', dv_t = -b_n |b_t| / (rho c'^2 - b_n^2), dB_t = rho c' |b_t| /
+    (rho c'^2 - b_n^2) (c' = sign c); Alfven c = |b_n| / sqrt(rho), dv_u = 1,
+    dB_u = -b_n / c'; entropy c = 0, drho = 1. Needs b_t != 0 for the
+    magnetosonic and Alfven families."""
+    n = np.asarray(khat, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    bv = np.asarray(b, dtype=np.float64)
+    v0 = np.asarray(v0, dtype=np.float64)
+    bn = float(bv @ n)
+    bt_vec = bv - bn * n
+    bt = float(np.linalg.norm(bt_vec))
+    r = np.zeros(8)
+    if family == "entropy":
+        r[0] = 1.0
+        return float(n @ v0), r
+    if bt == 0.0:
+        raise ValueError("field along the wave vector: degenerate eigenvectors")
+    t = bt_vec / bt
+    u = np.cross(n, t)
+    if family == "alfven":
+        c = sign * abs(bn) / math.sqrt(rho)
+        r[1:4] = u
+        r[5:8] = -bn / c * u
+        return float(n @ v0) + c, r
+    a2 = gamma * p / rho
+    s2 = a2 + (bv @ bv) / rho
+    disc = math.sqrt(s2 * s2 - 4.0 * a2 * bn * bn / rho)
+    c2 = 0.5 * (s2 + disc) if family == "fast" else 0.5 * (s2 - disc)
+    c = sign * math.sqrt(c2)
+    den = rho * c * c - bn * bn
+    r[0] = rho / c
+    r[1:4] = n - (bn * bt / den) * t
+    r[4] = gamma * p / c
+    r[5:8] = (rho * c * bt / den) * t
+    return float(n @ v0) + c, r
+
+
+def mhd_wave(dim, n, family, amp=1e-6, t=0.0, k=(1, 1, 1), rho=1.0, p=None, b=(0.9, 0.45, 0.3),
+             v0=(0.0, 0.0, 0.0), sign=1, psize=16, gamma=GAMMA):
+    """Linear MHD wave of one family (mhd_wave_mode) on periodic [0,1]^dim,
+    n^dim cells in psize^dim patches, wave vector 2 pi k (integers; k_z = 0 in
+    2D): the exact solution of the linearised equations at time t, W(x) =
+    W0 + amp r cos(2 pi k.x - omega t), omega = 2 pi |k| lam. Cell fields are
+    point values at the cell centres; face B is the uniform b plus the
+    discrete curl of the vector potential amp (r_B x K) / |K|^2 sin(phase)
+    (K = 2 pi k) sampled at edge midpoints (corners in 2D), so it is
+    divergence-free to round-off; in 2D Bz is a cell field. p defaults to
+    1/gamma (sound speed 1)."""
+    if p is None:
+        p = 1.0 / gamma
+    kk = np.array([k[d] if d < dim else 0 for d in range(3)], dtype=np.float64)
+    K = 2.0 * math.pi * kk
+    kn = float(np.linalg.norm(K))
+    lam, r = mhd_wave_mode(family, rho, p, b, K / kn, v0, sign, gamma)
+    omega = kn * lam
+    nn = tuple(n if d < dim else 1 for d in range(3))
+    dx = 1.0 / n
+    x, y, z = _cell_centres(nn, (0, 0, 0), (1, 1, 1), dim)
+    ph = K[0] * x + K[1] * y + K[2] * z - omega * t
+    cph = np.cos(ph)
+    rho_a = rho + amp * r[0] * cph
+    v = [v0[c] + amp * r[1 + c] * cph for c in range(3)]
+    p_a = p + amp * r[4] * cph
+    avec = amp * np.cross(r[5:8], K) / (kn * kn)  # vector potential amplitude
+    if dim == 2:
+        xc = np.arange(n + 1) * dx
+        Y, X = np.meshgrid(xc, xc, indexing="ij")
+        az = avec[2] * np.sin(K[0] * X + K[1] * Y - omega * t)
+        bx, by = _b_from_az_2d(az, nn, dx, dx)
+        bx = bx + b[0]
+        by = by + b[1]
+        bz = b[2] + amp * r[7] * cph
+        patches = tile(0, (0, 0, 0), nn, psize, 2)
+        st = _state_2d(nn, rho_a, v[0], v[1], v[2], p_a, bx, by, bz, gamma)
+        return Problem("mhd_wave_%s_2d" % family, 2, nn, patches, 1, {0: st}, gamma=gamma,
+                       meta={"amp": amp, "lam": lam, "omega": omega, "r": r})
+    ii = np.arange(n + 1)
+    ic = (np.arange(n) + 0.5) * dx  # centres
+    ie = ii * dx                    # low edges / faces (n + 1 entries)
+
+    def A(c, X, Y, Z):
+        return avec[c] * np.sin(K[0] * X + K[1] * Y + K[2] * Z - omega * t)
+
+    # A_x on x-edges (x centre; y, z low corners), A_y on y-edges, A_z on z-edges;
+    # arrays indexed [z, y, x] with n + 1 entries along the corner directions
+    Zx, Yx, Xx = np.meshgrid(ie, ie, ic, indexing="ij")
+    Ax = A(0, Xx, Yx, Zx)                         # (n+1, n+1, n)
+    Zy, Yy, Xy = np.meshgrid(ie, ic, ie, indexing="ij")
+    Ay = A(1, Xy, Yy, Zy)                         # (n+1, n, n+1)
+    Zz, Yz, Xz = np.meshgrid(ic, ie, ie, indexing="ij")
+    Az = A(2, Xz, Yz, Zz)                         # (n, n+1, n+1)
+    bx = (Az[:, 1:, :] - Az[:, :-1, :]) / dx - (Ay[1:, :, :] - Ay[:-1, :, :]) / dx   # (n, n, n+1)
+    by = (Ax[1:, :, :] - Ax[:-1, :, :]) / dx - (Az[:, :, 1:] - Az[:, :, :-1]) / dx   # (n, n+1, n)
+    bz = (Ay[:, :, 1:] - Ay[:, :, :-1]) / dx - (Ax[:, 1:, :] - Ax[:, :-1, :]) / dx   # (n+1, n, n)
+    bx = bx + b[0]
+    by = by + b[1]
+    bz = bz + b[2]
+    # the periodic copies (entry n along the normal) equal entry 0 exactly
+    bx[:, :, -1] = bx[:, :, 0]
+    by[:, -1, :] = by[:, 0, :]
+    bz[-1, :, :] = bz[0, :, :]
+    bcx, bcy, bcz = _cell_b_from_faces(bx, by, bz, 3)
+    e = _energy(rho_a, v[0], v[1], v[2], p_a, bcx, bcy, bcz, gamma)
+    st = [rho_a, rho_a * v[0], rho_a * v[1], rho_a * v[2], e, bx, by, bz]
+    patches = tile(0, (0, 0, 0), nn, psize, 3)
+    return Problem("mhd_wave_%s_3d" % family, 3, nn, patches, 1, {0: st}, gamma=gamma,
+                   meta={"amp": amp, "lam": lam, "omega": omega, "r": r})
+
+
 def blast_3d(n=128, psize=16, gamma=GAMMA):
     """3D blast wave on periodic [0,1]^3: rho = 1, p = 0.1, p = 10 for cell
     centres with r^2 < 0.01 around (1/2,1/2,1/2), v = 0, uniform
@@ -715,6 +836,29 @@ def packed_shock_clump(pb, patches=None, field=None):
             sh[d] += 1
             out[5 + d].append(np.full(int(np.prod(sh)), val))
     return [np.concatenate(a) for a in out]
+
+
+def shock_clump_3d_small(base=16, nlev=3, fft_n=64, **kw):
+    """The shock-clump workload down-scaled for parity tests (16^3 base, 3
+    levels by default) with whole-level arrays on every level: the same state
+    as shock_clump_3d / packed_shock_clump, each level generated as one box
+    over its whole domain."""
+    pb = shock_clump_3d(base=base, nlev=nlev, fft_n=fft_n, **kw)
+    g = fractal_field(fft_n, seed=pb.meta["seed"])
+    state = {}
+    for l in range(nlev):
+        n = [base << l] * 3
+        whole = [(l, (0, 0, 0), tuple(n))]
+        packed = packed_shock_clump(pb, patches=whole, field=g)
+        arrs = []
+        for f in range(8):
+            shp = [n[2], n[1], n[0]]
+            if f >= 5:
+                shp[2 - (f - 5)] += 1
+            arrs.append(packed[f].reshape(shp))
+        state[l] = arrs
+    pb.state = state
+    return pb
 
 
 def random_hierarchy(dim, seed, base=32, psize0=16, nlev=2, max_tries=200):
