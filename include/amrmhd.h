@@ -86,13 +86,17 @@ typedef struct {
   int32_t hi[3];
 } amrmhd_patch;
 
-/* Creates a context. cfg is copied. cuda_stream: the cudaStream_t all work of
+/* Creates a context: one AMR mesh of Sec. 2 (levels of grids, refinement ratio
+ * R = 2). The paper names the hyperbolic advance but neither its equations nor
+ * its boundary kinds: ideal MHD with the ratio of specific heats cfg.gamma and
+ * the per-side boundary kinds above are this library's readings. cfg is copied. cuda_stream: the cudaStream_t all work of
  * the context is ordered on; NULL makes the library create its own
  * non-blocking stream at bind_arena (the legacy default stream cannot be
  * captured into a CUDA graph). No device call is made until bind_arena. */
 amrmhd_status amrmhd_create(const amrmhd_config* cfg, void* cuda_stream, amrmhd_ctx** out);
 
-/* Destroys a context and frees library-owned memory (not the arena). */
+/* Destroys a context and frees library-owned memory (not the arena). The paper
+ * is silent (a resource call of this library). */
 amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx);
 
 /* Installs a hierarchy (patches copied). Validates: boxes inside the level
@@ -106,10 +110,15 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
                                    size_t* arena_bytes);
 
 /* Binds caller-owned device memory of at least arena_bytes bytes (256-byte
- * aligned) and uploads the maps. Must follow set_hierarchy. */
+ * aligned) and uploads the maps. Must follow set_hierarchy. The paper is silent
+ * on memory layout (its grids live in per-processor arrays); this library's
+ * reading is the arena layout above: patches in (level, id) order, 8 fields per
+ * patch over its ghosted box. */
 amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes);
 
-/* Copies one field of one patch in or out of the current state buffer.
+/* Copies one field of one patch in or out of the current state buffer. The
+ * paper is silent on I/O; the fields are the scheme's conserved variables
+ * (rho, m, E cell-centred; B on faces for constrained transport).
  * Values are double. Layout: the patch's interior, x fastest: cell fields
  * n_z x n_y x n_x; the face field along d has n_d + 1 entries along d (both
  * boundary faces). src/dst is device memory if *_on_device is 1, else host
@@ -143,7 +152,12 @@ amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_devi
 amrmhd_status amrmhd_set_state_all_f32(amrmhd_ctx* ctx, const float* src, int32_t on_device);
 amrmhd_status amrmhd_get_state_all_f32(amrmhd_ctx* ctx, float* dst, int32_t on_device);
 
-/* Exports integer map `which` (AMRMHD_MAP_*) as rows of int32; *width receives
+/* Integer parity export. The neighbour rows are the connections Sec. 2 calls
+ * neighbors, built by the inheritance of Sec. 3.1; the paper is silent on every
+ * row format, and the canonical layout below (ghosts in z,y,x order, sources
+ * by smallest (id, index), local indices into the ghosted box) is this
+ * library's reading.
+ * Exports integer map `which` (AMRMHD_MAP_*) as rows of int32; *width receives
  * the row width, *len the total int count; up to cap ints are written to dst
  * (host memory; dst may be NULL to query the size). Host-only. Row formats:
  *  NEIGHBORS      (p, q, sx, sy, sz): same-level q, periodic shift s, whose
@@ -185,7 +199,12 @@ amrmhd_status amrmhd_export_map(amrmhd_ctx* ctx, int32_t which, int32_t* dst, in
  * evolved by substep 1: extended ghost zones, Abstract and Sec. 1). */
 amrmhd_status amrmhd_fill_ghosts(amrmhd_ctx* ctx, int32_t level, int32_t substep);
 
-/* Advances every patch of `level` by dt (MUSCL-Hancock + minmod, HLLD, CT).
+/* The (A)dvance of Sec. 4 for every grid of `level`: the hyperbolic advance of
+ * each grid decoupled by its ghost zones (Abstract, Sec. 1). The paper does not
+ * give the scheme; this library's reading is MUSCL-Hancock with the primitive
+ * half-step predictor and minmod slopes, HLLD fluxes (Miyoshi & Kusano 2005)
+ * and constrained transport with Gardiner-Stone edge EMFs.
+ * Advances every patch of `level` by dt.
  * Level 0 updates the interior; above level 0, substep 1 updates the interior
  * plus 2 ghost layers and substep 2 the interior. Records the coarse-side
  * registers of the next finer level's C/F boundary and the fine-side registers
@@ -199,12 +218,18 @@ amrmhd_status amrmhd_advance_level(amrmhd_ctx* ctx, int32_t level, double dt, in
  * fine_level after advance_level(fine_level-1). */
 amrmhd_status amrmhd_reflux_restrict(amrmhd_ctx* ctx, int32_t fine_level);
 
-/* dt0 = cfl / max_l (2^-l max over level-l cells of sum_d (|v_d| + c_f,d)/dx_d),
+/* Time step of the coarse step. The paper is silent on the time step; this
+ * library's reading is the sum-form rate and one global dt0 per coarse step:
+ * dt0 = cfl / max_l (2^-l max over level-l cells of sum_d (|v_d| + c_f,d)/dx_d),
  * computed on the device in FP64; synchronises the stream.
  * AMRMHD_ENONPHYS if a density or pressure is not finite and positive. */
 amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0);
 
-/* n_coarse full coarse steps (CFL dt each, then the whole recursion), run as a
+/* n_coarse full coarse steps (CFL dt each, then the whole recursion of Sec. 4:
+ * level order 0,1,2,2,1,2,2 with P, O, A, S, R per level; finer levels advance
+ * concurrently with the coarser advance, Sec. 4's threads; the paper does
+ * not fix the ghost refresh: here fine ghosts are prolonged once per parent step
+ * and self-evolved, same-level ghosts refreshed every sub-step), run as a
  * captured CUDA graph. dt_used (host, may be NULL) receives the n_coarse dt0
  * values. Synchronises the stream at the end and reports device errors. */
 amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used);
@@ -216,7 +241,9 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used);
 amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq);
 
 /* Discrete adjoint of n_coarse coarse steps with the dt0 sequence dt_seq (host;
- * dt is a constant of the map, not differentiated). The paper's level advance
+ * dt is a constant of the map, not differentiated). The paper has no adjoint;
+ * the conventions here (dt fixed, the forward's branch at every kink, one entry
+ * per stored copy) are this library's. The level advance
  * (Sec. 4: prolongation, advance, reflux and restriction of the recursive
  * level order) is differentiated exactly: the call returns
  *   dL_dU0 = (dU_final / dU0)^T dL_dUfinal
@@ -246,8 +273,9 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
 /* The local transposed Jacobians that amrmhd_backward applies at every face
  * and cell, exposed for verification: gx = J^T g at n points, FP64, one point
  * per row, all arrays HOST, row-major.
- *  which 0: the HLLD flux (Sec. 4's hyperbolic advance; Miyoshi-Kusano) of a
- *           rotated face, x = (rho, u_n, u_t, u_u, p, B_t, B_u) of the left
+ *  which 0: the HLLD flux (the scheme's Riemann solver, Miyoshi & Kusano
+ *           2005; the paper names no solver)
+ *           of a rotated face, x = (rho, u_n, u_t, u_u, p, B_t, B_u) of the left
  *           state, the same of the right state, then B_n (15 per row);
  *           g = the 7 flux components (rho, m_n, m_t, m_u, E, B_t, B_u);
  *           dim is ignored.
@@ -267,9 +295,9 @@ amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const doub
                                const double* h, int32_t method, double* gx);
 
 /* Diagnostic: the FP32 <-> FP64 conversions of the mixed-precision recovery
- * (Sec. 1 names FP64 for the energy balance p = (gamma-1)(E - ke - me); the
- * mixed path widens its FP32 operands and rounds the FP64 pressure back to
- * FP32 with integer operations on the bit patterns). For i < n (host arrays):
+ * (the paper says nothing about precision; the mixed mode's split, FP64 for the
+ * energy balance p = (gamma-1)(E - ke - me), is this library's design: the mixed path widens its FP32 operands and rounds
+ * the FP64 pressure back to FP32 with integer operations on the bit patterns). For i < n (host arrays):
  * x_narrow[i] = x[i] rounded to FP32 (nearest even, results below 2^-126
  * flushed to a signed zero), y_widen[i] = y[i] widened to FP64 (FP32
  * subnormals flushed), and x_narrow_hw[i], y_widen_hw[i] the same conversions
@@ -281,6 +309,19 @@ amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const doub
  * AMRMHD_ECUDA if an allocation, copy or launch fails. */
 amrmhd_status amrmhd_fp_convert(int32_t on_device, int64_t n, const double* x, const float* y, float* x_narrow,
                                 double* y_widen, float* x_narrow_hw, double* y_widen_hw);
+
+/* Diagnostic: the primitive recovery (conservative -> primitive, the first
+ * step of the advance; the paper is silent on it) exactly as the mixed-precision
+ * advance runs it, for n cells (host arrays, row-major): u = (rho, mx, my, mz, E)
+ * (5 per cell), bl and br = the low and high face values of (Bx, By, Bz) (3 per
+ * cell) -> w = (rho, vx, vy, vz, p, Bx, By, Bz) with B the face means (8 per
+ * cell). All FP32 except the energy balance p = (gamma-1)(E - ke - me), which
+ * runs in FP64 with ke and me formed as double-float FP32 pairs. Allocates and
+ * frees device memory for the call and synchronises the device. Errors:
+ * AMRMHD_EINVAL for n < 0, NULL arrays with n > 0 or gamma <= 1; AMRMHD_ECUDA if
+ * an allocation, copy or launch fails. */
+amrmhd_status amrmhd_recover_mixed(int64_t n, const float* u, const float* bl, const float* br, double gamma,
+                                   float* w);
 
 /* Regrid: rebuilds every level above 0, coarse to fine, up to max_levels
  * levels (Sec. 2: the grids follow the flagged regions; a new grid takes its
