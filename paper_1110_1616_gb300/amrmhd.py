@@ -84,6 +84,7 @@ def lib():
             "amrmhd_set_option": [vp, i32, i64],
             "amrmhd_local_vjp": [i32, i32, i64, vp, vp, dbl, vp, i32, vp],
             "amrmhd_fp_convert": [i32, i64, vp, vp, vp, vp, vp, vp],
+            "amrmhd_recover_mixed": [i64, vp, vp, vp, dbl, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -135,6 +136,21 @@ def fp_convert(x, y, on_device=False):
     if st != 0:
         raise RuntimeError("amrmhd_fp_convert failed: status %d" % st)
     return xn, yw, xh, yh
+
+
+def recover_mixed(u, bl, br, gamma=5.0 / 3.0):
+    """The mixed-precision advance's primitive recovery of n cells on the GPU:
+    u (n, 5), bl and br (n, 3) FP32 numpy arrays -> w (n, 8) FP32."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    bl = np.ascontiguousarray(bl, dtype=np.float32)
+    br = np.ascontiguousarray(br, dtype=np.float32)
+    n = u.shape[0]
+    w = np.empty((n, 8), np.float32)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib().amrmhd_recover_mixed(n, p(u), p(bl), p(br), float(gamma), p(w))
+    if st != 0:
+        raise RuntimeError("amrmhd_recover_mixed failed: status %d" % st)
+    return w
 
 
 def declared_symbols():

@@ -15,7 +15,8 @@ UNITS = [
     # FP32 division and square root without IEEE rounding (FP64 code is unaffected)
     ("kernels_fast.cu", ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]),
     ("kernels_strict.cu", ["--fmad=false"]),
-    ("noalloc.cu", []),
+    # the same mixed-precision kernels as kernels_fast.cu, so the same flags
+    ("noalloc.cu", ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]),
     # no FMA contraction: the adjoint re-evaluates the forward's formulas (with
     # dual numbers) and must take the same branches as the strict FP64 forward
     ("adjoint.cu", ["--fmad=false"]),

@@ -1142,6 +1142,32 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+amrmhd_status amrmhd_recover_mixed(int64_t n, const float* u, const float* bl, const float* br, double gamma,
+                                   float* w) {
+  if (n < 0 || (n > 0 && (!u || !bl || !br || !w)) || !(gamma > 1.0)) return AMRMHD_EINVAL;
+  if (n == 0) return AMRMHD_OK;
+  const size_t nf = sizeof(float) * (size_t)n;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, 19 * nf) != cudaSuccess) return AMRMHD_ECUDA;
+  float* du = (float*)buf;
+  float* dl = du + 5 * n;
+  float* dr = dl + 3 * n;
+  float* dw = dr + 3 * n;
+  amrmhd_status st = AMRMHD_OK;
+  if (cudaMemcpy(du, u, 5 * nf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dl, bl, 3 * nf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dr, br, 3 * nf, cudaMemcpyHostToDevice) != cudaSuccess) {
+    st = AMRMHD_ECUDA;
+  } else {
+    amrk::launch_recover_mixed(n, du, dl, dr, gamma - 1.0, dw, 0);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(w, dw, 8 * nf, cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = AMRMHD_ECUDA;
+  }
+  cudaFree(buf);
+  return st;
+}
+
 amrmhd_status amrmhd_fp_convert(int32_t on_device, int64_t n, const double* x, const float* y, float* x_narrow,
                                 double* y_widen, float* x_narrow_hw, double* y_widen_hw) {
   if ((on_device != 0 && on_device != 1) || n < 0 ||

@@ -151,6 +151,8 @@ const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED
 const Ops* ops_strict(int dim);               // V_FP64_STRICT
 void launch_fp_convert(long long n, const double* x, const float* y, float* xn, double* yw, float* xn_hw,
                        double* yw_hw, cudaStream_t s);
+void launch_recover_mixed(long long n, const float* u, const float* bl, const float* br, double gm1, float* w,
+                          cudaStream_t s);
 
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_cfl_finalize(const unsigned long long* slots, int nlev, double cfl, double* dt_out, double* hist,

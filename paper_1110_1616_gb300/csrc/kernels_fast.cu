@@ -27,6 +27,27 @@ void launch_fp_convert(long long n, const double* x, const float* y, float* xn, 
   k_fp_convert<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, y, xn, yw, xn_hw, yw_hw);
 }
 
+// the mixed-precision recovery of one cell per thread, compiled with this
+// unit's flags (the code the mixed advance runs): u (5 per cell), the low and
+// high face values of B (3 + 3 per cell) -> w (8 per cell)
+__global__ void k_recover_mixed(long long n, const float* u, const float* bl, const float* br, double gm1, float* w) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float uu[5], l[3], r[3], wv[8];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) uu[f] = u[5 * i + f];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { l[c] = bl[3 * i + c]; r[c] = br[3 * i + c]; }
+  amrdev::recover_t(uu, l, r, gm1, wv);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) w[8 * i + f] = wv[f];
+}
+
+void launch_recover_mixed(long long n, const float* u, const float* bl, const float* br, double gm1, float* w,
+                          cudaStream_t s) {
+  k_recover_mixed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, u, bl, br, gm1, w);
+}
+
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }
