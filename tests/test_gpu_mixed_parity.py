@@ -9,6 +9,11 @@ Tolerances: smooth 3D problems 1e-5 relative L1 per field (the mixed-precision
 bound). Problems with shocks: 1e-4 per field, the observed errors written in
 each test's docstring (FP32 rounding of steep fronts feeds the limiter's and
 the HLLD's branch decisions, so the error is larger than on smooth data).
+For problems with shocks the error of a momentum or field component is taken
+relative to the L1 norm of the whole vector (sum of |m_x| + |m_y| + |m_z|, or
+of the three B components): a component that the flow leaves near zero (the
+transverse momentum of a flow along x) has no scale of its own, and FP32
+rounding of the O(1) fluxes sets its absolute error.
 """
 import numpy as np
 import pytest
@@ -64,10 +69,30 @@ def per_field(res, nlev):
     return {f: max(res[(l, f)] for l in range(nlev)) for f in range(8)}
 
 
+def vector_scaled_errors(g, o, pb):
+    """Per (level, field): sum |g - o| over the owned entries divided by the
+    owned L1 norm of the field's vector (momentum or B; the field itself for
+    rho and E). Any NaN or infinity in an owned entry gives infinity."""
+    from helpers import owned_mask
+    out = {}
+    for l in range(pb.nlev):
+        masks = [owned_mask(pb, l, f) for f in range(8)]
+        for f in range(8):
+            x, y = g[l][f][masks[f]], o[l][f][masks[f]]
+            if not (np.all(np.isfinite(x)) and np.all(np.isfinite(y))):
+                out[(l, f)] = float("inf")
+                continue
+            group = (1, 2, 3) if f in (1, 2, 3) else ((5, 6, 7) if f >= 5 else (f,))
+            den = sum(np.abs(o[l][h][masks[h]]).sum() for h in group) / len(group)
+            out[(l, f)] = np.abs(x - y).sum() / den if den > 0 else np.abs(x - y).sum()
+    return out
+
+
 def test_fused_mixed_smooth_3d_amr_20_steps():
     """A finite-amplitude fast magnetosonic wave (amplitude 1e-2, wave vector
     2 pi (1,1,1), background flow) on a two-level 3D hierarchy, 20 coarse
-    steps: every field within 1e-5 of the FP64 oracle."""
+    steps: every field within 1e-5 of the FP64 oracle (observed 1e-7 to
+    4.4e-7)."""
     def gen(n):
         return inputs.mhd_wave(3, n, "fast", amp=1e-2, v0=(0.3, -0.2, 0.25)).state[0]
     pb = two_level_3d(gen)
@@ -77,8 +102,8 @@ def test_fused_mixed_smooth_3d_amr_20_steps():
 
 def test_fused_mixed_blast_3d_amr_20_steps():
     """The 3D blast on the two-level hierarchy, 20 coarse steps; observed
-    relative L1 per field about 1e-7 (rho, E, B) to 1e-5 (momentum, which
-    starts at zero)."""
+    relative L1 per field: rho 9e-7, E 4e-6, B 9e-6, momentum 2.4e-5 (the
+    momentum starts at zero)."""
     pb = two_level_3d(lambda n: inputs.blast_3d(n, 16).state[0])
     res = mixed_vs_oracle(pb, 20)
     assert max_err(res) <= 1e-4, per_field(res, 2)
@@ -101,7 +126,9 @@ def _regrid_case(precision, nsteps_before=2, nsteps_after=2):
     cur = inputs.Problem(pb.name, 3, pb.base, gp, nlev, pb.state, gamma=pb.gamma)
     for dt in ctx.step(nsteps_after):
         o.step(float(dt))
-    return gp, op, compare_states(gpu_level_arrays(ctx, cur), o.get_state(), cur), nlev
+    g, ost = gpu_level_arrays(ctx, cur), o.get_state()
+    res = compare_states(g, ost, cur) if precision == A.FP64 else vector_scaled_errors(g, ost, cur)
+    return gp, op, res, nlev
 
 
 def test_deep_amr_downscaled_fp64():
@@ -112,13 +139,11 @@ def test_deep_amr_downscaled_fp64():
 
 
 def test_deep_amr_downscaled_mixed():
-    """Observed per-field relative L1 in mixed precision: about 1e-7 or below
-    for every field. The box lists are integer work; the flags are taken from
-    the FP32 state here, so they are compared only after checking that the
-    regrid kept three levels."""
+    """Mixed precision with one regrid: errors per field relative to the
+    field's vector norm (observed: rho 3e-7, m 2.4e-6, E 6e-7, B 1.5e-5). The flags are taken from the FP32 state, so the box lists are
+    compared with the oracle's (FP64 flags) before the states are."""
     gp, op, res, nlev = _regrid_case(A.MIXED)
-    if gp != op:
-        pytest.skip("the FP32 state flagged a different cell set than the FP64 oracle")
+    assert gp == op
     assert max_err(res) <= 1e-4, per_field(res, nlev)
 
 
@@ -128,7 +153,9 @@ def _shock_clump(precision, nsteps):
     o = oracle_for(pb)
     for dt in ctx.step(nsteps):
         o.step(float(dt))
-    return compare_states(gpu_level_arrays(ctx, pb), o.get_state(), pb), pb
+    g, ost = gpu_level_arrays(ctx, pb), o.get_state()
+    res = compare_states(g, ost, pb) if precision == A.FP64 else vector_scaled_errors(g, ost, pb)
+    return res, pb
 
 
 def test_shock_clump_downscaled_fp64():
@@ -139,7 +166,7 @@ def test_shock_clump_downscaled_fp64():
 
 
 def test_shock_clump_downscaled_mixed():
-    """The same in mixed precision (fused advance): per-field relative L1
-    within 1e-4."""
+    """The same in mixed precision (fused advance): per-field errors within
+    1e-4 (observed: rho 3e-8, m 4.6e-5, E 7e-8, B 6e-8)."""
     res, pb = _shock_clump(A.MIXED, 8)
     assert max_err(res) <= 1e-4, per_field(res, pb.nlev)
