@@ -310,6 +310,16 @@ amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const doub
 amrmhd_status amrmhd_fp_convert(int32_t on_device, int64_t n, const double* x, const float* y, float* x_narrow,
                                 double* y_widen, float* x_narrow_hw, double* y_widen_hw);
 
+/* Measurement: the device's floating-point multiply-add throughput (FP32 with
+ * fp64 = 0, FP64 with fp64 = 1) in operations per second (a multiply-add counts
+ * 2), from a kernel of independent multiply-add chains on every SM (8 blocks of
+ * 256 threads per SM, best of 5 timed launches after one warm-up, CUDA events on
+ * the legacy default stream); *sms (may be NULL) receives the SM count. The
+ * roofline of an ALU-bound kernel is taken against this number. Allocates and
+ * frees a small device buffer and synchronises the device. Errors:
+ * AMRMHD_EINVAL for bad arguments, AMRMHD_ECUDA if a CUDA call fails. */
+amrmhd_status amrmhd_alu_peak(int32_t fp64, double* flops_per_s, int32_t* sms);
+
 /* Diagnostic: the primitive recovery (conservative -> primitive, the first
  * step of the advance; the paper is silent on it) exactly as the mixed-precision
  * advance runs it, for n cells (host arrays, row-major): u = (rho, mx, my, mz, E)
@@ -389,10 +399,16 @@ enum {
                               side stream concurrently with the advance of level l (they meet
                               before the reflux), and the CFL reduction runs beside the level-0
                               ghost fill; 0: one stream, strictly in the recursive order */
-  AMRMHD_OPT_HOST_IO = 4    /* whole-state I/O with host buffers (amrmhd_set/get_state_all*): 0 (default):
+  AMRMHD_OPT_HOST_IO = 4,   /* whole-state I/O with host buffers (amrmhd_set/get_state_all*): 0 (default):
                               page-locked buffers are read and written in place by the packing kernels
                               over the host link, other host memory through a device staging buffer;
                               1: every host buffer through the staging buffer (copy engine) */
+  AMRMHD_OPT_DIRECT_HALO = 5 /* 1 (default): a 3D level without a finer level whose equal patches tile
+                              the fully periodic domain is advanced by the fused kernel reading its
+                              halo from the neighbour patches' interiors, and amrmhd_step skips that
+                              level's same-level ghost fill (its ghost cells are then not kept up to
+                              date; amrmhd_fill_ghosts still fills them); 0: fill, then read the
+                              ghosts. The results are the same either way. */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

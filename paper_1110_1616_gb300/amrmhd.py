@@ -20,7 +20,7 @@ MAPS = {
 }
 Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
 Q_REGRID_FLAG_US, Q_REGRID_CLUSTER_US, Q_REGRID_BUILD_US, Q_REGRID_TRANSFER_US, Q_REGRID_MAPS_US = range(6, 11)
-OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT, OPT_HOST_IO = 0, 1, 2, 3, 4
+OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT, OPT_HOST_IO, OPT_DIRECT_HALO = 0, 1, 2, 3, 4, 5
 
 
 class AmrmhdError(RuntimeError):
@@ -85,6 +85,7 @@ def lib():
             "amrmhd_local_vjp": [i32, i32, i64, vp, vp, dbl, vp, i32, vp],
             "amrmhd_fp_convert": [i32, i64, vp, vp, vp, vp, vp, vp],
             "amrmhd_recover_mixed": [i64, vp, vp, vp, dbl, vp],
+            "amrmhd_alu_peak": [i32, C.POINTER(dbl), C.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -136,6 +137,15 @@ def fp_convert(x, y, on_device=False):
     if st != 0:
         raise RuntimeError("amrmhd_fp_convert failed: status %d" % st)
     return xn, yw, xh, yh
+
+
+def alu_peak(fp64=False):
+    """Measured multiply-add throughput of the device: (FLOP/s, SM count)."""
+    v, n = C.c_double(0.0), C.c_int32(0)
+    st = lib().amrmhd_alu_peak(int(bool(fp64)), C.byref(v), C.byref(n))
+    if st != 0:
+        raise RuntimeError("amrmhd_alu_peak failed: status %d" % st)
+    return v.value, n.value
 
 
 def recover_mixed(u, bl, br, gamma=5.0 / 3.0):

@@ -87,7 +87,16 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
   a.gamma = ctx->cfg.gamma;
   a.w = w;
   a.bnd = (l > 0 && ctx->bnd_elems > 0) ? (void*)(ctx->arena + ctx->o_bnd) : nullptr;
+  a.nbr = nullptr;
   return a;
+}
+
+// The level's advance reads its halo straight from the neighbour patches
+// (fused 3D path, a level with direct_halo, no fill recording): its
+// same-level ghost fill is then not needed.
+bool direct_halo(const amrmhd_ctx* ctx, int l) {
+  return ctx->fused() && ctx->opt_advance != 1 && ctx->opt_direct_halo && !ctx->after_fill &&
+         l < (int)ctx->lev.size() && ctx->lev[l].direct_halo;
 }
 
 RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level) {
@@ -190,6 +199,7 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
     int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
     if (ctx->opt_tile < 0 && (int)ctx->tile_level.size() > l && ctx->tile_level[l][w ? 1 : 0] >= 0)
       v = ctx->tile_level[l][w ? 1 : 0];
+    if (w == 0 && direct_halo(ctx, l)) a.nbr = ctx->lev[l].nbr.p;
     ctx->ops->advance_fused(a, v, ctx->stream, nl);
   } else {
     ctx->ops->advance(a, ctx->stream, nl);
@@ -287,7 +297,8 @@ void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
 // level's advance).
 void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled) {
   if (!filled) {
-    op_fill(ctx, l, s, nl);
+    if (direct_halo(ctx, l)) ctx->start[l] = ctx->cur[l];  // no fill: the advance reads the neighbours
+    else op_fill(ctx, l, s, nl);
     if (ctx->after_fill) ctx->after_fill(ctx, l, s);
   }
   const bool kids = l + 1 < ctx->H.nlev;
@@ -326,7 +337,8 @@ void op_coarse_step(amrmhd_ctx* ctx, int* nl) {
     op_cfl(ctx, ctx->d_hist, nl);
     cudaEventRecord(ctx->ev_cfl_join, ctx->cfl_stream);
     ctx->stream = main;
-    op_fill(ctx, 0, 1, nl);
+    if (direct_halo(ctx, 0)) ctx->start[0] = ctx->cur[0];
+    else op_fill(ctx, 0, 1, nl);
     cudaStreamWaitEvent(main, ctx->ev_cfl_join, 0);
     op_level_step(ctx, 0, 1, nl, true);
     return;
@@ -448,6 +460,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 4) ctx->opt_tile = value;
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else if (option == AMRMHD_OPT_HOST_IO && (value == 0 || value == 1)) ctx->opt_host_io = value;
+  else if (option == AMRMHD_OPT_DIRECT_HALO && (value == 0 || value == 1)) ctx->opt_direct_halo = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -733,6 +746,55 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
            upload(slice(H.reflux_cells, H.rng_reflux_cells[l], 9), L.reflux_cells, 9);
       L.cf_face0 = H.rng_cf_faces[l][0];
       L.cf_edge0 = H.rng_cf_edges[l][0];
+    }
+    // direct halo reads: a 3D level without a finer level whose equal patches
+    // tile the periodic domain (so every halo position lies in the interior
+    // of the neighbour patch in the patch grid, at a shift of one patch)
+    L.direct_halo = false;
+    if (H.dim == 3 && l == nlev - 1 && !ctx->stage_light && !ids.empty()) {
+      bool periodic = true;
+      for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side) periodic = periodic && ctx->cfg.bc[d][side] == AMRMHD_BC_PERIODIC;
+      const int* n0 = H.p[ids[0]].n;
+      int N[3], G[3];
+      bool uniform = periodic;
+      for (int d = 0; d < 3 && uniform; ++d) {
+        N[d] = ctx->cfg.base[d] << l;
+        uniform = n0[d] >= 4 && N[d] % n0[d] == 0;
+        G[d] = uniform ? N[d] / n0[d] : 0;
+      }
+      std::vector<int> grid;
+      if (uniform && (long long)G[0] * G[1] * G[2] == (long long)ids.size()) {
+        grid.assign(ids.size(), -1);
+        for (int q : ids) {
+          const amrmhd::HPatch& Q = H.p[q];
+          int g[3];
+          for (int d = 0; d < 3 && uniform; ++d) {
+            uniform = Q.n[d] == n0[d] && Q.lo[d] % n0[d] == 0;
+            g[d] = Q.lo[d] / n0[d];
+          }
+          if (!uniform) break;
+          int& slot = grid[g[0] + G[0] * (g[1] + G[1] * g[2])];
+          if (slot >= 0) { uniform = false; break; }
+          slot = q;
+        }
+        if (uniform) {
+          std::vector<int32_t> nb;
+          nb.reserve(27 * ids.size());
+          for (int q : ids) {
+            const amrmhd::HPatch& Q = H.p[q];
+            const int g[3] = {Q.lo[0] / n0[0], Q.lo[1] / n0[1], Q.lo[2] / n0[2]};
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                  const int gx = (g[0] + dx + G[0]) % G[0], gy = (g[1] + dy + G[1]) % G[1],
+                            gz = (g[2] + dz + G[2]) % G[2];
+                  nb.push_back(grid[gx + G[0] * (gy + G[1] * gz)]);
+                }
+          }
+          L.direct_halo = upload(nb, L.nbr, 27);
+        }
+      }
     }
     if (!ok) return fail(ctx, AMRMHD_ECUDA, std::string("map upload: ") + cudaGetErrorString(e));
   }
@@ -1141,6 +1203,41 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
 }
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+amrmhd_status amrmhd_alu_peak(int32_t fp64, double* flops_per_s, int32_t* sms) {
+  if ((fp64 != 0 && fp64 != 1) || !flops_per_s) return AMRMHD_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    return AMRMHD_ECUDA;
+  if (sms) *sms = nsm;
+  const int threads = 256, blocks = nsm * 8;  // 64 warps per SM
+  void* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc(&out, sizeof(double) * blocks) != cudaSuccess) return AMRMHD_ECUDA;
+  amrmhd_status st = AMRMHD_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = AMRMHD_ECUDA;
+  // iterations sized for about 50-100 ms at the expected rate; best of 5
+  const int iters = fp64 ? 4096 : 1 << 17;
+  float best = 0.0f;
+  for (int rep = 0; rep < 6 && st == AMRMHD_OK; ++rep) {
+    cudaEventRecord(e0, 0);
+    amrk::launch_fma_peak(fp64, blocks, threads, iters, out, 0);
+    cudaEventRecord(e1, 0);
+    float ms = 0.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = AMRMHD_ECUDA;
+      break;
+    }
+    if (rep > 0 && (best == 0.0f || ms < best)) best = ms;  // the first run warms up
+  }
+  if (st == AMRMHD_OK) *flops_per_s = 2.0 * 8.0 * (double)iters * threads * (double)blocks / (best * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  return st;
+}
 
 amrmhd_status amrmhd_recover_mixed(int64_t n, const float* u, const float* bl, const float* br, double gamma,
                                    float* w) {

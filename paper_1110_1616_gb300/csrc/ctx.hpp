@@ -39,6 +39,11 @@ struct LevelDev {
   DevList row_same_cells, row_same_faces, row_prol_cells, row_prol_faces, row_bc_cells, row_bc_faces;
   DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
   int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
+  // a 3D level of equal patches that tiles the periodic domain and has no finer
+  // level: the fused advance reads its halo from the neighbour patches (27 ids
+  // per patch, in the order of ids) and the level's same-level fill is skipped
+  DevList nbr;
+  bool direct_halo = false;
 };
 
 struct AdjWork;  // discrete-adjoint workspace (adjoint.cu)
@@ -59,7 +64,7 @@ struct amrmhd_ctx {
   int stage_ghost_from = 0;
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
-  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1, opt_host_io = 0;
+  int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1, opt_host_io = 0, opt_direct_halo = 1;
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;

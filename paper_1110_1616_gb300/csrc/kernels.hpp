@@ -36,6 +36,13 @@ struct LevelArgs {
   // boundary capture buffer (fused 3D advance of a level > 0): the fluxes and
   // EMFs of every patch's boundary planes are written at P.boff; nullptr: none
   void* bnd;
+  // direct halo reads (fused 3D advance of a level of equal patches tiling the
+  // periodic domain, w = 0): per patch of the launch, the 27 patch ids of its
+  // neighbours at (dx, dy, dz) in {-1, 0, 1}^3, index (dx+1) + 3 (dy+1) +
+  // 9 (dz+1) (the patch itself at 13); the advance reads the cells and faces
+  // of its halo from those patches' interiors instead of its own ghost cells,
+  // so the level needs no same-level ghost fill. nullptr: read the ghosts.
+  const int* nbr;
 };
 
 struct RowArgs {
@@ -153,6 +160,7 @@ void launch_fp_convert(long long n, const double* x, const float* y, float* xn, 
                        double* yw_hw, cudaStream_t s);
 void launch_recover_mixed(long long n, const float* u, const float* bl, const float* br, double gm1, float* w,
                           cudaStream_t s);
+void launch_fma_peak(int fp64, int blocks, int threads, int iters, void* out, cudaStream_t s);
 
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_cfl_finalize(const unsigned long long* slots, int nlev, double cfl, double* dt_out, double* hist,

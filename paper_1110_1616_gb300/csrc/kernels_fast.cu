@@ -48,6 +48,28 @@ void launch_recover_mixed(long long n, const float* u, const float* bl, const fl
   k_recover_mixed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, u, bl, br, gm1, w);
 }
 
+// ALU peak probe: every thread runs 8 independent multiply-add chains of
+// `iters` steps (2 floating-point operations each); the sum of the chains is
+// stored only if it takes an impossible value, so nothing is eliminated.
+template <class T> __global__ void k_fma_peak(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = T(threadIdx.x) * T(1e-3) + T(c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = x[c] * a + b;
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  if (s == T(-1.2345e30)) out[blockIdx.x] = s;
+}
+
+void launch_fma_peak(int fp64, int blocks, int threads, int iters, void* out, cudaStream_t s) {
+  if (fp64) k_fma_peak<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.999999, 1e-7);
+  else k_fma_peak<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
+}
+
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }

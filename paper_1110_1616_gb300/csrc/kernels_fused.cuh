@@ -142,15 +142,23 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
 }
 
 // FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread).
-// CAP: the level's boundary fluxes and EMFs are captured for the fine registers.
-template <class T, int VAR, bool CAP>
+// MODE 0: plain; 1 (CAP): the level's boundary fluxes and EMFs are captured for
+// the fine registers; 2 (DH): direct halo reads from the neighbour patches
+// (a.nbr; a level of equal patches tiling the periodic domain, w = 0).
+template <class T, int VAR, int MODE>
 __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
+  constexpr bool CAP = MODE == 1, DH = MODE == 2;
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
   constexpr int TX = S::TX, TY = S::TY, PX = S::PX, QX = S::QX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S& sm = *reinterpret_cast<S*>(smem_raw);
+  __shared__ long long s_nb[DH ? 27 : 1];  // element offsets of the neighbour patches (DH)
   const DPatch P = a.P[a.ids[blockIdx.y]];
+  if constexpr (DH) {
+    if (threadIdx.x < 27) s_nb[threadIdx.x] = a.P[a.nbr[27 * blockIdx.y + threadIdx.x]].off;
+    __syncthreads();
+  }
   const int w = a.w;
   const int xlo = 4 - w, xhi = P.n[0] + 4 + w, ylo = 4 - w, yhi = P.n[1] + 4 + w;
   const int zlo = 4 - w, zhi = P.n[2] + 4 + w;
@@ -185,7 +193,19 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
         if (xi >= wx || yi >= wy) continue;
         const int x = x0 - 2 + xi, y = y0 - 2 + yi;
         T wv[8], dB[3];
-        load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB);
+        if constexpr (DH) {
+          // the cell (and its faces) in the neighbour patch that owns it: every
+          // patch has the interior extent n, so a coordinate outside [4, n+4)
+          // moves by n into the neighbour's interior (its own high faces at n+4
+          // included); the neighbours' strides are this patch's
+          int lx = x, ly = y, lz = t, k = 13;
+          if (x < 4) { lx += P.n[0]; k -= 1; } else if (x >= P.n[0] + 4) { lx -= P.n[0]; k += 1; }
+          if (y < 4) { ly += P.n[1]; k -= 3; } else if (y >= P.n[1] + 4) { ly -= P.n[1]; k += 3; }
+          if (t < 4) { lz += P.n[2]; k -= 9; } else if (t >= P.n[2] + 4) { lz -= P.n[2]; k += 9; }
+          load_recover((const T*)a.cur + s_nb[k], fs, lx + sy * ly + sz * lz, sy, sz, gm1, wv, dB);
+        } else {
+          load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB);
+        }
         const int i = widx(x, y);
 #pragma unroll
         for (int f = 0; f < 8; ++f) sm.w[slot][f][i] = wv[f];

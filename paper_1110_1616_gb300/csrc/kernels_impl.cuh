@@ -1070,9 +1070,11 @@ template <class T, int DIM> struct Impl {
   template <int V> static bool fused_fits() { return fused_smem<V>() <= 227 * 1024; }
   template <int V> static void prepare_v() {
     if (fused_fits<V>()) {
-      cudaFuncSetAttribute(k_advance3d_fused<T, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_smem<V>());
-      cudaFuncSetAttribute(k_advance3d_fused<T, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<V>());
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_smem<V>());
     }
   }
@@ -1083,8 +1085,10 @@ template <class T, int DIM> struct Impl {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
     const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
     const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
-    if (a.bnd) k_advance3d_fused<T, V, true><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
-    else k_advance3d_fused<T, V, false><<<dim3(ntx * nty, a.npatch), FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    const dim3 g(ntx * nty, a.npatch);
+    if (a.bnd) k_advance3d_fused<T, V, 1><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    else if (a.nbr && a.w == 0) k_advance3d_fused<T, V, 2><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    else k_advance3d_fused<T, V, 0><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
   }
   static void advance_fused(const LevelArgs& a, int variant, cudaStream_t s, int* nl) {
     if (DIM != 3) {

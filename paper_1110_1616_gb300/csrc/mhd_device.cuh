@@ -45,15 +45,19 @@ template <class T> __device__ __forceinline__ T mm(T a, T b) {
 template <class T> __device__ __forceinline__ T tmaxd(T a, T b) { return a > b ? a : b; }
 template <class T> __device__ __forceinline__ T tmind(T a, T b) { return a < b ? a : b; }
 
-// fast magnetosonic speed along a direction with normal field bn
-template <class T> __device__ __forceinline__ T cfast(T rho, T p, T bn, T bt, T bu, T gamma) {
+// square of the fast magnetosonic speed along a direction with normal field bn
+template <class T> __device__ __forceinline__ T cfast2(T rho, T p, T bn, T bt, T bu, T gamma) {
   T irho = T(1) / rho;
   T gp = gamma * p;
   T b2 = bn * bn + bt * bt + bu * bu;
   T a = (gp + b2) * irho;
   T disc = a * a - T(4) * (gp * irho) * (bn * bn * irho);
   if (disc < T(0)) disc = T(0);
-  return dsqrt(T(0.5) * (a + dsqrt(disc)));
+  return T(0.5) * (a + dsqrt(disc));
+}
+// fast magnetosonic speed along a direction with normal field bn
+template <class T> __device__ __forceinline__ T cfast(T rho, T p, T bn, T bt, T bu, T gamma) {
+  return dsqrt(cfast2(rho, p, bn, bt, bu, gamma));
 }
 
 // conservative -> primitive, always in FP64: p = (g-1)(E - m.m/(2 rho) - B.B/2)
@@ -181,6 +185,20 @@ template <class T> __device__ __forceinline__ void phys_flux(const T* q, T bn, T
   u[0] = r; u[1] = r * un; u[2] = r * ut; u[3] = r * uu; u[4] = e; u[5] = bt; u[6] = bu;
 }
 
+// Quotients that share a divisor: FP64 divides each time (the written
+// formula, bit for bit); FP32 multiplies by one reciprocal (the FP32 path
+// compiles its divisions as a reciprocal and a product anyway).
+template <class T> struct Quot {
+  T d;
+  __device__ __forceinline__ explicit Quot(T den) : d(den) {}
+  __device__ __forceinline__ T operator()(T num) const { return num / d; }
+};
+template <> struct Quot<float> {
+  float r;
+  __device__ __forceinline__ explicit Quot(float den) : r(1.0f / den) {}
+  __device__ __forceinline__ float operator()(float num) const { return num * r; }
+};
+
 // HLLD flux between rotated states ql, qr with common normal field bn
 template <class T> __device__ void hlld_flux(const T* ql, const T* qr, T bn, T gamma, T* f) {
   const T eps = Eps<T>::v();
@@ -189,9 +207,11 @@ template <class T> __device__ void hlld_flux(const T* ql, const T* qr, T bn, T g
   T fl[7], fr[7], ul[7], ur[7];
   phys_flux(ql, bn, igm1, fl, ul);
   phys_flux(qr, bn, igm1, fr, ur);
-  const T cl = cfast(ql[0], ql[4], bn, ql[5], ql[6], gamma);
-  const T cr = cfast(qr[0], qr[4], bn, qr[5], qr[6], gamma);
-  const T cmax = tmaxd(cl, cr);
+  // max(sqrt(a), sqrt(b)) = sqrt(max(a, b)): the square root is monotone and
+  // correctly rounded, so one root serves both sides
+  const T cl2 = cfast2(ql[0], ql[4], bn, ql[5], ql[6], gamma);
+  const T cr2 = cfast2(qr[0], qr[4], bn, qr[5], qr[6], gamma);
+  const T cmax = dsqrt(tmaxd(cl2, cr2));
   const T sl = tmind(ql[1], qr[1]) - cmax;
   const T sr = tmaxd(ql[1], qr[1]) + cmax;
   if (sl > T(0)) {
@@ -210,9 +230,9 @@ template <class T> __device__ void hlld_flux(const T* ql, const T* qr, T bn, T g
   const T ptl = ql[4] + T(0.5) * (bn2 + ql[5] * ql[5] + ql[6] * ql[6]);
   const T ptr = qr[4] + T(0.5) * (bn2 + qr[5] * qr[5] + qr[6] * qr[6]);
   const T dl = sl - uln, dr = sr - urn;
-  const T den = dr * rr - dl * rl;
-  const T sm = (dr * rr * urn - dl * rl * uln - ptr + ptl) / den;
-  const T pts = (dr * rr * ptl - dl * rl * ptr + rl * rr * dr * dl * (urn - uln)) / den;
+  const Quot<T> byden(dr * rr - dl * rl);
+  const T sm = byden(dr * rr * urn - dl * rl * uln - ptr + ptl);
+  const T pts = byden(dr * rr * ptl - dl * rl * ptr + rl * rr * dr * dl * (urn - uln));
 
   T rs[2], vs[2], ws[2], bts[2], bus[2], es[2], vbs[2];
 #pragma unroll
@@ -221,7 +241,8 @@ template <class T> __device__ void hlld_flux(const T* ql, const T* qr, T bn, T g
     const T sx = a == 0 ? sl : sr;
     const T da = sx - q[1];
     const T ssm = sx - sm;
-    rs[a] = q[0] * da / ssm;
+    const Quot<T> byssm(ssm);
+    rs[a] = byssm(q[0] * da);
     const T rds = q[0] * da * ssm;
     const T e = rds - bn2;
     if (dabs(e) <= eps * (dabs(rds) + bn2)) {
@@ -238,7 +259,7 @@ template <class T> __device__ void hlld_flux(const T* ql, const T* qr, T bn, T g
     const T vb = q[1] * bn + q[2] * q[5] + q[3] * q[6];
     vbs[a] = sm * bn + vs[a] * bts[a] + ws[a] * bus[a];
     const T ea = a == 0 ? ul[4] : ur[4];
-    es[a] = (da * ea - (a == 0 ? ptl : ptr) * q[1] + pts * sm + bn * (vb - vbs[a])) / ssm;
+    es[a] = byssm(da * ea - (a == 0 ? ptl : ptr) * q[1] + pts * sm + bn * (vb - vbs[a]));
   }
   const T usl[7] = {rs[0], rs[0] * sm, rs[0] * vs[0], rs[0] * ws[0], es[0], bts[0], bus[0]};
   const T usr[7] = {rs[1], rs[1] * sm, rs[1] * vs[1], rs[1] * ws[1], es[1], bts[1], bus[1]};

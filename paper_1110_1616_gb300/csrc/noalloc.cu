@@ -100,6 +100,7 @@ extern "C" amrmhd_status amrmhd_advance_patch_noalloc(const float* u_in, float* 
   for (int d = 0; d < 3; ++d) a.idx[d] = d < dim ? 1.0 / dx[d] : 1.0;
   a.gamma = gamma;
   a.bnd = nullptr;
+  a.nbr = nullptr;
   a.w = w;
   if (dim == 3) amrk_noalloc::Impl<float, 3>::advance(a, s, nullptr);
   else amrk_noalloc::Impl<float, 2>::advance(a, s, nullptr);
