@@ -3,9 +3,10 @@
 
 Workload: 3D periodic blast wave, 128^3 cells split into 512 patches of 16^3
 (rho = 1, p = 0.1, p = 10 inside r < 0.1, uniform B = (1,1,1)/sqrt 3). A step
-is one coarse step of the whole hot path: CFL reduction, ghost fill, the level
-advance (MUSCL-Hancock + minmod, HLLD, constrained transport) of every patch,
-replayed as one CUDA graph. The headline runs the mixed-precision path (FP32
+is one coarse step of the whole hot path: CFL reduction, the level advance
+(MUSCL-Hancock + minmod, HLLD, constrained transport) of every patch, replayed
+as one CUDA graph; the level tiles the periodic domain with equal patches, so
+the advance reads its halo from the neighbour patches and no ghost fill runs. The headline runs the mixed-precision path (FP32
 stencil, FP64 primitive recovery, registers, dt). Also reported: the FP64 path,
 the FP64 one-patch-per-launch baseline, the level advance alone against the
 HBM roofline, an end-to-end run through the C ABI with host buffers, and the
@@ -31,13 +32,14 @@ UNIT = "cell-updates/s"
 # by running the oracle's per-cell formulas with a counting scalar type
 # (oracle/opcount.cpp, 2000 subsonic samples, seed 1; tests/test_oracle_opcount.py).
 FLOPS_PER_CELL_UPDATE_3D = 1504.0
-# DRAM bytes (read + write) of one launch of the fused advance on the 128^3
-# blast in 16^3 patches, mixed precision, from one ncu capture of that launch
-# (224.92 MB read + 75.82 MB written; profiles/k_advance3d_fused_blast3d_128.md)
 TILE_NAMES = {0: "16x16", 1: "16x16/512 threads", 2: "16x8", 3: "8x8", 4: "12x12"}
-FUSED_TRAFFIC_BYTES = 300.44e6  # ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (profiles/)
-# FP32 peak of the part: 152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock
-SMS, FP32_LANES = 152, 128
+# DRAM bytes (read + write) of one launch of the fused advance (direct halo
+# reads, 16x8 tile) on the 128^3 blast in 16^3 patches, mixed precision, from
+# one ncu capture of that launch (profiles/k_advance3d_fused_blast3d_128.md);
+# None until the kernel's current version has been captured
+FUSED_TRAFFIC_BYTES = None
+# FP32 lanes per SM (the derived ALU peak: SMs x lanes x 2 (FMA) x max SM clock)
+FP32_LANES = 128
 
 
 def parse():
@@ -557,21 +559,36 @@ def main():
     achieved = alg_bytes / (t_adv / 1e3) / 1e9
     arena_gb = ctx.query(A.Q_ARENA_BYTES) / 1e9
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    # ALU peaks: derived from the unit counts and the clock, and measured by the
+    # library's multiply-add probe (FP32 and FP64) on this device
+    fp32_meas, sms = A.alu_peak(False)
+    fp64_meas, _ = A.alu_peak(True)
+    fp32_peak = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     flops_achieved = FLOPS_PER_CELL_UPDATE_3D * cells_step / (t_adv / 1e3) / 1e12
     del ctx
     torch.cuda.empty_cache()
 
-    extras = {}
+    extras = {"alu_peaks": {"fp32_tflops": fp32_meas / 1e12, "fp64_tflops": fp64_meas / 1e12, "sms": sms,
+                            "how": "amrmhd_alu_peak: 8 independent multiply-add chains per thread, 8 x 256 "
+                                   "threads per SM, best of 5 launches, CUDA events"}}
     if not args.skip_extras:
-        ctx64, s64 = make_ctx(pb, A.FP64)
-        ctx64.step(2, want_dt=False)
+        # FP64: the staged kernels (the default) and the fused kernel (option 3)
         k64 = max(5, args.steps // 5)
-        ms64, _ = timed_steps(ctx64, s64, k64)
-        extras["fp64"] = {"value": cells_step * k64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / k64,
-                          "steps": k64}
-        del ctx64
-        torch.cuda.empty_cache()
+        fp64 = {}
+        for name, opt in (("staged", None), ("fused", 3)):
+            ctx64, s64 = make_ctx(pb, A.FP64)
+            if opt is not None:
+                ctx64.set_option(A.OPT_ADVANCE, opt)
+            ctx64.step(2, want_dt=False)
+            ms64, _ = timed_steps(ctx64, s64, k64)
+            rate = cells_step * k64 / (ms64 / 1e3)
+            fp64[name] = {"value": rate, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                          "alu_frac_of_measured_fp64": FLOPS_PER_CELL_UPDATE_3D * rate / fp64_meas,
+                          "hbm_frac": 16 * 8 * rate / 1e9 / hbm_peak}
+            del ctx64
+            torch.cuda.empty_cache()
+        extras["fp64"] = dict(fp64["staged"], fused=fp64["fused"])
+
         ctxb, sb = make_ctx(pb, A.FP64, baseline=True, graph=False)
         ctxb.step(1, want_dt=False)
         kb = max(3, args.steps // 20)
@@ -589,7 +606,7 @@ def main():
         extras["cylinder3d_paper_shape"] = cylinder_leg()
     e2e = None
     if not args.skip_extras:
-        ke = max(3, args.steps // 10)
+        ke = max(10, args.steps // 4)
         ve, nbytes = e2e_run(pb, A.MIXED, ke)
         e2e = {"value": ve * world, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     cpu = None
@@ -609,16 +626,18 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (arena %.2f GB: ping-pong state and stage scratch)" % arena_gb},
         "roofline": {"bound": "alu",
-                     "kernel": "k_advance3d_fused<float,%s> (one launch per level advance, autotuned tile)"
-                               % TILE_NAMES.get(tile, str(tile)),
+                     "kernel": "k_advance3d_fused<float,%s> (one launch per level advance, autotuned tile; "
+                               "halo read from the neighbour patches)" % TILE_NAMES.get(tile, str(tile)),
                      "achieved": flops_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": flops_achieved / fp32_peak,
-                     "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (SMS, FP32_LANES, sm_max),
+                     "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 x %.0f MHz" % (sms, FP32_LANES, sm_max),
+                     "measured_peak": fp32_meas / 1e12, "frac_of_measured": flops_achieved / (fp32_meas / 1e12),
                      "traffic": FUSED_TRAFFIC_BYTES if args.n == 128 and args.psize == 16 and tile == 2 else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
                                        "this kernel on this workload (profiles/k_advance3d_fused_blast3d_128.md)",
                      "flops_per_cell_update": FLOPS_PER_CELL_UPDATE_3D,
-                     "ms_per_launch": t_adv, "fill_ms_per_launch": t_fill},
+                     "ms_per_launch": t_adv,
+                     "fill_ms_per_launch": t_fill, "fill_in_step": False},
         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback",
                 "alg_bytes_per_launch": alg_bytes},

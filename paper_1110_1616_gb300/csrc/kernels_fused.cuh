@@ -141,28 +141,29 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
   }
 }
 
-// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread).
-// MODE 0: plain; 1 (CAP): the level's boundary fluxes and EMFs are captured for
-// the fine registers; 2 (DH): direct halo reads from the neighbour patches
-// (a.nbr; a level of equal patches tiling the periodic domain, w = 0).
+// One x-y tile (index `tile`, ntx tiles along x) of the patch at position
+// `pslot` of a.ids, marched along z by the whole CTA; smem_raw: the CTA's
+// dynamic shared memory (a FusedSmem). MODE 0: plain; 1 (CAP): the level's
+// boundary fluxes and EMFs are captured for the fine registers (patches with
+// P.boff >= 0); 2 (DH): direct halo reads from the neighbour patches (a.nbr; a
+// level of equal patches tiling the periodic domain, w = 0). Every thread of
+// the CTA calls it with the same arguments.
 template <class T, int VAR, int MODE>
-__global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
-    k_advance3d_fused(LevelArgs a, int ntx) {
+__device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int tile, int ntx,
+                                           unsigned char* smem_raw) {
   constexpr bool CAP = MODE == 1, DH = MODE == 2;
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
   constexpr int TX = S::TX, TY = S::TY, PX = S::PX, QX = S::QX;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   S& sm = *reinterpret_cast<S*>(smem_raw);
   __shared__ long long s_nb[DH ? 27 : 1];  // element offsets of the neighbour patches (DH)
-  const DPatch P = a.P[a.ids[blockIdx.y]];
+  const DPatch P = a.P[a.ids[pslot]];
   if constexpr (DH) {
-    if (threadIdx.x < 27) s_nb[threadIdx.x] = a.P[a.nbr[27 * blockIdx.y + threadIdx.x]].off;
+    if (threadIdx.x < 27) s_nb[threadIdx.x] = a.P[a.nbr[27 * pslot + threadIdx.x]].off;
     __syncthreads();
   }
   const int w = a.w;
   const int xlo = 4 - w, xhi = P.n[0] + 4 + w, ylo = 4 - w, yhi = P.n[1] + 4 + w;
   const int zlo = 4 - w, zhi = P.n[2] + 4 + w;
-  const int tile = blockIdx.x;
   const int x0 = xlo + (tile % ntx) * TX, y0 = ylo + (tile / ntx) * TY;
   if (x0 >= xhi || y0 >= yhi) return;
   const int tx = min(TX, xhi - x0), ty = min(TY, yhi - y0);
@@ -444,6 +445,14 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg
     }
     // no barrier: the next S1 writes only the W ring slot that S2 no longer reads
   }
+}
+
+// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread).
+template <class T, int VAR, int MODE>
+__global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
+    k_advance3d_fused(LevelArgs a, int ntx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fused_tile<T, VAR, MODE>(a, blockIdx.y, blockIdx.x, ntx, smem_raw);
 }
 
 // ------------------------------------------------------------------ register recompute
