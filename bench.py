@@ -271,10 +271,18 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
             for q in range(5):
                 breakdown[q] += ctx.query(A.Q_REGRID_FLAG_US + q)
             ctx.autotune(2)
+    # the final hierarchy in three schedules: finer levels on side streams (the
+    # default), one stream in the recursive order, and the device work queue
+    # (one persistent launch per finest sub-step, finest level first)
     ms_c, _ = timed_steps(ctx, stream, 2)
     ctx.set_option(A.OPT_CONCURRENT, 0)
     ctx.step(1, want_dt=False)
     ms_s, _ = timed_steps(ctx, stream, 2)
+    ctx.set_option(A.OPT_CONCURRENT, 1)
+    ctx.set_option(A.OPT_QUEUE, 1)
+    ctx.step(1, want_dt=False)
+    ms_q, _ = timed_steps(ctx, stream, 2)
+    ctx.set_option(A.OPT_QUEUE, 0)
     cells = {}
     for (l, lo, hi) in ctx.get_patches():
         cells[l] = cells.get(l, 0) + (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
@@ -286,6 +294,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
                                    zip(("flag", "cluster", "build", "transfer", "build_host_maps"), breakdown)},
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
            "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
+           "final_hierarchy_ms_per_step": {"side_streams": ms_c / 2, "serial": ms_s / 2, "device_queue": ms_q / 2},
            "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}
     del ctx
     torch.cuda.empty_cache()

@@ -403,12 +403,26 @@ enum {
                               page-locked buffers are read and written in place by the packing kernels
                               over the host link, other host memory through a device staging buffer;
                               1: every host buffer through the staging buffer (copy engine) */
-  AMRMHD_OPT_DIRECT_HALO = 5 /* 1 (default): a 3D level without a finer level whose equal patches tile
-                              the fully periodic domain is advanced by the fused kernel reading its
+  AMRMHD_OPT_DIRECT_HALO = 5, /* 1 (default): the 3D base level of a one-level hierarchy whose equal patches
+                              tile the fully periodic domain is advanced by the fused kernel reading its
                               halo from the neighbour patches' interiors, and amrmhd_step skips that
                               level's same-level ghost fill (its ghost cells are then not kept up to
                               date; amrmhd_fill_ghosts still fills them); 0: fill, then read the
                               ghosts. The results are the same either way. */
+  AMRMHD_OPT_QUEUE = 6,      /* 1: a 3D hierarchy of 2 to 12 levels on the fused path advances through the
+                              device work queue: per sub-step of the finest level one persistent launch
+                              of the resident CTAs takes tasks in ticket order, finest level first (the
+                              paper's threaded level advances with preference to the finer levels,
+                              Sec. 4): the finest level's same-level ghost copies, then every starting
+                              level's advance tiles, each tile after the copies into its patch (bounded
+                              waits on per-patch counters; a wait that runs out makes amrmhd_step return
+                              AMRMHD_ETIMEOUT). Results equal the level-by-level launches. 0 (default):
+                              per-level launches, finer levels on side streams. */
+  AMRMHD_OPT_QUEUE_TILE = 7, /* tile of the queue's advance tasks: 3 (default) 8x8, 2 16x8 */
+  AMRMHD_OPT_QUEUE_WITHHOLD = 8 /* test switch, 0 (default) or 1: the first patch of the finest level waits
+                              in the first batch of a coarse step for one fill task more than exist,
+                              so the wait runs out (after 0.5 s) and amrmhd_step returns
+                              AMRMHD_ETIMEOUT; the device stays usable */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

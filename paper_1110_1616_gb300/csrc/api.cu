@@ -55,6 +55,7 @@ void free_device(amrmhd_ctx* ctx) {
   ctx->dev_allocs.clear();
   ctx->d_stage_all = nullptr;
   ctx->lev.clear();
+  ctx->qplan = QueuePlan();
   ctx->bound = false;
 }
 
@@ -133,8 +134,10 @@ void offset_regs(amrmhd_ctx* ctx, RowArgs& a, int l) {
 }
 
 // ----- the level operations, shared by the direct calls and graph capture
-void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
-  ctx->start[l] = ctx->cur[l];
+// the parts of a level's ghost fill: same-level copies, prolongation (sub-step
+// 1 above level 0), physical boundaries (last: their sources are domain cells
+// the other two fill)
+void op_fill_same(amrmhd_ctx* ctx, int l, int s, int* nl) {
   const LevelDev& L = ctx->lev[l];
   // an advance of the interior alone (w = 0) reads ghosts 2 cells deep
   const bool near = l == 0 || s == 2;
@@ -144,6 +147,11 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   a.nrows = near ? L.chunk_runs2.n : L.chunk_runs.n;
   a.nsplit = near ? L.runs2_split : L.runs_split;
   ctx->ops->fill_runs(a, ctx->stream, nl);
+}
+
+void op_fill_rest(amrmhd_ctx* ctx, int l, int s, int* nl) {
+  const LevelDev& L = ctx->lev[l];
+  const bool near = l == 0 || s == 2;
   if (s == 1 && l > 0) {
     RowArgs b = row_args(ctx, L.prol_cells, l - 1);
     b.fbuf = state_buf(ctx, ctx->cur[l]);
@@ -175,6 +183,12 @@ void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
   }
 }
 
+void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl) {
+  ctx->start[l] = ctx->cur[l];
+  op_fill_same(ctx, l, s, nl);
+  op_fill_rest(ctx, l, s, nl);
+}
+
 void level_idx(amrmhd_ctx* ctx, int l, double* idx) {
   for (int d = 0; d < 3; ++d) {
     int N = d < ctx->cfg.dim ? (ctx->cfg.base[d] << l) : 1;
@@ -204,6 +218,16 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
   } else {
     ctx->ops->advance(a, ctx->stream, nl);
   }
+  op_level_registers(ctx, l, dtp, dtscale, s, (fused && ctx->opt_advance != 1) ? a.bnd : nullptr, nl);
+  ctx->cur[l] ^= 1;
+}
+
+// The flux and EMF registers of level l's sub-step s after its advance (before
+// its buffer flips): the coarse side of level l+1's C/F boundary and the fine
+// side of level l's own (bnd: the boundary capture the fused advance wrote, or
+// nullptr to recompute).
+void op_level_registers(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, void* bnd, int* nl) {
+  const bool fused = ctx->fused();
   const int nlev = ctx->H.nlev;
   if (l + 1 < nlev) {
     const LevelDev& F = ctx->lev[l + 1];
@@ -238,13 +262,12 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
       double idx[3];
       level_idx(ctx, l, idx);
       // the fine advance just wrote its boundary fluxes and EMFs (when the fused kernel ran)
-      f.bnd = e.bnd = (ctx->opt_advance != 1 && a.bnd) ? a.bnd : nullptr;
+      f.bnd = e.bnd = bnd;
       ctx->ops->reg_fine_rc(f, e, idx, ctx->cfg.gamma, ctx->stream, nl);
     } else {
       ctx->ops->reg_fine(f, e, ctx->stream, nl);
     }
   }
-  ctx->cur[l] ^= 1;
 }
 
 void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl) {
@@ -328,7 +351,176 @@ void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled) {
 // the level-0 fill writes only level-0 ghosts, so with concurrency on the two
 // run side by side (both short, latency-bound kernels), joined before the
 // level-0 advance reads dt.
+// ----- the multi-level queue advance (AMRMHD_OPT_QUEUE)
+// A coarse step of L levels is 2^(L-1) batches, one per sub-step of the finest
+// level F. Level l's sub-step m (m < 2^l) spans the batches [m P_l, (m+1) P_l),
+// P_l = 2^(F-l): its fill runs before the first of them (coarse to fine: a
+// level's prolongation reads its parent's filled state; the finest level's
+// same-level copies are fill tasks of the launch), its advance tiles are split
+// into P_l equal shares, one per batch, and its registers and buffer flip
+// follow the last. Every batch is one queue launch: the finest level's fill
+// tasks, all of its tiles, then the shares of the coarser levels, finer first.
+// After the flips, fine to coarse, every level whose second sub-step ended is
+// refluxed and restricted. A level's advance reads only its filled state at
+// the sub-step's start and writes the other buffer, and its children read
+// only its state at that start (extended ghost zones), so this is the
+// recursive order's data flow (Sec. 4) and the results equal the level-by-level
+// launches bit for bit.
+bool queue_active(const amrmhd_ctx* ctx) {
+  const int nlev = ctx->H.nlev;
+  return ctx->opt_queue && ctx->fused() && ctx->opt_advance != 1 && ctx->opt_advance != 2 && !ctx->after_fill &&
+         !ctx->stage_light && nlev >= 2 && nlev <= amrk::QUEUE_MAX_LEVELS && (int)ctx->lev.size() == nlev;
+}
+
+static int substep_at(int l, int k, int F) { return l == 0 ? 1 : ((k >> (F - l)) & 1) + 1; }
+static bool starts_at(int l, int k, int F) { return k % (1 << (F - l)) == 0; }
+static bool ends_at(int l, int k, int F) { return (k + 1) % (1 << (F - l)) == 0; }
+
+amrmhd_status build_queue_plan(amrmhd_ctx* ctx) {
+  QueuePlan& Q = ctx->qplan;
+  const int var = ctx->opt_queue_tile == 2 ? 2 : 3;
+  if (Q.built && Q.variant == var && Q.withhold == (int)ctx->opt_queue_withhold) return AMRMHD_OK;
+  const amrmhd::Hierarchy& H = ctx->H;
+  const int nlev = H.nlev, F = nlev - 1, T = 1 << F;
+  const int np = (int)H.p.size();
+  const int TX = var == 2 ? 16 : 8, TY = 8;  // the tiles of variants 2 and 3
+  // the advance tiles of a sub-step of level l (w = 2: interior + 2 layers)
+  auto level_tiles = [&](int l, int w, std::vector<int32_t>& out) {
+    const int ntx = (ctx->lev[l].maxn[0] + 2 * w + TX - 1) / TX;
+    const std::vector<int>& ids = H.level_patches[l];
+    for (int i = 0; i < (int)ids.size(); ++i) {
+      const amrmhd::HPatch& P = H.p[ids[i]];
+      const int nx = (P.n[0] + 2 * w + TX - 1) / TX, ny = (P.n[1] + 2 * w + TY - 1) / TY;
+      for (int ty = 0; ty < ny; ++ty)
+        for (int tx = 0; tx < nx; ++tx) {
+          const int32_t rec[4] = {(F - l) << 4, i, ty * ntx + tx, ids[i]};
+          out.insert(out.end(), rec, rec + 4);
+        }
+    }
+  };
+  std::vector<int32_t> tasks;
+  std::vector<uint32_t> need((size_t)T * np, 0u);
+  Q.task_off.assign(T, 0);
+  Q.task_n.assign(T, 0);
+  Q.fill_in_queue.assign(T, 0);
+  const LevelDev& LF = ctx->lev[F];
+  std::vector<std::vector<int32_t>> cur_tiles(nlev);  // tiles of each level's current sub-step
+  for (int k = 0; k < T; ++k) {
+    const int64_t t0 = (int64_t)tasks.size() / 4;
+    Q.task_off[k] = t0;
+    for (int l = 0; l <= F; ++l)
+      if (starts_at(l, k, F)) {
+        const int s = substep_at(l, k, F);
+        cur_tiles[l].clear();
+        level_tiles(l, l == 0 ? 0 : (s == 1 ? 2 : 0), cur_tiles[l]);
+      }
+    // the finest level's same-level copies: ranges of at most 16 chunks into
+    // one patch, cell boxes (listed first) and face boxes apart
+    const bool fillq = !LF.has_bc;
+    Q.fill_in_queue[k] = fillq ? 1 : 0;
+    if (fillq) {
+      const int sF = substep_at(F, k, F);
+      const bool near = F == 0 || sF == 2;
+      const std::vector<int32_t>& ch = near ? LF.h_chunks2 : LF.h_chunks;
+      const std::vector<int32_t>& dst = near ? LF.h_dst2 : LF.h_dst;
+      const int64_t nsplit = near ? LF.runs2_split : LF.runs_split;
+      const int64_t nch = (int64_t)ch.size() / 4;
+      for (int64_t c = 0; c < nch;) {
+        const int d0 = dst[ch[4 * c]];
+        const bool cells = c < nsplit;
+        int64_t e = c + 1;
+        while (e < nch && e - c < 16 && dst[ch[4 * e]] == d0 && (e < nsplit) == cells) ++e;
+        const int32_t rec[4] = {1 | (cells ? 2 : 0), (int32_t)c, (int32_t)e, d0};
+        tasks.insert(tasks.end(), rec, rec + 4);
+        need[(size_t)k * np + d0] += 1u;
+        c = e;
+      }
+    }
+    // advance tiles, finest level first: share j of P_l of each level's sub-step
+    for (int l = F; l >= 0; --l) {
+      const int64_t P = 1 << (F - l), j = k % P, n = (int64_t)cur_tiles[l].size() / 4;
+      const int64_t a = n * j / P, b = n * (j + 1) / P;
+      tasks.insert(tasks.end(), cur_tiles[l].begin() + 4 * a, cur_tiles[l].begin() + 4 * b);
+    }
+    Q.task_n[k] = (int)((int64_t)tasks.size() / 4 - t0);
+  }
+  // test switch: the first patch of the finest level waits in the first batch
+  // for one fill task more than exist, so its wait runs out
+  if (ctx->opt_queue_withhold) need[H.level_patches[F].front()] += 1u;
+  cudaError_t e = cudaSuccess;
+  Q.d_tasks = dbuf<int>(ctx, tasks.size(), &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  Q.d_need = dbuf<unsigned int>(ctx, need.size(), &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  Q.d_ctr = dbuf<unsigned int>(ctx, (size_t)np + 2, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  CU(cudaMemcpy(Q.d_tasks, tasks.data(), sizeof(int32_t) * tasks.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(Q.d_need, need.data(), sizeof(uint32_t) * need.size(), cudaMemcpyHostToDevice));
+  Q.variant = var;
+  Q.withhold = (int)ctx->opt_queue_withhold;
+  Q.built = true;
+  return AMRMHD_OK;
+}
+
+void op_coarse_step_queue(amrmhd_ctx* ctx, int* nl) {
+  const QueuePlan& Q = ctx->qplan;
+  const int nlev = ctx->H.nlev, F = nlev - 1, T = 1 << F;
+  const int np = (int)ctx->H.p.size();
+  const int TX = Q.variant == 2 ? 16 : 8;
+  op_cfl(ctx, ctx->d_hist, nl);
+  for (int k = 0; k < T; ++k) {
+    for (int l = 0; l <= F; ++l) {
+      if (!starts_at(l, k, F)) continue;
+      const int s = substep_at(l, k, F);
+      if (l < F || !Q.fill_in_queue[k]) {
+        op_fill(ctx, l, s, nl);
+      } else {
+        ctx->start[l] = ctx->cur[l];
+        op_fill_rest(ctx, l, s, nl);
+      }
+    }
+    amrk::QueueArgs q;
+    std::memset(&q, 0, sizeof(q));
+    for (int l = 0; l <= F; ++l) {
+      const int s = substep_at(l, k, F), w = l == 0 ? 0 : (s == 1 ? 2 : 0);
+      const LevelDev& L = ctx->lev[l];
+      amrk::QueueLevel& QL = q.L[F - l];
+      QL.a = level_args(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), w);
+      QL.ntx = (L.maxn[0] + 2 * w + TX - 1) / TX;
+      const bool near = l == 0 || s == 2;
+      QL.boxes = near ? L.runs2.p : L.runs.p;
+      QL.chunks = near ? L.chunk_runs2.p : L.chunk_runs.p;
+    }
+    q.tasks = Q.d_tasks + 4 * Q.task_off[k];
+    q.ntasks = Q.task_n[k];
+    q.need = Q.d_need + (size_t)k * np;
+    q.done = Q.d_ctr;
+    q.head = Q.d_ctr + np;
+    q.abort = (int*)(Q.d_ctr + np + 1);
+    q.err = ctx->d_err;
+    q.wait_ns = 500000000ull;  // 0.5 s
+    cudaMemsetAsync(Q.d_ctr, 0, sizeof(unsigned int) * ((size_t)np + 2), ctx->stream);
+    ctx->ops->advance_queue(q, Q.variant, ctx->stream, nl);
+    // levels whose sub-step ends with this batch: registers, then the flip
+    for (int l = F; l >= 0; --l) {
+      if (!ends_at(l, k, F)) break;
+      op_level_registers(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), substep_at(l, k, F), q.L[F - l].a.bnd, nl);
+      ctx->cur[l] ^= 1;
+    }
+    // levels whose second sub-step ended, fine to coarse
+    for (int l = F; l >= 1; --l) {
+      const int per = 1 << (F - l);
+      if ((k + 1) % per != 0 || (((k + 1) / per) & 1) != 0) break;
+      op_reflux_restrict(ctx, l, nl);
+    }
+  }
+}
+
 void op_coarse_step(amrmhd_ctx* ctx, int* nl) {
+  if (queue_active(ctx)) {
+    op_coarse_step_queue(ctx, nl);
+    return;
+  }
   if (ctx->opt_concurrent && ctx->cfl_stream && !ctx->after_fill) {
     cudaStream_t main = ctx->stream;
     cudaEventRecord(ctx->ev_cfl_fork, main);
@@ -461,6 +653,9 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else if (option == AMRMHD_OPT_HOST_IO && (value == 0 || value == 1)) ctx->opt_host_io = value;
   else if (option == AMRMHD_OPT_DIRECT_HALO && (value == 0 || value == 1)) ctx->opt_direct_halo = value;
+  else if (option == AMRMHD_OPT_QUEUE && (value == 0 || value == 1)) ctx->opt_queue = value;
+  else if (option == AMRMHD_OPT_QUEUE_TILE && (value == 2 || value == 3)) ctx->opt_queue_tile = value;
+  else if (option == AMRMHD_OPT_QUEUE_WITHHOLD && (value == 0 || value == 1)) ctx->opt_queue_withhold = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -658,9 +853,11 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     // box's nx, ny, the number of fields, cx = min(nx, 64) and the multipliers
     // of the lane -> (x, row) and row -> (y, z) divisions; chunks (box, x0,
     // q0, nrows) of whole rows q = y + ny z of cx positions
-    auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
+    auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch,
+                       std::vector<int32_t>& dst) {
       // every listed box has a chunk: a range of k chunks spans at most k boxes
       if (b[7] <= 0 || b[8] <= 0 || b[9] <= 0) return;
+      dst.push_back(b[0]);
       const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
       const long long Ld = b[4] + (long long)D.ext[0] * (b[5] + (long long)D.ext[1] * b[6]);
       const long long Ls = (b[4] + b[10]) + (long long)S.ext[0] * ((b[5] + b[11]) + (long long)S.ext[1] * (b[6] + b[12]));
@@ -705,8 +902,8 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
         int32_t nb[amrmhd::GHOST_BOX_W];
         const bool near = clip_near(b, nb);
         if (b[2] == 0) {
-          add_run(b, rr, cr);
-          if (near) add_run(nb, rr2, cr2);
+          add_run(b, rr, cr, L.h_dst);
+          if (near) add_run(nb, rr2, cr2, L.h_dst2);
         } else if (b[2] == 1) {
           add_box(b, faces ? pfb : pcb, faces ? pfc : pcc);
         } else {
@@ -726,6 +923,9 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
         prev = b;
       }
     }
+    L.h_chunks = cr;
+    L.h_chunks2 = cr2;
+    L.has_bc = !bcb.empty() || !bfb.empty();
     const int GW = amrmhd::GHOST_BOX_W;
     bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 4) &&
               upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
@@ -747,11 +947,12 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       L.cf_face0 = H.rng_cf_faces[l][0];
       L.cf_edge0 = H.rng_cf_edges[l][0];
     }
-    // direct halo reads: a 3D level without a finer level whose equal patches
-    // tile the periodic domain (so every halo position lies in the interior
-    // of the neighbour patch in the patch grid, at a shift of one patch)
+    // direct halo reads: the 3D base level of a one-level hierarchy whose
+    // equal patches tile the periodic domain (every halo position lies in the
+    // interior of the neighbour patch in the patch grid, at a shift of one
+    // patch; every advance of the level updates the interior only, w = 0)
     L.direct_halo = false;
-    if (H.dim == 3 && l == nlev - 1 && !ctx->stage_light && !ids.empty()) {
+    if (H.dim == 3 && l == 0 && nlev == 1 && !ctx->stage_light && !ids.empty()) {
       bool periodic = true;
       for (int d = 0; d < 3; ++d)
         for (int side = 0; side < 2; ++side) periodic = periodic && ctx->cfg.bc[d][side] == AMRMHD_BC_PERIODIC;
@@ -1062,6 +1263,10 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
   if (n_coarse < 0) return fail(ctx, AMRMHD_EINVAL, "negative step count");
   if (n_coarse == 0) return AMRMHD_OK;
   const int nlev = ctx->H.nlev;
+  if (queue_active(ctx)) {
+    st = build_queue_plan(ctx);
+    if (st) return st;
+  }
   for (int32_t done = 0; done < n_coarse;) {
     const int32_t chunk = (int32_t)std::min<int64_t>(kHistCap, n_coarse - done);
     CU(cudaMemsetAsync(ctx->d_slots + nlev, 0, sizeof(unsigned long long), ctx->stream));
@@ -1112,6 +1317,8 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
   CU(cudaStreamSynchronize(ctx->stream));
   if (err) {
     CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    if (err & amrk::ERR_QUEUE_TIMEOUT)
+      return fail(ctx, AMRMHD_ETIMEOUT, "a wait of the queue advance ran out (a fill signal never came)");
     return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
   }
   return AMRMHD_OK;

@@ -39,11 +39,32 @@ struct LevelDev {
   DevList row_same_cells, row_same_faces, row_prol_cells, row_prol_faces, row_bc_cells, row_bc_faces;
   DevList cf_faces, cf_edges, emf_faces, restrict_cells, restrict_faces, reflux_cells;  // this level as fine level
   int64_t cf_face0 = 0, cf_edge0 = 0;  // global row offsets of this level's register rows
-  // a 3D level of equal patches that tiles the periodic domain and has no finer
-  // level: the fused advance reads its halo from the neighbour patches (27 ids
-  // per patch, in the order of ids) and the level's same-level fill is skipped
+  // the 3D base level of a one-level hierarchy whose equal patches tile the
+  // periodic domain: the fused advance reads its halo from the neighbour
+  // patches (27 ids per patch, in the order of ids) and the level's same-level
+  // fill is skipped
   DevList nbr;
   bool direct_halo = false;
+  // host copies for the queue advance's fill tasks: the chunk lists of the
+  // same-level boxes (4 ints per chunk; full and 2-cells-deep) and each box's
+  // destination patch; has_bc: the level has physical-boundary boxes (filled
+  // after its same-level copies, so its fill stays outside the queue)
+  std::vector<int32_t> h_chunks, h_chunks2, h_dst, h_dst2;
+  bool has_bc = false;
+};
+
+// The queue advance's plan of one hierarchy: per batch k of a coarse step (the
+// levels whose sub-steps start at finest sub-step k), its task list and the
+// expected fill count per patch; counters shared by the batches.
+struct QueuePlan {
+  bool built = false;
+  int variant = 3, withhold = 0;
+  std::vector<int64_t> task_off;  // per batch: first task
+  std::vector<int> task_n;        // per batch: task count
+  std::vector<int> fill_in_queue; // per batch: 1 if the finest level's same-level fill is in the queue
+  int* d_tasks = nullptr;         // 4 ints per task
+  unsigned int* d_need = nullptr; // batch x npatch
+  unsigned int* d_ctr = nullptr;  // done[npatch], head, abort
 };
 
 struct AdjWork;  // discrete-adjoint workspace (adjoint.cu)
@@ -65,6 +86,10 @@ struct amrmhd_ctx {
   int variant = amrk::V_FP64;
   const amrk::Ops* ops = nullptr;
   int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1, opt_host_io = 0, opt_direct_halo = 1;
+  // the multi-level queue advance: on/off, its tile variant (2: 16x8, 3: 8x8),
+  // and a test switch that withholds one fill signal (the wait times out)
+  int64_t opt_queue = 0, opt_queue_tile = 3, opt_queue_withhold = 0;
+  amrapi::QueuePlan qplan;
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;
@@ -129,6 +154,9 @@ amrk::RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level);
 void offset_regs(amrmhd_ctx* ctx, amrk::RowArgs& a, int l);
 void level_idx(amrmhd_ctx* ctx, int l, double* idx);
 void op_fill(amrmhd_ctx* ctx, int l, int s, int* nl);
+void op_fill_same(amrmhd_ctx* ctx, int l, int s, int* nl);
+void op_fill_rest(amrmhd_ctx* ctx, int l, int s, int* nl);
+void op_level_registers(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, void* bnd, int* nl);
 void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s, int* nl);
 void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl);
 void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled = false);

@@ -78,6 +78,31 @@ struct RowArgs {
   const void* bnd;
 };
 
+// Device work queue of the multi-level advance (k_advance_queue): one launch
+// advances the levels whose sub-steps start together in the recursive order.
+constexpr int QUEUE_MAX_LEVELS = 12;
+constexpr unsigned ERR_QUEUE_TIMEOUT = 4u;  // error-word bit: a queue wait gave up
+struct QueueLevel {
+  LevelArgs a;          // the level's advance (buffers, dt, w, boundary capture)
+  int ntx;              // tiles along x of the queue's tile variant for this level
+  const int* boxes;     // same-level copy boxes of the sub-step (fill tasks)
+  const int* chunks;    // their chunks (4 ints each)
+};
+struct QueueArgs {
+  QueueLevel L[QUEUE_MAX_LEVELS];
+  // tasks (4 ints): fill (code = slot << 4 | 1 | 2 for cell boxes, first
+  // chunk, end chunk, destination patch id) or advance tile (code = slot << 4,
+  // patch position in L[slot].a.ids, tile, patch id), in ticket order
+  const int* tasks;
+  int ntasks;
+  const unsigned int* need;  // per patch id: fill tasks into it in this launch
+  unsigned int* done;        // per patch id: fill tasks finished (zeroed before the launch)
+  unsigned int* head;        // next ticket (zeroed before the launch)
+  int* abort;                // set when a wait gave up (zeroed before the launch)
+  unsigned int* err;         // the context's error word
+  unsigned long long wait_ns;  // limit of one wait
+};
+
 struct CflArgs {
   const DPatch* P;
   const int* ids;
@@ -152,6 +177,8 @@ struct Ops {
   void (*transfer_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*transfer_faces)(const RowArgs&, cudaStream_t, int* launches);
   void (*closure)(const RowArgs&, cudaStream_t, int* launches);
+  // the multi-level queue advance (3D fused path); variant: 2 (16x8) or 3 (8x8)
+  void (*advance_queue)(const QueueArgs&, int variant, cudaStream_t, int* launches);
 };
 
 const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED

@@ -447,12 +447,100 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   }
 }
 
-// FP32 tiles of 256 threads keep two CTAs per SM (<= 128 registers a thread).
+// CTAs per SM of the FP32 tiles of 256 threads: two for the larger tiles
+// (shared memory), three for the 8x8 tile (80 registers a thread, no spills)
+template <int VAR> constexpr int fused_ctas_fp32() { return FusedCfg<VAR>::NT != 256 ? 1 : (VAR == 3 ? 3 : 2); }
 template <class T, int VAR, int MODE>
-__global__ void __launch_bounds__(FusedCfg<VAR>::NT, (sizeof(T) == 4 && FusedCfg<VAR>::NT == 256) ? 2 : 1)
+__global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? fused_ctas_fp32<VAR>() : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fused_tile<T, VAR, MODE>(a, blockIdx.y, blockIdx.x, ntx, smem_raw);
+}
+
+// ---------------------------------------------------------------- device work queue
+// The multi-level advance as persistent launches (the GPU analogue of the
+// paper's threaded level advances with preference to the finer levels, Sec. 4):
+// one launch per sub-step of the finest level; the resident CTAs take tasks in
+// ticket order from an atomic counter over a host-ordered list. Fill tasks (a
+// range of same-level copy chunks into one patch, the finest level's) come
+// first, then the advance tiles, finest level first: all of the finest
+// level's, then a share of every coarser level's (a coarser level's advance
+// is spread over the launches of its sub-step). An advance tile waits until every fill task into its patch has
+// finished (a per-patch counter against the expected count). A wait only ever
+// concerns tasks of smaller tickets, which running CTAs hold and finish
+// without waiting, so every wait ends; each is bounded in time all the same:
+// on expiry the CTA sets ERR_QUEUE_TIMEOUT in the error word and the abort
+// flag, and every CTA stops taking tasks (no wait is left in flight: the CTA
+// holds no asynchronous copies while it waits).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <class T, int VAR>
+__global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? 2 : 1)
+    k_advance_queue(const __grid_constant__ QueueArgs q) {
+  static_assert(FusedCfg<VAR>::NT == FILL_RUN_TPB, "the fill tasks use the CTA's threads as k_fill_runs does");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int4 s_task;
+  __shared__ int s_go;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int4 t = make_int4(-1, 0, 0, 0);
+      if (!(*(volatile unsigned int*)q.err & ERR_QUEUE_TIMEOUT) && !*(volatile int*)q.abort) {
+        const unsigned int k = atomicAdd(q.head, 1u);
+        if (k < (unsigned int)q.ntasks) t = reinterpret_cast<const int4*>(q.tasks)[k];
+      }
+      s_task = t;
+    }
+    __syncthreads();
+    const int4 t = s_task;
+    if (t.x < 0) return;
+    const QueueLevel& L = q.L[t.x >> 4];
+    if (t.x & 1) {
+      // fill task: the chunk range [t.y, t.z) of the level's same-level boxes
+      int4* sch = reinterpret_cast<int4*>(smem_raw);
+      T* B = (T*)L.a.cur;
+      const int4* ch = reinterpret_cast<const int4*>(L.chunks);
+      if (t.x & 2) fill_range<T, 5, 2>(B, L.boxes, ch, t.y, t.z, sch, sch + FILL_TILE);
+      else fill_range<T, 1, 4>(B, L.boxes, ch, t.y, t.z, sch, sch + FILL_TILE);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(q.done + t.w, 1u);
+      }
+    } else {
+      // advance tile: first every fill into its patch
+      if (threadIdx.x == 0) {
+        int go = 1;
+        const unsigned int need = q.need[t.w];
+        if (need) {
+          const unsigned long long t0 = global_ns();
+          while (load_acquire(q.done + t.w) < need) {
+            if (*(volatile int*)q.abort) { go = 0; break; }
+            if (global_ns() - t0 > q.wait_ns) {
+              atomicOr(q.err, ERR_QUEUE_TIMEOUT);
+              atomicExch(q.abort, 1);
+              go = 0;
+              break;
+            }
+            __nanosleep(128);
+          }
+          __threadfence();
+        }
+        s_go = go;
+      }
+      __syncthreads();
+      if (s_go) fused_tile<T, VAR, 1>(L.a, t.y, t.z, L.ntx, smem_raw);
+    }
+    __syncthreads();  // the task's shared memory is free for the next one
+  }
 }
 
 // ------------------------------------------------------------------ register recompute

@@ -1080,6 +1080,28 @@ template <class T, int DIM> struct Impl {
   }
   static void prepare() {
     if (DIM == 3) { prepare_v<0>(); prepare_v<1>(); prepare_v<2>(); prepare_v<3>(); prepare_v<4>(); }
+    if (DIM == 3) {
+      if (fused_fits<2>())
+        cudaFuncSetAttribute(k_advance_queue<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<2>());
+      cudaFuncSetAttribute(k_advance_queue<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem<3>());
+    }
+  }
+  // the queue advance: a persistent grid of the resident CTAs
+  template <int V> static void launch_queue(const QueueArgs& q, cudaStream_t s) {
+    static const int resident = [] {
+      int dev = 0, sms = 152, per = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_advance_queue<T, V>, FusedCfg<V>::NT, fused_smem<V>());
+      return sms * (per > 0 ? per : 1);
+    }();
+    k_advance_queue<T, V><<<resident, FusedCfg<V>::NT, fused_smem<V>(), s>>>(q);
+  }
+  static void advance_queue(const QueueArgs& q, int variant, cudaStream_t s, int* nl) {
+    if (DIM != 3 || q.ntasks <= 0) return;
+    if (variant == 2 && fused_fits<2>()) launch_queue<2>(q, s);
+    else launch_queue<3>(q, s);
+    if (nl) ++*nl;
   }
   template <int V> static void launch_fused(const LevelArgs& a, cudaStream_t s) {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
@@ -1125,7 +1147,7 @@ template <class T, int DIM> struct Impl {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           io_all, sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
-                          transfer_faces, closure};
+                          transfer_faces, closure, advance_queue};
     return &o;
   }
 };
