@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--n", type=int, default=128)
     p.add_argument("--psize", type=int, default=16)
     p.add_argument("--skip-extras", action="store_true", help="headline only (no FP64/baseline/e2e/oracle legs)")
-    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error", "cylinder"],
+    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error", "cylinder", "weakscale"],
                    help="run one extra leg alone and print its JSON (for profiling)")
     p.add_argument("--leg-steps", type=int, default=None, help="coarse steps of the --leg run")
     return p.parse_args()
@@ -281,6 +281,10 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     ctx.set_option(A.OPT_QUEUE, 1)
     ctx.step(1, want_dt=False)
     ms_q, _ = timed_steps(ctx, stream, 2)
+    ctx.set_option(A.OPT_QUEUE_BALANCE, 0)
+    ctx.step(1, want_dt=False)
+    ms_q0, _ = timed_steps(ctx, stream, 2)
+    ctx.set_option(A.OPT_QUEUE_BALANCE, 1)
     ctx.set_option(A.OPT_QUEUE, 0)
     cells = {}
     for (l, lo, hi) in ctx.get_patches():
@@ -293,7 +297,8 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
                                    zip(("flag", "cluster", "build", "transfer", "build_host_maps"), breakdown)},
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
            "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
-           "final_hierarchy_ms_per_step": {"side_streams": ms_c / 2, "serial": ms_s / 2, "device_queue": ms_q / 2},
+           "final_hierarchy_ms_per_step": {"side_streams": ms_c / 2, "serial": ms_s / 2, "device_queue": ms_q / 2,
+                                           "device_queue_equal_shares": ms_q0 / 2},
            "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}
     del ctx
     torch.cuda.empty_cache()
@@ -351,6 +356,8 @@ def shock_clump_leg(steps=10, theta=0.1):
     stream = torch.cuda.Stream()
     cfg = A.make_config(3, pb.base, precision=A.MIXED, gamma=pb.gamma, cfl=pb.cfl, bc=pb.bc, inflow=pb.inflow)
     ctx = A.Context(cfg, stream.cuda_stream)
+    # floors of 1e-8 of the ambient density and pressure (both 1)
+    ctx.set_floors(1e-8, 1e-8)
     ctx.set_hierarchy(pb.patches)
     ctx.alloc_arena()
     torch.cuda.synchronize()
@@ -372,6 +379,7 @@ def shock_clump_leg(steps=10, theta=0.1):
            "steps": steps, "ms_per_step": ms / steps,
            "cells_per_level": [cells[l] for l in sorted(cells)], "patches": ctx.query(A.Q_NPATCH),
            "arena_gb": ctx.query(A.Q_ARENA_BYTES) / 1e9, "regrid_s": t_regrid,
+           "floors": {"rho": 1e-8, "p": 1e-8, "raises": ctx.query(A.Q_FLOOR_EVENTS)},
            "regrid_host_us": {k: ctx.query(A.Q_REGRID_FLAG_US + i)
                               for i, k in enumerate(("flag", "cluster", "build", "transfer"))},
            "tiles": tiles,
@@ -379,6 +387,48 @@ def shock_clump_leg(steps=10, theta=0.1):
                        "clump r 0.15; B (sqrt2,0,0); inflow x-low, outflow elsewhere; mixed precision"}
     del ctx
     torch.cuda.empty_cache()
+    return out
+
+
+def weak_scale_leg(steps=10, unit_sms=16):
+    """The paper's weak-scaling experiment (Sec. 6: the advected magnetized
+    cylinder with one refined level at 12.5 % filling, 64^3 base cells per
+    processor) on SM partitions of one GPU: P = 1, 2, 4, 8 work units (unit
+    cubes, each with its cylinder and refined level) advanced on a partition
+    of P x unit_sms SMs (a green context, amrmhd_sm_partition_create), mixed
+    precision, one stream, CUDA events on the partition's stream. Efficiency
+    = time per coarse step at P = 1 / time at P (work and SMs both grow P-fold)."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    out = {"unit": "64^3 base + refined central eighth (12.5 %)", "unit_sms": unit_sms, "runs": []}
+    t1 = None
+    for P, reps in ((1, (1, 1, 1)), (2, (2, 1, 1)), (4, (2, 2, 1)), (8, (2, 2, 2))):
+        pb = inputs.cylinder_3d_tiled(reps, 64, 16)
+        part = A.SmPartition(P * unit_sms)
+        ext = torch.cuda.ExternalStream(part.stream)
+        ctx = A.context_for(pb, precision=A.MIXED, stream=part.stream)
+        ctx.set_option(A.OPT_CONCURRENT, 0)
+        ctx.alloc_arena()
+        torch.cuda.synchronize()
+        ctx.load_state(pb.state)
+        ctx.autotune(2)
+        ctx.step(2, want_dt=False)
+        per = ctx.query(A.Q_CELL_UPDATES_PER_STEP)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ext)
+        ctx.step(steps, want_dt=False)
+        e1.record(ext)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        t1 = ms if t1 is None else t1
+        out["runs"].append({"units": P, "sms": part.sms, "ms_per_step": ms, "cell_updates_per_s": per / (ms / 1e3),
+                            "per_sm": per / (ms / 1e3) / part.sms, "efficiency": t1 / ms})
+        del ctx
+        torch.cuda.synchronize()
+        part.close()
+        torch.cuda.empty_cache()
     return out
 
 
@@ -429,8 +479,13 @@ def adjoint_leg(steps=200, ckpt=20):
         ctx.backward(dts, g, g0, ckpt)
         t_bwd = time.perf_counter() - t0
         per = pb.cells_per_coarse_step()
+        # the configuration's control: the gradient with respect to the initial
+        # velocity (rho, p and B held), from dL/dU0
+        from paper_1110_1616_gb300.autograd import velocity_gradient
+        gv = velocity_gradient(u0, g0, ctx.packed_size(0))
         out[name] = {"forward_cell_updates_per_s": per * steps / t_fwd, "forward_s": t_fwd, "backward_s": t_bwd,
-                     "backward_over_forward": t_bwd / t_fwd, "grad_norm": float(g0.norm())}
+                     "backward_over_forward": t_bwd / t_fwd, "grad_norm": float(g0.norm()),
+                     "grad_v0_norm": float(gv.norm())}
         del ctx
         torch.cuda.empty_cache()
     return out
@@ -540,7 +595,7 @@ def main():
         if args.leg == "adjoint" and args.leg_steps is not None:
             kw["ckpt"] = max(1, args.leg_steps // 2)
         fn = {"adjoint": adjoint_leg, "deep": deep_amr_leg, "shockclump": shock_clump_leg,
-              "error": mixed_error_leg, "cylinder": cylinder_leg}[args.leg]
+              "error": mixed_error_leg, "cylinder": cylinder_leg, "weakscale": weak_scale_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(**kw) if args.leg != "error" else fn()}), flush=True)
         return
@@ -612,6 +667,7 @@ def main():
         extras["adjoint_2d"] = adjoint_leg()
         extras["shock_clump3d"] = shock_clump_leg()
         extras["cylinder3d_paper_shape"] = cylinder_leg()
+        extras["weak_scaling_sm_partitions"] = weak_scale_leg()
     e2e = None
     if not args.skip_extras:
         ke = max(10, args.steps // 4)

@@ -270,6 +270,19 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
 amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
                               const double* dL_dUfinal, double* dL_dU0);
 
+/* The gradient with respect to the initial velocity (the configuration's
+ * control: the adjoint of the level advance gives dL/dU0; the paper has no
+ * adjoint, and the chain rule here is this library's reading: rho, p and B are
+ * held while v varies). From the packed initial state u0 and dL/dU0 (DEVICE
+ * arrays in the amrmhd_backward layout; only the cell fields rho, mx, my, mz,
+ * E are read: the first 5 packed fields, ncells entries each) it writes
+ * dL_dv0 (DEVICE, 3 packed cell fields vx, vy, vz, ncells each):
+ * dL/dv_c = rho (dL/dm_c + v_c dL/dE), v = m / rho. Stream-ordered on
+ * cuda_stream (NULL: the legacy default stream). AMRMHD_EINVAL for bad
+ * arguments, AMRMHD_ECUDA if the launch fails. */
+amrmhd_status amrmhd_grad_velocity(int64_t ncells, const double* u0, const double* dL_dU0, double* dL_dv0,
+                                   void* cuda_stream);
+
 /* The local transposed Jacobians that amrmhd_backward applies at every face
  * and cell, exposed for verification: gx = J^T g at n points, FP64, one point
  * per row, all arrays HOST, row-major.
@@ -379,9 +392,23 @@ enum {
   AMRMHD_Q_REGRID_TRANSFER_US = 9,
   /* of AMRMHD_Q_REGRID_BUILD_US, the host building of hierarchies and maps
    * (the rest is device memory and map upload) */
-  AMRMHD_Q_REGRID_MAPS_US = 10
+  AMRMHD_Q_REGRID_MAPS_US = 10,
+  /* raises by the density and pressure floors since bind_arena (amrmhd_set_floors);
+   * synchronises the stream */
+  AMRMHD_Q_FLOOR_EVENTS = 11
 };
 amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value);
+
+/* Density and pressure floors (0, 0: off, the default). The paper is silent on
+ * floors; the reading for strong shocks: every recovery of the advance and the
+ * CFL reduction raises a density below rho_min to rho_min before forming the
+ * velocity and pressure, then a pressure below p_min to p_min, counting every
+ * raise (AMRMHD_Q_FLOOR_EVENTS). Floors act on the primitives only, so where
+ * they act the advance is not conservative; they are never needed in smooth
+ * problems. amrmhd_backward refuses to run with floors set (AMRMHD_ESTATE).
+ * AMRMHD_EINVAL for negative or non-finite values. Captured graphs are
+ * rebuilt at the next step. */
+amrmhd_status amrmhd_set_floors(amrmhd_ctx* ctx, double rho_min, double p_min);
 
 /* Options (set before set_hierarchy): AMRMHD_OPT_* */
 enum {
@@ -419,10 +446,15 @@ enum {
                               AMRMHD_ETIMEOUT). Results equal the level-by-level launches. 0 (default):
                               per-level launches, finer levels on side streams. */
   AMRMHD_OPT_QUEUE_TILE = 7, /* tile of the queue's advance tasks: 3 (default) 8x8, 2 16x8 */
-  AMRMHD_OPT_QUEUE_WITHHOLD = 8 /* test switch, 0 (default) or 1: the first patch of the finest level waits
-                              in the first batch of a coarse step for one fill task more than exist,
-                              so the wait runs out (after 0.5 s) and amrmhd_step returns
+  AMRMHD_OPT_QUEUE_WITHHOLD = 8, /* test switch, 0 (default) or 1: the first patch of the finest level
+                              waits in the first batch of a coarse step for one fill task more than
+                              exist, so the wait runs out (after 0.5 s) and amrmhd_step returns
                               AMRMHD_ETIMEOUT; the device stays usable */
+  AMRMHD_OPT_QUEUE_BALANCE = 9 /* how a coarser level's advance tiles are shared out over the queue
+                              launches of its sub-step: 1 (default) so that every launch's predicted
+                              total work (the finer levels' tiles included) reaches one common level,
+                              the paper's load balancing (Sec. 5) with the launches of a coarse step
+                              as its processors; 0 equal numbers of tiles per launch */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 
@@ -440,6 +472,24 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles);
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx);
+
+/* SM partitions, for the single-GPU analogue of the paper's weak-scaling
+ * experiment (Sec. 6: the work per processor fixed while processors are
+ * added). amrmhd_sm_partition_create makes a stream of the current device whose
+ * kernels run only on one group of at least sm_count SMs (a green context of
+ * the CUDA driver; the group is rounded up to the device's partition
+ * granularity): *sms receives the group's SM count, *stream the stream (pass it
+ * to amrmhd_create and set AMRMHD_OPT_CONCURRENT to 0, so that no work of the
+ * context leaves it), *handle the partition. amrmhd_sm_partition_destroy
+ * synchronises and releases the stream and the partition (contexts using the
+ * stream must be destroyed first). Device memory allocated outside the
+ * partition (the arena) is used as is. Errors: AMRMHD_EINVAL for bad arguments
+ * or a count above the device's SMs, AMRMHD_ECUDA if a driver call fails. */
+amrmhd_status amrmhd_sm_partition_create(int32_t sm_count, void** stream, int32_t* sms, void** handle);
+amrmhd_status amrmhd_sm_partition_destroy(void* handle);
+/* The calling thread's last failure of amrmhd_sm_partition_create (the step
+ * that failed and its driver code), "" if none. */
+const char* amrmhd_sm_partition_error(void);
 
 /* Advance of ONE patch that allocates no device memory (no counterpart in the
  * paper: it exists for callers that cannot call cudaMalloc, e.g. code running

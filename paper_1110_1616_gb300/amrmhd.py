@@ -20,8 +20,9 @@ MAPS = {
 }
 Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LAUNCHES = range(6)
 Q_REGRID_FLAG_US, Q_REGRID_CLUSTER_US, Q_REGRID_BUILD_US, Q_REGRID_TRANSFER_US, Q_REGRID_MAPS_US = range(6, 11)
+Q_FLOOR_EVENTS = 11
 OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT, OPT_HOST_IO, OPT_DIRECT_HALO = 0, 1, 2, 3, 4, 5
-OPT_QUEUE, OPT_QUEUE_TILE, OPT_QUEUE_WITHHOLD = 6, 7, 8
+OPT_QUEUE, OPT_QUEUE_TILE, OPT_QUEUE_WITHHOLD, OPT_QUEUE_BALANCE = 6, 7, 8, 9
 
 
 class AmrmhdError(RuntimeError):
@@ -87,6 +88,10 @@ def lib():
             "amrmhd_fp_convert": [i32, i64, vp, vp, vp, vp, vp, vp],
             "amrmhd_recover_mixed": [i64, vp, vp, vp, dbl, vp],
             "amrmhd_alu_peak": [i32, C.POINTER(dbl), C.POINTER(i32)],
+            "amrmhd_set_floors": [vp, dbl, dbl],
+            "amrmhd_grad_velocity": [i64, vp, vp, vp, vp],
+            "amrmhd_sm_partition_create": [i32, C.POINTER(vp), C.POINTER(i32), C.POINTER(vp)],
+            "amrmhd_sm_partition_destroy": [vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -94,6 +99,8 @@ def lib():
             f.restype = C.c_int
         L.amrmhd_advance_patch_noalloc.argtypes = [vp, vp, i32, C.POINTER(i32), C.POINTER(dbl), dbl, dbl, i32, vp]
         L.amrmhd_advance_patch_noalloc.restype = C.c_int
+        L.amrmhd_sm_partition_error.argtypes = []
+        L.amrmhd_sm_partition_error.restype = C.c_char_p
         L.amrmhd_last_error.argtypes = [vp]
         L.amrmhd_last_error.restype = C.c_char_p
         _lib = L
@@ -147,6 +154,25 @@ def alu_peak(fp64=False):
     if st != 0:
         raise RuntimeError("amrmhd_alu_peak failed: status %d" % st)
     return v.value, n.value
+
+
+class SmPartition:
+    """A stream whose kernels run on one group of at least sm_count SMs
+    (amrmhd_sm_partition_create); .stream is the cudaStream_t handle, .sms the
+    group's SM count. close() releases it."""
+
+    def __init__(self, sm_count):
+        s, h, n = C.c_void_p(), C.c_void_p(), C.c_int32(0)
+        st = lib().amrmhd_sm_partition_create(int(sm_count), C.byref(s), C.byref(n), C.byref(h))
+        if st != 0:
+            raise AmrmhdError(st, "amrmhd_sm_partition_create(%d): %s"
+                              % (sm_count, lib().amrmhd_sm_partition_error().decode()))
+        self.stream, self.sms, self._h = s.value, n.value, h
+
+    def close(self):
+        if self._h:
+            lib().amrmhd_sm_partition_destroy(self._h)
+            self._h = None
 
 
 def recover_mixed(u, bl, br, gamma=5.0 / 3.0):
@@ -418,6 +444,9 @@ class Context:
 
     def set_option(self, opt, value):
         self._check(lib().amrmhd_set_option(self.h, opt, value), "set_option")
+
+    def set_floors(self, rho_min, p_min):
+        self._check(lib().amrmhd_set_floors(self.h, float(rho_min), float(p_min)), "set_floors")
 
     def export_map(self, which):
         if isinstance(which, str):

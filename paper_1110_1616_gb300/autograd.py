@@ -49,3 +49,17 @@ class AdvanceFunction(torch.autograd.Function):
 def advance(ctx: "A.Context", u0: torch.Tensor, dts, ckpt_every: int = 20) -> torch.Tensor:
     """Differentiable len(dts) coarse steps of ctx from the packed state u0."""
     return AdvanceFunction.apply(u0, ctx, dts, ckpt_every)
+
+
+def velocity_gradient(u0: torch.Tensor, g0: torch.Tensor, ncells: int) -> torch.Tensor:
+    """dL/dv0 (3 packed cell fields vx, vy, vz) from the packed initial state u0
+    and dL/dU0 = the backward's output, with rho, p and B held
+    (amrmhd_grad_velocity); ncells = the packed count of one cell field."""
+    gv = torch.empty(3 * ncells, dtype=torch.float64, device=u0.device)
+    torch.cuda.synchronize()
+    st = A.lib().amrmhd_grad_velocity(int(ncells), A.C.c_void_p(u0.data_ptr()), A.C.c_void_p(g0.data_ptr()),
+                                      A.C.c_void_p(gv.data_ptr()), None)
+    if st != 0:
+        raise RuntimeError("amrmhd_grad_velocity failed: status %d" % st)
+    torch.cuda.synchronize()
+    return gv

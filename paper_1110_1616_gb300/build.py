@@ -21,6 +21,7 @@ UNITS = [
     # dual numbers) and must take the same branches as the strict FP64 forward
     ("adjoint.cu", ["--fmad=false"]),
     ("regrid_api.cu", []),
+    ("partition.cu", []),
 ]
 HOST_UNITS = ["hierarchy.cpp", "regrid.cpp"]
 HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp",

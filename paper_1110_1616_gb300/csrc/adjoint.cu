@@ -1364,6 +1364,8 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
     return fail(ctx, AMRMHD_EINVAL, "bad arguments");
   for (int i = 0; i < n_coarse; ++i)
     if (!(dt_seq[i] > 0.0)) return fail(ctx, AMRMHD_EINVAL, "dt must be positive");
+  if (ctx->floor_rho > 0.0 || ctx->floor_p > 0.0)
+    return fail(ctx, AMRMHD_ESTATE, "the adjoint does not differentiate floors: set them to 0");
   st = adj_setup(ctx);
   if (st) return st;
   const int k = std::min<int>(ckpt_every, n_coarse);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -89,6 +90,7 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
   a.w = w;
   a.bnd = (l > 0 && ctx->bnd_elems > 0) ? (void*)(ctx->arena + ctx->o_bnd) : nullptr;
   a.nbr = nullptr;
+  a.fl = ctx->floors();
   return a;
 }
 
@@ -97,7 +99,7 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
 // same-level ghost fill is then not needed.
 bool direct_halo(const amrmhd_ctx* ctx, int l) {
   return ctx->fused() && ctx->opt_advance != 1 && ctx->opt_direct_halo && !ctx->after_fill &&
-         l < (int)ctx->lev.size() && ctx->lev[l].direct_halo;
+         !(ctx->floor_rho > 0.0 || ctx->floor_p > 0.0) && l < (int)ctx->lev.size() && ctx->lev[l].direct_halo;
 }
 
 RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level) {
@@ -120,6 +122,7 @@ RowArgs row_args(amrmhd_ctx* ctx, const DevList& L, int coarse_level) {
   for (int n = 0; n < 3; ++n)
     for (int t = 0; t < 3; ++t) a.ratio[n][t] = dx[n] / dx[t];
   a.substep = 1;
+  a.fl = ctx->floors();
   return a;
 }
 
@@ -305,6 +308,7 @@ void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {
     a.gamma = ctx->cfg.gamma;
     a.slot = ctx->d_slots + l;
     a.err = ctx->d_err;
+    a.fl = ctx->floors();
     ctx->ops->cfl(a, ctx->stream, nl);
   }
   amrk::launch_cfl_finalize(ctx->d_slots, nlev, ctx->cfg.cfl, ctx->d_scal, hist, ctx->d_err, ctx->stream);
@@ -369,7 +373,8 @@ void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled) {
 bool queue_active(const amrmhd_ctx* ctx) {
   const int nlev = ctx->H.nlev;
   return ctx->opt_queue && ctx->fused() && ctx->opt_advance != 1 && ctx->opt_advance != 2 && !ctx->after_fill &&
-         !ctx->stage_light && nlev >= 2 && nlev <= amrk::QUEUE_MAX_LEVELS && (int)ctx->lev.size() == nlev;
+         !ctx->stage_light && !(ctx->floor_rho > 0.0 || ctx->floor_p > 0.0) && nlev >= 2 &&
+         nlev <= amrk::QUEUE_MAX_LEVELS && (int)ctx->lev.size() == nlev;
 }
 
 static int substep_at(int l, int k, int F) { return l == 0 ? 1 : ((k >> (F - l)) & 1) + 1; }
@@ -379,41 +384,94 @@ static bool ends_at(int l, int k, int F) { return (k + 1) % (1 << (F - l)) == 0;
 amrmhd_status build_queue_plan(amrmhd_ctx* ctx) {
   QueuePlan& Q = ctx->qplan;
   const int var = ctx->opt_queue_tile == 2 ? 2 : 3;
-  if (Q.built && Q.variant == var && Q.withhold == (int)ctx->opt_queue_withhold) return AMRMHD_OK;
+  if (Q.built && Q.variant == var && Q.withhold == (int)ctx->opt_queue_withhold &&
+      Q.balance == (int)ctx->opt_queue_balance)
+    return AMRMHD_OK;
   const amrmhd::Hierarchy& H = ctx->H;
   const int nlev = H.nlev, F = nlev - 1, T = 1 << F;
   const int np = (int)H.p.size();
   const int TX = var == 2 ? 16 : 8, TY = 8;  // the tiles of variants 2 and 3
   // the advance tiles of a sub-step of level l (w = 2: interior + 2 layers)
-  auto level_tiles = [&](int l, int w, std::vector<int32_t>& out) {
+  // and their work (cell updates)
+  auto level_tiles = [&](int l, int w, std::vector<int32_t>& out, std::vector<double>& work) {
     const int ntx = (ctx->lev[l].maxn[0] + 2 * w + TX - 1) / TX;
     const std::vector<int>& ids = H.level_patches[l];
     for (int i = 0; i < (int)ids.size(); ++i) {
       const amrmhd::HPatch& P = H.p[ids[i]];
-      const int nx = (P.n[0] + 2 * w + TX - 1) / TX, ny = (P.n[1] + 2 * w + TY - 1) / TY;
+      const int ex = P.n[0] + 2 * w, ey = P.n[1] + 2 * w, ez = P.n[2] + 2 * w;
+      const int nx = (ex + TX - 1) / TX, ny = (ey + TY - 1) / TY;
       for (int ty = 0; ty < ny; ++ty)
         for (int tx = 0; tx < nx; ++tx) {
           const int32_t rec[4] = {(F - l) << 4, i, ty * ntx + tx, ids[i]};
           out.insert(out.end(), rec, rec + 4);
+          work.push_back((double)std::min(TX, ex - tx * TX) * std::min(TY, ey - ty * TY) * ez);
         }
     }
   };
+  // shares of every level's sub-steps over the batches (first, end tile per batch)
+  // levels fine to coarse: the finest level's whole sub-step in its batch; a
+  // coarser level's sub-step of period P_l either in equal counts of tiles
+  // (balance 0) or so that the batches' total work (finer levels' included) is
+  // as even as its work allows (balance 1): the paper's load balancing (Sec. 5)
+  // with the batches of a coarse step as its processors: every batch is given
+  // the work that brings its predicted total to one common level.
+  std::vector<std::vector<int32_t>> tiles(nlev * (size_t)T);  // [l][m]: sub-step m of level l
+  std::vector<std::vector<double>> work(nlev * (size_t)T);
+  std::vector<std::vector<std::array<int64_t, 2>>> share(nlev, std::vector<std::array<int64_t, 2>>(T));
+  std::vector<double> load(T, 0.0);
+  for (int l = F; l >= 0; --l) {
+    const int P = 1 << (F - l), M = 1 << l;
+    for (int m = 0; m < M; ++m) {
+      const int s = l == 0 ? 1 : (m & 1) + 1, w = l == 0 ? 0 : (s == 1 ? 2 : 0);
+      std::vector<int32_t>& tl = tiles[(size_t)l * T + m];
+      std::vector<double>& wk = work[(size_t)l * T + m];
+      level_tiles(l, w, tl, wk);
+      const int64_t n = (int64_t)wk.size();
+      const int k0 = m * P;
+      if (ctx->opt_queue_balance == 0 || P == 1) {
+        for (int j = 0; j < P; ++j) share[l][k0 + j] = {n * j / P, n * (j + 1) / P};
+      } else {
+        // water level L*: sum_k max(0, L* - load_k) = total work of the sub-step
+        double tot = 0.0;
+        for (double x : wk) tot += x;
+        std::vector<double> ld(load.begin() + k0, load.begin() + k0 + P);
+        std::sort(ld.begin(), ld.end());
+        double lev = ld[0], acc = 0.0;
+        for (int j = 0; j < P; ++j) {
+          const double next = j + 1 < P ? ld[j + 1] : 1e300;
+          // raising the j+1 lowest batches from ld[j] to `next` costs (j+1)(next - ld[j])
+          if (acc + (j + 1) * (next - ld[j]) >= tot) {
+            lev = ld[j] + (tot - acc) / (j + 1);
+            break;
+          }
+          acc += (j + 1) * (next - ld[j]);
+        }
+        // contiguous runs of tiles: tile t goes to the batch whose cumulative
+        // target holds the tile's midpoint
+        int64_t t = 0;
+        double cum = 0.0, bound = 0.0;
+        for (int j = 0; j < P; ++j) {
+          bound += std::max(0.0, lev - load[k0 + j]);
+          const int64_t a = t;
+          while (t < n && (j == P - 1 || cum + 0.5 * wk[t] <= bound)) cum += wk[t++];
+          share[l][k0 + j] = {a, t};
+        }
+      }
+      for (int j = 0; j < P; ++j) {
+        const auto& sh = share[l][k0 + j];
+        for (int64_t t = sh[0]; t < sh[1]; ++t) load[k0 + j] += wk[t];
+      }
+    }
+  }
   std::vector<int32_t> tasks;
   std::vector<uint32_t> need((size_t)T * np, 0u);
   Q.task_off.assign(T, 0);
   Q.task_n.assign(T, 0);
   Q.fill_in_queue.assign(T, 0);
   const LevelDev& LF = ctx->lev[F];
-  std::vector<std::vector<int32_t>> cur_tiles(nlev);  // tiles of each level's current sub-step
   for (int k = 0; k < T; ++k) {
     const int64_t t0 = (int64_t)tasks.size() / 4;
     Q.task_off[k] = t0;
-    for (int l = 0; l <= F; ++l)
-      if (starts_at(l, k, F)) {
-        const int s = substep_at(l, k, F);
-        cur_tiles[l].clear();
-        level_tiles(l, l == 0 ? 0 : (s == 1 ? 2 : 0), cur_tiles[l]);
-      }
     // the finest level's same-level copies: ranges of at most 16 chunks into
     // one patch, cell boxes (listed first) and face boxes apart
     const bool fillq = !LF.has_bc;
@@ -436,14 +494,16 @@ amrmhd_status build_queue_plan(amrmhd_ctx* ctx) {
         c = e;
       }
     }
-    // advance tiles, finest level first: share j of P_l of each level's sub-step
+    // advance tiles, finest level first: each level's share of this batch
     for (int l = F; l >= 0; --l) {
-      const int64_t P = 1 << (F - l), j = k % P, n = (int64_t)cur_tiles[l].size() / 4;
-      const int64_t a = n * j / P, b = n * (j + 1) / P;
-      tasks.insert(tasks.end(), cur_tiles[l].begin() + 4 * a, cur_tiles[l].begin() + 4 * b);
+      const int m = k >> (F - l);
+      const std::vector<int32_t>& tl = tiles[(size_t)l * T + m];
+      const auto& sh = share[l][k];
+      tasks.insert(tasks.end(), tl.begin() + 4 * sh[0], tl.begin() + 4 * sh[1]);
     }
     Q.task_n[k] = (int)((int64_t)tasks.size() / 4 - t0);
   }
+  Q.batch_work = load;
   // test switch: the first patch of the finest level waits in the first batch
   // for one fill task more than exist, so its wait runs out
   if (ctx->opt_queue_withhold) need[H.level_patches[F].front()] += 1u;
@@ -458,6 +518,7 @@ amrmhd_status build_queue_plan(amrmhd_ctx* ctx) {
   CU(cudaMemcpy(Q.d_need, need.data(), sizeof(uint32_t) * need.size(), cudaMemcpyHostToDevice));
   Q.variant = var;
   Q.withhold = (int)ctx->opt_queue_withhold;
+  Q.balance = (int)ctx->opt_queue_balance;
   Q.built = true;
   return AMRMHD_OK;
 }
@@ -645,6 +706,17 @@ amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx) {
   return AMRMHD_OK;
 }
 
+amrmhd_status amrmhd_set_floors(amrmhd_ctx* ctx, double rho_min, double p_min) {
+  if (!ctx) return AMRMHD_EINVAL;
+  if (!(rho_min >= 0.0) || !(p_min >= 0.0) || !std::isfinite(rho_min) || !std::isfinite(p_min))
+    return fail(ctx, AMRMHD_EINVAL, "floors must be finite and non-negative");
+  ctx->floor_rho = rho_min;
+  ctx->floor_p = p_min;
+  for (int i = 0; i < 2; ++i)
+    if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
+  return AMRMHD_OK;
+}
+
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) {
   if (!ctx) return AMRMHD_EINVAL;
   if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
@@ -656,6 +728,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   else if (option == AMRMHD_OPT_QUEUE && (value == 0 || value == 1)) ctx->opt_queue = value;
   else if (option == AMRMHD_OPT_QUEUE_TILE && (value == 2 || value == 3)) ctx->opt_queue_tile = value;
   else if (option == AMRMHD_OPT_QUEUE_WITHHOLD && (value == 0 || value == 1)) ctx->opt_queue_withhold = value;
+  else if (option == AMRMHD_OPT_QUEUE_BALANCE && (value == 0 || value == 1)) ctx->opt_queue_balance = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -794,6 +867,9 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
   ctx->d_err = dbuf<unsigned int>(ctx, 1, &e);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
   CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+  ctx->d_floor_events = dbuf<unsigned long long>(ctx, 1, &e);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  CU(cudaMemset(ctx->d_floor_events, 0, sizeof(unsigned long long)));
   CU(cudaMemset(ctx->d_slots, 0, sizeof(unsigned long long) * (nlev + 1)));
   CU(cudaMemset(ctx->d_scal, 0, sizeof(double) * (2 + nlev)));
   ctx->hist_cap = kHistCap;
@@ -1405,11 +1481,28 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
     case AMRMHD_Q_REGRID_BUILD_US:
     case AMRMHD_Q_REGRID_TRANSFER_US:
     case AMRMHD_Q_REGRID_MAPS_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
+    case AMRMHD_Q_FLOOR_EVENTS: {
+      unsigned long long v = 0;
+      if (ctx->bound && ctx->d_floor_events) {
+        CU(cudaMemcpyAsync(&v, ctx->d_floor_events, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+      }
+      *value = (int64_t)v;
+      return AMRMHD_OK;
+    }
     default: return fail(ctx, AMRMHD_EINVAL, "unknown query");
   }
 }
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+amrmhd_status amrmhd_grad_velocity(int64_t ncells, const double* u0, const double* dL_dU0, double* dL_dv0,
+                                   void* cuda_stream) {
+  if (ncells < 0 || (ncells > 0 && (!u0 || !dL_dU0 || !dL_dv0))) return AMRMHD_EINVAL;
+  if (ncells == 0) return AMRMHD_OK;
+  amrk::launch_grad_velocity(ncells, u0, dL_dU0, dL_dv0, (cudaStream_t)cuda_stream);
+  return cudaGetLastError() == cudaSuccess ? AMRMHD_OK : AMRMHD_ECUDA;
+}
 
 amrmhd_status amrmhd_alu_peak(int32_t fp64, double* flops_per_s, int32_t* sms) {
   if ((fp64 != 0 && fp64 != 1) || !flops_per_s) return AMRMHD_EINVAL;

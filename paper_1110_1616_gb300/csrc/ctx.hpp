@@ -58,7 +58,8 @@ struct LevelDev {
 // expected fill count per patch; counters shared by the batches.
 struct QueuePlan {
   bool built = false;
-  int variant = 3, withhold = 0;
+  int variant = 3, withhold = 0, balance = 1;
+  std::vector<double> batch_work;  // per batch: the cell updates of its advance tiles
   std::vector<int64_t> task_off;  // per batch: first task
   std::vector<int> task_n;        // per batch: task count
   std::vector<int> fill_in_queue; // per batch: 1 if the finest level's same-level fill is in the queue
@@ -88,7 +89,19 @@ struct amrmhd_ctx {
   int64_t opt_advance = 0, opt_graph = 1, opt_tile = -1, opt_concurrent = 1, opt_host_io = 0, opt_direct_halo = 1;
   // the multi-level queue advance: on/off, its tile variant (2: 16x8, 3: 8x8),
   // and a test switch that withholds one fill signal (the wait times out)
-  int64_t opt_queue = 0, opt_queue_tile = 3, opt_queue_withhold = 0;
+  int64_t opt_queue = 0, opt_queue_tile = 3, opt_queue_withhold = 0, opt_queue_balance = 1;
+  // density and pressure floors (0: off) and the device count of their raises
+  double floor_rho = 0.0, floor_p = 0.0;
+  unsigned long long* d_floor_events = nullptr;
+  amrk::Floors floors() const {
+    amrk::Floors f;
+    if (floor_rho > 0.0 || floor_p > 0.0) {
+      f.rho = floor_rho;
+      f.p = floor_p;
+      f.events = d_floor_events;
+    }
+    return f;
+  }
   amrapi::QueuePlan qplan;
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)

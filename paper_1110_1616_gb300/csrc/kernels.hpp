@@ -6,6 +6,16 @@
 
 namespace amrk {
 
+// Density and pressure floors (off when both are 0): a recovered density below
+// rho is raised to rho before the velocity and pressure are formed, then a
+// pressure below p is raised to p; every raise adds 1 to *events. They act on
+// the primitives only (the stored conserved state is not changed), so where
+// they act the advance is not conservative.
+struct Floors {
+  double rho = 0.0, p = 0.0;
+  unsigned long long* events = nullptr;
+};
+
 // Per-patch descriptor in device memory.
 struct DPatch {
   int lo[3], n[3], ext[3];
@@ -43,6 +53,7 @@ struct LevelArgs {
   // of its halo from those patches' interiors instead of its own ghost cells,
   // so the level needs no same-level ghost fill. nullptr: read the ghosts.
   const int* nbr;
+  Floors fl;
 };
 
 struct RowArgs {
@@ -76,6 +87,7 @@ struct RowArgs {
   // fine-side registers of the fused path: the boundary capture buffer the fine
   // level's advance wrote (nullptr: recompute the fluxes and EMFs)
   const void* bnd;
+  Floors fl;  // the advance's floors (the register recompute repeats its recovery)
 };
 
 // Device work queue of the multi-level advance (k_advance_queue): one launch
@@ -113,6 +125,7 @@ struct CflArgs {
   double gamma;
   unsigned long long* slot;  // per-level max (bits of a non-negative double)
   unsigned int* err;
+  Floors fl;
 };
 
 // sizes of a patch's boundary capture block (fused 3D path, levels > 0): the
@@ -188,6 +201,7 @@ void launch_fp_convert(long long n, const double* x, const float* y, float* xn, 
 void launch_recover_mixed(long long n, const float* u, const float* bl, const float* br, double gm1, float* w,
                           cudaStream_t s);
 void launch_fma_peak(int fp64, int blocks, int threads, int iters, void* out, cudaStream_t s);
+void launch_grad_velocity(long long n, const double* u, const double* g, double* gv, cudaStream_t s);
 
 void launch_set_scalar(double* p, double v, cudaStream_t s);
 void launch_cfl_finalize(const unsigned long long* slots, int nlev, double cfl, double* dt_out, double* hist,

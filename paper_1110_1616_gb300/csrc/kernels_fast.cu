@@ -70,6 +70,25 @@ void launch_fma_peak(int fp64, int blocks, int threads, int iters, void* out, cu
   else k_fma_peak<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.999999f, 1e-7f);
 }
 
+// dL/dv of the initial velocity from dL/dU0 (reading 13): with rho, p and B
+// held, m = rho v and E = p/(g-1) + rho |v|^2 / 2 + |B|^2 / 2, so
+// dL/dv_c = rho (dL/dm_c + v_c dL/dE), v = m / rho; packed cell fields, field
+// stride n (rho, mx, my, mz, E first in u and g), 3 fields out
+__global__ void k_grad_velocity(long long n, const double* u, const double* g, double* gv) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double rho = u[i], gE = g[4 * n + i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double v = u[(1 + c) * n + i] / rho;
+    gv[c * n + i] = rho * (g[(1 + c) * n + i] + v * gE);
+  }
+}
+
+void launch_grad_velocity(long long n, const double* u, const double* g, double* gv, cudaStream_t s) {
+  k_grad_velocity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, u, g, gv);
+}
+
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
 void launch_set_scalar(double* p, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(p, v); }

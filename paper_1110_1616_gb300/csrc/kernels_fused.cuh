@@ -75,14 +75,16 @@ __device__ __forceinline__ void hlld_face(const T* wl, const T* wr, int D, T gam
 
 template <class T>
 __device__ __forceinline__ void load_recover(const T* U, long long fs, int L, int sy, int sz, double gm1, T* w,
-                                             T* dB = nullptr) {
+                                             T* dB = nullptr, const Floors* fl = nullptr) {
   T u[5], bl[3], br[3];
 #pragma unroll
   for (int f = 0; f < 5; ++f) u[f] = U[f * fs + L];
   bl[0] = U[5 * fs + L]; br[0] = U[5 * fs + L + 1];
   bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + sy];
   bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + sz];
+  if (fl) floor_density(u, fl->rho, fl->events);
   recover_t(u, bl, br, gm1, w);
+  if (fl) floor_pressure(w, fl->p, fl->events);
   if (dB) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) dB[d] = br[d] - bl[d];
@@ -146,9 +148,10 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
 // dynamic shared memory (a FusedSmem). MODE 0: plain; 1 (CAP): the level's
 // boundary fluxes and EMFs are captured for the fine registers (patches with
 // P.boff >= 0); 2 (DH): direct halo reads from the neighbour patches (a.nbr; a
-// level of equal patches tiling the periodic domain, w = 0). Every thread of
-// the CTA calls it with the same arguments.
-template <class T, int VAR, int MODE>
+// level of equal patches tiling the periodic domain, w = 0). FL: the recovery
+// applies the density and pressure floors of a.fl (never with DH). Every thread
+// of the CTA calls it with the same arguments.
+template <class T, int VAR, int MODE, bool FL = false>
 __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int tile, int ntx,
                                            unsigned char* smem_raw) {
   constexpr bool CAP = MODE == 1, DH = MODE == 2;
@@ -174,6 +177,7 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   T* V = (T*)a.nxt + P.off;
   const bool capture = CAP && P.boff >= 0;
   const double gm1 = a.gamma - 1.0;
+  const Floors* flp = FL ? &a.fl : nullptr;
   const T gamma = (T)a.gamma;
   const double dt = *a.dtp * a.dtscale;
   const T h0 = (T)(0.5 * dt * a.idx[0]), h1 = (T)(0.5 * dt * a.idx[1]), h2 = (T)(0.5 * dt * a.idx[2]);
@@ -203,9 +207,9 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
           if (x < 4) { lx += P.n[0]; k -= 1; } else if (x >= P.n[0] + 4) { lx -= P.n[0]; k += 1; }
           if (y < 4) { ly += P.n[1]; k -= 3; } else if (y >= P.n[1] + 4) { ly -= P.n[1]; k += 3; }
           if (t < 4) { lz += P.n[2]; k -= 9; } else if (t >= P.n[2] + 4) { lz -= P.n[2]; k += 9; }
-          load_recover((const T*)a.cur + s_nb[k], fs, lx + sy * ly + sz * lz, sy, sz, gm1, wv, dB);
+          load_recover((const T*)a.cur + s_nb[k], fs, lx + sy * ly + sz * lz, sy, sz, gm1, wv, dB, flp);
         } else {
-          load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB);
+          load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB, flp);
         }
         const int i = widx(x, y);
 #pragma unroll
@@ -450,11 +454,11 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
 // CTAs per SM of the FP32 tiles of 256 threads: two for the larger tiles
 // (shared memory), three for the 8x8 tile (80 registers a thread, no spills)
 template <int VAR> constexpr int fused_ctas_fp32() { return FusedCfg<VAR>::NT != 256 ? 1 : (VAR == 3 ? 3 : 2); }
-template <class T, int VAR, int MODE>
+template <class T, int VAR, int MODE, bool FL = false>
 __global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? fused_ctas_fp32<VAR>() : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_tile<T, VAR, MODE>(a, blockIdx.y, blockIdx.x, ntx, smem_raw);
+  fused_tile<T, VAR, MODE, FL>(a, blockIdx.y, blockIdx.x, ntx, smem_raw);
 }
 
 // ---------------------------------------------------------------- device work queue
@@ -548,16 +552,16 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? 2 : 1)
 // the same formulas as the fused kernel, evaluated at the listed faces/edges.
 template <class T>
 __device__ void predict_at(const T* U, const DPatch& P, int L, double dt, const double* idx, double gamma, T* wh,
-                           T* sd /* 3 x 8 */) {
+                           T* sd /* 3 x 8 */, const Floors* fl) {
   const long long fs = P.fs;
   const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
   const double gm1 = gamma - 1.0;
   T wc[8], wm[8], wp[8];
-  load_recover(U, fs, L, st[1], st[2], gm1, wc);
+  load_recover(U, fs, L, st[1], st[2], gm1, wc, (T*)nullptr, fl);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    load_recover(U, fs, L - st[d], st[1], st[2], gm1, wm);
-    load_recover(U, fs, L + st[d], st[1], st[2], gm1, wp);
+    load_recover(U, fs, L - st[d], st[1], st[2], gm1, wm, (T*)nullptr, fl);
+    load_recover(U, fs, L + st[d], st[1], st[2], gm1, wp, (T*)nullptr, fl);
 #pragma unroll
     for (int f = 0; f < 8; ++f) {
       if (f == BX + d) sd[8 * d + f] = U[(BX + d) * fs + L + st[d]] - U[(BX + d) * fs + L];
@@ -584,11 +588,11 @@ __device__ void predict_at(const T* U, const DPatch& P, int L, double dt, const 
 // flux through the d-face stored at L (cells L - st[d] and L), global field order
 template <class T>
 __device__ void face_flux_at(const T* U, const DPatch& P, int d, int L, double dt, const double* idx, double gamma,
-                             T* out8) {
+                             T* out8, const Floors* fl) {
   const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
   T whl[8], whr[8], sl[24], sr[24], wl[8], wr[8];
-  predict_at(U, P, L - st[d], dt, idx, gamma, whl, sl);
-  predict_at(U, P, L, dt, idx, gamma, whr, sr);
+  predict_at(U, P, L - st[d], dt, idx, gamma, whl, sl, fl);
+  predict_at(U, P, L, dt, idx, gamma, whr, sr, fl);
 #pragma unroll
   for (int f = 0; f < 8; ++f) {
     wl[f] = whl[f] + T(0.5) * sl[8 * d + f];
@@ -599,12 +603,13 @@ __device__ void face_flux_at(const T* U, const DPatch& P, int d, int L, double d
 
 // E_c at the c-edge stored at L (the low a,b corner of cell L), (a,b,c) cyclic
 template <class T>
-__device__ T edge_emf_at(const T* U, const DPatch& P, int c, int L, double dt, const double* idx, double gamma) {
+__device__ T edge_emf_at(const T* U, const DPatch& P, int c, int L, double dt, const double* idx, double gamma,
+                         const Floors* fl) {
   const int st[3] = {1, P.ext[0], P.ext[0] * P.ext[1]};
   const int a = (c + 1) % 3, b = (c + 2) % 3;
   const int Lc[4] = {L - st[a] - st[b], L - st[b], L - st[a], L};  // (a-1,b-1), (a,b-1), (a-1,b), (a,b)
   T wh[4][8], sd[4][24];
-  for (int k = 0; k < 4; ++k) predict_at(U, P, Lc[k], dt, idx, gamma, wh[k], sd[k]);
+  for (int k = 0; k < 4; ++k) predict_at(U, P, Lc[k], dt, idx, gamma, wh[k], sd[k], fl);
   T wl[8], wr[8], fa_lo[8], fa_hi[8], fb_lo[8], fb_hi[8];
   const T g = (T)gamma;
   // a-faces at rows b-1 (cells 0 -> 1) and b (cells 2 -> 3)
@@ -630,6 +635,11 @@ __device__ T edge_emf_at(const T* U, const DPatch& P, int c, int L, double dt, c
                    fa_hi[RHO], fb_lo[RHO], fb_hi[RHO]);
 }
 
+// the floors a register recompute repeats (those of the advance it mirrors)
+__device__ __forceinline__ const Floors* rc_floors(const RowArgs& a) {
+  return (a.fl.rho > 0.0 || a.fl.p > 0.0) ? &a.fl : nullptr;
+}
+
 // RowArgs.fbuf = the state the level's advance read (for the coarse side the
 // coarse level, for the fine side the fine level); dt = *dtp * dtscale.
 template <class T> __global__ void k_regrc_coarse_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
@@ -640,7 +650,7 @@ template <class T> __global__ void k_regrc_coarse_faces(RowArgs a, double gamma,
   const double dt = *a.dtp * a.dtscale;
   const double idx[3] = {ix, iy, iz};
   T f8[8];
-  face_flux_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma, f8);
+  face_flux_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma, f8, rc_floors(a));
 #pragma unroll
   for (int n = 0; n < 5; ++n) a.creg[r * 6 + n] = dt * (double)f8[n];
 }
@@ -652,7 +662,7 @@ template <class T> __global__ void k_regrc_coarse_edges(RowArgs a, double gamma,
   const DPatch P = a.P[row[1]];
   const double dt = *a.dtp * a.dtscale;
   const double idx[3] = {ix, iy, iz};
-  a.ecreg[r] = dt * (double)edge_emf_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma);
+  a.ecreg[r] = dt * (double)edge_emf_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma, rc_floors(a));
 }
 
 template <class T> __global__ void k_regrc_fine_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
@@ -672,7 +682,7 @@ template <class T> __global__ void k_regrc_fine_faces(RowArgs a, double gamma, d
   const int off[4] = {0, o1, o2, o1 + o2};
   T f[4][8];
   const T* U = (const T*)a.fbuf + P.off;
-  for (int k = 0; k < 4; ++k) face_flux_at<T>(U, P, d, L + off[k], dt, idx, gamma, f[k]);
+  for (int k = 0; k < 4; ++k) face_flux_at<T>(U, P, d, L + off[k], dt, idx, gamma, f[k], rc_floors(a));
   double* out = a.freg + (r * 2 + (a.substep - 1)) * 6;
 #pragma unroll
   for (int n = 0; n < 5; ++n)
@@ -689,8 +699,8 @@ template <class T> __global__ void k_regrc_fine_edges(RowArgs a, double gamma, d
   const double idx[3] = {ix, iy, iz};
   const int sc = c == 0 ? 1 : (c == 1 ? P.ext[0] : P.ext[0] * P.ext[1]);
   const T* U = (const T*)a.fbuf + P.off;
-  const T e0 = edge_emf_at<T>(U, P, c, L, dt, idx, gamma);
-  const T e1 = edge_emf_at<T>(U, P, c, L + sc, dt, idx, gamma);
+  const T e0 = edge_emf_at<T>(U, P, c, L, dt, idx, gamma, rc_floors(a));
+  const T e1 = edge_emf_at<T>(U, P, c, L + sc, dt, idx, gamma, rc_floors(a));
   a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)e0, (double)e1);
 }
 
@@ -724,7 +734,7 @@ template <class T> __global__ void k_regcap_fine_faces(RowArgs a, double gamma, 
     } else {
       const double idx[3] = {ix, iy, iz};
       T f8[8];
-      face_flux_at<T>((const T*)a.fbuf + P.off, P, d, Lk, dt, idx, gamma, f8);
+      face_flux_at<T>((const T*)a.fbuf + P.off, P, d, Lk, dt, idx, gamma, f8, rc_floors(a));
 #pragma unroll
       for (int n = 0; n < 5; ++n) f[k][n] = f8[n];
     }
@@ -755,7 +765,7 @@ template <class T> __global__ void k_regcap_fine_edges(RowArgs a, double gamma, 
       ev[k] = b[sl];
     } else {
       const double idx[3] = {ix, iy, iz};
-      ev[k] = edge_emf_at<T>((const T*)a.fbuf + P.off, P, c, Lk, dt, idx, gamma);
+      ev[k] = edge_emf_at<T>((const T*)a.fbuf + P.off, P, c, Lk, dt, idx, gamma, rc_floors(a));
     }
   }
   a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)ev[0], (double)ev[1]);

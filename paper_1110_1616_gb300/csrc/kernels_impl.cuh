@@ -57,7 +57,9 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_prim(LevelA
   bc[1] = 0.5 * ((double)U[6 * fs + L] + (double)U[6 * fs + L + P.ext[0]]);
   if (DIM == 3) bc[2] = 0.5 * ((double)U[7 * fs + L] + (double)U[7 * fs + L + P.ext[0] * P.ext[1]]);
   else bc[2] = (double)U[7 * fs + L];
+  floor_density(u, a.fl.rho, a.fl.events);
   recover(u, bc, a.gamma - 1.0, w);
+  floor_pressure(w, a.fl.p, a.fl.events);
   T* W = (T*)a.scr + P.soff + SC_W * fs;
 #pragma unroll
   for (int f = 0; f < 8; ++f) W[f * fs + L] = (T)w[f];
@@ -874,7 +876,9 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
     bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + P.ext[0]];
     if (DIM == 3) { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + P.ext[0] * P.ext[1]]; }
     else { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L]; }
+    floor_density(u, a.fl.rho, a.fl.events);
     recover_t(u, bl, br, a.gamma - 1.0, w);
+    floor_pressure(w, a.fl.p, a.fl.events);
     if (!(w[0] > T(0)) || !(w[4] > T(0))) bad = true;
     else {
       T rr = T(0);
@@ -1076,6 +1080,10 @@ template <class T, int DIM> struct Impl {
                            (int)fused_smem<V>());
       cudaFuncSetAttribute(k_advance3d_fused<T, V, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fused_smem<V>());
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<V>());
+      cudaFuncSetAttribute(k_advance3d_fused<T, V, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_smem<V>());
     }
   }
   static void prepare() {
@@ -1108,7 +1116,10 @@ template <class T, int DIM> struct Impl {
     const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
     const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
     const dim3 g(ntx * nty, a.npatch);
-    if (a.bnd) k_advance3d_fused<T, V, 1><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    const bool fl = a.fl.rho > 0.0 || a.fl.p > 0.0;  // floors (the host never combines them with DH)
+    if (fl && a.bnd) k_advance3d_fused<T, V, 1, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    else if (fl) k_advance3d_fused<T, V, 0, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
+    else if (a.bnd) k_advance3d_fused<T, V, 1><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
     else if (a.nbr && a.w == 0) k_advance3d_fused<T, V, 2><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
     else k_advance3d_fused<T, V, 0><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
   }

@@ -152,6 +152,21 @@ __device__ __forceinline__ void recover_t(const float* u, const float* bl, const
   w[7] = 0.5f * (bl[2] + br[2]);
 }
 
+// floors of the recovery (reading 12): the density before the recovery, the
+// pressure after it; each raise counted
+template <class T> __device__ __forceinline__ void floor_density(T* u, double rho_min, unsigned long long* events) {
+  if (rho_min > 0.0 && u[0] < (T)rho_min) {
+    u[0] = (T)rho_min;
+    atomicAdd(events, 1ull);
+  }
+}
+template <class T> __device__ __forceinline__ void floor_pressure(T* w, double p_min, unsigned long long* events) {
+  if (p_min > 0.0 && w[4] < (T)p_min) {
+    w[4] = (T)p_min;
+    atomicAdd(events, 1ull);
+  }
+}
+
 // A_d(W) s for the primitive predictor, direction d (n = d, t = d+1, u = d+2 mod 3)
 template <class T, int D> __device__ __forceinline__ void prim_terms(const T* w, const T* s, T gamma, T ir, T* dw) {
   constexpr int n = D, t = (D + 1) % 3, u = (D + 2) % 3;

@@ -354,6 +354,36 @@ def cylinder_3d(n=64, psize=16, contrast=10.0, radius=0.1, gamma=GAMMA):
     return Problem("cylinder_3d", 3, base, patches, 2, state, gamma=gamma)
 
 
+def cylinder_3d_tiled(reps=(1, 1, 1), n=64, psize=16, contrast=10.0, radius=0.1, gamma=GAMMA):
+    """The paper's weak-scaling workload unit (Sec. 6) repeated over a block of
+    unit cubes: domain [0, a) x [0, b) x [0, c) for reps = (a, b, c), base
+    (a n, b n, c n) in psize^3 patches (n^3 base cells per unit, the paper's 64^3
+    per processor), in every unit cube the magnetized cylinder of cylinder_3d
+    and a refined level over its central eighth (12.5 % filling per unit).
+    Whole-level arrays on both levels."""
+    a, b, c = reps
+    unit = cylinder_3d(n, psize, contrast, radius, gamma)
+    base = (a * n, b * n, c * n)
+    patches = tile(0, (0, 0, 0), base, psize, 3)
+    for k in range(c):
+        for j in range(b):
+            for i in range(a):
+                lo = (2 * (i * n + n // 4), 2 * (j * n + n // 4), 2 * (k * n + n // 4))
+                hi = (2 * (i * n + 3 * n // 4), 2 * (j * n + 3 * n // 4), 2 * (k * n + 3 * n // 4))
+                patches += tile(1, lo, hi, psize, 3)
+    state = {}
+    for l in range(2):
+        cells = [np.tile(unit.state[l][f], (c, b, a)) for f in range(5)]
+        m = n << l
+        b0 = float(unit.state[l][5].flat[0])
+        bx = np.full((c * m, b * m, a * m + 1), b0)
+        by = np.zeros((c * m, b * m + 1, a * m))
+        bz = np.zeros((c * m + 1, b * m, a * m))
+        state[l] = cells + [bx, by, bz]
+    return Problem("cylinder_3d_tiled_%dx%dx%d" % reps, 3, base, patches, 2, state, gamma=gamma,
+                   hi=(float(a), float(b), float(c)), meta={"units": a * b * c})
+
+
 def uniform_state(dim, base, patches, nlev, seed=0, gamma=GAMMA):
     """A random constant state on every level."""
     rng = np.random.default_rng(seed)

@@ -239,3 +239,60 @@ def test_mixed_precision_adjoint_close_to_fp64():
     go = oracle_for(pb).backward(dts, lam)
     err = rel_l2(g, go, mask)
     assert err <= 1e-4, err
+
+
+def test_velocity_gradient_against_central_differences():
+    """dL/dv0 (amrmhd_grad_velocity: the backward's dL/dU0 pushed through the
+    initial state's dependence on the velocity, rho, p and B held) against
+    central differences of the forward in v0: moving v0 by h dv changes the
+    momentum by rho h dv and the total energy by rho (h v.dv + h^2 |dv|^2 / 2)."""
+    import torch
+    from paper_1110_1616_gb300.autograd import velocity_gradient
+    pb = quadrant_2d()
+    o = oracle_for(pb)
+    dts = [o.step() for _ in range(3)]
+    ctx = gpu_ctx(pb)
+    rng = np.random.default_rng(21)
+    n = ctx.packed_size(0)
+    u0 = np.concatenate([ctx.pack(pb.state, f) for f in range(8)])
+    seed = np.zeros_like(u0)
+    seed[:n] = rng.normal(size=n)  # a loss linear in the final density
+    s_t = torch.tensor(seed, dtype=torch.float64, device="cuda")
+    g0 = torch.empty_like(s_t)
+    torch.cuda.synchronize()
+    ctx.backward(dts, s_t, g0, 3)
+    gv = velocity_gradient(torch.tensor(u0, device="cuda"), g0, n).cpu().numpy()
+
+    def loss(u):
+        t = torch.tensor(u, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        ctx.load_packed_all(t)
+        ctx.step_dt(dts)
+        out = torch.empty_like(t)
+        ctx.read_packed_all(out)
+        torch.cuda.synchronize()
+        return float((out.cpu().numpy() * seed).sum())
+
+    rho = u0[:n]
+    v = [u0[(1 + c) * n:(2 + c) * n] / rho for c in range(3)]
+
+    def moved(dv, h):
+        u = u0.copy()
+        for c in range(3):
+            u[(1 + c) * n:(2 + c) * n] += rho * h * dv[c]
+        u[4 * n:5 * n] += rho * sum(h * v[c] * dv[c] + 0.5 * h * h * dv[c] * dv[c] for c in range(3))
+        return u
+
+    checked = 0
+    for trial in range(4):
+        x = np.arange(n, dtype=np.float64)
+        dv = [np.cos(2 * np.pi * (rng.integers(1, 4) * x / n) + rng.uniform(0, 2 * np.pi)) for _ in range(3)]
+        h = 1e-6 / max(np.abs(np.concatenate(dv)).max(), 1e-30)
+        ad = float(sum((gv[c * n:(c + 1) * n] * dv[c]).sum() for c in range(3)))
+        fds = [(loss(moved(dv, hh)) - loss(moved(dv, -hh))) / (2 * hh) for hh in (h, h / 4, h / 16)]
+        for a_, b_ in zip(fds, fds[1:]):
+            if abs(a_ - b_) <= 1e-7 * abs(b_):
+                assert abs(b_ - ad) <= 1e-6 * abs(ad), (trial, fds, ad)
+                checked += 1
+                break
+    assert checked >= 2

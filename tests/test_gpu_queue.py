@@ -58,10 +58,12 @@ def test_queue_hierarchy_has_three_levels():
     assert three_level_3d().nlev == 3
 
 
-@pytest.mark.parametrize("tile", [3, 2])
-def test_queue_equals_level_launches_fp64(tile):
+@pytest.mark.parametrize("tile,balance", [(3, 1), (2, 1), (3, 0)])
+def test_queue_equals_level_launches_fp64(tile, balance):
+    """Tile variants and both ways of sharing out the coarser levels' tiles
+    (work-balanced or equal counts) give the level-by-level result."""
     pb = three_level_3d()
-    a, da = run(pb, A.FP64, 3, True, OPT_QUEUE_TILE=tile)
+    a, da = run(pb, A.FP64, 3, True, OPT_QUEUE_TILE=tile, OPT_QUEUE_BALANCE=balance)
     b, db = run(pb, A.FP64, 3, False)
     assert np.array_equal(da, db)
     sa, sb = a.read_state(), b.read_state()
