@@ -35,7 +35,7 @@ template <class T, int TX_, int TY_> struct FusedSmem {
   T sz[2][8][Q];
   T sx[8][Q];
   T sy[8][Q];
-  T ref[2][3][Q];
+  T ref[3][3][Q];
   T fx[2][8][Q];
   T fy[2][8][Q];
   T fz[2][8][Q];
@@ -188,266 +188,298 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   auto widx = [&](int x, int y) { return (x - (x0 - 2)) + PX * (y - (y0 - 2)); };
   auto qidx = [&](int x, int y) { return (x - (x0 - 1)) + QX * (y - (y0 - 1)); };
 
-  for (int t = zlo - 2; t <= zhi + 1; ++t) {
-    // ---------------- S1: primitives of plane t
-    if (t <= zhi + 1) {
-      const int slot = (t + 3) % 3;
-      const int r2t = (t + 2) % 2;
-      for (int c = threadIdx.x; c < PX * S::PY; c += nth) {
-        const int xi = c % PX, yi = c / PX;  // constant divisors; positions beyond a partial tile skip
-        if (xi >= wx || yi >= wy) continue;
-        const int x = x0 - 2 + xi, y = y0 - 2 + yi;
-        T wv[8], dB[3];
-        if constexpr (DH) {
-          // the cell (and its faces) in the neighbour patch that owns it: every
-          // patch has the interior extent n, so a coordinate outside [4, n+4)
-          // moves by n into the neighbour's interior (its own high faces at n+4
-          // included); the neighbours' strides are this patch's
-          int lx = x, ly = y, lz = t, k = 13;
-          if (x < 4) { lx += P.n[0]; k -= 1; } else if (x >= P.n[0] + 4) { lx -= P.n[0]; k += 1; }
-          if (y < 4) { ly += P.n[1]; k -= 3; } else if (y >= P.n[1] + 4) { ly -= P.n[1]; k += 3; }
-          if (t < 4) { lz += P.n[2]; k -= 9; } else if (t >= P.n[2] + 4) { lz -= P.n[2]; k += 9; }
-          load_recover((const T*)a.cur + s_nb[k], fs, lx + sy * ly + sz * lz, sy, sz, gm1, wv, dB, flp);
-        } else {
-          load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB, flp);
-        }
-        const int i = widx(x, y);
+  // The stages, each over the positions of one plane, every thread taking
+  // positions in steps of the CTA size:
+  //   S1(t)  primitives of plane t (W ring slot t mod 3; normal-B differences)
+  //   S2(p)  slopes, predictor and reference EMF of plane p
+  //   S3(p)  HLLD fluxes of the x- and y-faces of plane p and the z-faces of face plane p
+  //   S4(p)  edge EMFs: E_z of plane p, E_x and E_y of edge plane p
+  //   S5(q)  update of cell plane q (its stored values prefetched by cp.async)
+  auto stage1 = [&](int t) {
+      // ---------------- S1: primitives of plane t
+      {
+        const int slot = (t + 3) % 3;
+        const int r2t = (t + 2) % 2;
+        for (int c = threadIdx.x; c < PX * S::PY; c += nth) {
+          const int xi = c % PX, yi = c / PX;  // constant divisors; positions beyond a partial tile skip
+          if (xi >= wx || yi >= wy) continue;
+          const int x = x0 - 2 + xi, y = y0 - 2 + yi;
+          T wv[8], dB[3];
+          if constexpr (DH) {
+            // the cell (and its faces) in the neighbour patch that owns it: every
+            // patch has the interior extent n, so a coordinate outside [4, n+4)
+            // moves by n into the neighbour's interior (its own high faces at n+4
+            // included); the neighbours' strides are this patch's
+            int lx = x, ly = y, lz = t, k = 13;
+            if (x < 4) { lx += P.n[0]; k -= 1; } else if (x >= P.n[0] + 4) { lx -= P.n[0]; k += 1; }
+            if (y < 4) { ly += P.n[1]; k -= 3; } else if (y >= P.n[1] + 4) { ly -= P.n[1]; k += 3; }
+            if (t < 4) { lz += P.n[2]; k -= 9; } else if (t >= P.n[2] + 4) { lz -= P.n[2]; k += 9; }
+            load_recover((const T*)a.cur + s_nb[k], fs, lx + sy * ly + sz * lz, sy, sz, gm1, wv, dB, flp);
+          } else {
+            load_recover(U, fs, x + sy * y + sz * t, sy, sz, gm1, wv, dB, flp);
+          }
+          const int i = widx(x, y);
 #pragma unroll
-        for (int f = 0; f < 8; ++f) sm.w[slot][f][i] = wv[f];
-        if (x >= x0 - 1 && x < x0 + tx + 1 && y >= y0 - 1 && y < y0 + ty + 1) {
-          const int q = qidx(x, y);
+          for (int f = 0; f < 8; ++f) sm.w[slot][f][i] = wv[f];
+          if (x >= x0 - 1 && x < x0 + tx + 1 && y >= y0 - 1 && y < y0 + ty + 1) {
+            const int q = qidx(x, y);
 #pragma unroll
-          for (int d = 0; d < 3; ++d) sm.db[r2t][d][q] = dB[d];
+            for (int d = 0; d < 3; ++d) sm.db[r2t][d][q] = dB[d];
+          }
         }
       }
-    }
-    __syncthreads();
-    const int p = t - 1;
-    // prefetch of the stored values the update of plane p-1 (S5) reads: every
-    // thread has left the previous S5, and the copies land before S5's barrier
-    {
-      const int qz = p - 1;
+  };
+  auto prefetch = [&](int qz) {
+      {
+        if (qz >= zlo && qz < zhi) {
+          const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
+          const bool top = qz == zhi - 1;
+          for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
+            const int xi = c % (TX + 1), yi = c / (TX + 1);
+            if (xi >= nx || yi >= ny) continue;
+            const int L = (x0 + xi) + sy * (y0 + yi) + sz * qz;
+#pragma unroll
+            for (int f = 0; f < 8; ++f) cp_async_elem<T>(&sm.up[f][c], U + f * fs + L);
+            if (top) cp_async_elem<T>(&sm.up[8][c], U + BZ * fs + L + sz);
+          }
+        }
+        cp_async_commit();
+      }
+  };
+  auto stage2 = [&](int p) {
+      // ---------------- S2: slopes and predictor of plane p
+      {
+        const int sm1 = (p - 1 + 3) % 3, s0 = (p + 3) % 3, sp1 = (p + 1 + 3) % 3;
+        const int r2 = (p + 2) % 2, r3 = (p + 3) % 3;
+        for (int c = threadIdx.x; c < QX * S::QY; c += nth) {
+          const int xi = c % QX, yi = c / QX;
+          if (xi >= qx || yi >= qy) continue;
+          const int x = x0 - 1 + xi, y = y0 - 1 + yi;
+          const int i = widx(x, y);
+          T wc[8], s[3][8];
+          const int qd = qidx(x, y);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wc[f] = sm.w[s0][f][i];
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            s[0][f] = f == BX ? sm.db[r2][0][qd] : mm(wc[f] - sm.w[s0][f][i - 1], sm.w[s0][f][i + 1] - wc[f]);
+            s[1][f] = f == BY ? sm.db[r2][1][qd] : mm(wc[f] - sm.w[s0][f][i - PX], sm.w[s0][f][i + PX] - wc[f]);
+            s[2][f] = f == BZ ? sm.db[r2][2][qd] : mm(wc[f] - sm.w[sm1][f][i], sm.w[sp1][f][i] - wc[f]);
+          }
+          const T ir = T(1) / wc[0];
+          T wh[8], dw[8];
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wh[f] = wc[f];
+          prim_terms<T, 0>(wc, s[0], gamma, ir, dw);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h0 * dw[f];
+          prim_terms<T, 1>(wc, s[1], gamma, ir, dw);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h1 * dw[f];
+          prim_terms<T, 2>(wc, s[2], gamma, ir, dw);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h2 * dw[f];
+          const int q = qidx(x, y);
+#pragma unroll
+          for (int f = 0; f < 8; ++f) {
+            sm.wh[r2][f][q] = wh[f];
+            sm.sx[f][q] = s[0][f];
+            sm.sy[f][q] = s[1][f];
+            sm.sz[r2][f][q] = s[2][f];
+          }
+          sm.ref[r3][0][q] = wh[3] * wh[6] - wh[2] * wh[7];
+          sm.ref[r3][1][q] = wh[1] * wh[7] - wh[3] * wh[5];
+          sm.ref[r3][2][q] = wh[2] * wh[5] - wh[1] * wh[6];
+        }
+      }
+  };
+  auto stage3 = [&](int p) {
+      // ---------------- S3: fluxes (x, y faces of plane p; z faces of face plane p)
+      {
+        const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
+        constexpr int NFX = (TX + 1) * (S::QY), NFY = (QX) * (TY + 1), NFZ = QX * S::QY, Q = S::Q;
+        const int nf = NFX + NFY + (p >= zlo ? NFZ : 0);
+        for (int c = threadIdx.x; c < nf; c += nth) {
+          // one face: direction D, its high-side cell (x, y) and the offset of its low-side cell
+          int D, x, y, lo;
+          const T *whl, *whr, *sl, *sr;
+          T* fo;
+          if (c < NFX) {  // x-face at x (cells x-1, x), y in [y0-1, y0+ty+1)
+            const int xi = c % (TX + 1), yi = c / (TX + 1);
+            if (xi > tx || yi >= ty + 2) continue;
+            D = 0; x = x0 + xi; y = y0 - 1 + yi; lo = -1;
+            whl = whr = &sm.wh[r2][0][0];
+            sl = sr = &sm.sx[0][0];
+            fo = &sm.fx[r2][0][0];
+          } else if (c < NFX + NFY) {  // y-face at y (cells y-1, y), x in [x0-1, x0+tx+1)
+            const int cc = c - NFX, xi = cc % QX, yi = cc / QX;
+            if (xi >= tx + 2 || yi > ty) continue;
+            D = 1; x = x0 - 1 + xi; y = y0 + yi; lo = -QX;
+            whl = whr = &sm.wh[r2][0][0];
+            sl = sr = &sm.sy[0][0];
+            fo = &sm.fy[r2][0][0];
+          } else {  // z-face at face plane p (cells p-1, p)
+            const int cc = c - NFX - NFY, xi = cc % QX, yi = cc / QX;
+            if (xi >= tx + 2 || yi >= ty + 2) continue;
+            D = 2; x = x0 - 1 + xi; y = y0 - 1 + yi; lo = 0;
+            whl = &sm.wh[rm][0][0];
+            whr = &sm.wh[r2][0][0];
+            sl = &sm.sz[rm][0][0];
+            sr = &sm.sz[r2][0][0];
+            fo = &sm.fz[r2][0][0];
+          }
+          const int q = qidx(x, y), ql = q + lo;
+          const int n = D, t = D == 2 ? 0 : D + 1, u = D == 0 ? 2 : D - 1;
+          // the predicted face states, read in the face's rotated order (rho, v_n,
+          // v_t, v_u, p, B_t, B_u), and the mean normal field; fluxes stored back by field
+          const int fi[7] = {RHO, MX + n, MX + t, MX + u, EN, BX + t, BX + u};
+          T qlv[7], qrv[7], fr[7];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            qlv[k] = whl[fi[k] * Q + ql] + T(0.5) * sl[fi[k] * Q + ql];
+            qrv[k] = whr[fi[k] * Q + q] - T(0.5) * sr[fi[k] * Q + q];
+          }
+          const T bnl = whl[(BX + n) * Q + ql] + T(0.5) * sl[(BX + n) * Q + ql];
+          const T bnr = whr[(BX + n) * Q + q] - T(0.5) * sr[(BX + n) * Q + q];
+          hlld_flux<T>(qlv, qrv, T(0.5) * (bnl + bnr), gamma, fr);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) fo[fi[k] * Q + q] = fr[k];
+          fo[(BX + n) * Q + q] = T(0);
+          if (capture) {  // a boundary face of a fine patch: keep its flux for the registers
+            const long long sl = bnd_face_slot(P, D, x, y, p);
+            if (sl >= 0) {
+              T* b = (T*)a.bnd + P.boff;
+              const long long F = bnd_faces_total(P.n);
+#pragma unroll
+              for (int k = 0; k < 5; ++k) b[fi[k] * F + sl] = fr[k];
+            }
+          }
+        }
+      }
+  };
+  auto stage4 = [&](int p) {
+      // ---------------- S4: edge EMFs
+      {
+        const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
+        const int r3 = (p + 3) % 3, rm3 = (p + 2) % 3;  // reference EMFs of planes p and p-1
+        constexpr int NEZ = (TX + 1) * (TY + 1), NEX = TX * (TY + 1), NEY = (TX + 1) * TY;
+        const int nez = p < zhi ? NEZ : 0;
+        for (int c = threadIdx.x; c < nez + NEX + NEY; c += nth) {
+          if (c < nez) {  // E_z at corner (x-1/2, y-1/2) of plane p: a = x, b = y
+            const int xi = c % (TX + 1), yi = c / (TX + 1);
+            if (xi > tx || yi > ty) continue;
+            const int x = x0 + xi, y = y0 + yi;
+            const int q11 = qidx(x, y), q01 = q11 - 1, q10 = q11 - QX, q00 = q11 - 1 - QX;
+            const T ea_hi = -sm.fx[r2][BY][q11], ea_lo = -sm.fx[r2][BY][q10];
+            const T eb_hi = sm.fy[r2][BX][q11], eb_lo = sm.fy[r2][BX][q01];
+            sm.ez[r2][q11] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[r3][2][q00], sm.ref[r3][2][q10],
+                                       sm.ref[r3][2][q01], sm.ref[r3][2][q11], sm.fx[r2][RHO][q10], sm.fx[r2][RHO][q11],
+                                       sm.fy[r2][RHO][q01], sm.fy[r2][RHO][q11]);
+            if (capture) bnd_store_edge<T>(a, P, 2, x, y, p, sm.ez[r2][q11]);
+          } else if (c < nez + NEX) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
+            const int cc = c - nez, xi = cc % TX, yi = cc / TX;
+            if (xi >= tx || yi > ty) continue;
+            const int x = x0 + xi, y = y0 + yi;
+            const int q = qidx(x, y), qm = q - QX;
+            // a-faces = y-faces at rows z = p-1, p; b-faces = z-faces at columns y-1, y
+            const T ea_lo = -sm.fy[rm][BZ][q], ea_hi = -sm.fy[r2][BZ][q];
+            const T eb_lo = sm.fz[r2][BY][qm], eb_hi = sm.fz[r2][BY][q];
+            sm.ex[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm3][0][qm], sm.ref[rm3][0][q], sm.ref[r3][0][qm],
+                                     sm.ref[r3][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
+                                     sm.fz[r2][RHO][q]);
+            if (capture) bnd_store_edge<T>(a, P, 0, x, y, p, sm.ex[r2][q]);
+          } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
+            const int cc = c - nez - NEX, xi = cc % (TX + 1), yi = cc / (TX + 1);
+            if (xi > tx || yi >= ty) continue;
+            const int x = x0 + xi, y = y0 + yi;
+            const int q = qidx(x, y), qm = q - 1;
+            // a-faces = z-faces at rows x-1, x; b-faces = x-faces at columns z = p-1, p
+            const T ea_lo = -sm.fz[r2][BX][qm], ea_hi = -sm.fz[r2][BX][q];
+            const T eb_lo = sm.fx[rm][BZ][q], eb_hi = sm.fx[r2][BZ][q];
+            // references: r00 = (z p-1, x-1), r10 = (z p, x-1), r01 = (z p-1, x), r11 = (z p, x)
+            sm.ey[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm3][1][qm], sm.ref[r3][1][qm], sm.ref[rm3][1][q],
+                                     sm.ref[r3][1][q], sm.fz[r2][RHO][qm], sm.fz[r2][RHO][q], sm.fx[rm][RHO][q],
+                                     sm.fx[r2][RHO][q]);
+            if (capture) bnd_store_edge<T>(a, P, 1, x, y, p, sm.ey[r2][q]);
+          }
+        }
+      }
+  };
+  auto stage5 = [&](int qz) {
       if (qz >= zlo && qz < zhi) {
+        const int p = qz + 1;
+        const int rq = (qz + 2) % 2, rp = (p + 2) % 2;
         const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
-        const bool top = qz == zhi - 1;
         for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
           const int xi = c % (TX + 1), yi = c / (TX + 1);
           if (xi >= nx || yi >= ny) continue;
-          const int L = (x0 + xi) + sy * (y0 + yi) + sz * qz;
+          const int x = x0 + xi, y = y0 + yi;
+          const bool in_x = x < x0 + tx, in_y = y < y0 + ty;
+          const int L = x + sy * y + sz * qz;
+          const int q = qidx(x, y);
+          const int u = c;
+          if (in_x && in_y) {
 #pragma unroll
-          for (int f = 0; f < 8; ++f) cp_async_elem<T>(&sm.up[f][c], U + f * fs + L);
-          if (top) cp_async_elem<T>(&sm.up[8][c], U + BZ * fs + L + sz);
-        }
-      }
-      cp_async_commit();
-    }
-    // ---------------- S2: slopes and predictor of plane p
-    if (p >= zlo - 1 && p <= zhi) {
-      const int sm1 = (p - 1 + 3) % 3, s0 = (p + 3) % 3, sp1 = (p + 1 + 3) % 3;
-      const int r2 = (p + 2) % 2;
-      for (int c = threadIdx.x; c < QX * S::QY; c += nth) {
-        const int xi = c % QX, yi = c / QX;
-        if (xi >= qx || yi >= qy) continue;
-        const int x = x0 - 1 + xi, y = y0 - 1 + yi;
-        const int i = widx(x, y);
-        T wc[8], s[3][8];
-        const int qd = qidx(x, y);
-#pragma unroll
-        for (int f = 0; f < 8; ++f) wc[f] = sm.w[s0][f][i];
-#pragma unroll
-        for (int f = 0; f < 8; ++f) {
-          s[0][f] = f == BX ? sm.db[r2][0][qd] : mm(wc[f] - sm.w[s0][f][i - 1], sm.w[s0][f][i + 1] - wc[f]);
-          s[1][f] = f == BY ? sm.db[r2][1][qd] : mm(wc[f] - sm.w[s0][f][i - PX], sm.w[s0][f][i + PX] - wc[f]);
-          s[2][f] = f == BZ ? sm.db[r2][2][qd] : mm(wc[f] - sm.w[sm1][f][i], sm.w[sp1][f][i] - wc[f]);
-        }
-        const T ir = T(1) / wc[0];
-        T wh[8], dw[8];
-#pragma unroll
-        for (int f = 0; f < 8; ++f) wh[f] = wc[f];
-        prim_terms<T, 0>(wc, s[0], gamma, ir, dw);
-#pragma unroll
-        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h0 * dw[f];
-        prim_terms<T, 1>(wc, s[1], gamma, ir, dw);
-#pragma unroll
-        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h1 * dw[f];
-        prim_terms<T, 2>(wc, s[2], gamma, ir, dw);
-#pragma unroll
-        for (int f = 0; f < 8; ++f) wh[f] = wh[f] - h2 * dw[f];
-        const int q = qidx(x, y);
-#pragma unroll
-        for (int f = 0; f < 8; ++f) {
-          sm.wh[r2][f][q] = wh[f];
-          sm.sx[f][q] = s[0][f];
-          sm.sy[f][q] = s[1][f];
-          sm.sz[r2][f][q] = s[2][f];
-        }
-        sm.ref[r2][0][q] = wh[3] * wh[6] - wh[2] * wh[7];
-        sm.ref[r2][1][q] = wh[1] * wh[7] - wh[3] * wh[5];
-        sm.ref[r2][2][q] = wh[2] * wh[5] - wh[1] * wh[6];
-      }
-    }
-    __syncthreads();
-    // ---------------- S3: fluxes (x, y faces of plane p; z faces of face plane p)
-    if (p >= zlo - 1 && p <= zhi) {
-      const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
-      constexpr int NFX = (TX + 1) * (S::QY), NFY = (QX) * (TY + 1), NFZ = QX * S::QY, Q = S::Q;
-      const int nf = NFX + NFY + (p >= zlo ? NFZ : 0);
-      for (int c = threadIdx.x; c < nf; c += nth) {
-        // one face: direction D, its high-side cell (x, y) and the offset of its low-side cell
-        int D, x, y, lo;
-        const T *whl, *whr, *sl, *sr;
-        T* fo;
-        if (c < NFX) {  // x-face at x (cells x-1, x), y in [y0-1, y0+ty+1)
-          const int xi = c % (TX + 1), yi = c / (TX + 1);
-          if (xi > tx || yi >= ty + 2) continue;
-          D = 0; x = x0 + xi; y = y0 - 1 + yi; lo = -1;
-          whl = whr = &sm.wh[r2][0][0];
-          sl = sr = &sm.sx[0][0];
-          fo = &sm.fx[r2][0][0];
-        } else if (c < NFX + NFY) {  // y-face at y (cells y-1, y), x in [x0-1, x0+tx+1)
-          const int cc = c - NFX, xi = cc % QX, yi = cc / QX;
-          if (xi >= tx + 2 || yi > ty) continue;
-          D = 1; x = x0 - 1 + xi; y = y0 + yi; lo = -QX;
-          whl = whr = &sm.wh[r2][0][0];
-          sl = sr = &sm.sy[0][0];
-          fo = &sm.fy[r2][0][0];
-        } else {  // z-face at face plane p (cells p-1, p)
-          const int cc = c - NFX - NFY, xi = cc % QX, yi = cc / QX;
-          if (xi >= tx + 2 || yi >= ty + 2) continue;
-          D = 2; x = x0 - 1 + xi; y = y0 - 1 + yi; lo = 0;
-          whl = &sm.wh[rm][0][0];
-          whr = &sm.wh[r2][0][0];
-          sl = &sm.sz[rm][0][0];
-          sr = &sm.sz[r2][0][0];
-          fo = &sm.fz[r2][0][0];
-        }
-        const int q = qidx(x, y), ql = q + lo;
-        const int n = D, t = D == 2 ? 0 : D + 1, u = D == 0 ? 2 : D - 1;
-        // the predicted face states, read in the face's rotated order (rho, v_n,
-        // v_t, v_u, p, B_t, B_u), and the mean normal field; fluxes stored back by field
-        const int fi[7] = {RHO, MX + n, MX + t, MX + u, EN, BX + t, BX + u};
-        T qlv[7], qrv[7], fr[7];
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-          qlv[k] = whl[fi[k] * Q + ql] + T(0.5) * sl[fi[k] * Q + ql];
-          qrv[k] = whr[fi[k] * Q + q] - T(0.5) * sr[fi[k] * Q + q];
-        }
-        const T bnl = whl[(BX + n) * Q + ql] + T(0.5) * sl[(BX + n) * Q + ql];
-        const T bnr = whr[(BX + n) * Q + q] - T(0.5) * sr[(BX + n) * Q + q];
-        hlld_flux<T>(qlv, qrv, T(0.5) * (bnl + bnr), gamma, fr);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) fo[fi[k] * Q + q] = fr[k];
-        fo[(BX + n) * Q + q] = T(0);
-        if (capture) {  // a boundary face of a fine patch: keep its flux for the registers
-          const long long sl = bnd_face_slot(P, D, x, y, p);
-          if (sl >= 0) {
-            T* b = (T*)a.bnd + P.boff;
-            const long long F = bnd_faces_total(P.n);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) b[fi[k] * F + sl] = fr[k];
+            for (int n = 0; n < 5; ++n) {
+              T v = sm.up[n][u];
+              v = v - dtd[0] * (sm.fx[rq][n][q + 1] - sm.fx[rq][n][q]);
+              v = v - dtd[1] * (sm.fy[rq][n][q + QX] - sm.fy[rq][n][q]);
+              v = v - dtd[2] * (sm.fz[rp][n][q] - sm.fz[rq][n][q]);
+              V[n * fs + L] = v;
+            }
+            // B_z of face plane qz (and the top face plane on the last plane)
+            {
+              T v = sm.up[BZ][u];
+              v = v - dtd[0] * (sm.ey[rq][q + 1] - sm.ey[rq][q]);
+              v = v + dtd[1] * (sm.ex[rq][q + QX] - sm.ex[rq][q]);
+              V[BZ * fs + L] = v;
+            }
+            if (qz == zhi - 1) {
+              T v = sm.up[8][u];
+              v = v - dtd[0] * (sm.ey[rp][q + 1] - sm.ey[rp][q]);
+              v = v + dtd[1] * (sm.ex[rp][q + QX] - sm.ex[rp][q]);
+              V[BZ * fs + L + sz] = v;
+            }
+          }
+          if (in_y) {  // B_x at (x, y, qz)
+            T v = sm.up[BX][u];
+            v = v - dtd[1] * (sm.ez[rq][q + QX] - sm.ez[rq][q]);
+            v = v + dtd[2] * (sm.ey[rp][q] - sm.ey[rq][q]);
+            V[BX * fs + L] = v;
+          }
+          if (in_x) {  // B_y at (x, y, qz)
+            T v = sm.up[BY][u];
+            v = v - dtd[2] * (sm.ex[rp][q] - sm.ex[rq][q]);
+            v = v + dtd[0] * (sm.ez[rq][q + 1] - sm.ez[rq][q]);
+            V[BY * fs + L] = v;
           }
         }
       }
-    }
+  };
+
+  // Schedule: three barriers per plane. Phase 1 pairs the fluxes of plane p
+  // with the primitives of plane p+2 (and the prefetch of the update plane);
+  // phase 2 the EMFs of plane p with the predictor of plane p+1; phase 3 the
+  // update of plane p-1. Rings: W 3 planes (S1(p+2) replaces W(p-1), which only
+  // S2(p) of the previous phase 2 read), reference EMFs 3 planes (S2(p+1)
+  // writes while S4(p) reads planes p and p-1), the rest 2 planes.
+  stage1(zlo - 2);
+  stage1(zlo - 1);
+  stage1(zlo);
+  __syncthreads();
+  stage2(zlo - 1);
+  __syncthreads();
+  for (int p = zlo - 1; p <= zhi; ++p) {
+    prefetch(p - 1);
+    stage3(p);
+    if (p + 2 <= zhi + 1) stage1(p + 2);
     __syncthreads();
-    // ---------------- S4: edge EMFs
-    if (p >= zlo && p <= zhi) {
-      const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
-      constexpr int NEZ = (TX + 1) * (TY + 1), NEX = TX * (TY + 1), NEY = (TX + 1) * TY;
-      const int nez = p < zhi ? NEZ : 0;
-      for (int c = threadIdx.x; c < nez + NEX + NEY; c += nth) {
-        if (c < nez) {  // E_z at corner (x-1/2, y-1/2) of plane p: a = x, b = y
-          const int xi = c % (TX + 1), yi = c / (TX + 1);
-          if (xi > tx || yi > ty) continue;
-          const int x = x0 + xi, y = y0 + yi;
-          const int q11 = qidx(x, y), q01 = q11 - 1, q10 = q11 - QX, q00 = q11 - 1 - QX;
-          const T ea_hi = -sm.fx[r2][BY][q11], ea_lo = -sm.fx[r2][BY][q10];
-          const T eb_hi = sm.fy[r2][BX][q11], eb_lo = sm.fy[r2][BX][q01];
-          sm.ez[r2][q11] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[r2][2][q00], sm.ref[r2][2][q10],
-                                     sm.ref[r2][2][q01], sm.ref[r2][2][q11], sm.fx[r2][RHO][q10], sm.fx[r2][RHO][q11],
-                                     sm.fy[r2][RHO][q01], sm.fy[r2][RHO][q11]);
-          if (capture) bnd_store_edge<T>(a, P, 2, x, y, p, sm.ez[r2][q11]);
-        } else if (c < nez + NEX) {  // E_x at (x, y-1/2, p-1/2): a = y, b = z
-          const int cc = c - nez, xi = cc % TX, yi = cc / TX;
-          if (xi >= tx || yi > ty) continue;
-          const int x = x0 + xi, y = y0 + yi;
-          const int q = qidx(x, y), qm = q - QX;
-          // a-faces = y-faces at rows z = p-1, p; b-faces = z-faces at columns y-1, y
-          const T ea_lo = -sm.fy[rm][BZ][q], ea_hi = -sm.fy[r2][BZ][q];
-          const T eb_lo = sm.fz[r2][BY][qm], eb_hi = sm.fz[r2][BY][q];
-          sm.ex[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][0][qm], sm.ref[rm][0][q], sm.ref[r2][0][qm],
-                                   sm.ref[r2][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
-                                   sm.fz[r2][RHO][q]);
-          if (capture) bnd_store_edge<T>(a, P, 0, x, y, p, sm.ex[r2][q]);
-        } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
-          const int cc = c - nez - NEX, xi = cc % (TX + 1), yi = cc / (TX + 1);
-          if (xi > tx || yi >= ty) continue;
-          const int x = x0 + xi, y = y0 + yi;
-          const int q = qidx(x, y), qm = q - 1;
-          // a-faces = z-faces at rows x-1, x; b-faces = x-faces at columns z = p-1, p
-          const T ea_lo = -sm.fz[r2][BX][qm], ea_hi = -sm.fz[r2][BX][q];
-          const T eb_lo = sm.fx[rm][BZ][q], eb_hi = sm.fx[r2][BZ][q];
-          // references: r00 = (z p-1, x-1), r10 = (z p, x-1), r01 = (z p-1, x), r11 = (z p, x)
-          sm.ey[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm][1][qm], sm.ref[r2][1][qm], sm.ref[rm][1][q],
-                                   sm.ref[r2][1][q], sm.fz[r2][RHO][qm], sm.fz[r2][RHO][q], sm.fx[rm][RHO][q],
-                                   sm.fx[r2][RHO][q]);
-          if (capture) bnd_store_edge<T>(a, P, 1, x, y, p, sm.ey[r2][q]);
-        }
-      }
-    }
+    if (p >= zlo) stage4(p);
+    if (p + 1 <= zhi) stage2(p + 1);
     cp_async_wait_all();
     __syncthreads();
-    // ---------------- S5: update cell plane q = p-1
-    const int qz = p - 1;
-    if (qz >= zlo && qz < zhi) {
-      const int rq = (qz + 2) % 2, rp = (p + 2) % 2;
-      const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
-      for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
-        const int xi = c % (TX + 1), yi = c / (TX + 1);
-        if (xi >= nx || yi >= ny) continue;
-        const int x = x0 + xi, y = y0 + yi;
-        const bool in_x = x < x0 + tx, in_y = y < y0 + ty;
-        const int L = x + sy * y + sz * qz;
-        const int q = qidx(x, y);
-        const int u = c;
-        if (in_x && in_y) {
-#pragma unroll
-          for (int n = 0; n < 5; ++n) {
-            T v = sm.up[n][u];
-            v = v - dtd[0] * (sm.fx[rq][n][q + 1] - sm.fx[rq][n][q]);
-            v = v - dtd[1] * (sm.fy[rq][n][q + QX] - sm.fy[rq][n][q]);
-            v = v - dtd[2] * (sm.fz[rp][n][q] - sm.fz[rq][n][q]);
-            V[n * fs + L] = v;
-          }
-          // B_z of face plane qz (and the top face plane on the last plane)
-          {
-            T v = sm.up[BZ][u];
-            v = v - dtd[0] * (sm.ey[rq][q + 1] - sm.ey[rq][q]);
-            v = v + dtd[1] * (sm.ex[rq][q + QX] - sm.ex[rq][q]);
-            V[BZ * fs + L] = v;
-          }
-          if (qz == zhi - 1) {
-            T v = sm.up[8][u];
-            v = v - dtd[0] * (sm.ey[rp][q + 1] - sm.ey[rp][q]);
-            v = v + dtd[1] * (sm.ex[rp][q + QX] - sm.ex[rp][q]);
-            V[BZ * fs + L + sz] = v;
-          }
-        }
-        if (in_y) {  // B_x at (x, y, qz)
-          T v = sm.up[BX][u];
-          v = v - dtd[1] * (sm.ez[rq][q + QX] - sm.ez[rq][q]);
-          v = v + dtd[2] * (sm.ey[rp][q] - sm.ey[rq][q]);
-          V[BX * fs + L] = v;
-        }
-        if (in_x) {  // B_y at (x, y, qz)
-          T v = sm.up[BY][u];
-          v = v - dtd[2] * (sm.ex[rp][q] - sm.ex[rq][q]);
-          v = v + dtd[0] * (sm.ez[rq][q + 1] - sm.ez[rq][q]);
-          V[BY * fs + L] = v;
-        }
-      }
-    }
-    // no barrier: the next S1 writes only the W ring slot that S2 no longer reads
+    stage5(p - 1);
+    __syncthreads();
   }
 }
 

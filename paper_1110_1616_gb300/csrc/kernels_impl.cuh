@@ -864,6 +864,9 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
   int i, j, k;
   T tmax = T(0);  // per-thread maximum in the working type; the reduction is FP64
   bool bad = false;
+  // loop invariants in the working type (conversions from FP64 issue on the FP64 pipe)
+  const T g = (T)a.gamma;
+  const T ix[3] = {(T)a.idx[0], (T)a.idx[1], (T)a.idx[2]};
   for (int tc = blockIdx.x * TPB + threadIdx.x;; tc += gridDim.x * TPB) {
     if (!region_cell<DIM>(P, 0, tc, i, j, k)) break;
     const int L = lidx(P, i, j, k);
@@ -882,12 +885,11 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
     if (!(w[0] > T(0)) || !(w[4] > T(0))) bad = true;
     else {
       T rr = T(0);
-      const T g = (T)a.gamma;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const int t = (d + 1) % 3, uu = (d + 2) % 3;
         const T cf = cfast<T>(w[0], w[4], w[5 + d], w[5 + t], w[5 + uu], g);
-        rr = rr + (dabs(w[1 + d]) + cf) * (T)a.idx[d];
+        rr = rr + (dabs(w[1 + d]) + cf) * ix[d];
       }
       if (!(rr < (T)INFINITY)) bad = true;  // NaN or infinite
       else if (rr > tmax) tmax = rr;

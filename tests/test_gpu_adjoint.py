@@ -284,15 +284,22 @@ def test_velocity_gradient_against_central_differences():
         return u
 
     checked = 0
-    for trial in range(4):
+    seen = []
+    for trial in range(10):
         x = np.arange(n, dtype=np.float64)
         dv = [np.cos(2 * np.pi * (rng.integers(1, 4) * x / n) + rng.uniform(0, 2 * np.pi)) for _ in range(3)]
+        # |h dv| up to 1e-6 (velocities of order 0.3); a direction whose
+        # differences at h, h/4, h/16 disagree crosses a limiter or HLLD branch
+        # change of some cell and is not used
         h = 1e-6 / max(np.abs(np.concatenate(dv)).max(), 1e-30)
         ad = float(sum((gv[c * n:(c + 1) * n] * dv[c]).sum() for c in range(3)))
         fds = [(loss(moved(dv, hh)) - loss(moved(dv, -hh))) / (2 * hh) for hh in (h, h / 4, h / 16)]
+        seen.append((fds, ad))
         for a_, b_ in zip(fds, fds[1:]):
-            if abs(a_ - b_) <= 1e-7 * abs(b_):
+            if abs(a_ - b_) <= 1e-6 * abs(b_):
                 assert abs(b_ - ad) <= 1e-6 * abs(ad), (trial, fds, ad)
                 checked += 1
                 break
-    assert checked >= 2
+        if checked >= 3:
+            break
+    assert checked >= 3, seen
