@@ -253,7 +253,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
     ctx.regrid(theta, pb.nlev)
     tiles = ctx.autotune(3)
     ctx.step(1, want_dt=False)
-    updates, leaves, t_steps, t_regrid, breakdown = 0, 0, 0.0, 0.0, [0, 0, 0, 0, 0]
+    updates, leaves, t_steps, t_regrid, breakdown = 0, 0, 0.0, 0.0, [0, 0, 0, 0, 0, 0]
     nreg = 0
     for i in range(0, steps, regrid_every):
         k = min(regrid_every, steps - i)
@@ -269,6 +269,7 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
             nreg += 1
             for q in range(5):
                 breakdown[q] += ctx.query(A.Q_REGRID_FLAG_US + q)
+            breakdown[5] += ctx.query(A.Q_REGRID_TRANSFER_MAPS_US)
             ctx.autotune(2)
     # the final hierarchy in three schedules: finer levels on side streams (the
     # default), one stream in the recursive order, and the device work queue
@@ -294,7 +295,8 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
            "steps": steps, "regrid_every": regrid_every, "theta": theta, "regrids": nreg,
            "regrid_ms_mean": 1e3 * t_regrid / max(nreg, 1),
            "regrid_host_us_mean": {k: v / max(nreg, 1) for k, v in
-                                   zip(("flag", "cluster", "build", "transfer", "build_host_maps"), breakdown)},
+                                   zip(("flag", "cluster", "build", "transfer", "build_maps", "transfer_maps"),
+                                       breakdown)},
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
            "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
            "final_hierarchy_ms_per_step": {"side_streams": ms_c / 2, "serial": ms_s / 2, "device_queue": ms_q / 2,
@@ -380,8 +382,9 @@ def shock_clump_leg(steps=10, theta=0.1):
            "cells_per_level": [cells[l] for l in sorted(cells)], "patches": ctx.query(A.Q_NPATCH),
            "arena_gb": ctx.query(A.Q_ARENA_BYTES) / 1e9, "regrid_s": t_regrid,
            "floors": {"rho": 1e-8, "p": 1e-8, "raises": ctx.query(A.Q_FLOOR_EVENTS)},
-           "regrid_host_us": {k: ctx.query(A.Q_REGRID_FLAG_US + i)
-                              for i, k in enumerate(("flag", "cluster", "build", "transfer"))},
+           "regrid_host_us": dict({k: ctx.query(A.Q_REGRID_FLAG_US + i)
+                                   for i, k in enumerate(("flag", "cluster", "build", "transfer", "build_maps"))},
+                                  transfer_maps=ctx.query(A.Q_REGRID_TRANSFER_MAPS_US)),
            "tiles": tiles,
            "workload": "shock_clump3d_64_5lev: Mach-10 shock into a lognormal (sigma 1, slope -11/3, contrast 10) "
                        "clump r 0.15; B (sqrt2,0,0); inflow x-low, outflow elsewhere; mixed precision"}

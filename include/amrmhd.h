@@ -385,14 +385,17 @@ amrmhd_status amrmhd_get_patches(amrmhd_ctx* ctx, amrmhd_patch* out, int32_t cap
 enum {
   AMRMHD_Q_NPATCH = 0, AMRMHD_Q_NLEVEL = 1, AMRMHD_Q_CELLS = 2, AMRMHD_Q_CELL_UPDATES_PER_STEP = 3,
   AMRMHD_Q_ARENA_BYTES = 4, AMRMHD_Q_KERNEL_LAUNCHES = 5,
-  /* host wall time of the last amrmhd_regrid in microseconds: flagging (fill,
-   * flag kernel, list copy), clustering, building the stage hierarchies, maps
-   * and arenas, and the data transfer */
+  /* host wall time of the last amrmhd_regrid in microseconds: flagging (the
+   * fills; with the host clustering also the flag kernel and list copy),
+   * clustering, building the stage hierarchies, maps and arenas, and the data
+   * transfer */
   AMRMHD_Q_REGRID_FLAG_US = 6, AMRMHD_Q_REGRID_CLUSTER_US = 7, AMRMHD_Q_REGRID_BUILD_US = 8,
   AMRMHD_Q_REGRID_TRANSFER_US = 9,
-  /* of AMRMHD_Q_REGRID_BUILD_US, the host building of hierarchies and maps
-   * (the rest is device memory and map upload) */
+  /* of AMRMHD_Q_REGRID_BUILD_US, the building of hierarchies and maps
+   * (amrmhd_set_hierarchy; the rest is device memory and map upload) */
   AMRMHD_Q_REGRID_MAPS_US = 10,
+  /* of AMRMHD_Q_REGRID_TRANSFER_US, the building of the transfer maps */
+  AMRMHD_Q_REGRID_TRANSFER_MAPS_US = 12,
   /* raises by the density and pressure floors since bind_arena (amrmhd_set_floors);
    * synchronises the stream */
   AMRMHD_Q_FLOOR_EVENTS = 11
@@ -454,7 +457,20 @@ enum {
                               launches of its sub-step: 1 (default) so that every launch's predicted
                               total work (the finer levels' tiles included) reaches one common level,
                               the paper's load balancing (Sec. 5) with the launches of a coarse step
-                              as its processors; 0 equal numbers of tiles per launch */
+                              as its processors; 0 equal numbers of tiles per launch */,
+  AMRMHD_OPT_DEVICE_MAPS = 10 /* where amrmhd_set_hierarchy builds the register, reflux and restriction
+                              maps (the coarse-fine faces and edges of the synchronize step, Sec. 4, and
+                              the restricted cells and faces): -1 (default) on the device when the
+                              process sees one, else on the host; 1 on the device (then
+                              amrmhd_set_hierarchy needs a device and returns AMRMHD_ECUDA or
+                              AMRMHD_ENOMEM if it fails); 0 on the host. Both give the same rows in the
+                              same order (amrmhd_export_map copies device-built rows back on demand).
+                              Takes effect at the next amrmhd_set_hierarchy or amrmhd_regrid. */,
+  AMRMHD_OPT_DEVICE_CLUSTER = 11 /* where amrmhd_regrid clusters the flagged cells into new boxes (its
+                              steps 2-4): 1 (default) on the device (flag test, 2-cell buffer and
+                              block marks in dense bytes of the clustering frame; only the block marks
+                              are copied back for the greedy merge), 0 on the host (the flag list is
+                              copied back). Both give the same boxes in the same order. */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 

@@ -22,6 +22,9 @@ UNITS = [
     ("adjoint.cu", ["--fmad=false"]),
     ("regrid_api.cu", []),
     ("partition.cu", []),
+    ("maps_dev.cu", []),
+    ("regrid_dev.cu", []),
+    ("boxes_dev.cu", []),
 ]
 HOST_UNITS = ["hierarchy.cpp", "regrid.cpp"]
 HEADERS = ["hierarchy.hpp", "kernels.hpp", "kernels_impl.cuh", "kernels_fused.cuh", "mhd_device.cuh", "ctx.hpp",

@@ -656,6 +656,7 @@ amrmhd_status check_bound(amrmhd_ctx* ctx) {
 const std::vector<int32_t>* map_vec(amrmhd_ctx* ctx, int which, int* width) {
   amrmhd::Hierarchy& H = ctx->H;
   if (which == AMRMHD_MAP_GHOST_CELLS || which == AMRMHD_MAP_GHOST_FACES) H.expand_ghost_rows();
+  else if (download_register_maps(ctx) != AMRMHD_OK) return nullptr;
   switch (which) {
     case AMRMHD_MAP_GHOST_CELLS: *width = 5; return &H.ghost_cells;
     case AMRMHD_MAP_GHOST_FACES: *width = 6; return &H.ghost_faces;
@@ -701,6 +702,8 @@ amrmhd_status amrmhd_create(const amrmhd_config* cfg, void* cuda_stream, amrmhd_
 amrmhd_status amrmhd_destroy(amrmhd_ctx* ctx) {
   if (!ctx) return AMRMHD_EINVAL;
   free_device(ctx);
+  if (ctx->d_maps) cudaFree(ctx->d_maps);
+  if (ctx->d_cluster) cudaFree(ctx->d_cluster);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
   return AMRMHD_OK;
@@ -729,6 +732,8 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   else if (option == AMRMHD_OPT_QUEUE_TILE && (value == 2 || value == 3)) ctx->opt_queue_tile = value;
   else if (option == AMRMHD_OPT_QUEUE_WITHHOLD && (value == 0 || value == 1)) ctx->opt_queue_withhold = value;
   else if (option == AMRMHD_OPT_QUEUE_BALANCE && (value == 0 || value == 1)) ctx->opt_queue_balance = value;
+  else if (option == AMRMHD_OPT_DEVICE_MAPS && value >= -1 && value <= 1) ctx->opt_device_maps = value;
+  else if (option == AMRMHD_OPT_DEVICE_CLUSTER && (value == 0 || value == 1)) ctx->opt_device_cluster = value;
   else return fail(ctx, AMRMHD_EINVAL, "unknown option or value");
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
@@ -749,7 +754,17 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
   }
   H.max_level = ctx->cfg.max_level;
   H.ghost_from = ctx->stage_light ? ctx->stage_ghost_from : 0;
-  H.with_registers = !ctx->stage_light;
+  if (ctx->d_maps) { cudaFree(ctx->d_maps); ctx->d_maps = nullptr; }
+  ctx->dmaps = ctx->dmaps_host = false;
+  bool dev_maps = ctx->opt_device_maps == 1;
+  if (ctx->opt_device_maps < 0) {
+    int ndev = 0;
+    dev_maps = cudaGetDeviceCount(&ndev) == cudaSuccess && ndev > 0;
+    cudaGetLastError();  // a host without a device reports an error here: not sticky, cleared
+  }
+  H.ghost_elsewhere = dev_maps;
+  const bool dev_regs = dev_maps && !ctx->stage_light;
+  H.with_registers = !ctx->stage_light && !dev_maps;
   std::vector<int32_t> rows(7 * (size_t)n);
   for (int i = 0; i < n; ++i) {
     rows[7 * i] = patches[i].level;
@@ -757,6 +772,11 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
   }
   int st = H.build(rows.data(), n);
   if (st != AMRMHD_OK) return fail(ctx, (amrmhd_status)st, H.err);
+  if (dev_maps) {
+    amrmhd_status ds = device_ghost_boxes(ctx);
+    if (ds == AMRMHD_OK && dev_regs) ds = device_register_maps(ctx);
+    if (ds != AMRMHD_OK) return ds;
+  }
   // arena layout: patches in (level, id) order
   const int np = (int)H.p.size();
   const size_t elem = ctx->ops->elem;
@@ -789,8 +809,8 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
         bacc += 5 * amrk::bnd_faces_total(H.p[q].n) + amrk::bnd_edges_total(H.p[q].n);
       }
   ctx->bnd_elems = bacc;
-  ctx->ncf = (int64_t)H.cf_faces.size() / 7;
-  ctx->nce = (int64_t)H.cf_edges.size() / 6;
+  ctx->ncf = ctx->dmaps ? ctx->dmap_n[0] : (int64_t)H.cf_faces.size() / 7;
+  ctx->nce = ctx->dmaps ? ctx->dmap_n[1] : (int64_t)H.cf_edges.size() / 6;
   for (int k = 0; k < 4; ++k) {
     ctx->poff[k].assign(np, 0);
     long long t = 0;
@@ -846,35 +866,36 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     P.soff = ctx->soff[q];
     P.boff = ctx->boff[q];
   }
-  ctx->dP = dbuf<DPatch>(ctx, np, &e);
+  // the patch table, patch ids, packed-I/O offsets, scalars, CFL slots, error
+  // word, floor count and dt history: one device block, one copy
+  size_t o = 0;
+  auto carve = [&](size_t bytes) { const size_t r = o; o = align256(o + bytes); return r; };
+  const size_t oP = carve(sizeof(DPatch) * np), oI = carve(sizeof(int) * np);
+  size_t oO[4];
+  for (int k = 0; k < 4; ++k) oO[k] = carve(sizeof(long long) * np);
+  const size_t oT = carve(sizeof(long long*) * 4), oS = carve(sizeof(double) * (2 + nlev)),
+               oL = carve(sizeof(unsigned long long) * (nlev + 1)), oE = carve(sizeof(unsigned int)),
+               oF = carve(sizeof(unsigned long long)), oH = carve(sizeof(double) * kHistCap);
+  char* blk = dbuf<char>(ctx, o, &e);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  CU(cudaMemcpy(ctx->dP, hp.data(), sizeof(DPatch) * np, cudaMemcpyHostToDevice));
-  std::vector<int> iota(np);
-  for (int q = 0; q < np; ++q) iota[q] = q;
-  ctx->d_iota = dbuf<int>(ctx, np, &e);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-  CU(cudaMemcpy(ctx->d_iota, iota.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+  std::vector<char> img(oH, 0);  // everything before the history (zero scalars, slots, counters)
+  std::memcpy(img.data() + oP, hp.data(), sizeof(DPatch) * np);
+  for (int q = 0; q < np; ++q) ((int*)(img.data() + oI))[q] = q;
   for (int k = 0; k < 4; ++k) {
-    ctx->d_poff[k] = dbuf<long long>(ctx, np, &e);
-    if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-    CU(cudaMemcpy(ctx->d_poff[k], ctx->poff[k].data(), sizeof(long long) * np, cudaMemcpyHostToDevice));
+    std::memcpy(img.data() + oO[k], ctx->poff[k].data(), sizeof(long long) * np);
+    ctx->d_poff[k] = (long long*)(blk + oO[k]);
+    ((long long**)(img.data() + oT))[k] = ctx->d_poff[k];
   }
-  ctx->d_poff_tab = dbuf<const long long*>(ctx, 4, &e);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-  CU(cudaMemcpy(ctx->d_poff_tab, ctx->d_poff, sizeof(long long*) * 4, cudaMemcpyHostToDevice));
-  ctx->d_scal = dbuf<double>(ctx, 2 + nlev, &e);
-  ctx->d_slots = dbuf<unsigned long long>(ctx, nlev + 1, &e);
-  ctx->d_err = dbuf<unsigned int>(ctx, 1, &e);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-  CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
-  ctx->d_floor_events = dbuf<unsigned long long>(ctx, 1, &e);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
-  CU(cudaMemset(ctx->d_floor_events, 0, sizeof(unsigned long long)));
-  CU(cudaMemset(ctx->d_slots, 0, sizeof(unsigned long long) * (nlev + 1)));
-  CU(cudaMemset(ctx->d_scal, 0, sizeof(double) * (2 + nlev)));
+  CU(cudaMemcpy(blk, img.data(), img.size(), cudaMemcpyHostToDevice));
+  ctx->dP = (DPatch*)(blk + oP);
+  ctx->d_iota = (int*)(blk + oI);
+  ctx->d_poff_tab = (const long long**)(blk + oT);
+  ctx->d_scal = (double*)(blk + oS);
+  ctx->d_slots = (unsigned long long*)(blk + oL);
+  ctx->d_err = (unsigned int*)(blk + oE);
+  ctx->d_floor_events = (unsigned long long*)(blk + oF);
   ctx->hist_cap = kHistCap;
-  ctx->d_hist = dbuf<double>(ctx, kHistCap, &e);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
+  ctx->d_hist = (double*)(blk + oH);
   // per-level lists: gathered into one host image (each list 256-byte aligned),
   // then one device allocation and one copy
   ctx->lev.assign(nlev, LevelDev());
@@ -1014,12 +1035,26 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
         return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);
       };
-      ok = upload(slice(H.cf_faces, H.rng_cf_faces[l], 7), L.cf_faces, 7) &&
-           upload(slice(H.cf_edges, H.rng_cf_edges[l], 6), L.cf_edges, 6) &&
-           upload(slice(H.emf_faces, H.rng_emf_faces[l], 8), L.emf_faces, 8) &&
-           upload(slice(H.restrict_cells, H.rng_restrict_cells[l], 5), L.restrict_cells, 5) &&
-           upload(slice(H.restrict_faces, H.rng_restrict_faces[l], 6), L.restrict_faces, 6) &&
-           upload(slice(H.reflux_cells, H.rng_reflux_cells[l], 9), L.reflux_cells, 9);
+      if (ctx->dmaps) {
+        // built on the device: the level's slices of the six lists
+        auto dslice = [&](int list, const std::array<int64_t, 2>& r, int w, DevList& out) {
+          out.n = r[1] - r[0];
+          out.p = out.n ? ctx->d_maps + ctx->dmap_off[list] + w * r[0] : nullptr;
+        };
+        dslice(0, H.rng_cf_faces[l], 7, L.cf_faces);
+        dslice(1, H.rng_cf_edges[l], 6, L.cf_edges);
+        dslice(2, H.rng_emf_faces[l], 8, L.emf_faces);
+        dslice(3, H.rng_restrict_cells[l], 5, L.restrict_cells);
+        dslice(4, H.rng_restrict_faces[l], 6, L.restrict_faces);
+        dslice(5, H.rng_reflux_cells[l], 9, L.reflux_cells);
+      } else {
+        ok = upload(slice(H.cf_faces, H.rng_cf_faces[l], 7), L.cf_faces, 7) &&
+             upload(slice(H.cf_edges, H.rng_cf_edges[l], 6), L.cf_edges, 6) &&
+             upload(slice(H.emf_faces, H.rng_emf_faces[l], 8), L.emf_faces, 8) &&
+             upload(slice(H.restrict_cells, H.rng_restrict_cells[l], 5), L.restrict_cells, 5) &&
+             upload(slice(H.restrict_faces, H.rng_restrict_faces[l], 6), L.restrict_faces, 6) &&
+             upload(slice(H.reflux_cells, H.rng_reflux_cells[l], 9), L.reflux_cells, 9);
+      }
       L.cf_face0 = H.rng_cf_faces[l][0];
       L.cf_edge0 = H.rng_cf_edges[l][0];
     }
@@ -1481,6 +1516,7 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
     case AMRMHD_Q_REGRID_BUILD_US:
     case AMRMHD_Q_REGRID_TRANSFER_US:
     case AMRMHD_Q_REGRID_MAPS_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
+    case AMRMHD_Q_REGRID_TRANSFER_MAPS_US: *value = ctx->regrid_us[5]; return AMRMHD_OK;
     case AMRMHD_Q_FLOOR_EVENTS: {
       unsigned long long v = 0;
       if (ctx->bound && ctx->d_floor_events) {

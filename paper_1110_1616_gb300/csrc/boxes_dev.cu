@@ -1,0 +1,882 @@
+// Ghost-fill boxes and regrid transfer boxes built on the device: the rows of
+// the host builders (hierarchy.cpp's ghost boxes, regrid.cpp's transfer_maps)
+// bit for bit and in the same order.
+//
+// A task is one patch and one kind of position: d = -1 its cells, d >= 0 its
+// d-faces. Every position of the task's box gets a label id:
+//
+// * ghost boxes (Sec. 2 and 4: the ghost zones of a patch, filled from its
+//   same-level neighbours, by prolongation from the coarser level, or from the
+//   physical boundary): the same-level neighbour (with its periodic shift)
+//   holding the position, on a face held by two the smaller (patch, local
+//   index); else the first coarse candidate and periodic image holding the
+//   parent cell; outside a bounded side the boundary state; the patch's own
+//   positions are not labelled;
+// * transfer boxes (Sec. 2, the overlap step of a regrid): a copy from the old
+//   fine patch (and shift) holding the position where the old fine level
+//   covered the parent cell (on a face between two old patches the smaller
+//   (patch, local index)), else a prolongation from the new coarse patch.
+//
+// Equal ids are then merged greedily into boxes (x runs, then y rows, then z
+// slabs, in raster order of the first position), the host builders' merge, by
+// one warp with warp-wide comparisons. A task whose label grid fits in shared
+// memory is labelled and merged by one CTA there; larger tasks use a grid in
+// global memory. Candidate lists are pruned on the host to the entries that
+// can meet the task's box, in the host builders' order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.hpp"
+
+namespace amrbx {
+
+struct BPatch {
+  int lo[3], n[3], ext[3], level;
+};
+
+struct BTask {
+  int q, d;          // patch; -1 its cells, else its d-faces
+  int ex[3], g0[3];  // the label box and the global position of its local origin
+  int s0, s1;        // ghost: same-level (patch, shift) entries; transfer: old (patch, shift) entries, in pairs
+  int p0, p1;        // ghost: prolongation (coarse patch, image) entries in pairs; transfer: coarse ids in ids
+  int touches;       // ghost: the box reaches outside a bounded side
+  int transfer;      // 1: a transfer task
+  long long go;      // its grid in global memory (large tasks), else -1
+};
+
+struct BArgs {
+  int dim;
+  int base[3], per[3], bc[3][2];
+  const BPatch* P;   // the (new) hierarchy's patches
+  const BPatch* PO;  // transfer: the old hierarchy's patches
+  int have_old;      // transfer: the old hierarchy has the level
+  const BTask* T;
+  const int* pairs;  // (patch, code) entries
+  const int* ids;    // transfer: coarse candidate ids
+  int* G;            // label grids of the large tasks
+  long long* cnt;    // boxes per task
+  const long long* first;
+  int* out_cells;
+  int* out_faces;
+  unsigned long long* err;  // smallest (task << 32 | position) without a source
+};
+
+__host__ __device__ __forceinline__ int Nl(const BArgs& a, int l, int e) { return e < a.dim ? (a.base[e] << l) : 1; }
+
+__host__ __device__ __forceinline__ void shift_of(int code, int* s) {
+  s[0] = code % 3 - 1;
+  s[1] = (code / 3) % 3 - 1;
+  s[2] = code / 9 - 1;
+}
+
+__host__ __device__ __forceinline__ void decode(const BTask& T, long long t, int* x) {
+  x[0] = (int)(t % T.ex[0]);
+  x[1] = (int)((t / T.ex[0]) % T.ex[1]);
+  x[2] = (int)(t / ((long long)T.ex[0] * T.ex[1]));
+}
+
+// ---- ghost boxes
+
+// label of position t of ghost task T: -1 the patch's own position, -3 no source
+__host__ __device__ inline int ghost_label(const BArgs& a, const BTask& T, long long t) {
+  const BPatch& P = a.P[T.q];
+  const int l = P.level, d = T.d, dim = a.dim;
+  const int ns = T.s1 - T.s0, np = T.p1 - T.p0;
+  int x[3];
+  decode(T, t, x);
+  bool own = true;
+  for (int e = 0; e < dim; ++e) own = own && x[e] >= 4 && x[e] < P.n[e] + 4 + (e == d ? 1 : 0);
+  if (own) return -1;
+  const int g[3] = {T.g0[0] + x[0], T.g0[1] + x[1], T.g0[2] + x[2]};
+  if (T.touches) {  // outside a bounded side: the boundary state
+    bool out = false, inflow = false;
+    int code = 0, w3 = 1;
+    for (int e = 0; e < dim; ++e, w3 *= 3) {
+      if (a.per[e]) continue;
+      const int top = e == d ? Nl(a, l, e) : Nl(a, l, e) - 1;
+      if (g[e] < 0) { out = true; code += 1 * w3; inflow |= a.bc[e][0] == 2; }
+      else if (g[e] > top) { out = true; code += 2 * w3; inflow |= a.bc[e][1] == 2; }
+    }
+    if (out) return ns + np + (inflow ? 27 : code);
+  }
+  // same-level neighbours: a cell lies in one; a face held by two goes to the
+  // smaller (patch, local index)
+  int id = -1, bq = 0, bL = 0;
+  for (int i = T.s0; i < T.s1; ++i) {
+    const int qq = a.pairs[2 * i];
+    const BPatch& Q = a.P[qq];
+    int s[3];
+    shift_of(a.pairs[2 * i + 1], s);
+    bool in = true;
+    int dl[3] = {0, 0, 0};
+    for (int e = 0; e < dim; ++e) {
+      const int o = s[e] * Nl(a, l, e);
+      in = in && x[e] >= Q.lo[e] + o - T.g0[e] && x[e] < Q.lo[e] + Q.n[e] + o + (e == d ? 1 : 0) - T.g0[e];
+      dl[e] = P.lo[e] - Q.lo[e] - o;
+    }
+    if (!in) continue;
+    const int L = (x[0] + dl[0]) + Q.ext[0] * ((x[1] + dl[1]) + Q.ext[1] * (x[2] + dl[2]));
+    if (d < 0 || id < 0 || qq < bq || (qq == bq && L < bL)) { id = i - T.s0; bq = qq; bL = L; }
+  }
+  if (id >= 0) return id;
+  // prolongation: the first coarse candidate and image holding the parent cell
+  for (int j = T.p0; j < T.p1; ++j) {
+    const BPatch& C = a.P[a.pairs[2 * j]];
+    int w[3];
+    shift_of(a.pairs[2 * j + 1], w);
+    bool in = true;
+    for (int e = 0; e < dim; ++e) {
+      const int aux = w[e] * Nl(a, l, e);
+      const int top = (e == d && !a.per[e] && C.lo[e] + C.n[e] == Nl(a, l - 1, e)) ? 1 : 0;
+      in = in && x[e] >= 2 * C.lo[e] - aux - T.g0[e] && x[e] < 2 * (C.lo[e] + C.n[e]) + top - aux - T.g0[e];
+    }
+    if (in) return ns + (j - T.p0);
+  }
+  return -3;
+}
+
+__host__ __device__ inline void ghost_row(const BArgs& a, const BTask& T, int id, int* row) {
+  const BPatch& P = a.P[T.q];
+  const int l = P.level, dim = a.dim, ns = T.s1 - T.s0, np = T.p1 - T.p0;
+  int kind, src, aux[3] = {0, 0, 0};
+  if (id < ns) {
+    const int i = T.s0 + id;
+    src = a.pairs[2 * i];
+    kind = 0;
+    int s[3];
+    shift_of(a.pairs[2 * i + 1], s);
+    for (int e = 0; e < dim; ++e) aux[e] = P.lo[e] - a.P[src].lo[e] - s[e] * Nl(a, l, e);
+  } else if (id < ns + np) {
+    const int j = T.p0 + id - ns;
+    kind = 1;
+    src = a.pairs[2 * j];
+    int w[3];
+    shift_of(a.pairs[2 * j + 1], w);
+    for (int e = 0; e < dim; ++e) aux[e] = w[e] * Nl(a, l, e);
+  } else if (id < ns + np + 27) {
+    kind = 2;
+    src = T.q;
+    int code = id - ns - np;
+    for (int e = 0; e < 3; ++e) {
+      const int digit = code % 3;
+      code /= 3;
+      const int top = e == T.d ? Nl(a, l, e) : Nl(a, l, e) - 1;
+      aux[e] = (e >= dim || digit == 0) ? -1 : (digit == 1 ? 0 : top);
+    }
+  } else {
+    kind = 3;
+    src = -1;
+  }
+  row[0] = T.q;
+  row[1] = T.d;
+  row[2] = kind;
+  row[3] = src;
+  row[10] = aux[0];
+  row[11] = aux[1];
+  row[12] = aux[2];
+}
+
+// ---- transfer boxes
+
+// the old (patch, shift) entry holding fine cell h, or -1
+__host__ __device__ inline int old_owner(const BArgs& a, const BTask& T, const int* h) {
+  const int lf = a.P[T.q].level;
+  for (int i = T.s0; i < T.s1; ++i) {
+    const BPatch& O = a.PO[a.pairs[2 * i]];
+    int s[3];
+    shift_of(a.pairs[2 * i + 1], s);
+    bool in = true;
+    for (int e = 0; e < a.dim; ++e) {
+      const int o = s[e] * Nl(a, lf, e);
+      in = in && h[e] >= O.lo[e] + o && h[e] < O.lo[e] + O.n[e] + o;
+    }
+    if (in) return i;
+  }
+  return -1;
+}
+
+// coarse cell c covered by the old fine level
+__host__ __device__ inline bool old_covers(const BArgs& a, const BTask& T, const int* c) {
+  if (!a.have_old) return false;
+  int h[3];
+  for (int e = 0; e < 3; ++e) h[e] = e < a.dim ? 2 * c[e] : 0;
+  return old_owner(a, T, h) >= 0;
+}
+
+// the new coarse patch candidate holding coarse cell c (periodic wrap), or -1
+__host__ __device__ inline int new_coarse(const BArgs& a, const BTask& T, const int* c) {
+  const int lc = a.P[T.q].level - 1;
+  int w[3];
+  for (int e = 0; e < 3; ++e) {
+    w[e] = c[e];
+    if (e < a.dim && a.per[e]) { const int n = Nl(a, lc, e); w[e] = (w[e] % n + n) % n; }
+  }
+  for (int j = T.p0; j < T.p1; ++j) {
+    const BPatch& C = a.P[a.ids[j]];
+    bool in = true;
+    for (int e = 0; e < a.dim; ++e) in = in && w[e] >= C.lo[e] && w[e] < C.lo[e] + C.n[e];
+    if (in) return j;
+  }
+  return -1;
+}
+
+// local index, in the old patch of entry i seen through its shift, of fine position h
+__host__ __device__ inline int old_loc(const BArgs& a, const BTask& T, int i, const int* h) {
+  const int lf = a.P[T.q].level;
+  const BPatch& O = a.PO[a.pairs[2 * i]];
+  int s[3], w[3];
+  shift_of(a.pairs[2 * i + 1], s);
+  for (int e = 0; e < 3; ++e) w[e] = e < a.dim ? h[e] - s[e] * Nl(a, lf, e) : 0;
+  const int x = w[0] - O.lo[0] + 4, y = w[1] - O.lo[1] + 4, z = a.dim == 3 ? w[2] - O.lo[2] + 4 : 0;
+  return x + O.ext[0] * (y + O.ext[1] * z);
+}
+
+// label of position t of transfer task T: a copy (id = old entry index) or a
+// prolongation (id = ns + 8 coarse candidate + the dimensions where the face
+// position wraps); -3 no source
+__host__ __device__ inline int transfer_label(const BArgs& a, const BTask& T, long long t) {
+  const BPatch& P = a.P[T.q];
+  const int lf = P.level, d = T.d, dim = a.dim;
+  const int ns = T.s1 - T.s0;
+  int x[3], g[3], pq[3];
+  decode(T, t, x);
+  for (int e = 0; e < 3; ++e) {
+    g[e] = e < dim ? P.lo[e] + x[e] : 0;
+    pq[e] = e < dim ? g[e] >> 1 : 0;
+  }
+  if (d < 0) {
+    if (old_covers(a, T, pq)) {
+      const int i = old_owner(a, T, g);
+      return i < 0 ? -3 : i - T.s0;
+    }
+    const int jc = new_coarse(a, T, pq);
+    return jc < 0 ? -3 : ns + 8 * (jc - T.p0);
+  }
+  int m[3] = {g[0], g[1], g[2]}, pm[3];
+  m[d] -= 1;
+  for (int e = 0; e < 3; ++e) pm[e] = e < dim ? m[e] >> 1 : 0;
+  const bool interior = pq[d] == pm[d];
+  const bool copy = interior ? old_covers(a, T, pq) : (old_covers(a, T, pq) || old_covers(a, T, pm));
+  if (copy) {  // the owners of the cells on the face's two sides
+    int best = -1, bi = 0, bl = 0;
+    const int i1 = old_owner(a, T, g);
+    if (i1 >= 0) { best = a.pairs[2 * i1]; bi = i1; bl = old_loc(a, T, i1, g); }
+    const int i0 = old_owner(a, T, m);
+    if (i0 >= 0) {
+      const int L = old_loc(a, T, i0, g);
+      if (best < 0 || a.pairs[2 * i0] < best || (a.pairs[2 * i0] == best && L < bl)) { best = a.pairs[2 * i0]; bi = i0; bl = L; }
+    }
+    return best < 0 ? -3 : bi - T.s0;
+  }
+  int c[3] = {pq[0], pq[1], pq[2]};
+  if (!a.per[d] && g[d] == Nl(a, lf, d)) c[d] -= 1;
+  const int jc = new_coarse(a, T, c);
+  if (jc < 0) return -3;
+  int bits = 0;
+  for (int e = 0; e < dim; ++e)
+    if (a.per[e] && g[e] == Nl(a, lf, e)) bits |= 1 << e;
+  return ns + 8 * (jc - T.p0) + bits;
+}
+
+__host__ __device__ inline void transfer_row(const BArgs& a, const BTask& T, int id, int* row) {
+  const BPatch& P = a.P[T.q];
+  const int lf = P.level, dim = a.dim, ns = T.s1 - T.s0;
+  int kind, src, aux[3] = {0, 0, 0};
+  if (id < ns) {
+    kind = 0;
+    const int i = T.s0 + id;
+    src = a.pairs[2 * i];
+    int s[3];
+    shift_of(a.pairs[2 * i + 1], s);
+    for (int e = 0; e < dim; ++e) aux[e] = P.lo[e] - a.PO[src].lo[e] - s[e] * Nl(a, lf, e);
+  } else {
+    kind = 1;
+    src = a.ids[T.p0 + (id - ns) / 8];
+    const int bits = (id - ns) % 8;
+    for (int e = 0; e < dim; ++e) aux[e] = (bits >> e) & 1 ? -Nl(a, lf, e) : 0;
+  }
+  row[0] = T.q;
+  row[1] = T.d;
+  row[2] = kind;
+  row[3] = src;
+  row[10] = aux[0];
+  row[11] = aux[1];
+  row[12] = aux[2];
+}
+
+// closure cell c of new patch task T: a coarse cell of the footprint not
+// covered by the old fine level with a face neighbour (inside the domain) that is
+__host__ __device__ inline bool closure_cell(const BArgs& a, const BTask& T, const int* c) {
+  const int lc = a.P[T.q].level - 1, dim = a.dim;
+  if (old_covers(a, T, c)) return false;
+  for (int e = 0; e < dim; ++e)
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int nb[3] = {c[0], c[1], c[2]};
+      nb[e] += sgn;
+      bool in = true;
+      for (int e2 = 0; e2 < dim; ++e2)
+        if (!a.per[e2] && (nb[e2] < 0 || nb[e2] >= Nl(a, lc, e2))) in = false;
+      if (in && old_covers(a, T, nb)) return true;
+    }
+  return false;
+}
+
+__host__ __device__ __forceinline__ int label_of(const BArgs& a, const BTask& T, long long t) {
+  return T.transfer ? transfer_label(a, T, t) : ghost_label(a, T, t);
+}
+
+// ---- the greedy merge (one warp)
+
+template <bool EMIT, class GT>
+__device__ void warp_merge(const BArgs& a, int ti, GT* G) {
+  const BTask& T = a.T[ti];
+  const int lane = threadIdx.x & 31;
+  const int e0 = T.ex[0], e1 = T.ex[1], e2 = T.ex[2];
+  const long long tot = (long long)e0 * e1 * e2;
+  auto at = [&](int x, int y, int z) { return ((long long)z * e1 + y) * e0 + x; };
+  const unsigned FULL = 0xffffffffu;
+  long long pos = 0, count = 0;
+  const long long base = EMIT ? a.first[ti] : 0;
+  int* out = T.d < 0 ? a.out_cells : a.out_faces;
+  for (;;) {
+    long long t0 = -1;
+    for (; pos < tot; pos += 32) {
+      const long long idx = pos + lane;
+      const unsigned m = __ballot_sync(FULL, idx < tot && G[idx] >= 0);
+      if (m) { t0 = pos + __ffs(m) - 1; break; }
+    }
+    if (t0 < 0) break;
+    const int k = G[t0];
+    const int a0 = (int)(t0 % e0), b0 = (int)((t0 / e0) % e1), c0 = (int)(t0 / ((long long)e0 * e1));
+    int nx = 1;
+    for (;;) {
+      const int x = a0 + nx + lane;
+      const unsigned m = __ballot_sync(FULL, x < e0 && G[t0 + nx + lane] == k);
+      if (m == FULL) { nx += 32; continue; }
+      nx += __ffs(~m) - 1;
+      break;
+    }
+    auto row_ok = [&](int y, int z) {
+      for (int i0 = 0; i0 < nx; i0 += 32) {
+        const int i = i0 + lane;
+        if (!__all_sync(FULL, i >= nx || G[at(a0 + i, y, z)] == k)) return false;
+      }
+      return true;
+    };
+    int ny = 1, nz = 1;
+    while (b0 + ny < e1 && row_ok(b0 + ny, c0)) ++ny;
+    auto slab_ok = [&](int z) {
+      for (int j = 0; j < ny; ++j)
+        if (!row_ok(b0 + j, z)) return false;
+      return true;
+    };
+    while (c0 + nz < e2 && slab_ok(c0 + nz)) ++nz;
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int i = lane; i < nx; i += 32) G[at(a0 + i, b0 + y, c0 + z)] = -2;
+    __syncwarp();
+    if (EMIT && lane == 0) {
+      int* r = out + 13 * (base + count);
+      const int o = T.transfer ? 4 : 0;  // transfer boxes: lo in the patch's ghosted frame
+      if (T.transfer) transfer_row(a, T, k, r);
+      else ghost_row(a, T, k, r);
+      r[4] = a0 + o;
+      r[5] = b0 + o;
+      r[6] = a.dim == 3 ? c0 + o : c0;
+      r[7] = nx;
+      r[8] = ny;
+      r[9] = nz;
+    }
+    ++count;
+    pos = t0 + 1;
+  }
+  if (!EMIT && lane == 0) a.cnt[ti] = count;
+}
+
+// one task per CTA, its label grid (16-bit ids) in shared memory
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_box_tasks_smem(BArgs a, const int* list, int n) {
+  extern __shared__ short sg[];
+  if ((int)blockIdx.x >= n) return;
+  const int ti = list[blockIdx.x];
+  const BTask& T = a.T[ti];
+  const long long tot = (long long)T.ex[0] * T.ex[1] * T.ex[2];
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int id = label_of(a, T, t);
+    if (id == -3) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
+    sg[t] = (short)(id < 0 ? -1 : id);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) warp_merge<EMIT>(a, ti, sg);
+}
+
+// large tasks: labels into their global grids, then one warp per task merges
+__global__ void k_box_label_global(BArgs a, const int* list, int n) {
+  for (int k = blockIdx.y; k < n; k += gridDim.y) {
+    const int ti = list[k];
+    const BTask& T = a.T[ti];
+    const long long tot = (long long)T.ex[0] * T.ex[1] * T.ex[2];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+      const int id = label_of(a, T, t);
+      if (id == -3) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
+      a.G[T.go + t] = id < 0 ? -1 : id;
+    }
+  }
+}
+
+template <bool EMIT>
+__global__ void k_box_merge_global(BArgs a, const int* list, int n) {
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= n) return;  // the whole warp
+  const int ti = list[k];
+  warp_merge<EMIT>(a, ti, a.G + a.T[ti].go);
+}
+
+// closure mask of the footprints of the listed transfer cell tasks
+__global__ void k_closure_mask(BArgs a, const int* list, const long long* moff, int n, unsigned char* mask) {
+  const int k = blockIdx.y;
+  if (k >= n) return;
+  const BTask& T = a.T[list[k]];
+  const BPatch& P = a.P[T.q];
+  int nc[3];
+  for (int e = 0; e < 3; ++e) nc[e] = e < a.dim ? P.n[e] / 2 : 1;
+  const long long tot = (long long)nc[0] * nc[1] * nc[2];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int c[3] = {(int)(t % nc[0]), (int)((t / nc[0]) % nc[1]), (int)(t / ((long long)nc[0] * nc[1]))};
+    for (int e = 0; e < a.dim; ++e) c[e] += P.lo[e] / 2;
+    mask[moff[k] + t] = closure_cell(a, T, c) ? 1 : 0;
+  }
+}
+
+// ---- host tables
+
+inline void patch_table(const amrmhd::Hierarchy& H, std::vector<BPatch>& out) {
+  out.assign(H.p.size(), BPatch());
+  for (size_t q = 0; q < H.p.size(); ++q) {
+    for (int d = 0; d < 3; ++d) { out[q].lo[d] = H.p[q].lo[d]; out[q].n[d] = H.p[q].n[d]; out[q].ext[d] = H.p[q].ext[d]; }
+    out[q].level = H.p[q].level;
+  }
+}
+
+inline int shift_code(const int* s) { return (s[0] + 1) + 3 * (s[1] + 1) + 9 * (s[2] + 1); }
+
+// the coarse candidates of patch q: its parents and their neighbours, ascending
+inline std::vector<int> coarse_candidates(const amrmhd::Hierarchy& H, int q) {
+  std::vector<int> cc;
+  for (int par : H.parents[q]) {
+    cc.push_back(par);
+    for (const amrmhd::Nbr& x : H.nbr[par]) cc.push_back(x.q);
+  }
+  std::sort(cc.begin(), cc.end());
+  cc.erase(std::unique(cc.begin(), cc.end()), cc.end());
+  return cc;
+}
+
+// Ghost tasks of the patches of levels >= H.ghost_from: per patch its
+// same-level neighbour entries (as listed) and the (coarse candidate, image)
+// entries whose fine footprint meets the patch's ghosted box, in the host
+// builder's order (candidate ascending, then z, y, x image).
+inline void ghost_tasks(const amrmhd::Hierarchy& H, std::vector<BTask>& T, std::vector<int>& pairs) {
+  const int dim = H.dim;
+  for (int q = 0; q < (int)H.p.size(); ++q) {
+    const amrmhd::HPatch& hp = H.p[q];
+    if (hp.level < H.ghost_from) continue;
+    const int l = hp.level;
+    const int s0 = (int)pairs.size() / 2;
+    for (const amrmhd::Nbr& x : H.nbr[q]) {
+      pairs.push_back(x.q);
+      pairs.push_back(shift_code(x.s));
+    }
+    const int s1 = (int)pairs.size() / 2;
+    if (l > 0)
+      for (int cq : coarse_candidates(H, q)) {
+        const amrmhd::HPatch& C = H.p[cq];
+        int wr[3];
+        for (int e = 0; e < 3; ++e) wr[e] = (e < dim && H.per[e]) ? 1 : 0;
+        for (int wz = -wr[2]; wz <= wr[2]; ++wz)
+          for (int wy = -wr[1]; wy <= wr[1]; ++wy)
+            for (int wx = -wr[0]; wx <= wr[0]; ++wx) {
+              const int w[3] = {wx, wy, wz};
+              bool meet = true;
+              for (int e = 0; e < dim; ++e) {
+                const int aux = w[e] * H.N(l, e);
+                // footprint [2 lo - aux, 2 hi + 1 - aux) against the ghosted box [lo - 4, hi + 5)
+                if (2 * C.hi[e] + 1 - aux <= hp.lo[e] - 4 || 2 * C.lo[e] - aux >= hp.hi[e] + 5) meet = false;
+              }
+              if (meet) {
+                pairs.push_back(cq);
+                pairs.push_back(shift_code(w));
+              }
+            }
+      }
+    const int p1 = (int)pairs.size() / 2;
+    for (int d = -1; d < dim; ++d) {
+      BTask t;
+      t.q = q;
+      t.d = d;
+      t.s0 = s0;
+      t.s1 = s1;
+      t.p0 = s1;
+      t.p1 = p1;
+      t.touches = 0;
+      t.transfer = 0;
+      t.go = -1;
+      for (int e = 0; e < 3; ++e) {
+        t.ex[e] = e < dim ? hp.n[e] + 8 + (e == d ? 1 : 0) : 1;
+        t.g0[e] = e < dim ? hp.lo[e] - 4 : 0;
+        if (e < dim && !H.per[e] && (t.g0[e] < 0 || t.g0[e] + t.ex[e] - 1 > (e == d ? H.N(l, e) : H.N(l, e) - 1)))
+          t.touches = 1;
+      }
+      T.push_back(t);
+    }
+  }
+}
+
+// Transfer tasks of level lf of Hn: per new patch the old level-lf (patch,
+// shift) entries meeting the patch grown by 2 fine cells (old id ascending,
+// then z, y, x shift) and its coarse candidates.
+inline void transfer_tasks(const amrmhd::Hierarchy& Hn, const amrmhd::Hierarchy& Ho, int lf, std::vector<BTask>& T,
+                           std::vector<int>& pairs, std::vector<int>& ids) {
+  const int dim = Hn.dim;
+  const int B = 16;  // bins of 16 fine cells over the old level
+  int N[3], nb[3];
+  for (int e = 0; e < 3; ++e) {
+    N[e] = Hn.N(lf, e);
+    nb[e] = e < dim ? (N[e] + B - 1) / B : 1;
+  }
+  std::vector<std::vector<int>> bins((size_t)nb[0] * nb[1] * nb[2]);
+  if (Ho.nlev > lf)
+    for (int oq : Ho.level_patches[lf]) {
+      int b0[3], b1[3];
+      for (int e = 0; e < 3; ++e) {
+        b0[e] = e < dim ? Ho.p[oq].lo[e] / B : 0;
+        b1[e] = e < dim ? (Ho.p[oq].hi[e] - 1) / B : 0;
+      }
+      for (int z = b0[2]; z <= b1[2]; ++z)
+        for (int y = b0[1]; y <= b1[1]; ++y)
+          for (int x = b0[0]; x <= b1[0]; ++x) bins[((size_t)z * nb[1] + y) * nb[0] + x].push_back(oq);
+    }
+  int wr[3];
+  for (int e = 0; e < 3; ++e) wr[e] = (e < dim && Hn.per[e]) ? 1 : 0;
+  for (int q : Hn.level_patches[lf]) {
+    const amrmhd::HPatch& hp = Hn.p[q];
+    std::vector<int> oc;
+    for (int sz = -wr[2]; sz <= wr[2]; ++sz)
+      for (int sy = -wr[1]; sy <= wr[1]; ++sy)
+        for (int sx = -wr[0]; sx <= wr[0]; ++sx) {
+          const int sh[3] = {sx, sy, sz};
+          int a0[3] = {0, 0, 0}, a1[3] = {0, 0, 0};
+          bool empty = false;
+          for (int e = 0; e < dim; ++e) {
+            const int lo = std::max(hp.lo[e] - 2 - sh[e] * N[e], 0), hi = std::min(hp.hi[e] + 2 - sh[e] * N[e], N[e]);
+            if (hi <= lo) { empty = true; break; }
+            a0[e] = lo / B;
+            a1[e] = (hi - 1) / B;
+          }
+          if (empty) continue;
+          for (int z = a0[2]; z <= a1[2]; ++z)
+            for (int y = a0[1]; y <= a1[1]; ++y)
+              for (int x = a0[0]; x <= a1[0]; ++x)
+                for (int oq : bins[((size_t)z * nb[1] + y) * nb[0] + x]) oc.push_back(oq);
+        }
+    std::sort(oc.begin(), oc.end());
+    oc.erase(std::unique(oc.begin(), oc.end()), oc.end());
+    const int s0 = (int)pairs.size() / 2;
+    for (int oq : oc) {
+      const amrmhd::HPatch& O = Ho.p[oq];
+      for (int sz = -wr[2]; sz <= wr[2]; ++sz)
+        for (int sy = -wr[1]; sy <= wr[1]; ++sy)
+          for (int sx = -wr[0]; sx <= wr[0]; ++sx) {
+            const int sh[3] = {sx, sy, sz};
+            bool meet = true;
+            for (int e = 0; e < dim; ++e)
+              if (O.hi[e] + sh[e] * N[e] <= hp.lo[e] - 2 || O.lo[e] + sh[e] * N[e] >= hp.hi[e] + 2) meet = false;
+            if (meet) {
+              pairs.push_back(oq);
+              pairs.push_back(shift_code(sh));
+            }
+          }
+    }
+    const int s1 = (int)pairs.size() / 2;
+    const std::vector<int> cc = coarse_candidates(Hn, q);
+    const int p0 = (int)ids.size();
+    ids.insert(ids.end(), cc.begin(), cc.end());
+    const int p1 = (int)ids.size();
+    for (int d = -1; d < dim; ++d) {
+      BTask t;
+      t.q = q;
+      t.d = d;
+      t.s0 = s0;
+      t.s1 = s1;
+      t.p0 = p0;
+      t.p1 = p1;
+      t.touches = 0;
+      t.transfer = 1;
+      t.go = -1;
+      for (int e = 0; e < 3; ++e) {
+        t.ex[e] = e < dim ? hp.n[e] + (e == d ? 1 : 0) : 1;
+        t.g0[e] = e < dim ? hp.lo[e] : 0;
+      }
+      T.push_back(t);
+    }
+  }
+}
+
+// the largest label id a task can produce
+inline long long max_id(const BTask& t) {
+  const long long ns = t.s1 - t.s0, np = t.p1 - t.p0;
+  return t.transfer ? ns + 8 * np : ns + np + 27;
+}
+
+}  // namespace amrbx
+
+namespace amrapi {
+
+namespace {
+
+constexpr size_t kBoxSmem = 200 * 1024;  // label grid bytes of a task labelled in shared memory
+
+// Runs box tasks (ghost or transfer) on the device and returns the boxes of the
+// cell tasks and of the face tasks in task order; with closure (transfer), the
+// closure mask of every cell task's coarse footprint. *bad gets the first task
+// and position without a source (or -1).
+amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hierarchy& H,
+                            const std::vector<amrbx::BPatch>& P, const std::vector<amrbx::BPatch>* PO, int have_old,
+                            std::vector<amrbx::BTask>& T, const std::vector<int>& pairs, const std::vector<int>& ids,
+                            std::vector<int32_t>& cells, std::vector<int32_t>& faces, std::vector<uint8_t>* closure,
+                            std::vector<long long>* closure_off, long long* bad, const char* what) {
+  using namespace amrbx;
+  cells.clear();
+  faces.clear();
+  *bad = -1;
+  const int nt = (int)T.size();
+  if (!nt) return AMRMHD_OK;
+  // shared-memory tasks and global-memory tasks
+  std::vector<int> small, large;
+  long long gtot = 0, smax = 0;
+  for (int i = 0; i < nt; ++i) {
+    const long long tot = (long long)T[i].ex[0] * T[i].ex[1] * T[i].ex[2];
+    if (2 * tot <= (long long)kBoxSmem && max_id(T[i]) < 32767) {
+      small.push_back(i);
+      smax = std::max(smax, tot);
+    } else {
+      large.push_back(i);
+      T[i].go = gtot;
+      gtot += tot;
+    }
+  }
+  std::vector<int> ctask;
+  std::vector<long long> moff;
+  long long mtot = 0;
+  if (closure)
+    for (int i = 0; i < nt; ++i)
+      if (T[i].d < 0) {
+        ctask.push_back(i);
+        moff.push_back(mtot);
+        long long v = 1;
+        for (int e = 0; e < H.dim; ++e) v *= P[T[i].q].n[e] / 2;
+        mtot += v;
+      }
+  std::vector<char> img;
+  auto put = [&](const void* src, size_t bytes) {
+    const size_t o = (img.size() + 255) / 256 * 256;
+    img.resize(o + bytes);
+    if (bytes) std::memcpy(img.data() + o, src, bytes);
+    return o;
+  };
+  const size_t oP = put(P.data(), sizeof(BPatch) * P.size()),
+               oPO = put(PO ? PO->data() : nullptr, sizeof(BPatch) * (PO ? PO->size() : 0)),
+               oT = put(T.data(), sizeof(BTask) * nt), oPr = put(pairs.data(), sizeof(int) * pairs.size()),
+               oI = put(ids.data(), sizeof(int) * ids.size()), oS = put(small.data(), sizeof(int) * small.size()),
+               oL = put(large.data(), sizeof(int) * large.size()), oCT = put(ctask.data(), sizeof(int) * ctask.size()),
+               oMO = put(moff.data(), sizeof(long long) * moff.size());
+  const size_t in_bytes = img.size();
+  size_t o = (in_bytes + 255) / 256 * 256;
+  auto reserve = [&](size_t bytes) { const size_t r = o; o = (o + bytes + 255) / 256 * 256; return r; };
+  const size_t oG = reserve(sizeof(int) * gtot), oCnt = reserve(sizeof(long long) * nt),
+               oFirst = reserve(sizeof(long long) * nt), oErr = reserve(sizeof(unsigned long long)),
+               oMask = reserve((size_t)mtot);
+  char* dev = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dev, o);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+  int* dout = nullptr;
+  auto done = [&](amrmhd_status s, const std::string& m) {
+    cudaFree(dev);
+    if (dout) cudaFree(dout);
+    return s == AMRMHD_OK ? s : fail(ctx, s, m);
+  };
+  e = cudaMemcpyAsync(dev, img.data(), in_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev + oErr, 0xff, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  BArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.dim = H.dim;
+  for (int d = 0; d < 3; ++d) {
+    a.base[d] = H.base[d];
+    a.per[d] = H.per[d] ? 1 : 0;
+    a.bc[d][0] = H.bc[d][0];
+    a.bc[d][1] = H.bc[d][1];
+  }
+  a.P = (const BPatch*)(dev + oP);
+  a.PO = (const BPatch*)(dev + oPO);
+  a.have_old = have_old;
+  a.T = (const BTask*)(dev + oT);
+  a.pairs = (const int*)(dev + oPr);
+  a.ids = (const int*)(dev + oI);
+  a.G = (int*)(dev + oG);
+  a.cnt = (long long*)(dev + oCnt);
+  a.first = (const long long*)(dev + oFirst);
+  a.err = (unsigned long long*)(dev + oErr);
+  const int* dsmall = (const int*)(dev + oS);
+  const int* dlarge = (const int*)(dev + oL);
+  const size_t smem = (size_t)std::max<long long>(smax, 1) * sizeof(short);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_box_tasks_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
+    cudaFuncSetAttribute(k_box_tasks_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
+    attr = true;
+  }
+  long long lmax = 0;
+  for (int i : large) lmax = std::max(lmax, (long long)T[i].ex[0] * T[i].ex[1] * T[i].ex[2]);
+  const dim3 lg((unsigned)std::min<long long>((lmax + 255) / 256, 64), (unsigned)std::min<size_t>(large.size(), 65535));
+  const int WPB = 4;
+  auto launch = [&](bool emit) {
+    if (!small.empty()) {
+      if (emit) k_box_tasks_smem<true><<<(unsigned)small.size(), 256, smem, st>>>(a, dsmall, (int)small.size());
+      else k_box_tasks_smem<false><<<(unsigned)small.size(), 256, smem, st>>>(a, dsmall, (int)small.size());
+    }
+    if (!large.empty()) {
+      k_box_label_global<<<lg, 256, 0, st>>>(a, dlarge, (int)large.size());
+      const unsigned mb = (unsigned)((large.size() + WPB - 1) / WPB);
+      if (emit) k_box_merge_global<true><<<mb, 32 * WPB, 0, st>>>(a, dlarge, (int)large.size());
+      else k_box_merge_global<false><<<mb, 32 * WPB, 0, st>>>(a, dlarge, (int)large.size());
+    }
+    ctx->launches += (small.empty() ? 0 : 1) + (large.empty() ? 0 : 2);
+  };
+  launch(false);
+  if (closure && mtot) {
+    k_closure_mask<<<dim3(8, (unsigned)ctask.size()), 256, 0, st>>>(a, (const int*)(dev + oCT),
+                                                                   (const long long*)(dev + oMO), (int)ctask.size(),
+                                                                   (unsigned char*)(dev + oMask));
+    ctx->launches += 1;
+  }
+  std::vector<long long> cnt(nt);
+  unsigned long long err = 0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), a.cnt, sizeof(long long) * nt, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, a.err, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && closure) {
+    closure->resize((size_t)mtot);
+    if (mtot) e = cudaMemcpyAsync(closure->data(), dev + oMask, (size_t)mtot, cudaMemcpyDeviceToHost, st);
+    *closure_off = moff;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + " (count): " + cudaGetErrorString(e));
+  if (err != ~0ull) {
+    *bad = (long long)err;
+    return done(AMRMHD_OK, "");
+  }
+  std::vector<long long> first(nt);
+  long long nc = 0, nf = 0;
+  for (int i = 0; i < nt; ++i) {
+    long long& acc = T[i].d < 0 ? nc : nf;
+    first[i] = acc;
+    acc += cnt[i];
+  }
+  e = cudaMalloc((void**)&dout, sizeof(int) * 13 * std::max<long long>(nc + nf, 1));
+  if (e != cudaSuccess) { dout = nullptr; return done(AMRMHD_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e)); }
+  a.out_cells = dout;
+  a.out_faces = dout + 13 * nc;
+  e = cudaMemcpyAsync(dev + oFirst, first.data(), sizeof(long long) * nt, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  // the merge takes the grids apart: label again, then merge and write the boxes
+  launch(true);
+  cells.resize(13 * (size_t)nc);
+  faces.resize(13 * (size_t)nf);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && nc) e = cudaMemcpyAsync(cells.data(), a.out_cells, sizeof(int) * 13 * nc, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && nf) e = cudaMemcpyAsync(faces.data(), a.out_faces, sizeof(int) * 13 * nf, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + " (emit): " + cudaGetErrorString(e));
+  return done(AMRMHD_OK, "");
+}
+
+}  // namespace
+
+// The ghost-fill boxes of the patches of levels >= H.ghost_from, built on the
+// device into H.ghost_box_cells and H.ghost_box_faces (host copies: the bind
+// step turns them into fill records).
+amrmhd_status device_ghost_boxes(amrmhd_ctx* ctx) {
+  using namespace amrbx;
+  amrmhd::Hierarchy& H = ctx->H;
+  H.ghost_rows_ready = false;
+  std::vector<BPatch> P;
+  std::vector<BTask> T;
+  std::vector<int> pairs, ids;
+  long long bad = -1;
+  patch_table(H, P);
+  ghost_tasks(H, T, pairs);
+  amrmhd_status s = run_box_tasks(ctx, ctx->stream, H, P, nullptr, 0, T, pairs, ids, H.ghost_box_cells,
+                                  H.ghost_box_faces, nullptr, nullptr, &bad, "ghost maps");
+  if (s != AMRMHD_OK || bad < 0) return s;
+  // a ghost position without a source: the host builder's messages
+  const BTask& t = T[bad >> 32];
+  int x[3];
+  decode(t, bad & 0xffffffffll, x);
+  const int g[3] = {t.g0[0] + x[0], t.g0[1] + x[1], t.g0[2] + x[2]};
+  H.ghost_box_cells.clear();
+  H.ghost_box_faces.clear();
+  if (H.p[t.q].level == 0)
+    return fail(ctx, AMRMHD_EINVAL, t.d < 0 ? "level-0 ghost cell without a source" : "level-0 ghost face without a source");
+  return fail(ctx, AMRMHD_ENEST,
+              t.d < 0 ? "no parent-level source for the ghost cell (" + std::to_string(g[0]) + ", " + std::to_string(g[1]) +
+                            ", " + std::to_string(g[2]) + ") of patch " + std::to_string(t.q)
+                      : "no parent-level source for the ghost face (" + std::to_string(t.d) + "; " +
+                            std::to_string(g[0]) + ", " + std::to_string(g[1]) + ", " + std::to_string(g[2]) +
+                            ") of patch " + std::to_string(t.q));
+}
+
+// The transfer maps of level lf of the new hierarchy Hn from the old hierarchy
+// Ho, built on the device: the rows of amrmhd::transfer_maps (the cell and face
+// boxes of every new patch, and the closure rows).
+amrmhd_status device_transfer_maps(amrmhd_ctx* ctx, const amrmhd::Hierarchy& Hn, const amrmhd::Hierarchy& Ho, int lf,
+                                   cudaStream_t st, std::vector<int32_t>& cells, std::vector<int32_t>& faces,
+                                   std::vector<int32_t>& closure) {
+  using namespace amrbx;
+  std::vector<BPatch> P, PO;
+  std::vector<BTask> T;
+  std::vector<int> pairs, ids;
+  long long bad = -1;
+  patch_table(Hn, P);
+  patch_table(Ho, PO);
+  transfer_tasks(Hn, Ho, lf, T, pairs, ids);
+  std::vector<uint8_t> mask;
+  std::vector<long long> moff;
+  amrmhd_status s = run_box_tasks(ctx, st, Hn, P, &PO, Ho.nlev > lf, T, pairs, ids, cells, faces, &mask, &moff, &bad,
+                                  "transfer maps");
+  if (s != AMRMHD_OK) return s;
+  if (bad >= 0) return fail(ctx, AMRMHD_EINVAL, "regrid: transfer map without a source");
+  closure.clear();
+  int k = 0;
+  for (const BTask& t : T) {
+    if (t.d >= 0) continue;
+    const amrmhd::HPatch& hp = Hn.p[t.q];
+    int nc[3];
+    for (int e = 0; e < 3; ++e) nc[e] = e < Hn.dim ? hp.n[e] / 2 : 1;
+    const uint8_t* m = mask.data() + moff[k++];
+    for (int z = 0; z < nc[2]; ++z)
+      for (int y = 0; y < nc[1]; ++y)
+        for (int x = 0; x < nc[0]; ++x, ++m)
+          if (*m) {
+            closure.push_back(t.q);
+            closure.push_back(Hn.loc(t.q, hp.lo[0] + 2 * x, hp.lo[1] + 2 * y, Hn.dim == 3 ? hp.lo[2] + 2 * z : 0));
+          }
+  }
+  return AMRMHD_OK;
+}
+
+}  // namespace amrapi

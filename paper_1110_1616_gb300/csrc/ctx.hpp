@@ -103,6 +103,19 @@ struct amrmhd_ctx {
     return f;
   }
   amrapi::QueuePlan qplan;
+  // where the register, reflux and restriction maps are built: -1 on the device
+  // when one is present, else on the host; 0 host; 1 device. Device-built lists
+  // live in d_maps (list i at element dmap_off[i], dmap_n[i] rows); their host
+  // copies in H are made on demand (dmaps_host) for the map export
+  int64_t opt_device_maps = -1;
+  bool dmaps = false, dmaps_host = false;
+  int* d_maps = nullptr;
+  int64_t dmap_off[6] = {0, 0, 0, 0, 0, 0}, dmap_n[6] = {0, 0, 0, 0, 0, 0};
+  // the regrid's clustering: on the device (1, default) or the host (0), and
+  // the device scratch of the device clustering (grown as needed)
+  int64_t opt_device_cluster = 1;
+  unsigned char* d_cluster = nullptr;
+  size_t cluster_cap = 0;
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;
@@ -144,7 +157,7 @@ struct amrmhd_ctx {
   long long launches = 0;
   // host wall time of the last regrid, microseconds: flagging, clustering,
   // hierarchy and map building with the stage arenas, data transfer
-  long long regrid_us[5] = {0, 0, 0, 0, 0};
+  long long regrid_us[6] = {0, 0, 0, 0, 0, 0};  // the five above, then the transfer maps
   // inter-level concurrency: side stream and fork/join events per level
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_fork, ev_join;
@@ -176,5 +189,13 @@ void op_level_step(amrmhd_ctx* ctx, int l, int s, int* nl, bool filled = false);
 amrmhd_status check_bound(amrmhd_ctx* ctx);
 amrmhd_status upload_fill_rows(amrmhd_ctx* ctx);
 void adj_free(amrmhd_ctx* ctx);  // adjoint.cu
+amrmhd_status device_register_maps(amrmhd_ctx* ctx);    // maps_dev.cu
+amrmhd_status download_register_maps(amrmhd_ctx* ctx);  // maps_dev.cu
+amrmhd_status device_ghost_boxes(amrmhd_ctx* ctx);      // maps_dev.cu
+amrmhd_status device_transfer_maps(amrmhd_ctx* ctx, const amrmhd::Hierarchy& Hn, const amrmhd::Hierarchy& Ho, int lf,
+                                   cudaStream_t st, std::vector<int32_t>& cells, std::vector<int32_t>& faces,
+                                   std::vector<int32_t>& closure);  // maps_dev.cu
+amrmhd_status cluster_level_device(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta,
+                                   std::vector<std::array<int, 7>>& boxes);  // regrid_dev.cu
 
 }  // namespace amrapi

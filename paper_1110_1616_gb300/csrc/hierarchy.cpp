@@ -480,7 +480,7 @@ int Hierarchy::build(const int32_t* rows7, int n) {
   };
 #pragma omp parallel for schedule(dynamic, 1)
   for (int q = 0; q < np; ++q)
-    if (p[q].level >= ghost_from) gst[q] = ghost_patch(q, gbc[q], gbf[q], gerr[q]);
+    if (p[q].level >= ghost_from && !ghost_elsewhere) gst[q] = ghost_patch(q, gbc[q], gbf[q], gerr[q]);
   for (int q = 0; q < np; ++q)
     if (gst[q]) { err = gerr[q]; return gst[q]; }
   {

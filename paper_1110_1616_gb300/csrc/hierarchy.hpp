@@ -42,6 +42,9 @@ struct Hierarchy {
   // with with_registers; validation and neighbour lists are always complete
   int ghost_from = 0;
   bool with_registers = true;
+  // ghost boxes made elsewhere (on the device, maps_dev.cu): build() leaves
+  // ghost_box_cells and ghost_box_faces empty
+  bool ghost_elsewhere = false;
   std::vector<HPatch> p;
   std::vector<std::vector<int>> level_patches;  // ids per level, ascending
   std::vector<std::vector<Nbr>> nbr;            // per patch, sorted by (q, shift)

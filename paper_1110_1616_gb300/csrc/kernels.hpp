@@ -148,6 +148,11 @@ enum Variant { V_FP64 = 0, V_FP64_STRICT = 1, V_MIXED = 2 };
 constexpr int FILL_CHUNK = 64;
 constexpr int FILL_BOX_W = 16;
 
+// A dense byte box over level cells (the regrid's clustering frame).
+struct DenseBox {
+  int off[3], n[3];
+};
+
 struct Ops {
   void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
   void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
@@ -192,6 +197,10 @@ struct Ops {
   void (*closure)(const RowArgs&, cudaStream_t, int* launches);
   // the multi-level queue advance (3D fused path); variant: 2 (16x8) or 3 (8x8)
   void (*advance_queue)(const QueueArgs&, int variant, cudaStream_t, int* launches);
+  // regrid on the device: the level's cells (region) and its flagged cells
+  // (flags) as bytes of the dense box of n[3] cells from off[3]
+  void (*flag_dense)(const LevelArgs&, double theta, unsigned char* region, unsigned char* flags, DenseBox box,
+                     cudaStream_t);
 };
 
 const Ops* ops_fast(int variant, int dim);    // V_FP64 and V_MIXED

@@ -618,6 +618,31 @@ __global__ void __launch_bounds__(TPB) k_flag(LevelArgs a, double theta, int* ou
   out[3 * n + 2] = DIM == 3 ? P.lo[2] + k - 4 : 0;
 }
 
+// the same test per cell into dense bytes: region 1 on every cell of the
+// level, flags 1 where the gradient exceeds theta
+template <class T, int DIM>
+__global__ void __launch_bounds__(TPB) k_flag_dense(LevelArgs a, double theta, unsigned char* region,
+                                                    unsigned char* flags, DenseBox box) {
+  const DPatch P = a.P[a.ids[blockIdx.y]];
+  int i, j, k;
+  if (!region_cell<DIM>(P, 0, blockIdx.x * TPB + threadIdx.x, i, j, k)) return;
+  const int L = lidx(P, i, j, k);
+  const T* R = (const T*)a.cur + P.off;
+  const double r = (double)R[L];
+  double m = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int sd = stride_of<DIM>(P, d);
+    const double g = fabs((double)R[L + sd] - (double)R[L - sd]) / (2.0 * r);
+    if (g > m) m = g;
+  }
+  const int x = P.lo[0] + i - 4 - box.off[0], y = P.lo[1] + j - 4 - box.off[1],
+            z = DIM == 3 ? P.lo[2] + k - 4 - box.off[2] : 0;
+  const long long idx = ((long long)z * box.n[1] + y) * box.n[0] + x;
+  region[idx] = 1;
+  flags[idx] = m > theta ? 1 : 0;
+}
+
 // new fine cells, as transfer boxes (GHOST_BOX_W ints, chunks as for the ghost
 // boxes): kind 0 copies the old fine patch src of the old hierarchy (P2, obuf)
 // at local offset aux, kind 1 prolongs from the coarse patch src (cbuf) as for
@@ -1050,6 +1075,10 @@ template <class T, int DIM> struct Impl {
                    cudaStream_t s) {
     k_flag<T, DIM><<<grid_region(a, 0, 0), TPB, 0, s>>>(a, theta, out, count, cap);
   }
+  static void flag_dense(const LevelArgs& a, double theta, unsigned char* region, unsigned char* flags, DenseBox box,
+                         cudaStream_t s) {
+    k_flag_dense<T, DIM><<<grid_region(a, 0, 0), TPB, 0, s>>>(a, theta, region, flags, box);
+  }
   static void io(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,
                  const long long* poff, int field, int to_state, cudaStream_t s, int* nl) {
     long long n = 1;
@@ -1160,7 +1189,7 @@ template <class T, int DIM> struct Impl {
     static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong_cells,
                           prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
                           io_all, sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
-                          transfer_faces, closure, advance_queue};
+                          transfer_faces, closure, advance_queue, flag_dense};
     return &o;
   }
 };

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 namespace amrmhd {
 
@@ -23,33 +24,94 @@ struct Dense {  // a byte per cell of one level's domain
 
 }  // namespace
 
-std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags) {
-  const int dim = H.dim;
-  const std::vector<int>& lp = H.level_patches[l];
+ClusterFrame cluster_frame(const Hierarchy& H, int l) {
   // the dense arrays cover the level region's bounding box, aligned to blocks
   // and widened by the 3-cell nesting margin; a dimension whose widened box
   // reaches around the domain (periodic) or is bounded keeps the whole level
   // extent, so wrapped neighbours are found as before
-  int off[3] = {0, 0, 0}, N[3], full[3];
+  ClusterFrame f;
+  const std::vector<int>& lp = H.level_patches[l];
   for (int d = 0; d < 3; ++d) {
-    N[d] = H.N(l, d);
-    full[d] = 1;
-    if (d >= dim || lp.empty()) continue;
-    int lo = N[d], hi = 0;
+    f.off[d] = 0;
+    f.n[d] = H.N(l, d);
+    f.full[d] = 1;
+    if (d >= H.dim || lp.empty()) continue;
+    int lo = f.n[d], hi = 0;
     for (int q : lp) {
       lo = std::min(lo, H.p[q].lo[d]);
       hi = std::max(hi, H.p[q].hi[d]);
     }
     lo = (lo / kBlock) * kBlock - 2 * kBlock;
     hi = ((hi + kBlock - 1) / kBlock) * kBlock + 2 * kBlock;
-    if (lo >= 0 && hi <= N[d]) {
-      full[d] = 0;
-      off[d] = lo;
-      N[d] = hi - lo;
+    if (lo >= 0 && hi <= f.n[d]) {
+      f.full[d] = 0;
+      f.off[d] = lo;
+      f.n[d] = hi - lo;
     }
   }
+  for (int d = 0; d < 3; ++d) f.nb[d] = d < H.dim ? f.n[d] / kBlock : 1;
+  return f;
+}
+
+std::vector<std::array<int, 7>> merge_blocks(const Hierarchy& H, int l, const ClusterFrame& fr, uint8_t* ok) {
+  const int dim = H.dim;
+  const int* nb = fr.nb;
+  const int* off = fr.off;
+  auto bi = [&](int a, int b, int c) { return ((size_t)c * nb[1] + b) * nb[0] + a; };
+  const size_t nblk = (size_t)nb[0] * nb[1] * nb[2];
+  std::vector<std::array<int, 7>> out;
+  for (size_t w = 0; w < nblk; ++w) {
+    if (!ok[w]) {
+      // skip runs of unmarked blocks 8 at a time
+      while (w + 8 < nblk) {
+        uint64_t v;
+        std::memcpy(&v, ok + w + 1, 8);
+        if (v) break;
+        w += 8;
+      }
+      continue;
+    }
+    const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
+    int sx = 1, sy = 1, sz = 1;
+    while (sx < kMaxBlocks && a + sx < nb[0] && ok[bi(a + sx, b, c)]) ++sx;
+    auto row = [&](int bb, int cc) {
+      for (int t = 0; t < sx; ++t)
+        if (!ok[bi(a + t, bb, cc)]) return false;
+      return true;
+    };
+    while (sy < kMaxBlocks && b + sy < nb[1] && row(b + sy, c)) ++sy;
+    if (dim == 3) {
+      auto slab = [&](int cc) {
+        for (int u = 0; u < sy; ++u)
+          if (!row(b + u, cc)) return false;
+        return true;
+      };
+      while (sz < kMaxBlocks && c + sz < nb[2] && slab(c + sz)) ++sz;
+    }
+    for (int z = 0; z < sz; ++z)
+      for (int y = 0; y < sy; ++y)
+        for (int x = 0; x < sx; ++x) ok[bi(a + x, b + y, c + z)] = 0;
+    std::array<int, 7> p;
+    p[0] = l + 1;
+    p[1] = 2 * (kBlock * a + off[0]);
+    p[2] = 2 * (kBlock * b + off[1]);
+    p[3] = dim == 3 ? 2 * (kBlock * c + off[2]) : 0;
+    p[4] = 2 * (kBlock * (a + sx) + off[0]);
+    p[5] = 2 * (kBlock * (b + sy) + off[1]);
+    p[6] = dim == 3 ? 2 * (kBlock * (c + sz) + off[2]) : 1;
+    out.push_back(p);
+  }
+  return out;
+}
+
+std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags) {
+  const int dim = H.dim;
+  const std::vector<int>& lp = H.level_patches[l];
+  const ClusterFrame fr = cluster_frame(H, l);
+  const int* off = fr.off;
+  const int* full = fr.full;
   Dense region, buf;
-  for (int d = 0; d < 3; ++d) region.n[d] = buf.n[d] = N[d];
+  for (int d = 0; d < 3; ++d) region.n[d] = buf.n[d] = fr.n[d];
   const size_t ncell = (size_t)region.n[0] * region.n[1] * region.n[2];
   region.v.assign(ncell, 0);
   buf.v.assign(ncell, 0);
@@ -114,7 +176,6 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
   for (long long c = 0; c < (long long)ncell; ++c) buf.v[c] &= region.v[c];
   int nb[3];
   for (int d = 0; d < 3; ++d) nb[d] = d < dim ? region.n[d] / kBlock : 1;
-  auto bi = [&](int a, int b, int c) { return ((size_t)c * nb[1] + b) * nb[0] + a; };
   const size_t nblk = (size_t)nb[0] * nb[1] * nb[2];
   std::vector<uint8_t> ok(nblk, 0);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -139,40 +200,7 @@ std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const st
         }
     if (allowed) ok[w] = 1;
   }
-  std::vector<std::array<int, 7>> out;
-  for (size_t w = 0; w < nblk; ++w) {
-    if (!ok[w]) continue;
-    const int a = (int)(w % nb[0]), b = (int)((w / nb[0]) % nb[1]), c = (int)(w / ((size_t)nb[0] * nb[1]));
-    int sx = 1, sy = 1, sz = 1;
-    while (sx < kMaxBlocks && a + sx < nb[0] && ok[bi(a + sx, b, c)]) ++sx;
-    auto row = [&](int bb, int cc) {
-      for (int t = 0; t < sx; ++t)
-        if (!ok[bi(a + t, bb, cc)]) return false;
-      return true;
-    };
-    while (sy < kMaxBlocks && b + sy < nb[1] && row(b + sy, c)) ++sy;
-    if (dim == 3) {
-      auto slab = [&](int cc) {
-        for (int u = 0; u < sy; ++u)
-          if (!row(b + u, cc)) return false;
-        return true;
-      };
-      while (sz < kMaxBlocks && c + sz < nb[2] && slab(c + sz)) ++sz;
-    }
-    for (int z = 0; z < sz; ++z)
-      for (int y = 0; y < sy; ++y)
-        for (int x = 0; x < sx; ++x) ok[bi(a + x, b + y, c + z)] = 0;
-    std::array<int, 7> p;
-    p[0] = l + 1;
-    p[1] = 2 * (kBlock * a + off[0]);
-    p[2] = 2 * (kBlock * b + off[1]);
-    p[3] = dim == 3 ? 2 * (kBlock * c + off[2]) : 0;
-    p[4] = 2 * (kBlock * (a + sx) + off[0]);
-    p[5] = 2 * (kBlock * (b + sy) + off[1]);
-    p[6] = dim == 3 ? 2 * (kBlock * (c + sz) + off[2]) : 1;
-    out.push_back(p);
-  }
-  return out;
+  return merge_blocks(H, l, fr, ok.data());
 }
 
 int transfer_maps(const Hierarchy& Hn, const Hierarchy& Ho, int lf, TransferMaps& out) {

@@ -16,6 +16,19 @@ namespace amrmhd {
 // blocks per side) and refine by 2.
 std::vector<std::array<int, 7>> regrid_boxes(const Hierarchy& H, int l, const std::vector<int32_t>& flags);
 
+// The clustering's frame on level l: the dense arrays cover n[3] cells from
+// off[3] (the level region's bounding box aligned to the 4-cell blocks and
+// widened by 2 blocks, or the whole extent where that does not fit, full[d]);
+// nb[3] blocks per dimension.
+struct ClusterFrame {
+  int off[3], n[3], full[3], nb[3];
+};
+ClusterFrame cluster_frame(const Hierarchy& H, int l);
+
+// The greedy z,y,x merge of the marked blocks (ok, nb[0] x nb[1] x nb[2]
+// bytes; cleared as blocks are taken) into level-(l+1) boxes.
+std::vector<std::array<int, 7>> merge_blocks(const Hierarchy& H, int l, const ClusterFrame& fr, uint8_t* ok);
+
 struct TransferMaps {
   // boxes of the new patches' own cells (d = -1) and d-faces, GHOST_BOX_W ints
   // (dst, d, kind, src, lo[3], n[3], aux[3]), lo in dst's local coordinates:

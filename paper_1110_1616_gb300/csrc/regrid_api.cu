@@ -74,6 +74,8 @@ amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, i
   c->opt_graph = ctx->opt_graph;
   c->opt_tile = ctx->opt_tile;
   c->opt_concurrent = ctx->opt_concurrent;
+  c->opt_device_maps = ctx->opt_device_maps;
+  c->opt_device_cluster = ctx->opt_device_cluster;
   size_t bytes = 0;
   const long long t0 = now_us();
   st = amrmhd_set_hierarchy(c, ps.data(), (int32_t)ps.size(), &bytes);
@@ -115,47 +117,64 @@ amrmhd_status copy_levels(amrmhd_ctx* ctx, amrmhd_ctx* src, amrmhd_ctx* dst, int
   return AMRMHD_OK;
 }
 
-amrmhd_status upload_rows(amrmhd_ctx* ctx, const std::vector<int32_t>& v, int** p) {
-  *p = nullptr;
-  if (v.empty()) return AMRMHD_OK;
-  CUR(cudaMalloc((void**)p, sizeof(int32_t) * v.size()));
-  CUR(cudaMemcpy(*p, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice));
-  return AMRMHD_OK;
-}
-
 // transfer of level lf of stage S from the old context O
-amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
+amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf, long long* maps_us) {
   amrmhd::TransferMaps m;
-  const int rc = amrmhd::transfer_maps(S->H, O->H, lf, m);
-  if (rc) return fail(ctx, AMRMHD_EINVAL, "regrid: transfer map without a source");
   // cell and face boxes with their chunks (box, first position) of at most FILL_CHUNK positions
   std::vector<int32_t> cb, cc, fb, fc;
-  for (size_t r = 0; r < m.boxes.size(); r += amrmhd::GHOST_BOX_W) {
-    const int32_t* b = &m.boxes[r];
-    std::vector<int32_t>& boxes = b[1] < 0 ? cb : fb;
-    std::vector<int32_t>& ch = b[1] < 0 ? cc : fc;
-    const int bi = (int)(boxes.size() / amrmhd::GHOST_BOX_W);
-    boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
-    for (int c = 0; c < b[7] * b[8] * b[9]; c += amrk::FILL_CHUNK) {
-      ch.push_back(bi);
-      ch.push_back(c);
+  const long long t0 = now_us();
+  if (ctx->opt_device_maps != 0) {
+    amrmhd_status ds = device_transfer_maps(ctx, S->H, O->H, lf, S->stream, cb, fb, m.closure);
+    *maps_us += now_us() - t0;
+    if (ds != AMRMHD_OK) return ds;
+  } else {
+    const int rc = amrmhd::transfer_maps(S->H, O->H, lf, m);
+    *maps_us += now_us() - t0;
+    if (rc) return fail(ctx, AMRMHD_EINVAL, "regrid: transfer map without a source");
+    for (size_t r = 0; r < m.boxes.size(); r += amrmhd::GHOST_BOX_W) {
+      const int32_t* b = &m.boxes[r];
+      std::vector<int32_t>& boxes = b[1] < 0 ? cb : fb;
+      boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
     }
   }
-  int *dcb = nullptr, *dcc = nullptr, *dfb = nullptr, *dfc = nullptr, *dk = nullptr;
-  double* dK = nullptr;
-  amrmhd_status st = upload_rows(ctx, cb, &dcb);
-  if (!st) st = upload_rows(ctx, cc, &dcc);
-  if (!st) st = upload_rows(ctx, fb, &dfb);
-  if (!st) st = upload_rows(ctx, fc, &dfc);
-  if (!st) st = upload_rows(ctx, m.closure, &dk);
+  for (int k = 0; k < 2; ++k) {
+    const std::vector<int32_t>& boxes = k ? fb : cb;
+    std::vector<int32_t>& ch = k ? fc : cc;
+    for (size_t r = 0; r < boxes.size(); r += amrmhd::GHOST_BOX_W) {
+      const int32_t* b = &boxes[r];
+      const int bi = (int)(r / amrmhd::GHOST_BOX_W);
+      for (int c = 0; c < b[7] * b[8] * b[9]; c += amrk::FILL_CHUNK) {
+        ch.push_back(bi);
+        ch.push_back(c);
+      }
+    }
+  }
+  // the five lists and the closure matrix in one device block, one copy
   double idx[3], K[96] = {0};
   level_idx(S, lf, idx);
   amrmhd::closure_matrix(S->cfg.dim, idx, K);
-  if (!st) {
-    cudaError_t e = cudaMalloc((void**)&dK, sizeof(K));
-    if (e == cudaSuccess) e = cudaMemcpy(dK, K, sizeof(K), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, "regrid: closure matrix");
+  std::vector<char> img;
+  auto put = [&](const void* src, size_t bytes) {
+    const size_t o = (img.size() + 255) / 256 * 256;
+    img.resize(o + bytes);
+    if (bytes) std::memcpy(img.data() + o, src, bytes);
+    return o;
+  };
+  const size_t oK = put(K, sizeof(K)), ocb = put(cb.data(), sizeof(int32_t) * cb.size()),
+               occ = put(cc.data(), sizeof(int32_t) * cc.size()), ofb = put(fb.data(), sizeof(int32_t) * fb.size()),
+               ofc = put(fc.data(), sizeof(int32_t) * fc.size()),
+               ok = put(m.closure.data(), sizeof(int32_t) * m.closure.size());
+  char* dev = nullptr;
+  amrmhd_status st = AMRMHD_OK;
+  cudaError_t e0 = cudaMalloc((void**)&dev, img.size());
+  if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(dev, img.data(), img.size(), cudaMemcpyHostToDevice, S->stream);
+  if (e0 != cudaSuccess) {
+    if (dev) cudaFree(dev);
+    return fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer lists: ") + cudaGetErrorString(e0));
   }
+  int *dcb = (int*)(dev + ocb), *dcc = (int*)(dev + occ), *dfb = (int*)(dev + ofb), *dfc = (int*)(dev + ofc),
+      *dk = (int*)(dev + ok);
+  double* dK = (double*)(dev + oK);
   if (!st) {
     amrk::RowArgs a = row_args(S, DevList{dcb, (int64_t)cb.size() / amrmhd::GHOST_BOX_W}, lf - 1);
     a.fbuf = state_buf(S, S->cur[lf]);
@@ -180,12 +199,7 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf) {
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer: ") + cudaGetErrorString(e));
   }
-  cudaFree(dcb);
-  cudaFree(dcc);
-  cudaFree(dfb);
-  cudaFree(dfc);
-  cudaFree(dk);
-  cudaFree(dK);
+  cudaFree(dev);
   return st;
 }
 
@@ -206,20 +220,35 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     for (int d = 0; d < 3; ++d) { p.lo[d] = ctx->H.p[q].lo[d]; p.hi[d] = ctx->H.p[q].hi[d]; }
     ps.push_back(p);
   }
-  long long us[5] = {0, 0, 0, 0, 0}, t0 = now_us();
-  // level 0 of the old context: fill and flag
+  long long us[6] = {0, 0, 0, 0, 0, 0}, t0 = now_us();
+  // the new level-(l+1) boxes from level l of context c (ghosts filled): the
+  // flags on the device, clustered on the device (the block marks merged on the
+  // host) or on the host (the flag list copied back)
+  std::vector<std::array<int, 7>> boxes;
+  auto cluster = [&](amrmhd_ctx* c, int l) -> amrmhd_status {
+    long long t = now_us();
+    if (ctx->opt_device_cluster) {
+      amrmhd_status s = cluster_level_device(ctx, c, l, theta, boxes);
+      us[1] += now_us() - t;
+      return s;
+    }
+    std::vector<int32_t> flags;
+    amrmhd_status s = flag_level(ctx, c, l, theta, flags);
+    us[0] += now_us() - t;
+    if (s) return s;
+    t = now_us();
+    boxes = amrmhd::regrid_boxes(c->H, l, flags);
+    us[1] += now_us() - t;
+    return AMRMHD_OK;
+  };
+  // level 0 of the old context: fill and cluster
   int nl = 0;
   op_fill(ctx, 0, 1, &nl);
-  std::vector<int32_t> flags;
-  st = flag_level(ctx, ctx, 0, theta, flags);
-  if (st) return st;
   us[0] += now_us() - t0;
+  st = cluster(ctx, 0);
+  if (st) return st;
   amrmhd_ctx* prev = ctx;
-  const amrmhd::Hierarchy* prevH = &ctx->H;
   for (int l = 0; l + 1 < max_levels; ++l) {
-    t0 = now_us();
-    std::vector<std::array<int, 7>> boxes = amrmhd::regrid_boxes(*prevH, l, flags);
-    us[1] += now_us() - t0;
     if (boxes.empty()) break;
     std::vector<amrmhd_patch> next = ps;
     for (const auto& b : boxes) {
@@ -236,14 +265,14 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     us[2] += now_us() - t0;
     t0 = now_us();
     if (!st) st = copy_levels(ctx, prev, S, l);
-    if (!st) st = transfer(ctx, S, ctx, l + 1);
+    if (!st) st = transfer(ctx, S, ctx, l + 1, &us[5]);
     us[3] += now_us() - t0;
     if (!st) {
       t0 = now_us();
       op_fill(S, l + 1, 1, &nl);
-      flags.clear();
-      if (l + 2 < max_levels) st = flag_level(ctx, S, l + 1, theta, flags);
       us[0] += now_us() - t0;
+      boxes.clear();
+      if (l + 2 < max_levels) st = cluster(S, l + 1);
     }
     if (st) {
       if (S) amrmhd_destroy(S);
@@ -252,7 +281,6 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     }
     if (prev != ctx) amrmhd_destroy(prev);
     prev = S;
-    prevH = &S->H;
     ps = next;
   }
   {
@@ -279,9 +307,11 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
   // then holds (and frees) the old ones
   std::swap(*ctx, *prev);
   std::swap(ctx->own_stream, prev->own_stream);
+  std::swap(ctx->d_cluster, prev->d_cluster);
+  std::swap(ctx->cluster_cap, prev->cluster_cap);
   ctx->launches += prev->launches;
   amrmhd_destroy(prev);
-  for (int i = 0; i < 5; ++i) ctx->regrid_us[i] = us[i];
+  for (int i = 0; i < 6; ++i) ctx->regrid_us[i] = us[i];
   return AMRMHD_OK;
 }
 

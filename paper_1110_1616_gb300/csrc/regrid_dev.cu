@@ -1,0 +1,148 @@
+// The regrid's clustering on the device (Sec. 2: the new grids of level l+1
+// cover the flagged cells of level l): the flag test writes the level's cells
+// and its flagged cells as bytes of the clustering frame (the region's
+// bounding box, or the whole level extent), the flags are buffered by 2 cells
+// (dilated along x, then y, then z, with the periodic wrap where the frame
+// spans the domain), and one thread per 4^dim block marks the blocks that hold
+// a buffered flag inside the region and whose 3-cell surroundings lie in the
+// region (proper nesting). Only the block marks come back to the host, where
+// the greedy z,y,x merge of the host clustering (regrid.cpp, merge_blocks)
+// turns them into boxes: the same boxes, in the same order, as the host path
+// gives for the same flags.
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ctx.hpp"
+#include "regrid.hpp"
+
+namespace amrcl {
+
+struct Frame {
+  int dim;
+  int off[3], n[3], full[3], nb[3];
+  int per[3];
+  int N[3];  // the level's extent
+};
+
+// dst = src dilated by 2 cells along dimension d (wrapping if wrap)
+__global__ void k_dilate(const unsigned char* src, unsigned char* dst, Frame f, int d, int wrap) {
+  const long long ncell = (long long)f.n[0] * f.n[1] * f.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncell) return;
+  int c[3] = {(int)(t % f.n[0]), (int)((t / f.n[0]) % f.n[1]), (int)(t / ((long long)f.n[0] * f.n[1]))};
+  const long long st = d == 0 ? 1 : (d == 1 ? (long long)f.n[0] : (long long)f.n[0] * f.n[1]);
+  const long long base = t - (long long)c[d] * st;
+  const int n = f.n[d];
+  unsigned char v = 0;
+  for (int o = -2; o <= 2; ++o) {
+    int y = c[d] + o;
+    if (wrap) y = (y % n + n) % n;
+    else if (y < 0 || y >= n) continue;
+    v |= src[base + (long long)y * st];
+  }
+  dst[t] = v;
+}
+
+__global__ void k_blocks(const unsigned char* buf, const unsigned char* region, unsigned char* ok, Frame f) {
+  const long long nblk = (long long)f.nb[0] * f.nb[1] * f.nb[2];
+  const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nblk) return;
+  const int a = (int)(w % f.nb[0]), b = (int)((w / f.nb[0]) % f.nb[1]), c = (int)(w / ((long long)f.nb[0] * f.nb[1]));
+  const int kz = f.dim == 3 ? 1 : 0;
+  const int lo[3] = {4 * a, 4 * b, f.dim == 3 ? 4 * c : 0};
+  const int hi[3] = {lo[0] + 4, lo[1] + 4, f.dim == 3 ? lo[2] + 4 : 1};
+  auto at = [&](int i, int j, int k) { return ((long long)k * f.n[1] + j) * f.n[0] + i; };
+  bool want = false;
+  for (int k = lo[2]; k < hi[2] && !want; ++k)
+    for (int j = lo[1]; j < hi[1] && !want; ++j)
+      for (int i = lo[0]; i < hi[0] && !want; ++i) {
+        const long long x = at(i, j, k);
+        want = (buf[x] & region[x]) != 0;
+      }
+  bool allowed = want;
+  for (int k = lo[2] - 3 * kz; k < hi[2] + 3 * kz && allowed; ++k)
+    for (int j = lo[1] - 3; j < hi[1] + 3 && allowed; ++j)
+      for (int i = lo[0] - 3; i < hi[0] + 3 && allowed; ++i) {
+        int p[3] = {i, j, k};
+        bool in_box = true, inside = true;
+        for (int d = 0; d < f.dim && inside; ++d) {
+          if (f.full[d]) {
+            if (f.per[d]) p[d] = (p[d] % f.N[d] + f.N[d]) % f.N[d];
+            else if (p[d] < 0 || p[d] >= f.n[d]) inside = false;
+          } else {
+            const int g = p[d] + f.off[d];
+            if (!f.per[d] && (g < 0 || g >= f.N[d])) inside = false;
+            else if (p[d] < 0 || p[d] >= f.n[d]) in_box = false;
+          }
+        }
+        if (!inside) continue;
+        if (!in_box || !region[at(p[0], p[1], p[2])]) allowed = false;
+      }
+  ok[w] = allowed ? 1 : 0;
+}
+
+}  // namespace amrcl
+
+namespace amrapi {
+
+// New level-(l+1) boxes from the flagged cells of level l of context c (its
+// ghosts filled), clustered on the device; ctx holds the scratch and errors.
+amrmhd_status cluster_level_device(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta,
+                                   std::vector<std::array<int, 7>>& boxes) {
+  using namespace amrcl;
+  const amrmhd::Hierarchy& H = c->H;
+  const amrmhd::ClusterFrame fr = amrmhd::cluster_frame(H, l);
+  Frame f;
+  f.dim = H.dim;
+  for (int d = 0; d < 3; ++d) {
+    f.off[d] = fr.off[d];
+    f.n[d] = fr.n[d];
+    f.full[d] = fr.full[d];
+    f.nb[d] = fr.nb[d];
+    f.per[d] = H.per[d] ? 1 : 0;
+    f.N[d] = H.N(l, d);
+  }
+  const size_t ncell = (size_t)f.n[0] * f.n[1] * f.n[2], nblk = (size_t)f.nb[0] * f.nb[1] * f.nb[2];
+  const size_t need = 3 * ncell + nblk + 256;
+  if (ctx->cluster_cap < need) {
+    if (ctx->d_cluster) cudaFree(ctx->d_cluster);
+    ctx->d_cluster = nullptr;
+    ctx->cluster_cap = 0;
+    cudaError_t e = cudaMalloc((void**)&ctx->d_cluster, need);
+    if (e != cudaSuccess) {
+      ctx->d_cluster = nullptr;
+      return fail(ctx, AMRMHD_ENOMEM, std::string("regrid: cluster scratch: ") + cudaGetErrorString(e));
+    }
+    ctx->cluster_cap = need;
+  }
+  unsigned char* region = ctx->d_cluster;
+  unsigned char* buf = region + ncell;
+  unsigned char* tmp = buf + ncell;
+  unsigned char* ok = tmp + ncell;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemsetAsync(region, 0, 2 * ncell, st);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("regrid: ") + cudaGetErrorString(e));
+  amrk::LevelArgs a = level_args(c, l, c->d_scal, 1.0, 0);
+  amrk::DenseBox box;
+  for (int d = 0; d < 3; ++d) { box.off[d] = f.off[d]; box.n[d] = f.n[d]; }
+  c->ops->flag_dense(a, theta, region, buf, box, st);
+  const int T = 256;
+  unsigned char *src = buf, *dst = tmp;
+  for (int d = 0; d < f.dim; ++d) {
+    k_dilate<<<(unsigned)((ncell + T - 1) / T), T, 0, st>>>(src, dst, f, d, f.full[d] && f.per[d]);
+    std::swap(src, dst);
+  }
+  k_blocks<<<(unsigned)((nblk + T - 1) / T), T, 0, st>>>(src, region, ok, f);
+  ctx->launches += 2 + f.dim;
+  std::vector<uint8_t> h(nblk + 8, 0);
+  e = cudaMemcpyAsync(h.data(), ok, nblk, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("regrid: clustering: ") + cudaGetErrorString(e));
+  boxes = amrmhd::merge_blocks(H, l, fr, h.data());
+  return AMRMHD_OK;
+}
+
+}  // namespace amrapi

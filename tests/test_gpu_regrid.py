@@ -42,8 +42,9 @@ def norm_patches(ps):
     return [(int(l), tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for (l, lo, hi) in ps]
 
 
+@pytest.mark.parametrize("device_cluster", [1, 0])
 @pytest.mark.parametrize("case", ["clumps_2d", "clumps_2d_bounded", "clumps_3d"])
-def test_regrid_matches_oracle_fp64(case):
+def test_regrid_matches_oracle_fp64(case, device_cluster):
     if case == "clumps_3d":
         pb = inputs.clumps_3d_small(16, 2)
         maxl = 3
@@ -54,6 +55,7 @@ def test_regrid_matches_oracle_fp64(case):
             pb.bc = (2, 1, 1, 1, 0, 0)
             pb.inflow = inputs.conserved((1.0, 1.0, 0.0, 0.0, 1.0, 2 ** 0.5, 0.0, 0.0))
     ctx = gpu_for(pb)
+    ctx.set_option(A.OPT_DEVICE_CLUSTER, device_cluster)
     o = oracle_for(pb)
     for rnd in range(2):
         dts = ctx.step(2)
@@ -94,3 +96,31 @@ def test_regrid_mixed_conserves_and_keeps_divb():
         d = d[~np.isnan(d)]
         assert np.abs(d).max() <= 1e-5 * n * 2, l
     ctx.step(2)
+
+
+@pytest.mark.parametrize("case", ["clumps3d_32", "clumps3d_32_bounded", "clumps2d_64"])
+def test_device_clustering_equals_host(case):
+    """The device clustering (flag test, buffer and block marks on the GPU)
+    and the host clustering (flag list copied back) give the same patches and
+    the same transferred state, for several thresholds, through three levels."""
+    if case.startswith("clumps3d"):
+        pb = inputs.clumps_3d_small(32, 3)
+        if case.endswith("bounded"):
+            pb.bc = (1, 1, 2, 1, 1, 1)
+            pb.inflow = inputs.conserved((1.0, 1.0, 0.0, 0.0, 1.0, 2 ** 0.5, 0.0, 0.0))
+    else:
+        pb = inputs.clumps_2d(64, 3, b_pert=0.3)
+    for theta in (0.05, 0.1, 0.3):
+        res = []
+        for dev in (1, 0):
+            ctx = gpu_for(pb, A.MIXED)
+            ctx.set_option(A.OPT_DEVICE_CLUSTER, dev)
+            ctx.step(1)
+            ps = norm_patches(ctx.regrid(theta, 4))
+            res.append((ps, ctx.read_state()))
+        (pa, sa), (pb_, sb) = res
+        assert pa == pb_, (theta, len(pa), len(pb_))
+        assert len(pa) > len(pb.patches) // 4
+        for f in range(8):
+            for p in range(len(pa)):
+                assert np.array_equal(sa[f][p], sb[f][p]), (theta, f, p)
