@@ -396,6 +396,9 @@ enum {
   AMRMHD_Q_REGRID_MAPS_US = 10,
   /* of AMRMHD_Q_REGRID_TRANSFER_US, the building of the transfer maps */
   AMRMHD_Q_REGRID_TRANSFER_MAPS_US = 12,
+  /* host wall time of the last amrmhd_set_hierarchy in microseconds: validation and
+   * neighbour lists (host), the ghost boxes, the register/reflux/restriction maps */
+  AMRMHD_Q_MAPS_HOST_US = 13, AMRMHD_Q_MAPS_GHOST_US = 14, AMRMHD_Q_MAPS_REGISTERS_US = 15,
   /* raises by the density and pressure floors since bind_arena (amrmhd_set_floors);
    * synchronises the stream */
   AMRMHD_Q_FLOOR_EVENTS = 11

@@ -22,6 +22,7 @@ Q_NPATCH, Q_NLEVEL, Q_CELLS, Q_CELL_UPDATES_PER_STEP, Q_ARENA_BYTES, Q_KERNEL_LA
 Q_REGRID_FLAG_US, Q_REGRID_CLUSTER_US, Q_REGRID_BUILD_US, Q_REGRID_TRANSFER_US, Q_REGRID_MAPS_US = range(6, 11)
 Q_FLOOR_EVENTS = 11
 Q_REGRID_TRANSFER_MAPS_US = 12
+Q_MAPS_HOST_US, Q_MAPS_GHOST_US, Q_MAPS_REGISTERS_US = 13, 14, 15
 OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT, OPT_HOST_IO, OPT_DIRECT_HALO = 0, 1, 2, 3, 4, 5
 OPT_QUEUE, OPT_QUEUE_TILE, OPT_QUEUE_WITHHOLD, OPT_QUEUE_BALANCE = 6, 7, 8, 9
 OPT_DEVICE_MAPS, OPT_DEVICE_CLUSTER = 10, 11

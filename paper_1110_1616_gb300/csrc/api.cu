@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -770,11 +771,22 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
     rows[7 * i] = patches[i].level;
     for (int d = 0; d < 3; ++d) { rows[7 * i + 1 + d] = patches[i].lo[d]; rows[7 * i + 4 + d] = patches[i].hi[d]; }
   }
+  auto now = [] {
+    return std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+  };
+  long long t0 = now();
   int st = H.build(rows.data(), n);
+  ctx->maps_us[0] = now() - t0;
+  ctx->maps_us[1] = ctx->maps_us[2] = 0;
   if (st != AMRMHD_OK) return fail(ctx, (amrmhd_status)st, H.err);
   if (dev_maps) {
+    t0 = now();
     amrmhd_status ds = device_ghost_boxes(ctx);
+    ctx->maps_us[1] = now() - t0;
+    t0 = now();
     if (ds == AMRMHD_OK && dev_regs) ds = device_register_maps(ctx);
+    ctx->maps_us[2] = now() - t0;
     if (ds != AMRMHD_OK) return ds;
   }
   // arena layout: patches in (level, id) order
@@ -1517,6 +1529,9 @@ amrmhd_status amrmhd_query(amrmhd_ctx* ctx, int32_t what, int64_t* value) {
     case AMRMHD_Q_REGRID_TRANSFER_US:
     case AMRMHD_Q_REGRID_MAPS_US: *value = ctx->regrid_us[what - AMRMHD_Q_REGRID_FLAG_US]; return AMRMHD_OK;
     case AMRMHD_Q_REGRID_TRANSFER_MAPS_US: *value = ctx->regrid_us[5]; return AMRMHD_OK;
+    case AMRMHD_Q_MAPS_HOST_US:
+    case AMRMHD_Q_MAPS_GHOST_US:
+    case AMRMHD_Q_MAPS_REGISTERS_US: *value = ctx->maps_us[what - AMRMHD_Q_MAPS_HOST_US]; return AMRMHD_OK;
     case AMRMHD_Q_FLOOR_EVENTS: {
       unsigned long long v = 0;
       if (ctx->bound && ctx->d_floor_events) {

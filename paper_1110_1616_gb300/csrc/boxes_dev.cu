@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.hpp"
@@ -63,6 +64,8 @@ struct BArgs {
   int* out_cells;
   int* out_faces;
   unsigned long long* err;  // smallest (task << 32 | position) without a source
+  int* scratch;             // one pass: up to cap rows per task at task * cap
+  int cap;
 };
 
 __host__ __device__ __forceinline__ int Nl(const BArgs& a, int l, int e) { return e < a.dim ? (a.base[e] << l) : 1; }
@@ -73,16 +76,18 @@ __host__ __device__ __forceinline__ void shift_of(int code, int* s) {
   s[2] = code / 9 - 1;
 }
 
-__host__ __device__ __forceinline__ void decode(const BTask& T, long long t, int* x) {
-  x[0] = (int)(t % T.ex[0]);
-  x[1] = (int)((t / T.ex[0]) % T.ex[1]);
-  x[2] = (int)(t / ((long long)T.ex[0] * T.ex[1]));
+// (positions within a task are below 2^31: a patch has at most 2^28 elements per field)
+__host__ __device__ __forceinline__ void decode(const BTask& T, int t, int* x) {
+  const int r = t / T.ex[0];
+  x[0] = t - r * T.ex[0];
+  x[1] = r % T.ex[1];
+  x[2] = r / T.ex[1];
 }
 
 // ---- ghost boxes
 
 // label of position t of ghost task T: -1 the patch's own position, -3 no source
-__host__ __device__ inline int ghost_label(const BArgs& a, const BTask& T, long long t) {
+__host__ __device__ inline int ghost_label(const BArgs& a, const BTask& T, int t) {
   const BPatch& P = a.P[T.q];
   const int l = P.level, d = T.d, dim = a.dim;
   const int ns = T.s1 - T.s0, np = T.p1 - T.p0;
@@ -199,12 +204,40 @@ __host__ __device__ inline int old_owner(const BArgs& a, const BTask& T, const i
   return -1;
 }
 
+// the owner lookup of the host emulation and the global-memory path: a scan of the entries
+struct LoopOwner {
+  const BArgs& a;
+  const BTask& T;
+  __host__ __device__ int operator()(const int* h) const { return old_owner(a, T, h); }
+};
+
+// the shared-memory path: the entries scattered over the patch's box grown by
+// 2 fine cells (entry index relative to T.s0, or -1)
+template <class ET>
+struct GridOwner {
+  const BArgs& a;
+  const BTask& T;
+  const ET* grid;
+  __host__ __device__ int operator()(const int* h) const {
+    const BPatch& P = a.P[T.q];
+    long long i = 0, st = 1;
+    for (int e = 0; e < a.dim; ++e) {
+      const int x = h[e] - (P.lo[e] - 2), n = P.n[e] + 4;
+      if (x < 0 || x >= n) return old_owner(a, T, h);
+      i += x * st;
+      st *= n;
+    }
+    return grid[i] < 0 ? -1 : T.s0 + grid[i];
+  }
+};
+
 // coarse cell c covered by the old fine level
-__host__ __device__ inline bool old_covers(const BArgs& a, const BTask& T, const int* c) {
+template <class OW>
+__host__ __device__ inline bool old_covers(const BArgs& a, const OW& own, const int* c) {
   if (!a.have_old) return false;
   int h[3];
   for (int e = 0; e < 3; ++e) h[e] = e < a.dim ? 2 * c[e] : 0;
-  return old_owner(a, T, h) >= 0;
+  return own(h) >= 0;
 }
 
 // the new coarse patch candidate holding coarse cell c (periodic wrap), or -1
@@ -238,7 +271,8 @@ __host__ __device__ inline int old_loc(const BArgs& a, const BTask& T, int i, co
 // label of position t of transfer task T: a copy (id = old entry index) or a
 // prolongation (id = ns + 8 coarse candidate + the dimensions where the face
 // position wraps); -3 no source
-__host__ __device__ inline int transfer_label(const BArgs& a, const BTask& T, long long t) {
+template <class OW>
+__host__ __device__ inline int transfer_label(const BArgs& a, const BTask& T, int t, const OW& own) {
   const BPatch& P = a.P[T.q];
   const int lf = P.level, d = T.d, dim = a.dim;
   const int ns = T.s1 - T.s0;
@@ -249,8 +283,8 @@ __host__ __device__ inline int transfer_label(const BArgs& a, const BTask& T, lo
     pq[e] = e < dim ? g[e] >> 1 : 0;
   }
   if (d < 0) {
-    if (old_covers(a, T, pq)) {
-      const int i = old_owner(a, T, g);
+    if (old_covers(a, own, pq)) {
+      const int i = own(g);
       return i < 0 ? -3 : i - T.s0;
     }
     const int jc = new_coarse(a, T, pq);
@@ -260,12 +294,12 @@ __host__ __device__ inline int transfer_label(const BArgs& a, const BTask& T, lo
   m[d] -= 1;
   for (int e = 0; e < 3; ++e) pm[e] = e < dim ? m[e] >> 1 : 0;
   const bool interior = pq[d] == pm[d];
-  const bool copy = interior ? old_covers(a, T, pq) : (old_covers(a, T, pq) || old_covers(a, T, pm));
+  const bool copy = interior ? old_covers(a, own, pq) : (old_covers(a, own, pq) || old_covers(a, own, pm));
   if (copy) {  // the owners of the cells on the face's two sides
     int best = -1, bi = 0, bl = 0;
-    const int i1 = old_owner(a, T, g);
+    const int i1 = own(g);
     if (i1 >= 0) { best = a.pairs[2 * i1]; bi = i1; bl = old_loc(a, T, i1, g); }
-    const int i0 = old_owner(a, T, m);
+    const int i0 = own(m);
     if (i0 >= 0) {
       const int L = old_loc(a, T, i0, g);
       if (best < 0 || a.pairs[2 * i0] < best || (a.pairs[2 * i0] == best && L < bl)) { best = a.pairs[2 * i0]; bi = i0; bl = L; }
@@ -310,9 +344,10 @@ __host__ __device__ inline void transfer_row(const BArgs& a, const BTask& T, int
 
 // closure cell c of new patch task T: a coarse cell of the footprint not
 // covered by the old fine level with a face neighbour (inside the domain) that is
-__host__ __device__ inline bool closure_cell(const BArgs& a, const BTask& T, const int* c) {
+template <class OW>
+__host__ __device__ inline bool closure_cell(const BArgs& a, const BTask& T, const int* c, const OW& own) {
   const int lc = a.P[T.q].level - 1, dim = a.dim;
-  if (old_covers(a, T, c)) return false;
+  if (old_covers(a, own, c)) return false;
   for (int e = 0; e < dim; ++e)
     for (int sgn = -1; sgn <= 1; sgn += 2) {
       int nb[3] = {c[0], c[1], c[2]};
@@ -320,38 +355,41 @@ __host__ __device__ inline bool closure_cell(const BArgs& a, const BTask& T, con
       bool in = true;
       for (int e2 = 0; e2 < dim; ++e2)
         if (!a.per[e2] && (nb[e2] < 0 || nb[e2] >= Nl(a, lc, e2))) in = false;
-      if (in && old_covers(a, T, nb)) return true;
+      if (in && old_covers(a, own, nb)) return true;
     }
   return false;
 }
 
-__host__ __device__ __forceinline__ int label_of(const BArgs& a, const BTask& T, long long t) {
-  return T.transfer ? transfer_label(a, T, t) : ghost_label(a, T, t);
+__host__ __device__ __forceinline__ int label_of(const BArgs& a, const BTask& T, int t) {
+  return T.transfer ? transfer_label(a, T, t, LoopOwner{a, T}) : ghost_label(a, T, t);
 }
 
 // ---- the greedy merge (one warp)
 
-template <bool EMIT, class GT>
+// MODE 0 counts the boxes, 1 writes them at the task's first row, 2 counts
+// them and writes the first a.cap of them into the task's scratch rows
+template <int MODE, class GT>
 __device__ void warp_merge(const BArgs& a, int ti, GT* G) {
   const BTask& T = a.T[ti];
   const int lane = threadIdx.x & 31;
   const int e0 = T.ex[0], e1 = T.ex[1], e2 = T.ex[2];
-  const long long tot = (long long)e0 * e1 * e2;
-  auto at = [&](int x, int y, int z) { return ((long long)z * e1 + y) * e0 + x; };
+  const int tot = e0 * e1 * e2;
+  auto at = [&](int x, int y, int z) { return (z * e1 + y) * e0 + x; };
   const unsigned FULL = 0xffffffffu;
-  long long pos = 0, count = 0;
-  const long long base = EMIT ? a.first[ti] : 0;
-  int* out = T.d < 0 ? a.out_cells : a.out_faces;
+  int pos = 0;
+  long long count = 0;
+  const long long base = MODE == 1 ? a.first[ti] : 0;
+  int* out = MODE == 2 ? a.scratch + 13LL * ti * a.cap : (T.d < 0 ? a.out_cells : a.out_faces);
   for (;;) {
-    long long t0 = -1;
+    int t0 = -1;
     for (; pos < tot; pos += 32) {
-      const long long idx = pos + lane;
+      const int idx = pos + lane;
       const unsigned m = __ballot_sync(FULL, idx < tot && G[idx] >= 0);
       if (m) { t0 = pos + __ffs(m) - 1; break; }
     }
     if (t0 < 0) break;
     const int k = G[t0];
-    const int a0 = (int)(t0 % e0), b0 = (int)((t0 / e0) % e1), c0 = (int)(t0 / ((long long)e0 * e1));
+    const int r0 = t0 / e0, a0 = t0 - r0 * e0, b0 = r0 % e1, c0 = r0 / e1;
     int nx = 1;
     for (;;) {
       const int x = a0 + nx + lane;
@@ -379,7 +417,7 @@ __device__ void warp_merge(const BArgs& a, int ti, GT* G) {
       for (int y = 0; y < ny; ++y)
         for (int i = lane; i < nx; i += 32) G[at(a0 + i, b0 + y, c0 + z)] = -2;
     __syncwarp();
-    if (EMIT && lane == 0) {
+    if (MODE != 0 && lane == 0 && (MODE == 1 || count < a.cap)) {
       int* r = out + 13 * (base + count);
       const int o = T.transfer ? 4 : 0;  // transfer boxes: lo in the patch's ghosted frame
       if (T.transfer) transfer_row(a, T, k, r);
@@ -394,24 +432,192 @@ __device__ void warp_merge(const BArgs& a, int ti, GT* G) {
     ++count;
     pos = t0 + 1;
   }
-  if (!EMIT && lane == 0) a.cnt[ti] = count;
+  if (MODE != 1 && lane == 0) a.cnt[ti] = count;
 }
 
-// one task per CTA, its label grid (16-bit ids) in shared memory
-template <bool EMIT>
-__global__ void __launch_bounds__(256) k_box_tasks_smem(BArgs a, const int* list, int n) {
-  extern __shared__ short sg[];
+// the positions of the task box meeting [lo, hi) (local coordinates): false if none
+__device__ __forceinline__ bool clip_box(const BTask& T, int* lo, int* hi) {
+  for (int e = 0; e < 3; ++e) {
+    lo[e] = max(lo[e], 0);
+    hi[e] = min(hi[e], T.ex[e]);
+    if (hi[e] <= lo[e]) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool own_pos(const BPatch& P, int d, int dim, const int* x) {
+  bool own = true;
+  for (int e = 0; e < dim; ++e) own = own && x[e] >= 4 && x[e] < P.n[e] + 4 + (e == d ? 1 : 0);
+  return own;
+}
+
+// f(x) for every position x of the box [lo, hi): one warp per row, lanes along x
+template <class F>
+__device__ __forceinline__ void for_box(const int* lo, const int* hi, F&& f) {
+  const int by = hi[1] - lo[1], rows = by * (hi[2] - lo[2]);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = threadIdx.x >> 5; r < rows; r += nw) {
+    int x[3];
+    x[1] = lo[1] + r % by;
+    x[2] = lo[2] + r / by;
+    for (x[0] = lo[0] + lane; x[0] < hi[0]; x[0] += 32) f(x);
+  }
+}
+
+// Ghost labels of task T into the shared-memory grid G by scattering the
+// entries' boxes in the host builder's order (the labels of ghost_label)
+template <class ET>
+__device__ void ghost_scatter(const BArgs& a, int ti, ET* G) {
+  const BTask& T = a.T[ti];
+  const BPatch& P = a.P[T.q];
+  const int l = P.level, d = T.d, dim = a.dim, ns = T.s1 - T.s0, np = T.p1 - T.p0;
+  const int tot = T.ex[0] * T.ex[1] * T.ex[2];
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) G[t] = -1;
+  __syncthreads();
+  auto at = [&](const int* x) { return (x[2] * T.ex[1] + x[1]) * T.ex[0] + x[0]; };
+  // same-level neighbours in list order: a cell is held by one; a face held by
+  // two goes to the smaller (patch, local index)
+  for (int i = T.s0; i < T.s1; ++i) {
+    const int qq = a.pairs[2 * i];
+    const BPatch& Q = a.P[qq];
+    int s[3], lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, dl[3] = {0, 0, 0};
+    shift_of(a.pairs[2 * i + 1], s);
+    for (int e = 0; e < dim; ++e) {
+      const int o = s[e] * Nl(a, l, e);
+      lo[e] = Q.lo[e] + o - T.g0[e];
+      hi[e] = Q.lo[e] + Q.n[e] + o + (e == d ? 1 : 0) - T.g0[e];
+      dl[e] = P.lo[e] - Q.lo[e] - o;
+    }
+    if (clip_box(T, lo, hi))
+      for_box(lo, hi, [&](const int* x) {
+        if (own_pos(P, d, dim, x)) return;
+        const int t = at(x);
+        const int cur = G[t];
+        bool take = d < 0 || cur < 0;
+        if (!take) {
+          const int L = (x[0] + dl[0]) + Q.ext[0] * ((x[1] + dl[1]) + Q.ext[1] * (x[2] + dl[2]));
+          const int ci = T.s0 + cur, cq = a.pairs[2 * ci];
+          const BPatch& C = a.P[cq];
+          int cs[3], cd[3] = {0, 0, 0};
+          shift_of(a.pairs[2 * ci + 1], cs);
+          for (int e = 0; e < dim; ++e) cd[e] = P.lo[e] - C.lo[e] - cs[e] * Nl(a, l, e);
+          const int Lc = (x[0] + cd[0]) + C.ext[0] * ((x[1] + cd[1]) + C.ext[1] * (x[2] + cd[2]));
+          take = qq < cq || (qq == cq && L < Lc);
+        }
+        if (take) G[t] = (ET)(i - T.s0);
+      });
+    __syncthreads();
+  }
+  // prolongation: the first coarse candidate and image holding the parent cell
+  for (int j = T.p0; j < T.p1; ++j) {
+    const BPatch& C = a.P[a.pairs[2 * j]];
+    int w[3], lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    shift_of(a.pairs[2 * j + 1], w);
+    for (int e = 0; e < dim; ++e) {
+      const int aux = w[e] * Nl(a, l, e);
+      const int top = (e == d && !a.per[e] && C.lo[e] + C.n[e] == Nl(a, l - 1, e)) ? 1 : 0;
+      lo[e] = 2 * C.lo[e] - aux - T.g0[e];
+      hi[e] = 2 * (C.lo[e] + C.n[e]) + top - aux - T.g0[e];
+    }
+    if (clip_box(T, lo, hi))
+      for_box(lo, hi, [&](const int* x) {
+        if (own_pos(P, d, dim, x)) return;
+        const int t = at(x);
+        if (G[t] < 0) G[t] = (ET)(ns + (j - T.p0));
+      });
+    __syncthreads();
+  }
+  // outside a bounded side: the boundary state; every other ghost position must have a source
+  const int lo[3] = {0, 0, 0}, hi[3] = {T.ex[0], T.ex[1], T.ex[2]};
+  for_box(lo, hi, [&](const int* x) {
+    if (own_pos(P, d, dim, x)) return;
+    const int t = at(x);
+    if (T.touches) {
+      const int g[3] = {T.g0[0] + x[0], T.g0[1] + x[1], T.g0[2] + x[2]};
+      bool out = false, inflow = false;
+      int code = 0, w3 = 1;
+      for (int e = 0; e < dim; ++e, w3 *= 3) {
+        if (a.per[e]) continue;
+        const int top = e == d ? Nl(a, l, e) : Nl(a, l, e) - 1;
+        if (g[e] < 0) { out = true; code += 1 * w3; inflow |= a.bc[e][0] == 2; }
+        else if (g[e] > top) { out = true; code += 2 * w3; inflow |= a.bc[e][1] == 2; }
+      }
+      if (out) { G[t] = (ET)(ns + np + (inflow ? 27 : code)); return; }
+    }
+    if (G[t] < 0) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
+  });
+  __syncthreads();
+}
+
+// Transfer labels of task T into G: the old entries scattered over the patch's
+// box grown by 2 fine cells (W), then every position's label with owner lookups in W
+template <class ET>
+__device__ void transfer_fill(const BArgs& a, int ti, ET* G, ET* W) {
+  const BTask& T = a.T[ti];
+  const BPatch& P = a.P[T.q];
+  const int lf = P.level, dim = a.dim;
+  int gn[3];
+  for (int e = 0; e < 3; ++e) gn[e] = e < dim ? P.n[e] + 4 : 1;
+  const int gw = gn[0] * gn[1] * gn[2];
+  for (int t = threadIdx.x; t < gw; t += blockDim.x) W[t] = -1;
+  __syncthreads();
+  if (a.have_old)
+    for (int i = T.s0; i < T.s1; ++i) {
+      const BPatch& O = a.PO[a.pairs[2 * i]];
+      int s[3], lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+      shift_of(a.pairs[2 * i + 1], s);
+      bool empty = false;
+      for (int e = 0; e < dim; ++e) {
+        const int o = s[e] * Nl(a, lf, e);
+        lo[e] = max(O.lo[e] + o - (P.lo[e] - 2), 0);
+        hi[e] = min(O.lo[e] + O.n[e] + o - (P.lo[e] - 2), gn[e]);
+        if (hi[e] <= lo[e]) empty = true;
+      }
+      if (!empty)
+        for_box(lo, hi, [&](const int* x) {
+          const int t = (x[2] * gn[1] + x[1]) * gn[0] + x[0];
+          if (W[t] < 0) W[t] = (ET)(i - T.s0);
+        });
+      __syncthreads();
+    }
+  const GridOwner<ET> own{a, T, W};
+  const int tot = T.ex[0] * T.ex[1] * T.ex[2];
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int id = transfer_label(a, T, t, own);
+    if (id == -3) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
+    G[t] = (ET)(id < 0 ? -1 : id);
+  }
+  __syncthreads();
+}
+
+constexpr int kBoxThreads = 256;
+
+// one task per CTA, its label grid (ids of type ET) in shared memory (transfer
+// tasks: followed by the owner grid)
+template <class ET, int MODE>
+__global__ void __launch_bounds__(kBoxThreads) k_box_tasks_smem(BArgs a, const int* list, int n) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  ET* sg = (ET*)sraw;
   if ((int)blockIdx.x >= n) return;
   const int ti = list[blockIdx.x];
   const BTask& T = a.T[ti];
-  const long long tot = (long long)T.ex[0] * T.ex[1] * T.ex[2];
-  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int id = label_of(a, T, t);
-    if (id == -3) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
-    sg[t] = (short)(id < 0 ? -1 : id);
+  if (T.transfer) {
+    const int tot = T.ex[0] * T.ex[1] * T.ex[2];
+    transfer_fill(a, ti, sg, sg + (tot + 15) / 16 * 16);
+  } else {
+    ghost_scatter(a, ti, sg);
   }
-  __syncthreads();
-  if (threadIdx.x < 32) warp_merge<EMIT>(a, ti, sg);
+  if (threadIdx.x < 32) warp_merge<MODE>(a, ti, sg);
+}
+
+// the one-pass rows of every task to their places in the cell and face lists
+__global__ void k_box_compact(BArgs a, int nt) {
+  const int ti = blockIdx.x;
+  if (ti >= nt) return;
+  const long long n = 13LL * a.cnt[ti];
+  const int* src = a.scratch + 13LL * ti * a.cap;
+  int* dst = (a.T[ti].d < 0 ? a.out_cells : a.out_faces) + 13LL * a.first[ti];
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 // large tasks: labels into their global grids, then one warp per task merges
@@ -419,8 +625,8 @@ __global__ void k_box_label_global(BArgs a, const int* list, int n) {
   for (int k = blockIdx.y; k < n; k += gridDim.y) {
     const int ti = list[k];
     const BTask& T = a.T[ti];
-    const long long tot = (long long)T.ex[0] * T.ex[1] * T.ex[2];
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int tot = T.ex[0] * T.ex[1] * T.ex[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
       const int id = label_of(a, T, t);
       if (id == -3) atomicMin(a.err, ((unsigned long long)ti << 32) | (unsigned long long)t);
       a.G[T.go + t] = id < 0 ? -1 : id;
@@ -428,12 +634,12 @@ __global__ void k_box_label_global(BArgs a, const int* list, int n) {
   }
 }
 
-template <bool EMIT>
+template <int MODE>
 __global__ void k_box_merge_global(BArgs a, const int* list, int n) {
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (k >= n) return;  // the whole warp
   const int ti = list[k];
-  warp_merge<EMIT>(a, ti, a.G + a.T[ti].go);
+  warp_merge<MODE>(a, ti, a.G + a.T[ti].go);
 }
 
 // closure mask of the footprints of the listed transfer cell tasks
@@ -444,11 +650,11 @@ __global__ void k_closure_mask(BArgs a, const int* list, const long long* moff, 
   const BPatch& P = a.P[T.q];
   int nc[3];
   for (int e = 0; e < 3; ++e) nc[e] = e < a.dim ? P.n[e] / 2 : 1;
-  const long long tot = (long long)nc[0] * nc[1] * nc[2];
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    int c[3] = {(int)(t % nc[0]), (int)((t / nc[0]) % nc[1]), (int)(t / ((long long)nc[0] * nc[1]))};
+  const int tot = nc[0] * nc[1] * nc[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    int c[3] = {t % nc[0], (t / nc[0]) % nc[1], t / (nc[0] * nc[1])};
     for (int e = 0; e < a.dim; ++e) c[e] += P.lo[e] / 2;
-    mask[moff[k] + t] = closure_cell(a, T, c) ? 1 : 0;
+    mask[moff[k] + t] = closure_cell(a, T, c, LoopOwner{a, T}) ? 1 : 0;
   }
 }
 
@@ -655,14 +861,25 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   *bad = -1;
   const int nt = (int)T.size();
   if (!nt) return AMRMHD_OK;
-  // shared-memory tasks and global-memory tasks
-  std::vector<int> small, large;
-  long long gtot = 0, smax = 0;
+  // tasks labelled in shared memory with 8-bit ids, with 16-bit ids, and the
+  // large ones in global memory
+  std::vector<int> s8, s16, large;
+  long long gtot = 0, need8 = 1, need16 = 1;
   for (int i = 0; i < nt; ++i) {
     const long long tot = (long long)T[i].ex[0] * T[i].ex[1] * T[i].ex[2];
-    if (2 * tot <= (long long)kBoxSmem && max_id(T[i]) < 32767) {
-      small.push_back(i);
-      smax = std::max(smax, tot);
+    long long need = tot;
+    if (T[i].transfer) {  // the owner grid over the patch grown by 2 fine cells
+      long long gw = 1;
+      for (int e = 0; e < H.dim; ++e) gw *= P[T[i].q].n[e] + 4;
+      need = (tot + 15) / 16 * 16 + gw;
+    }
+    const long long mid = std::max<long long>(max_id(T[i]), T[i].s1 - T[i].s0);
+    if (mid < 127 && need <= (long long)kBoxSmem) {
+      s8.push_back(i);
+      need8 = std::max(need8, need);
+    } else if (mid < 32767 && 2 * need <= (long long)kBoxSmem) {
+      s16.push_back(i);
+      need16 = std::max(need16, need);
     } else {
       large.push_back(i);
       T[i].go = gtot;
@@ -681,6 +898,7 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
         for (int e = 0; e < H.dim; ++e) v *= P[T[i].q].n[e] / 2;
         mtot += v;
       }
+  const int cap = 256;  // rows per task kept by the one-pass merge
   std::vector<char> img;
   auto put = [&](const void* src, size_t bytes) {
     const size_t o = (img.size() + 255) / 256 * 256;
@@ -691,22 +909,23 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   const size_t oP = put(P.data(), sizeof(BPatch) * P.size()),
                oPO = put(PO ? PO->data() : nullptr, sizeof(BPatch) * (PO ? PO->size() : 0)),
                oT = put(T.data(), sizeof(BTask) * nt), oPr = put(pairs.data(), sizeof(int) * pairs.size()),
-               oI = put(ids.data(), sizeof(int) * ids.size()), oS = put(small.data(), sizeof(int) * small.size()),
-               oL = put(large.data(), sizeof(int) * large.size()), oCT = put(ctask.data(), sizeof(int) * ctask.size()),
-               oMO = put(moff.data(), sizeof(long long) * moff.size());
+               oI = put(ids.data(), sizeof(int) * ids.size()), o8 = put(s8.data(), sizeof(int) * s8.size()),
+               o16 = put(s16.data(), sizeof(int) * s16.size()), oL = put(large.data(), sizeof(int) * large.size()),
+               oCT = put(ctask.data(), sizeof(int) * ctask.size()), oMO = put(moff.data(), sizeof(long long) * moff.size());
   const size_t in_bytes = img.size();
   size_t o = (in_bytes + 255) / 256 * 256;
   auto reserve = [&](size_t bytes) { const size_t r = o; o = (o + bytes + 255) / 256 * 256; return r; };
   const size_t oG = reserve(sizeof(int) * gtot), oCnt = reserve(sizeof(long long) * nt),
                oFirst = reserve(sizeof(long long) * nt), oErr = reserve(sizeof(unsigned long long)),
-               oMask = reserve((size_t)mtot);
+               oMask = reserve((size_t)mtot), oScr = reserve(sizeof(int) * 13 * (size_t)cap * nt);
+  // scratch from the stream-ordered allocator (no device-wide synchronisation on free)
   char* dev = nullptr;
-  cudaError_t e = cudaMalloc((void**)&dev, o);
+  cudaError_t e = cudaMallocAsync((void**)&dev, o, st);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
   int* dout = nullptr;
   auto done = [&](amrmhd_status s, const std::string& m) {
-    cudaFree(dev);
-    if (dout) cudaFree(dout);
+    cudaFreeAsync(dev, st);
+    if (dout) cudaFreeAsync(dout, st);
     return s == AMRMHD_OK ? s : fail(ctx, s, m);
   };
   e = cudaMemcpyAsync(dev, img.data(), in_bytes, cudaMemcpyHostToDevice, st);
@@ -731,33 +950,35 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   a.cnt = (long long*)(dev + oCnt);
   a.first = (const long long*)(dev + oFirst);
   a.err = (unsigned long long*)(dev + oErr);
-  const int* dsmall = (const int*)(dev + oS);
-  const int* dlarge = (const int*)(dev + oL);
-  const size_t smem = (size_t)std::max<long long>(smax, 1) * sizeof(short);
+  a.scratch = (int*)(dev + oScr);
+  a.cap = cap;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_box_tasks_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
-    cudaFuncSetAttribute(k_box_tasks_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
+    for (auto f : {k_box_tasks_smem<signed char, 0>, k_box_tasks_smem<signed char, 1>, k_box_tasks_smem<signed char, 2>})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
+    for (auto f : {k_box_tasks_smem<short, 0>, k_box_tasks_smem<short, 1>, k_box_tasks_smem<short, 2>})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
     attr = true;
   }
   long long lmax = 0;
   for (int i : large) lmax = std::max(lmax, (long long)T[i].ex[0] * T[i].ex[1] * T[i].ex[2]);
   const dim3 lg((unsigned)std::min<long long>((lmax + 255) / 256, 64), (unsigned)std::min<size_t>(large.size(), 65535));
   const int WPB = 4;
-  auto launch = [&](bool emit) {
-    if (!small.empty()) {
-      if (emit) k_box_tasks_smem<true><<<(unsigned)small.size(), 256, smem, st>>>(a, dsmall, (int)small.size());
-      else k_box_tasks_smem<false><<<(unsigned)small.size(), 256, smem, st>>>(a, dsmall, (int)small.size());
-    }
+  const size_t sm8 = (size_t)need8, sm16 = 2 * (size_t)need16;
+  auto launch = [&](auto mode) {
+    constexpr int M = decltype(mode)::value;
+    if (!s8.empty())
+      k_box_tasks_smem<signed char, M><<<(unsigned)s8.size(), kBoxThreads, sm8, st>>>(a, (const int*)(dev + o8), (int)s8.size());
+    if (!s16.empty())
+      k_box_tasks_smem<short, M><<<(unsigned)s16.size(), kBoxThreads, sm16, st>>>(a, (const int*)(dev + o16), (int)s16.size());
     if (!large.empty()) {
-      k_box_label_global<<<lg, 256, 0, st>>>(a, dlarge, (int)large.size());
-      const unsigned mb = (unsigned)((large.size() + WPB - 1) / WPB);
-      if (emit) k_box_merge_global<true><<<mb, 32 * WPB, 0, st>>>(a, dlarge, (int)large.size());
-      else k_box_merge_global<false><<<mb, 32 * WPB, 0, st>>>(a, dlarge, (int)large.size());
+      k_box_label_global<<<lg, 256, 0, st>>>(a, (const int*)(dev + oL), (int)large.size());
+      k_box_merge_global<M><<<(unsigned)((large.size() + WPB - 1) / WPB), 32 * WPB, 0, st>>>(a, (const int*)(dev + oL), (int)large.size());
     }
-    ctx->launches += (small.empty() ? 0 : 1) + (large.empty() ? 0 : 2);
+    ctx->launches += (s8.empty() ? 0 : 1) + (s16.empty() ? 0 : 1) + (large.empty() ? 0 : 2);
   };
-  launch(false);
+  // one pass: count every task's boxes and keep up to cap of them
+  launch(std::integral_constant<int, 2>());
   if (closure && mtot) {
     k_closure_mask<<<dim3(8, (unsigned)ctask.size()), 256, 0, st>>>(a, (const int*)(dev + oCT),
                                                                    (const long long*)(dev + oMO), (int)ctask.size(),
@@ -782,19 +1003,26 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   }
   std::vector<long long> first(nt);
   long long nc = 0, nf = 0;
+  bool over = false;
   for (int i = 0; i < nt; ++i) {
     long long& acc = T[i].d < 0 ? nc : nf;
     first[i] = acc;
     acc += cnt[i];
+    over = over || cnt[i] > cap;
   }
-  e = cudaMalloc((void**)&dout, sizeof(int) * 13 * std::max<long long>(nc + nf, 1));
+  e = cudaMallocAsync((void**)&dout, sizeof(int) * 13 * std::max<long long>(nc + nf, 1), st);
   if (e != cudaSuccess) { dout = nullptr; return done(AMRMHD_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e)); }
   a.out_cells = dout;
   a.out_faces = dout + 13 * nc;
   e = cudaMemcpyAsync(dev + oFirst, first.data(), sizeof(long long) * nt, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-  // the merge takes the grids apart: label again, then merge and write the boxes
-  launch(true);
+  if (over) {
+    // a task with more boxes than the one-pass rows: label again and write every box in place
+    launch(std::integral_constant<int, 1>());
+  } else {
+    k_box_compact<<<nt, 128, 0, st>>>(a, nt);
+    ctx->launches += 1;
+  }
   cells.resize(13 * (size_t)nc);
   faces.resize(13 * (size_t)nf);
   e = cudaGetLastError();

@@ -158,6 +158,7 @@ struct amrmhd_ctx {
   // host wall time of the last regrid, microseconds: flagging, clustering,
   // hierarchy and map building with the stage arenas, data transfer
   long long regrid_us[6] = {0, 0, 0, 0, 0, 0};  // the five above, then the transfer maps
+  long long maps_us[3] = {0, 0, 0};  // the last set_hierarchy: host build, ghost boxes, register maps
   // inter-level concurrency: side stream and fork/join events per level
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev_fork, ev_join;

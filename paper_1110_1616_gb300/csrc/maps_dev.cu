@@ -567,12 +567,14 @@ amrmhd_status device_register_maps(amrmhd_ctx* ctx) {
     oCnt[s] = reserve(sizeof(long long) * 3 * nch[s]);
     oFirst[s] = reserve(sizeof(long long) * 3 * nch[s]);
   }
+  // scratch from the stream-ordered allocator: freed on the stream, reused by
+  // the next builder call without a device-wide synchronisation
   char* dev = nullptr;
-  cudaError_t e = cudaMalloc((void**)&dev, o);
-  if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, std::string("device maps: ") + cudaGetErrorString(e));
   cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMallocAsync((void**)&dev, o, st);
+  if (e != cudaSuccess) return fail(ctx, AMRMHD_ENOMEM, std::string("device maps: ") + cudaGetErrorString(e));
   auto done = [&](amrmhd_status s, const std::string& m) {
-    cudaFree(dev);
+    cudaFreeAsync(dev, st);
     return s == AMRMHD_OK ? s : fail(ctx, s, m);
   };
   e = cudaMemcpyAsync(dev, img.data(), in_bytes, cudaMemcpyHostToDevice, st);

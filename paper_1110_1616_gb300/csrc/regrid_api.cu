@@ -166,10 +166,10 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf, lo
                ok = put(m.closure.data(), sizeof(int32_t) * m.closure.size());
   char* dev = nullptr;
   amrmhd_status st = AMRMHD_OK;
-  cudaError_t e0 = cudaMalloc((void**)&dev, img.size());
+  cudaError_t e0 = cudaMallocAsync((void**)&dev, img.size(), S->stream);
   if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(dev, img.data(), img.size(), cudaMemcpyHostToDevice, S->stream);
   if (e0 != cudaSuccess) {
-    if (dev) cudaFree(dev);
+    if (dev) cudaFreeAsync(dev, S->stream);
     return fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer lists: ") + cudaGetErrorString(e0));
   }
   int *dcb = (int*)(dev + ocb), *dcc = (int*)(dev + occ), *dfb = (int*)(dev + ofb), *dfc = (int*)(dev + ofc),
@@ -199,7 +199,7 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf, lo
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer: ") + cudaGetErrorString(e));
   }
-  cudaFree(dev);
+  cudaFreeAsync(dev, S->stream);
   return st;
 }
 
