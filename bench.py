@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--n", type=int, default=128)
     p.add_argument("--psize", type=int, default=16)
     p.add_argument("--skip-extras", action="store_true", help="headline only (no FP64/baseline/e2e/oracle legs)")
-    p.add_argument("--leg", default=None, choices=["adjoint", "deep", "shockclump", "error", "cylinder", "weakscale"],
+    p.add_argument("--leg", default=None,
+                   choices=["adjoint", "deep", "shockclump", "error", "cylinder", "weakscale", "queue"],
                    help="run one extra leg alone and print its JSON (for profiling)")
     p.add_argument("--leg-steps", type=int, default=None, help="coarse steps of the --leg run")
     return p.parse_args()
@@ -246,6 +247,37 @@ def e2e_run(pb, precision, k):
     del dev
     torch.cuda.empty_cache()
     return cells * k / t, nbytes, link
+
+
+def queue_leg(steps=2, theta=0.1):
+    """The deep clump hierarchy after one regrid, advanced through the device
+    work queue with the coarser levels' tiles shared out by predicted work
+    (balance 1) and in equal counts (balance 0): `steps` coarse steps each,
+    CUDA events on the stream (the leg the idle-SM capture of the queue
+    kernel runs)."""
+    import torch
+    from paper_1110_1616_gb300 import amrmhd as A
+    from paper_1110_1616_gb300 import inputs
+    pb = inputs.clumps_3d()
+    stream = torch.cuda.Stream()
+    ctx = A.Context(A.make_config(3, pb.base, precision=A.MIXED, gamma=pb.gamma, cfl=pb.cfl), stream.cuda_stream)
+    ctx.set_hierarchy(pb.patches)
+    ctx.alloc_arena()
+    torch.cuda.synchronize()
+    for f, a in enumerate(inputs.packed_clumps(pb)):
+        ctx.set_field_packed(f, a)
+    ctx.regrid(theta, pb.nlev)
+    ctx.set_option(A.OPT_QUEUE, 1)
+    out = {}
+    for bal in (1, 0):
+        ctx.set_option(A.OPT_QUEUE_BALANCE, bal)
+        ctx.step(1, want_dt=False)
+        ms, _ = timed_steps(ctx, stream, steps)
+        out["balance_%d_ms_per_step" % bal] = ms / steps
+    out["patches"] = ctx.query(A.Q_NPATCH)
+    del ctx
+    torch.cuda.empty_cache()
+    return out
 
 
 def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
@@ -614,7 +646,8 @@ def main():
         if args.leg == "adjoint" and args.leg_steps is not None:
             kw["ckpt"] = max(1, args.leg_steps // 2)
         fn = {"adjoint": adjoint_leg, "deep": deep_amr_leg, "shockclump": shock_clump_leg,
-              "error": mixed_error_leg, "cylinder": cylinder_leg, "weakscale": weak_scale_leg}[args.leg]
+              "error": mixed_error_leg, "cylinder": cylinder_leg, "weakscale": weak_scale_leg,
+              "queue": queue_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(**kw) if args.leg != "error" else fn()}), flush=True)
         return

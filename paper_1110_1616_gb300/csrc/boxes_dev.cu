@@ -26,6 +26,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -464,6 +467,30 @@ __device__ __forceinline__ void for_box(const int* lo, const int* hi, F&& f) {
   }
 }
 
+// f(x) for every position of the box [lo, hi) outside the patch's own
+// positions: the box minus the own box, as at most 6 disjoint slabs (z, then
+// y, then x)
+template <class F>
+__device__ __forceinline__ void for_shell(const BPatch& P, int d, int dim, const int* lo, const int* hi, F&& f) {
+  int l[3] = {lo[0], lo[1], lo[2]}, h[3] = {hi[0], hi[1], hi[2]};
+  for (int e = dim - 1; e >= 0; --e) {
+    const int o0 = 4, o1 = P.n[e] + 4 + (e == d ? 1 : 0);
+    if (l[e] < o0) {
+      int sl[3] = {l[0], l[1], l[2]}, sh[3] = {h[0], h[1], h[2]};
+      sh[e] = min(h[e], o0);
+      if (sh[e] > sl[e]) for_box(sl, sh, f);
+    }
+    if (h[e] > o1) {
+      int sl[3] = {l[0], l[1], l[2]}, sh[3] = {h[0], h[1], h[2]};
+      sl[e] = max(l[e], o1);
+      if (sh[e] > sl[e]) for_box(sl, sh, f);
+    }
+    l[e] = max(l[e], o0);
+    h[e] = min(h[e], o1);
+    if (h[e] <= l[e]) return;
+  }
+}
+
 // Ghost labels of task T into the shared-memory grid G by scattering the
 // entries' boxes in the host builder's order (the labels of ghost_label)
 template <class ET>
@@ -489,8 +516,7 @@ __device__ void ghost_scatter(const BArgs& a, int ti, ET* G) {
       dl[e] = P.lo[e] - Q.lo[e] - o;
     }
     if (clip_box(T, lo, hi))
-      for_box(lo, hi, [&](const int* x) {
-        if (own_pos(P, d, dim, x)) return;
+      for_shell(P, d, dim, lo, hi, [&](const int* x) {
         const int t = at(x);
         const int cur = G[t];
         bool take = d < 0 || cur < 0;
@@ -520,8 +546,7 @@ __device__ void ghost_scatter(const BArgs& a, int ti, ET* G) {
       hi[e] = 2 * (C.lo[e] + C.n[e]) + top - aux - T.g0[e];
     }
     if (clip_box(T, lo, hi))
-      for_box(lo, hi, [&](const int* x) {
-        if (own_pos(P, d, dim, x)) return;
+      for_shell(P, d, dim, lo, hi, [&](const int* x) {
         const int t = at(x);
         if (G[t] < 0) G[t] = (ET)(ns + (j - T.p0));
       });
@@ -529,8 +554,7 @@ __device__ void ghost_scatter(const BArgs& a, int ti, ET* G) {
   }
   // outside a bounded side: the boundary state; every other ghost position must have a source
   const int lo[3] = {0, 0, 0}, hi[3] = {T.ex[0], T.ex[1], T.ex[2]};
-  for_box(lo, hi, [&](const int* x) {
-    if (own_pos(P, d, dim, x)) return;
+  for_shell(P, d, dim, lo, hi, [&](const int* x) {
     const int t = at(x);
     if (T.touches) {
       const int g[3] = {T.g0[0] + x[0], T.g0[1] + x[1], T.g0[2] + x[2]};
@@ -592,6 +616,83 @@ __device__ void transfer_fill(const BArgs& a, int ti, ET* G, ET* W) {
 
 constexpr int kBoxThreads = 256;
 
+// The same greedy merge by the whole CTA (the grid in shared memory): the next
+// unmerged position, the x run, the rows and the slabs are each found by all
+// threads at once (the smallest failing index by a shared atomic minimum), so
+// the critical path is a few barriers per box rather than one warp step per
+// row or 32 positions.
+template <int MODE, class GT>
+__device__ void block_merge(const BArgs& a, int ti, GT* G) {
+  __shared__ int sh[4];
+  const BTask& T = a.T[ti];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int e0 = T.ex[0], e1 = T.ex[1], e2 = T.ex[2];
+  const int tot = e0 * e1 * e2;
+  auto at = [&](int x, int y, int z) { return (z * e1 + y) * e0 + x; };
+  const long long base = MODE == 1 ? a.first[ti] : 0;
+  int* out = MODE == 2 ? a.scratch + 13LL * ti * a.cap : (T.d < 0 ? a.out_cells : a.out_faces);
+  const int big = 0x7fffffff;
+  int pos = 0;
+  long long count = 0;
+  for (;;) {
+    int t0 = -1;
+    while (pos < tot) {
+      if (tid == 0) sh[0] = big;
+      __syncthreads();
+      const int idx = pos + tid;
+      if (idx < tot && G[idx] >= 0) atomicMin(&sh[0], idx);
+      __syncthreads();
+      const int m = sh[0];
+      __syncthreads();
+      if (m != big) { t0 = m; break; }
+      pos += nth;
+    }
+    if (t0 < 0) break;
+    const int k = G[t0];
+    const int r0 = t0 / e0, a0 = t0 - r0 * e0, b0 = r0 % e1, c0 = r0 / e1;
+    if (tid == 0) { sh[1] = e0; sh[2] = e1; sh[3] = e2; }
+    __syncthreads();
+    for (int x = a0 + 1 + tid; x < e0; x += nth)
+      if (G[at(x, b0, c0)] != k) atomicMin(&sh[1], x);
+    __syncthreads();
+    const int nx = sh[1] - a0;
+    for (int y = b0 + 1 + tid; y < e1; y += nth) {
+      bool ok = true;
+      for (int i = 0; i < nx && ok; ++i) ok = G[at(a0 + i, y, c0)] == k;
+      if (!ok) atomicMin(&sh[2], y);
+    }
+    __syncthreads();
+    const int ny = sh[2] - b0;
+    for (int z = c0 + 1 + (tid / 32); z < e2; z += nth / 32) {  // a warp per slab
+      bool ok = true;
+      for (int p = tid & 31; p < nx * ny && ok; p += 32) ok = G[at(a0 + p % nx, b0 + p / nx, z)] == k;
+      if (!__all_sync(0xffffffffu, ok) && (tid & 31) == 0) atomicMin(&sh[3], z);
+    }
+    __syncthreads();
+    const int nz = sh[3] - c0;
+    for (int p = tid; p < nx * ny * nz; p += nth) {
+      const int x = p % nx, yz = p / nx;
+      G[at(a0 + x, b0 + yz % ny, c0 + yz / ny)] = -2;
+    }
+    if (MODE != 0 && tid == 0 && (MODE == 1 || count < a.cap)) {
+      int* r = out + 13 * (base + count);
+      const int o = T.transfer ? 4 : 0;  // transfer boxes: lo in the patch's ghosted frame
+      if (T.transfer) transfer_row(a, T, k, r);
+      else ghost_row(a, T, k, r);
+      r[4] = a0 + o;
+      r[5] = b0 + o;
+      r[6] = a.dim == 3 ? c0 + o : c0;
+      r[7] = nx;
+      r[8] = ny;
+      r[9] = nz;
+    }
+    __syncthreads();
+    ++count;
+    pos = t0 + 1;
+  }
+  if (MODE != 1 && tid == 0) a.cnt[ti] = count;
+}
+
 // one task per CTA, its label grid (ids of type ET) in shared memory (transfer
 // tasks: followed by the owner grid)
 template <class ET, int MODE>
@@ -607,7 +708,7 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_tasks_smem(BArgs a, const i
   } else {
     ghost_scatter(a, ti, sg);
   }
-  if (threadIdx.x < 32) warp_merge<MODE>(a, ti, sg);
+  block_merge<MODE>(a, ti, sg);
 }
 
 // the one-pass rows of every task to their places in the cell and face lists
@@ -844,6 +945,17 @@ namespace amrapi {
 
 namespace {
 
+long long box_now_us() {
+  return std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// AMRMHD_REGRID_TRACE set in the environment: the builder's phases on stderr
+bool box_trace() {
+  static const bool on = std::getenv("AMRMHD_REGRID_TRACE") != nullptr;
+  return on;
+}
+
 constexpr size_t kBoxSmem = 200 * 1024;  // label grid bytes of a task labelled in shared memory
 
 // Runs box tasks (ghost or transfer) on the device and returns the boxes of the
@@ -861,6 +973,7 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   *bad = -1;
   const int nt = (int)T.size();
   if (!nt) return AMRMHD_OK;
+  const long long tt0 = box_now_us();
   // tasks labelled in shared memory with 8-bit ids, with 16-bit ids, and the
   // large ones in global memory
   std::vector<int> s8, s16, large;
@@ -978,7 +1091,15 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
     ctx->launches += (s8.empty() ? 0 : 1) + (s16.empty() ? 0 : 1) + (large.empty() ? 0 : 2);
   };
   // one pass: count every task's boxes and keep up to cap of them
+  const long long tt1 = box_now_us();
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (box_trace()) {
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    cudaEventRecord(ev[0], st);
+  }
   launch(std::integral_constant<int, 2>());
+  if (box_trace()) cudaEventRecord(ev[1], st);
   if (closure && mtot) {
     k_closure_mask<<<dim3(8, (unsigned)ctask.size()), 256, 0, st>>>(a, (const int*)(dev + oCT),
                                                                    (const long long*)(dev + oMO), (int)ctask.size(),
@@ -996,6 +1117,7 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
     *closure_off = moff;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const long long tt2 = box_now_us();
   if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + " (count): " + cudaGetErrorString(e));
   if (err != ~0ull) {
     *bad = (long long)err;
@@ -1030,6 +1152,16 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   if (e == cudaSuccess && nf) e = cudaMemcpyAsync(faces.data(), a.out_faces, sizeof(int) * 13 * nf, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return done(AMRMHD_ECUDA, std::string(what) + " (emit): " + cudaGetErrorString(e));
+  if (box_trace()) {
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    std::fprintf(stderr, "amrmhd %s: %d tasks (%zu + %zu in shared memory, %zu global): host tables %lld us, "
+                 "label and merge to sync %lld us (kernels %.0f us), placement to sync %lld us, %lld + %lld boxes\n",
+                 what, nt, s8.size(), s16.size(), large.size(), tt1 - tt0, tt2 - tt1, 1e3 * kms, box_now_us() - tt2,
+                 nc, nf);
+  }
   return done(AMRMHD_OK, "");
 }
 

@@ -9,6 +9,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -20,6 +22,12 @@
 using namespace amrapi;
 
 namespace {
+
+// AMRMHD_REGRID_TRACE set in the environment: per-stage host timings on stderr
+bool trace() {
+  static const bool on = std::getenv("AMRMHD_REGRID_TRACE") != nullptr;
+  return on;
+}
 
 long long now_us() {
   return std::chrono::duration_cast<std::chrono::microseconds>(
@@ -86,13 +94,20 @@ amrmhd_status make_stage(amrmhd_ctx* ctx, const std::vector<amrmhd_patch>& ps, i
     return fail(ctx, st, "regrid: new hierarchy rejected: " + m);
   }
   void* mem = nullptr;
+  const long long t1 = now_us();
   cudaError_t e = cudaMalloc(&mem, std::max<size_t>(bytes, 256));
   if (e != cudaSuccess) {
     amrmhd_destroy(c);
     return fail(ctx, AMRMHD_ENOMEM, std::string("regrid: arena: ") + cudaGetErrorString(e));
   }
+  const long long t2 = now_us();
   st = amrmhd_bind_arena(c, mem, bytes);
   c->dev_allocs.push_back(mem);
+  if (trace())
+    std::fprintf(stderr, "amrmhd regrid stage (%zu patches, ghosts from level %d): set_hierarchy %lld us (host %lld, "
+                 "ghost boxes %lld, register maps %lld), arena %.1f MB %lld us, bind %lld us\n",
+                 ps.size(), ghost_from, t1 - t0, c->maps_us[0], c->maps_us[1], c->maps_us[2], bytes / 1e6, t2 - t1,
+                 now_us() - t2);
   if (st) {
     std::string m = c->err;
     amrmhd_destroy(c);
@@ -137,6 +152,7 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf, lo
       boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
     }
   }
+  const long long t1 = now_us();
   for (int k = 0; k < 2; ++k) {
     const std::vector<int32_t>& boxes = k ? fb : cb;
     std::vector<int32_t>& ch = k ? fc : cc;
@@ -200,6 +216,10 @@ amrmhd_status transfer(amrmhd_ctx* ctx, amrmhd_ctx* S, amrmhd_ctx* O, int lf, lo
     if (e != cudaSuccess) st = fail(ctx, AMRMHD_ECUDA, std::string("regrid: transfer: ") + cudaGetErrorString(e));
   }
   cudaFreeAsync(dev, S->stream);
+  if (trace())
+    std::fprintf(stderr, "amrmhd regrid transfer level %d: maps %lld us (%zu cell, %zu face boxes, %zu closure rows), "
+                 "lists, kernels and sync %lld us\n", lf, t1 - t0, cb.size() / amrmhd::GHOST_BOX_W,
+                 fb.size() / amrmhd::GHOST_BOX_W, m.closure.size() / 2, now_us() - t1);
   return st;
 }
 
@@ -230,6 +250,8 @@ amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels) {
     if (ctx->opt_device_cluster) {
       amrmhd_status s = cluster_level_device(ctx, c, l, theta, boxes);
       us[1] += now_us() - t;
+      if (trace())
+        std::fprintf(stderr, "amrmhd regrid cluster level %d: %lld us, %zu boxes\n", l, now_us() - t, boxes.size());
       return s;
     }
     std::vector<int32_t> flags;

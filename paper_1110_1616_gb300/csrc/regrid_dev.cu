@@ -11,6 +11,9 @@
 // gives for the same flags.
 #include <cuda_runtime.h>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -26,23 +29,28 @@ struct Frame {
   int N[3];  // the level's extent
 };
 
-// dst = src dilated by 2 cells along dimension d (wrapping if wrap)
+// dst = src dilated by 2 cells along dimension d (wrapping if wrap): one
+// block per row of the frame (y, z), threads along x
 __global__ void k_dilate(const unsigned char* src, unsigned char* dst, Frame f, int d, int wrap) {
-  const long long ncell = (long long)f.n[0] * f.n[1] * f.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncell) return;
-  int c[3] = {(int)(t % f.n[0]), (int)((t / f.n[0]) % f.n[1]), (int)(t / ((long long)f.n[0] * f.n[1]))};
-  const long long st = d == 0 ? 1 : (d == 1 ? (long long)f.n[0] : (long long)f.n[0] * f.n[1]);
-  const long long base = t - (long long)c[d] * st;
-  const int n = f.n[d];
-  unsigned char v = 0;
-  for (int o = -2; o <= 2; ++o) {
-    int y = c[d] + o;
-    if (wrap) y = (y % n + n) % n;
-    else if (y < 0 || y >= n) continue;
-    v |= src[base + (long long)y * st];
+  const int row = blockIdx.x;
+  const int y = row % f.n[1], z = row / f.n[1];
+  const long long rbase = (long long)row * f.n[0];
+  const long long sx = (long long)f.n[0], sxy = (long long)f.n[0] * f.n[1];
+  for (int x = threadIdx.x; x < f.n[0]; x += blockDim.x) {
+    const int c[3] = {x, y, z};
+    const long long st = d == 0 ? 1 : (d == 1 ? sx : sxy);
+    const long long t = rbase + x;
+    const long long base = t - (long long)c[d] * st;
+    const int n = f.n[d];
+    unsigned char v = 0;
+    for (int o = -2; o <= 2; ++o) {
+      int q = c[d] + o;
+      if (wrap) q = q < 0 ? q + n : (q >= n ? q - n : q);
+      else if (q < 0 || q >= n) continue;
+      v |= src[base + (long long)q * st];
+    }
+    dst[t] = v;
   }
-  dst[t] = v;
 }
 
 __global__ void k_blocks(const unsigned char* buf, const unsigned char* region, unsigned char* ok, Frame f) {
@@ -92,6 +100,7 @@ namespace amrapi {
 amrmhd_status cluster_level_device(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double theta,
                                    std::vector<std::array<int, 7>>& boxes) {
   using namespace amrcl;
+  const auto t0 = std::chrono::steady_clock::now();
   const amrmhd::Hierarchy& H = c->H;
   const amrmhd::ClusterFrame fr = amrmhd::cluster_frame(H, l);
   Frame f;
@@ -122,26 +131,54 @@ amrmhd_status cluster_level_device(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double
   unsigned char* tmp = buf + ncell;
   unsigned char* ok = tmp + ncell;
   cudaStream_t st = c->stream;
+  const bool tr = std::getenv("AMRMHD_REGRID_TRACE") != nullptr;
+  long long wait_prior = 0;
+  cudaEvent_t ev[5];
+  if (tr) {  // the work queued before (fills) first, then events between the steps
+    const auto w0 = std::chrono::steady_clock::now();
+    cudaStreamSynchronize(st);
+    wait_prior = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - w0).count();
+    for (auto& x : ev) cudaEventCreate(&x);
+    cudaEventRecord(ev[0], st);
+  }
   cudaError_t e = cudaMemsetAsync(region, 0, 2 * ncell, st);
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("regrid: ") + cudaGetErrorString(e));
   amrk::LevelArgs a = level_args(c, l, c->d_scal, 1.0, 0);
   amrk::DenseBox box;
   for (int d = 0; d < 3; ++d) { box.off[d] = f.off[d]; box.n[d] = f.n[d]; }
+  if (tr) cudaEventRecord(ev[1], st);
   c->ops->flag_dense(a, theta, region, buf, box, st);
+  if (tr) cudaEventRecord(ev[2], st);
   const int T = 256;
   unsigned char *src = buf, *dst = tmp;
   for (int d = 0; d < f.dim; ++d) {
-    k_dilate<<<(unsigned)((ncell + T - 1) / T), T, 0, st>>>(src, dst, f, d, f.full[d] && f.per[d]);
+    k_dilate<<<(unsigned)(f.n[1] * f.n[2]), T, 0, st>>>(src, dst, f, d, f.full[d] && f.per[d]);
     std::swap(src, dst);
   }
+  if (tr) cudaEventRecord(ev[3], st);
   k_blocks<<<(unsigned)((nblk + T - 1) / T), T, 0, st>>>(src, region, ok, f);
+  if (tr) cudaEventRecord(ev[4], st);
   ctx->launches += 2 + f.dim;
   std::vector<uint8_t> h(nblk + 8, 0);
+  const auto t1 = std::chrono::steady_clock::now();
   e = cudaMemcpyAsync(h.data(), ok, nblk, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, std::string("regrid: clustering: ") + cudaGetErrorString(e));
+  const auto t2 = std::chrono::steady_clock::now();
   boxes = amrmhd::merge_blocks(H, l, fr, h.data());
+  if (std::getenv("AMRMHD_REGRID_TRACE")) {
+    auto us = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return (long long)std::chrono::duration_cast<std::chrono::microseconds>(b - a).count();
+    };
+    float m[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&m[i], ev[i], ev[i + 1]);
+    for (auto& x : ev) cudaEventDestroy(x);
+    std::fprintf(stderr, "amrmhd cluster level %d: frame %d x %d x %d, prior work %lld us, enqueue %lld us, device and "
+                 "copy %lld us (memset %.0f, flag %.0f, dilate %.0f, blocks %.0f us), merge %lld us\n", l, f.n[0],
+                 f.n[1], f.n[2], wait_prior, us(t0, t1), us(t1, t2), 1e3 * m[0], 1e3 * m[1], 1e3 * m[2], 1e3 * m[3],
+                 us(t2, std::chrono::steady_clock::now()));
+  }
   return AMRMHD_OK;
 }
 
