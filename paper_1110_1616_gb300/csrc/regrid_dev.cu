@@ -30,65 +30,90 @@ struct Frame {
 };
 
 // dst = src dilated by 2 cells along dimension d (wrapping if wrap): one
-// block per row of the frame (y, z), threads along x
+// block per row of the frame (y, z), each thread 4 consecutive x (the frame's
+// x extent is a multiple of the 4-cell block)
 __global__ void k_dilate(const unsigned char* src, unsigned char* dst, Frame f, int d, int wrap) {
   const int row = blockIdx.x;
   const int y = row % f.n[1], z = row / f.n[1];
-  const long long rbase = (long long)row * f.n[0];
-  const long long sx = (long long)f.n[0], sxy = (long long)f.n[0] * f.n[1];
-  for (int x = threadIdx.x; x < f.n[0]; x += blockDim.x) {
-    const int c[3] = {x, y, z};
-    const long long st = d == 0 ? 1 : (d == 1 ? sx : sxy);
-    const long long t = rbase + x;
-    const long long base = t - (long long)c[d] * st;
-    const int n = f.n[d];
-    unsigned char v = 0;
-    for (int o = -2; o <= 2; ++o) {
-      int q = c[d] + o;
-      if (wrap) q = q < 0 ? q + n : (q >= n ? q - n : q);
-      else if (q < 0 || q >= n) continue;
-      v |= src[base + (long long)q * st];
+  const int n0 = f.n[0];
+  const unsigned char* srow = src + (long long)row * n0;
+  unsigned char* drow = dst + (long long)row * n0;
+  for (int x = 4 * threadIdx.x; x < n0; x += 4 * blockDim.x) {
+    uchar4 v;
+    if (d == 0) {
+      unsigned char w[8];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        int q = x - 2 + o;
+        if (wrap) q = q < 0 ? q + n0 : (q >= n0 ? q - n0 : q);
+        w[o] = (q >= 0 && q < n0) ? srow[q] : 0;
+      }
+      v.x = w[0] | w[1] | w[2] | w[3] | w[4];
+      v.y = w[1] | w[2] | w[3] | w[4] | w[5];
+      v.z = w[2] | w[3] | w[4] | w[5] | w[6];
+      v.w = w[3] | w[4] | w[5] | w[6] | w[7];
+    } else {
+      const int c = d == 1 ? y : z, n = f.n[d];
+      const long long st = d == 1 ? (long long)n0 : (long long)n0 * f.n[1];
+      unsigned int acc = 0;
+      for (int o = -2; o <= 2; ++o) {
+        int q = c + o;
+        if (wrap) q = q < 0 ? q + n : (q >= n ? q - n : q);
+        else if (q < 0 || q >= n) continue;
+        acc |= *(const unsigned int*)(srow + (long long)(q - c) * st + x);
+      }
+      v = *(const uchar4*)&acc;
     }
-    dst[t] = v;
+    *(uchar4*)(drow + x) = v;
   }
 }
 
+// one warp per 4^dim block: the block holds a buffered flag inside the region
+// (want) and every cell within 3 of it lies in the region (proper nesting)
 __global__ void k_blocks(const unsigned char* buf, const unsigned char* region, unsigned char* ok, Frame f) {
   const long long nblk = (long long)f.nb[0] * f.nb[1] * f.nb[2];
-  const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nblk) return;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nblk) return;  // the whole warp
   const int a = (int)(w % f.nb[0]), b = (int)((w / f.nb[0]) % f.nb[1]), c = (int)(w / ((long long)f.nb[0] * f.nb[1]));
   const int kz = f.dim == 3 ? 1 : 0;
   const int lo[3] = {4 * a, 4 * b, f.dim == 3 ? 4 * c : 0};
-  const int hi[3] = {lo[0] + 4, lo[1] + 4, f.dim == 3 ? lo[2] + 4 : 1};
   auto at = [&](int i, int j, int k) { return ((long long)k * f.n[1] + j) * f.n[0] + i; };
+  // want: 64 cells (16 in 2D), two per lane
   bool want = false;
-  for (int k = lo[2]; k < hi[2] && !want; ++k)
-    for (int j = lo[1]; j < hi[1] && !want; ++j)
-      for (int i = lo[0]; i < hi[0] && !want; ++i) {
-        const long long x = at(i, j, k);
-        want = (buf[x] & region[x]) != 0;
-      }
-  bool allowed = want;
-  for (int k = lo[2] - 3 * kz; k < hi[2] + 3 * kz && allowed; ++k)
-    for (int j = lo[1] - 3; j < hi[1] + 3 && allowed; ++j)
-      for (int i = lo[0] - 3; i < hi[0] + 3 && allowed; ++i) {
-        int p[3] = {i, j, k};
-        bool in_box = true, inside = true;
-        for (int d = 0; d < f.dim && inside; ++d) {
-          if (f.full[d]) {
-            if (f.per[d]) p[d] = (p[d] % f.N[d] + f.N[d]) % f.N[d];
-            else if (p[d] < 0 || p[d] >= f.n[d]) inside = false;
-          } else {
-            const int g = p[d] + f.off[d];
-            if (!f.per[d] && (g < 0 || g >= f.N[d])) inside = false;
-            else if (p[d] < 0 || p[d] >= f.n[d]) in_box = false;
-          }
-        }
-        if (!inside) continue;
-        if (!in_box || !region[at(p[0], p[1], p[2])]) allowed = false;
-      }
-  ok[w] = allowed ? 1 : 0;
+  const int ncell = f.dim == 3 ? 64 : 16;
+  for (int p = lane; p < ncell; p += 32) {
+    const long long x = at(lo[0] + (p & 3), lo[1] + ((p >> 2) & 3), lo[2] + (p >> 4));
+    want = want || (buf[x] & region[x]) != 0;
+  }
+  if (!__any_sync(0xffffffffu, want)) {
+    if (lane == 0) ok[w] = 0;
+    return;
+  }
+  // the surroundings: per dimension the 10 coordinates (wrapped where the frame
+  // spans a periodic dimension), -1 outside a bounded side (skipped), -2
+  // outside the frame's box (not in the region)
+  const int ext = 10;
+  auto coord = [&](int e, int i) {
+    int q = lo[e] - 3 + i;
+    if (f.full[e]) {
+      if (f.per[e]) return (q % f.N[e] + f.N[e]) % f.N[e];
+      return (q < 0 || q >= f.n[e]) ? -1 : q;
+    }
+    const int g = q + f.off[e];
+    if (!f.per[e] && (g < 0 || g >= f.N[e])) return -1;
+    return (q < 0 || q >= f.n[e]) ? -2 : q;
+  };
+  const int nz = kz ? ext : 1, tot = ext * ext * nz;
+  bool allowed = true;
+  for (int p = lane; p < tot && allowed; p += 32) {
+    const int i = p % ext, j = (p / ext) % ext, k = p / (ext * ext);
+    const int x = coord(0, i), y = coord(1, j), z = kz ? coord(2, k) : 0;
+    if (x == -1 || y == -1 || z == -1) continue;
+    if (x == -2 || y == -2 || z == -2 || !region[at(x, y, z)]) allowed = false;
+  }
+  allowed = __all_sync(0xffffffffu, allowed);
+  if (lane == 0) ok[w] = allowed ? 1 : 0;
 }
 
 }  // namespace amrcl
@@ -152,11 +177,11 @@ amrmhd_status cluster_level_device(amrmhd_ctx* ctx, amrmhd_ctx* c, int l, double
   const int T = 256;
   unsigned char *src = buf, *dst = tmp;
   for (int d = 0; d < f.dim; ++d) {
-    k_dilate<<<(unsigned)(f.n[1] * f.n[2]), T, 0, st>>>(src, dst, f, d, f.full[d] && f.per[d]);
+    k_dilate<<<(unsigned)(f.n[1] * f.n[2]), 128, 0, st>>>(src, dst, f, d, f.full[d] && f.per[d]);
     std::swap(src, dst);
   }
   if (tr) cudaEventRecord(ev[3], st);
-  k_blocks<<<(unsigned)((nblk + T - 1) / T), T, 0, st>>>(src, region, ok, f);
+  k_blocks<<<(unsigned)((32 * nblk + T - 1) / T), T, 0, st>>>(src, region, ok, f);
   if (tr) cudaEventRecord(ev[4], st);
   ctx->launches += 2 + f.dim;
   std::vector<uint8_t> h(nblk + 8, 0);
