@@ -368,6 +368,11 @@ amrmhd_status amrmhd_recover_mixed(int64_t n, const float* u, const float* bl, c
  * (amrmhd_get_patches). After the call the context owns a new arena allocated
  * with cudaMalloc (a caller's arena is no longer referenced); the adjoint
  * workspace and captured graphs are released. Base sizes must be divisible by 4.
+ * Steps 1-3 run on the device by default (AMRMHD_OPT_DEVICE_CLUSTER; step 4 on
+ * the host from the block marks), the maps of the intermediate and final
+ * hierarchies and of step 5 on the device when AMRMHD_OPT_DEVICE_MAPS allows;
+ * the results do not depend on either option. With AMRMHD_REGRID_TRACE set in
+ * the environment each stage's host timings are printed to stderr.
  * Synchronises the stream. */
 amrmhd_status amrmhd_regrid(amrmhd_ctx* ctx, double theta, int32_t max_levels);
 
