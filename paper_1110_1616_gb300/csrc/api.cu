@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -910,6 +912,7 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
   ctx->d_hist = (double*)(blk + oH);
   // per-level lists: gathered into one host image (each list 256-byte aligned),
   // then one device allocation and one copy
+  const auto tb0 = std::chrono::steady_clock::now();
   ctx->lev.assign(nlev, LevelDev());
   std::vector<int32_t> pack;
   std::vector<std::pair<DevList*, size_t>> pend;  // list -> element offset in pack
@@ -1122,12 +1125,19 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     }
     if (!ok) return fail(ctx, AMRMHD_ECUDA, std::string("map upload: ") + cudaGetErrorString(e));
   }
+  const auto tb1 = std::chrono::steady_clock::now();
   if (!pack.empty()) {
     int* dlists = dbuf<int>(ctx, pack.size(), &e);
     if (e != cudaSuccess) return fail(ctx, AMRMHD_ECUDA, "cudaMalloc");
     CU(cudaMemcpy(dlists, pack.data(), sizeof(int) * pack.size(), cudaMemcpyHostToDevice));
     for (auto& pr : pend) pr.first->p = dlists + pr.second;
   }
+  if (std::getenv("AMRMHD_REGRID_TRACE"))
+    std::fprintf(stderr, "amrmhd bind: lists %lld us, upload of %.1f MB %lld us\n",
+                 (long long)std::chrono::duration_cast<std::chrono::microseconds>(tb1 - tb0).count(),
+                 4e-6 * pack.size(),
+                 (long long)std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - tb1)
+                     .count());
   for (int l = 0; l < nlev; ++l) ctx->lev[l].ids = id_lists[l].p;
   ctx->cur.assign(nlev, 0);
   ctx->start.assign(nlev, 0);
