@@ -55,7 +55,9 @@ def test_regrid_matches_oracle_fp64(case, device_cluster):
             pb.bc = (2, 1, 1, 1, 0, 0)
             pb.inflow = inputs.conserved((1.0, 1.0, 0.0, 0.0, 1.0, 2 ** 0.5, 0.0, 0.0))
     ctx = gpu_for(pb)
+    # the device path (clustering and maps on the device) and the host path
     ctx.set_option(A.OPT_DEVICE_CLUSTER, device_cluster)
+    ctx.set_option(A.OPT_DEVICE_MAPS, -1 if device_cluster else 0)
     o = oracle_for(pb)
     for rnd in range(2):
         dts = ctx.step(2)
