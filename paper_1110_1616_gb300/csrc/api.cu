@@ -482,15 +482,23 @@ amrmhd_status build_queue_plan(amrmhd_ctx* ctx) {
     if (fillq) {
       const int sF = substep_at(F, k, F);
       const bool near = F == 0 || sF == 2;
-      const std::vector<int32_t>& ch = near ? LF.h_chunks2 : LF.h_chunks;
+      const std::vector<int32_t>& c0 = near ? LF.h_chunk0_2 : LF.h_chunk0;
       const std::vector<int32_t>& dst = near ? LF.h_dst2 : LF.h_dst;
       const int64_t nsplit = near ? LF.runs2_split : LF.runs_split;
-      const int64_t nch = (int64_t)ch.size() / 4;
+      const int64_t nch = c0.empty() ? 0 : c0.back();
+      // the destination of chunk c: its record's, found by walking the
+      // records' first chunks forwards (c only grows)
+      size_t rb = 0, re = 0;
+      auto dst_of = [&](int64_t c, size_t& r) {
+        while (r + 1 < dst.size() && c0[r + 1] <= c) ++r;
+        return dst[r];
+      };
       for (int64_t c = 0; c < nch;) {
-        const int d0 = dst[ch[4 * c]];
+        const int d0 = dst_of(c, rb);
         const bool cells = c < nsplit;
         int64_t e = c + 1;
-        while (e < nch && e - c < 16 && dst[ch[4 * e]] == d0 && (e < nsplit) == cells) ++e;
+        re = rb;
+        while (e < nch && e - c < 16 && dst_of(e, re) == d0 && (e < nsplit) == cells) ++e;
         const int32_t rec[4] = {1 | (cells ? 2 : 0), (int32_t)c, (int32_t)e, d0};
         tasks.insert(tasks.end(), rec, rec + 4);
         need[(size_t)k * np + d0] += 1u;
@@ -927,6 +935,15 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     return true;
   };
   std::vector<DevList> id_lists(nlev);
+  // the ghost boxes of each level in list order (cells, then faces)
+  std::vector<std::vector<const int32_t*>> level_boxes(nlev);
+  std::vector<int64_t> level_cell_boxes(nlev, 0);
+  for (int faces = 0; faces < 2; ++faces) {
+    const std::vector<int32_t>& gb = faces ? H.ghost_box_faces : H.ghost_box_cells;
+    for (size_t r = 0; r < gb.size(); r += amrmhd::GHOST_BOX_W) level_boxes[H.p[gb[r]].level].push_back(&gb[r]);
+    if (!faces)
+      for (int l = 0; l < nlev; ++l) level_cell_boxes[l] = (int64_t)level_boxes[l].size();
+  }
   for (int l = 0; l < nlev; ++l) {
     LevelDev& L = ctx->lev[l];
     const std::vector<int>& ids = H.level_patches[l];
@@ -937,20 +954,22 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       ctx->maxn_all[d] = std::max(ctx->maxn_all[d], L.maxn[d]);
     }
     upload(ids, id_lists[l], 1);
-    // ghost fill lists of this level from the hierarchy's boxes (see LevelDev)
-    std::vector<int32_t> rr, cr, pcb, pcc, pfb, pfc, bcb, bcc, bfb, bfc;
-    std::vector<int32_t> rr2, cr2, bcb2, bcc2, bfb2, bfc2;
-    auto chunks_of = [](std::vector<int32_t>& ch, int bi, int vol) {
-      for (int c = 0; c < vol; c += amrk::FILL_CHUNK) {
-        ch.push_back(bi);
-        ch.push_back(c);
-      }
-    };
+    // ghost fill lists of this level from the hierarchy's boxes (see LevelDev),
+    // written straight into the upload image: a count pass over the level's
+    // boxes (cells, then faces), prefix sums per list, then a write pass, both
+    // over the boxes in parallel
+    enum { RR, CR, PCB, PCC, PFB, PFC, BCB, BCC, BFB, BFC, RR2, CR2, BCB2, BCC2, BFB2, BFC2, NLIST };
+    const int GW = amrmhd::GHOST_BOX_W, FW = amrk::FILL_BOX_W;
+    static const int LW[NLIST] = {amrk::FILL_BOX_W, 4, amrmhd::GHOST_BOX_W, 2, amrmhd::GHOST_BOX_W, 2,
+                                  amrmhd::GHOST_BOX_W, 2, amrmhd::GHOST_BOX_W, 2, amrk::FILL_BOX_W, 4,
+                                  amrmhd::GHOST_BOX_W, 2, amrmhd::GHOST_BOX_W, 2};
+    const std::vector<const int32_t*>& lb = level_boxes[l];
+    const int64_t nb = (int64_t)lb.size(), nbc = level_cell_boxes[l];
     // a box clipped to the ghosts within 2 cells of the interior (faces: either
     // adjacent cell within 2); false if nothing is left
     auto clip_near = [&](const int32_t* b, int32_t* o) {
       const amrmhd::HPatch& P = H.p[b[0]];
-      std::copy(b, b + amrmhd::GHOST_BOX_W, o);
+      std::copy(b, b + GW, o);
       for (int e = 0; e < H.dim; ++e) {
         const int lo = std::max(b[4 + e], 2), hi = std::min(b[4 + e] + b[7 + e], P.n[e] + 6 + (e == b[1] ? 1 : 0));
         if (hi <= lo) return false;
@@ -959,93 +978,145 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
       }
       return true;
     };
-    // a same-level box as a self-contained copy record (see k_fill_runs): element
-    // offsets of the first destination and source positions (with the face
-    // field for a face box), both patches' x/y extents and field strides, the
-    // box's nx, ny, the number of fields, cx = min(nx, 64) and the multipliers
-    // of the lane -> (x, row) and row -> (y, z) divisions; chunks (box, x0,
-    // q0, nrows) of whole rows q = y + ny z of cx positions
-    auto add_run = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch,
-                       std::vector<int32_t>& dst) {
-      // every listed box has a chunk: a range of k chunks spans at most k boxes
-      if (b[7] <= 0 || b[8] <= 0 || b[9] <= 0) return;
-      dst.push_back(b[0]);
-      const amrmhd::HPatch &D = H.p[b[0]], &S = H.p[b[3]];
-      const long long Ld = b[4] + (long long)D.ext[0] * (b[5] + (long long)D.ext[1] * b[6]);
-      const long long Ls = (b[4] + b[10]) + (long long)S.ext[0] * ((b[5] + b[11]) + (long long)S.ext[1] * (b[6] + b[12]));
-      const long long fd = ctx->fs[b[0]], fsrc = ctx->fs[b[3]];
-      const int fl = b[1] < 0 ? 0 : 5 + b[1];  // B_x, B_y, B_z are fields 5, 6, 7
-      const long long db = ctx->off[b[0]] + fl * fd + Ld, sb = ctx->off[b[3]] + fl * fsrc + Ls;
-      const int nv = b[1] >= 0 ? 1 : (H.dim == 3 ? 5 : 6);
-      const int nx = b[7], ny = b[8], nz = b[9];
-      const int cx = std::min(nx, amrk::FILL_CHUNK);
-      const uint64_t two31 = 1ull << 31;
-      const uint32_t mcx = (uint32_t)((two31 + cx - 1) / cx), mny = (uint32_t)((two31 + ny - 1) / ny);
-      const int bi = (int)(boxes.size() / amrk::FILL_BOX_W);
-      const int32_t rec[amrk::FILL_BOX_W] = {(int32_t)(db & 0xffffffffLL), (int32_t)(db >> 32),
-                                             (int32_t)(sb & 0xffffffffLL), (int32_t)(sb >> 32),
-                                             D.ext[0], D.ext[1], S.ext[0], S.ext[1],
-                                             (int32_t)fd, (int32_t)fsrc, nx, ny,
-                                             nv, cx, (int32_t)mcx, (int32_t)mny};
-      boxes.insert(boxes.end(), rec, rec + amrk::FILL_BOX_W);
-      const int rows = ny * nz, per = amrk::FILL_CHUNK / cx;
-      for (int q0 = 0; q0 < rows; q0 += per)
-        for (int x0 = 0; x0 < nx; x0 += cx) {
-          ch.push_back(bi);
-          ch.push_back(x0);
-          ch.push_back(q0);
-          ch.push_back(std::min(per, rows - q0));
+    // the ints box b adds to each list (count), or writes them at cur[] (write)
+    auto proc = [&](const int32_t* b, bool faces, bool write, int64_t* cur, int32_t* pk, const int64_t* base) {
+      // a same-level box as a self-contained copy record (see k_fill_runs):
+      // element offsets of the first destination and source positions (with
+      // the face field for a face box), both patches' x/y extents and field
+      // strides, the box's nx, ny, the number of fields, cx = min(nx, 64) and
+      // the multipliers of the lane -> (x, row) and row -> (y, z) divisions;
+      // chunks (box, x0, q0, nrows) of whole rows q = y + ny z of cx positions.
+      // Every listed box has a chunk: a range of k chunks spans at most k boxes
+      auto add_run = [&](const int32_t* r, int lr, int lc) {
+        if (r[7] <= 0 || r[8] <= 0 || r[9] <= 0) return;
+        const int nx = r[7], ny = r[8], nz = r[9];
+        const int cx = std::min(nx, amrk::FILL_CHUNK);
+        const int rows = ny * nz, per = amrk::FILL_CHUNK / cx;
+        const int64_t nch = (int64_t)((rows + per - 1) / per) * ((nx + cx - 1) / cx);
+        if (!write) {
+          cur[lr] += FW;
+          cur[lc] += 4 * nch;
+          return;
         }
-    };
-    auto add_box = [&](const int32_t* b, std::vector<int32_t>& boxes, std::vector<int32_t>& ch) {
-      const int bi = (int)(boxes.size() / amrmhd::GHOST_BOX_W);
-      boxes.insert(boxes.end(), b, b + amrmhd::GHOST_BOX_W);
-      chunks_of(ch, bi, b[7] * b[8] * b[9]);
-    };
-    for (int faces = 0; faces < 2; ++faces) {
-      if (faces) {
-        L.runs_split = (int64_t)cr.size() / 4;
-        L.runs2_split = (int64_t)cr2.size() / 4;
+        const amrmhd::HPatch &D = H.p[r[0]], &S = H.p[r[3]];
+        const long long Ld = r[4] + (long long)D.ext[0] * (r[5] + (long long)D.ext[1] * r[6]);
+        const long long Ls = (r[4] + r[10]) + (long long)S.ext[0] * ((r[5] + r[11]) + (long long)S.ext[1] * (r[6] + r[12]));
+        const long long fd = ctx->fs[r[0]], fsrc = ctx->fs[r[3]];
+        const int fl = r[1] < 0 ? 0 : 5 + r[1];  // B_x, B_y, B_z are fields 5, 6, 7
+        const long long db = ctx->off[r[0]] + fl * fd + Ld, sb = ctx->off[r[3]] + fl * fsrc + Ls;
+        const int nv = r[1] >= 0 ? 1 : (H.dim == 3 ? 5 : 6);
+        const uint64_t two31 = 1ull << 31;
+        const uint32_t mcx = (uint32_t)((two31 + cx - 1) / cx), mny = (uint32_t)((two31 + ny - 1) / ny);
+        const int bi = (int)((cur[lr] - base[lr]) / FW);
+        const int32_t rec[amrk::FILL_BOX_W] = {(int32_t)(db & 0xffffffffLL), (int32_t)(db >> 32),
+                                               (int32_t)(sb & 0xffffffffLL), (int32_t)(sb >> 32),
+                                               D.ext[0], D.ext[1], S.ext[0], S.ext[1],
+                                               (int32_t)fd, (int32_t)fsrc, nx, ny,
+                                               nv, cx, (int32_t)mcx, (int32_t)mny};
+        std::copy(rec, rec + FW, pk + cur[lr]);
+        cur[lr] += FW;
+        int32_t* c = pk + cur[lc];
+        for (int q0 = 0; q0 < rows; q0 += per)
+          for (int x0 = 0; x0 < nx; x0 += cx) {
+            c[0] = bi;
+            c[1] = x0;
+            c[2] = q0;
+            c[3] = std::min(per, rows - q0);
+            c += 4;
+          }
+        cur[lc] += 4 * nch;
+      };
+      auto add_box = [&](const int32_t* r, int lr, int lc) {
+        const int vol = r[7] * r[8] * r[9];
+        const int64_t nch = (vol + amrk::FILL_CHUNK - 1) / amrk::FILL_CHUNK;
+        if (!write) {
+          cur[lr] += GW;
+          cur[lc] += 2 * nch;
+          return;
+        }
+        const int bi = (int)((cur[lr] - base[lr]) / GW);
+        std::copy(r, r + GW, pk + cur[lr]);
+        cur[lr] += GW;
+        int32_t* c = pk + cur[lc];
+        for (int k = 0; k < vol; k += amrk::FILL_CHUNK) {
+          c[0] = bi;
+          c[1] = k;
+          c += 2;
+        }
+        cur[lc] += 2 * nch;
+      };
+      int32_t nbx[amrmhd::GHOST_BOX_W];
+      const bool near = clip_near(b, nbx);
+      if (b[2] == 0) {
+        add_run(b, RR, CR);
+        if (near) add_run(nbx, RR2, CR2);
+      } else if (b[2] == 1) {
+        add_box(b, faces ? PFB : PCB, faces ? PFC : PCC);
+      } else {
+        add_box(b, faces ? BFB : BCB, faces ? BFC : BCC);
+        if (near) add_box(nbx, faces ? BFB2 : BCB2, faces ? BFC2 : BCC2);
       }
-      const std::vector<int32_t>& gb = faces ? H.ghost_box_faces : H.ghost_box_cells;
-      for (size_t r = 0; r < gb.size(); r += amrmhd::GHOST_BOX_W) {
-        const int32_t* b = &gb[r];
-        if (H.p[b[0]].level != l) continue;
-        int32_t nb[amrmhd::GHOST_BOX_W];
-        const bool near = clip_near(b, nb);
-        if (b[2] == 0) {
-          add_run(b, rr, cr, L.h_dst);
-          if (near) add_run(nb, rr2, cr2, L.h_dst2);
-        } else if (b[2] == 1) {
-          add_box(b, faces ? pfb : pcb, faces ? pfc : pcc);
-        } else {
-          add_box(b, faces ? bfb : bcb, faces ? bfc : bcc);
-          if (near) add_box(nb, faces ? bfb2 : bcb2, faces ? bfc2 : bcc2);
+    };
+    // count pass: offs[i] holds box i's ints per list, then the exclusive prefix
+    std::vector<int64_t> offs((size_t)(nb + 1) * NLIST, 0);
+#pragma omp parallel for schedule(static) if (nb > 4096)
+    for (int64_t i = 0; i < nb; ++i) proc(lb[i], i >= nbc, false, &offs[(size_t)i * NLIST], nullptr, nullptr);
+    int64_t tot[NLIST];
+    for (int k = 0; k < NLIST; ++k) {
+      int64_t acc = 0;
+      for (int64_t i = 0; i <= nb; ++i) {
+        const int64_t v = offs[(size_t)i * NLIST + k];
+        offs[(size_t)i * NLIST + k] = acc;
+        acc += v;
+      }
+      tot[k] = acc;
+    }
+    // the lists' places in the upload image (each 64-int aligned, in list order)
+    int64_t base[NLIST];
+    size_t psz = pack.size();
+    for (int k = 0; k < NLIST; ++k) {
+      psz = (psz + 63) / 64 * 64;
+      base[k] = (int64_t)psz;
+      psz += (size_t)tot[k];
+    }
+    pack.resize(psz);
+    // the host copies the queue advance needs: per copy record its destination
+    // patch and its first chunk
+    L.h_dst.assign((size_t)(tot[RR] / FW), 0);
+    L.h_dst2.assign((size_t)(tot[RR2] / FW), 0);
+    L.h_chunk0.assign((size_t)(tot[RR] / FW) + 1, (int32_t)(tot[CR] / 4));
+    L.h_chunk0_2.assign((size_t)(tot[RR2] / FW) + 1, (int32_t)(tot[CR2] / 4));
+    int32_t* pk = pack.data();
+#pragma omp parallel for schedule(static) if (nb > 4096)
+    for (int64_t i = 0; i < nb; ++i) {
+      int64_t cur[NLIST];
+      const int64_t* o = &offs[(size_t)i * NLIST];
+      for (int k = 0; k < NLIST; ++k) cur[k] = base[k] + o[k];
+      const int32_t* b = lb[i];
+      if (b[2] == 0) {
+        if (o[(size_t)NLIST + RR] > o[RR]) {  // this box has a record (every box but empty ones)
+          L.h_dst[o[RR] / FW] = b[0];
+          L.h_chunk0[o[RR] / FW] = (int32_t)(o[CR] / 4);
+        }
+        if (o[(size_t)NLIST + RR2] > o[RR2]) {
+          L.h_dst2[o[RR2] / FW] = b[0];
+          L.h_chunk0_2[o[RR2] / FW] = (int32_t)(o[CR2] / 4);
         }
       }
+      proc(b, i >= nbc, true, cur, pk, base);
     }
-    // k_fill_runs stages a block's chunk and box records in shared memory and
-    // relies on k chunks spanning at most k boxes: every box listed once, in
-    // order, each followed by its own chunks
-    for (const std::vector<int32_t>* chl : {&cr, &cr2}) {
-      int32_t prev = -1;
-      for (size_t i = 0; i < chl->size(); i += 4) {
-        const int32_t b = (*chl)[i];
-        if (b != prev && b != prev + 1) return fail(ctx, AMRMHD_EINVAL, "internal: same-level fill list out of order");
-        prev = b;
-      }
+    L.runs_split = offs[(size_t)nbc * NLIST + CR] / 4;
+    L.runs2_split = offs[(size_t)nbc * NLIST + CR2] / 4;
+    L.has_bc = tot[BCB] + tot[BFB] > 0;
+    DevList* outs[NLIST] = {&L.runs, &L.chunk_runs, &L.prol_cells, &L.chunk_pcells, &L.prol_faces, &L.chunk_pfaces,
+                            &L.bc_cells, &L.chunk_bcells, &L.bc_faces, &L.chunk_bfaces, &L.runs2, &L.chunk_runs2,
+                            &L.bc_cells2, &L.chunk_bcells2, &L.bc_faces2, &L.chunk_bfaces2};
+    for (int k = 0; k < NLIST; ++k) {
+      outs[k]->n = tot[k] / LW[k];
+      outs[k]->p = nullptr;
+      if (tot[k]) pend.push_back({outs[k], (size_t)base[k]});
     }
-    L.h_chunks = cr;
-    L.h_chunks2 = cr2;
-    L.has_bc = !bcb.empty() || !bfb.empty();
-    const int GW = amrmhd::GHOST_BOX_W;
-    bool ok = upload(rr, L.runs, amrk::FILL_BOX_W) && upload(cr, L.chunk_runs, 4) &&
-              upload(pcb, L.prol_cells, GW) && upload(pcc, L.chunk_pcells, 2) &&
-              upload(pfb, L.prol_faces, GW) && upload(pfc, L.chunk_pfaces, 2) && upload(bcb, L.bc_cells, GW) &&
-              upload(bcc, L.chunk_bcells, 2) && upload(bfb, L.bc_faces, GW) && upload(bfc, L.chunk_bfaces, 2);
-    ok = ok && upload(rr2, L.runs2, amrk::FILL_BOX_W) && upload(cr2, L.chunk_runs2, 4) &&
-         upload(bcb2, L.bc_cells2, GW) && upload(bcc2, L.chunk_bcells2, 2) &&
-         upload(bfb2, L.bc_faces2, GW) && upload(bfc2, L.chunk_bfaces2, 2);
+    bool ok = true;
     if (l > 0 && ok) {
       auto slice = [&](const std::vector<int32_t>& v, const std::array<int64_t, 2>& r, int w) {
         return std::vector<int32_t>(v.begin() + r[0] * w, v.begin() + r[1] * w);

@@ -45,11 +45,11 @@ struct LevelDev {
   // fill is skipped
   DevList nbr;
   bool direct_halo = false;
-  // host copies for the queue advance's fill tasks: the chunk lists of the
-  // same-level boxes (4 ints per chunk; full and 2-cells-deep) and each box's
-  // destination patch; has_bc: the level has physical-boundary boxes (filled
-  // after its same-level copies, so its fill stays outside the queue)
-  std::vector<int32_t> h_chunks, h_chunks2, h_dst, h_dst2;
+  // host copies for the queue advance's fill tasks: per same-level copy record
+  // (full and 2-cells-deep) its destination patch and its first chunk (one
+  // more entry: the chunk count); has_bc: the level has physical-boundary boxes
+  // (filled after its same-level copies, so its fill stays outside the queue)
+  std::vector<int32_t> h_dst, h_dst2, h_chunk0, h_chunk0_2;
   bool has_bc = false;
 };
 

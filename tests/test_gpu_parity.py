@@ -266,6 +266,32 @@ def test_blast3d_full_size_sampled(precision):
             assert abs(gv - ov) <= tol * (abs(ov) + 1e-30) + (0 if precision == A.FP64 else 1e-6), (i, j, k, f, gv, ov)
 
 
+def test_blast3d_full_size_invariants():
+    """Config-2 size in the benchmark's launch configuration (mixed precision,
+    fused advance reading its halo from the neighbour patches, one graph per
+    coarse step), 10 coarse steps: every stored value finite, mass, momentum
+    and energy conserved on the periodic domain to FP32 round-off, and div B
+    of every cell at round-off (properties that hold at any size; the sampled
+    test above compares values with the oracle)."""
+    pb = inputs.blast_3d(128, 16)
+    ctx = gpu_for(pb, A.MIXED, strict=True)
+    ctx.step(1)
+    g0 = gpu_level_arrays(ctx, pb)[0]
+    ctx.step(10)
+    g = gpu_level_arrays(ctx, pb)[0]
+    for f in range(8):
+        assert np.all(np.isfinite(g[f])), f
+    n = 128
+    for f in range(5):
+        t0, t1 = np.sum(g0[f], dtype=np.float64), np.sum(g[f], dtype=np.float64)
+        scale = np.sum(np.abs(g0[f]), dtype=np.float64) + np.sum(np.abs(g0[0]), dtype=np.float64) * 1e-3
+        assert abs(t1 - t0) <= 2e-6 * scale, (f, t0, t1)
+    bx, by, bz = g[5], g[6], g[7]  # face arrays (z, y, x+1), (z, y+1, x), (z+1, y, x)
+    d = (bx[:, :, 1:] - bx[:, :, :-1]) + (by[:, 1:, :] - by[:, :-1, :]) + (bz[1:, :, :] - bz[:-1, :, :])
+    bmax = max(np.abs(bx).max(), np.abs(by).max(), np.abs(bz).max())
+    assert np.abs(d).max() <= 1e-5 * bmax, np.abs(d).max() / bmax
+
+
 @pytest.mark.parametrize("precision", [A.FP64, A.MIXED])
 def test_fused_equals_staged_3d_amr(precision):
     """The fused 3D advance (option 3) and the staged kernels (option 2) give
