@@ -780,6 +780,12 @@ amrmhd_status amrmhd_set_hierarchy(amrmhd_ctx* ctx, const amrmhd_patch* patches,
   for (int i = 0; i < n; ++i) {
     rows[7 * i] = patches[i].level;
     for (int d = 0; d < 3; ++d) { rows[7 * i + 1 + d] = patches[i].lo[d]; rows[7 * i + 4 + d] = patches[i].hi[d]; }
+    // the fill records carry field strides (x 8 fields) in 32 bits: reject a
+    // patch over 2^28 elements per field before any map is built
+    long long e = 1;
+    for (int d = 0; d < H.dim; ++d) e *= std::max(0, patches[i].hi[d] - patches[i].lo[d]) + 9LL;
+    if (8 * ((e + 63) / 64 * 64) > INT32_MAX)
+      return fail(ctx, AMRMHD_EINVAL, "patch too large (over 2^28 elements per field)");
   }
   auto now = [] {
     return std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now().time_since_epoch())

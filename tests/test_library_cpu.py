@@ -120,6 +120,14 @@ def test_error_codes():
     with pytest.raises(A.AmrmhdError) as e:
         ctx_for(2, base, lvl0 + [(2, (40, 40, 0), (48, 48, 1))])
     assert e.value.status == A.EINVAL
+    # an empty patch list
+    with pytest.raises(A.AmrmhdError) as e:
+        A.Context(A.make_config(2, base)).set_hierarchy([])
+    assert e.value.status == A.EINVAL
+    # a patch over 2^28 elements per field (rejected before any map is built)
+    with pytest.raises(A.AmrmhdError) as e:
+        ctx_for(3, (1024, 512, 512), [(0, (0, 0, 0), (1024, 512, 512))])
+    assert e.value.status == A.EINVAL and "too large" in str(e.value)
     # calls out of order
     c = A.Context(A.make_config(2, base))
     with pytest.raises(A.AmrmhdError) as e:
