@@ -256,9 +256,10 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
  * derivative of a shared face among its copies in any way, and dL_dU0 gives
  * each copy its own partial derivative (the derivative with respect to the
  * face value is their sum).
- * The forward is run once storing a checkpoint of every level's state every
- * ckpt_every coarse steps, then each segment is recomputed storing the filled
- * state of every level sub-step, and swept backwards. Branches (minmod, HLLD
+ * The forward is run up to the last segment's start storing a checkpoint of
+ * every level's state every ckpt_every coarse steps, then each segment is
+ * recomputed storing the filled state of every level sub-step, and swept
+ * backwards (ckpt_every >= n_coarse: one segment, no separate forward pass). Branches (minmod, HLLD
  * cases, upwinding) take the forward's decisions. Adjoint accumulation is FP64;
  * the local Jacobians of the HLLD flux and the half-step predictor are
  * evaluated in the forward's compute type (FP64, or FP32 in mixed precision, on

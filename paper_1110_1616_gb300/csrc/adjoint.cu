@@ -1374,10 +1374,12 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
   if (st) return st;
   AdjWork* A = ctx->adj;
   CUA(cudaMemcpyAsync(A->d_dts, dt_seq, sizeof(double) * n_coarse, cudaMemcpyHostToDevice, ctx->stream));
-  // forward pass: checkpoints at the start of every segment
+  // forward pass: checkpoints at the start of every segment (it stops at the
+  // last segment's start: the sweep recomputes that segment from its checkpoint)
   std::vector<std::vector<int>> cur_at(nseg);
   for (int i = 0; i < n_coarse; ++i) {
     if (i % k == 0) save_ckpt(ctx, i / k, cur_at[i / k]);
+    if (i / k == nseg - 1) break;
     fwd_step(ctx, A->d_dts + i);
   }
   // seed: the adjoint of the final state

@@ -1065,14 +1065,15 @@ amrmhd_status run_box_tasks(amrmhd_ctx* ctx, cudaStream_t st, const amrmhd::Hier
   a.err = (unsigned long long*)(dev + oErr);
   a.scratch = (int*)(dev + oScr);
   a.cap = cap;
-  static bool attr = false;
-  if (!attr) {
+  // the kernels' shared-memory limit, once per process (thread-safe static initialisation)
+  static const bool attr = [] {
     for (auto f : {k_box_tasks_smem<signed char, 0>, k_box_tasks_smem<signed char, 1>, k_box_tasks_smem<signed char, 2>})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
     for (auto f : {k_box_tasks_smem<short, 0>, k_box_tasks_smem<short, 1>, k_box_tasks_smem<short, 2>})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoxSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   long long lmax = 0;
   for (int i : large) lmax = std::max(lmax, (long long)T[i].ex[0] * T[i].ex[1] * T[i].ex[2]);
   const dim3 lg((unsigned)std::min<long long>((lmax + 255) / 256, 64), (unsigned)std::min<size_t>(large.size(), 65535));
