@@ -486,7 +486,8 @@ def weak_scale_leg(steps=10, unit_sms=16):
 def adjoint_leg(steps=200, ckpt=20):
     """The adjoint workload (2D, 256^2 base in 32^2 patches + refined quadrant):
     forward amrmhd_step_dt and amrmhd_backward with checkpoints every ckpt
-    coarse steps for a fixed dt sequence, FP64 and mixed precision; the seed is
+    coarse steps for a fixed dt sequence, FP64 and mixed precision, and the
+    recorded pair (amrmhd_step_dt_ckpt, amrmhd_backward_recorded); the seed is
     the derivative of 0.5 sum (rho - rho_target)^2 over the level-0 cells with
     rho_target the final density of a second seed's forward run."""
     import torch
@@ -530,13 +531,28 @@ def adjoint_leg(steps=200, ckpt=20):
         ctx.backward(dts, g, g0, ckpt)
         t_bwd = time.perf_counter() - t0
         per = pb.cells_per_coarse_step()
+        # the recorded forward (checkpoints kept by the forward, as the autograd
+        # path runs it) and its backward without a second forward pass
+        ctx.load_packed_all(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_dt_ckpt(dts, ckpt)
+        t_fwd_rec = time.perf_counter() - t0
+        g0r = torch.empty_like(u0)
+        t0 = time.perf_counter()
+        ok = ctx.backward_recorded(g, g0r)
+        t_bwd_rec = time.perf_counter() - t0
+        assert ok
         # the configuration's control: the gradient with respect to the initial
         # velocity (rho, p and B held), from dL/dU0
         from paper_1110_1616_gb300.autograd import velocity_gradient
         gv = velocity_gradient(u0, g0, ctx.packed_size(0))
         out[name] = {"forward_cell_updates_per_s": per * steps / t_fwd, "forward_s": t_fwd, "backward_s": t_bwd,
                      "backward_over_forward": t_bwd / t_fwd, "grad_norm": float(g0.norm()),
-                     "grad_v0_norm": float(gv.norm())}
+                     "grad_v0_norm": float(gv.norm()),
+                     "recorded": {"forward_s": t_fwd_rec, "backward_s": t_bwd_rec,
+                                  "backward_over_forward": t_bwd_rec / t_fwd,
+                                  "grad_max_rel_diff": float((g0 - g0r).abs().max() / g0.abs().max())}}
         del ctx
         torch.cuda.empty_cache()
     return out

@@ -271,6 +271,22 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
 amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
                               const double* dL_dUfinal, double* dL_dU0);
 
+/* The forward of amrmhd_backward recorded: the n_coarse steps of amrmhd_step_dt
+ * storing a checkpoint of every level's state every ckpt_every coarse steps, so
+ * that amrmhd_backward_recorded can differentiate them without running the
+ * forward again (the state-changing calls of this header drop the record:
+ * stepping, advancing, refluxing, setting the state, a new hierarchy or arena,
+ * a regrid, a backward). Same errors as amrmhd_backward. Synchronises the stream. */
+amrmhd_status amrmhd_step_dt_ckpt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every);
+
+/* amrmhd_backward of the steps of the last amrmhd_step_dt_ckpt, the context
+ * still at their final state: dL_dU0 = (dU_final / dU0)^T dL_dUfinal with U0
+ * the state before those steps (layouts and conventions of amrmhd_backward); the
+ * segments are recomputed from the recorded checkpoints and swept backwards. On
+ * return the context holds U0 and the record is dropped. AMRMHD_ESTATE if no
+ * record matches the current state. Synchronises the stream. */
+amrmhd_status amrmhd_backward_recorded(amrmhd_ctx* ctx, const double* dL_dUfinal, double* dL_dU0);
+
 /* The gradient with respect to the initial velocity (the configuration's
  * control: the adjoint of the level advance gives dL/dU0; the paper has no
  * adjoint, and the chain rule here is this library's reading: rho, p and B are

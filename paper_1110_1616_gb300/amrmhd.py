@@ -81,6 +81,8 @@ def lib():
             "amrmhd_set_state_all_f32": [vp, vp, i32],
             "amrmhd_get_state_all_f32": [vp, vp, i32],
             "amrmhd_backward": [vp, i32, vp, i32, vp, vp],
+            "amrmhd_step_dt_ckpt": [vp, i32, vp, i32],
+            "amrmhd_backward_recorded": [vp, vp, vp],
             "amrmhd_regrid": [vp, dbl, i32],
             "amrmhd_autotune": [vp, i32, vp],
             "amrmhd_get_patches": [vp, vp, i32, C.POINTER(i32)],
@@ -439,6 +441,23 @@ class Context:
         self._check(lib().amrmhd_backward(self.h, len(d), d.ctypes.data_as(C.c_void_p), int(ckpt_every),
                                           C.c_void_p(g_final.data_ptr()), C.c_void_p(g0.data_ptr())), "backward")
         return g0
+
+    def step_dt_ckpt(self, dts, ckpt_every=20):
+        """step_dt recording checkpoints every ckpt_every coarse steps for
+        backward_recorded (amrmhd_step_dt_ckpt)."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(lib().amrmhd_step_dt_ckpt(self.h, len(d), d.ctypes.data_as(C.c_void_p), int(ckpt_every)),
+                    "step_dt_ckpt")
+
+    def backward_recorded(self, g_final, g0):
+        """The backward of the last step_dt_ckpt from its final state (the
+        context then holds the initial state). Returns False, doing nothing, if
+        no record matches the current state."""
+        st = lib().amrmhd_backward_recorded(self.h, C.c_void_p(g_final.data_ptr()), C.c_void_p(g0.data_ptr()))
+        if st == ESTATE:
+            return False
+        self._check(st, "backward_recorded")
+        return True
 
     def query(self, what):
         v = C.c_int64(0)

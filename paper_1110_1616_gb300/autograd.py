@@ -4,10 +4,13 @@ context as a differentiable function of the packed initial state.
     u_final = advance(ctx, u0, dts, ckpt_every)
 
 u0 and u_final are float64 CUDA tensors holding all 8 packed fields (the
-amrmhd_backward layout). The forward runs amrmhd_step_dt with the fixed dt0
-sequence dts (dt is not differentiated); the backward reloads u0 and calls
-amrmhd_backward, which recomputes the forward from checkpoints every ckpt_every
-coarse steps. Every step of both passes runs in the library's CUDA kernels.
+amrmhd_backward layout). The forward runs amrmhd_step_dt_ckpt with the fixed
+dt0 sequence dts (dt is not differentiated), keeping a checkpoint every
+ckpt_every coarse steps; the backward differentiates that recorded forward
+(amrmhd_backward_recorded: each segment recomputed from its checkpoint) while
+the context still holds its final state, else it reloads u0 and calls
+amrmhd_backward (forward pass, then the same sweep). Every step of both passes
+runs in the library's CUDA kernels.
 """
 import torch
 
@@ -24,7 +27,7 @@ class AdvanceFunction(torch.autograd.Function):
         # the library runs on its own stream: order it after torch's work and back
         torch.cuda.synchronize()
         ctx.load_packed_all(u0)
-        ctx.step_dt(dts)
+        ctx.step_dt_ckpt(dts, int(ckpt_every))
         ctx.read_packed_all(out)
         torch.cuda.synchronize()
         fctx.save_for_backward(u0)
@@ -40,8 +43,9 @@ class AdvanceFunction(torch.autograd.Function):
         g = g.contiguous().to(torch.float64)
         g0 = torch.empty_like(u0)
         torch.cuda.synchronize()
-        ctx.load_packed_all(u0)
-        ctx.backward(fctx.dts, g, g0, fctx.ckpt)
+        if not ctx.backward_recorded(g, g0):
+            ctx.load_packed_all(u0)
+            ctx.backward(fctx.dts, g, g0, fctx.ckpt)
         torch.cuda.synchronize()
         return g0, None, None, None
 

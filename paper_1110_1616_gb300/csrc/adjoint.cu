@@ -1015,6 +1015,13 @@ struct AdjWork {
   size_t step_bytes = 0;
   int rec_step = 0, rec_slot = 0;
   std::vector<void*> allocs;
+  // the record of the last amrmhd_step_dt_ckpt: its steps, dt sequence (in
+  // d_dts), checkpoints (the level buffers in use at each) and the state count
+  // after it
+  bool rec_valid = false;
+  int rec_n = 0, rec_k = 0;
+  std::vector<std::vector<int>> rec_cur;
+  unsigned long long rec_version = 0;
 };
 
 void adj_free(amrmhd_ctx* ctx) {
@@ -1339,6 +1346,7 @@ using namespace amrapi;
 extern "C" {
 
 amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
   if (n_coarse < 0 || (n_coarse > 0 && !dt_seq)) return fail(ctx, AMRMHD_EINVAL, "bad step count or dt sequence");
@@ -1356,32 +1364,17 @@ amrmhd_status amrmhd_step_dt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt
   return AMRMHD_OK;
 }
 
-amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
-                              const double* dL_dUfinal, double* dL_dU0) {
-  amrmhd_status st = check_bound(ctx);
-  if (st) return st;
-  if (n_coarse < 1 || !dt_seq || ckpt_every < 1 || !dL_dUfinal || !dL_dU0)
-    return fail(ctx, AMRMHD_EINVAL, "bad arguments");
-  for (int i = 0; i < n_coarse; ++i)
-    if (!(dt_seq[i] > 0.0)) return fail(ctx, AMRMHD_EINVAL, "dt must be positive");
-  if (ctx->floor_rho > 0.0 || ctx->floor_p > 0.0)
-    return fail(ctx, AMRMHD_ESTATE, "the adjoint does not differentiate floors: set them to 0");
-  st = adj_setup(ctx);
-  if (st) return st;
-  const int k = std::min<int>(ckpt_every, n_coarse);
-  const int nseg = (n_coarse + k - 1) / k;
-  st = adj_reserve(ctx, k, nseg, n_coarse);
-  if (st) return st;
+}  // extern "C"
+
+namespace {
+
+// The reverse sweep of amrmhd_backward over n_coarse steps of dt0 in A->d_dts,
+// from the checkpoints saved every k steps (cur_at: the level buffers in use
+// at each); leaves the context at the first checkpoint.
+amrmhd_status adj_sweep(amrmhd_ctx* ctx, int n_coarse, int k, const std::vector<std::vector<int>>& cur_at,
+                        const double* dL_dUfinal, double* dL_dU0) {
   AdjWork* A = ctx->adj;
-  CUA(cudaMemcpyAsync(A->d_dts, dt_seq, sizeof(double) * n_coarse, cudaMemcpyHostToDevice, ctx->stream));
-  // forward pass: checkpoints at the start of every segment (it stops at the
-  // last segment's start: the sweep recomputes that segment from its checkpoint)
-  std::vector<std::vector<int>> cur_at(nseg);
-  for (int i = 0; i < n_coarse; ++i) {
-    if (i % k == 0) save_ckpt(ctx, i / k, cur_at[i / k]);
-    if (i / k == nseg - 1) break;
-    fwd_step(ctx, A->d_dts + i);
-  }
+  const int nseg = (n_coarse + k - 1) / k;
   // seed: the adjoint of the final state
   const size_t se = (size_t)ctx->state_elems;
   CUA(cudaMemsetAsync(A->lam, 0, se * sizeof(double), ctx->stream));
@@ -1406,9 +1399,91 @@ amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* d
   lam_io(ctx, dL_dU0, 0);
   // leave the context at the initial state
   load_ckpt(ctx, 0, cur_at[0]);
+  ++ctx->state_version;
+  A->rec_valid = false;
   CUA(cudaStreamSynchronize(ctx->stream));
   CUA(cudaGetLastError());
   return AMRMHD_OK;
+}
+
+amrmhd_status adj_check(amrmhd_ctx* ctx, int n_coarse, const double* dt_seq, int ckpt_every) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (n_coarse < 1 || !dt_seq || ckpt_every < 1) return fail(ctx, AMRMHD_EINVAL, "bad arguments");
+  for (int i = 0; i < n_coarse; ++i)
+    if (!(dt_seq[i] > 0.0)) return fail(ctx, AMRMHD_EINVAL, "dt must be positive");
+  if (ctx->floor_rho > 0.0 || ctx->floor_p > 0.0)
+    return fail(ctx, AMRMHD_ESTATE, "the adjoint does not differentiate floors: set them to 0");
+  return AMRMHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amrmhd_status amrmhd_backward(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every,
+                              const double* dL_dUfinal, double* dL_dU0) {
+  amrmhd_status st = adj_check(ctx, n_coarse, dt_seq, ckpt_every);
+  if (st) return st;
+  if (!dL_dUfinal || !dL_dU0) return fail(ctx, AMRMHD_EINVAL, "bad arguments");
+  st = adj_setup(ctx);
+  if (st) return st;
+  const int k = std::min<int>(ckpt_every, n_coarse);
+  const int nseg = (n_coarse + k - 1) / k;
+  st = adj_reserve(ctx, k, nseg, n_coarse);
+  if (st) return st;
+  AdjWork* A = ctx->adj;
+  A->rec_valid = false;
+  CUA(cudaMemcpyAsync(A->d_dts, dt_seq, sizeof(double) * n_coarse, cudaMemcpyHostToDevice, ctx->stream));
+  // forward pass: checkpoints at the start of every segment (it stops at the
+  // last segment's start: the sweep recomputes that segment from its checkpoint)
+  std::vector<std::vector<int>> cur_at(nseg);
+  for (int i = 0; i < n_coarse; ++i) {
+    if (i % k == 0) save_ckpt(ctx, i / k, cur_at[i / k]);
+    if (i / k == nseg - 1) break;
+    fwd_step(ctx, A->d_dts + i);
+  }
+  return adj_sweep(ctx, n_coarse, k, cur_at, dL_dUfinal, dL_dU0);
+}
+
+amrmhd_status amrmhd_step_dt_ckpt(amrmhd_ctx* ctx, int32_t n_coarse, const double* dt_seq, int32_t ckpt_every) {
+  amrmhd_status st = adj_check(ctx, n_coarse, dt_seq, ckpt_every);
+  if (st) return st;
+  st = adj_setup(ctx);
+  if (st) return st;
+  const int k = std::min<int>(ckpt_every, n_coarse);
+  const int nseg = (n_coarse + k - 1) / k;
+  st = adj_reserve(ctx, k, nseg, n_coarse);
+  if (st) return st;
+  AdjWork* A = ctx->adj;
+  A->rec_valid = false;
+  CUA(cudaMemcpyAsync(A->d_dts, dt_seq, sizeof(double) * n_coarse, cudaMemcpyHostToDevice, ctx->stream));
+  A->rec_cur.assign(nseg, {});
+  for (int i = 0; i < n_coarse; ++i) {
+    if (i % k == 0) save_ckpt(ctx, i / k, A->rec_cur[i / k]);
+    fwd_step(ctx, A->d_dts + i);
+  }
+  CUA(cudaStreamSynchronize(ctx->stream));
+  CUA(cudaGetLastError());
+  ++ctx->state_version;
+  A->rec_valid = true;
+  A->rec_n = n_coarse;
+  A->rec_k = k;
+  A->rec_version = ctx->state_version;
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_backward_recorded(amrmhd_ctx* ctx, const double* dL_dUfinal, double* dL_dU0) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  if (!dL_dUfinal || !dL_dU0) return fail(ctx, AMRMHD_EINVAL, "bad arguments");
+  AdjWork* A = ctx->adj;
+  if (!A || !A->rec_valid || A->rec_version != ctx->state_version)
+    return fail(ctx, AMRMHD_ESTATE, "no recorded forward matches the current state (amrmhd_step_dt_ckpt)");
+  if (ctx->floor_rho > 0.0 || ctx->floor_p > 0.0)
+    return fail(ctx, AMRMHD_ESTATE, "the adjoint does not differentiate floors: set them to 0");
+  const std::vector<std::vector<int>> cur_at = A->rec_cur;
+  return adj_sweep(ctx, A->rec_n, A->rec_k, cur_at, dL_dUfinal, dL_dU0);
 }
 
 amrmhd_status amrmhd_local_vjp(int32_t which, int32_t dim, int64_t n, const double* x, const double* g, double gamma,

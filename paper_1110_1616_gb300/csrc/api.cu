@@ -1292,6 +1292,7 @@ static amrmhd_status io_one(amrmhd_ctx* ctx, int32_t patch, int32_t field, void*
 }
 
 amrmhd_status amrmhd_set_state(amrmhd_ctx* ctx, int32_t patch, int32_t field, const void* src, int32_t on_device) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
   return io_one(ctx, patch, field, (void*)src, on_device, 1, false);
 }
@@ -1311,6 +1312,7 @@ amrmhd_status amrmhd_packed_size(amrmhd_ctx* ctx, int32_t field, int64_t* count)
 }
 
 amrmhd_status amrmhd_set_state_packed(amrmhd_ctx* ctx, int32_t field, const double* src, int32_t on_device) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
   return io_one(ctx, 0, field, (void*)src, on_device, 1, true);
 }
@@ -1369,6 +1371,7 @@ static amrmhd_status io_all(amrmhd_ctx* ctx, void* buf, int32_t on_device, int t
 }
 
 amrmhd_status amrmhd_set_state_all(amrmhd_ctx* ctx, const double* src, int32_t on_device) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
   return io_all(ctx, (void*)src, on_device, 1, 0);
 }
@@ -1379,6 +1382,7 @@ amrmhd_status amrmhd_get_state_all(amrmhd_ctx* ctx, double* dst, int32_t on_devi
 }
 
 amrmhd_status amrmhd_set_state_all_f32(amrmhd_ctx* ctx, const float* src, int32_t on_device) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   if (!src) return fail(ctx, AMRMHD_EINVAL, "null source");
   return io_all(ctx, (void*)src, on_device, 1, 1);
 }
@@ -1424,6 +1428,7 @@ amrmhd_status amrmhd_fill_ghosts(amrmhd_ctx* ctx, int32_t level, int32_t substep
 }
 
 amrmhd_status amrmhd_advance_level(amrmhd_ctx* ctx, int32_t level, double dt, int32_t substep) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
   if (level < 0 || level >= ctx->H.nlev || (substep != 1 && substep != 2) || !(dt >= 0.0))
@@ -1438,6 +1443,7 @@ amrmhd_status amrmhd_advance_level(amrmhd_ctx* ctx, int32_t level, double dt, in
 }
 
 amrmhd_status amrmhd_reflux_restrict(amrmhd_ctx* ctx, int32_t fine_level) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
   if (fine_level < 1 || fine_level >= ctx->H.nlev) return fail(ctx, AMRMHD_EINVAL, "bad fine level");
@@ -1468,6 +1474,7 @@ amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0) {
 }
 
 amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
+  if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
   if (n_coarse < 0) return fail(ctx, AMRMHD_EINVAL, "negative step count");

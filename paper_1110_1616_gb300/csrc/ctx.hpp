@@ -169,6 +169,9 @@ struct amrmhd_ctx {
   // adjoint records the filled states there
   void (*after_fill)(amrmhd_ctx*, int, int) = nullptr;
   amrapi::AdjWork* adj = nullptr;
+  // counts the calls that change the state: a recorded forward stays valid
+  // for amrmhd_backward_recorded while the count is unchanged
+  unsigned long long state_version = 0;
 };
 
 namespace amrapi {

@@ -120,6 +120,42 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert np.abs(r - res[0]).max() <= 1e-12 * np.abs(res[0]).max()
 
 
+@pytest.mark.parametrize("name,ckpt", [("quadrant_2d", 2), ("three_level_2d", 5), ("small_3d", 1)])
+def test_recorded_backward_equals_backward(name, ckpt):
+    """amrmhd_step_dt_ckpt + amrmhd_backward_recorded (the forward's own
+    checkpoints, no second forward pass) give amrmhd_backward's gradient (to
+    the round-off of the adjoint's atomic accumulations, whose order varies
+    from run to run) and leave the initial state; a state change drops the
+    record."""
+    import torch
+    pb = PROBLEMS[name]()
+    o = oracle_for(pb)
+    dts = [o.step() for _ in range(4)]
+    ctx = gpu_ctx(pb)
+    before = ctx.read_state()
+    mask = stored_mask(ctx, pb)
+    lam = random_lam(pb, np.random.default_rng(11), mask)
+    g_ref = gpu_backward(ctx, pb, dts, lam, ckpt)
+    seed = torch.tensor(levels_to_packed_seed(ctx, pb, lam), dtype=torch.float64, device="cuda")
+    g0 = torch.empty_like(seed)
+    ctx.step_dt_ckpt(dts, ckpt)
+    assert ctx.backward_recorded(seed, g0)
+    g_rec = g0.cpu().numpy()
+    assert np.abs(g_rec - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+    after = ctx.read_state()
+    for f in range(8):
+        for p in range(len(pb.patches)):
+            assert np.array_equal(before[f][p], after[f][p])
+    # the record is used once, and any state change drops it
+    assert not ctx.backward_recorded(seed, g0)
+    ctx.step_dt_ckpt(dts, ckpt)
+    ctx.step_dt(dts[:1])
+    assert not ctx.backward_recorded(seed, g0)
+    ctx.step_dt_ckpt(dts, ckpt)
+    ctx.load_state(pb.state)
+    assert not ctx.backward_recorded(seed, g0)
+
+
 def test_backward_restores_the_initial_state():
     pb = quadrant_2d()
     ctx = gpu_ctx(pb)
