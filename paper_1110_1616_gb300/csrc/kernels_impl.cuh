@@ -889,9 +889,12 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
   int i, j, k;
   T tmax = T(0);  // per-thread maximum in the working type; the reduction is FP64
   bool bad = false;
-  // loop invariants in the working type (conversions from FP64 issue on the FP64 pipe)
+  // loop invariants in the working type (conversions and comparisons of FP64
+  // values issue on the FP64 pipe): gamma, 1/dx, gamma - 1 and the floors
   const T g = (T)a.gamma;
   const T ix[3] = {(T)a.idx[0], (T)a.idx[1], (T)a.idx[2]};
+  const double gm1 = a.gamma - 1.0;
+  const bool floors = a.fl.rho > 0.0 || a.fl.p > 0.0;
   for (int tc = blockIdx.x * TPB + threadIdx.x;; tc += gridDim.x * TPB) {
     if (!region_cell<DIM>(P, 0, tc, i, j, k)) break;
     const int L = lidx(P, i, j, k);
@@ -904,9 +907,9 @@ template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_cfl(CflArgs
     bl[1] = U[6 * fs + L]; br[1] = U[6 * fs + L + P.ext[0]];
     if (DIM == 3) { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L + P.ext[0] * P.ext[1]]; }
     else { bl[2] = U[7 * fs + L]; br[2] = U[7 * fs + L]; }
-    floor_density(u, a.fl.rho, a.fl.events);
-    recover_t(u, bl, br, a.gamma - 1.0, w);
-    floor_pressure(w, a.fl.p, a.fl.events);
+    if (floors) floor_density(u, a.fl.rho, a.fl.events);
+    recover_t(u, bl, br, gm1, w);
+    if (floors) floor_pressure(w, a.fl.p, a.fl.events);
     if (!(w[0] > T(0)) || !(w[4] > T(0))) bad = true;
     else {
       T rr = T(0);
