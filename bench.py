@@ -346,12 +346,22 @@ def deep_amr_leg(steps=20, regrid_every=2, theta=0.1):
                                    zip(("flag", "cluster", "build", "transfer", "build_maps", "transfer_maps"),
                                        breakdown)},
            "cells_per_level_final": [cells[l] for l in sorted(cells)], "patches_final": ctx.query(A.Q_NPATCH),
-           "tiles": tiles, "concurrent_levels_speedup": ms_s / ms_c,
+           "tiles": tiles, "tile_zchunk": launch_shapes(ctx), "concurrent_levels_speedup": ms_s / ms_c,
            "final_hierarchy_ms_per_step": {"side_streams": ms_c / 2, "serial": ms_s / 2, "device_queue": ms_q / 2,
                                            "device_queue_equal_shares": ms_q0 / 2},
            "workload": "clumps3d_32_6lev: 8 clumps rho 100 r 0.02, v (1,0,0), B (sqrt2,0,0); mixed precision"}
     del ctx
     torch.cuda.empty_cache()
+    return out
+
+
+def launch_shapes(ctx):
+    """Per level, the fused advance's (tile variant, z planes per CTA) of its
+    interior-only advance and of its advance with the extended ghost layers."""
+    from paper_1110_1616_gb300 import amrmhd as A
+    out = []
+    for l in range(ctx.query(A.Q_NLEVEL)):
+        out.append([list(ctx.tile_choice(l, 0)), list(ctx.tile_choice(l, 1)) if l > 0 else None])
     return out
 
 
@@ -385,6 +395,7 @@ def cylinder_leg(steps=20):
     leaf = leaf_updates(pb.patches)
     out = {"value": per * steps / (ms / 1e3), "unit": UNIT, "leaf_cell_updates_per_s": leaf * steps / (ms / 1e3),
            "ms_per_step": ms / steps, "steps": steps, "cell_updates_per_step": per, "tiles": tiles,
+           "tile_zchunk": launch_shapes(ctx),
            "workload": "cylinder3d_64_2lev: magnetized cylinder (contrast 10, r 0.1) advected by v (1, 1/2, 0), "
                        "B (sqrt2,0,0), level 1 over 12.5 % of the volume; mixed precision"}
     del ctx
@@ -433,7 +444,7 @@ def shock_clump_leg(steps=10, theta=0.1):
            "regrid_host_us": dict({k: ctx.query(A.Q_REGRID_FLAG_US + i)
                                    for i, k in enumerate(("flag", "cluster", "build", "transfer", "build_maps"))},
                                   transfer_maps=ctx.query(A.Q_REGRID_TRANSFER_MAPS_US)),
-           "tiles": tiles,
+           "tiles": tiles, "tile_zchunk": launch_shapes(ctx),
            "workload": "shock_clump3d_64_5lev: Mach-10 shock into a lognormal (sigma 1, slope -11/3, contrast 10) "
                        "clump r 0.15; B (sqrt2,0,0); inflow x-low, outflow elsewhere; mixed precision"}
     del ctx

@@ -495,15 +495,25 @@ enum {
                               steps 2-4): 1 (default) on the device (flag test, 2-cell buffer and
                               block marks in dense bytes of the clustering frame; only the block marks
                               are copied back for the greedy merge), 0 on the host (the flag list is
-                              copied back). Both give the same boxes in the same order. */
+                              copied back). Both give the same boxes in the same order. */,
+  AMRMHD_OPT_ZCHUNK = 12 /* z planes per CTA of the fused 3D advance: -1 (default) the length
+                              amrmhd_autotune chose for the level and sub-step kind (the whole column
+                              before it runs), 0 the whole column, n in 1..4096 chunks of n planes
+                              (each chunk restarts the z march 2 planes below its first plane: more
+                              CTAs with shorter marches, for levels of few or tall patches, at the cost
+                              of recomputed planes). The results are the same bit for bit for every
+                              length. May be changed between steps (it is read at the next launch or
+                              graph capture). */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 
 /* Autotuner of the fused 3D advance: for every level, and separately for its
  * interior-only advance and (above level 0) its advance with 2 extended ghost
  * layers (sub-step 1), times `trials` advances with each tile variant
- * (AMRMHD_OPT_TILE 0..4) on the current state with CUDA events and keeps the
- * fastest (used while AMRMHD_OPT_TILE is -1). The state is not changed: an
+ * (AMRMHD_OPT_TILE 0..4) and each z chunk (AMRMHD_OPT_ZCHUNK 0, 4, 8 and 16 where
+ * shorter than the level's column) on the current state with CUDA events and
+ * keeps the fastest pair (used while AMRMHD_OPT_TILE, respectively
+ * AMRMHD_OPT_ZCHUNK, is -1; amrmhd_tile_choice reads it). The state is not changed: an
  * advance reads the current buffer and writes the other one. tiles (host, may
  * be NULL) receives the interior-only choice per level (-1 where the staged
  * kernels are used, i.e. FP64 by default and 2D). The variants compute the
@@ -511,6 +521,17 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
  * FP32 rounding differences in mixed precision (where the compiler may
  * contract multiply-adds differently per variant). Synchronises the stream. */
 amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles);
+
+/* The fused 3D advance's launch shape in use for level `level`: kind 0 its
+ * interior-only advance, kind 1 its advance with 2 extended ghost layers
+ * (levels above 0). *tile (host) receives the tile variant (AMRMHD_OPT_TILE
+ * numbering; -1 where the staged kernels advance the level), *zlen (host) the z
+ * planes per CTA (0: the whole column), both after the options and the
+ * autotuner's choice. The paper is silent on launch shapes (they are this
+ * implementation's mapping of a level's grids onto the GPU). Errors:
+ * AMRMHD_ESTATE without a hierarchy; AMRMHD_EINVAL for a null pointer, a level
+ * out of range or kind not 0 or 1. */
+amrmhd_status amrmhd_tile_choice(amrmhd_ctx* ctx, int32_t level, int32_t kind, int32_t* tile, int32_t* zlen);
 
 const char* amrmhd_last_error(const amrmhd_ctx* ctx);
 

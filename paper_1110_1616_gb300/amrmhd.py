@@ -25,7 +25,7 @@ Q_REGRID_TRANSFER_MAPS_US = 12
 Q_MAPS_HOST_US, Q_MAPS_GHOST_US, Q_MAPS_REGISTERS_US = 13, 14, 15
 OPT_ADVANCE, OPT_GRAPH, OPT_TILE, OPT_CONCURRENT, OPT_HOST_IO, OPT_DIRECT_HALO = 0, 1, 2, 3, 4, 5
 OPT_QUEUE, OPT_QUEUE_TILE, OPT_QUEUE_WITHHOLD, OPT_QUEUE_BALANCE = 6, 7, 8, 9
-OPT_DEVICE_MAPS, OPT_DEVICE_CLUSTER = 10, 11
+OPT_DEVICE_MAPS, OPT_DEVICE_CLUSTER, OPT_ZCHUNK = 10, 11, 12
 
 
 class AmrmhdError(RuntimeError):
@@ -85,6 +85,7 @@ def lib():
             "amrmhd_backward_recorded": [vp, vp, vp],
             "amrmhd_regrid": [vp, dbl, i32],
             "amrmhd_autotune": [vp, i32, vp],
+            "amrmhd_tile_choice": [vp, i32, i32, C.POINTER(i32), C.POINTER(i32)],
             "amrmhd_get_patches": [vp, vp, i32, C.POINTER(i32)],
             "amrmhd_regrid_boxes": [vp, i32, vp, i64, vp, i32, C.POINTER(i32)],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
@@ -370,6 +371,14 @@ class Context:
         out = np.zeros(max(n, 1), dtype=np.int32)
         self._check(lib().amrmhd_autotune(self.h, int(trials), out.ctypes.data_as(C.c_void_p)), "autotune")
         return out[:n].tolist()
+
+    def tile_choice(self, level, kind):
+        """(tile variant, z planes per CTA) of the fused advance of a level:
+        kind 0 interior only, 1 with the extended ghost layers (see
+        amrmhd_tile_choice)."""
+        t, z = C.c_int32(0), C.c_int32(0)
+        self._check(lib().amrmhd_tile_choice(self.h, int(level), int(kind), C.byref(t), C.byref(z)), "tile_choice")
+        return t.value, z.value
 
     def regrid(self, theta, max_levels):
         """Rebuilds the levels above 0 from density-gradient flags (threshold

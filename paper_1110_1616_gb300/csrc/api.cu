@@ -53,6 +53,7 @@ void free_device(amrmhd_ctx* ctx) {
   ctx->cfl_stream = nullptr;
   ctx->ev_cfl_fork = ctx->ev_cfl_join = nullptr;
   ctx->tile_level.clear();
+  ctx->zlen_level.clear();
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
   for (void* p : ctx->dev_allocs) cudaFree(p);
@@ -91,6 +92,7 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
   }
   a.gamma = ctx->cfg.gamma;
   a.w = w;
+  a.zlen = 0;
   a.bnd = (l > 0 && ctx->bnd_elems > 0) ? (void*)(ctx->arena + ctx->o_bnd) : nullptr;
   a.nbr = nullptr;
   a.fl = ctx->floors();
@@ -216,9 +218,8 @@ void op_advance(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, int s
       ctx->ops->advance(b, ctx->stream, nl);
     }
   } else if (fused) {
-    int v = ctx->opt_tile >= 0 ? (int)ctx->opt_tile : (ctx->variant == amrk::V_MIXED ? 2 : 3);
-    if (ctx->opt_tile < 0 && (int)ctx->tile_level.size() > l && ctx->tile_level[l][w ? 1 : 0] >= 0)
-      v = ctx->tile_level[l][w ? 1 : 0];
+    const int v = ctx->tile_of(l, w ? 1 : 0);
+    a.zlen = ctx->zlen_of(l, w ? 1 : 0);
     if (w == 0 && direct_halo(ctx, l)) a.nbr = ctx->lev[l].nbr.p;
     ctx->ops->advance_fused(a, v, ctx->stream, nl);
   } else {
@@ -736,6 +737,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 4) ctx->opt_tile = value;
+  else if (option == AMRMHD_OPT_ZCHUNK && value >= -1 && value <= 4096) ctx->opt_zchunk = value;
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else if (option == AMRMHD_OPT_HOST_IO && (value == 0 || value == 1)) ctx->opt_host_io = value;
   else if (option == AMRMHD_OPT_DIRECT_HALO && (value == 0 || value == 1)) ctx->opt_direct_halo = value;
@@ -1235,6 +1237,7 @@ amrmhd_status amrmhd_bind_arena(amrmhd_ctx* ctx, void* dev_ptr, size_t bytes) {
     CU(cudaEventCreateWithFlags(&ctx->ev_cfl_join, cudaEventDisableTiming));
   }
   ctx->tile_level.assign(nlev, {-1, -1});
+  ctx->zlen_level.assign(nlev, {0, 0});
   ctx->ops->prepare();
   CU(cudaGetLastError());
   ctx->bound = true;
@@ -1558,17 +1561,25 @@ amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  const int64_t keep = ctx->opt_tile;
+  const int64_t keep = ctx->opt_tile, keepz = ctx->opt_zchunk;
   ctx->opt_tile = -1;
+  ctx->opt_zchunk = -1;
   for (int l = 0; l < nlev; ++l) {
     // sub-step 1 of a level above 0 advances 2 extended ghost layers, sub-step 2
-    // (and level 0) the interior only: each gets its own tile
+    // (and level 0) the interior only: each gets its own tile and z chunk (the
+    // whole column, or 4, 8 or 16 planes per CTA: shorter marches in more
+    // CTAs for levels of few or tall patches)
     for (int s = 1; s <= (l > 0 ? 2 : 1); ++s) {
       const int wi = (l > 0 && s == 1) ? 1 : 0;
       float best = 0.0f;
-      int bv = -1;
-      for (int v = 0; v < 5; ++v) {
+      int bv = -1, bz = 0;
+      const int ez = ctx->lev[l].maxn[2] + (wi ? 4 : 0);
+      static const int zlens[4] = {0, 4, 8, 16};
+      for (int k = 0; k < 20; ++k) {
+        const int v = k % 5, zl = zlens[k / 5];
+        if (zl > 0 && zl >= ez) continue;  // one chunk: the whole column, timed already
         ctx->tile_level[l][wi] = v;
+        ctx->zlen_level[l][wi] = zl;
         const int c0 = ctx->cur[l];
         op_advance(ctx, l, ctx->d_scal, 1.0 / (double)(1 << l), s, &nl);  // warm-up
         ctx->cur[l] = c0;
@@ -1583,18 +1594,34 @@ amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {
         if (cudaGetLastError() != cudaSuccess) continue;
         float ms = 0.0f;
         CU(cudaEventElapsedTime(&ms, e0, e1));
-        if (bv < 0 || ms < best) { best = ms; bv = v; }
+        if (bv < 0 || ms < best) { best = ms; bv = v; bz = zl; }
       }
       ctx->tile_level[l][wi] = bv;
+      ctx->zlen_level[l][wi] = bv < 0 ? 0 : bz;
       if (tiles && wi == 0) tiles[l] = bv;
     }
   }
   ctx->opt_tile = keep;
+  ctx->opt_zchunk = keepz;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (int i = 0; i < 2; ++i)
     if (ctx->gexec[i]) { cudaGraphExecDestroy(ctx->gexec[i]); ctx->gexec[i] = nullptr; }
   CU(cudaStreamSynchronize(ctx->stream));
+  return AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_tile_choice(amrmhd_ctx* ctx, int32_t level, int32_t kind, int32_t* tile, int32_t* zlen) {
+  if (!ctx || !tile || !zlen) return AMRMHD_EINVAL;
+  if (!ctx->have_h) return fail(ctx, AMRMHD_ESTATE, "no hierarchy set");
+  if (level < 0 || level >= ctx->H.nlev || (kind != 0 && kind != 1)) return fail(ctx, AMRMHD_EINVAL, "level or kind");
+  if (!ctx->fused()) {
+    *tile = -1;
+    *zlen = 0;
+  } else {
+    *tile = ctx->tile_of(level, kind);
+    *zlen = ctx->zlen_of(level, kind);
+  }
   return AMRMHD_OK;
 }
 

@@ -90,6 +90,9 @@ struct amrmhd_ctx {
   // the multi-level queue advance: on/off, its tile variant (2: 16x8, 3: 8x8),
   // and a test switch that withholds one fill signal (the wait times out)
   int64_t opt_queue = 0, opt_queue_tile = 3, opt_queue_withhold = 0, opt_queue_balance = 1;
+  // z planes per CTA of the fused advance: -1 the autotuned length per level (else
+  // the whole column), 0 the whole column, n > 0 chunks of n planes
+  int64_t opt_zchunk = -1;
   // density and pressure floors (0: off) and the device count of their raises
   double floor_rho = 0.0, floor_p = 0.0;
   unsigned long long* d_floor_events = nullptr;
@@ -119,6 +122,19 @@ struct amrmhd_ctx {
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;
+  // autotuned z planes per CTA, same indexing (0: the whole column)
+  std::vector<std::array<int, 2>> zlen_level;
+  // the fused tile variant and z chunk of level l's advance with (wi = 1) or
+  // without (wi = 0) the extended ghost layers, after options and autotuning
+  int tile_of(int l, int wi) const {
+    int v = opt_tile >= 0 ? (int)opt_tile : (variant == amrk::V_MIXED ? 2 : 3);
+    if (opt_tile < 0 && (int)tile_level.size() > l && tile_level[l][wi] >= 0) v = tile_level[l][wi];
+    return v;
+  }
+  int zlen_of(int l, int wi) const {
+    if (opt_zchunk >= 0) return (int)opt_zchunk;
+    return (int)zlen_level.size() > l ? zlen_level[l][wi] : 0;
+  }
   // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is
   // faster; FP64 defaults to the staged kernels (faster there: FP64-ALU bound)
   bool fused() const {

@@ -43,6 +43,7 @@ struct LevelArgs {
   double idx[3];   // 1/dx of this level
   double gamma;
   int w;           // extra ghost layers updated (0 or 2)
+  int zlen;        // fused 3D advance: z planes per CTA (0: the whole column)
   // boundary capture buffer (fused 3D advance of a level > 0): the fluxes and
   // EMFs of every patch's boundary planes are written at P.boff; nullptr: none
   void* bnd;

@@ -1,10 +1,16 @@
-// Fused 3D level advance: one CTA per (patch, x-y tile), marching along z with
-// rolling plane buffers in shared memory, so that primitives, slopes,
-// predicted states, HLLD fluxes and CT EMFs never leave the SM. Only the state
-// is read and written in HBM. Included by kernels_impl.cuh inside AMRK_NS.
+// Fused 3D level advance: one CTA per (patch, x-y tile, z chunk), marching
+// along z with rolling plane buffers in shared memory, so that primitives,
+// slopes, predicted states, HLLD fluxes and CT EMFs never leave the SM. Only
+// the state is read and written in HBM. Included by kernels_impl.cuh inside
+// AMRK_NS.
 //
 // Pipeline per iteration t (planes in patch-local storage coordinates; the
-// output z range is [zlo, zhi) = [4-w, n_z+4+w)):
+// patch's output z range is [zlo, zhi) = [4-w, n_z+4+w), a CTA's the chunk
+// [zs, ze) of it: a.zlen planes from zlo + a.zlen * chunk, or all of them when
+// a.zlen is 0; a chunk restarts the march 2 planes below its first output
+// plane, so a split column recomputes 4 planes of primitives, 2 of predictor
+// and fluxes and 1 of EMFs per extra chunk, and every output value is the
+// same bit for bit whatever the split):
 //   S1  W at plane t                     (tile + 2 halo)        -> ring of 3
 //       (and the normal-B differences of the tile + 1 halo; then cp.async
 //       prefetch of the stored values of the plane S5 updates)
@@ -12,7 +18,7 @@
 //   S3  HLLD fluxes: x- and y-faces of plane p, z-faces of face plane p
 //   S4  edge EMFs: E_z at plane p, E_x and E_y at edge plane p
 //   S5  update of cell plane q = p-1: cells, B_x and B_y of plane q, B_z of face
-//       plane q (and the top face plane zhi on the last plane)
+//       plane q (and the top face plane zhi on the patch's last plane)
 // followed in the next iteration by S1 without a barrier (S5 touches no buffer
 // S1 writes). Buffers that span iterations are 2- or 3-slot rings by plane.
 
@@ -144,7 +150,8 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
 }
 
 // One x-y tile (index `tile`, ntx tiles along x) of the patch at position
-// `pslot` of a.ids, marched along z by the whole CTA; smem_raw: the CTA's
+// `pslot` of a.ids, marched along z by the whole CTA over the z chunk `zc`
+// (a.zlen planes each; 0: the whole column); smem_raw: the CTA's
 // dynamic shared memory (a FusedSmem). MODE 0: plain; 1 (CAP): the level's
 // boundary fluxes and EMFs are captured for the fine registers (patches with
 // P.boff >= 0); 2 (DH): direct halo reads from the neighbour patches (a.nbr; a
@@ -152,7 +159,7 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
 // applies the density and pressure floors of a.fl (never with DH). Every thread
 // of the CTA calls it with the same arguments.
 template <class T, int VAR, int MODE, bool FL = false>
-__device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int tile, int ntx,
+__device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int tile, int ntx, int zc,
                                            unsigned char* smem_raw) {
   constexpr bool CAP = MODE == 1, DH = MODE == 2;
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
@@ -168,7 +175,11 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   const int xlo = 4 - w, xhi = P.n[0] + 4 + w, ylo = 4 - w, yhi = P.n[1] + 4 + w;
   const int zlo = 4 - w, zhi = P.n[2] + 4 + w;
   const int x0 = xlo + (tile % ntx) * TX, y0 = ylo + (tile / ntx) * TY;
-  if (x0 >= xhi || y0 >= yhi) return;
+  const int zs = zlo + zc * a.zlen, ze = a.zlen > 0 ? min(zs + a.zlen, zhi) : zhi;
+  if (x0 >= xhi || y0 >= yhi || zs >= zhi) return;
+  // a face or edge plane shared by two chunks (ze of one, zs of the next) is
+  // captured by the upper chunk only
+  const bool cap_ze = ze == zhi;
   const int tx = min(TX, xhi - x0), ty = min(TY, yhi - y0);
   const bool last_x = x0 + tx == xhi, last_y = y0 + ty == yhi;
   const long long fs = P.fs;
@@ -231,7 +242,7 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   };
   auto prefetch = [&](int qz) {
       {
-        if (qz >= zlo && qz < zhi) {
+        if (qz >= zs && qz < ze) {
           const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
           const bool top = qz == zhi - 1;
           for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
@@ -298,7 +309,10 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
       {
         const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
         constexpr int NFX = (TX + 1) * (S::QY), NFY = (QX) * (TY + 1), NFZ = QX * S::QY, Q = S::Q;
-        const int nf = NFX + NFY + (p >= zlo ? NFZ : 0);
+        const int nf = NFX + NFY + (p >= zs ? NFZ : 0);
+        // boundary capture: x- and y-faces of the chunk's own planes, z-faces of
+        // its face planes (the top one only on the column's last chunk)
+        const bool cap_xy = capture && p >= zs && p < ze, cap_z = capture && (p < ze || cap_ze);
         for (int c = threadIdx.x; c < nf; c += nth) {
           // one face: direction D, its high-side cell (x, y) and the offset of its low-side cell
           int D, x, y, lo;
@@ -345,7 +359,7 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
 #pragma unroll
           for (int k = 0; k < 7; ++k) fo[fi[k] * Q + q] = fr[k];
           fo[(BX + n) * Q + q] = T(0);
-          if (capture) {  // a boundary face of a fine patch: keep its flux for the registers
+          if (D < 2 ? cap_xy : cap_z) {  // a boundary face of a fine patch: keep its flux for the registers
             const long long sl = bnd_face_slot(P, D, x, y, p);
             if (sl >= 0) {
               T* b = (T*)a.bnd + P.boff;
@@ -363,7 +377,8 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
         const int r2 = (p + 2) % 2, rm = (p + 1) % 2;
         const int r3 = (p + 3) % 3, rm3 = (p + 2) % 3;  // reference EMFs of planes p and p-1
         constexpr int NEZ = (TX + 1) * (TY + 1), NEX = TX * (TY + 1), NEY = (TX + 1) * TY;
-        const int nez = p < zhi ? NEZ : 0;
+        const int nez = p < ze ? NEZ : 0;
+        const bool cap_e = capture && (p < ze || cap_ze);  // E_x, E_y of edge plane p
         for (int c = threadIdx.x; c < nez + NEX + NEY; c += nth) {
           if (c < nez) {  // E_z at corner (x-1/2, y-1/2) of plane p: a = x, b = y
             const int xi = c % (TX + 1), yi = c / (TX + 1);
@@ -387,7 +402,7 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
             sm.ex[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm3][0][qm], sm.ref[rm3][0][q], sm.ref[r3][0][qm],
                                      sm.ref[r3][0][q], sm.fy[rm][RHO][q], sm.fy[r2][RHO][q], sm.fz[r2][RHO][qm],
                                      sm.fz[r2][RHO][q]);
-            if (capture) bnd_store_edge<T>(a, P, 0, x, y, p, sm.ex[r2][q]);
+            if (cap_e) bnd_store_edge<T>(a, P, 0, x, y, p, sm.ex[r2][q]);
           } else {  // E_y at (x-1/2, y, p-1/2): a = z, b = x
             const int cc = c - nez - NEX, xi = cc % (TX + 1), yi = cc / (TX + 1);
             if (xi > tx || yi >= ty) continue;
@@ -400,13 +415,13 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
             sm.ey[r2][q] = gs_emf<T>(ea_lo, ea_hi, eb_lo, eb_hi, sm.ref[rm3][1][qm], sm.ref[r3][1][qm], sm.ref[rm3][1][q],
                                      sm.ref[r3][1][q], sm.fz[r2][RHO][qm], sm.fz[r2][RHO][q], sm.fx[rm][RHO][q],
                                      sm.fx[r2][RHO][q]);
-            if (capture) bnd_store_edge<T>(a, P, 1, x, y, p, sm.ey[r2][q]);
+            if (cap_e) bnd_store_edge<T>(a, P, 1, x, y, p, sm.ey[r2][q]);
           }
         }
       }
   };
   auto stage5 = [&](int qz) {
-      if (qz >= zlo && qz < zhi) {
+      if (qz >= zs && qz < ze) {
         const int p = qz + 1;
         const int rq = (qz + 2) % 2, rp = (p + 2) % 2;
         const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
@@ -463,19 +478,19 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   // update of plane p-1. Rings: W 3 planes (S1(p+2) replaces W(p-1), which only
   // S2(p) of the previous phase 2 read), reference EMFs 3 planes (S2(p+1)
   // writes while S4(p) reads planes p and p-1), the rest 2 planes.
-  stage1(zlo - 2);
-  stage1(zlo - 1);
-  stage1(zlo);
+  stage1(zs - 2);
+  stage1(zs - 1);
+  stage1(zs);
   __syncthreads();
-  stage2(zlo - 1);
+  stage2(zs - 1);
   __syncthreads();
-  for (int p = zlo - 1; p <= zhi; ++p) {
+  for (int p = zs - 1; p <= ze; ++p) {
     prefetch(p - 1);
     stage3(p);
-    if (p + 2 <= zhi + 1) stage1(p + 2);
+    if (p + 2 <= ze + 1) stage1(p + 2);
     __syncthreads();
-    if (p >= zlo) stage4(p);
-    if (p + 1 <= zhi) stage2(p + 1);
+    if (p >= zs) stage4(p);
+    if (p + 1 <= ze) stage2(p + 1);
     cp_async_wait_all();
     __syncthreads();
     stage5(p - 1);
@@ -490,7 +505,7 @@ template <class T, int VAR, int MODE, bool FL = false>
 __global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? fused_ctas_fp32<VAR>() : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_tile<T, VAR, MODE, FL>(a, blockIdx.y, blockIdx.x, ntx, smem_raw);
+  fused_tile<T, VAR, MODE, FL>(a, blockIdx.y, blockIdx.x, ntx, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------- device work queue
@@ -573,7 +588,7 @@ __global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? 2 : 1)
         s_go = go;
       }
       __syncthreads();
-      if (s_go) fused_tile<T, VAR, 1>(L.a, t.y, t.z, L.ntx, smem_raw);
+      if (s_go) fused_tile<T, VAR, 1>(L.a, t.y, t.z, L.ntx, 0, smem_raw);
     }
     __syncthreads();  // the task's shared memory is free for the next one
   }

@@ -1149,7 +1149,8 @@ template <class T, int DIM> struct Impl {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
     const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
     const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
-    const dim3 g(ntx * nty, a.npatch);
+    const int ez = a.maxn[2] + 2 * a.w, nzc = a.zlen > 0 ? (ez + a.zlen - 1) / a.zlen : 1;
+    const dim3 g(ntx * nty, a.npatch, nzc);
     const bool fl = a.fl.rho > 0.0 || a.fl.p > 0.0;  // floors (the host never combines them with DH)
     if (fl && a.bnd) k_advance3d_fused<T, V, 1, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
     else if (fl) k_advance3d_fused<T, V, 0, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
