@@ -243,15 +243,24 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   auto prefetch = [&](int qz) {
       {
         if (qz >= zs && qz < ze) {
+          // the tile's cells (all 8 stored values; B_z of the top face plane
+          // too on the patch's last plane), and on the patch's high x (y) side
+          // the B_x (B_y) faces of the column x0+tx (the row y0+ty)
           const int nx = tx + (last_x ? 1 : 0), ny = ty + (last_y ? 1 : 0);
           const bool top = qz == zhi - 1;
           for (int c = threadIdx.x; c < (TX + 1) * (TY + 1); c += nth) {
             const int xi = c % (TX + 1), yi = c / (TX + 1);
             if (xi >= nx || yi >= ny) continue;
             const int L = (x0 + xi) + sy * (y0 + yi) + sz * qz;
+            if (xi < tx && yi < ty) {
 #pragma unroll
-            for (int f = 0; f < 8; ++f) cp_async_elem<T>(&sm.up[f][c], U + f * fs + L);
-            if (top) cp_async_elem<T>(&sm.up[8][c], U + BZ * fs + L + sz);
+              for (int f = 0; f < 8; ++f) cp_async_elem<T>(&sm.up[f][c], U + f * fs + L);
+              if (top) cp_async_elem<T>(&sm.up[8][c], U + BZ * fs + L + sz);
+            } else if (yi < ty) {
+              cp_async_elem<T>(&sm.up[BX][c], U + BX * fs + L);
+            } else if (xi < tx) {
+              cp_async_elem<T>(&sm.up[BY][c], U + BY * fs + L);
+            }
           }
         }
         cp_async_commit();
