@@ -208,9 +208,10 @@ def e2e_run(pb, precision, k):
     - pipelined (a stream of independent inputs): each step's input is copied
       from pinned host memory into one of two device staging buffers on an
       upload stream while the previous step computes, loaded with
-      amrmhd_set_state_all from the device buffer, stepped, written with
-      amrmhd_get_state_all into one of two device result buffers and copied to
-      pinned host memory on a download stream while the next step computes.
+      amrmhd_set_state_all from the device buffer, stepped (amrmhd_step_async:
+      the host queues ahead), written with amrmhd_get_state_all into one of two
+      device result buffers and copied to pinned host memory on a download
+      stream while the next step computes; amrmhd_sync at the end.
     Returns (pipelined rate, serial rate, bytes per direction per step, host
     link rates)."""
     import numpy as np
@@ -265,7 +266,7 @@ def e2e_run(pb, precision, k):
             stream.wait_event(ev["in_ready"][b])
             ctx._check(set_all(ctx.h, C.c_void_p(dev_in[b].data_ptr()), 1), "set_all")
             ev["in_free"][b].record(stream)
-            ctx.step(1, want_dt=False)
+            ctx.step_async(1)
             stream.wait_event(ev["out_free"][b])
             ctx._check(get_all(ctx.h, C.c_void_p(dev_out[b].data_ptr()), 1), "get_all")
             ev["out_ready"][b].record(stream)
@@ -273,6 +274,7 @@ def e2e_run(pb, precision, k):
             with torch.cuda.stream(dn):
                 outs[b].copy_(dev_out[b], non_blocking=True)
                 ev["out_free"][b].record(dn)
+        ctx.sync()  # device errors of the queued steps
         torch.cuda.synchronize()
 
     pipelined(2)
@@ -297,7 +299,19 @@ def e2e_run(pb, precision, k):
         e1.record()
         torch.cuda.synchronize()
         link[name] = 5 * nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
-    del dev
+    # both directions at once (an upload and a download on two streams)
+    dev2 = torch.empty_like(host_in, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for _ in range(5):
+        with torch.cuda.stream(s1):
+            dev.copy_(host_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            host_out.copy_(dev2, non_blocking=True)
+    torch.cuda.synchronize()
+    link["both_ways_gbs_each"] = 5 * nbytes / (time.perf_counter() - t2) / 1e9
+    del dev, dev2
     torch.cuda.empty_cache()
     link["pipelined_result_equals_serial"] = same
     return cells * k / tp, cells * k / t, nbytes, link
@@ -808,7 +822,8 @@ def main():
         e2e = {"value": ve * world, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "how": "pipelined: step n+1's input uploads and step n-1's result downloads (pinned host "
                       "memory, double-buffered device staging, own streams) overlap step n's "
-                      "amrmhd_set_state_all + amrmhd_step + amrmhd_get_state_all; host clock over %d steps" % ke,
+                      "amrmhd_set_state_all + amrmhd_step_async + amrmhd_get_state_all, amrmhd_sync at the end; "
+                      "host clock over %d steps" % ke,
                "serial": {"value": vs * world, "how": "amrmhd_set/get_state_all on the pinned host buffers, "
                                                       "one step after the other"},
                "host_link_measured": link}

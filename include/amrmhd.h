@@ -234,6 +234,21 @@ amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0);
  * values. Synchronises the stream at the end and reports device errors. */
 amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used);
 
+/* The same n_coarse coarse steps, stream-ordered: the call returns once the
+ * steps are queued on the context's stream, without waiting for them, so that
+ * a caller can queue further work (state I/O with device pointers, copies on
+ * its own streams ordered by events) while they run. Device errors of the
+ * steps (a non-physical state, a queue wait that ran out) stay in the
+ * context's error word and are reported by the next synchronising call
+ * (amrmhd_sync, amrmhd_step, amrmhd_cfl_dt); a dt0 of a step that follows such
+ * an error is 0 (the state does not change). Like amrmhd_step, the paper is
+ * silent on how the steps are issued. */
+amrmhd_status amrmhd_step_async(amrmhd_ctx* ctx, int32_t n_coarse);
+
+/* Waits for the work queued on the context's stream and reports (then clears)
+ * a device error: AMRMHD_ENONPHYS, AMRMHD_ETIMEOUT, else AMRMHD_OK. */
+amrmhd_status amrmhd_sync(amrmhd_ctx* ctx);
+
 /* n_coarse coarse steps with the prescribed dt0 sequence dt_seq (host, n_coarse
  * positive values; level l steps with dt0 2^-l) instead of the CFL dt, with
  * plain launches: the forward map that amrmhd_backward differentiates.

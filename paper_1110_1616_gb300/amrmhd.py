@@ -86,6 +86,8 @@ def lib():
             "amrmhd_regrid": [vp, dbl, i32],
             "amrmhd_autotune": [vp, i32, vp],
             "amrmhd_tile_choice": [vp, i32, i32, C.POINTER(i32), C.POINTER(i32)],
+            "amrmhd_step_async": [vp, i32],
+            "amrmhd_sync": [vp],
             "amrmhd_get_patches": [vp, vp, i32, C.POINTER(i32)],
             "amrmhd_regrid_boxes": [vp, i32, vp, i64, vp, i32, C.POINTER(i32)],
             "amrmhd_query": [vp, i32, C.POINTER(i64)],
@@ -364,6 +366,14 @@ class Context:
         buf = np.zeros(max(n, 1), dtype=np.float64) if want_dt else None
         self._check(lib().amrmhd_step(self.h, n, buf.ctypes.data_as(C.c_void_p) if want_dt else None), "step")
         return buf
+
+    def step_async(self, n=1):
+        """n coarse steps queued on the context's stream (see amrmhd_step_async)."""
+        self._check(lib().amrmhd_step_async(self.h, n), "step_async")
+
+    def sync(self):
+        """Waits for the context's stream; raises on a device error (amrmhd_sync)."""
+        self._check(lib().amrmhd_sync(self.h), "sync")
 
     def autotune(self, trials=5):
         """Per-level fused-tile choice by timing (see amrmhd_autotune)."""

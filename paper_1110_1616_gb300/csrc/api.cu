@@ -1476,7 +1476,22 @@ amrmhd_status amrmhd_cfl_dt(amrmhd_ctx* ctx, double* dt0) {
   return AMRMHD_OK;
 }
 
-amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
+// waits for the context's stream, then reports and clears the error word
+static amrmhd_status report_device_error(amrmhd_ctx* ctx) {
+  unsigned int err = 0;
+  CU(cudaMemcpyAsync(&err, ctx->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (err) {
+    CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
+    if (err & amrk::ERR_QUEUE_TIMEOUT)
+      return fail(ctx, AMRMHD_ETIMEOUT, "a wait of the queue advance ran out (a fill signal never came)");
+    return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
+  }
+  return AMRMHD_OK;
+}
+
+// n_coarse coarse steps; wait: synchronise and report device errors
+static amrmhd_status step_impl(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used, bool wait) {
   if (ctx) ++ctx->state_version;  // a recorded forward (amrmhd_step_dt_ckpt) no longer matches
   amrmhd_status st = check_bound(ctx);
   if (st) return st;
@@ -1532,16 +1547,19 @@ amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
       CU(cudaMemcpyAsync(dt_used + done, ctx->d_hist, sizeof(double) * chunk, cudaMemcpyDeviceToHost, ctx->stream));
     done += chunk;
   }
-  unsigned int err = 0;
-  CU(cudaMemcpyAsync(&err, ctx->d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  if (err) {
-    CU(cudaMemset(ctx->d_err, 0, sizeof(unsigned int)));
-    if (err & amrk::ERR_QUEUE_TIMEOUT)
-      return fail(ctx, AMRMHD_ETIMEOUT, "a wait of the queue advance ran out (a fill signal never came)");
-    return fail(ctx, AMRMHD_ENONPHYS, "non-finite or non-positive density or pressure");
-  }
-  return AMRMHD_OK;
+  return wait ? report_device_error(ctx) : AMRMHD_OK;
+}
+
+amrmhd_status amrmhd_step(amrmhd_ctx* ctx, int32_t n_coarse, double* dt_used) {
+  return step_impl(ctx, n_coarse, dt_used, true);
+}
+
+amrmhd_status amrmhd_step_async(amrmhd_ctx* ctx, int32_t n_coarse) { return step_impl(ctx, n_coarse, nullptr, false); }
+
+amrmhd_status amrmhd_sync(amrmhd_ctx* ctx) {
+  amrmhd_status st = check_bound(ctx);
+  if (st) return st;
+  return report_device_error(ctx);
 }
 
 amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {

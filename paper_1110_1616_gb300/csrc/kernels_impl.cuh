@@ -961,6 +961,13 @@ __global__ void __launch_bounds__(TPB) k_io(const DPatch* PP, const int* ids, vo
 struct IoAll {
   long long foff[8];
 };
+// Each warp takes 32 x IO_EPT consecutive packed elements of one (patch,
+// field), lane l the elements l, l+32, ...: the packed side is read or written
+// in whole 128-byte lines, the positions in the patch follow by stepping x
+// (and wrapping into y and z) instead of dividing per element, and a thread's
+// IO_EPT loads are issued before its stores (device memory, or page-locked
+// host memory over the host link).
+constexpr int IO_EPT = 8;
 template <class T, int DIM, class Q>
 __global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids, void* state, Q* packed,
                                                 const long long* const* poff, IoAll io, int to_state) {
@@ -971,14 +978,38 @@ __global__ void __launch_bounds__(TPB) k_io_all(const DPatch* PP, const int* ids
   int r[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) r[e] = e >= DIM ? 1 : P.n[e] + (e == fd ? 1 : 0);
-  const int t = blockIdx.x * TPB + threadIdx.x;
-  if (t >= r[0] * r[1] * r[2]) return;
-  const int i = t % r[0], j = (t / r[0]) % r[1], k = t / (r[0] * r[1]);
-  const int L = lidx(P, i + 4, j + 4, DIM == 3 ? k + 4 : 0);
-  T* s = (T*)state + P.off + field * P.fs + L;
-  Q* q = packed + io.foff[field] + poff[fd + 1][pid] + t;
-  if (to_state) *s = (T)*q;
-  else *q = (Q)*s;
+  const int n = r[0] * r[1] * r[2];
+  const int t0 = blockIdx.x * (TPB * IO_EPT) + (threadIdx.x >> 5) * (32 * IO_EPT) + (threadIdx.x & 31);
+  if (t0 >= n) return;
+  T* sb = (T*)state + P.off + field * P.fs;
+  Q* qb = packed + io.foff[field] + poff[fd + 1][pid];
+  int i = t0 % r[0], j = (t0 / r[0]) % r[1], k = t0 / (r[0] * r[1]);
+  int ls[IO_EPT];
+#pragma unroll
+  for (int m = 0; m < IO_EPT; ++m) {
+    // an element past the end reads element t0 again and is not stored
+    ls[m] = t0 + 32 * m < n ? lidx(P, i + 4, j + 4, DIM == 3 ? k + 4 : 0) : ls[0];
+    i += 32;
+    while (i >= r[0]) {
+      i -= r[0];
+      if (++j == r[1]) { j = 0; ++k; }
+    }
+  }
+  if (to_state) {
+    Q v[IO_EPT];
+#pragma unroll
+    for (int m = 0; m < IO_EPT; ++m) v[m] = qb[t0 + 32 * m < n ? t0 + 32 * m : t0];
+#pragma unroll
+    for (int m = 0; m < IO_EPT; ++m)
+      if (t0 + 32 * m < n) sb[ls[m]] = (T)v[m];
+  } else {
+    T v[IO_EPT];
+#pragma unroll
+    for (int m = 0; m < IO_EPT; ++m) v[m] = sb[ls[m]];
+#pragma unroll
+    for (int m = 0; m < IO_EPT; ++m)
+      if (t0 + 32 * m < n) qb[t0 + 32 * m] = (Q)v[m];
+  }
 }
 
 #include "kernels_fused.cuh"
@@ -1092,11 +1123,11 @@ template <class T, int DIM> struct Impl {
   static void io_all(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, void* packed,
                      int packed_f32, const long long* const* poff, const long long* foff, int to_state, cudaStream_t s,
                      int* nl) {
-    long long n = 1;
+    long long n = 1;  // elements of the largest (patch, field)
     for (int d = 0; d < DIM; ++d) n *= maxn[d] + 1;
     IoAll io;
     for (int f = 0; f < 8; ++f) io.foff[f] = foff[f];
-    const dim3 g(cdiv(n, TPB), npatch, 8);
+    const dim3 g(cdiv(n, TPB * IO_EPT), npatch, 8);
     if (packed_f32) k_io_all<T, DIM, float><<<g, TPB, 0, s>>>(P, ids, state, (float*)packed, poff, io, to_state);
     else k_io_all<T, DIM, double><<<g, TPB, 0, s>>>(P, ids, state, (double*)packed, poff, io, to_state);
     if (nl) ++*nl;

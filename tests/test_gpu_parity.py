@@ -438,6 +438,38 @@ def test_whole_state_io_page_locked_host_memory(precision):
     assert np.array_equal(back, expect)
 
 
+@pytest.mark.parametrize("where", ["device", "pinned"])
+def test_whole_state_io_3d_ragged(where):
+    """3D, three levels of patches 8 to 16 cells wide (face fields one longer
+    along their normal, rows of 8 to 17 elements, row counts not multiples of
+    the packing kernel's row batch): the whole-state calls (device pointers, or
+    page-locked host memory) move the values of the per-field packed calls,
+    both ways."""
+    import ctypes as C
+    import torch
+    patches = inputs.random_hierarchy(3, 5, base=16, psize0=8, nlev=3)
+    nlev = max(p[0] for p in patches) + 1
+    st = {l: inputs.mhd_wave(3, 16 << l, "fast", amp=1e-2).state[0] for l in range(nlev)}
+    pb = inputs.Problem("rand3d", 3, (16, 16, 16), patches, nlev, st)
+    ctx = gpu_for(pb, A.FP64)
+    ref = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    if where == "device":
+        buf = torch.empty(ref.size, dtype=torch.float64, device="cuda")
+        on_dev = 1
+    else:
+        buf = torch.empty(ref.size, dtype=torch.float64).pin_memory()
+        on_dev = 0
+    ctx._check(A.lib().amrmhd_get_state_all(ctx.h, C.c_void_p(buf.data_ptr()), on_dev), "get_all")
+    torch.cuda.synchronize()
+    assert np.array_equal(buf.cpu().numpy(), ref)
+    new = ref * 1.5 + 0.25
+    buf.copy_(torch.from_numpy(new))
+    torch.cuda.synchronize()
+    ctx._check(A.lib().amrmhd_set_state_all(ctx.h, C.c_void_p(buf.data_ptr()), on_dev), "set_all")
+    back = np.concatenate([ctx.get_field_packed(f) for f in range(8)])
+    assert np.array_equal(back, new)
+
+
 @pytest.mark.parametrize("pinned,staged", [(False, 0), (True, 0), (True, 1)])
 def test_whole_state_io_float_elements(pinned, staged):
     """amrmhd_set_state_all_f32 / get_state_all_f32 move the stored FP32 values
