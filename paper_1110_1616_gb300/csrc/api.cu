@@ -166,11 +166,11 @@ void op_fill_rest(amrmhd_ctx* ctx, int l, int s, int* nl) {
     b.cbuf = state_buf(ctx, ctx->start[l - 1]);
     b.chunks = L.chunk_pcells.p;
     b.nrows = L.chunk_pcells.n;
-    ctx->ops->prolong_cells(b, ctx->stream, nl);
-    b.rows = L.prol_faces.p;
-    b.chunks = L.chunk_pfaces.p;
-    b.nrows = L.chunk_pfaces.n;
-    ctx->ops->prolong_faces(b, ctx->stream, nl);
+    RowArgs bf = b;
+    bf.rows = L.prol_faces.p;
+    bf.chunks = L.chunk_pfaces.p;
+    bf.nrows = L.chunk_pfaces.n;
+    ctx->ops->prolong(b, bf, ctx->stream, nl);
   }
   // physical boundaries last: their sources are domain cells filled above
   const DevList& bcc = near ? L.bc_cells2 : L.bc_cells;
@@ -283,16 +283,16 @@ void op_reflux_restrict(amrmhd_ctx* ctx, int l, int* nl) {
   a.cbuf = state_buf(ctx, ctx->cur[l - 1]);
   a.fbuf = state_buf(ctx, ctx->cur[l]);
   // reflux rows hold global C/F face row numbers: registers are not offset here
-  ctx->ops->reflux_cells(a, ctx->stream, nl);
-  a.rows = F.emf_faces.p;
-  a.nrows = F.emf_faces.n;
-  ctx->ops->reflux_faces(a, ctx->stream, nl);
-  a.rows = F.restrict_cells.p;
-  a.nrows = F.restrict_cells.n;
-  ctx->ops->restrict_cells(a, ctx->stream, nl);
-  a.rows = F.restrict_faces.p;
-  a.nrows = F.restrict_faces.n;
-  ctx->ops->restrict_faces(a, ctx->stream, nl);
+  amrk::RRLists L;
+  L.rows[0] = F.reflux_cells.p;
+  L.n[0] = F.reflux_cells.n;
+  L.rows[1] = F.emf_faces.p;
+  L.n[1] = F.emf_faces.n;
+  L.rows[2] = F.restrict_cells.p;
+  L.n[2] = F.restrict_cells.n;
+  L.rows[3] = F.restrict_faces.p;
+  L.n[3] = F.restrict_faces.n;
+  ctx->ops->reflux_restrict(a, L, ctx->stream, nl);
 }
 
 void op_cfl(amrmhd_ctx* ctx, double* hist, int* nl) {

@@ -154,6 +154,15 @@ struct DenseBox {
   int off[3], n[3];
 };
 
+// the four row lists of a fine level's reflux and restriction (reflux cells,
+// reflux faces, restriction cells, restriction faces) and, set by the
+// launcher, the first block of each list's range
+struct RRLists {
+  const int* rows[4];
+  long long n[4];
+  unsigned b[5];
+};
+
 struct Ops {
   void (*advance)(const LevelArgs&, cudaStream_t, int* launches);
   void (*reg_coarse)(const RowArgs& faces, const RowArgs& edges, cudaStream_t, int* launches);
@@ -164,14 +173,13 @@ struct Ops {
   // nrows) of whole box rows), then prolongation and physical boundaries
   // (ghost boxes of amrmhd::GHOST_BOX_W ints; chunks (box, first position))
   void (*fill_runs)(const RowArgs&, cudaStream_t, int* launches);
-  void (*prolong_cells)(const RowArgs&, cudaStream_t, int* launches);
-  void (*prolong_faces)(const RowArgs&, cudaStream_t, int* launches);
+  // the prolonged ghost cells and faces in one launch
+  void (*prolong)(const RowArgs& cells, const RowArgs& faces, cudaStream_t, int* launches);
   void (*fill_bc_cells)(const RowArgs&, cudaStream_t, int* launches);
   void (*fill_bc_faces)(const RowArgs&, cudaStream_t, int* launches);
-  void (*reflux_cells)(const RowArgs&, cudaStream_t, int* launches);
-  void (*reflux_faces)(const RowArgs&, cudaStream_t, int* launches);
-  void (*restrict_cells)(const RowArgs&, cudaStream_t, int* launches);
-  void (*restrict_faces)(const RowArgs&, cudaStream_t, int* launches);
+  // reflux (cells, faces) and restriction (cells, faces) of a fine level in
+  // one launch: RowArgs gives the buffers and registers, RRLists the rows
+  void (*reflux_restrict)(const RowArgs&, const RRLists&, cudaStream_t, int* launches);
   void (*cfl)(const CflArgs&, cudaStream_t, int* launches);
   // packed I/O of one field: to_state = 1 copies packed -> state
   void (*io)(const DPatch* P, const int* ids, int npatch, const int* maxn, void* state, double* packed,

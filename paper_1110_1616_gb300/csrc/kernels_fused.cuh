@@ -698,8 +698,8 @@ __device__ __forceinline__ const Floors* rc_floors(const RowArgs& a) {
 
 // RowArgs.fbuf = the state the level's advance read (for the coarse side the
 // coarse level, for the fine side the fine level); dt = *dtp * dtscale.
-template <class T> __global__ void k_regrc_coarse_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regrc_coarse_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[1]];
@@ -711,8 +711,8 @@ template <class T> __global__ void k_regrc_coarse_faces(RowArgs a, double gamma,
   for (int n = 0; n < 5; ++n) a.creg[r * 6 + n] = dt * (double)f8[n];
 }
 
-template <class T> __global__ void k_regrc_coarse_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regrc_coarse_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[1]];
@@ -721,8 +721,8 @@ template <class T> __global__ void k_regrc_coarse_edges(RowArgs a, double gamma,
   a.ecreg[r] = dt * (double)edge_emf_at<T>((const T*)a.fbuf + P.off, P, row[2], row[3], dt, idx, gamma, rc_floors(a));
 }
 
-template <class T> __global__ void k_regrc_fine_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regrc_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[5]];
@@ -745,8 +745,8 @@ template <class T> __global__ void k_regrc_fine_faces(RowArgs a, double gamma, d
     out[n] = af * tree4((double)f[0][n], (double)f[1][n], (double)f[2][n], (double)f[3][n]);
 }
 
-template <class T> __global__ void k_regrc_fine_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regrc_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[4]];
@@ -763,8 +763,8 @@ template <class T> __global__ void k_regrc_fine_edges(RowArgs a, double gamma, d
 // fine-side registers from the boundary capture of the fine level's fused
 // advance (the same fluxes and EMFs the recompute kernels above evaluate); a
 // face or edge off the boundary planes (none by construction) is recomputed
-template <class T> __global__ void k_regcap_fine_faces(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regcap_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[5]];
@@ -801,8 +801,8 @@ template <class T> __global__ void k_regcap_fine_faces(RowArgs a, double gamma, 
     out[n] = af * tree4((double)f[0][n], (double)f[1][n], (double)f[2][n], (double)f[3][n]);
 }
 
-template <class T> __global__ void k_regcap_fine_edges(RowArgs a, double gamma, double ix, double iy, double iz) {
-  const long long r = (long long)blockIdx.x * 128 + threadIdx.x;
+template <class T>
+__device__ __forceinline__ void regcap_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[4]];
@@ -826,3 +826,17 @@ template <class T> __global__ void k_regcap_fine_edges(RowArgs a, double gamma, 
   }
   a.efreg[r * 2 + (a.substep - 1)] = (dt * 0.5) * tree2((double)ev[0], (double)ev[1]);
 }
+
+// the face and the edge rows of one register side in one launch: blocks [0,
+// nbf) take the face rows, the rest the edge rows (128 rows per block)
+#define AMRK_REG_PAIR(NAME)                                                                          \
+  template <class T>                                                                                 \
+  __global__ void __launch_bounds__(128)                                                             \
+      k_##NAME(RowArgs f, RowArgs e, unsigned nbf, double gamma, double ix, double iy, double iz) {  \
+    if (blockIdx.x < nbf) NAME##_faces_row<T>(f, (long long)blockIdx.x * 128 + threadIdx.x, gamma, ix, iy, iz); \
+    else NAME##_edges_row<T>(e, (long long)(blockIdx.x - nbf) * 128 + threadIdx.x, gamma, ix, iy, iz);  \
+  }
+AMRK_REG_PAIR(regrc_coarse)
+AMRK_REG_PAIR(regrc_fine)
+AMRK_REG_PAIR(regcap_fine)
+#undef AMRK_REG_PAIR

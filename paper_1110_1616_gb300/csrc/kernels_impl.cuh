@@ -433,12 +433,13 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_RUN_TPB) k_fi
 // Prolongation and physical-boundary fills as ghost boxes of GHOST_BOX_W
 // ints (dst, d, kind, src, lo[3], n[3], aux[3]), lo in dst's local ghosted
 // coordinates; chunks as for the same-level boxes. gbox_pos gives the local
-// coordinates x of this thread's position and its global position g.
+// coordinates x of this thread's position and its global position g (chunk
+// bid: the block's index among the list's blocks).
 constexpr int GBW = amrmhd::GHOST_BOX_W;
 template <int DIM>
-__device__ __forceinline__ bool gbox_pos(const RowArgs& a, const int*& box, int* x, int* g) {
-  const int bi = a.chunks[2 * blockIdx.x];
-  const int c = a.chunks[2 * blockIdx.x + 1] + threadIdx.x;
+__device__ __forceinline__ bool gbox_pos(const RowArgs& a, unsigned bid, const int*& box, int* x, int* g) {
+  const int bi = a.chunks[2 * bid];
+  const int c = a.chunks[2 * bid + 1] + threadIdx.x;
   box = a.rows + GBW * bi;
   const int nx = box[7], ny = box[8], nz = box[9];
   if (c >= nx * ny * nz) return false;
@@ -460,7 +461,7 @@ __device__ __forceinline__ int local_of(const DPatch& P, const int* g) {
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_bc_cells(RowArgs a) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, blockIdx.x, box, x, g)) return;
   const DPatch D = a.P[box[0]];
   T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
   constexpr int NCF = DIM == 3 ? 5 : 6;
@@ -487,7 +488,7 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_b
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_fill_bc_faces(RowArgs a) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, blockIdx.x, box, x, g)) return;
   const DPatch D = a.P[box[0]];
   const int f = BX + box[1];
   T* B = (T*)a.fbuf + D.off + f * D.fs;
@@ -515,10 +516,10 @@ template <int DIM> __device__ __forceinline__ int parent_local(const DPatch& C, 
 // prolonged ghost cells (Sec. 2 prolongation): minmod-limited linear
 // reconstruction of the parent cell at the child's centre; coarse data from
 // cbuf (the parent level's state at the start of its current sub-step)
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolong_cells(RowArgs a) {
+template <class T, int DIM> __device__ __forceinline__ void prolong_cells_at(const RowArgs& a, unsigned bid) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, bid, box, x, g)) return;
   const DPatch D = a.P[box[0]], C = a.P[box[3]];
   T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
   const T* src = (const T*)a.cbuf + C.off + parent_local<DIM>(C, g, box + 10);
@@ -556,10 +557,10 @@ __device__ __forceinline__ T coincident(const T* b, const int* st, int n, const 
 
 // prolonged ghost faces (the box's n-faces): divergence-free (Balsara) from the
 // coarse faces
-template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolong_faces(RowArgs a) {
+template <class T, int DIM> __device__ __forceinline__ void prolong_faces_at(const RowArgs& a, unsigned bid) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, bid, box, x, g)) return;
   const DPatch D = a.P[box[0]], C = a.P[box[3]];
   const int n = box[1];
   const int Lc = parent_local<DIM>(C, g, box + 10);
@@ -589,6 +590,14 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolon
     v = T(0.5) * (lo_v + hi_v) + T(0.125) * corr;
   }
   ((T*)a.fbuf)[D.off + (BX + n) * D.fs + x[0] + D.ext[0] * (x[1] + D.ext[1] * x[2])] = v;
+}
+
+// the prolonged ghost cells and faces of a level in one launch: blocks [0,
+// c.nrows) take the cell chunks, the rest the face chunks (the two write
+// disjoint positions from disjoint coarse data)
+template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_prolong(RowArgs c, RowArgs f) {
+  if (blockIdx.x < (unsigned)c.nrows) prolong_cells_at<T, DIM>(c, blockIdx.x);
+  else prolong_faces_at<T, DIM>(f, blockIdx.x - (unsigned)c.nrows);
 }
 
 // ------------------------------------------------------------------ regrid
@@ -650,7 +659,7 @@ __global__ void __launch_bounds__(TPB) k_flag_dense(LevelArgs a, double theta, u
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_transfer_cells(RowArgs a) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, blockIdx.x, box, x, g)) return;
   const DPatch D = a.P[box[0]];
   T* dst = (T*)a.fbuf + D.off + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
   constexpr int NCF = DIM == 3 ? 5 : 6;
@@ -689,7 +698,7 @@ template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_transf
 template <class T, int DIM> __global__ void __launch_bounds__(FILL_TPB) k_transfer_faces(RowArgs a) {
   const int* box;
   int x[3], g[3];
-  if (!gbox_pos<DIM>(a, box, x, g)) return;
+  if (!gbox_pos<DIM>(a, blockIdx.x, box, x, g)) return;
   const DPatch D = a.P[box[0]];
   const int n = box[1];
   T* out = (T*)a.fbuf + D.off + (BX + n) * D.fs + x[0] + (long long)D.ext[0] * (x[1] + (long long)D.ext[1] * x[2]);
@@ -775,10 +784,8 @@ template <class T, int DIM> __global__ void k_closure(RowArgs a) {
 
 // ------------------------------------------------------------------ reflux and restriction
 // rows (l, qc, Lcell, f0..f5); R = (S1 + S2) - C per C/F face, applied in slot order
-template <class T, int DIM> __global__ void k_reflux_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 9 * r;
+template <class T, int DIM> __device__ __forceinline__ void reflux_cells_row(const RowArgs& a, const int* rows, long long r) {
+  const int* row = rows + 9 * r;
   const DPatch P = a.P[row[1]];
   T* U = (T*)a.cbuf + P.off + row[2];
   constexpr int NCF = DIM == 3 ? 5 : 6;
@@ -798,10 +805,8 @@ template <class T, int DIM> __global__ void k_reflux_cells(RowArgs a) {
 }
 
 // rows (l, qc, d, Lface, e0..e3): B += +e0/dx_t1 - e1/dx_t1 - e2/dx_t2 + e3/dx_t2
-template <class T, int DIM> __global__ void k_reflux_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 8 * r;
+template <class T, int DIM> __device__ __forceinline__ void reflux_faces_row(const RowArgs& a, const int* rows, long long r) {
+  const int* row = rows + 8 * r;
   const DPatch P = a.P[row[1]];
   const int d = row[2];
   T* B = (T*)a.cbuf + P.off + (BX + d) * P.fs + row[3];
@@ -819,10 +824,8 @@ template <class T, int DIM> __global__ void k_reflux_faces(RowArgs a) {
 }
 
 // rows (l, qc, Lcell, pf, Lchild0)
-template <class T, int DIM> __global__ void k_restrict_cells(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 5 * r;
+template <class T, int DIM> __device__ __forceinline__ void restrict_cells_row(const RowArgs& a, const int* rows, long long r) {
+  const int* row = rows + 5 * r;
   const DPatch C = a.P[row[1]], F = a.P[row[3]];
   T* dst = (T*)a.cbuf + C.off + row[2];
   const T* src = (const T*)a.fbuf + F.off + row[4];
@@ -845,10 +848,8 @@ template <class T, int DIM> __global__ void k_restrict_cells(RowArgs a) {
 }
 
 // rows (l, qc, d, Lface, pf, Lfine0)
-template <class T, int DIM> __global__ void k_restrict_faces(RowArgs a) {
-  const long long r = (long long)blockIdx.x * TPB + threadIdx.x;
-  if (r >= a.nrows) return;
-  const int* row = a.rows + 6 * r;
+template <class T, int DIM> __device__ __forceinline__ void restrict_faces_row(const RowArgs& a, const int* rows, long long r) {
+  const int* row = rows + 6 * r;
   const DPatch C = a.P[row[1]], F = a.P[row[4]];
   const int d = row[2];
   const T* c = (const T*)a.fbuf + F.off + (BX + d) * F.fs + row[5];
@@ -864,6 +865,23 @@ template <class T, int DIM> __global__ void k_restrict_faces(RowArgs a) {
     s = tree4((double)c[0], (double)c[o1], (double)c[o2], (double)c[o1 + o2]) * 0.25;
   }
   ((T*)a.cbuf)[C.off + (BX + d) * C.fs + row[3]] = (T)s;
+}
+
+// the reflux and restriction of a fine level into its parent in one launch:
+// block ranges L.b[k] .. L.b[k+1] of TPB rows take list k (reflux cells,
+// reflux faces, restriction cells, restriction faces). The four write disjoint
+// coarse positions (reflux only uncovered cells and faces that touch no
+// covered cell, restriction the covered cells and the faces of the fine
+// region's closure) and none reads what another writes.
+template <class T, int DIM> __global__ void __launch_bounds__(TPB) k_reflux_restrict(RowArgs a, RRLists L) {
+  const unsigned b = blockIdx.x;
+  const int k = b < L.b[1] ? 0 : (b < L.b[2] ? 1 : (b < L.b[3] ? 2 : 3));
+  const long long r = (long long)(b - L.b[k]) * TPB + threadIdx.x;
+  if (r >= L.n[k]) return;
+  if (k == 0) reflux_cells_row<T, DIM>(a, L.rows[0], r);
+  else if (k == 1) reflux_faces_row<T, DIM>(a, L.rows[1], r);
+  else if (k == 2) restrict_cells_row<T, DIM>(a, L.rows[2], r);
+  else restrict_faces_row<T, DIM>(a, L.rows[3], r);
 }
 
 // ------------------------------------------------------------------ CFL
@@ -1055,8 +1073,6 @@ template <class T, int DIM> struct Impl {
     k_##NAME<T, DIM><<<(unsigned)a.nrows, FILL_TPB, 0, s>>>(a);                          \
     if (nl) ++*nl;                                                                      \
   }
-  AMRK_BOXES(prolong_cells)
-  AMRK_BOXES(prolong_faces)
   AMRK_BOXES(fill_bc_cells)
   AMRK_BOXES(fill_bc_faces)
 #undef AMRK_BOXES
@@ -1094,11 +1110,20 @@ template <class T, int DIM> struct Impl {
   AMRK_BOXES(transfer_faces)
 #undef AMRK_BOXES
   AMRK_ROWS(closure)
-  AMRK_ROWS(reflux_cells)
-  AMRK_ROWS(reflux_faces)
-  AMRK_ROWS(restrict_cells)
-  AMRK_ROWS(restrict_faces)
 #undef AMRK_ROWS
+  static void prolong(const RowArgs& c, const RowArgs& f, cudaStream_t s, int* nl) {
+    if (!c.nrows && !f.nrows) return;
+    k_prolong<T, DIM><<<(unsigned)(c.nrows + f.nrows), FILL_TPB, 0, s>>>(c, f);
+    if (nl) ++*nl;
+  }
+  static void reflux_restrict(const RowArgs& a, const RRLists& lists, cudaStream_t s, int* nl) {
+    RRLists L = lists;
+    L.b[0] = 0;
+    for (int k = 0; k < 4; ++k) L.b[k + 1] = L.b[k] + (unsigned)cdiv(L.n[k], TPB);
+    if (!L.b[4]) return;
+    k_reflux_restrict<T, DIM><<<L.b[4], TPB, 0, s>>>(a, L);
+    if (nl) ++*nl;
+  }
   static void cfl(const CflArgs& a, cudaStream_t s, int* nl) {
     long long n = 1;
     for (int d = 0; d < DIM; ++d) n *= a.maxn[d];
@@ -1203,26 +1228,29 @@ template <class T, int DIM> struct Impl {
     if (nl) ++*nl;
   }
   // registers recomputed from the state read by the advance (fused path, 3D)
+  // one launch per register side: the face rows' blocks, then the edge rows'
   static void reg_coarse_rc(const RowArgs& f, const RowArgs& e, const double* idx, double gamma, cudaStream_t s,
                             int* nl) {
     if (DIM != 3) return;
-    if (f.nrows) { k_regrc_coarse_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
-    if (e.nrows) { k_regrc_coarse_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+    const unsigned nbf = (unsigned)cdiv(f.nrows, 128), nbe = (unsigned)cdiv(e.nrows, 128);
+    if (!(nbf + nbe)) return;
+    k_regrc_coarse<T><<<nbf + nbe, 128, 0, s>>>(f, e, nbf, gamma, idx[0], idx[1], idx[2]);
+    if (nl) ++*nl;
   }
   static void reg_fine_rc(const RowArgs& f, const RowArgs& e, const double* idx, double gamma, cudaStream_t s,
                           int* nl) {
     if (DIM != 3) return;
-    if (f.bnd) {  // from the fine advance's boundary capture
-      if (f.nrows) { k_regcap_fine_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
-      if (e.nrows) { k_regcap_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
-      return;
-    }
-    if (f.nrows) { k_regrc_fine_faces<T><<<cdiv(f.nrows, 128), 128, 0, s>>>(f, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
-    if (e.nrows) { k_regrc_fine_edges<T><<<cdiv(e.nrows, 128), 128, 0, s>>>(e, gamma, idx[0], idx[1], idx[2]); if (nl) ++*nl; }
+    const unsigned nbf = (unsigned)cdiv(f.nrows, 128), nbe = (unsigned)cdiv(e.nrows, 128);
+    if (!(nbf + nbe)) return;
+    if (f.bnd)  // from the fine advance's boundary capture
+      k_regcap_fine<T><<<nbf + nbe, 128, 0, s>>>(f, e, nbf, gamma, idx[0], idx[1], idx[2]);
+    else
+      k_regrc_fine<T><<<nbf + nbe, 128, 0, s>>>(f, e, nbf, gamma, idx[0], idx[1], idx[2]);
+    if (nl) ++*nl;
   }
   static const Ops* ops() {
-    static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong_cells,
-                          prolong_faces, fill_bc_cells, fill_bc_faces, reflux_cells, reflux_faces, restrict_cells, restrict_faces, cfl, io,
+    static const Ops o = {advance, reg_coarse, reg_fine, fill_runs, prolong, fill_bc_cells, fill_bc_faces,
+                          reflux_restrict, cfl, io,
                           io_all, sizeof(T), prepare, advance_fused, reg_coarse_rc, reg_fine_rc, flag, transfer_cells,
                           transfer_faces, closure, advance_queue, flag_dense};
     return &o;
