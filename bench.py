@@ -689,6 +689,33 @@ def cpu_oracle_rate(pb, steps=1):
     return (s.cell_updates() - c0) / t, t
 
 
+def _oracle_one_step(n_psize):
+    """One oracle coarse step of the n^3 blast in psize^3 patches, in a process
+    of its own: (cell updates, seconds of the step)."""
+    from paper_1110_1616_gb300 import inputs
+    from oracle import OracleSim
+    n, psize = n_psize
+    pb = inputs.blast_3d(n, psize)
+    s = OracleSim(pb.dim, pb.base, pb.patches, pb.nlev, gamma=pb.gamma, cfl=pb.cfl)
+    s.set_state(pb.state)
+    c0 = s.cell_updates()
+    t0 = time.perf_counter()
+    s.step()
+    return s.cell_updates() - c0, time.perf_counter() - t0
+
+
+def cpu_oracle_rate_all_cores(n, psize):
+    """The oracle as it stands on every host core this process may use: one
+    process per core (spawned, so none inherits the GPU context), each taking
+    one coarse step of its own copy of the workload at once; the rate is the
+    cell updates of all of them over the longest step."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_one_step, [(n, psize)] * cores)
+    return sum(c for c, _ in res) / max(t for _, t in res), cores, max(t for _, t in res)
+
+
 def run_reference(args, world, rank):
     """The oracle, as it stands, on the host cores: each step is one coarse step
     of a bounded sample of the workload (the same blast physics and 16^3 patches
@@ -832,6 +859,10 @@ def main():
         rate, t = cpu_oracle_rate(pb, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "1 coarse step of the same %d^3 blast, single-threaded FP64 (%.1f s)" % (args.n, t)}
+        rate_all, cores, t_all = cpu_oracle_rate_all_cores(args.n, args.psize)
+        cpu["all_cores"] = {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "one process per host core, each 1 coarse step of its own copy of the "
+                                      "%d^3 blast (FP64, the longest step %.1f s)" % (args.n, t_all)}
     barrier(world)
     if rank != 0:
         return
