@@ -129,3 +129,29 @@ def test_tile_choice_errors():
         ctx.set_option(A.OPT_ZCHUNK, -2)
     fp64 = A.context_for(pb, precision=A.FP64)
     assert fp64.tile_choice(0, 0) == (-1, 0)  # staged kernels by default in FP64
+
+
+@pytest.mark.parametrize("zlen", [3, 8])
+def test_zchunk_bounded_domain_with_floors(zlen):
+    """The down-scaled shock clump (inflow and outflow boundaries, 3 levels,
+    floors on: the recovery's floor instances of the fused kernel), mixed
+    precision: chunks give the whole-column result bit for bit, and the floor
+    counts agree."""
+    pb = inputs.shock_clump_3d_small(16, 3)
+
+    def make(z):
+        import torch
+        s = torch.cuda.Stream()
+        ctx = A.context_for(pb, precision=A.MIXED, strict_fp64=True, stream=s.cuda_stream)
+        ctx.set_option(A.OPT_ZCHUNK, z)
+        ctx.set_floors(1e-8, 1e-8)
+        ctx.alloc_arena()
+        torch.cuda.synchronize()
+        ctx.load_state(pb.state)
+        return ctx
+
+    a, b = make(0), make(zlen)
+    da, db = a.step(3), b.step(3)
+    assert np.array_equal(da, db)
+    assert a.query(A.Q_FLOOR_EVENTS) == b.query(A.Q_FLOOR_EVENTS)
+    assert_same(pb, a, b)
