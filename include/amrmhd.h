@@ -516,8 +516,10 @@ enum {
                               before it runs), 0 the whole column, n in 1..4096 chunks of n planes
                               (each chunk restarts the z march 2 planes below its first plane: more
                               CTAs with shorter marches, for levels of few or tall patches, at the cost
-                              of recomputed planes). The results are the same bit for bit for every
-                              length. May be changed between steps (it is read at the next launch or
+                              of recomputed planes), -2 whole columns except those of the launch's last
+                              partial wave of resident CTAs, which run as two halves each when they
+                              fill at most half of that wave (a level of many columns). The results
+                              are the same bit for bit for every choice. May be changed between steps (it is read at the next launch or
                               graph capture). */
 };
 amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
@@ -525,7 +527,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value);
 /* Autotuner of the fused 3D advance: for every level, and separately for its
  * interior-only advance and (above level 0) its advance with 2 extended ghost
  * layers (sub-step 1), times `trials` advances with each tile variant
- * (AMRMHD_OPT_TILE 0..4) and each z chunk (AMRMHD_OPT_ZCHUNK 0, 4, 8 and 16 where
+ * (AMRMHD_OPT_TILE 0..4) and each z chunk (AMRMHD_OPT_ZCHUNK 0, -2, 4, 8 and 16 where
  * shorter than the level's column) on the current state with CUDA events and
  * keeps the fastest pair (used while AMRMHD_OPT_TILE, respectively
  * AMRMHD_OPT_ZCHUNK, is -1; amrmhd_tile_choice reads it). The state is not changed: an
@@ -541,7 +543,8 @@ amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles);
  * interior-only advance, kind 1 its advance with 2 extended ghost layers
  * (levels above 0). *tile (host) receives the tile variant (AMRMHD_OPT_TILE
  * numbering; -1 where the staged kernels advance the level), *zlen (host) the z
- * planes per CTA (0: the whole column), both after the options and the
+ * planes per CTA (AMRMHD_OPT_ZCHUNK numbering: 0 the whole column, -2 the last
+ * partial wave's columns halved), both after the options and the
  * autotuner's choice. The paper is silent on launch shapes (they are this
  * implementation's mapping of a level's grids onto the GPU). Errors:
  * AMRMHD_ESTATE without a hierarchy; AMRMHD_EINVAL for a null pointer, a level

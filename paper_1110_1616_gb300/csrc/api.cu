@@ -93,6 +93,7 @@ LevelArgs level_args(amrmhd_ctx* ctx, int l, const double* dtp, double dtscale, 
   a.gamma = ctx->cfg.gamma;
   a.w = w;
   a.zlen = 0;
+  a.tail = 0;
   a.bnd = (l > 0 && ctx->bnd_elems > 0) ? (void*)(ctx->arena + ctx->o_bnd) : nullptr;
   a.nbr = nullptr;
   a.fl = ctx->floors();
@@ -737,7 +738,7 @@ amrmhd_status amrmhd_set_option(amrmhd_ctx* ctx, int32_t option, int64_t value) 
   if (option == AMRMHD_OPT_ADVANCE && value >= 0 && value <= 3) ctx->opt_advance = value;
   else if (option == AMRMHD_OPT_GRAPH && (value == 0 || value == 1)) ctx->opt_graph = value;
   else if (option == AMRMHD_OPT_TILE && value >= -1 && value <= 4) ctx->opt_tile = value;
-  else if (option == AMRMHD_OPT_ZCHUNK && value >= -1 && value <= 4096) ctx->opt_zchunk = value;
+  else if (option == AMRMHD_OPT_ZCHUNK && value >= -2 && value <= 4096) ctx->opt_zchunk = value;
   else if (option == AMRMHD_OPT_CONCURRENT && (value == 0 || value == 1)) ctx->opt_concurrent = value;
   else if (option == AMRMHD_OPT_HOST_IO && (value == 0 || value == 1)) ctx->opt_host_io = value;
   else if (option == AMRMHD_OPT_DIRECT_HALO && (value == 0 || value == 1)) ctx->opt_direct_halo = value;
@@ -1586,14 +1587,15 @@ amrmhd_status amrmhd_autotune(amrmhd_ctx* ctx, int32_t trials, int32_t* tiles) {
     // sub-step 1 of a level above 0 advances 2 extended ghost layers, sub-step 2
     // (and level 0) the interior only: each gets its own tile and z chunk (the
     // whole column, or 4, 8 or 16 planes per CTA: shorter marches in more
-    // CTAs for levels of few or tall patches)
+    // CTAs for levels of few or tall patches; or whole columns with those of
+    // the launch's last partial wave halved, for a level of many columns)
     for (int s = 1; s <= (l > 0 ? 2 : 1); ++s) {
       const int wi = (l > 0 && s == 1) ? 1 : 0;
       float best = 0.0f;
       int bv = -1, bz = 0;
       const int ez = ctx->lev[l].maxn[2] + (wi ? 4 : 0);
-      static const int zlens[4] = {0, 4, 8, 16};
-      for (int k = 0; k < 20; ++k) {
+      static const int zlens[5] = {0, -2, 4, 8, 16};
+      for (int k = 0; k < 25; ++k) {
         const int v = k % 5, zl = zlens[k / 5];
         if (zl > 0 && zl >= ez) continue;  // one chunk: the whole column, timed already
         ctx->tile_level[l][wi] = v;

@@ -91,7 +91,8 @@ struct amrmhd_ctx {
   // and a test switch that withholds one fill signal (the wait times out)
   int64_t opt_queue = 0, opt_queue_tile = 3, opt_queue_withhold = 0, opt_queue_balance = 1;
   // z planes per CTA of the fused advance: -1 the autotuned length per level (else
-  // the whole column), 0 the whole column, n > 0 chunks of n planes
+  // the whole column), 0 the whole column, -2 whole columns with those of the
+  // launch's last partial wave halved, n > 0 chunks of n planes
   int64_t opt_zchunk = -1;
   // density and pressure floors (0: off) and the device count of their raises
   double floor_rho = 0.0, floor_p = 0.0;
@@ -122,7 +123,8 @@ struct amrmhd_ctx {
   // autotuned fused tile per level, for the interior-only advance ([0]) and the
   // advance with 2 extended ghost layers ([1]) (-1: none)
   std::vector<std::array<int, 2>> tile_level;
-  // autotuned z planes per CTA, same indexing (0: the whole column)
+  // autotuned z planes per CTA, same indexing (0: the whole column, -2: the
+  // last partial wave's columns halved)
   std::vector<std::array<int, 2>> zlen_level;
   // the fused tile variant and z chunk of level l's advance with (wi = 1) or
   // without (wi = 0) the extended ghost layers, after options and autotuning
@@ -132,7 +134,7 @@ struct amrmhd_ctx {
     return v;
   }
   int zlen_of(int l, int wi) const {
-    if (opt_zchunk >= 0) return (int)opt_zchunk;
+    if (opt_zchunk != -1) return (int)opt_zchunk;
     return (int)zlen_level.size() > l ? zlen_level[l][wi] : 0;
   }
   // the fused 3D kernel: forced (3), or by default (0) in mixed precision where it is

@@ -43,7 +43,9 @@ struct LevelArgs {
   double idx[3];   // 1/dx of this level
   double gamma;
   int w;           // extra ghost layers updated (0 or 2)
-  int zlen;        // fused 3D advance: z planes per CTA (0: the whole column)
+  int zlen;        // fused 3D advance: z planes per CTA (0: the whole column; -2: whole
+                   // columns, those of the launch's last partial wave halved)
+  int tail;        // set by the fused launcher: the last `tail` columns run as two halves
   // boundary capture buffer (fused 3D advance of a level > 0): the fluxes and
   // EMFs of every patch's boundary planes are written at P.boff; nullptr: none
   void* bnd;

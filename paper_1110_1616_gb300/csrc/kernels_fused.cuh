@@ -160,7 +160,7 @@ __device__ __forceinline__ void bnd_store_edge(const LevelArgs& a, const DPatch&
 // of the CTA calls it with the same arguments.
 template <class T, int VAR, int MODE, bool FL = false>
 __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int tile, int ntx, int zc,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, bool halves = false) {
   constexpr bool CAP = MODE == 1, DH = MODE == 2;
   using S = FusedSmem<T, FusedCfg<VAR>::TX, FusedCfg<VAR>::TY>;
   constexpr int TX = S::TX, TY = S::TY, PX = S::PX, QX = S::QX;
@@ -175,7 +175,10 @@ __device__ __forceinline__ void fused_tile(const LevelArgs& a, int pslot, int ti
   const int xlo = 4 - w, xhi = P.n[0] + 4 + w, ylo = 4 - w, yhi = P.n[1] + 4 + w;
   const int zlo = 4 - w, zhi = P.n[2] + 4 + w;
   const int x0 = xlo + (tile % ntx) * TX, y0 = ylo + (tile / ntx) * TY;
-  const int zs = zlo + zc * a.zlen, ze = a.zlen > 0 ? min(zs + a.zlen, zhi) : zhi;
+  // the chunk: a.zlen planes from zlo + a.zlen zc, the whole column (a.zlen
+  // 0), or with halves its lower (zc 0) or upper (zc 1) half
+  const int zl = halves ? (zhi - zlo + 1) / 2 : a.zlen;
+  const int zs = zlo + zc * zl, ze = zl > 0 ? min(zs + zl, zhi) : zhi;
   if (x0 >= xhi || y0 >= yhi || zs >= zhi) return;
   // a face or edge plane shared by two chunks (ze of one, zs of the next) is
   // captured by the upper chunk only
@@ -514,7 +517,23 @@ template <class T, int VAR, int MODE, bool FL = false>
 __global__ void __launch_bounds__(FusedCfg<VAR>::NT, sizeof(T) == 4 ? fused_ctas_fp32<VAR>() : 1)
     k_advance3d_fused(LevelArgs a, int ntx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_tile<T, VAR, MODE, FL>(a, blockIdx.y, blockIdx.x, ntx, blockIdx.z, smem_raw);
+  int pslot = blockIdx.y, tile = blockIdx.x, zc = blockIdx.z;
+  bool halves = false;
+  if (a.tail > 0) {
+    // one-dimensional grid over the columns (patch-major): the first ones
+    // whole, the last a.tail ones as two halves each, so that the launch's last
+    // partial wave holds half-length marches
+    constexpr int TY = FusedCfg<VAR>::TY;
+    const int ntiles = ntx * ((a.maxn[1] + 2 * a.w + TY - 1) / TY);
+    const int full = ntiles * a.npatch - a.tail;
+    const int item = blockIdx.x;
+    const int col = item < full ? item : full + (item - full) / 2;
+    pslot = col / ntiles;
+    tile = col % ntiles;
+    zc = item < full ? 0 : (item - full) % 2;
+    halves = item >= full;
+  }
+  fused_tile<T, VAR, MODE, FL>(a, pslot, tile, ntx, zc, smem_raw, halves);
 }
 
 // ---------------------------------------------------------------- device work queue

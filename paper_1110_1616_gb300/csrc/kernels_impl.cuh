@@ -1201,13 +1201,43 @@ template <class T, int DIM> struct Impl {
     else launch_queue<3>(q, s);
     if (nl) ++*nl;
   }
-  template <int V> static void launch_fused(const LevelArgs& a, cudaStream_t s) {
+  // resident CTAs of a fused instance on the whole GPU
+  template <int V, int MODE, bool FL> static long long fused_slots() {
+    static const long long slots = [] {
+      int dev = 0, sms = 152, per = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_advance3d_fused<T, V, MODE, FL>, FusedCfg<V>::NT,
+                                                    fused_smem<V>());
+      return (long long)sms * (per > 0 ? per : 1);
+    }();
+    return slots;
+  }
+  template <int V> static void launch_fused(const LevelArgs& a0, cudaStream_t s) {
     constexpr int TX = FusedCfg<V>::TX, TY = FusedCfg<V>::TY;
+    LevelArgs a = a0;
     const int ex = a.maxn[0] + 2 * a.w, ey = a.maxn[1] + 2 * a.w;
     const int ntx = (ex + TX - 1) / TX, nty = (ey + TY - 1) / TY;
-    const int ez = a.maxn[2] + 2 * a.w, nzc = a.zlen > 0 ? (ez + a.zlen - 1) / a.zlen : 1;
-    const dim3 g(ntx * nty, a.npatch, nzc);
     const bool fl = a.fl.rho > 0.0 || a.fl.p > 0.0;  // floors (the host never combines them with DH)
+    dim3 g;
+    a.tail = 0;
+    if (a.zlen == -2) {
+      // whole columns; those of the last partial wave halved when they fill
+      // at most half of it (else whole columns throughout)
+      a.zlen = 0;
+      const long long cols = (long long)ntx * nty * a.npatch;
+      const long long slots = fl ? (a.bnd ? fused_slots<V, 1, true>() : fused_slots<V, 0, true>())
+                                 : (a.bnd ? fused_slots<V, 1, false>()
+                                          : (a.nbr && a.w == 0 ? fused_slots<V, 2, false>() : fused_slots<V, 0, false>()));
+      const long long rem = cols % slots;
+      if (cols > slots && rem > 0 && 2 * rem <= slots) a.tail = (int)rem;
+    }
+    if (a.tail > 0) {
+      g = dim3((unsigned)((long long)ntx * nty * a.npatch + a.tail));
+    } else {
+      const int ez = a.maxn[2] + 2 * a.w, nzc = a.zlen > 0 ? (ez + a.zlen - 1) / a.zlen : 1;
+      g = dim3(ntx * nty, a.npatch, nzc);
+    }
     if (fl && a.bnd) k_advance3d_fused<T, V, 1, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
     else if (fl) k_advance3d_fused<T, V, 0, true><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);
     else if (a.bnd) k_advance3d_fused<T, V, 1><<<g, FusedCfg<V>::NT, fused_smem<V>(), s>>>(a, ntx);

@@ -103,6 +103,7 @@ extern "C" amrmhd_status amrmhd_advance_patch_noalloc(const float* u_in, float* 
   a.nbr = nullptr;
   a.w = w;
   a.zlen = 0;
+  a.tail = 0;
   if (dim == 3) amrk_noalloc::Impl<float, 3>::advance(a, s, nullptr);
   else amrk_noalloc::Impl<float, 2>::advance(a, s, nullptr);
   if (cudaGetLastError() != cudaSuccess) return AMRMHD_ECUDA;

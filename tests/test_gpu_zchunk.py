@@ -108,7 +108,7 @@ def test_autotune_chooses_a_chunk_and_keeps_results():
     for l in range(pb.nlev):
         for kind in ((0, 1) if l > 0 else (0,)):
             t, z = ctx.tile_choice(l, kind)
-            assert 0 <= t <= 4 and z in (0, 4, 8, 16), (l, kind, t, z)
+            assert 0 <= t <= 4 and z in (0, -2, 4, 8, 16), (l, kind, t, z)
     ctx.step(3)
     ref, _ = run(pb, A.MIXED, 3, OPT_TILE=2, OPT_ZCHUNK=0)
     sa, sb = ctx.read_state(), ref.read_state()
@@ -126,7 +126,7 @@ def test_tile_choice_errors():
     with pytest.raises(A.AmrmhdError):
         ctx.tile_choice(0, 2)
     with pytest.raises(A.AmrmhdError):
-        ctx.set_option(A.OPT_ZCHUNK, -2)
+        ctx.set_option(A.OPT_ZCHUNK, -3)
     fp64 = A.context_for(pb, precision=A.FP64)
     assert fp64.tile_choice(0, 0) == (-1, 0)  # staged kernels by default in FP64
 
@@ -155,3 +155,29 @@ def test_zchunk_bounded_domain_with_floors(zlen):
     assert np.array_equal(da, db)
     assert a.query(A.Q_FLOOR_EVENTS) == b.query(A.Q_FLOOR_EVENTS)
     assert_same(pb, a, b)
+
+
+def test_tail_halves_uniform_blast_128():
+    """AMRMHD_OPT_ZCHUNK -2 on the 128^3 blast (1024 columns of the 16x8 tile,
+    3.4 waves at two CTAs per SM): the columns of the last partial wave run as
+    two halves each; the result is the whole-column one bit for bit."""
+    pb = inputs.blast_3d(128, 16)
+    ref, dref = run(pb, A.MIXED, 2, OPT_TILE=2, OPT_ZCHUNK=0)
+    got, dgot = run(pb, A.MIXED, 2, OPT_TILE=2, OPT_ZCHUNK=-2)
+    assert np.array_equal(dref, dgot)
+    assert_same(pb, ref, got)
+    assert got.tile_choice(0, 0) == (2, -2)
+
+
+def test_tail_halves_with_boundary_capture():
+    """A refined level of 64 patches of 16^3 (384 columns in its extended
+    sub-step, so a partial last wave): the halved columns' boundary fluxes and
+    EMFs reach the registers once; the result is the whole-column one bit for
+    bit."""
+    base = (64, 64, 64)
+    p3 = inputs.tile(0, (0, 0, 0), base, 16, 3) + inputs.tile(1, (32, 32, 32), (96, 96, 96), 16, 3)
+    pb = inputs.Problem("b3", 3, base, p3, 2, {0: inputs.blast_3d(64, 16).state[0], 1: inputs.blast_3d(128, 16).state[0]})
+    ref, dref = run(pb, A.MIXED, 2, OPT_TILE=2, OPT_ZCHUNK=0)
+    got, dgot = run(pb, A.MIXED, 2, OPT_TILE=2, OPT_ZCHUNK=-2)
+    assert np.array_equal(dref, dgot)
+    assert_same(pb, ref, got)
