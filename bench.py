@@ -36,7 +36,7 @@ TILE_NAMES = {0: "16x16", 1: "16x16/512 threads", 2: "16x8", 3: "8x8", 4: "12x12
 # DRAM bytes (read + write) of one launch of the fused advance (direct halo
 # reads, 16x8 tile) on the 128^3 blast in 16^3 patches, mixed precision, from
 # one ncu capture of that launch (profiles/k_advance3d_fused_blast3d_128.md)
-FUSED_TRAFFIC_BYTES = 242.60e6  # 167.53 MB read + 75.07 MB written
+FUSED_TRAFFIC_BYTES = 242.48e6  # 167.31 MB read + 75.17 MB written
 # FP32 lanes per SM (the derived ALU peak: SMs x lanes x 2 (FMA) x max SM clock)
 FP32_LANES = 128
 
