@@ -219,3 +219,41 @@ def test_regrid_clustering_bit_exact_vs_oracle(name, dim, base, patches, bc):
             got = c.regrid_boxes(l, fl)
             exp = o.regrid_boxes(l, fl)
             assert np.array_equal(got, exp), (l, got[:4], exp[:4])
+
+
+def test_launch_shape_options_and_async_calls_on_the_host():
+    """The fused advance's launch shape as the options set it (no device
+    needed: the choice is host state), and the stream-ordered step and sync
+    refused before an arena is bound."""
+    base = (32, 32, 32)
+    patches = inputs.tile(0, (0, 0, 0), base, 16, 3) + inputs.tile(1, (16, 16, 16), (48, 48, 48), 16, 3)
+    c = A.Context(A.make_config(3, base, precision=A.MIXED))
+    with pytest.raises(A.AmrmhdError) as e:
+        c.tile_choice(0, 0)  # no hierarchy yet
+    assert e.value.status == A.ESTATE
+    c.set_hierarchy(patches)
+    assert c.tile_choice(0, 0) == (2, 0) and c.tile_choice(1, 1) == (2, 0)  # 16x8, whole columns
+    c.set_option(A.OPT_TILE, 3)
+    c.set_option(A.OPT_ZCHUNK, -2)
+    assert c.tile_choice(1, 0) == (3, -2)
+    c.set_option(A.OPT_ZCHUNK, 8)
+    assert c.tile_choice(1, 1) == (3, 8)
+    for bad in ((2, 0), (0, 2), (-1, 0)):
+        with pytest.raises(A.AmrmhdError) as e:
+            c.tile_choice(*bad)
+        assert e.value.status == A.EINVAL
+    for bad in (-3, 4097):
+        with pytest.raises(A.AmrmhdError) as e:
+            c.set_option(A.OPT_ZCHUNK, bad)
+        assert e.value.status == A.EINVAL
+    with pytest.raises(A.AmrmhdError) as e:
+        c.step_async(1)
+    assert e.value.status == A.ESTATE
+    with pytest.raises(A.AmrmhdError) as e:
+        c.sync()
+    assert e.value.status == A.ESTATE
+    f = A.Context(A.make_config(3, base))  # FP64: the staged kernels by default
+    f.set_hierarchy(patches)
+    assert f.tile_choice(0, 0) == (-1, 0)
+    f.set_option(A.OPT_ADVANCE, 3)  # the fused kernel in FP64: the 8x8 tile by default
+    assert f.tile_choice(0, 0) == (3, 0)
