@@ -6,11 +6,14 @@ Workload: 3D periodic blast wave, 128^3 cells split into 512 patches of 16^3
 is one coarse step of the whole hot path: CFL reduction, the level advance
 (MUSCL-Hancock + minmod, HLLD, constrained transport) of every patch, replayed
 as one CUDA graph; the level tiles the periodic domain with equal patches, so
-the advance reads its halo from the neighbour patches and no ghost fill runs. The headline runs the mixed-precision path (FP32
-stencil, FP64 primitive recovery, registers, dt). Also reported: the FP64 path,
-the FP64 one-patch-per-launch baseline, the level advance alone against the
-HBM roofline, an end-to-end run through the C ABI with host buffers, and the
-CPU oracle.
+the advance reads its halo from the neighbour patches and no ghost fill runs.
+The headline runs the mixed-precision path (FP32 stencil, FP64 primitive
+recovery, registers, dt). Also reported: the FP64 path, the FP64
+one-patch-per-launch baseline, the level advance alone against the HBM and
+FP32 rooflines, end-to-end runs through the C ABI with the state exchanged with
+pinned host memory every step (pipelined and serial), the CPU oracle on one
+core and on every core, and the extra workloads (deep AMR clumps, shock clump,
+the paper's cylinder, weak scaling over SM partitions, the adjoint).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
