@@ -718,7 +718,8 @@ __device__ __forceinline__ const Floors* rc_floors(const RowArgs& a) {
 // RowArgs.fbuf = the state the level's advance read (for the coarse side the
 // coarse level, for the fine side the fine level); dt = *dtp * dtscale.
 template <class T>
-__device__ __forceinline__ void regrc_coarse_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regrc_coarse_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[1]];
@@ -731,7 +732,8 @@ __device__ __forceinline__ void regrc_coarse_faces_row(const RowArgs& a, long lo
 }
 
 template <class T>
-__device__ __forceinline__ void regrc_coarse_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regrc_coarse_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[1]];
@@ -741,7 +743,8 @@ __device__ __forceinline__ void regrc_coarse_edges_row(const RowArgs& a, long lo
 }
 
 template <class T>
-__device__ __forceinline__ void regrc_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regrc_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[5]];
@@ -765,7 +768,8 @@ __device__ __forceinline__ void regrc_fine_faces_row(const RowArgs& a, long long
 }
 
 template <class T>
-__device__ __forceinline__ void regrc_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regrc_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[4]];
@@ -783,7 +787,8 @@ __device__ __forceinline__ void regrc_fine_edges_row(const RowArgs& a, long long
 // advance (the same fluxes and EMFs the recompute kernels above evaluate); a
 // face or edge off the boundary planes (none by construction) is recomputed
 template <class T>
-__device__ __forceinline__ void regcap_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regcap_fine_faces_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 7 * r;
   const DPatch P = a.P[row[5]];
@@ -821,7 +826,8 @@ __device__ __forceinline__ void regcap_fine_faces_row(const RowArgs& a, long lon
 }
 
 template <class T>
-__device__ __forceinline__ void regcap_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy, double iz) {
+__device__ __forceinline__ void regcap_fine_edges_row(const RowArgs& a, long long r, double gamma, double ix, double iy,
+                                      double iz) {
   if (r >= a.nrows) return;
   const int* row = a.rows + 6 * r;
   const DPatch P = a.P[row[4]];

@@ -784,7 +784,8 @@ template <class T, int DIM> __global__ void k_closure(RowArgs a) {
 
 // ------------------------------------------------------------------ reflux and restriction
 // rows (l, qc, Lcell, f0..f5); R = (S1 + S2) - C per C/F face, applied in slot order
-template <class T, int DIM> __device__ __forceinline__ void reflux_cells_row(const RowArgs& a, const int* rows, long long r) {
+template <class T, int DIM>
+__device__ __forceinline__ void reflux_cells_row(const RowArgs& a, const int* rows, long long r) {
   const int* row = rows + 9 * r;
   const DPatch P = a.P[row[1]];
   T* U = (T*)a.cbuf + P.off + row[2];
@@ -805,7 +806,8 @@ template <class T, int DIM> __device__ __forceinline__ void reflux_cells_row(con
 }
 
 // rows (l, qc, d, Lface, e0..e3): B += +e0/dx_t1 - e1/dx_t1 - e2/dx_t2 + e3/dx_t2
-template <class T, int DIM> __device__ __forceinline__ void reflux_faces_row(const RowArgs& a, const int* rows, long long r) {
+template <class T, int DIM>
+__device__ __forceinline__ void reflux_faces_row(const RowArgs& a, const int* rows, long long r) {
   const int* row = rows + 8 * r;
   const DPatch P = a.P[row[1]];
   const int d = row[2];
@@ -824,7 +826,8 @@ template <class T, int DIM> __device__ __forceinline__ void reflux_faces_row(con
 }
 
 // rows (l, qc, Lcell, pf, Lchild0)
-template <class T, int DIM> __device__ __forceinline__ void restrict_cells_row(const RowArgs& a, const int* rows, long long r) {
+template <class T, int DIM>
+__device__ __forceinline__ void restrict_cells_row(const RowArgs& a, const int* rows, long long r) {
   const int* row = rows + 5 * r;
   const DPatch C = a.P[row[1]], F = a.P[row[3]];
   T* dst = (T*)a.cbuf + C.off + row[2];
@@ -848,7 +851,8 @@ template <class T, int DIM> __device__ __forceinline__ void restrict_cells_row(c
 }
 
 // rows (l, qc, d, Lface, pf, Lfine0)
-template <class T, int DIM> __device__ __forceinline__ void restrict_faces_row(const RowArgs& a, const int* rows, long long r) {
+template <class T, int DIM>
+__device__ __forceinline__ void restrict_faces_row(const RowArgs& a, const int* rows, long long r) {
   const int* row = rows + 6 * r;
   const DPatch C = a.P[row[1]], F = a.P[row[4]];
   const int d = row[2];
